@@ -1,0 +1,379 @@
+"""Oracle: plain FP64 CPU restatement of the method (test infrastructure only).
+
+Only the test-suite, the smoke check and the CPU-baseline leg of the benchmark
+import this package.  It loads `liboracle.so`, built from the C sources beside
+this file, and shares nothing with the CUDA library.
+
+All arrays are numpy arrays in the canonical layouts of `oracle.h`:
+links complex128 [V, 4, 3, 3]; full spinors complex128 [V, 4, 3]; half spinors
+complex128 [V/2, 4, 3]; algebra fields float64 [V, 4, 8].
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_SOURCES = sorted(f for f in os.listdir(_HERE) if f.endswith(".c"))
+
+
+def build(force=False):
+    """Compile liboracle.so with gcc (plain C11, -O2)."""
+    srcs = [os.path.join(_HERE, f) for f in _SOURCES]
+    hdr = os.path.join(_HERE, "oracle.h")
+    if not force and os.path.exists(_SO):
+        newest = max(os.path.getmtime(p) for p in srcs + [hdr])
+        if os.path.getmtime(_SO) >= newest:
+            return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", *srcs, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = ctypes.CDLL(_SO)
+        _declare(_lib)
+    return _lib
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_L = ctypes.c_long
+
+
+class TrajParams(ctypes.Structure):
+    _fields_ = [
+        ("beta", _D), ("kappa", _D), ("tau", _D),
+        ("n_md", _I), ("n_gauge", _I), ("filter_k", _I),
+        ("n_t", _I), ("n_max", _I),
+        ("tol_md", _D), ("tol_action", _D),
+        ("b", _P), ("c", _P), ("alpha", _D),
+    ]
+
+
+class TrajResult(ctypes.Structure):
+    _fields_ = [
+        ("H0", _D), ("H1", _D), ("dH", _D),
+        ("plaq0", _D), ("plaq1", _D),
+        ("accepted", _I), ("cg_iters", _I),
+    ]
+
+
+def _declare(l):
+    sig = {
+        "or_volume": (_L, [_P]),
+        "or_neighbour": (_L, [_P, _L, _I, _I, _P]),
+        "or_site_of_half": (_L, [_P, _I, _L]),
+        "or_gamma": (None, [_I, _P]),
+        "or_gellmann": (None, [_I, _P]),
+        "or_hop": (None, [_P, _P, _P, _P]),
+        "or_hop_eo": (None, [_P, _P, _I, _P, _P]),
+        "or_hop_eo_dag": (None, [_P, _P, _I, _P, _P]),
+        "or_wilson": (None, [_P, _P, _D, _P, _P]),
+        "or_mhat": (None, [_P, _P, _D, _I, _P, _P]),
+        "or_mhat_dag_mhat": (None, [_P, _P, _D, _P, _P]),
+        "or_K": (None, [_P, _P, _D, _I, _P, _P]),
+        "or_cg": (_I, [_P, _P, _D, _P, _P, _D, _I, _P]),
+        "or_mhat_inverse": (_I, [_P, _P, _D, _P, _P, _D, _I]),
+        "or_plaquette_sum": (_D, [_P, _P]),
+        "or_gauge_action": (_D, [_P, _P, _D]),
+        "or_gauge_force": (None, [_P, _P, _D, _D, _P]),
+        "or_pf_action": (_D, [_P, _P, _D, _P, _D]),
+        "or_pf_force": (None, [_P, _P, _D, _P, _D, _D, _P]),
+        "or_hop_force": (None, [_P, _P, _D, _P, _P, _D, _P]),
+        "or_trace_K_brute": (_D, [_P, _P, _D, _I]),
+        "or_trace_H_paths": (_D, [_P, _P, _I]),
+        "or_hopexp_action": (_D, [_P, _P, _D, _I]),
+        "or_hopexp_force": (None, [_P, _P, _D, _I, _D, _P]),
+        "or_poly_K": (None, [_P, _P, _D, _P, _I, _P, _P]),
+        "or_filtered_action": (_D, [_P, _P, _D, _P, _I, _D, _P, _D]),
+        "or_filtered_force": (None, [_P, _P, _D, _P, _I, _D, _P, _D, _D, _P]),
+        "or_expm3": (None, [_P, _P]),
+        "or_update_links": (None, [_P, _P, _P, _D]),
+        "or_reunitarise": (None, [_P, _P]),
+        "or_rotate_link": (None, [_P, _P, _L, _I, _P, _D]),
+        "or_kinetic": (_D, [_P, _P]),
+        "or_trajectory": (_I, [_P, _P, _P, _P, _D, _P, _P, _P, _P]),
+        "or_md_evolve": (None, [_P, _P, _P, _P, _P, _P]),
+        "or_hamiltonian": (_D, [_P, _P, _P, _P, _P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(l, name)
+        f.restype = res
+        f.argtypes = args
+
+
+# ---- helpers -----------------------------------------------------------------
+
+def _dims(L):
+    return (ctypes.c_int * 4)(*[int(v) for v in L])
+
+
+def _c(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def volume(L):
+    return int(np.prod(L))
+
+
+def gamma(mu):
+    g = np.zeros(16, np.complex128)
+    lib().or_gamma(mu, _ptr(g))
+    return g.reshape(4, 4)
+
+
+def gellmann(a):
+    g = np.zeros(9, np.complex128)
+    lib().or_gellmann(a, _ptr(g))
+    return g.reshape(3, 3)
+
+
+def neighbour(L, site, mu, d):
+    s = ctypes.c_int(0)
+    y = lib().or_neighbour(_dims(L), site, mu, d, ctypes.byref(s))
+    return y, s.value
+
+
+def site_of_half(L, parity, h):
+    return lib().or_site_of_half(_dims(L), parity, h)
+
+
+def hop(L, U, psi):
+    U = _c(U, np.complex128); psi = _c(psi, np.complex128)
+    out = np.zeros_like(psi)
+    lib().or_hop(_dims(L), _ptr(U), _ptr(psi), _ptr(out))
+    return out
+
+
+def hop_eo(L, U, out_parity, psi, dagger=False):
+    U = _c(U, np.complex128); psi = _c(psi, np.complex128)
+    out = np.zeros_like(psi)
+    f = lib().or_hop_eo_dag if dagger else lib().or_hop_eo
+    f(_dims(L), _ptr(U), out_parity, _ptr(psi), _ptr(out))
+    return out
+
+
+def wilson(L, U, kappa, psi):
+    U = _c(U, np.complex128); psi = _c(psi, np.complex128)
+    out = np.zeros_like(psi)
+    lib().or_wilson(_dims(L), _ptr(U), kappa, _ptr(psi), _ptr(out))
+    return out
+
+
+def mhat(L, U, kappa, psi, dagger=False):
+    U = _c(U, np.complex128); psi = _c(psi, np.complex128)
+    out = np.zeros_like(psi)
+    lib().or_mhat(_dims(L), _ptr(U), kappa, int(dagger), _ptr(psi), _ptr(out))
+    return out
+
+
+def mdagm(L, U, kappa, psi):
+    U = _c(U, np.complex128); psi = _c(psi, np.complex128)
+    out = np.zeros_like(psi)
+    lib().or_mhat_dag_mhat(_dims(L), _ptr(U), kappa, _ptr(psi), _ptr(out))
+    return out
+
+
+def K(L, U, kappa, psi, dagger=False):
+    U = _c(U, np.complex128); psi = _c(psi, np.complex128)
+    out = np.zeros_like(psi)
+    lib().or_K(_dims(L), _ptr(U), kappa, int(dagger), _ptr(psi), _ptr(out))
+    return out
+
+
+def cg(L, U, kappa, phi, tol=1e-12, max_iter=10000):
+    """Returns (x, iterations, true relative residual); iterations = -1 when
+    max_iter was reached."""
+    U = _c(U, np.complex128); phi = _c(phi, np.complex128)
+    x = np.zeros_like(phi)
+    rel = ctypes.c_double(0)
+    it = lib().or_cg(_dims(L), _ptr(U), kappa, _ptr(phi), _ptr(x), tol,
+                     max_iter, ctypes.byref(rel))
+    return x, it, rel.value
+
+
+def mhat_inverse(L, U, kappa, phi, tol=1e-13):
+    U = _c(U, np.complex128); phi = _c(phi, np.complex128)
+    y = np.zeros_like(phi)
+    lib().or_mhat_inverse(_dims(L), _ptr(U), kappa, _ptr(phi), _ptr(y), tol,
+                          100000)
+    return y
+
+
+def plaquette_sum(L, U):
+    U = _c(U, np.complex128)
+    return lib().or_plaquette_sum(_dims(L), _ptr(U))
+
+
+def gauge_action(L, U, beta):
+    U = _c(U, np.complex128)
+    return lib().or_gauge_action(_dims(L), _ptr(U), beta)
+
+
+def _force_buf(L):
+    return np.zeros((volume(L), 4, 8), np.float64)
+
+
+def gauge_force(L, U, beta):
+    U = _c(U, np.complex128)
+    F = _force_buf(L)
+    lib().or_gauge_force(_dims(L), _ptr(U), beta, 1.0, _ptr(F))
+    return F
+
+
+def pf_action(L, U, kappa, phi, tol=1e-13):
+    U = _c(U, np.complex128); phi = _c(phi, np.complex128)
+    return lib().or_pf_action(_dims(L), _ptr(U), kappa, _ptr(phi), tol)
+
+
+def pf_force(L, U, kappa, phi, tol=1e-13):
+    U = _c(U, np.complex128); phi = _c(phi, np.complex128)
+    F = _force_buf(L)
+    lib().or_pf_force(_dims(L), _ptr(U), kappa, _ptr(phi), tol, 1.0, _ptr(F))
+    return F
+
+
+def hop_force(L, U, kappa, W, Vf):
+    U = _c(U, np.complex128); W = _c(W, np.complex128); Vf = _c(Vf, np.complex128)
+    F = _force_buf(L)
+    lib().or_hop_force(_dims(L), _ptr(U), kappa, _ptr(W), _ptr(Vf), 1.0, _ptr(F))
+    return F
+
+
+def trace_K_brute(L, U, kappa, n):
+    U = _c(U, np.complex128)
+    return lib().or_trace_K_brute(_dims(L), _ptr(U), kappa, n)
+
+
+def trace_H_paths(L, U, length):
+    U = _c(U, np.complex128)
+    return lib().or_trace_H_paths(_dims(L), _ptr(U), length)
+
+
+def hopexp_action(L, U, kappa, k):
+    U = _c(U, np.complex128)
+    return lib().or_hopexp_action(_dims(L), _ptr(U), kappa, k)
+
+
+def hopexp_force(L, U, kappa, k):
+    U = _c(U, np.complex128)
+    F = _force_buf(L)
+    lib().or_hopexp_force(_dims(L), _ptr(U), kappa, k, 1.0, _ptr(F))
+    return F
+
+
+def poly_K(L, U, kappa, c, psi):
+    U = _c(U, np.complex128); psi = _c(psi, np.complex128)
+    c = _c(c, np.float64)
+    out = np.zeros_like(psi)
+    lib().or_poly_K(_dims(L), _ptr(U), kappa, _ptr(c), len(c) - 1, _ptr(psi),
+                    _ptr(out))
+    return out
+
+
+def filtered_action(L, U, kappa, b, alpha, phi, tol=1e-13):
+    U = _c(U, np.complex128); phi = _c(phi, np.complex128)
+    b = _c(b, np.float64)
+    return lib().or_filtered_action(_dims(L), _ptr(U), kappa, _ptr(b),
+                                    len(b) - 1, alpha, _ptr(phi), tol)
+
+
+def filtered_force(L, U, kappa, b, alpha, phi, tol=1e-13):
+    U = _c(U, np.complex128); phi = _c(phi, np.complex128)
+    b = _c(b, np.float64)
+    F = _force_buf(L)
+    lib().or_filtered_force(_dims(L), _ptr(U), kappa, _ptr(b), len(b) - 1,
+                            alpha, _ptr(phi), tol, 1.0, _ptr(F))
+    return F
+
+
+def expm3(A):
+    A = _c(A, np.complex128)
+    E = np.zeros(9, np.complex128)
+    lib().or_expm3(_ptr(A), _ptr(E))
+    return E.reshape(3, 3)
+
+
+def update_links(L, U, P, eps):
+    U = np.array(U, np.complex128, copy=True); P = _c(P, np.float64)
+    lib().or_update_links(_dims(L), _ptr(U), _ptr(P), eps)
+    return U
+
+
+def reunitarise(L, U):
+    U = np.array(U, np.complex128, copy=True)
+    lib().or_reunitarise(_dims(L), _ptr(U))
+    return U
+
+
+def rotate_link(L, U, site, mu, omega, eps):
+    U = np.array(U, np.complex128, copy=True)
+    om = _c(omega, np.float64)
+    lib().or_rotate_link(_dims(L), _ptr(U), site, mu, _ptr(om), eps)
+    return U
+
+
+def kinetic(L, P):
+    P = _c(P, np.float64)
+    return lib().or_kinetic(_dims(L), _ptr(P))
+
+
+def _params(beta, kappa, tau, n_md, n_gauge, filter_k=0, n_t=0, n_max=0,
+            tol_md=1e-12, tol_action=1e-13, b=None, c=None, alpha=0.0):
+    keep = []
+    p = TrajParams(beta=beta, kappa=kappa, tau=tau, n_md=n_md, n_gauge=n_gauge,
+                   filter_k=filter_k, n_t=n_t, n_max=n_max, tol_md=tol_md,
+                   tol_action=tol_action, alpha=alpha)
+    if b is not None:
+        b = _c(b, np.float64); keep.append(b); p.b = b.ctypes.data
+    if c is not None:
+        c = _c(c, np.float64); keep.append(c); p.c = c.ctypes.data
+    return p, keep
+
+
+def hamiltonian(L, U, P, phi, **kw):
+    p, keep = _params(**kw)
+    U = _c(U, np.complex128); P = _c(P, np.float64); phi = _c(phi, np.complex128)
+    return lib().or_hamiltonian(_dims(L), _ptr(U), _ptr(P), _ptr(phi),
+                                ctypes.byref(p))
+
+
+def md_evolve(L, U, P, phi, **kw):
+    p, keep = _params(**kw)
+    U = np.array(U, np.complex128, copy=True)
+    P = np.array(P, np.float64, copy=True)
+    phi = _c(phi, np.complex128)
+    it = ctypes.c_int(0)
+    lib().or_md_evolve(_dims(L), _ptr(U), _ptr(P), _ptr(phi), ctypes.byref(p),
+                       ctypes.byref(it))
+    return U, P
+
+
+def trajectory(L, U, P, eta, u, **kw):
+    """One HMC trajectory.  Returns (U_next, result dict, U_end, P_end)."""
+    p, keep = _params(**kw)
+    U = np.array(U, np.complex128, copy=True)
+    P = _c(P, np.float64); eta = _c(eta, np.complex128)
+    Uo = np.zeros_like(U); Po = np.zeros_like(P)
+    res = TrajResult()
+    lib().or_trajectory(_dims(L), _ptr(U), _ptr(P), _ptr(eta), u,
+                        ctypes.byref(p), ctypes.byref(res), _ptr(Uo), _ptr(Po))
+    out = {f: getattr(res, f) for f, _ in TrajResult._fields_}
+    return U, out, Uo, Po
