@@ -1,0 +1,315 @@
+/*
+ * libhmc: GB300 (sm_103a) hot path of the two-flavour Wilson HMC with the
+ * hopping-parameter expansion as UV filter (Hasenbusch, arXiv:1805.03560).
+ *
+ * C ABI.  Plain pointers and sizes only; no C++ or framework types cross it.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Lattice.  hmc_lattice.L = {Lt, Lx, Ly, Lz}; every extent even and >= 2,
+ *   Lz >= 2; the volume V = Lt Lx Ly Lz < 2^31.  Site (t, x, y, z) has the
+ *   lexicographic index ((t*Lx + x)*Ly + y)*Lz + z; direction mu = 0 is time.
+ *   Parity (t+x+y+z) mod 2, even = 0; the h-th site of a parity is the site of
+ *   that parity with lex >> 1 == h (Vh = V/2 sites per parity).  Fermions are
+ *   antiperiodic in time and periodic in space, the gauge field is periodic
+ *   (Sec. IV).  Chiral gamma basis, gamma_5 = gamma_0 gamma_1 gamma_2 gamma_3
+ *   = diag(-1, -1, 1, 1).
+ *
+ * Canonical layouts (used only by the pack / unpack calls):
+ *   links   complex double [V][4][3][3]   U[site][mu][row][col]
+ *   spinor  complex double [n_rhs][Vh][4][3]   (one parity, spin-major)
+ *   algebra double [V][4][8]  components on T_a = i lambda_a / 2, so that the
+ *           scalar product (A, B) = -2 sum Tr(A B) of Sec. I is the dot
+ *           product of the components.
+ *
+ * Device layouts (what every compute call reads and writes):
+ *   gauge   for parity p of the base site, direction mu, chunk c, site h:
+ *           chunk index ((p*4 + mu)*NC + c)*Vh + h.  A chunk is 16 bytes
+ *           where the format allows it:
+ *             F64/LINK18: double2 (1 complex) x 9    F64/LINK12: double2 x 6
+ *             F32/LINK18: float2  (1 complex) x 9    F32/LINK12: float4 (2 complex) x 3
+ *             F16/LINK18: half2   (1 complex) x 9    F16/LINK12: 4 halves (2 complex) x 3
+ *           Complex entries are row-major; LINK12 stores rows 0 and 1 and the
+ *           kernels rebuild row 2 = conj(row0 x row1) (exact for SU(3)).  The
+ *           fermion time-boundary sign is applied by the kernels, never folded
+ *           into the links.
+ *   spinor  one parity, n_rhs right-hand sides, element s = h*n_rhs + r,
+ *           S = Vh*n_rhs:
+ *             F64: double2 [12][S]   (chunk = spin*3 + colour)
+ *             F32: float4  [6][S]    (chunk k holds complexes 2k, 2k+1)
+ *             F16: 8 halves [3][S] followed by float norm[S]; value = half *
+ *                  norm, norm a power of two >= the site's largest |real|.
+ *   algebra double [2][4][8][Vh]: ((p*4 + mu)*8 + a)*Vh + h.
+ *
+ * Memory and streams.  Every field pointer is a caller-owned DEVICE pointer,
+ * 256-byte aligned, of the size the *_bytes helpers return.  The library
+ * never frees or reallocates caller memory; it owns only workspace inside the
+ * context, released by hmc_ctx_destroy.  Calls are asynchronous on the
+ * context's stream (hmc_ctx_set_stream) unless stated otherwise; calls that
+ * return results to host memory (statistics, actions) synchronise that
+ * stream.  A context is not thread-safe; use one per host thread.
+ *
+ * Errors.  Every call returns an hmc_status.  On failure nothing is thrown
+ * across the ABI; hmc_last_error(ctx) returns a message.  HMC_EINVAL: bad
+ * argument (null pointer, odd or too small extent, unsupported precision or
+ * format); HMC_ENOMEM: workspace allocation failed; HMC_ENOCONV: a solver hit
+ * max_iter (its output holds the last iterate); HMC_ENAN: a reduction saw a
+ * NaN or Inf; HMC_ECUDA: a CUDA error (message has the CUDA error string).
+ */
+#ifndef HMC_H
+#define HMC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HMC_OK = 0,
+  HMC_EINVAL = 1,
+  HMC_ENOMEM = 2,
+  HMC_ENOCONV = 3,
+  HMC_ETIMEOUT = 4,
+  HMC_ENAN = 5,
+  HMC_ECUDA = 6
+} hmc_status;
+
+typedef enum { HMC_F64 = 0, HMC_F32 = 1, HMC_F16 = 2 } hmc_prec;
+typedef enum { HMC_LINK18 = 18, HMC_LINK12 = 12 } hmc_link_fmt;
+
+typedef struct hmc_ctx hmc_ctx;
+
+typedef struct {
+  int L[4]; /* Lt, Lx, Ly, Lz */
+} hmc_lattice;
+
+/* A gauge field on the device in the layout above. */
+typedef struct {
+  const void *data;
+  int prec; /* hmc_prec */
+  int fmt;  /* hmc_link_fmt */
+} hmc_gauge;
+
+/* ---- context --------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device` (made current for the call).
+ * *out receives the handle.  The default stream is the legacy stream 0. */
+int hmc_ctx_create(int device, hmc_ctx **out);
+/* Free the context and its workspace.  Synchronises its stream. */
+int hmc_ctx_destroy(hmc_ctx *ctx);
+/* Make every later call run on `stream` (a cudaStream_t, may be NULL). */
+int hmc_ctx_set_stream(hmc_ctx *ctx, void *stream);
+/* Message of the last failed call on ctx ("" if none).  Owned by ctx. */
+const char *hmc_last_error(hmc_ctx *ctx);
+/* Number of kernels this context has launched so far. */
+long long hmc_launch_count(hmc_ctx *ctx);
+
+/* ---- sizes (host-only, no GPU needed) ---------------------------------------- */
+
+size_t hmc_gauge_bytes(const hmc_lattice *lat, int prec, int fmt);
+size_t hmc_spinor_bytes(const hmc_lattice *lat, int prec, int n_rhs);
+size_t hmc_algebra_bytes(const hmc_lattice *lat);
+
+/* ---- layout conversion --------------------------------------------------------
+ * Canonical arrays are DEVICE pointers too.  Packing to LINK12 drops row 2;
+ * packing to F32/F16 rounds to nearest.  Bit-exact for values representable
+ * in the target precision. */
+int hmc_pack_gauge(hmc_ctx *ctx, const hmc_lattice *lat, const double *U_canon,
+                   void *U_dev, int prec, int fmt);
+/* Inverse of hmc_pack_gauge (LINK12 rebuilds row 2). */
+int hmc_unpack_gauge(hmc_ctx *ctx, const hmc_lattice *lat, const void *U_dev,
+                     int prec, int fmt, double *U_canon);
+int hmc_pack_spinor(hmc_ctx *ctx, const hmc_lattice *lat,
+                    const double *psi_canon, void *psi_dev, int prec, int n_rhs);
+int hmc_unpack_spinor(hmc_ctx *ctx, const hmc_lattice *lat, const void *psi_dev,
+                      int prec, int n_rhs, double *psi_canon);
+int hmc_pack_algebra(hmc_ctx *ctx, const hmc_lattice *lat, const double *A_canon,
+                     double *A_dev);
+int hmc_unpack_algebra(hmc_ctx *ctx, const hmc_lattice *lat, const double *A_dev,
+                       double *A_canon);
+
+/* ---- hopping matrix -------------------------------------------------------------
+ * hmc_dslash: hemi-Dslash (Sec. I, definition of H_xy; Sec. II.B for the
+ * even/odd blocks).  out (parity p) = H_{p,1-p} in (parity 1-p); with
+ * dagger != 0, out = gamma_5 H_{p,1-p} gamma_5 in = (H_{1-p,p})^dag in.
+ * `prec` is the storage precision of in and out (F64 computes in double,
+ * F32/F16 in float); U may have any precision and format.  n_rhs fields are
+ * processed in one launch, sharing every link load.  out must not alias in. */
+int hmc_dslash(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U,
+               void *out, const void *in, int out_parity, int dagger, int prec,
+               int n_rhs);
+
+/* hmc_mhat: even-site preconditioned operator (Sec. II.B, with M = 1 - kappa H
+ * of Sec. I): out = Mhat in, Mhat = 1 - kappa^2 H_eo H_oe, or
+ * Mhat^dag = gamma_5 Mhat gamma_5 when dagger != 0.  in/out are even fields.
+ * kappas (nullable, host array of n_rhs) gives each right-hand side its own
+ * kappa (mass preconditioning); otherwise every RHS uses `kappa`.  Two
+ * launches; out must not alias in. */
+int hmc_mhat(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U,
+             void *out, const void *in, double kappa, int dagger, int prec,
+             int n_rhs, const double *kappas);
+
+/* ---- solver ------------------------------------------------------------------- */
+
+typedef struct {
+  int inner_prec;        /* HMC_F64: plain FP64 CG; HMC_F32/HMC_F16: mixed
+                            precision with FP64 reliable updates */
+  double reliable_delta; /* reliable update when |r| drops below delta times
+                            its maximum since the last update (0: 0.1) */
+  int check_every;       /* iterations between host convergence checks
+                            (0: 16); does not change the result */
+} hmc_solver_opts;
+
+typedef struct {
+  int iterations;       /* CG iterations */
+  int reliable_updates; /* FP64 residual recomputations */
+  double true_rel_res;  /* |phi - A x| / |phi| recomputed in FP64 at exit */
+} hmc_solve_stats;
+
+/* hmc_cg_solve: x = (Mhat^dag Mhat)^{-1} phi by conjugate gradients from
+ * x = 0 (the paper solves with BiCGstab to machine precision, Sec. IV; the
+ * solution is the same).  Stops when the true FP64 residual satisfies
+ * |phi - Mhat^dag Mhat x| / |phi| <= tol.  U_hi: F64 gauge field; U_lo: the
+ * gauge field in the inner precision (required when opts->inner_prec != F64,
+ * ignored otherwise).  x and phi are F64 even fields, n_rhs = 1.  Blocks the
+ * host until done.  opts and stats may be NULL. */
+int hmc_cg_solve(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
+                 const hmc_gauge *U_lo, void *x, const void *phi, double kappa,
+                 double tol, int max_iter, const hmc_solver_opts *opts,
+                 hmc_solve_stats *stats);
+
+/* ---- actions and forces -------------------------------------------------------- */
+
+/* Filter of the pseudo-fermion action (Sec. II): with filt == NULL the plain
+ * action S_PF = phi^dag (Mhat^dag Mhat)^{-1} phi is used (the gamma_5
+ * equivalent of |M^{-1} phi|^2, Sec. I); otherwise
+ * S~_PF = |(alpha Mhat^{-1} + sum_{n=0}^{n} b_n K^n) phi|^2 with
+ * K = kappa^2 H_eo H_oe (eq. ModPF). */
+typedef struct {
+  const double *b; /* host array b_0 .. b_n */
+  int n;           /* truncation (n_t for forces, n_max for actions) */
+  double alpha;
+} hmc_filter;
+
+/* hmc_force_pf: F += coeff * F_PF, (omega, F_PF) = delta_omega S for
+ * delta U = omega U (Sec. I); delta S_PF = -X^dag delta M Y + h.c. (Sec. II)
+ * for the plain action, the Horner-scheme force of Sec. II for the filtered
+ * one.  Performs its own solves (tolerance tol, options opts).  U_hi is the
+ * F64 gauge field, U_lo the inner-precision copy (as for hmc_cg_solve); F is
+ * an algebra field on the device.  stats (nullable) sums over the solves. */
+int hmc_force_pf(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
+                 const hmc_gauge *U_lo, const void *phi, double kappa,
+                 const hmc_filter *filt, double coeff, double *F, double tol,
+                 const hmc_solver_opts *opts, hmc_solve_stats *stats);
+
+/* hmc_action_pf: the pseudo-fermion action of the filter above (NULL: plain),
+ * into *action (host), solving to tol.  Blocks. */
+int hmc_action_pf(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
+                  const hmc_gauge *U_lo, const void *phi, double kappa,
+                  const hmc_filter *filt, double tol,
+                  const hmc_solver_opts *opts, double *action,
+                  hmc_solve_stats *stats);
+
+/* hmc_force_hopexp: gauge part of the action, S_G (Sec. I) plus the
+ * hopping-expansion term T_k = 2 sum_{n=1}^{k} (1/n) Tr_e K^n (eq. ModGauge in
+ * even/odd form), k in {0, 1, 2} counting powers of K.  For every extent >= 6
+ * T_1 = 0 and T_2 = -(96 kappa^4 / 3) sum_p Re Tr U_p (Sec. II, Delta beta =
+ * 96 kappa^4); an extent of 4 adds the straight winding loops of length 4.
+ * F += coeff * force of (S_G + T_k); *action (host, nullable) receives
+ * S_G + T_k (blocks when non-NULL).  U: F64 gauge, any format.  Extents of 2
+ * with k >= 1 return HMC_EINVAL (longer windings are not implemented). */
+int hmc_force_hopexp(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U,
+                     double beta, double kappa, int k, double coeff, double *F,
+                     double *action);
+
+/* hmc_plaquette: (1 / (3 N_p)) sum_p Re Tr U_p (Sec. IV), blocks. */
+int hmc_plaquette(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U,
+                  double *plaq);
+
+/* hmc_poly_apply: out = sum_{i=0}^{degree} c_i K^i in by Horner's scheme
+ * (Sec. II), K = kappa^2 H_eo H_oe; in/out even fields of precision prec,
+ * n_rhs = 1.  horner_store (nullable): device buffer of degree+1 fields of
+ * the same precision receiving the Horner iterates Y_degree .. Y_0
+ * (field j at offset j*hmc_spinor_bytes). */
+int hmc_poly_apply(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U,
+                   void *out, const void *in, const double *coeffs, int degree,
+                   double kappa, int prec, void *horner_store);
+
+/* ---- molecular dynamics -------------------------------------------------------- */
+
+/* hmc_update_links: U <- exp(eps Pi) U with Pi = sum_a P_a T_a (Sec. I, update
+ * step T; reading: dU/dtau = Pi U fixes exp(eps Pi), the printed step writes
+ * exp(i eps Pi)), then projection onto SU(3).  U: F64/LINK18. */
+int hmc_update_links(hmc_ctx *ctx, const hmc_lattice *lat, void *U,
+                     const double *P, double eps);
+/* hmc_update_momenta: P <- P - eps F (Sec. I, update step P; reading:
+ * dPi/dtau = -F fixes the sign). */
+int hmc_update_momenta(hmc_ctx *ctx, const hmc_lattice *lat, double *P,
+                       const double *F, double eps);
+/* hmc_kinetic: (1/2)(Pi, Pi) = (1/2) sum P_a^2 into *out (host).  Blocks. */
+int hmc_kinetic(hmc_ctx *ctx, const hmc_lattice *lat, const double *P,
+                double *out);
+
+typedef struct {
+  double beta, kappa, tau;
+  int n_md;      /* coarse (pseudo-fermion) leapfrog steps per trajectory */
+  int n_gauge;   /* fine gauge steps per coarse step */
+  int filter_k;  /* 0: plain S_PF; 1, 2: kappa^2 / kappa^4 filtering */
+  int n_t, n_max;
+  const double *b; /* host, b_0 .. b_{n_max} (filter_k > 0) */
+  const double *c; /* host, c_0 .. c_{n_max}: heatbath phi = Mhat sum c_n K^n eta */
+  double alpha;
+  double tol_md, tol_action;
+  hmc_solver_opts solver; /* inner precision of every solve */
+  int link_fmt_lo;        /* format of the inner-precision gauge copy */
+} hmc_traj_params;
+
+typedef struct {
+  double H0, H1, dH;
+  double plaq0, plaq1;
+  int accepted;
+  int cg_iterations;
+  int solves;
+} hmc_traj_result;
+
+/* hmc_trajectory: one HMC trajectory (Sec. I): heatbath phi = Mhat^dag eta
+ * (plain) or phi = Mhat sum_n c_n K^n eta (filtered); H0; leapfrog on two
+ * time scales, T_L = P(dt/2) T(dt) P(dt/2), pseudo-fermion force on the coarse
+ * scale and gauge (+ hopping-expansion) force on the fine scale (Sec. I,
+ * Sec. IV); H1 with the action solves at tol_action; Metropolis
+ * min(1, exp(-dH)) against u.  The random inputs are the caller's: P (algebra
+ * field, device, N(0,1) components), eta (F64 even spinor, device, density
+ * ~ exp(-|eta|^2)) and u (uniform in [0,1)).  U (F64/LINK18, device) is
+ * replaced by the final field when accepted and left unchanged otherwise;
+ * U_end (nullable, device, same layout) receives the final field and P_end
+ * (nullable, device algebra field) the final momenta, accepted or not (used
+ * for the reversibility test of Sec. IV: flip P_end and run back).
+ * Blocks; *res is filled on the host. */
+int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U,
+                   const hmc_traj_params *params, const double *P,
+                   const void *eta, double u, hmc_traj_result *res,
+                   void *U_end, double *P_end);
+
+/* hmc_md_evolve: the molecular-dynamics part of hmc_trajectory alone: evolve
+ * (U, P) in place for tau with the same two-scale leapfrog, the
+ * pseudo-fermion field phi held fixed (the phi-algorithm, Sec. I).  With the
+ * momenta flipped at the end this runs the trajectory backwards, which is the
+ * reversibility test of Sec. IV.  U: F64/LINK18; P: algebra field; phi: F64
+ * even field (the heatbath output); res (nullable) receives cg_iterations and
+ * solves.  Blocks. */
+int hmc_md_evolve(hmc_ctx *ctx, const hmc_lattice *lat, void *U, double *P,
+                  const void *phi, const hmc_traj_params *params,
+                  hmc_traj_result *res);
+
+/* ---- host helpers (no GPU needed) -------------------------------------------- */
+
+/* Filter coefficients of Sec. II for order k (powers of K): b_0..b_n into b,
+ * alpha = exp(-sum_{m<=k} 1/m) into *alpha, and (c nullable) the heatbath
+ * series c_0..c_n of exp(sum_{m<=k} K^m/m) into c.  Computed in long double. */
+int hmc_filter_coeffs(int k, int n, double *b, double *alpha, double *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

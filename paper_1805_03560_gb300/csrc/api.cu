@@ -1,0 +1,322 @@
+// C-ABI entry points of libhmc (declared and documented in include/hmc.h):
+// context, sizes, layout conversion, Dslash, Mhat and the solver.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "hmc_host.h"
+
+namespace hmc {
+
+int fail(hmc_ctx *ctx, int code, const char *fmt, ...) {
+  if (ctx) {
+    char buf[768];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return code;
+}
+
+int cuda_ok(hmc_ctx *ctx, cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return HMC_OK;
+  return fail(ctx, HMC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int launched(hmc_ctx *ctx, const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(ctx, HMC_ECUDA, "launch of %s: %s", what, cudaGetErrorString(e));
+  ctx->launches += 1;
+  return HMC_OK;
+}
+
+void *workspace(hmc_ctx *ctx, const char *name, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  hmc_ctx::Buf &b = ctx->ws[name];
+  if (b.p && b.n >= bytes) return b.p;
+  if (b.p) {
+    // the old buffer may still be in use by queued work
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+  }
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    fail(ctx, HMC_ENOMEM, "workspace %s: cudaMalloc(%zu) failed: %s", name, bytes,
+         cudaGetErrorString(e));
+    return nullptr;
+  }
+  b.n = bytes;
+  return b.p;
+}
+
+int check_lattice(hmc_ctx *ctx, const hmc_lattice *lat) {
+  if (!lat) return fail(ctx, HMC_EINVAL, "lattice is NULL");
+  long long V = 1;
+  for (int i = 0; i < 4; ++i) {
+    int l = lat->L[i];
+    if (l < 2 || (l & 1))
+      return fail(ctx, HMC_EINVAL, "lattice extent L[%d] = %d must be even and >= 2", i, l);
+    V *= l;
+  }
+  if (V >= (1LL << 31)) return fail(ctx, HMC_EINVAL, "lattice volume %lld too large", V);
+  return HMC_OK;
+}
+
+int check_prec(hmc_ctx *ctx, int prec) {
+  if (prec != HMC_F64 && prec != HMC_F32 && prec != HMC_F16)
+    return fail(ctx, HMC_EINVAL, "unsupported precision %d", prec);
+  return HMC_OK;
+}
+
+int check_gauge(hmc_ctx *ctx, const hmc_gauge *U) {
+  if (!U || !U->data) return fail(ctx, HMC_EINVAL, "gauge field is NULL");
+  if (check_prec(ctx, U->prec)) return HMC_EINVAL;
+  if (U->fmt != HMC_LINK18 && U->fmt != HMC_LINK12)
+    return fail(ctx, HMC_EINVAL, "unsupported link format %d", U->fmt);
+  return HMC_OK;
+}
+
+size_t spinor_bytes(const Geo &g, int prec, int n_rhs) {
+  size_t S = (size_t)g.Vh * n_rhs, b = 0;
+  switch (prec) {
+    case HMC_F64: b = SpinorIO<HMC_F64>::bytes(S); break;
+    case HMC_F32: b = SpinorIO<HMC_F32>::bytes(S); break;
+    case HMC_F16: b = SpinorIO<HMC_F16>::bytes(S); break;
+    default: return 0;
+  }
+  return (b + 255) & ~(size_t)255;
+}
+
+size_t gauge_bytes(const Geo &g, int prec, int fmt) {
+  if (fmt != 18 && fmt != 12) return 0;
+  size_t per;  // bytes per link
+  switch (prec) {
+    case HMC_F64: per = (size_t)fmt * 8; break;
+    case HMC_F32: per = (size_t)fmt * 4; break;
+    case HMC_F16: per = (size_t)fmt * 2; break;
+    default: return 0;
+  }
+  return ((size_t)2 * 4 * g.Vh * per + 255) & ~(size_t)255;
+}
+
+int pack_gauge(hmc_ctx *ctx, const Geo &g, const double *Uc, void *Ud, int prec, int fmt,
+               bool pack);
+int pack_spinor(hmc_ctx *ctx, const Geo &g, const double *c, void *d, int prec, int n_rhs,
+                bool pack);
+int pack_algebra(hmc_ctx *ctx, const Geo &g, const double *c, double *d, bool pack);
+
+}  // namespace hmc
+
+using namespace hmc;
+
+#define CTX_CHECK(ctx) \
+  if (!(ctx)) return HMC_EINVAL
+#define TRY(e)         \
+  do {                 \
+    int _s = (e);      \
+    if (_s) return _s; \
+  } while (0)
+
+extern "C" {
+
+int hmc_ctx_create(int device, hmc_ctx **out) {
+  if (!out) return HMC_EINVAL;
+  *out = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) return HMC_ECUDA;
+  hmc_ctx *c = new hmc_ctx();
+  c->device = device;
+  if (cudaMallocHost(&c->h_pinned, 64 * sizeof(double)) != cudaSuccess) {
+    delete c;
+    return HMC_ENOMEM;
+  }
+  *out = c;
+  return HMC_OK;
+}
+
+int hmc_ctx_destroy(hmc_ctx *ctx) {
+  CTX_CHECK(ctx);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto &kv : ctx->ws)
+    if (kv.second.p) cudaFree(kv.second.p);
+  if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  delete ctx;
+  return HMC_OK;
+}
+
+int hmc_ctx_set_stream(hmc_ctx *ctx, void *stream) {
+  CTX_CHECK(ctx);
+  ctx->stream = (cudaStream_t)stream;
+  return HMC_OK;
+}
+
+const char *hmc_last_error(hmc_ctx *ctx) { return ctx ? ctx->err.c_str() : "context is NULL"; }
+
+long long hmc_launch_count(hmc_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+size_t hmc_gauge_bytes(const hmc_lattice *lat, int prec, int fmt) {
+  if (check_lattice(nullptr, lat)) return 0;
+  return gauge_bytes(make_geo(*lat), prec, fmt);
+}
+
+size_t hmc_spinor_bytes(const hmc_lattice *lat, int prec, int n_rhs) {
+  if (check_lattice(nullptr, lat) || n_rhs < 1) return 0;
+  return spinor_bytes(make_geo(*lat), prec, n_rhs);
+}
+
+size_t hmc_algebra_bytes(const hmc_lattice *lat) {
+  if (check_lattice(nullptr, lat)) return 0;
+  return (size_t)make_geo(*lat).Vh * 2 * 4 * 8 * sizeof(double);
+}
+
+int hmc_pack_gauge(hmc_ctx *ctx, const hmc_lattice *lat, const double *U_canon, void *U_dev,
+                   int prec, int fmt) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  if (!U_canon || !U_dev) return fail(ctx, HMC_EINVAL, "pack_gauge: NULL pointer");
+  return pack_gauge(ctx, make_geo(*lat), U_canon, U_dev, prec, fmt, true);
+}
+
+int hmc_unpack_gauge(hmc_ctx *ctx, const hmc_lattice *lat, const void *U_dev, int prec, int fmt,
+                     double *U_canon) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  if (!U_canon || !U_dev) return fail(ctx, HMC_EINVAL, "unpack_gauge: NULL pointer");
+  return pack_gauge(ctx, make_geo(*lat), U_canon, (void *)U_dev, prec, fmt, false);
+}
+
+int hmc_pack_spinor(hmc_ctx *ctx, const hmc_lattice *lat, const double *psi_canon, void *psi_dev,
+                    int prec, int n_rhs) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  if (!psi_canon || !psi_dev || n_rhs < 1) return fail(ctx, HMC_EINVAL, "pack_spinor: bad args");
+  return pack_spinor(ctx, make_geo(*lat), psi_canon, psi_dev, prec, n_rhs, true);
+}
+
+int hmc_unpack_spinor(hmc_ctx *ctx, const hmc_lattice *lat, const void *psi_dev, int prec,
+                      int n_rhs, double *psi_canon) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  if (!psi_canon || !psi_dev || n_rhs < 1)
+    return fail(ctx, HMC_EINVAL, "unpack_spinor: bad args");
+  return pack_spinor(ctx, make_geo(*lat), psi_canon, (void *)psi_dev, prec, n_rhs, false);
+}
+
+int hmc_pack_algebra(hmc_ctx *ctx, const hmc_lattice *lat, const double *A_canon, double *A_dev) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  if (!A_canon || !A_dev) return fail(ctx, HMC_EINVAL, "pack_algebra: NULL pointer");
+  return pack_algebra(ctx, make_geo(*lat), A_canon, A_dev, true);
+}
+
+int hmc_unpack_algebra(hmc_ctx *ctx, const hmc_lattice *lat, const double *A_dev,
+                       double *A_canon) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  if (!A_canon || !A_dev) return fail(ctx, HMC_EINVAL, "unpack_algebra: NULL pointer");
+  return pack_algebra(ctx, make_geo(*lat), A_canon, (double *)A_dev, false);
+}
+
+int hmc_dslash(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U, void *out, const void *in,
+               int out_parity, int dagger, int prec, int n_rhs) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  TRY(check_gauge(ctx, U));
+  TRY(check_prec(ctx, prec));
+  if (!out || !in || n_rhs < 1 || (out_parity != 0 && out_parity != 1))
+    return fail(ctx, HMC_EINVAL, "dslash: bad arguments");
+  if (out == in) return fail(ctx, HMC_EINVAL, "dslash: out must not alias in");
+  DslashArgs a{};
+  a.g = make_geo(*lat);
+  a.p = out_parity;
+  a.n_rhs = n_rhs;
+  a.out = out;
+  a.in = in;
+  a.gauge = U->data;
+  a.cb = 1.0;
+  return dslash(ctx, a, *U, prec, dagger, nullptr);
+}
+
+int hmc_mhat(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U, void *out, const void *in,
+             double kappa, int dagger, int prec, int n_rhs, const double *kappas) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  TRY(check_gauge(ctx, U));
+  TRY(check_prec(ctx, prec));
+  if (!out || !in || n_rhs < 1) return fail(ctx, HMC_EINVAL, "mhat: bad arguments");
+  if (out == in) return fail(ctx, HMC_EINVAL, "mhat: out must not alias in");
+  Geo g = make_geo(*lat);
+  void *tmp = workspace(ctx, "mhat_tmp", spinor_bytes(g, prec, n_rhs));
+  if (!tmp) return HMC_ENOMEM;
+  const double *cb = nullptr;
+  if (kappas) {
+    double *d = (double *)workspace(ctx, "mhat_cb", sizeof(double) * n_rhs);
+    if (!d) return HMC_ENOMEM;
+    double hb[256];
+    if (n_rhs > 256) return fail(ctx, HMC_EINVAL, "mhat: at most 256 right-hand sides");
+    for (int r = 0; r < n_rhs; ++r) hb[r] = -kappas[r] * kappas[r];
+    TRY(cuda_ok(ctx, cudaMemcpyAsync(d, hb, sizeof(double) * n_rhs, cudaMemcpyHostToDevice,
+                                     ctx->stream),
+                "mhat: kappas"));
+    cb = d;
+  }
+  return mhat(ctx, g, *U, prec, dagger, n_rhs, out, in, tmp, kappa, cb, nullptr, nullptr);
+}
+
+int hmc_cg_solve(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
+                 const hmc_gauge *U_lo, void *x, const void *phi, double kappa, double tol,
+                 int max_iter, const hmc_solver_opts *opts, hmc_solve_stats *stats) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  TRY(check_gauge(ctx, U_hi));
+  if (!x || !phi || max_iter < 1) return fail(ctx, HMC_EINVAL, "cg: bad arguments");
+  if (x == phi) return fail(ctx, HMC_EINVAL, "cg: x must not alias phi");
+  if (opts && opts->inner_prec != HMC_F64) TRY(check_gauge(ctx, U_lo));
+  return cg_solve(ctx, make_geo(*lat), *U_hi, U_lo, x, phi, kappa, tol, max_iter, opts, stats);
+}
+
+int hmc_filter_coeffs(int k, int n, double *b, double *alpha, double *c) {
+  if (k < 0 || k > 8 || n < 0 || n > 4096 || !b || !alpha) return HMC_EINVAL;
+  // e_m = [x^m] exp(-sum_{j<=k} x^j / j) from m e_m = -sum_{j=1}^{min(m,k)} e_{m-j}
+  const int tail = 120;
+  const int N = n + tail;
+  long double *e = new long double[N + 1];
+  e[0] = 1.0L;
+  for (int m = 1; m <= N; ++m) {
+    long double s = 0.0L;
+    for (int j = 1; j <= k && j <= m; ++j) s += e[m - j];
+    e[m] = -s / m;
+  }
+  // b_m = -sum_{i>m} e_i (tail sum from the far end, small terms first)
+  long double acc = 0.0L;
+  long double *bt = new long double[N + 1];
+  for (int m = N; m >= 0; --m) {
+    bt[m] = -acc;
+    acc += e[m];
+  }
+  for (int m = 0; m <= n; ++m) b[m] = (double)bt[m];
+  long double hk = 0.0L;
+  for (int j = 1; j <= k; ++j) hk += 1.0L / j;
+  *alpha = (double)expl(-hk);
+  if (c) {
+    long double *cc = new long double[n + 1];
+    cc[0] = 1.0L;
+    for (int m = 1; m <= n; ++m) {
+      long double s = 0.0L;
+      for (int j = 1; j <= k && j <= m; ++j) s += cc[m - j];
+      cc[m] = s / m;
+    }
+    for (int m = 0; m <= n; ++m) c[m] = (double)cc[m];
+    delete[] cc;
+  }
+  delete[] e;
+  delete[] bt;
+  return HMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,242 @@
+// Hemi-Dslash: the even/odd blocks of the hopping matrix (Sec. I, H_xy;
+// Sec. II.B) applied with half-spinor projection.
+//
+// For a hop in direction mu the spin factor 1 - s gamma_mu (s = +1 forwards,
+// s = -1 backwards; the adjoint flips s) has rank two.  In the chiral basis
+// gamma_mu = [[0, B_mu], [B_mu^dag, 0]] with B_0 = 1, B_k = -i sigma_k, so
+// (1 - s gamma_mu) psi = (h, -s B_mu^dag h) with h = u - s B_mu d for the upper
+// (u) and lower (d) spin pairs.  Only the two-spinor h is multiplied by the
+// link; the lower half is rebuilt from it.  One thread computes one output
+// site (and one right-hand side); links are shared by the threads of the
+// right-hand sides of a site through the load coalescer.
+#include <cstdio>
+
+#include "hmc_host.h"
+
+namespace hmc {
+
+// h = u - S B_mu d
+template <int MU, int S, typename R>
+__device__ __forceinline__ void project(const Cx<R> p[12], Cx<R> h[6]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    Cx<R> u0 = p[a], u1 = p[3 + a], d0 = p[6 + a], d1 = p[9 + a];
+    if (MU == 0) {
+      h[a] = S > 0 ? u0 - d0 : u0 + d0;
+      h[3 + a] = S > 0 ? u1 - d1 : u1 + d1;
+    } else if (MU == 1) {
+      h[a] = S > 0 ? u0 + ti(d1) : u0 - ti(d1);
+      h[3 + a] = S > 0 ? u1 + ti(d0) : u1 - ti(d0);
+    } else if (MU == 2) {
+      h[a] = S > 0 ? u0 + d1 : u0 - d1;
+      h[3 + a] = S > 0 ? u1 - d0 : u1 + d0;
+    } else {
+      h[a] = S > 0 ? u0 + ti(d0) : u0 - ti(d0);
+      h[3 + a] = S > 0 ? u1 - ti(d1) : u1 + ti(d1);
+    }
+  }
+}
+
+// acc += (w, -S B_mu^dag w)
+template <int MU, int S, typename R>
+__device__ __forceinline__ void accumulate(Cx<R> acc[12], const Cx<R> w[6]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    Cx<R> w0 = w[a], w1 = w[3 + a];
+    acc[a] = acc[a] + w0;
+    acc[3 + a] = acc[3 + a] + w1;
+    if (MU == 0) {
+      acc[6 + a] = S > 0 ? acc[6 + a] - w0 : acc[6 + a] + w0;
+      acc[9 + a] = S > 0 ? acc[9 + a] - w1 : acc[9 + a] + w1;
+    } else if (MU == 1) {
+      acc[6 + a] = S > 0 ? acc[6 + a] - ti(w1) : acc[6 + a] + ti(w1);
+      acc[9 + a] = S > 0 ? acc[9 + a] - ti(w0) : acc[9 + a] + ti(w0);
+    } else if (MU == 2) {
+      acc[6 + a] = S > 0 ? acc[6 + a] - w1 : acc[6 + a] + w1;
+      acc[9 + a] = S > 0 ? acc[9 + a] + w0 : acc[9 + a] - w0;
+    } else {
+      acc[6 + a] = S > 0 ? acc[6 + a] - ti(w0) : acc[6 + a] + ti(w0);
+      acc[9 + a] = S > 0 ? acc[9 + a] + ti(w1) : acc[9 + a] - ti(w1);
+    }
+  }
+}
+
+// w = U h (two colour vectors)
+template <typename R>
+__device__ __forceinline__ void mul_link(const Cx<R> u[9], const Cx<R> h[6], Cx<R> w[6]) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      Cx<R> t = u[a * 3] * h[s * 3];
+      t = fmac(t, u[a * 3 + 1], h[s * 3 + 1]);
+      t = fmac(t, u[a * 3 + 2], h[s * 3 + 2]);
+      w[s * 3 + a] = t;
+    }
+}
+
+// w = U^dag h
+template <typename R>
+__device__ __forceinline__ void mul_link_dag(const Cx<R> u[9], const Cx<R> h[6], Cx<R> w[6]) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      Cx<R> t = cjmul(u[a], h[s * 3]);
+      t = fmacj(t, u[3 + a], h[s * 3 + 1]);
+      t = fmacj(t, u[6 + a], h[s * 3 + 2]);
+      w[s * 3 + a] = t;
+    }
+}
+
+template <int SP, int FMT, int MU, int S>
+__device__ __forceinline__ void hop_fwd(const DslashArgs &a, int h, int r, int lex, const int c[4],
+                                        Cx<typename SpinorIO<SP>::R> acc[12]) {
+  using SIO = SpinorIO<SP>;
+  using R = typename SIO::R;
+  using LIO = LinkIO<SP, FMT>;
+  const int Vh = a.g.Vh, S_ = Vh * a.n_rhs;
+  int hn = nb_fwd(a.g, lex, c, MU);
+  Cx<R> psi[12], u[9], hs[6], w[6];
+  SIO::load(a.in, S_, hn * a.n_rhs + r, psi);
+  LIO::load(link_base<SP, FMT>(a.gauge, Vh, a.p, MU), Vh, h, u);
+  project<MU, S>(psi, hs);
+  if (MU == 0 && c[0] == a.g.L[0] - 1) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) hs[k] = -hs[k];
+  }
+  mul_link(u, hs, w);
+  accumulate<MU, S>(acc, w);
+}
+
+template <int SP, int FMT, int MU, int S>
+__device__ __forceinline__ void hop_bwd(const DslashArgs &a, int r, int lex, const int c[4],
+                                        Cx<typename SpinorIO<SP>::R> acc[12]) {
+  using SIO = SpinorIO<SP>;
+  using R = typename SIO::R;
+  using LIO = LinkIO<SP, FMT>;
+  const int Vh = a.g.Vh, S_ = Vh * a.n_rhs;
+  int hn = nb_bwd(a.g, lex, c, MU);
+  Cx<R> psi[12], u[9], hs[6], w[6];
+  SIO::load(a.in, S_, hn * a.n_rhs + r, psi);
+  LIO::load(link_base<SP, FMT>(a.gauge, Vh, 1 - a.p, MU), Vh, hn, u);
+  project<MU, S>(psi, hs);
+  if (MU == 0 && c[0] == 0) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) hs[k] = -hs[k];
+  }
+  mul_link_dag(u, hs, w);
+  accumulate<MU, S>(acc, w);
+}
+
+template <int SP, int FMT, bool DAG>
+__global__ void __launch_bounds__(DS_NT) k_dslash(const DslashArgs a) {
+  using SIO = SpinorIO<SP>;
+  using R = typename SIO::R;
+  constexpr int SF = DAG ? -1 : 1;  // forwards: 1 - gamma (1 + gamma for the adjoint)
+  if (a.gate && *a.gate == 0) return;
+  const int S_ = a.g.Vh * a.n_rhs;
+  const int i = blockIdx.x * DS_NT + threadIdx.x;
+  double nrm = 0.0;
+  if (i < S_) {
+    const int h = a.n_rhs == 1 ? i : i / a.n_rhs;
+    const int r = i - h * a.n_rhs;
+    int c[4];
+    const int lex = site_coords(a.g, h, a.p, c);
+    Cx<R> acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = {R(0), R(0)};
+    hop_fwd<SP, FMT, 0, SF>(a, h, r, lex, c, acc);
+    hop_bwd<SP, FMT, 0, -SF>(a, r, lex, c, acc);
+    hop_fwd<SP, FMT, 1, SF>(a, h, r, lex, c, acc);
+    hop_bwd<SP, FMT, 1, -SF>(a, r, lex, c, acc);
+    hop_fwd<SP, FMT, 2, SF>(a, h, r, lex, c, acc);
+    hop_bwd<SP, FMT, 2, -SF>(a, r, lex, c, acc);
+    hop_fwd<SP, FMT, 3, SF>(a, h, r, lex, c, acc);
+    hop_bwd<SP, FMT, 3, -SF>(a, r, lex, c, acc);
+    const R cb = (R)(a.cb_rhs ? a.cb_rhs[r] : a.cb);
+    if (a.x) {
+      Cx<R> xv[12];
+      SIO::load(a.x, S_, i, xv);
+      const R ca = (R)a.ca;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        acc[k].re = fma(ca, xv[k].re, cb * acc[k].re);
+        acc[k].im = fma(ca, xv[k].im, cb * acc[k].im);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[k] = cb * acc[k];
+    }
+    SIO::store(a.out, S_, i, acc);
+    if (a.partials) {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) nrm += (double)norm2(acc[k]);
+    }
+  }
+  if (a.partials) {
+    double s = block_sum<DS_NT>(nrm);
+    if (threadIdx.x == 0) a.partials[blockIdx.x] = s;
+  }
+}
+
+template <int SP, int FMT>
+static void launch_sf(const DslashArgs &a, int dagger, int nb, cudaStream_t st) {
+  if (dagger)
+    k_dslash<SP, FMT, true><<<nb, DS_NT, 0, st>>>(a);
+  else
+    k_dslash<SP, FMT, false><<<nb, DS_NT, 0, st>>>(a);
+}
+
+int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int dagger,
+           int *nblocks) {
+  if (U.prec != sprec)
+    return fail(ctx, HMC_EINVAL, "dslash: gauge precision %d must match spinor precision %d",
+                U.prec, sprec);
+  const long long S = (long long)a.g.Vh * a.n_rhs;
+  const int nb = blocks_for(S, DS_NT);
+  if (nblocks) *nblocks = nb;
+  cudaStream_t st = ctx->stream;
+  switch (sprec * 100 + U.fmt) {
+    case HMC_F64 * 100 + 18: launch_sf<HMC_F64, 18>(a, dagger, nb, st); break;
+    case HMC_F64 * 100 + 12: launch_sf<HMC_F64, 12>(a, dagger, nb, st); break;
+    case HMC_F32 * 100 + 18: launch_sf<HMC_F32, 18>(a, dagger, nb, st); break;
+    case HMC_F32 * 100 + 12: launch_sf<HMC_F32, 12>(a, dagger, nb, st); break;
+    case HMC_F16 * 100 + 18: launch_sf<HMC_F16, 18>(a, dagger, nb, st); break;
+    case HMC_F16 * 100 + 12: launch_sf<HMC_F16, 12>(a, dagger, nb, st); break;
+    default:
+      return fail(ctx, HMC_EINVAL, "dslash: unsupported precision %d / link format %d", sprec,
+                  U.fmt);
+  }
+  return launched(ctx, "dslash");
+}
+
+int mhat(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, int sprec, int dagger, int n_rhs,
+         void *out, const void *in, void *tmp, double kappa, const double *cb_rhs,
+         double *partials, int *nblocks) {
+  DslashArgs a{};
+  a.g = g;
+  a.n_rhs = n_rhs;
+  a.gauge = U.data;
+  // tmp (odd) = H_oe in
+  a.p = 1;
+  a.out = tmp;
+  a.in = in;
+  a.x = nullptr;
+  a.ca = 0.0;
+  a.cb = 1.0;
+  int st = dslash(ctx, a, U, sprec, dagger, nullptr);
+  if (st) return st;
+  // out (even) = in - kappa^2 H_eo tmp
+  a.p = 0;
+  a.out = out;
+  a.in = tmp;
+  a.x = in;
+  a.ca = 1.0;
+  a.cb = -kappa * kappa;
+  a.cb_rhs = cb_rhs;
+  a.partials = partials;
+  return dslash(ctx, a, U, sprec, dagger, nblocks);
+}
+
+}  // namespace hmc

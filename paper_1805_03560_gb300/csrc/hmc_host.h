@@ -1,0 +1,99 @@
+// Host-side internals of libhmc: the context, error reporting, workspace and
+// the launchers that the C-ABI entry points compose.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+
+#include "hmc_internal.cuh"
+
+struct hmc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  long long launches = 0;
+  struct Buf {
+    void *p = nullptr;
+    size_t n = 0;
+  };
+  std::map<std::string, Buf> ws;
+  double *h_pinned = nullptr;  // small pinned host buffer for scalar reads
+};
+
+namespace hmc {
+
+constexpr int DS_NT = 128;   // threads per block, stencil kernels
+constexpr int BL_NT = 256;   // threads per block, BLAS kernels
+constexpr int FIN_NT = 1024; // threads of the single-block finalisers
+
+int fail(hmc_ctx *ctx, int code, const char *fmt, ...);
+// Checks the launch that just happened and counts it.
+int launched(hmc_ctx *ctx, const char *what);
+int cuda_ok(hmc_ctx *ctx, cudaError_t e, const char *what);
+// Device workspace owned by the context, grown on demand; nullptr on failure
+// (ctx->err set).  Contents are undefined on return.
+void *workspace(hmc_ctx *ctx, const char *name, size_t bytes);
+int check_lattice(hmc_ctx *ctx, const hmc_lattice *lat);
+int check_prec(hmc_ctx *ctx, int prec);
+int check_gauge(hmc_ctx *ctx, const hmc_gauge *U);
+
+inline int blocks_for(long long n, int nt) { return (int)((n + nt - 1) / nt); }
+
+size_t spinor_bytes(const Geo &g, int prec, int n_rhs);
+size_t gauge_bytes(const Geo &g, int prec, int fmt);
+
+// out (parity p) = cb * H_{p,1-p} in  [+ ca * x]; with dagger, gamma_5 H gamma_5.
+// cb_rhs (device, nullable) overrides cb per right-hand side.  partials
+// (device, nullable) receives one |out|^2 partial sum per block; *nblocks the
+// number of blocks.
+struct DslashArgs {
+  Geo g;
+  int p;
+  int n_rhs;
+  void *out;
+  const void *in;
+  const void *x;
+  const void *gauge;
+  double ca, cb;
+  const double *cb_rhs;
+  double *partials;
+  const int *gate;  // device flag (nullable): the launch does nothing when *gate == 0
+};
+int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int dagger,
+           int *nblocks);
+
+int zero_field(hmc_ctx *ctx, int prec, void *d, int S);
+int copy_convert(hmc_ctx *ctx, int pd, int ps, void *d, const void *s, int S);
+int norm_partials(hmc_ctx *ctx, int prec, const void *v, int S, double *partials, int *nb);
+// out = a x + b y (y nullable), any precision, n_rhs folded into S
+int axpby(hmc_ctx *ctx, int prec, void *out, double a, const void *x, double b, const void *y,
+          int S);
+// partial sums of Re <x, y> for F64 fields
+int dot_partials(hmc_ctx *ctx, const void *x, const void *y, int S, double *partials, int *nb);
+int hop_force(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, const void *We, const void *Wo,
+              const void *Ve, const void *Vo, double *F, double c);
+int gauge_force(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, double beta, double kappa, int k,
+                double coeff, double *F);
+int gauge_action_sums(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, int with_lines,
+                      double *partials, double *dst);
+int gauge_action_coeffs(hmc_ctx *ctx, const Geo &g, double beta, double kappa, int k,
+                        double *beta_eff, double cline[4], bool *lines);
+int update_momenta(hmc_ctx *ctx, const Geo &g, double *P, const double *F, double eps);
+int kinetic_partials(hmc_ctx *ctx, const Geo &g, const double *P, double *partials, int *nb);
+int update_links(hmc_ctx *ctx, const Geo &g, void *U, const double *P, double eps);
+int convert_gauge(hmc_ctx *ctx, const Geo &g, const void *src, void *dst, int prec, int fmt);
+int cg_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul, void *x,
+             const void *b, double kappa, double tol, int max_iter, const hmc_solver_opts *opts,
+             hmc_solve_stats *stats);
+
+// dst[0] = sum of partials[0..n) in a fixed order (one block).
+int reduce_partials(hmc_ctx *ctx, const double *partials, int n, double *dst);
+
+// Mhat (or Mhat^dag) on an even field: tmp (odd) = H_oe in; out = in - kappa^2 H_eo tmp.
+// partials (nullable) gets |out|^2 partials; *nblocks their count.
+int mhat(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, int sprec, int dagger, int n_rhs,
+         void *out, const void *in, void *tmp, double kappa, const double *cb_rhs,
+         double *partials, int *nblocks);
+
+}  // namespace hmc

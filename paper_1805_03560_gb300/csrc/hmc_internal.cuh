@@ -1,0 +1,382 @@
+// Internal device-side building blocks of libhmc: complex arithmetic, lattice
+// geometry, and the load/store traits of the spinor and gauge layouts that
+// include/hmc.h documents.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hmc.h"
+
+namespace hmc {
+
+// ---- complex ------------------------------------------------------------------
+
+template <typename R>
+struct Cx {
+  R re, im;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ Cx<R> mk(R a, R b) {
+  return Cx<R>{a, b};
+}
+template <typename R>
+__host__ __device__ __forceinline__ Cx<R> operator+(Cx<R> a, Cx<R> b) {
+  return {a.re + b.re, a.im + b.im};
+}
+template <typename R>
+__host__ __device__ __forceinline__ Cx<R> operator-(Cx<R> a, Cx<R> b) {
+  return {a.re - b.re, a.im - b.im};
+}
+template <typename R>
+__host__ __device__ __forceinline__ Cx<R> operator-(Cx<R> a) {
+  return {-a.re, -a.im};
+}
+template <typename R>
+__host__ __device__ __forceinline__ Cx<R> operator*(Cx<R> a, Cx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__host__ __device__ __forceinline__ Cx<R> operator*(R s, Cx<R> a) {
+  return {s * a.re, s * a.im};
+}
+template <typename R>
+__host__ __device__ __forceinline__ Cx<R> cj(Cx<R> a) {
+  return {a.re, -a.im};
+}
+// i * a
+template <typename R>
+__host__ __device__ __forceinline__ Cx<R> ti(Cx<R> a) {
+  return {-a.im, a.re};
+}
+// conj(a) * b
+template <typename R>
+__host__ __device__ __forceinline__ Cx<R> cjmul(Cx<R> a, Cx<R> b) {
+  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+// acc + a * b, written as fused multiply-adds
+template <typename R>
+__host__ __device__ __forceinline__ Cx<R> fmac(Cx<R> acc, Cx<R> a, Cx<R> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+  return acc;
+}
+// acc + conj(a) * b
+template <typename R>
+__host__ __device__ __forceinline__ Cx<R> fmacj(Cx<R> acc, Cx<R> a, Cx<R> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+  return acc;
+}
+template <typename R>
+__host__ __device__ __forceinline__ R norm2(Cx<R> a) {
+  return a.re * a.re + a.im * a.im;
+}
+
+// ---- geometry -----------------------------------------------------------------
+
+struct Geo {
+  int L[4];   // t, x, y, z
+  int st[4];  // lexicographic strides
+  int Vh;
+  int Lzh;
+};
+
+inline Geo make_geo(const hmc_lattice &lat) {
+  Geo g;
+  for (int i = 0; i < 4; ++i) g.L[i] = lat.L[i];
+  g.st[3] = 1;
+  g.st[2] = g.L[3];
+  g.st[1] = g.L[3] * g.L[2];
+  g.st[0] = g.L[3] * g.L[2] * g.L[1];
+  g.Vh = g.L[0] * g.st[0] / 2;
+  g.Lzh = g.L[3] / 2;
+  return g;
+}
+
+// Coordinates and lexicographic index of the h-th site of parity p.
+__device__ __forceinline__ int site_coords(const Geo &g, int h, int p, int c[4]) {
+  int zh = h % g.Lzh;
+  int q = h / g.Lzh;
+  c[2] = q % g.L[2];
+  q /= g.L[2];
+  c[1] = q % g.L[1];
+  c[0] = q / g.L[1];
+  c[3] = 2 * zh + ((c[0] + c[1] + c[2] + p) & 1);
+  return ((c[0] * g.L[1] + c[1]) * g.L[2] + c[2]) * g.L[3] + c[3];
+}
+
+// Half-site index of the neighbour of (lex, c) in direction mu, forwards or
+// backwards (periodic wrap; the fermion sign is handled by the caller).
+__device__ __forceinline__ int nb_fwd(const Geo &g, int lex, const int c[4], int mu) {
+  int d = (c[mu] + 1 == g.L[mu]) ? (1 - g.L[mu]) : 1;
+  return (lex + d * g.st[mu]) >> 1;
+}
+__device__ __forceinline__ int nb_bwd(const Geo &g, int lex, const int c[4], int mu) {
+  int d = (c[mu] == 0) ? (g.L[mu] - 1) : -1;
+  return (lex + d * g.st[mu]) >> 1;
+}
+
+// ---- spinor storage -----------------------------------------------------------
+
+template <int P>
+struct SpinorIO;
+
+template <>
+struct SpinorIO<HMC_F64> {
+  using R = double;
+  static size_t bytes(size_t S) { return S * 12 * sizeof(double2); }
+  static __device__ __forceinline__ void load(const void *base, int S, int s, Cx<double> v[12]) {
+    const double2 *b = (const double2 *)base;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      double2 t = __ldg(b + (size_t)c * S + s);
+      v[c] = {t.x, t.y};
+    }
+  }
+  static __device__ __forceinline__ void store(void *base, int S, int s, const Cx<double> v[12]) {
+    double2 *b = (double2 *)base;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) b[(size_t)c * S + s] = make_double2(v[c].re, v[c].im);
+  }
+};
+
+template <>
+struct SpinorIO<HMC_F32> {
+  using R = float;
+  static size_t bytes(size_t S) { return S * 6 * sizeof(float4); }
+  static __device__ __forceinline__ void load(const void *base, int S, int s, Cx<float> v[12]) {
+    const float4 *b = (const float4 *)base;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      float4 t = __ldg(b + (size_t)k * S + s);
+      v[2 * k] = {t.x, t.y};
+      v[2 * k + 1] = {t.z, t.w};
+    }
+  }
+  static __device__ __forceinline__ void store(void *base, int S, int s, const Cx<float> v[12]) {
+    float4 *b = (float4 *)base;
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      b[(size_t)k * S + s] = make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im);
+  }
+};
+
+// Half storage: 24 halves per site in three 16-byte chunks and one float
+// norm per site.  The norm is a power of two at least as large as the largest
+// |component|, so scaling by it is exact and only the half rounding is lossy.
+template <>
+struct SpinorIO<HMC_F16> {
+  using R = float;
+  static size_t bytes(size_t S) { return S * 3 * sizeof(uint4) + S * sizeof(float); }
+  static __device__ __forceinline__ void load(const void *base, int S, int s, Cx<float> v[12]) {
+    const uint4 *b = (const uint4 *)base;
+    const float *nrm = (const float *)(b + (size_t)3 * S);
+    float n = __ldg(nrm + s);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 t = __ldg(b + (size_t)k * S + s);
+      const __half2 *hp = reinterpret_cast<const __half2 *>(&t);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float2 f = __half22float2(hp[j]);
+        v[4 * k + j] = {f.x * n, f.y * n};
+      }
+    }
+  }
+  static __device__ __forceinline__ void store(void *base, int S, int s, const Cx<float> v[12]) {
+    uint4 *b = (uint4 *)base;
+    float *nrm = (float *)(b + (size_t)3 * S);
+    float m = 0.f;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) m = fmaxf(m, fmaxf(fabsf(v[c].re), fabsf(v[c].im)));
+    float n = 0.f, inv = 0.f;
+    if (m > 0.f) {
+      int e;
+      frexpf(m, &e);  // m = f * 2^e, f in [0.5, 1)
+      n = ldexpf(1.f, e);
+      inv = ldexpf(1.f, -e);
+    }
+    nrm[s] = n;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 t;
+      __half2 *hp = reinterpret_cast<__half2 *>(&t);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        hp[j] = __floats2half2_rn(v[4 * k + j].re * inv, v[4 * k + j].im * inv);
+      b[(size_t)k * S + s] = t;
+    }
+  }
+};
+
+// ---- gauge storage -------------------------------------------------------------
+
+// Third row of an SU(3) matrix from the first two: conj(row0 x row1).
+template <typename R>
+__device__ __forceinline__ void reconstruct_row2(Cx<R> u[9]) {
+  u[6] = cj(u[1] * u[5] - u[2] * u[4]);
+  u[7] = cj(u[2] * u[3] - u[0] * u[5]);
+  u[8] = cj(u[0] * u[4] - u[1] * u[3]);
+}
+
+template <int P, int FMT>
+struct LinkIO;
+
+// chunks per link
+template <int P, int FMT>
+struct LinkNC {
+  static constexpr int value = (FMT == 18) ? 9 : ((P == HMC_F64) ? 6 : 3);
+};
+
+template <int FMT>
+struct LinkIO<HMC_F64, FMT> {
+  using R = double;
+  static constexpr int NC = LinkNC<HMC_F64, FMT>::value;
+  static constexpr size_t chunk = 16;
+  // base: chunk array of this parity and direction, Vh: chunk stride
+  static __device__ __forceinline__ void load(const void *base, int Vh, int h, Cx<double> u[9]) {
+    const double2 *b = (const double2 *)base;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      double2 t = __ldg(b + (size_t)c * Vh + h);
+      u[c] = {t.x, t.y};
+    }
+    if (FMT == 12) reconstruct_row2(u);
+  }
+  static __device__ __forceinline__ void store(void *base, int Vh, int h, const Cx<double> u[9]) {
+    double2 *b = (double2 *)base;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) b[(size_t)c * Vh + h] = make_double2(u[c].re, u[c].im);
+  }
+};
+
+template <>
+struct LinkIO<HMC_F32, 18> {
+  using R = float;
+  static constexpr int NC = 9;
+  static constexpr size_t chunk = 8;
+  static __device__ __forceinline__ void load(const void *base, int Vh, int h, Cx<float> u[9]) {
+    const float2 *b = (const float2 *)base;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      float2 t = __ldg(b + (size_t)c * Vh + h);
+      u[c] = {t.x, t.y};
+    }
+  }
+  static __device__ __forceinline__ void store(void *base, int Vh, int h, const Cx<double> u[9]) {
+    float2 *b = (float2 *)base;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) b[(size_t)c * Vh + h] = make_float2((float)u[c].re, (float)u[c].im);
+  }
+};
+
+template <>
+struct LinkIO<HMC_F32, 12> {
+  using R = float;
+  static constexpr int NC = 3;
+  static constexpr size_t chunk = 16;
+  static __device__ __forceinline__ void load(const void *base, int Vh, int h, Cx<float> u[9]) {
+    const float4 *b = (const float4 *)base;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float4 t = __ldg(b + (size_t)c * Vh + h);
+      u[2 * c] = {t.x, t.y};
+      u[2 * c + 1] = {t.z, t.w};
+    }
+    reconstruct_row2(u);
+  }
+  static __device__ __forceinline__ void store(void *base, int Vh, int h, const Cx<double> u[9]) {
+    float4 *b = (float4 *)base;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      b[(size_t)c * Vh + h] = make_float4((float)u[2 * c].re, (float)u[2 * c].im,
+                                          (float)u[2 * c + 1].re, (float)u[2 * c + 1].im);
+  }
+};
+
+template <>
+struct LinkIO<HMC_F16, 18> {
+  using R = float;
+  static constexpr int NC = 9;
+  static constexpr size_t chunk = 4;
+  static __device__ __forceinline__ void load(const void *base, int Vh, int h, Cx<float> u[9]) {
+    const __half2 *b = (const __half2 *)base;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      float2 t = __half22float2(b[(size_t)c * Vh + h]);
+      u[c] = {t.x, t.y};
+    }
+  }
+  static __device__ __forceinline__ void store(void *base, int Vh, int h, const Cx<double> u[9]) {
+    __half2 *b = (__half2 *)base;
+#pragma unroll
+    for (int c = 0; c < 9; ++c)
+      b[(size_t)c * Vh + h] = __floats2half2_rn((float)u[c].re, (float)u[c].im);
+  }
+};
+
+template <>
+struct LinkIO<HMC_F16, 12> {
+  using R = float;
+  static constexpr int NC = 3;
+  static constexpr size_t chunk = 8;
+  static __device__ __forceinline__ void load(const void *base, int Vh, int h, Cx<float> u[9]) {
+    const uint2 *b = (const uint2 *)base;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      uint2 t = __ldg(b + (size_t)c * Vh + h);
+      const __half2 *hp = reinterpret_cast<const __half2 *>(&t);
+      float2 a = __half22float2(hp[0]), d = __half22float2(hp[1]);
+      u[2 * c] = {a.x, a.y};
+      u[2 * c + 1] = {d.x, d.y};
+    }
+    reconstruct_row2(u);
+  }
+  static __device__ __forceinline__ void store(void *base, int Vh, int h, const Cx<double> u[9]) {
+    uint2 *b = (uint2 *)base;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      uint2 t;
+      __half2 *hp = reinterpret_cast<__half2 *>(&t);
+      hp[0] = __floats2half2_rn((float)u[2 * c].re, (float)u[2 * c].im);
+      hp[1] = __floats2half2_rn((float)u[2 * c + 1].re, (float)u[2 * c + 1].im);
+      b[(size_t)c * Vh + h] = t;
+    }
+  }
+};
+
+// Chunk array of the links of base parity p, direction mu.
+template <int P, int FMT>
+__device__ __forceinline__ const void *link_base(const void *gauge, int Vh, int p, int mu) {
+  using IO = LinkIO<P, FMT>;
+  return (const char *)gauge + (size_t)(p * 4 + mu) * IO::NC * Vh * IO::chunk;
+}
+
+// ---- block reductions -----------------------------------------------------------
+
+// Sum of v over the block; the result is valid in thread 0.  Fixed order, so
+// repeated runs give bit-identical sums.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[NT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) s += red[i];
+  }
+  return s;
+}
+
+}  // namespace hmc

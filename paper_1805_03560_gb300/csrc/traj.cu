@@ -1,0 +1,469 @@
+// C-ABI entry points for actions, forces, the filter polynomial, the
+// molecular-dynamics steps and the HMC trajectory (Sec. I and Sec. II).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "hmc_host.h"
+
+namespace hmc {
+
+#define TRY(e)         \
+  do {                 \
+    int _s = (e);      \
+    if (_s) return _s; \
+  } while (0)
+
+static int read_dev(hmc_ctx *ctx, const double *dev, int n, double *host) {
+  cudaError_t e =
+      cudaMemcpyAsync(ctx->h_pinned, dev, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  TRY(cuda_ok(ctx, e, "reading a device scalar"));
+  for (int i = 0; i < n; ++i) host[i] = ctx->h_pinned[i];
+  return HMC_OK;
+}
+
+static double *scalars(hmc_ctx *ctx) { return (double *)workspace(ctx, "tr_scalars", 64 * 8); }
+
+static double *partials_buf(hmc_ctx *ctx, const Geo &g) {
+  // enough for two reductions over 8 Vh elements in blocks of 128
+  return (double *)workspace(ctx, "tr_partials", sizeof(double) * (2 * (8LL * g.Vh / 128 + 2) + 64));
+}
+
+// S_G + T_k on the host
+static int gauge_action(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, double beta, double kappa,
+                        int k, double *S, double *plaq_sum) {
+  double beff, cl[4];
+  bool lines;
+  TRY(gauge_action_coeffs(ctx, g, beta, kappa, k, &beff, cl, &lines));
+  double *part = partials_buf(ctx, g), *dst = scalars(ctx);
+  if (!part || !dst) return HMC_ENOMEM;
+  TRY(gauge_action_sums(ctx, g, U, lines ? 1 : 0, part, dst));
+  double h[2];
+  TRY(read_dev(ctx, dst, 2, h));
+  const double k4 = kappa * kappa * kappa * kappa;
+  *S = -beff / 3.0 * h[0] + (lines ? 32.0 * k4 * h[1] : 0.0);
+  if (plaq_sum) *plaq_sum = h[0];
+  if (!std::isfinite(*S)) return fail(ctx, HMC_ENAN, "gauge action is not finite");
+  return HMC_OK;
+}
+
+static int norm2_host(hmc_ctx *ctx, const Geo &g, int prec, const void *v, double *out) {
+  double *part = partials_buf(ctx, g), *dst = scalars(ctx);
+  if (!part || !dst) return HMC_ENOMEM;
+  int nb;
+  TRY(norm_partials(ctx, prec, v, g.Vh, part, &nb));
+  TRY(reduce_partials(ctx, part, nb, dst));
+  return read_dev(ctx, dst, 1, out);
+}
+
+static int dot_host(hmc_ctx *ctx, const Geo &g, const void *x, const void *y, double *out) {
+  double *part = partials_buf(ctx, g), *dst = scalars(ctx);
+  if (!part || !dst) return HMC_ENOMEM;
+  int nb;
+  TRY(dot_partials(ctx, x, y, g.Vh, part, &nb));
+  TRY(reduce_partials(ctx, part, nb, dst));
+  return read_dev(ctx, dst, 1, out);
+}
+
+// out = c_x * x + cb * H_{p,1-p}(in)   (one hemi-Dslash)
+static int hop(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, int prec, int p, int dagger,
+               void *out, const void *in, const void *x, double cx, double cb) {
+  DslashArgs a{};
+  a.g = g;
+  a.n_rhs = 1;
+  a.gauge = U.data;
+  a.p = p;
+  a.out = out;
+  a.in = in;
+  a.x = x;
+  a.ca = cx;
+  a.cb = cb;
+  return dslash(ctx, a, U, prec, dagger, nullptr);
+}
+
+// out = c * x + K in   (K = kappa^2 H_eo H_oe, or K^dag), tmp: odd field
+static int apply_K(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, int prec, int dagger,
+                   double kappa, void *out, const void *in, const void *x, double c, void *tmp) {
+  TRY(hop(ctx, g, U, prec, 1, dagger, tmp, in, nullptr, 0.0, 1.0));
+  return hop(ctx, g, U, prec, 0, dagger, out, tmp, x, c, kappa * kappa);
+}
+
+static void add_stats(hmc_solve_stats *acc, const hmc_solve_stats &s) {
+  if (!acc) return;
+  acc->iterations += s.iterations;
+  acc->reliable_updates += s.reliable_updates;
+  acc->true_rel_res = fmax(acc->true_rel_res, s.true_rel_res);
+}
+
+static int solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul, void *x,
+                 const void *b, double kappa, double tol, const hmc_solver_opts *opts,
+                 hmc_solve_stats *acc) {
+  hmc_solve_stats s{};
+  int st = cg_solve(ctx, g, Uh, Ul, x, b, kappa, tol, 100000, opts, &s);
+  add_stats(acc, s);
+  return st;
+}
+
+// F += coeff * d/dU 2 Re[A^dag dK B] = coeff kappa^2 (W^dag dH V + h.c.),
+// W = (A, H_eo^dag A), V = (B, H_oe B)
+static int pair_force(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, double kappa, const void *A,
+                      const void *B, double coeff, double *F) {
+  size_t f64 = spinor_bytes(g, HMC_F64, 1);
+  void *Wo = workspace(ctx, "pf_wo", f64), *Vo = workspace(ctx, "pf_vo", f64);
+  if (!Wo || !Vo) return HMC_ENOMEM;
+  TRY(hop(ctx, g, U, HMC_F64, 1, 1, Wo, A, nullptr, 0.0, 1.0));  // H_eo^dag A
+  TRY(hop(ctx, g, U, HMC_F64, 1, 0, Vo, B, nullptr, 0.0, 1.0));  // H_oe B
+  return hop_force(ctx, g, U, A, Wo, B, Vo, F, coeff * kappa * kappa);
+}
+
+// y = Mhat^{-1} phi via the normal equations
+static int mhat_inverse(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
+                        void *y, const void *phi, double kappa, double tol,
+                        const hmc_solver_opts *opts, hmc_solve_stats *acc) {
+  size_t f64 = spinor_bytes(g, HMC_F64, 1);
+  void *src = workspace(ctx, "pf_src", f64), *tmp = workspace(ctx, "pf_tmp", f64);
+  if (!src || !tmp) return HMC_ENOMEM;
+  TRY(mhat(ctx, g, Uh, HMC_F64, 1, 1, src, phi, tmp, kappa, nullptr, nullptr, nullptr));
+  return solve(ctx, g, Uh, Ul, y, src, kappa, tol, opts, acc);
+}
+
+int force_pf(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
+             const void *phi, double kappa, const hmc_filter *filt, double coeff, double *F,
+             double tol, const hmc_solver_opts *opts, hmc_solve_stats *acc) {
+  size_t f64 = spinor_bytes(g, HMC_F64, 1);
+  void *X = workspace(ctx, "pf_x", f64), *Y = workspace(ctx, "pf_y", f64);
+  void *tmp = workspace(ctx, "pf_tmp", f64);
+  if (!X || !Y || !tmp) return HMC_ENOMEM;
+  if (!filt) {
+    // X = (Mhat^dag Mhat)^{-1} phi, Y = Mhat X; delta S = 2 Re[Y^dag dK ... ] form
+    TRY(solve(ctx, g, Uh, Ul, X, phi, kappa, tol, opts, acc));
+    TRY(mhat(ctx, g, Uh, HMC_F64, 0, 1, Y, X, tmp, kappa, nullptr, nullptr, nullptr));
+    return pair_force(ctx, g, Uh, kappa, Y, X, coeff, F);
+  }
+  const int n = filt->n;
+  if (n < 0 || !filt->b) return fail(ctx, HMC_EINVAL, "force_pf: bad filter");
+  // Horner iterates Y_n .. Y_0 (Y_j at slot j)
+  char *Hs = (char *)workspace(ctx, "pf_horner", f64 * (n + 1));
+  void *Yt = workspace(ctx, "pf_ytilde", f64), *Xt = workspace(ctx, "pf_xtilde", f64);
+  void *Xi = workspace(ctx, "pf_xi", f64), *Xn = workspace(ctx, "pf_xnext", f64);
+  if (!Hs || !Yt || !Xt || !Xi || !Xn) return HMC_ENOMEM;
+  auto slot = [&](int j) { return (void *)(Hs + f64 * j); };
+  TRY(axpby(ctx, HMC_F64, slot(n), filt->b[n], phi, 0.0, nullptr, g.Vh));
+  for (int j = n; j >= 1; --j)
+    TRY(apply_K(ctx, g, Uh, HMC_F64, 0, kappa, slot(j - 1), slot(j), phi, filt->b[j - 1], tmp));
+  // Ytilde = alpha Mhat^{-1} phi
+  TRY(mhat_inverse(ctx, g, Uh, Ul, Yt, phi, kappa, tol, opts, acc));
+  TRY(axpby(ctx, HMC_F64, Yt, filt->alpha, Yt, 0.0, nullptr, g.Vh));
+  // X_1 = Y_0 + Ytilde ; Xtilde = Mhat (Mhat^dag Mhat)^{-1} X_1
+  TRY(axpby(ctx, HMC_F64, Xi, 1.0, slot(0), 1.0, Yt, g.Vh));
+  TRY(solve(ctx, g, Uh, Ul, X, Xi, kappa, tol, opts, acc));
+  TRY(mhat(ctx, g, Uh, HMC_F64, 0, 1, Xt, X, tmp, kappa, nullptr, nullptr, nullptr));
+  TRY(pair_force(ctx, g, Uh, kappa, Xt, Yt, coeff, F));
+  for (int i = 1; i <= n; ++i) {
+    TRY(pair_force(ctx, g, Uh, kappa, Xi, slot(i), coeff, F));
+    if (i < n) {
+      TRY(apply_K(ctx, g, Uh, HMC_F64, 1, kappa, Xn, Xi, nullptr, 0.0, tmp));
+      void *t = Xi;
+      Xi = Xn;
+      Xn = t;
+    }
+  }
+  return HMC_OK;
+}
+
+int action_pf(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
+              const void *phi, double kappa, const hmc_filter *filt, double tol,
+              const hmc_solver_opts *opts, double *S, hmc_solve_stats *acc) {
+  size_t f64 = spinor_bytes(g, HMC_F64, 1);
+  void *X = workspace(ctx, "pa_x", f64), *Z = workspace(ctx, "pa_z", f64);
+  void *tmp = workspace(ctx, "pa_tmp", f64);
+  if (!X || !Z || !tmp) return HMC_ENOMEM;
+  if (!filt) {
+    TRY(solve(ctx, g, Uh, Ul, X, phi, kappa, tol, opts, acc));
+    return dot_host(ctx, g, phi, X, S);
+  }
+  const int n = filt->n;
+  if (n < 0 || !filt->b) return fail(ctx, HMC_EINVAL, "action_pf: bad filter");
+  // Z = sum_j b_j K^j phi (Horner), then Z += alpha Mhat^{-1} phi
+  TRY(axpby(ctx, HMC_F64, Z, filt->b[n], phi, 0.0, nullptr, g.Vh));
+  for (int j = n - 1; j >= 0; --j)
+    TRY(apply_K(ctx, g, Uh, HMC_F64, 0, kappa, Z, Z, phi, filt->b[j], tmp));
+  TRY(mhat_inverse(ctx, g, Uh, Ul, X, phi, kappa, tol, opts, acc));
+  TRY(axpby(ctx, HMC_F64, Z, 1.0, Z, filt->alpha, X, g.Vh));
+  return norm2_host(ctx, g, HMC_F64, Z, S);
+}
+
+// Leapfrog on two time scales (Sec. I; gauge on the fine scale, pseudo-fermion
+// on the coarse one, Sec. IV): per coarse step
+//   P_PF(dt/2) [P_G(dt0/2) T(dt0) P_G(dt0/2)]^n_gauge P_PF(dt/2),  dt0 = dt/n_gauge.
+// Adjacent momentum steps of the same force at the same U are merged (the sum
+// of the two half steps), which leaves the integrator unchanged.  U1 is the
+// F64/LINK18 field, Ulo its inner-precision copy (refreshed from U1 before
+// every pseudo-fermion force), F scratch for the force.
+int md_evolve(hmc_ctx *ctx, const Geo &g, void *U1, void *Ulo, double *P, double *F,
+              const void *phi, const hmc_traj_params *prm, int *solves, hmc_solve_stats *acc) {
+  const int plo = prm->solver.inner_prec;
+  const int fmt_lo = prm->link_fmt_lo ? prm->link_fmt_lo : HMC_LINK12;
+  const int k = prm->filter_k;
+  hmc_gauge Uh{U1, HMC_F64, HMC_LINK18};
+  hmc_gauge Ul{Ulo, plo, fmt_lo};
+  const hmc_gauge *Ulp = plo != HMC_F64 ? &Ul : nullptr;
+  hmc_filter fmd{prm->b, prm->n_t, prm->alpha};
+  const hmc_filter *filt_md = k ? &fmd : nullptr;
+  const size_t fbytes = (size_t)g.Vh * 2 * 4 * 8 * sizeof(double);
+  cudaStream_t st = ctx->stream;
+  const double dt = prm->tau / prm->n_md, dt0 = dt / prm->n_gauge;
+  auto pf_step = [&](double eps) -> int {
+    TRY(cuda_ok(ctx, cudaMemsetAsync(F, 0, fbytes, st), "md: zero F"));
+    if (plo != HMC_F64) TRY(convert_gauge(ctx, g, U1, Ulo, plo, fmt_lo));
+    TRY(force_pf(ctx, g, Uh, Ulp, phi, prm->kappa, filt_md, 1.0, F, prm->tol_md, &prm->solver,
+                 acc));
+    *solves += k ? 2 : 1;
+    return update_momenta(ctx, g, P, F, eps);
+  };
+  auto gauge_step = [&](double eps) -> int {
+    TRY(cuda_ok(ctx, cudaMemsetAsync(F, 0, fbytes, st), "md: zero F"));
+    TRY(gauge_force(ctx, g, Uh, prm->beta, prm->kappa, k, 1.0, F));
+    return update_momenta(ctx, g, P, F, eps);
+  };
+  TRY(pf_step(0.5 * dt));
+  for (int s = 0; s < prm->n_md; ++s) {
+    TRY(gauge_step(0.5 * dt0));
+    for (int j = 0; j < prm->n_gauge; ++j) {
+      TRY(update_links(ctx, g, U1, P, dt0));
+      TRY(gauge_step(j + 1 < prm->n_gauge ? dt0 : 0.5 * dt0));
+    }
+    TRY(pf_step(s + 1 < prm->n_md ? dt : 0.5 * dt));
+  }
+  return HMC_OK;
+}
+
+static int check_traj_params(hmc_ctx *ctx, const hmc_traj_params *prm) {
+  if (prm->n_md < 1 || prm->n_gauge < 1 || !(prm->tau > 0))
+    return fail(ctx, HMC_EINVAL, "trajectory: need n_md, n_gauge >= 1 and tau > 0");
+  if (prm->filter_k < 0 || prm->filter_k > 2)
+    return fail(ctx, HMC_EINVAL, "trajectory: filter_k must be 0, 1 or 2");
+  if (prm->filter_k > 0 && (!prm->b || !prm->c || prm->n_t < 0 || prm->n_max < prm->n_t))
+    return fail(ctx, HMC_EINVAL, "trajectory: filter needs b, c and 0 <= n_t <= n_max");
+  return check_prec(ctx, prm->solver.inner_prec);
+}
+
+}  // namespace hmc
+
+using namespace hmc;
+
+#define CTX_CHECK(ctx) \
+  if (!(ctx)) return HMC_EINVAL
+
+static int check_solver_args(hmc_ctx *ctx, const hmc_gauge *U_hi, const hmc_gauge *U_lo,
+                             const hmc_solver_opts *opts) {
+  TRY(check_gauge(ctx, U_hi));
+  if (U_hi->prec != HMC_F64) return fail(ctx, HMC_EINVAL, "U_hi must be F64");
+  if (opts && opts->inner_prec != HMC_F64) TRY(check_gauge(ctx, U_lo));
+  return HMC_OK;
+}
+
+extern "C" {
+
+int hmc_force_pf(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
+                 const hmc_gauge *U_lo, const void *phi, double kappa, const hmc_filter *filt,
+                 double coeff, double *F, double tol, const hmc_solver_opts *opts,
+                 hmc_solve_stats *stats) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  TRY(check_solver_args(ctx, U_hi, U_lo, opts));
+  if (!phi || !F) return fail(ctx, HMC_EINVAL, "force_pf: NULL field");
+  if (stats) memset(stats, 0, sizeof(*stats));
+  return force_pf(ctx, make_geo(*lat), *U_hi, U_lo, phi, kappa, filt, coeff, F, tol, opts, stats);
+}
+
+int hmc_action_pf(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
+                  const hmc_gauge *U_lo, const void *phi, double kappa, const hmc_filter *filt,
+                  double tol, const hmc_solver_opts *opts, double *action,
+                  hmc_solve_stats *stats) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  TRY(check_solver_args(ctx, U_hi, U_lo, opts));
+  if (!phi || !action) return fail(ctx, HMC_EINVAL, "action_pf: NULL argument");
+  if (stats) memset(stats, 0, sizeof(*stats));
+  return action_pf(ctx, make_geo(*lat), *U_hi, U_lo, phi, kappa, filt, tol, opts, action, stats);
+}
+
+int hmc_force_hopexp(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U, double beta,
+                     double kappa, int k, double coeff, double *F, double *action) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  TRY(check_gauge(ctx, U));
+  if (U->prec != HMC_F64) return fail(ctx, HMC_EINVAL, "force_hopexp: U must be F64");
+  Geo g = make_geo(*lat);
+  if (F) TRY(gauge_force(ctx, g, *U, beta, kappa, k, coeff, F));
+  if (action) TRY(gauge_action(ctx, g, *U, beta, kappa, k, action, nullptr));
+  return HMC_OK;
+}
+
+int hmc_plaquette(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U, double *plaq) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  TRY(check_gauge(ctx, U));
+  if (U->prec != HMC_F64 || !plaq) return fail(ctx, HMC_EINVAL, "plaquette: U must be F64");
+  Geo g = make_geo(*lat);
+  double S, ps;
+  TRY(gauge_action(ctx, g, *U, 0.0, 0.0, 0, &S, &ps));
+  *plaq = ps / (18.0 * 2.0 * g.Vh);
+  return HMC_OK;
+}
+
+int hmc_poly_apply(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U, void *out,
+                   const void *in, const double *coeffs, int degree, double kappa, int prec,
+                   void *horner_store) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  TRY(check_gauge(ctx, U));
+  TRY(check_prec(ctx, prec));
+  if (!out || !in || !coeffs || degree < 0) return fail(ctx, HMC_EINVAL, "poly_apply: bad args");
+  if (out == in) return fail(ctx, HMC_EINVAL, "poly_apply: out must not alias in");
+  Geo g = make_geo(*lat);
+  size_t fb = spinor_bytes(g, prec, 1);
+  void *tmp = workspace(ctx, "poly_tmp", fb);
+  if (!tmp) return HMC_ENOMEM;
+  TRY(axpby(ctx, prec, out, coeffs[degree], in, 0.0, nullptr, g.Vh));
+  if (horner_store)
+    TRY(copy_convert(ctx, prec, prec, (char *)horner_store + fb * degree, out, g.Vh));
+  for (int j = degree - 1; j >= 0; --j) {
+    TRY(apply_K(ctx, g, *U, prec, 0, kappa, out, out, in, coeffs[j], tmp));
+    if (horner_store) TRY(copy_convert(ctx, prec, prec, (char *)horner_store + fb * j, out, g.Vh));
+  }
+  return HMC_OK;
+}
+
+int hmc_update_links(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const double *P, double eps) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  if (!U || !P) return fail(ctx, HMC_EINVAL, "update_links: NULL");
+  return update_links(ctx, make_geo(*lat), U, P, eps);
+}
+
+int hmc_update_momenta(hmc_ctx *ctx, const hmc_lattice *lat, double *P, const double *F,
+                       double eps) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  if (!P || !F) return fail(ctx, HMC_EINVAL, "update_momenta: NULL");
+  return update_momenta(ctx, make_geo(*lat), P, F, eps);
+}
+
+int hmc_kinetic(hmc_ctx *ctx, const hmc_lattice *lat, const double *P, double *out) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  if (!P || !out) return fail(ctx, HMC_EINVAL, "kinetic: NULL");
+  Geo g = make_geo(*lat);
+  double *part = partials_buf(ctx, g), *dst = scalars(ctx);
+  if (!part || !dst) return HMC_ENOMEM;
+  int nb;
+  TRY(kinetic_partials(ctx, g, P, part, &nb));
+  TRY(reduce_partials(ctx, part, nb, dst));
+  double s;
+  TRY(read_dev(ctx, dst, 1, &s));
+  *out = 0.5 * s;
+  return HMC_OK;
+}
+
+int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj_params *prm,
+                   const double *P0, const void *eta, double u, hmc_traj_result *res,
+                   void *U_end, double *P_end) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  if (!U || !prm || !P0 || !eta || !res) return fail(ctx, HMC_EINVAL, "trajectory: NULL argument");
+  TRY(check_traj_params(ctx, prm));
+  memset(res, 0, sizeof(*res));
+  Geo g = make_geo(*lat);
+  const int plo = prm->solver.inner_prec;
+  const int fmt_lo = prm->link_fmt_lo ? prm->link_fmt_lo : HMC_LINK12;
+  TRY(check_prec(ctx, plo));
+  const size_t gb = gauge_bytes(g, HMC_F64, 18), f64 = spinor_bytes(g, HMC_F64, 1);
+  const size_t ab = (size_t)g.Vh * 2 * 4 * 8 * sizeof(double);
+  void *U1 = workspace(ctx, "tr_u1", gb);
+  void *Ulo = plo != HMC_F64 ? workspace(ctx, "tr_ulo", gauge_bytes(g, plo, fmt_lo)) : nullptr;
+  double *P = (double *)workspace(ctx, "tr_p", ab), *F = (double *)workspace(ctx, "tr_f", ab);
+  void *phi = workspace(ctx, "tr_phi", f64), *t1 = workspace(ctx, "tr_t1", f64);
+  void *t2 = workspace(ctx, "tr_t2", f64);
+  if (!U1 || (plo != HMC_F64 && !Ulo) || !P || !F || !phi || !t1 || !t2) return HMC_ENOMEM;
+  cudaStream_t st = ctx->stream;
+  TRY(cuda_ok(ctx, cudaMemcpyAsync(U1, U, gb, cudaMemcpyDeviceToDevice, st), "trajectory: copy U"));
+  TRY(cuda_ok(ctx, cudaMemcpyAsync(P, P0, ab, cudaMemcpyDeviceToDevice, st), "trajectory: copy P"));
+  hmc_gauge Uh{U1, HMC_F64, HMC_LINK18};
+  hmc_gauge Ul{Ulo, plo, fmt_lo};
+  const hmc_gauge *Ulp = plo != HMC_F64 ? &Ul : nullptr;
+  auto refresh_lo = [&]() -> int {
+    if (plo == HMC_F64) return HMC_OK;
+    return convert_gauge(ctx, g, U1, Ulo, plo, fmt_lo);
+  };
+  const int k = prm->filter_k;
+  hmc_filter fmd{prm->b, prm->n_t, prm->alpha}, fact{prm->b, prm->n_max, prm->alpha};
+  const hmc_filter *filt_md = k ? &fmd : nullptr, *filt_act = k ? &fact : nullptr;
+  hmc_solve_stats acc{};
+  // heatbath of the pseudo-fermion field and H0
+  double kin0, sg0, spf0;
+  if (k == 0) {
+    TRY(mhat(ctx, g, Uh, HMC_F64, 1, 1, phi, eta, t1, prm->kappa, nullptr, nullptr, nullptr));
+    TRY(norm2_host(ctx, g, HMC_F64, eta, &spf0));  // S_PF(Mhat^dag eta) = |eta|^2
+  } else {
+    TRY(hmc_poly_apply(ctx, lat, &Uh, t2, eta, prm->c, prm->n_max, prm->kappa, HMC_F64, nullptr));
+    TRY(mhat(ctx, g, Uh, HMC_F64, 0, 1, phi, t2, t1, prm->kappa, nullptr, nullptr, nullptr));
+    TRY(refresh_lo());
+    TRY(action_pf(ctx, g, Uh, Ulp, phi, prm->kappa, filt_act, prm->tol_action, &prm->solver,
+                  &spf0, &acc));
+    res->solves += 2;
+  }
+  TRY(hmc_kinetic(ctx, lat, P, &kin0));
+  double ps0;
+  TRY(gauge_action(ctx, g, Uh, prm->beta, prm->kappa, k, &sg0, &ps0));
+  res->plaq0 = ps0 / (18.0 * 2.0 * g.Vh);
+  res->H0 = kin0 + sg0 + spf0;
+  (void)filt_md;
+  TRY(md_evolve(ctx, g, U1, Ulo, P, F, phi, prm, &res->solves, &acc));
+  // H1 with the action solves
+  double kin1, sg1, spf1, ps1;
+  TRY(hmc_kinetic(ctx, lat, P, &kin1));
+  TRY(gauge_action(ctx, g, Uh, prm->beta, prm->kappa, k, &sg1, &ps1));
+  TRY(refresh_lo());
+  TRY(action_pf(ctx, g, Uh, Ulp, phi, prm->kappa, filt_act, prm->tol_action, &prm->solver, &spf1,
+                &acc));
+  res->solves += 1;
+  res->H1 = kin1 + sg1 + spf1;
+  res->dH = res->H1 - res->H0;
+  res->plaq1 = ps1 / (18.0 * 2.0 * g.Vh);
+  res->cg_iterations = acc.iterations;
+  if (!std::isfinite(res->dH)) return fail(ctx, HMC_ENAN, "trajectory: dH is not finite");
+  res->accepted = u < exp(-res->dH) ? 1 : 0;
+  if (U_end) TRY(cuda_ok(ctx, cudaMemcpyAsync(U_end, U1, gb, cudaMemcpyDeviceToDevice, st), "U_end"));
+  if (P_end) TRY(cuda_ok(ctx, cudaMemcpyAsync(P_end, P, ab, cudaMemcpyDeviceToDevice, st), "P_end"));
+  if (res->accepted) TRY(cuda_ok(ctx, cudaMemcpyAsync(U, U1, gb, cudaMemcpyDeviceToDevice, st), "U"));
+  return cuda_ok(ctx, cudaStreamSynchronize(st), "trajectory");
+}
+
+}  // extern "C"
+
+extern "C" int hmc_md_evolve(hmc_ctx *ctx, const hmc_lattice *lat, void *U, double *P,
+                             const void *phi, const hmc_traj_params *prm, hmc_traj_result *res) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  if (!U || !P || !phi || !prm) return fail(ctx, HMC_EINVAL, "md_evolve: NULL argument");
+  TRY(check_traj_params(ctx, prm));
+  Geo g = make_geo(*lat);
+  const int plo = prm->solver.inner_prec;
+  const int fmt_lo = prm->link_fmt_lo ? prm->link_fmt_lo : HMC_LINK12;
+  const size_t ab = (size_t)g.Vh * 2 * 4 * 8 * sizeof(double);
+  void *Ulo = plo != HMC_F64 ? workspace(ctx, "tr_ulo", gauge_bytes(g, plo, fmt_lo)) : nullptr;
+  double *F = (double *)workspace(ctx, "tr_f", ab);
+  if ((plo != HMC_F64 && !Ulo) || !F) return HMC_ENOMEM;
+  hmc_solve_stats acc{};
+  int solves = 0;
+  TRY(md_evolve(ctx, g, U, Ulo, P, F, phi, prm, &solves, &acc));
+  if (res) {
+    memset(res, 0, sizeof(*res));
+    res->cg_iterations = acc.iterations;
+    res->solves = solves;
+  }
+  return cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), "md_evolve");
+}

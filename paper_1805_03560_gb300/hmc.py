@@ -1,0 +1,429 @@
+"""Thin ctypes binding of libhmc (include/hmc.h).  Argument marshalling only:
+every step runs in the CUDA library.  Device memory comes from PyTorch; each
+call runs on torch's current CUDA stream.
+
+Importing this module loads libhmc.so and raises if it is missing: there is no
+CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhmc.so")
+
+F64, F32, F16 = 0, 1, 2
+LINK18, LINK12 = 18, 12
+PREC_NAMES = {F64: "f64", F32: "f32", F16: "f16"}
+
+OK, EINVAL, ENOMEM, ENOCONV, ETIMEOUT, ENAN, ECUDA = range(7)
+_STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ENOCONV", 4: "ETIMEOUT", 5: "ENAN", 6: "ECUDA"}
+
+_P, _I, _D, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+
+
+class Lat(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int * 4)]
+
+
+class Gauge(ctypes.Structure):
+    _fields_ = [("data", _P), ("prec", _I), ("fmt", _I)]
+
+
+class SolverOpts(ctypes.Structure):
+    _fields_ = [("inner_prec", _I), ("reliable_delta", _D), ("check_every", _I)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("iterations", _I), ("reliable_updates", _I), ("true_rel_res", _D)]
+
+
+class Filter(ctypes.Structure):
+    _fields_ = [("b", _P), ("n", _I), ("alpha", _D)]
+
+
+class TrajParams(ctypes.Structure):
+    _fields_ = [("beta", _D), ("kappa", _D), ("tau", _D),
+                ("n_md", _I), ("n_gauge", _I), ("filter_k", _I), ("n_t", _I), ("n_max", _I),
+                ("b", _P), ("c", _P), ("alpha", _D),
+                ("tol_md", _D), ("tol_action", _D),
+                ("solver", SolverOpts), ("link_fmt_lo", _I)]
+
+
+class TrajResult(ctypes.Structure):
+    _fields_ = [("H0", _D), ("H1", _D), ("dH", _D), ("plaq0", _D), ("plaq1", _D),
+                ("accepted", _I), ("cg_iterations", _I), ("solves", _I)]
+
+
+class HmcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_SIGS = {
+    "hmc_ctx_create": (_I, [_I, _P]),
+    "hmc_ctx_destroy": (_I, [_P]),
+    "hmc_ctx_set_stream": (_I, [_P, _P]),
+    "hmc_last_error": (ctypes.c_char_p, [_P]),
+    "hmc_launch_count": (ctypes.c_longlong, [_P]),
+    "hmc_gauge_bytes": (_SZ, [_P, _I, _I]),
+    "hmc_spinor_bytes": (_SZ, [_P, _I, _I]),
+    "hmc_algebra_bytes": (_SZ, [_P]),
+    "hmc_pack_gauge": (_I, [_P, _P, _P, _P, _I, _I]),
+    "hmc_unpack_gauge": (_I, [_P, _P, _P, _I, _I, _P]),
+    "hmc_pack_spinor": (_I, [_P, _P, _P, _P, _I, _I]),
+    "hmc_unpack_spinor": (_I, [_P, _P, _P, _I, _I, _P]),
+    "hmc_pack_algebra": (_I, [_P, _P, _P, _P]),
+    "hmc_unpack_algebra": (_I, [_P, _P, _P, _P]),
+    "hmc_dslash": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _I]),
+    "hmc_mhat": (_I, [_P, _P, _P, _P, _P, _D, _I, _I, _I, _P]),
+    "hmc_cg_solve": (_I, [_P, _P, _P, _P, _P, _P, _D, _D, _I, _P, _P]),
+    "hmc_force_pf": (_I, [_P, _P, _P, _P, _P, _D, _P, _D, _P, _D, _P, _P]),
+    "hmc_action_pf": (_I, [_P, _P, _P, _P, _P, _D, _P, _D, _P, _P, _P]),
+    "hmc_force_hopexp": (_I, [_P, _P, _P, _D, _D, _I, _D, _P, _P]),
+    "hmc_plaquette": (_I, [_P, _P, _P, _P]),
+    "hmc_poly_apply": (_I, [_P, _P, _P, _P, _P, _P, _I, _D, _I, _P]),
+    "hmc_update_links": (_I, [_P, _P, _P, _P, _D]),
+    "hmc_update_momenta": (_I, [_P, _P, _P, _P, _D]),
+    "hmc_kinetic": (_I, [_P, _P, _P, _P]),
+    "hmc_trajectory": (_I, [_P, _P, _P, _P, _P, _P, _D, _P, _P, _P]),
+    "hmc_filter_coeffs": (_I, [_I, _I, _P, _P, _P]),
+    "hmc_md_evolve": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libhmc.so (raises when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libhmc.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        l = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(l, name, None)
+            if f is None:
+                continue
+            f.restype = res
+            f.argtypes = args
+        _lib = l
+    return _lib
+
+
+def lattice(L):
+    return Lat((ctypes.c_int * 4)(*[int(v) for v in L]))
+
+
+def _ref(x):
+    return ctypes.byref(x) if x is not None else None
+
+
+def _dp(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def filter_coeffs(k, n, with_c=True):
+    """Library-side filter coefficients (host, long double): (b, alpha, c)."""
+    b = np.zeros(n + 1)
+    c = np.zeros(n + 1) if with_c else None
+    a = ctypes.c_double(0)
+    st = lib().hmc_filter_coeffs(k, n, b.ctypes.data_as(_P), ctypes.byref(a),
+                                 c.ctypes.data_as(_P) if with_c else None)
+    if st:
+        raise HmcError(st, "hmc_filter_coeffs")
+    return b, a.value, c
+
+
+class Field:
+    """A device buffer in one of the library's layouts."""
+
+    def __init__(self, data, kind, prec, n_rhs=1, fmt=None):
+        self.data, self.kind, self.prec, self.n_rhs, self.fmt = data, kind, prec, n_rhs, fmt
+
+    def ptr(self):
+        return ctypes.c_void_p(self.data.data_ptr())
+
+    def gauge(self):
+        assert self.kind == "gauge"
+        return Gauge(self.data.data_ptr(), self.prec, self.fmt)
+
+
+class Context:
+    """One libhmc context on one CUDA device."""
+
+    def __init__(self, device=0):
+        import torch
+        self.torch = torch
+        self.device = device
+        h = ctypes.c_void_p()
+        st = lib().hmc_ctx_create(device, ctypes.byref(h))
+        if st:
+            raise HmcError(st, "hmc_ctx_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hmc_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- plumbing -----------------------------------------------------------
+    def _stream(self):
+        s = self.torch.cuda.current_stream(self.device).cuda_stream
+        lib().hmc_ctx_set_stream(self.h, ctypes.c_void_p(s))
+
+    def _check(self, st, what):
+        if st:
+            msg = lib().hmc_last_error(self.h).decode()
+            raise HmcError(st, f"{what}: {msg}")
+
+    def launches(self):
+        return lib().hmc_launch_count(self.h)
+
+    def _bytes(self, n):
+        return self.torch.empty(int(n), dtype=self.torch.uint8, device=f"cuda:{self.device}")
+
+    # ---- allocation ---------------------------------------------------------
+    def new_spinor(self, L, prec, n_rhs=1):
+        n = lib().hmc_spinor_bytes(_ref(lattice(L)), prec, n_rhs)
+        return Field(self._bytes(n), "spinor", prec, n_rhs)
+
+    def new_gauge(self, L, prec, fmt):
+        n = lib().hmc_gauge_bytes(_ref(lattice(L)), prec, fmt)
+        return Field(self._bytes(n), "gauge", prec, fmt=fmt)
+
+    def new_algebra(self, L):
+        n = lib().hmc_algebra_bytes(_ref(lattice(L)))
+        t = self.torch.zeros(int(n) // 8, dtype=self.torch.float64, device=f"cuda:{self.device}")
+        return Field(t, "algebra", F64)
+
+    # ---- layout conversion ----------------------------------------------------
+    def _canon(self, a):
+        t = self.torch.as_tensor(a)
+        if t.is_complex():
+            t = self.torch.view_as_real(t.to(self.torch.complex128))
+        return t.to(dtype=self.torch.float64, device=f"cuda:{self.device}").contiguous()
+
+    def pack_gauge(self, L, U, prec=F64, fmt=LINK18):
+        self._stream()
+        Uc = self._canon(U)
+        f = self.new_gauge(L, prec, fmt)
+        st = lib().hmc_pack_gauge(self.h, _ref(lattice(L)), _dp(Uc), f.ptr(), prec, fmt)
+        self._check(st, "hmc_pack_gauge")
+        return f
+
+    def unpack_gauge(self, L, f):
+        self._stream()
+        V = int(np.prod(L))
+        out = self.torch.empty((V, 4, 3, 3, 2), dtype=self.torch.float64, device=f"cuda:{self.device}")
+        st = lib().hmc_unpack_gauge(self.h, _ref(lattice(L)), f.ptr(), f.prec, f.fmt, _dp(out))
+        self._check(st, "hmc_unpack_gauge")
+        return self.torch.view_as_complex(out)
+
+    def pack_spinor(self, L, psi, prec=F64):
+        """psi: [Vh,4,3] or [n_rhs,Vh,4,3] complex (numpy or torch)."""
+        self._stream()
+        c = self._canon(psi)
+        n_rhs = 1 if c.dim() == 4 else c.shape[0]
+        f = self.new_spinor(L, prec, n_rhs)
+        st = lib().hmc_pack_spinor(self.h, _ref(lattice(L)), _dp(c), f.ptr(), prec, n_rhs)
+        self._check(st, "hmc_pack_spinor")
+        return f
+
+    def unpack_spinor(self, L, f):
+        self._stream()
+        Vh = int(np.prod(L)) // 2
+        shape = (Vh, 4, 3, 2) if f.n_rhs == 1 else (f.n_rhs, Vh, 4, 3, 2)
+        out = self.torch.empty(shape, dtype=self.torch.float64, device=f"cuda:{self.device}")
+        st = lib().hmc_unpack_spinor(self.h, _ref(lattice(L)), f.ptr(), f.prec, f.n_rhs, _dp(out))
+        self._check(st, "hmc_unpack_spinor")
+        return self.torch.view_as_complex(out)
+
+    def pack_algebra(self, L, A):
+        self._stream()
+        c = self._canon(A)
+        f = self.new_algebra(L)
+        st = lib().hmc_pack_algebra(self.h, _ref(lattice(L)), _dp(c), _dp(f.data))
+        self._check(st, "hmc_pack_algebra")
+        return f
+
+    def unpack_algebra(self, L, f):
+        self._stream()
+        V = int(np.prod(L))
+        out = self.torch.empty((V, 4, 8), dtype=self.torch.float64, device=f"cuda:{self.device}")
+        st = lib().hmc_unpack_algebra(self.h, _ref(lattice(L)), _dp(f.data), _dp(out))
+        self._check(st, "hmc_unpack_algebra")
+        return out
+
+    # ---- operators ---------------------------------------------------------------
+    def dslash(self, L, U, out, inp, out_parity, dagger=False):
+        self._stream()
+        g = U.gauge()
+        st = lib().hmc_dslash(self.h, _ref(lattice(L)), ctypes.byref(g), out.ptr(), inp.ptr(),
+                              out_parity, int(dagger), inp.prec, inp.n_rhs)
+        self._check(st, "hmc_dslash")
+        return out
+
+    def mhat(self, L, U, out, inp, kappa, dagger=False, kappas=None):
+        self._stream()
+        g = U.gauge()
+        ks = None
+        if kappas is not None:
+            ks = np.ascontiguousarray(kappas, dtype=np.float64)
+        st = lib().hmc_mhat(self.h, _ref(lattice(L)), ctypes.byref(g), out.ptr(), inp.ptr(), kappa,
+                            int(dagger), inp.prec, inp.n_rhs,
+                            ks.ctypes.data_as(_P) if ks is not None else None)
+        self._check(st, "hmc_mhat")
+        return out
+
+    def cg_solve(self, L, U_hi, x, phi, kappa, tol, max_iter=10000, U_lo=None, inner_prec=F64,
+                 reliable_delta=0.1, check_every=16):
+        self._stream()
+        gh = U_hi.gauge()
+        gl = U_lo.gauge() if U_lo is not None else None
+        opts = SolverOpts(inner_prec, reliable_delta, check_every)
+        stats = SolveStats()
+        st = lib().hmc_cg_solve(self.h, _ref(lattice(L)), ctypes.byref(gh),
+                                ctypes.byref(gl) if gl is not None else None, x.ptr(), phi.ptr(),
+                                kappa, tol, max_iter, ctypes.byref(opts), ctypes.byref(stats))
+        res = {"iterations": stats.iterations, "reliable_updates": stats.reliable_updates,
+               "true_rel_res": stats.true_rel_res, "status": st}
+        if st and st != ENOCONV:
+            self._check(st, "hmc_cg_solve")
+        return res
+
+    # ---- actions and forces -------------------------------------------------------
+    @staticmethod
+    def _filter(b, alpha):
+        if b is None:
+            return None, None
+        arr = np.ascontiguousarray(b, dtype=np.float64)
+        return Filter(arr.ctypes.data, len(arr) - 1, alpha), arr
+
+    def force_pf(self, L, U_hi, phi, kappa, F, coeff=1.0, tol=1e-12, U_lo=None, inner_prec=F64,
+                 b=None, alpha=0.0, reliable_delta=0.1):
+        """F += coeff * F_PF (plain action when b is None, else the filtered one)."""
+        self._stream()
+        gh = U_hi.gauge()
+        gl = U_lo.gauge() if U_lo is not None else None
+        flt, keep = self._filter(b, alpha)
+        opts = SolverOpts(inner_prec, reliable_delta, 16)
+        stats = SolveStats()
+        st = lib().hmc_force_pf(self.h, _ref(lattice(L)), ctypes.byref(gh),
+                                ctypes.byref(gl) if gl is not None else None, phi.ptr(), kappa,
+                                ctypes.byref(flt) if flt is not None else None, coeff,
+                                _dp(F.data), tol, ctypes.byref(opts), ctypes.byref(stats))
+        self._check(st, "hmc_force_pf")
+        return {"iterations": stats.iterations, "true_rel_res": stats.true_rel_res}
+
+    def action_pf(self, L, U_hi, phi, kappa, tol=1e-13, U_lo=None, inner_prec=F64, b=None,
+                  alpha=0.0):
+        self._stream()
+        gh = U_hi.gauge()
+        gl = U_lo.gauge() if U_lo is not None else None
+        flt, keep = self._filter(b, alpha)
+        opts = SolverOpts(inner_prec, 0.1, 16)
+        out = ctypes.c_double(0)
+        st = lib().hmc_action_pf(self.h, _ref(lattice(L)), ctypes.byref(gh),
+                                 ctypes.byref(gl) if gl is not None else None, phi.ptr(), kappa,
+                                 ctypes.byref(flt) if flt is not None else None, tol,
+                                 ctypes.byref(opts), ctypes.byref(out), None)
+        self._check(st, "hmc_action_pf")
+        return out.value
+
+    def force_hopexp(self, L, U, beta, kappa, k, F=None, coeff=1.0, want_action=True):
+        self._stream()
+        g = U.gauge()
+        act = ctypes.c_double(0)
+        st = lib().hmc_force_hopexp(self.h, _ref(lattice(L)), ctypes.byref(g), beta, kappa, k,
+                                    coeff, _dp(F.data) if F is not None else None,
+                                    ctypes.byref(act) if want_action else None)
+        self._check(st, "hmc_force_hopexp")
+        return act.value
+
+    def plaquette(self, L, U):
+        self._stream()
+        g = U.gauge()
+        out = ctypes.c_double(0)
+        st = lib().hmc_plaquette(self.h, _ref(lattice(L)), ctypes.byref(g), ctypes.byref(out))
+        self._check(st, "hmc_plaquette")
+        return out.value
+
+    def poly_apply(self, L, U, out, inp, coeffs, kappa, horner_store=None):
+        self._stream()
+        g = U.gauge()
+        c = np.ascontiguousarray(coeffs, dtype=np.float64)
+        st = lib().hmc_poly_apply(self.h, _ref(lattice(L)), ctypes.byref(g), out.ptr(), inp.ptr(),
+                                  c.ctypes.data_as(_P), len(c) - 1, kappa, inp.prec,
+                                  _dp(horner_store) if horner_store is not None else None)
+        self._check(st, "hmc_poly_apply")
+        return out
+
+    def update_links(self, L, U, P, eps):
+        self._stream()
+        st = lib().hmc_update_links(self.h, _ref(lattice(L)), U.ptr(), _dp(P.data), eps)
+        self._check(st, "hmc_update_links")
+
+    def update_momenta(self, L, P, F, eps):
+        self._stream()
+        st = lib().hmc_update_momenta(self.h, _ref(lattice(L)), _dp(P.data), _dp(F.data), eps)
+        self._check(st, "hmc_update_momenta")
+
+    def kinetic(self, L, P):
+        self._stream()
+        out = ctypes.c_double(0)
+        st = lib().hmc_kinetic(self.h, _ref(lattice(L)), _dp(P.data), ctypes.byref(out))
+        self._check(st, "hmc_kinetic")
+        return out.value
+
+    def trajectory(self, L, U, P, eta, u, beta, kappa, tau, n_md, n_gauge, filter_k=0, n_t=0,
+                   n_max=0, b=None, c=None, alpha=0.0, tol_md=1e-10, tol_action=1e-12,
+                   inner_prec=F64, link_fmt_lo=LINK12, reliable_delta=0.1, U_end=None,
+                   P_end=None):
+        """One HMC trajectory; U (F64/LINK18 gauge Field) is updated in place
+        when accepted.  Returns the result as a dict."""
+        self._stream()
+        keep = []
+        prm = TrajParams(beta=beta, kappa=kappa, tau=tau, n_md=n_md, n_gauge=n_gauge,
+                         filter_k=filter_k, n_t=n_t, n_max=n_max, alpha=alpha, tol_md=tol_md,
+                         tol_action=tol_action, solver=SolverOpts(inner_prec, reliable_delta, 16),
+                         link_fmt_lo=link_fmt_lo)
+        if b is not None:
+            ab = np.ascontiguousarray(b, dtype=np.float64); keep.append(ab); prm.b = ab.ctypes.data
+        if c is not None:
+            ac = np.ascontiguousarray(c, dtype=np.float64); keep.append(ac); prm.c = ac.ctypes.data
+        res = TrajResult()
+        st = lib().hmc_trajectory(self.h, _ref(lattice(L)), U.ptr(), ctypes.byref(prm),
+                                  _dp(P.data), eta.ptr(), u, ctypes.byref(res),
+                                  U_end.ptr() if U_end is not None else None,
+                                  _dp(P_end.data) if P_end is not None else None)
+        self._check(st, "hmc_trajectory")
+        return {f: getattr(res, f) for f, _ in TrajResult._fields_}
+
+    def md_evolve(self, L, U, P, phi, beta, kappa, tau, n_md, n_gauge, filter_k=0, n_t=0,
+                  b=None, alpha=0.0, tol_md=1e-10, inner_prec=F64, link_fmt_lo=LINK12,
+                  reliable_delta=0.1):
+        """Molecular dynamics with phi fixed; U (F64/LINK18) and P updated in place."""
+        self._stream()
+        keep = []
+        prm = TrajParams(beta=beta, kappa=kappa, tau=tau, n_md=n_md, n_gauge=n_gauge,
+                         filter_k=filter_k, n_t=n_t, n_max=n_t, alpha=alpha, tol_md=tol_md,
+                         tol_action=tol_md, solver=SolverOpts(inner_prec, reliable_delta, 16),
+                         link_fmt_lo=link_fmt_lo)
+        if b is not None:
+            ab = np.ascontiguousarray(b, dtype=np.float64); keep.append(ab)
+            prm.b = ab.ctypes.data
+            prm.c = ab.ctypes.data  # unused by the MD step; satisfies the filter check
+        res = TrajResult()
+        st = lib().hmc_md_evolve(self.h, _ref(lattice(L)), U.ptr(), _dp(P.data), phi.ptr(),
+                                 ctypes.byref(prm), ctypes.byref(res))
+        self._check(st, "hmc_md_evolve")
+        return {"cg_iterations": res.cg_iterations, "solves": res.solves}

@@ -1,0 +1,146 @@
+"""GPU parity of the molecular dynamics and the trajectory against the oracle,
+plus the integrator invariants the paper checks (Sec. IV: reversibility;
+Sec. I: second-order integrator, dH ~ dt^2).
+
+Tolerances.  Link updates are FP64 link algebra: 1e-13.  A trajectory
+accumulates the solver tolerance through every force; with FP64 solves at
+1e-12 (MD) and 1e-14 (action) the final fields agree to 1e-9 and dH to
+1e-7 absolute on these small lattices.
+"""
+import numpy as np
+import pytest
+
+from oracle import coeffs as C
+from paper_1805_03560_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+BETA, KAPPA = 5.6, 0.156
+
+
+@pytest.fixture(scope="module")
+def H():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1805_03560_gb300 import hmc
+    return hmc
+
+
+@pytest.fixture(scope="module")
+def ctx(H):
+    return H.Context(0)
+
+
+def _np(t):
+    return t.cpu().numpy()
+
+
+def test_update_links_and_momenta(orc, ctx, H):
+    L = (4, 6, 6, 8)
+    U = I.gauge_links(L, 0.3, 1)
+    P = I.momenta(L, 3)
+    Ud = ctx.pack_gauge(L, U, 0, 18)
+    Pd = ctx.pack_algebra(L, P)
+    ctx.update_links(L, Ud, Pd, 0.13)
+    got = _np(ctx.unpack_gauge(L, Ud))
+    want = orc.update_links(L, U, P, 0.13)
+    assert np.abs(got - want).max() < 1e-13
+    F = ctx.pack_algebra(L, I.momenta(L, 9))
+    ctx.update_momenta(L, Pd, F, 0.25)
+    assert np.abs(_np(ctx.unpack_algebra(L, Pd)) - (P - 0.25 * I.momenta(L, 9))).max() < 1e-15
+    kin = orc.kinetic(L, P - 0.25 * I.momenta(L, 9))
+    assert abs(ctx.kinetic(L, Pd) - kin) < 1e-13 * kin
+
+
+def _traj_kw(k, **kw):
+    d = dict(beta=BETA, kappa=KAPPA, tau=0.5, n_md=4, n_gauge=2, filter_k=k)
+    if k:
+        n_t, n_max = (7, 19) if k == 1 else (9, 29)
+        b, alpha, _ = C.filter_coeffs(k, n_max)
+        d.update(n_t=n_t, n_max=n_max, b=b, c=C.heatbath_coeffs(k, n_max), alpha=alpha)
+    d.update(kw)
+    return d
+
+
+@pytest.mark.parametrize("k", [0, 2])
+def test_trajectory_matches_oracle(orc, ctx, H, k):
+    L = (4, 4, 4, 4)  # every extent 4: winding lines enter the k = 2 action
+    U = I.gauge_links(L, 0.3, 1)
+    P = I.momenta(L, 3)
+    eta = I.gaussian_half(L, 2)
+    kw = _traj_kw(k)
+    Uo_next, ro, Uo_end, Po_end = orc.trajectory(L, U, P, eta, 0.5, tol_md=1e-13,
+                                                 tol_action=1e-14, **kw)
+    Ud = ctx.pack_gauge(L, U, 0, 18)
+    Ue = ctx.new_gauge(L, 0, 18)
+    Pe = ctx.new_algebra(L)
+    r = ctx.trajectory(L, Ud, ctx.pack_algebra(L, P), ctx.pack_spinor(L, eta, 0), 0.5,
+                       tol_md=1e-13, tol_action=1e-14, U_end=Ue, P_end=Pe, **kw)
+    assert abs(r["H0"] - ro["H0"]) <= 1e-9 * abs(ro["H0"])
+    assert abs(r["dH"] - ro["dH"]) <= 1e-7
+    assert np.abs(_np(ctx.unpack_gauge(L, Ue)) - Uo_end).max() <= 1e-9
+    assert np.abs(_np(ctx.unpack_algebra(L, Pe)) - Po_end).max() <= 1e-8
+    assert r["accepted"] == ro["accepted"]
+    assert abs(r["plaq0"] - ro["plaq0"]) < 1e-14
+
+
+@pytest.mark.parametrize("k,inner", [(0, 0), (2, 0), (2, 1)])
+def test_reversibility(orc, ctx, H, k, inner):
+    """Forward, flip the momenta, backward: Delta = sum |U - U'|^2 at the
+    rounding level for tight solves (Sec. IV: 6.3e-21 on 12^3 x 24)."""
+    L = (4, 6, 6, 8)
+    U = I.gauge_links(L, 0.3, 1)
+    P = I.momenta(L, 3)
+    eta = I.gaussian_half(L, 2)
+    kw = _traj_kw(k)
+    kw.pop("n_max", None)
+    kw.pop("c", None)
+    Ud = ctx.pack_gauge(L, U, 0, 18)
+    Ul = ctx.pack_gauge(L, U, 0, 18)
+    # phi from the oracle's heatbath, fixed through both runs
+    if k == 0:
+        phi = orc.mhat(L, U, KAPPA, eta, dagger=True)
+    else:
+        cc = C.heatbath_coeffs(k, 29)
+        phi = orc.mhat(L, U, KAPPA, orc.poly_K(L, U, KAPPA, cc, eta))
+    ph = ctx.pack_spinor(L, phi, 0)
+    Pd = ctx.pack_algebra(L, P)
+    tol = 1e-14 if inner == 0 else 1e-13
+    ctx.md_evolve(L, Ud, Pd, ph, tol_md=tol, inner_prec=inner, **kw)
+    moved = np.sum(np.abs(_np(ctx.unpack_gauge(L, Ud)) - U) ** 2)
+    Pd.data.neg_()
+    ctx.md_evolve(L, Ud, Pd, ph, tol_md=tol, inner_prec=inner, **kw)
+    delta = np.sum(np.abs(_np(ctx.unpack_gauge(L, Ud)) - U) ** 2)
+    assert moved > 1e-2
+    assert delta < (1e-20 if inner == 0 else 1e-16), delta
+    del Ul
+
+
+def test_dH_scales_as_dt_squared(ctx, H):
+    L = (4, 6, 6, 8)
+    U = I.gauge_links(L, 0.3, 1)
+    P = I.momenta(L, 3)
+    eta = I.gaussian_half(L, 2)
+    dH = []
+    for n_md in (8, 16, 32):
+        Ud = ctx.pack_gauge(L, U, 0, 18)
+        r = ctx.trajectory(L, Ud, ctx.pack_algebra(L, P), ctx.pack_spinor(L, eta, 0), 0.5,
+                           **_traj_kw(0, tau=0.25, n_md=n_md, n_gauge=4, tol_md=1e-13,
+                                      tol_action=1e-14))
+        dH.append(r["dH"])
+    r1, r2 = dH[0] / dH[1], dH[1] / dH[2]
+    assert 3.5 < r1 < 4.5 and 3.8 < r2 < 4.2, dH
+
+
+def test_trajectory_rejected_leaves_U(ctx, H):
+    L = (4, 4, 4, 4)
+    U = I.gauge_links(L, 0.3, 1)
+    Ud = ctx.pack_gauge(L, U, 0, 18)
+    before = _np(ctx.unpack_gauge(L, Ud))
+    r = ctx.trajectory(L, Ud, ctx.pack_algebra(L, I.momenta(L, 3)),
+                       ctx.pack_spinor(L, I.gaussian_half(L, 2), 0), 1.0 - 1e-16,
+                       **_traj_kw(0, n_md=1, n_gauge=1))
+    if r["dH"] > 0:
+        assert r["accepted"] == 0
+        assert np.array_equal(_np(ctx.unpack_gauge(L, Ud)), before)
