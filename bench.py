@@ -1,0 +1,445 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 hot path: one HMC trajectory per step.
+
+Workload: 24^3 x 48 lattice, beta = 5.6, kappa = 0.1575, synthetic links
+U = exp(i 0.3 A) (seeded), kappa^4 filtering (n_t = 9 in the force, n_max = 29
+in the action), leapfrog on two time scales (tau = 1, 10 coarse steps,
+4 gauge steps each), pseudo-fermion solves to relative residual 1e-10 (MD) and
+1e-12 (action) with FP16-storage / FP32-arithmetic CG and FP64 reliable
+updates.  One step = the whole path: heatbath, every force, every solve, the
+filter polynomials, link updates, the Hamiltonian and the Metropolis test.
+
+Prints one JSON line.  value = hemi-Dslash algorithmic bytes per trajectory
+(each link and spinor of every launch counted once) over the device time of
+the trajectory, i.e. the whole job expressed in the metric's unit.  The
+roofline object gives the dominant Dslash kernel alone, timed with CUDA events
+on its launch stream during the timed steps.
+
+--impl reference runs the FP64 CPU oracle instead (bounded sample: one
+hemi-Dslash of the same lattice per step, on the host cores).
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Dslash HBM GB/s (% of peak); s/trajectory mixed-batched vs plain FP64 at rr<=1e-10"
+LAT = (48, 24, 24, 24)  # Lt, Lx, Ly, Lz
+WORK = dict(beta=5.6, kappa=0.1575, tau=1.0, n_md=10, n_gauge=4, filter_k=2, n_t=9, n_max=29,
+            tol_md=1e-10, tol_action=1e-12)
+EPS_LINKS = 0.3
+FLUSH_BYTES = 256 << 20  # > 129 MB L2
+FP64_PEAK_GFLOPS = 1250.0  # nominal dense FP64 of GB300 (no measured figure in the peaks file)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hmc", choices=["hmc", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--inner", default="f32", choices=["f16", "f32"])
+    ap.add_argument("--delta", type=float, default=1e-5, help="reliable-update threshold")
+    ap.add_argument("--force-prec", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--kernel", default=None,
+                    help="time one hemi-Dslash variant alone, e.g. f16-12 (for profiling)")
+    ap.add_argument("--launches", type=int, default=20)
+    return ap.parse_args()
+
+
+def run_kernel(args):
+    """Launch one hemi-Dslash variant `--launches` times on the benchmark
+    lattice (two input fields alternated) and print its event-timed average."""
+    import numpy as np
+    import torch
+    from paper_1805_03560_gb300 import hmc
+    from paper_1805_03560_gb300 import inputs as I
+    pname, fmt = args.kernel.split("-")
+    prec = {"f64": hmc.F64, "f32": hmc.F32, "f16": hmc.F16}[pname]
+    fmt = int(fmt)
+    ctx = hmc.Context(0)
+    U = ctx.pack_gauge(LAT, I.gauge_links(LAT, EPS_LINKS, 1), prec, fmt)
+    srcs = [ctx.pack_spinor(LAT, I.gaussian_half(LAT, 2 + i), prec) for i in range(2)]
+    out = ctx.new_spinor(LAT, prec)
+    for i in range(3):
+        ctx.dslash(LAT, U, out, srcs[i % 2], i % 2)
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    for i in range(args.launches):
+        ctx.dslash(LAT, U, out, srcs[i % 2], i % 2)
+    torch.cuda.synchronize()
+    n, ms, byt = next(iter(ctx.timing().values()))
+    Vh = int(np.prod(LAT)) // 2
+    print(json.dumps({"kernel": args.kernel, "launches": n, "us_per_launch": round(ms / n * 1e3, 2),
+                      "GBs": round(byt / (ms * 1e-3) / 1e9, 1),
+                      "TFLOPs": round(1320.0 * Vh * n / (ms * 1e-3) / 1e12, 3)}), flush=True)
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def dslash_source_hash():
+    h = hashlib.sha256()
+    for f in ("dslash.cu", "hmc_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1805_03560_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kclass):
+    """DRAM bytes per launch from the committed ncu summary of this kernel, or
+    None when absent or taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "dslash_traffic.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
+    if not m or m.group(1) != dslash_source_hash():
+        return None
+    m = re.search(re.escape(kclass.split("/")[0]) + r"\s+traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    return float(m.group(1)) if m else None
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_inputs(rank):
+    from paper_1805_03560_gb300 import inputs as I
+    U = I.gauge_links(LAT, EPS_LINKS, seed=1 + 100 * rank)
+    P = I.momenta(LAT, seed=3 + 100 * rank)
+    eta = I.gaussian_half(LAT, seed=2 + 100 * rank)
+    return U, P, eta
+
+
+def coeffs():
+    from paper_1805_03560_gb300 import hmc
+    b, alpha, _ = hmc.filter_coeffs(WORK["filter_k"], WORK["n_max"], with_c=False)
+    _, _, c = hmc.filter_coeffs(WORK["filter_k"], WORK["n_max"])
+    return b, alpha, c
+
+
+def run_hmc(args):
+    import numpy as np
+    import torch
+    from paper_1805_03560_gb300 import hmc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def allmax(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def allsum(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    inner = hmc.F16 if args.inner == "f16" else hmc.F32
+    ctx = hmc.Context(local)
+    U, P, eta = build_inputs(rank)
+    b, alpha, c = coeffs()
+    U0 = ctx.pack_gauge(LAT, U, hmc.F64, hmc.LINK18)
+    Ud = ctx.new_gauge(LAT, hmc.F64, hmc.LINK18)
+    Pd = ctx.pack_algebra(LAT, P)
+    ed = ctx.pack_spinor(LAT, eta, hmc.F64)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    fprec = hmc.F32 if args.force_prec == "f32" else hmc.F64
+    kw = dict(WORK, b=b, c=c, alpha=alpha, inner_prec=inner, link_fmt_lo=hmc.LINK12,
+              reliable_delta=args.delta, force_prec=fprec)
+    stream = torch.cuda.current_stream()
+
+    def one(kwargs):
+        Ud.data.copy_(U0.data)
+        return ctx.trajectory(LAT, Ud, Pd, ed, 0.5, **kwargs)
+
+    for _ in range(args.warmup):
+        one(kw)
+    torch.cuda.synchronize()
+    # ---- timed region --------------------------------------------------------
+    clocks = Clocks(local)
+    ctx.set_timing(True)
+    l0 = ctx.launches()
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times, results = [], []
+    for _ in range(args.steps):
+        Ud.data.copy_(U0.data)
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        results.append(ctx.trajectory(LAT, Ud, Pd, ed, 0.5, **kw))
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = ctx.launches() - l0
+    kst = ctx.timing()
+    ctx.set_timing(False)
+    ms_step = allmax(sum(times) / len(times))
+    ds_bytes = sum(v[2] for k, v in kst.items() if k.startswith("dslash")) / args.steps
+    value = allsum(ds_bytes) / (ms_step * 1e-3) / 1e9
+    # dominant Dslash class by time
+    dom = max((k for k in kst if k.startswith("dslash")), key=lambda k: kst[k][1])
+    n_dom, ms_dom, b_dom = kst[dom]
+    pk = peaks()
+    if dom.startswith("dslash_f64"):
+        Vh = int(np.prod(LAT)) // 2
+        achieved = 1320.0 * Vh * n_dom / (ms_dom * 1e-3) / 1e9
+        roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 1),
+                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": None,
+                "peak_source": "nominal FP64 rate of GB300 (recipe table)"}
+    else:
+        achieved = b_dom / (ms_dom * 1e-3) / 1e9
+        peak = pk["hbm_gbs"] if pk else 6800.0
+        roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": ncu_traffic(dom),
+                "bytes_per_launch": round(b_dom / n_dom),
+                "us_per_launch": round(ms_dom / n_dom * 1e3, 2),
+                "peak_source": "measured" if pk else "fallback"}
+    kernels = {k: {"launches_per_step": v[0] // args.steps, "us": round(v[1] / v[0] * 1e3, 2),
+                   "GBs": round(v[2] / (v[1] * 1e-3) / 1e9, 1)} for k, v in sorted(kst.items())}
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.inner,
+        "data": "synthetic (seeded exp(i 0.3 A) links, Gaussian momenta and sources)",
+        "config": {"workload": "hmc-trajectory 24^3x48 kappa=0.1575 beta=5.6 kappa^4-filter",
+                   "lattice": "x".join(str(v) for v in LAT[::-1]), **{k: v for k, v in WORK.items()},
+                   "inner_prec": args.inner, "reliable_delta": args.delta,
+                   "force_prec": args.force_prec, "links": "12-real (inner), 18-real FP64",
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roof,
+        "gpu_launches": launches,
+        "kernels": kernels,
+        "trajectory": {"s": round(ms_step / 1e3, 4), "dH": results[-1]["dH"],
+                       "accepted": results[-1]["accepted"],
+                       "cg_iterations": results[-1]["cg_iterations"],
+                       "solves": results[-1]["solves"]},
+    }
+    if clk:
+        out["clocks"] = clk
+    # ---- plain FP64 GPU path, same trajectory ----------------------------------
+    if not args.no_fp64:
+        kw64 = dict(kw, inner_prec=hmc.F64, force_prec=hmc.F64)
+        one(kw64)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        Ud.data.copy_(U0.data)
+        flush.zero_()
+        e0.record(stream)
+        r64 = ctx.trajectory(LAT, Ud, Pd, ed, 0.5, **kw64)
+        e1.record(stream)
+        e1.synchronize()
+        s64 = allmax(e0.elapsed_time(e1)) / 1e3
+        out["fp64_path"] = {"s_per_trajectory": round(s64, 4), "dH": r64["dH"],
+                            "accepted": r64["accepted"], "cg_iterations": r64["cg_iterations"]}
+        out["speedup_vs_fp64"] = round(s64 / (ms_step / 1e3), 3)
+        out["dH_diff_vs_fp64"] = abs(r64["dH"] - results[-1]["dH"])
+    # ---- end to end through the public API with host buffers ----------------------
+    if not args.no_e2e:
+        Uh = torch.view_as_real(torch.from_numpy(U)).pin_memory()
+        Ph = torch.from_numpy(P).pin_memory()
+        eh = torch.view_as_real(torch.from_numpy(eta)).pin_memory()
+        Uout = torch.empty_like(Uh).pin_memory()
+        Ucd = torch.empty(Uh.shape, dtype=torch.float64, device="cuda")
+        Pcd = torch.empty(Ph.shape, dtype=torch.float64, device="cuda")
+        ecd = torch.empty(eh.shape, dtype=torch.float64, device="cuda")
+        Ue = ctx.new_gauge(LAT, hmc.F64, hmc.LINK18)
+        Pe = ctx.new_algebra(LAT)
+        ee = ctx.new_spinor(LAT, hmc.F64)
+        lat = hmc.lattice(LAT)
+        lib = hmc.lib()
+        import ctypes
+
+        def e2e_step():
+            Ucd.copy_(Uh, non_blocking=True)
+            Pcd.copy_(Ph, non_blocking=True)
+            ecd.copy_(eh, non_blocking=True)
+            ctx._stream()
+            ctx._check(lib.hmc_pack_gauge(ctx.h, ctypes.byref(lat), ctypes.c_void_p(Ucd.data_ptr()),
+                                          Ue.ptr(), hmc.F64, hmc.LINK18), "pack")
+            ctx._check(lib.hmc_pack_algebra(ctx.h, ctypes.byref(lat), ctypes.c_void_p(Pcd.data_ptr()),
+                                            ctypes.c_void_p(Pe.data.data_ptr())), "pack")
+            ctx._check(lib.hmc_pack_spinor(ctx.h, ctypes.byref(lat), ctypes.c_void_p(ecd.data_ptr()),
+                                           ee.ptr(), hmc.F64, 1), "pack")
+            r = ctx.trajectory(LAT, Ue, Pe, ee, 0.5, **kw)
+            ctx._check(lib.hmc_unpack_gauge(ctx.h, ctypes.byref(lat), Ue.ptr(), hmc.F64, hmc.LINK18,
+                                            ctypes.c_void_p(Ucd.data_ptr())), "unpack")
+            Uout.copy_(Ucd, non_blocking=True)
+            return r
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        tt = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step()
+            torch.cuda.synchronize()
+            tt.append(time.perf_counter() - t0)
+        t_e2e = allmax(sum(tt) / len(tt))
+        out["e2e"] = {"value": round(allsum(ds_bytes) / t_e2e / 1e9, 1), "unit": "GB/s",
+                      "s_per_trajectory": round(t_e2e, 4),
+                      "h2d_bytes_per_step": int(Uh.numel() * 8 + Ph.numel() * 8 + eh.numel() * 8),
+                      "d2h_bytes_per_step": int(Uout.numel() * 8 + 8 * 8)}
+    if rank == 0:
+        if not args.no_cpu:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def oracle_dslash_sample(n_apply):
+    """The FP64 oracle hemi-Dslash on the benchmark lattice, n_apply times."""
+    import numpy as np
+    import oracle
+    from paper_1805_03560_gb300 import inputs as I
+    oracle.build()
+    U = I.gauge_links(LAT, EPS_LINKS, seed=1)
+    psi = I.gaussian_half(LAT, seed=2)
+    oracle.hop_eo(LAT, U, 0, psi)  # warm
+    t0 = time.perf_counter()
+    for i in range(n_apply):
+        oracle.hop_eo(LAT, U, i % 2, psi)
+    dt = (time.perf_counter() - t0) / n_apply
+    Vh = int(np.prod(LAT)) // 2
+    byt = Vh * (8 * 18 * 8 + 24 * 8 * 2)  # FP64, 18-real links: the oracle's own data
+    return byt / dt / 1e9, dt
+
+
+def cpu_baseline():
+    gbs, dt = oracle_dslash_sample(4)
+    return {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"4 hemi-Dslash applications of the FP64 C oracle on 24^3x48 "
+                      f"({dt:.2f} s each, single thread), FP64 18-real algorithmic bytes"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_dslash_sample(1)
+    t = []
+    for _ in range(args.steps):
+        g, dt = oracle_dslash_sample(1)
+        t.append(dt)
+    dt = sum(t) / len(t)
+    import numpy as np
+    Vh = int(np.prod(LAT)) // 2
+    val = Vh * (8 * 18 * 8 + 24 * 8 * 2) / dt / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": round(val, 3), "unit": "GB/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(dt * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "hmc-trajectory 24^3x48 kappa=0.1575 beta=5.6 kappa^4-filter",
+                      "sample": "one FP64 oracle hemi-Dslash of the lattice per step"},
+           "cpu_baseline": {"value": round(val, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                            "sample": "one hemi-Dslash of 24^3x48 per step, single thread"},
+           "e2e": {"value": round(val, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.kernel:
+        run_kernel(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_hmc(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -104,6 +104,19 @@ int hmc_ctx_set_stream(hmc_ctx *ctx, void *stream);
 const char *hmc_last_error(hmc_ctx *ctx);
 /* Number of kernels this context has launched so far. */
 long long hmc_launch_count(hmc_ctx *ctx);
+/* Per-kernel-class timing.  Mode 1: every hemi-Dslash launch is bracketed by
+ * two CUDA events on the context's stream and its algorithmic bytes (links,
+ * input, output and epilogue spinors, each once) are counted.  Mode 2 (launch
+ * timeline): one event after every kernel launch; the time since the previous
+ * event (kernel time plus any idle gap before it) is charged to the launch.
+ * Mode 0 switches timing off.  Any call clears the statistics. */
+int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
+/* Statistics of the index-th kernel class seen since timing was enabled:
+ * class name (e.g. "dslash_f16_12/cg"), launches, summed event time in ms and
+ * summed algorithmic bytes.  Synchronises the stream.  HMC_EINVAL past the
+ * last class. */
+int hmc_timing_get(hmc_ctx *ctx, int index, char *name, int name_len,
+                   long long *launches, double *total_ms, double *bytes);
 
 /* ---- sizes (host-only, no GPU needed) ---------------------------------------- */
 
@@ -159,6 +172,11 @@ typedef struct {
                             its maximum since the last update (0: 0.1) */
   int check_every;       /* iterations between host convergence checks
                             (0: 16); does not change the result */
+  int force_prec;        /* hmc_force_pf only: precision of the Dslash
+                            applications, filter polynomials and outer
+                            products outside the solves (HMC_F64 or HMC_F32;
+                            the solves always reach tol in FP64).  HMC_F32
+                            needs U_lo in F32 or U_hi in LINK18. */
 } hmc_solver_opts;
 
 typedef struct {
@@ -217,7 +235,9 @@ int hmc_action_pf(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
  * T_1 = 0 and T_2 = -(96 kappa^4 / 3) sum_p Re Tr U_p (Sec. II, Delta beta =
  * 96 kappa^4); an extent of 4 adds the straight winding loops of length 4.
  * F += coeff * force of (S_G + T_k); *action (host, nullable) receives
- * S_G + T_k (blocks when non-NULL).  U: F64 gauge, any format.  Extents of 2
+ * S_G + T_k (blocks when non-NULL).  U: F64 or F32 gauge, any format (the
+ * force is computed in the precision of U and accumulated in FP64; the
+ * action needs F64).  Extents of 2
  * with k >= 1 return HMC_EINVAL (longer windings are not implemented). */
 int hmc_force_hopexp(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U,
                      double beta, double kappa, int k, double coeff, double *F,
@@ -285,6 +305,10 @@ typedef struct {
  * U_end (nullable, device, same layout) receives the final field and P_end
  * (nullable, device algebra field) the final momenta, accepted or not (used
  * for the reversibility test of Sec. IV: flip P_end and run back).
+ * params->solver.force_prec == HMC_F32 computes the molecular-dynamics forces
+ * (gauge force on an F32 copy of the links, pseudo-fermion outer products and
+ * filter polynomials) in FP32 with FP64 accumulation; the heatbath, the
+ * actions of H0 and H1 and the link updates stay FP64.
  * Blocks; *res is filled on the host. */
 int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U,
                    const hmc_traj_params *params, const double *P,

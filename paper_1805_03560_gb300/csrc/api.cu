@@ -26,10 +26,13 @@ int cuda_ok(hmc_ctx *ctx, cudaError_t e, const char *what) {
   return fail(ctx, HMC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+static void trace_launch(hmc_ctx *ctx, const char *what);
+
 int launched(hmc_ctx *ctx, const char *what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(ctx, HMC_ECUDA, "launch of %s: %s", what, cudaGetErrorString(e));
   ctx->launches += 1;
+  if (ctx->timing == 2) trace_launch(ctx, what);
   return HMC_OK;
 }
 
@@ -53,6 +56,73 @@ void *workspace(hmc_ctx *ctx, const char *name, size_t bytes) {
   }
   b.n = bytes;
   return b.p;
+}
+
+static cudaEvent_t take_event(hmc_ctx *ctx) {
+  if (!ctx->ev_free.empty()) {
+    cudaEvent_t e = ctx->ev_free.back();
+    ctx->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+static int class_index(hmc_ctx *ctx, const char *cls) {
+  for (size_t i = 0; i < ctx->kstats.size(); ++i)
+    if (ctx->kstats[i].name == cls) return (int)i;
+  ctx->kstats.push_back(hmc_ctx::KStat());
+  ctx->kstats.back().name = cls;
+  return (int)ctx->kstats.size() - 1;
+}
+
+TimedLaunch::TimedLaunch(hmc_ctx *ctx, const char *cls, double bytes)
+    : ctx_(ctx), cls_(-1), bytes_(bytes) {
+  if (ctx->timing != 1) return;
+  cls_ = class_index(ctx, cls);
+  a_ = take_event(ctx);
+  if (a_) cudaEventRecord(a_, ctx->stream);
+}
+
+// timeline mode: one event after each launch, charged to that launch
+static void trace_launch(hmc_ctx *ctx, const char *what) {
+  cudaEvent_t e = take_event(ctx);
+  if (!e) return;
+  cudaEventRecord(e, ctx->stream);
+  if (ctx->trace_prev) ctx->pending.push_back({ctx->trace_prev, e, class_index(ctx, what), 0.0});
+  ctx->trace_prev = e;
+  if (ctx->pending.size() >= 4096) timing_resolve(ctx);
+}
+
+TimedLaunch::~TimedLaunch() {
+  if (!a_) return;
+  cudaEvent_t b = take_event(ctx_);
+  if (!b) return;
+  cudaEventRecord(b, ctx_->stream);
+  ctx_->pending.push_back({a_, b, cls_, bytes_});
+  if (ctx_->pending.size() >= 4096) timing_resolve(ctx_);
+}
+
+int timing_resolve(hmc_ctx *ctx) {
+  if (ctx->pending.empty()) return HMC_OK;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_ok(ctx, e, "timing: synchronise");
+  for (auto &p : ctx->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      hmc_ctx::KStat &k = ctx->kstats[p.cls];
+      k.n += 1;
+      k.ms += ms;
+      k.bytes += p.bytes;
+    }
+    // in timeline mode the end event of one pair is the start of the next, so
+    // only the start events are recycled
+    ctx->ev_free.push_back(p.a);
+    if (ctx->timing != 2) ctx->ev_free.push_back(p.b);
+  }
+  ctx->pending.clear();
+  return HMC_OK;
 }
 
 int check_lattice(hmc_ctx *ctx, const hmc_lattice *lat) {
@@ -142,6 +212,9 @@ int hmc_ctx_create(int device, hmc_ctx **out) {
 int hmc_ctx_destroy(hmc_ctx *ctx) {
   CTX_CHECK(ctx);
   cudaStreamSynchronize(ctx->stream);
+  timing_resolve(ctx);
+  if (ctx->trace_prev) cudaEventDestroy(ctx->trace_prev);
+  for (cudaEvent_t e : ctx->ev_free) cudaEventDestroy(e);
   for (auto &kv : ctx->ws)
     if (kv.second.p) cudaFree(kv.second.p);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
@@ -158,6 +231,35 @@ int hmc_ctx_set_stream(hmc_ctx *ctx, void *stream) {
 const char *hmc_last_error(hmc_ctx *ctx) { return ctx ? ctx->err.c_str() : "context is NULL"; }
 
 long long hmc_launch_count(hmc_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+int hmc_ctx_set_timing(hmc_ctx *ctx, int enable) {
+  CTX_CHECK(ctx);
+  if (enable < 0 || enable > 2) return fail(ctx, HMC_EINVAL, "timing mode must be 0, 1 or 2");
+  TRY(timing_resolve(ctx));
+  if (ctx->trace_prev) {
+    ctx->ev_free.push_back(ctx->trace_prev);
+    ctx->trace_prev = nullptr;
+  }
+  ctx->kstats.clear();
+  ctx->timing = enable;
+  return HMC_OK;
+}
+
+int hmc_timing_get(hmc_ctx *ctx, int index, char *name, int name_len, long long *launches,
+                   double *total_ms, double *bytes) {
+  CTX_CHECK(ctx);
+  TRY(timing_resolve(ctx));
+  if (index < 0 || index >= (int)ctx->kstats.size()) return HMC_EINVAL;
+  const hmc_ctx::KStat &k = ctx->kstats[index];
+  if (name && name_len > 0) {
+    strncpy(name, k.name.c_str(), name_len - 1);
+    name[name_len - 1] = 0;
+  }
+  if (launches) *launches = k.n;
+  if (total_ms) *total_ms = k.ms;
+  if (bytes) *bytes = k.bytes;
+  return HMC_OK;
+}
 
 size_t hmc_gauge_bytes(const hmc_lattice *lat, int prec, int fmt) {
   if (check_lattice(nullptr, lat)) return 0;

@@ -197,6 +197,17 @@ int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int
   const int nb = blocks_for(S, DS_NT);
   if (nblocks) *nblocks = nb;
   cudaStream_t st = ctx->stream;
+  // algorithmic bytes: every link once (8 per output site, shared by the
+  // right-hand sides), the input and output spinors once, the epilogue field
+  // once, and the per-site norms of half storage
+  const double rb = sprec == HMC_F64 ? 8.0 : (sprec == HMC_F32 ? 4.0 : 2.0);
+  double bytes = (double)a.g.Vh * 8.0 * U.fmt * rb + (double)S * 24.0 * rb * (a.x ? 3.0 : 2.0);
+  if (sprec == HMC_F16) bytes += (double)S * 4.0 * (a.x ? 3.0 : 2.0);
+  char cls[64];
+  snprintf(cls, sizeof(cls), "dslash_%s_%d%s%s",
+           sprec == HMC_F64 ? "f64" : (sprec == HMC_F32 ? "f32" : "f16"), U.fmt, a.tag ? "/" : "",
+           a.tag ? a.tag : "");
+  TimedLaunch timer(ctx, cls, bytes);
   switch (sprec * 100 + U.fmt) {
     case HMC_F64 * 100 + 18: launch_sf<HMC_F64, 18>(a, dagger, nb, st); break;
     case HMC_F64 * 100 + 12: launch_sf<HMC_F64, 12>(a, dagger, nb, st); break;
@@ -208,7 +219,7 @@ int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int
       return fail(ctx, HMC_EINVAL, "dslash: unsupported precision %d / link format %d", sprec,
                   U.fmt);
   }
-  return launched(ctx, "dslash");
+  return launched(ctx, cls);
 }
 
 int mhat(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, int sprec, int dagger, int n_rhs,

@@ -21,11 +21,11 @@
 namespace hmc {
 
 // h = u - S B_mu d  (same projection as the Dslash)
-template <int MU, int S>
-__device__ __forceinline__ void fproject(const Cx<double> p[12], Cx<double> h[6]) {
+template <int MU, int S, typename R>
+__device__ __forceinline__ void fproject(const Cx<R> p[12], Cx<R> h[6]) {
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    Cx<double> u0 = p[a], u1 = p[3 + a], d0 = p[6 + a], d1 = p[9 + a];
+    Cx<R> u0 = p[a], u1 = p[3 + a], d0 = p[6 + a], d1 = p[9 + a];
     if (MU == 0) {
       h[a] = S > 0 ? u0 - d0 : u0 + d0;
       h[3 + a] = S > 0 ? u1 - d1 : u1 + d1;
@@ -43,65 +43,68 @@ __device__ __forceinline__ void fproject(const Cx<double> p[12], Cx<double> h[6]
 }
 
 // f_a = Im Tr(lambda_a Q)
-__device__ __forceinline__ void im_tr_lambda(const Cx<double> q[9], double f[8]) {
+template <typename R>
+__device__ __forceinline__ void im_tr_lambda(const Cx<R> q[9], double f[8]) {
   const double r3 = 0.57735026918962576451;  // 1/sqrt(3)
-  f[0] = q[3].im + q[1].im;
-  f[1] = q[1].re - q[3].re;
-  f[2] = q[0].im - q[4].im;
-  f[3] = q[6].im + q[2].im;
-  f[4] = q[2].re - q[6].re;
-  f[5] = q[7].im + q[5].im;
-  f[6] = q[5].re - q[7].re;
-  f[7] = (q[0].im + q[4].im - 2.0 * q[8].im) * r3;
+  f[0] = (double)q[3].im + (double)q[1].im;
+  f[1] = (double)q[1].re - (double)q[3].re;
+  f[2] = (double)q[0].im - (double)q[4].im;
+  f[3] = (double)q[6].im + (double)q[2].im;
+  f[4] = (double)q[2].re - (double)q[6].re;
+  f[5] = (double)q[7].im + (double)q[5].im;
+  f[6] = (double)q[5].re - (double)q[7].re;
+  f[7] = ((double)q[0].im + (double)q[4].im - 2.0 * (double)q[8].im) * r3;
 }
 
 struct HopForceArgs {
   Geo g;
-  const void *gauge;  // F64 links
+  const void *gauge;  // links in the precision of the fields
   const void *W[2];   // W even, W odd   (F64 half fields)
   const void *V[2];   // V even, V odd
   double *F;          // algebra field
   double c;           // F_a += c * (-Im Tr(lambda_a Q)) ; c = coeff * kappa^2
 };
 
-template <int FMT, int MU>
+template <int FMT, int SP, int MU>
 __device__ __forceinline__ void link_force(const HopForceArgs &a, int p, int h, int lex,
                                            const int c[4]) {
+  using R = typename SpinorIO<SP>::R;
+  using SIO = SpinorIO<SP>;
   const int Vh = a.g.Vh;
   const int hn = nb_fwd(a.g, lex, c, MU);
   const double sg = (MU == 0 && c[0] == a.g.L[0] - 1) ? -1.0 : 1.0;
-  Cx<double> s[12], hv[6], hw[6], u[9];
-  Cx<double> A[9], B[9];
+  Cx<R> s[12], hv[6], hw[6], u[9];
+  Cx<R> A[9], B[9];
   // A = sum_s P- V_{x+mu} (x) (P- W_x)^*   with P- = 1 - gamma_mu
-  SpinorIO<HMC_F64>::load(a.V[1 - p], Vh, hn, s);
+  SIO::load(a.V[1 - p], Vh, hn, s);
   fproject<MU, +1>(s, hv);
-  SpinorIO<HMC_F64>::load(a.W[p], Vh, h, s);
+  SIO::load(a.W[p], Vh, h, s);
   fproject<MU, +1>(s, hw);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) A[i * 3 + j] = fmacj(cjmul(hw[j], hv[i]), hw[3 + j], hv[3 + i]);
   // B = sum_s P+ V_x (x) (P+ W_{x+mu})^*   with P+ = 1 + gamma_mu
-  SpinorIO<HMC_F64>::load(a.V[p], Vh, h, s);
+  SIO::load(a.V[p], Vh, h, s);
   fproject<MU, -1>(s, hv);
-  SpinorIO<HMC_F64>::load(a.W[1 - p], Vh, hn, s);
+  SIO::load(a.W[1 - p], Vh, hn, s);
   fproject<MU, -1>(s, hw);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) B[i * 3 + j] = fmacj(cjmul(hw[j], hv[i]), hw[3 + j], hv[3 + i]);
-  LinkIO<HMC_F64, FMT>::load(link_base<HMC_F64, FMT>(a.gauge, Vh, p, MU), Vh, h, u);
+  LinkIO<SP, FMT>::load(link_base<SP, FMT>(a.gauge, Vh, p, MU), Vh, h, u);
   // Q = U A - B U^dag
-  Cx<double> Q[9];
+  Cx<R> Q[9];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      Cx<double> t = u[i * 3] * A[j];
+      Cx<R> t = u[i * 3] * A[j];
       t = fmac(t, u[i * 3 + 1], A[3 + j]);
       t = fmac(t, u[i * 3 + 2], A[6 + j]);
       // (B U^dag)_ij = sum_k B_ik conj(U_jk)
-      Cx<double> v = B[i * 3] * cj(u[j * 3]);
+      Cx<R> v = B[i * 3] * cj(u[j * 3]);
       v = fmac(v, B[i * 3 + 1], cj(u[j * 3 + 1]));
       v = fmac(v, B[i * 3 + 2], cj(u[j * 3 + 2]));
       Q[i * 3 + j] = t - v;
@@ -114,7 +117,7 @@ __device__ __forceinline__ void link_force(const HopForceArgs &a, int p, int h, 
   for (int k = 0; k < 8; ++k) F[(size_t)k * Vh] += cf * f[k];
 }
 
-template <int FMT>
+template <int FMT, int SP>
 __global__ void __launch_bounds__(128) k_hop_force(const HopForceArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 2 * a.g.Vh) return;
@@ -122,15 +125,18 @@ __global__ void __launch_bounds__(128) k_hop_force(const HopForceArgs a) {
   const int h = i - p * a.g.Vh;
   int c[4];
   const int lex = site_coords(a.g, h, p, c);
-  link_force<FMT, 0>(a, p, h, lex, c);
-  link_force<FMT, 1>(a, p, h, lex, c);
-  link_force<FMT, 2>(a, p, h, lex, c);
-  link_force<FMT, 3>(a, p, h, lex, c);
+  link_force<FMT, SP, 0>(a, p, h, lex, c);
+  link_force<FMT, SP, 1>(a, p, h, lex, c);
+  link_force<FMT, SP, 2>(a, p, h, lex, c);
+  link_force<FMT, SP, 3>(a, p, h, lex, c);
 }
 
 int hop_force(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, const void *We, const void *Wo,
-              const void *Ve, const void *Vo, double *F, double c) {
-  if (U.prec != HMC_F64) return fail(ctx, HMC_EINVAL, "force: gauge field must be F64");
+              const void *Ve, const void *Vo, double *F, double c, int sprec) {
+  if (sprec != HMC_F64 && sprec != HMC_F32)
+    return fail(ctx, HMC_EINVAL, "force: spinor precision must be F64 or F32");
+  if (U.prec != sprec)
+    return fail(ctx, HMC_EINVAL, "force: gauge precision must match the fields");
   HopForceArgs a{};
   a.g = g;
   a.gauge = U.data;
@@ -141,11 +147,15 @@ int hop_force(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, const void *We, co
   a.F = F;
   a.c = c;
   int nb = blocks_for(2LL * g.Vh, 128);
-  if (U.fmt == 18)
-    k_hop_force<18><<<nb, 128, 0, ctx->stream>>>(a);
-  else
-    k_hop_force<12><<<nb, 128, 0, ctx->stream>>>(a);
-  return launched(ctx, "hop_force");
+  const bool d = sprec == HMC_F64;
+  if (U.fmt == 18) {
+    if (d) k_hop_force<18, HMC_F64><<<nb, 128, 0, ctx->stream>>>(a);
+    else k_hop_force<18, HMC_F32><<<nb, 128, 0, ctx->stream>>>(a);
+  } else {
+    if (d) k_hop_force<12, HMC_F64><<<nb, 128, 0, ctx->stream>>>(a);
+    else k_hop_force<12, HMC_F32><<<nb, 128, 0, ctx->stream>>>(a);
+  }
+  return launched(ctx, d ? "hop_force_f64" : "hop_force_f32");
 }
 
 }  // namespace hmc

@@ -18,14 +18,13 @@
 
 namespace hmc {
 
-using C = Cx<double>;
-
-__device__ __forceinline__ void m_mul(const C a[9], const C b[9], C c[9]) {
+template <typename R>
+__device__ __forceinline__ void m_mul(const Cx<R> a[9], const Cx<R> b[9], Cx<R> c[9]) {
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      C t = a[i * 3] * b[j];
+      Cx<R> t = a[i * 3] * b[j];
       t = fmac(t, a[i * 3 + 1], b[3 + j]);
       t = fmac(t, a[i * 3 + 2], b[6 + j]);
       c[i * 3 + j] = t;
@@ -33,12 +32,13 @@ __device__ __forceinline__ void m_mul(const C a[9], const C b[9], C c[9]) {
 }
 
 // c = a b^dag
-__device__ __forceinline__ void m_mul_d(const C a[9], const C b[9], C c[9]) {
+template <typename R>
+__device__ __forceinline__ void m_mul_d(const Cx<R> a[9], const Cx<R> b[9], Cx<R> c[9]) {
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      C t = a[i * 3] * cj(b[j * 3]);
+      Cx<R> t = a[i * 3] * cj(b[j * 3]);
       t = fmac(t, a[i * 3 + 1], cj(b[j * 3 + 1]));
       t = fmac(t, a[i * 3 + 2], cj(b[j * 3 + 2]));
       c[i * 3 + j] = t;
@@ -46,47 +46,53 @@ __device__ __forceinline__ void m_mul_d(const C a[9], const C b[9], C c[9]) {
 }
 
 // c = a^dag b
-__device__ __forceinline__ void m_dmul(const C a[9], const C b[9], C c[9]) {
+template <typename R>
+__device__ __forceinline__ void m_dmul(const Cx<R> a[9], const Cx<R> b[9], Cx<R> c[9]) {
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      C t = cjmul(a[i], b[j]);
+      Cx<R> t = cjmul(a[i], b[j]);
       t = fmacj(t, a[3 + i], b[3 + j]);
       t = fmacj(t, a[6 + i], b[6 + j]);
       c[i * 3 + j] = t;
     }
 }
 
-__device__ __forceinline__ double re_tr(const C m[9]) { return m[0].re + m[4].re + m[8].re; }
+template <typename R>
+__device__ __forceinline__ double re_tr(const Cx<R> m[9]) {
+  return (double)m[0].re + (double)m[4].re + (double)m[8].re;
+}
 
 __device__ __forceinline__ int lex_of(const Geo &g, const int c[4]) {
   return ((c[0] * g.L[1] + c[1]) * g.L[2] + c[2]) * g.L[3] + c[3];
 }
 
 // link (mu) at the site with coordinates c shifted by d1 along n1 and d2 along n2
-template <int FMT>
+template <int P, int FMT>
 __device__ __forceinline__ void link_at(const Geo &g, const void *gauge, const int c[4], int mu,
-                                        int n1, int d1, int n2, int d2, C u[9]) {
+                                        int n1, int d1, int n2, int d2,
+                                        Cx<typename LinkIO<P, FMT>::R> u[9]) {
   int s[4] = {c[0], c[1], c[2], c[3]};
   if (d1) s[n1] = (s[n1] + d1 + g.L[n1]) % g.L[n1];
   if (d2) s[n2] = (s[n2] + d2 + g.L[n2]) % g.L[n2];
   int lex = lex_of(g, s);
   int p = (s[0] + s[1] + s[2] + s[3]) & 1;
-  LinkIO<HMC_F64, FMT>::load(link_base<HMC_F64, FMT>(gauge, g.Vh, p, mu), g.Vh, lex >> 1, u);
+  LinkIO<P, FMT>::load(link_base<P, FMT>(gauge, g.Vh, p, mu), g.Vh, lex >> 1, u);
 }
 
 // f_a = Im Tr(lambda_a Q)
-__device__ __forceinline__ void im_tr_lambda_g(const C q[9], double f[8]) {
+template <typename R>
+__device__ __forceinline__ void im_tr_lambda_g(const Cx<R> q[9], double f[8]) {
   const double r3 = 0.57735026918962576451;
-  f[0] = q[3].im + q[1].im;
-  f[1] = q[1].re - q[3].re;
-  f[2] = q[0].im - q[4].im;
-  f[3] = q[6].im + q[2].im;
-  f[4] = q[2].re - q[6].re;
-  f[5] = q[7].im + q[5].im;
-  f[6] = q[5].re - q[7].re;
-  f[7] = (q[0].im + q[4].im - 2.0 * q[8].im) * r3;
+  f[0] = (double)q[3].im + (double)q[1].im;
+  f[1] = (double)q[1].re - (double)q[3].re;
+  f[2] = (double)q[0].im - (double)q[4].im;
+  f[3] = (double)q[6].im + (double)q[2].im;
+  f[4] = (double)q[2].re - (double)q[6].re;
+  f[5] = (double)q[7].im + (double)q[5].im;
+  f[6] = (double)q[5].re - (double)q[7].re;
+  f[7] = ((double)q[0].im + (double)q[4].im - 2.0 * (double)q[8].im) * r3;
 }
 
 struct GaugeArgs {
@@ -98,8 +104,10 @@ struct GaugeArgs {
   double *partials; // action kernel: [block] plaquette sums, [nblocks + block] line sums
 };
 
-template <int FMT>
+template <int P, int FMT>
 __global__ void __launch_bounds__(128) k_gauge_force(const GaugeArgs a) {
+  using R = typename LinkIO<P, FMT>::R;
+  using C = Cx<R>;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 8 * a.g.Vh) return;
   const int mu = i / (2 * a.g.Vh);
@@ -110,27 +118,27 @@ __global__ void __launch_bounds__(128) k_gauge_force(const GaugeArgs a) {
   site_coords(a.g, h, p, c);
   C A[9], t[9], u1[9], u2[9], u3[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) A[k] = {0.0, 0.0};
+  for (int k = 0; k < 9; ++k) A[k] = {R(0), R(0)};
   for (int nu = 0; nu < 4; ++nu) {
     if (nu == mu) continue;
     // upper staple U_{x+mu,nu} U^dag_{x+nu,mu} U^dag_{x,nu}
-    link_at<FMT>(a.g, a.gauge, c, nu, mu, 1, 0, 0, u1);
-    link_at<FMT>(a.g, a.gauge, c, mu, nu, 1, 0, 0, u2);
-    link_at<FMT>(a.g, a.gauge, c, nu, 0, 0, 0, 0, u3);
+    link_at<P, FMT>(a.g, a.gauge, c, nu, mu, 1, 0, 0, u1);
+    link_at<P, FMT>(a.g, a.gauge, c, mu, nu, 1, 0, 0, u2);
+    link_at<P, FMT>(a.g, a.gauge, c, nu, 0, 0, 0, 0, u3);
     m_mul_d(u1, u2, t);
     m_mul_d(t, u3, u1);
 #pragma unroll
     for (int k = 0; k < 9; ++k) A[k] = A[k] + u1[k];
     // lower staple U^dag_{x+mu-nu,nu} U^dag_{x-nu,mu} U_{x-nu,nu}
-    link_at<FMT>(a.g, a.gauge, c, nu, mu, 1, nu, -1, u1);
-    link_at<FMT>(a.g, a.gauge, c, mu, nu, -1, 0, 0, u2);
-    link_at<FMT>(a.g, a.gauge, c, nu, nu, -1, 0, 0, u3);
+    link_at<P, FMT>(a.g, a.gauge, c, nu, mu, 1, nu, -1, u1);
+    link_at<P, FMT>(a.g, a.gauge, c, mu, nu, -1, 0, 0, u2);
+    link_at<P, FMT>(a.g, a.gauge, c, nu, nu, -1, 0, 0, u3);
     m_mul(u2, u1, t);  // U_{x-nu,mu} U_{x+mu-nu,nu}
     m_dmul(t, u3, u1); // (U_{x-nu,mu} U_{x+mu-nu,nu})^dag U_{x-nu,nu}
 #pragma unroll
     for (int k = 0; k < 9; ++k) A[k] = A[k] + u1[k];
   }
-  link_at<FMT>(a.g, a.gauge, c, mu, 0, 0, 0, 0, u1);
+  link_at<P, FMT>(a.g, a.gauge, c, mu, 0, 0, 0, 0, u1);
   m_mul(u1, A, t);
   double f[8], fp[8];
   im_tr_lambda_g(t, f);
@@ -141,7 +149,7 @@ __global__ void __launch_bounds__(128) k_gauge_force(const GaugeArgs a) {
     // P = U_{x,mu} U_{x+mu,mu} ... around the torus (extent 4)
     for (int k = 0; k < 9; ++k) t[k] = u1[k];
     for (int s = 1; s < a.g.L[mu]; ++s) {
-      link_at<FMT>(a.g, a.gauge, c, mu, mu, s, 0, 0, u2);
+      link_at<P, FMT>(a.g, a.gauge, c, mu, mu, s, 0, 0, u2);
       m_mul(t, u2, u3);
       for (int k = 0; k < 9; ++k) t[k] = u3[k];
     }
@@ -157,6 +165,7 @@ __global__ void __launch_bounds__(128) k_gauge_force(const GaugeArgs a) {
 // per site: sum_{mu<nu} Re Tr U_p and sum over extent-4 directions of s_mu Re Tr P_mu(x)
 template <int FMT>
 __global__ void __launch_bounds__(128) k_gauge_action(const GaugeArgs a, int want_lines) {
+  using C = Cx<double>;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double plaq = 0.0, line = 0.0;
   if (i < 2 * a.g.Vh) {
@@ -167,10 +176,10 @@ __global__ void __launch_bounds__(128) k_gauge_action(const GaugeArgs a, int wan
     C u1[9], u2[9], u3[9], u4[9], t[9], w[9];
     for (int mu = 0; mu < 4; ++mu)
       for (int nu = mu + 1; nu < 4; ++nu) {
-        link_at<FMT>(a.g, a.gauge, c, mu, 0, 0, 0, 0, u1);
-        link_at<FMT>(a.g, a.gauge, c, nu, mu, 1, 0, 0, u2);
-        link_at<FMT>(a.g, a.gauge, c, mu, nu, 1, 0, 0, u3);
-        link_at<FMT>(a.g, a.gauge, c, nu, 0, 0, 0, 0, u4);
+        link_at<HMC_F64, FMT>(a.g, a.gauge, c, mu, 0, 0, 0, 0, u1);
+        link_at<HMC_F64, FMT>(a.g, a.gauge, c, nu, mu, 1, 0, 0, u2);
+        link_at<HMC_F64, FMT>(a.g, a.gauge, c, mu, nu, 1, 0, 0, u3);
+        link_at<HMC_F64, FMT>(a.g, a.gauge, c, nu, 0, 0, 0, 0, u4);
         m_mul(u1, u2, t);
         m_mul_d(t, u3, w);
         m_mul_d(w, u4, t);
@@ -179,9 +188,9 @@ __global__ void __launch_bounds__(128) k_gauge_action(const GaugeArgs a, int wan
     if (want_lines) {
       for (int mu = 0; mu < 4; ++mu) {
         if (a.g.L[mu] != 4) continue;
-        link_at<FMT>(a.g, a.gauge, c, mu, 0, 0, 0, 0, t);
+        link_at<HMC_F64, FMT>(a.g, a.gauge, c, mu, 0, 0, 0, 0, t);
         for (int s = 1; s < 4; ++s) {
-          link_at<FMT>(a.g, a.gauge, c, mu, mu, s, 0, 0, u2);
+          link_at<HMC_F64, FMT>(a.g, a.gauge, c, mu, mu, s, 0, 0, u2);
           m_mul(t, u2, u3);
           for (int k = 0; k < 9; ++k) t[k] = u3[k];
         }
@@ -237,11 +246,15 @@ int gauge_force(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, double beta, dou
   // each giving Re Tr(omega P) -> F_a = -(c L_mu / 2) Im Tr(lambda_a P)
   for (int mu = 0; mu < 4; ++mu) a.cpoly[mu] = -coeff * cl[mu] * g.L[mu] / 2.0;
   int nb = blocks_for(8LL * g.Vh, 128);
-  if (U.fmt == 18)
-    k_gauge_force<18><<<nb, 128, 0, ctx->stream>>>(a);
-  else
-    k_gauge_force<12><<<nb, 128, 0, ctx->stream>>>(a);
-  return launched(ctx, "gauge_force");
+  cudaStream_t strm = ctx->stream;
+  switch (U.prec * 100 + U.fmt) {
+    case HMC_F64 * 100 + 18: k_gauge_force<HMC_F64, 18><<<nb, 128, 0, strm>>>(a); break;
+    case HMC_F64 * 100 + 12: k_gauge_force<HMC_F64, 12><<<nb, 128, 0, strm>>>(a); break;
+    case HMC_F32 * 100 + 18: k_gauge_force<HMC_F32, 18><<<nb, 128, 0, strm>>>(a); break;
+    case HMC_F32 * 100 + 12: k_gauge_force<HMC_F32, 12><<<nb, 128, 0, strm>>>(a); break;
+    default: return fail(ctx, HMC_EINVAL, "gauge_force: links must be F64 or F32");
+  }
+  return launched(ctx, U.prec == HMC_F64 ? "gauge_force_f64" : "gauge_force_f32");
 }
 
 // Enqueues the action reduction: dst[0] = plaquette sum, dst[1] = signed line

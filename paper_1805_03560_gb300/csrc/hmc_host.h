@@ -5,6 +5,7 @@
 
 #include <map>
 #include <string>
+#include <vector>
 
 #include "hmc_internal.cuh"
 
@@ -19,9 +20,44 @@ struct hmc_ctx {
   };
   std::map<std::string, Buf> ws;
   double *h_pinned = nullptr;  // small pinned host buffer for scalar reads
+  // optional per-kernel-class timing: mode 1 brackets every hemi-Dslash with
+  // two CUDA events; mode 2 records one event after every launch and charges
+  // the time since the previous event to that launch (a launch timeline).
+  int timing = 0;
+  cudaEvent_t trace_prev = nullptr;
+  struct Pending {
+    cudaEvent_t a, b;
+    int cls;
+    double bytes;
+  };
+  struct KStat {
+    std::string name;
+    long long n = 0;
+    double ms = 0.0, bytes = 0.0;
+  };
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<Pending> pending;
+  std::vector<KStat> kstats;
 };
 
 namespace hmc {
+
+// Event-timed launch region: records an event before construction returns and
+// one at destruction, both on ctx->stream, when timing is enabled.  `bytes`
+// are the algorithmic bytes the launch moves.
+class TimedLaunch {
+ public:
+  TimedLaunch(hmc_ctx *ctx, const char *cls, double bytes);
+  ~TimedLaunch();
+
+ private:
+  hmc_ctx *ctx_;
+  int cls_;
+  double bytes_;
+  cudaEvent_t a_ = nullptr;
+};
+// Sync the stream and fold pending event pairs into ctx->kstats.
+int timing_resolve(hmc_ctx *ctx);
 
 constexpr int DS_NT = 128;   // threads per block, stencil kernels
 constexpr int BL_NT = 256;   // threads per block, BLAS kernels
@@ -59,6 +95,7 @@ struct DslashArgs {
   const double *cb_rhs;
   double *partials;
   const int *gate;  // device flag (nullable): the launch does nothing when *gate == 0
+  const char *tag;  // timing class suffix (nullable)
 };
 int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int dagger,
            int *nblocks);
@@ -71,8 +108,9 @@ int axpby(hmc_ctx *ctx, int prec, void *out, double a, const void *x, double b, 
           int S);
 // partial sums of Re <x, y> for F64 fields
 int dot_partials(hmc_ctx *ctx, const void *x, const void *y, int S, double *partials, int *nb);
+// F += c * (-Im Tr(lambda_a Q)) per link; W, V halves in precision sprec (F64 or F32)
 int hop_force(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, const void *We, const void *Wo,
-              const void *Ve, const void *Vo, double *F, double c);
+              const void *Ve, const void *Vo, double *F, double c, int sprec);
 int gauge_force(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, double beta, double kappa, int k,
                 double coeff, double *F);
 int gauge_action_sums(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, int with_lines,

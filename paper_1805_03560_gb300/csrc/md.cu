@@ -2,11 +2,12 @@
 //   P(eps): Pi <- Pi - eps F      (dPi/dtau = -F fixes the sign)
 //   T(eps): U  <- exp(eps Pi) U   (dU/dtau = Pi U, Pi antihermitian)
 // The kinetic term (1/2)(Pi, Pi) = (1/2) sum_a P_a^2 with Pi = sum_a P_a T_a,
-// T_a = i lambda_a / 2.  The exponential is a degree-16 Taylor polynomial in
-// Horner form after scaling by a power of two (norm <= 1/2) and squaring back;
-// the truncation error is below 2^-17 / 17! relative, far under double
-// rounding.  Links are projected back onto SU(3) after every update
-// (Gram-Schmidt of rows 0, 1; row 2 = conj(row0 x row1)).
+// T_a = i lambda_a / 2.  The exponential uses the Cayley-Hamilton theorem of
+// 3x3 matrices (exp A = f0 + f1 A + f2 A^2, see expm_su3), which needs one
+// matrix product instead of a Taylor polynomial's dozen; FP64 arithmetic is
+// scarce on this GPU and the link update is FP64-ALU bound.  Links are
+// projected back onto SU(3) after every update (Gram-Schmidt of rows 0, 1;
+// row 2 = conj(row0 x row1)).
 #include "hmc_host.h"
 
 namespace hmc {
@@ -38,6 +39,14 @@ __device__ __forceinline__ void mm(const C a[9], const C b[9], C c[9]) {
     }
 }
 
+// exp(A) for a traceless 3x3 matrix by the Cayley-Hamilton theorem:
+// A^3 = s A + d I with s = Tr(A^2)/2 and d = det A, so every power is
+// A^n = a_n I + b_n A + c_n A^2 with
+//   (a, b, c)_{n+1} = (c_n d, a_n + c_n s, b_n),
+// and exp(A) = f0 I + f1 A + f2 A^2 with f = sum_n (a, b, c)_n / n!.  The
+// scalar series is summed until its terms fall below 2^-60 of the leading
+// coefficient; matrices of norm above 1 are first scaled by a power of two and
+// squared back.  Cost: one 3x3 product for A^2 (plus one per squaring).
 __device__ __forceinline__ void expm_su3(const C A[9], C E[9]) {
   double nrm = 0.0;
 #pragma unroll
@@ -47,33 +56,43 @@ __device__ __forceinline__ void expm_su3(const C A[9], C E[9]) {
     for (int j = 0; j < 3; ++j) r += sqrt(norm2(A[i * 3 + j]));
     nrm = fmax(nrm, r);
   }
-  int s = 0;
-  while (nrm > 0.5 && s < 60) {
+  int sq = 0;
+  while (nrm > 1.0 && sq < 60) {
     nrm *= 0.5;
-    ++s;
+    ++sq;
   }
-  const double sc = ldexp(1.0, -s);
-  C B[9], R[9], T[9];
+  const double sc = ldexp(1.0, -sq);
+  C B[9], B2[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) B[k] = sc * A[k];
-  // Horner: R = I + B/16, R = I + B R / n for n = 15 .. 1
-#pragma unroll
-  for (int k = 0; k < 9; ++k) R[k] = (1.0 / 16.0) * B[k];
-  R[0].re += 1.0;
-  R[4].re += 1.0;
-  R[8].re += 1.0;
+  mm(B, B, B2);
+  const C s = 0.5 * (B2[0] + B2[4] + B2[8]);
+  const C d = B[0] * (B[4] * B[8] - B[5] * B[7]) - B[1] * (B[3] * B[8] - B[5] * B[6]) +
+              B[2] * (B[3] * B[7] - B[4] * B[6]);
+  C ta = {1.0, 0.0}, tb = {0.0, 0.0}, tc = {0.0, 0.0};  // (a, b, c)_n / n!
+  C f0 = ta, f1 = tb, f2 = tc;
 #pragma unroll 1
-  for (int n = 15; n >= 1; --n) {
-    mm(B, R, T);
-    const double inv = 1.0 / n;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) R[k] = inv * T[k];
-    R[0].re += 1.0;
-    R[4].re += 1.0;
-    R[8].re += 1.0;
+  for (int n = 0; n < 40; ++n) {
+    const double inv = 1.0 / (n + 1);
+    const C na = inv * (tc * d), nb = inv * (ta + tc * s), nc = inv * tb;
+    ta = na;
+    tb = nb;
+    tc = nc;
+    f0 = f0 + ta;
+    f1 = f1 + tb;
+    f2 = f2 + tc;
+    const double m = fmax(norm2(ta), fmax(norm2(tb), norm2(tc)));
+    if (m < 7.6e-37 && n >= 2) break;  // (2^-60)^2: the terms are exhausted
   }
+  C R[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) R[k] = f1 * B[k] + f2 * B2[k];
+  R[0] = R[0] + f0;
+  R[4] = R[4] + f0;
+  R[8] = R[8] + f0;
 #pragma unroll 1
-  for (int k = 0; k < s; ++k) {
+  for (int k = 0; k < sq; ++k) {
+    C T[9];
     mm(R, R, T);
 #pragma unroll
     for (int q = 0; q < 9; ++q) R[q] = T[q];

@@ -420,12 +420,7 @@ struct Solve {
   } while (0)
 
 // A x in FP64 into q (uses y64, t64); partials of nothing.
-int apply_A64(Solve &s, const void *in, void *out, const int *gate) {
-  DslashArgs a{};
-  a.g = s.g;
-  a.n_rhs = 1;
-  a.gauge = s.Uh.data;
-  (void)gate;
+int apply_A64(Solve &s, const void *in, void *out) {
   TRY(mhat(s.ctx, s.g, s.Uh, HMC_F64, 0, 1, s.y64, in, s.t64, s.kappa, nullptr, nullptr, nullptr));
   TRY(mhat(s.ctx, s.g, s.Uh, HMC_F64, 1, 1, out, s.y64, s.t64, s.kappa, nullptr, nullptr,
            nullptr));
@@ -466,6 +461,7 @@ int one_iteration(Solve &s) {
     a.n_rhs = 1;
     a.gauge = U.data;
     a.gate = &s.st->active;
+    a.tag = "cg";
     a.p = 1; a.out = s.tlo; a.in = s.p; a.cb = 1.0;
     TRY(dslash(ctx, a, U, s.plo, 0, nullptr));
     a.p = 0; a.out = s.y; a.in = s.tlo; a.x = s.p; a.ca = 1.0; a.cb = -s.kappa * s.kappa;
@@ -517,6 +513,7 @@ int apply_A64_gated(Solve &s, const void *in, void *out, const int *gate) {
   a.n_rhs = 1;
   a.gauge = s.Uh.data;
   a.gate = gate;
+  a.tag = "reliable";
   a.p = 1; a.out = s.t64; a.in = in; a.cb = 1.0;
   TRY(dslash(s.ctx, a, s.Uh, HMC_F64, 0, nullptr));
   a.p = 0; a.out = s.y64; a.in = s.t64; a.x = in; a.ca = 1.0; a.cb = -s.kappa * s.kappa;
@@ -535,7 +532,7 @@ int read_state(Solve &s, CGState *h) {
 
 // true residual of x into r (F64), returns |r|^2 / |b|^2 on the host
 int true_residual(Solve &s, double *rel2, double b2) {
-  TRY(apply_A64(s, s.x, s.q, nullptr));
+  TRY(apply_A64(s, s.x, s.q));
   launch_residual<HMC_F32>(s, nullptr, nullptr);
   TRY(launched(s.ctx, "residual"));
   double *d = (double *)((char *)s.st + sizeof(CGState));
@@ -625,14 +622,25 @@ int cg_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
   double rel2 = 0.0;
   if (h.done == 2) return fail(ctx, HMC_ENAN, "cg: source has NaN/Inf");
   int restarts = 0;
+  int next_batch = check;
   while (!h.done || (h.done == 1 && s.plo == HMC_F64)) {
     if (!h.done) {
-      int todo = check;
+      int todo = next_batch;
       if (h.iter + todo > max_iter) todo = max_iter - h.iter;
+      const double rr_before = h.rr;
+      const int it_before = h.iter;
       for (int k = 0; k < todo; ++k) TRY(one_iteration(s));
       TRY(read_state(s, &h));
       if (h.done == 2) break;
       if (!h.done && h.iter >= max_iter) break;
+      // size the next batch from the observed convergence rate, so that few
+      // gated-off iterations are queued after convergence
+      next_batch = check;
+      if (!h.done && h.iter > it_before && h.rr > 0.0 && h.rr < rr_before) {
+        const double rate = log(h.rr / rr_before) / (h.iter - it_before);
+        const double left = log(tol * tol * b2 / h.rr) / rate;
+        if (left < check) next_batch = left < 1.0 ? 1 : (int)ceil(left);
+      }
       continue;
     }
     // plain FP64: confirm on the true residual, restart from it if needed

@@ -106,15 +106,19 @@ static int solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gaug
 }
 
 // F += coeff * d/dU 2 Re[A^dag dK B] = coeff kappa^2 (W^dag dH V + h.c.),
-// W = (A, H_eo^dag A), V = (B, H_oe B)
-static int pair_force(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, double kappa, const void *A,
-                      const void *B, double coeff, double *F) {
+// W = (A, H_eo^dag A), V = (B, H_oe B).  A, B are fields of precision fp, Uf
+// the gauge field of that precision (for the two hemi-Dslashes) and U64 the
+// FP64 links (for the outer products).
+static int pair_force(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U64, const hmc_gauge &Uf,
+                      int fp, double kappa, const void *A, const void *B, double coeff, double *F) {
+  // scratch is always requested at its FP64 size so it is never reallocated
   size_t f64 = spinor_bytes(g, HMC_F64, 1);
   void *Wo = workspace(ctx, "pf_wo", f64), *Vo = workspace(ctx, "pf_vo", f64);
   if (!Wo || !Vo) return HMC_ENOMEM;
-  TRY(hop(ctx, g, U, HMC_F64, 1, 1, Wo, A, nullptr, 0.0, 1.0));  // H_eo^dag A
-  TRY(hop(ctx, g, U, HMC_F64, 1, 0, Vo, B, nullptr, 0.0, 1.0));  // H_oe B
-  return hop_force(ctx, g, U, A, Wo, B, Vo, F, coeff * kappa * kappa);
+  TRY(hop(ctx, g, Uf, fp, 1, 1, Wo, A, nullptr, 0.0, 1.0));  // H_eo^dag A
+  TRY(hop(ctx, g, Uf, fp, 1, 0, Vo, B, nullptr, 0.0, 1.0));  // H_oe B
+  (void)U64;
+  return hop_force(ctx, g, Uf, A, Wo, B, Vo, F, coeff * kappa * kappa, fp);
 }
 
 // y = Mhat^{-1} phi via the normal equations
@@ -128,42 +132,94 @@ static int mhat_inverse(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const h
   return solve(ctx, g, Uh, Ul, y, src, kappa, tol, opts, acc);
 }
 
+// The pseudo-fermion force.  Solves always run to tol with their FP64
+// residual; with opts->force_prec == HMC_F32 every other Dslash, the filter
+// polynomials (Horner chain Y_i, the chain X_i = K^dag X_{i-1}) and the spin
+// projections of the outer products run on F32 fields; the outer products and
+// the force accumulate in FP64 on the FP64 links.
 int force_pf(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
              const void *phi, double kappa, const hmc_filter *filt, double coeff, double *F,
              double tol, const hmc_solver_opts *opts, hmc_solve_stats *acc) {
-  size_t f64 = spinor_bytes(g, HMC_F64, 1);
+  const int fp = opts ? opts->force_prec : HMC_F64;
+  if (fp != HMC_F64 && fp != HMC_F32)
+    return fail(ctx, HMC_EINVAL, "force_pf: force_prec must be F64 or F32");
+  hmc_gauge Uf = Uh;
+  if (fp == HMC_F32) {
+    if (Ul && Ul->prec == HMC_F32) {
+      Uf = *Ul;
+    } else if (Uh.fmt == HMC_LINK18) {
+      void *u32 = workspace(ctx, "pf_u32", gauge_bytes(g, HMC_F32, HMC_LINK12));
+      if (!u32) return HMC_ENOMEM;
+      TRY(convert_gauge(ctx, g, Uh.data, u32, HMC_F32, HMC_LINK12));
+      Uf = hmc_gauge{u32, HMC_F32, HMC_LINK12};
+    } else {
+      return fail(ctx, HMC_EINVAL, "force_pf: F32 force needs U_lo in F32 or U_hi in LINK18");
+    }
+  }
+  const size_t f64 = spinor_bytes(g, HMC_F64, 1);
   void *X = workspace(ctx, "pf_x", f64), *Y = workspace(ctx, "pf_y", f64);
-  void *tmp = workspace(ctx, "pf_tmp", f64);
-  if (!X || !Y || !tmp) return HMC_ENOMEM;
+  void *tmp = workspace(ctx, "pf_tmp", f64), *Xf = workspace(ctx, "pf_xf", f64);
+  if (!X || !Y || !tmp || !Xf) return HMC_ENOMEM;
+  // field in the force precision from an FP64 field
+  auto to_fp = [&](void *dst, const void *src) -> int {
+    return copy_convert(ctx, fp, HMC_F64, dst, src, g.Vh);
+  };
   if (!filt) {
-    // X = (Mhat^dag Mhat)^{-1} phi, Y = Mhat X; delta S = 2 Re[Y^dag dK ... ] form
+    // X = (Mhat^dag Mhat)^{-1} phi, Y = Mhat X: delta S = 2 Re[Y^dag dK X]-form
     TRY(solve(ctx, g, Uh, Ul, X, phi, kappa, tol, opts, acc));
-    TRY(mhat(ctx, g, Uh, HMC_F64, 0, 1, Y, X, tmp, kappa, nullptr, nullptr, nullptr));
-    return pair_force(ctx, g, Uh, kappa, Y, X, coeff, F);
+    const void *Xp = X;
+    if (fp != HMC_F64) {
+      TRY(to_fp(Xf, X));
+      Xp = Xf;
+    }
+    TRY(mhat(ctx, g, Uf, fp, 0, 1, Y, Xp, tmp, kappa, nullptr, nullptr, nullptr));
+    return pair_force(ctx, g, Uh, Uf, fp, kappa, Y, Xp, coeff, F);
   }
   const int n = filt->n;
   if (n < 0 || !filt->b) return fail(ctx, HMC_EINVAL, "force_pf: bad filter");
-  // Horner iterates Y_n .. Y_0 (Y_j at slot j)
+  // Horner iterates Y_n .. Y_0 (Y_j at slot j), in the force precision
+  const size_t fb = spinor_bytes(g, fp, 1);
   char *Hs = (char *)workspace(ctx, "pf_horner", f64 * (n + 1));
   void *Yt = workspace(ctx, "pf_ytilde", f64), *Xt = workspace(ctx, "pf_xtilde", f64);
   void *Xi = workspace(ctx, "pf_xi", f64), *Xn = workspace(ctx, "pf_xnext", f64);
-  if (!Hs || !Yt || !Xt || !Xi || !Xn) return HMC_ENOMEM;
-  auto slot = [&](int j) { return (void *)(Hs + f64 * j); };
-  TRY(axpby(ctx, HMC_F64, slot(n), filt->b[n], phi, 0.0, nullptr, g.Vh));
+  void *phf = workspace(ctx, "pf_phif", f64), *Ytf = workspace(ctx, "pf_ytf", f64);
+  if (!Hs || !Yt || !Xt || !Xi || !Xn || !phf || !Ytf) return HMC_ENOMEM;
+  auto slot = [&](int j) { return (void *)(Hs + fb * j); };
+  const void *phi_f = phi;
+  if (fp != HMC_F64) {
+    TRY(to_fp(phf, phi));
+    phi_f = phf;
+  }
+  TRY(axpby(ctx, fp, slot(n), filt->b[n], phi_f, 0.0, nullptr, g.Vh));
   for (int j = n; j >= 1; --j)
-    TRY(apply_K(ctx, g, Uh, HMC_F64, 0, kappa, slot(j - 1), slot(j), phi, filt->b[j - 1], tmp));
-  // Ytilde = alpha Mhat^{-1} phi
+    TRY(apply_K(ctx, g, Uf, fp, 0, kappa, slot(j - 1), slot(j), phi_f, filt->b[j - 1], tmp));
+  // Ytilde = alpha Mhat^{-1} phi (FP64 solve)
   TRY(mhat_inverse(ctx, g, Uh, Ul, Yt, phi, kappa, tol, opts, acc));
   TRY(axpby(ctx, HMC_F64, Yt, filt->alpha, Yt, 0.0, nullptr, g.Vh));
+  const void *Yt_f = Yt;
+  if (fp != HMC_F64) {
+    TRY(to_fp(Ytf, Yt));
+    Yt_f = Ytf;
+  }
   // X_1 = Y_0 + Ytilde ; Xtilde = Mhat (Mhat^dag Mhat)^{-1} X_1
-  TRY(axpby(ctx, HMC_F64, Xi, 1.0, slot(0), 1.0, Yt, g.Vh));
-  TRY(solve(ctx, g, Uh, Ul, X, Xi, kappa, tol, opts, acc));
-  TRY(mhat(ctx, g, Uh, HMC_F64, 0, 1, Xt, X, tmp, kappa, nullptr, nullptr, nullptr));
-  TRY(pair_force(ctx, g, Uh, kappa, Xt, Yt, coeff, F));
+  TRY(axpby(ctx, fp, Xi, 1.0, slot(0), 1.0, Yt_f, g.Vh));
+  const void *x1_64 = Xi;
+  if (fp != HMC_F64) {
+    TRY(copy_convert(ctx, HMC_F64, fp, Y, Xi, g.Vh));
+    x1_64 = Y;
+  }
+  TRY(solve(ctx, g, Uh, Ul, X, x1_64, kappa, tol, opts, acc));
+  const void *Xs = X;
+  if (fp != HMC_F64) {
+    TRY(to_fp(Xf, X));
+    Xs = Xf;
+  }
+  TRY(mhat(ctx, g, Uf, fp, 0, 1, Xt, Xs, tmp, kappa, nullptr, nullptr, nullptr));
+  TRY(pair_force(ctx, g, Uh, Uf, fp, kappa, Xt, Yt_f, coeff, F));
   for (int i = 1; i <= n; ++i) {
-    TRY(pair_force(ctx, g, Uh, kappa, Xi, slot(i), coeff, F));
+    TRY(pair_force(ctx, g, Uh, Uf, fp, kappa, Xi, slot(i), coeff, F));
     if (i < n) {
-      TRY(apply_K(ctx, g, Uh, HMC_F64, 1, kappa, Xn, Xi, nullptr, 0.0, tmp));
+      TRY(apply_K(ctx, g, Uf, fp, 1, kappa, Xn, Xi, nullptr, 0.0, tmp));
       void *t = Xi;
       Xi = Xn;
       Xn = t;
@@ -222,9 +278,19 @@ int md_evolve(hmc_ctx *ctx, const Geo &g, void *U1, void *Ulo, double *P, double
     *solves += k ? 2 : 1;
     return update_momenta(ctx, g, P, F, eps);
   };
+  // with force_prec F32 the gauge force runs on an F32 copy of the links
+  const bool g32 = prm->solver.force_prec == HMC_F32;
+  void *U32 = g32 ? workspace(ctx, "tr_u32", gauge_bytes(g, HMC_F32, HMC_LINK12)) : nullptr;
+  if (g32 && !U32) return HMC_ENOMEM;
+  const hmc_gauge Ug32{U32, HMC_F32, HMC_LINK12};
   auto gauge_step = [&](double eps) -> int {
     TRY(cuda_ok(ctx, cudaMemsetAsync(F, 0, fbytes, st), "md: zero F"));
-    TRY(gauge_force(ctx, g, Uh, prm->beta, prm->kappa, k, 1.0, F));
+    if (g32) {
+      TRY(convert_gauge(ctx, g, U1, U32, HMC_F32, HMC_LINK12));
+      TRY(gauge_force(ctx, g, Ug32, prm->beta, prm->kappa, k, 1.0, F));
+    } else {
+      TRY(gauge_force(ctx, g, Uh, prm->beta, prm->kappa, k, 1.0, F));
+    }
     return update_momenta(ctx, g, P, F, eps);
   };
   TRY(pf_step(0.5 * dt));
@@ -295,7 +361,9 @@ int hmc_force_hopexp(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U, d
   CTX_CHECK(ctx);
   TRY(check_lattice(ctx, lat));
   TRY(check_gauge(ctx, U));
-  if (U->prec != HMC_F64) return fail(ctx, HMC_EINVAL, "force_hopexp: U must be F64");
+  if (U->prec == HMC_F16) return fail(ctx, HMC_EINVAL, "force_hopexp: U must be F64 or F32");
+  if (action && U->prec != HMC_F64)
+    return fail(ctx, HMC_EINVAL, "force_hopexp: the action needs F64 links");
   Geo g = make_geo(*lat);
   if (F) TRY(gauge_force(ctx, g, *U, beta, kappa, k, coeff, F));
   if (action) TRY(gauge_action(ctx, g, *U, beta, kappa, k, action, nullptr));

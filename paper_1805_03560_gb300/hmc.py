@@ -32,7 +32,8 @@ class Gauge(ctypes.Structure):
 
 
 class SolverOpts(ctypes.Structure):
-    _fields_ = [("inner_prec", _I), ("reliable_delta", _D), ("check_every", _I)]
+    _fields_ = [("inner_prec", _I), ("reliable_delta", _D), ("check_every", _I),
+                ("force_prec", _I)]
 
 
 class SolveStats(ctypes.Structure):
@@ -68,6 +69,8 @@ _SIGS = {
     "hmc_ctx_set_stream": (_I, [_P, _P]),
     "hmc_last_error": (ctypes.c_char_p, [_P]),
     "hmc_launch_count": (ctypes.c_longlong, [_P]),
+    "hmc_ctx_set_timing": (_I, [_P, _I]),
+    "hmc_timing_get": (_I, [_P, _I, ctypes.c_char_p, _I, _P, _P, _P]),
     "hmc_gauge_bytes": (_SZ, [_P, _I, _I]),
     "hmc_spinor_bytes": (_SZ, [_P, _I, _I]),
     "hmc_algebra_bytes": (_SZ, [_P]),
@@ -187,6 +190,24 @@ class Context:
 
     def launches(self):
         return lib().hmc_launch_count(self.h)
+
+    def set_timing(self, enable):
+        self._check(lib().hmc_ctx_set_timing(self.h, int(enable)), "hmc_ctx_set_timing")
+
+    def timing(self):
+        """{class: (launches, total_ms, algorithmic_bytes)} since timing was enabled."""
+        out = {}
+        i = 0
+        while True:
+            name = ctypes.create_string_buffer(64)
+            n, ms, b = ctypes.c_longlong(0), ctypes.c_double(0), ctypes.c_double(0)
+            st = lib().hmc_timing_get(self.h, i, name, 64, ctypes.byref(n), ctypes.byref(ms),
+                                      ctypes.byref(b))
+            if st:
+                break
+            out[name.value.decode()] = (n.value, ms.value, b.value)
+            i += 1
+        return out
 
     def _bytes(self, n):
         return self.torch.empty(int(n), dtype=self.torch.uint8, device=f"cuda:{self.device}")
@@ -309,13 +330,13 @@ class Context:
         return Filter(arr.ctypes.data, len(arr) - 1, alpha), arr
 
     def force_pf(self, L, U_hi, phi, kappa, F, coeff=1.0, tol=1e-12, U_lo=None, inner_prec=F64,
-                 b=None, alpha=0.0, reliable_delta=0.1):
+                 b=None, alpha=0.0, reliable_delta=0.1, force_prec=F64):
         """F += coeff * F_PF (plain action when b is None, else the filtered one)."""
         self._stream()
         gh = U_hi.gauge()
         gl = U_lo.gauge() if U_lo is not None else None
         flt, keep = self._filter(b, alpha)
-        opts = SolverOpts(inner_prec, reliable_delta, 16)
+        opts = SolverOpts(inner_prec, reliable_delta, 16, force_prec)
         stats = SolveStats()
         st = lib().hmc_force_pf(self.h, _ref(lattice(L)), ctypes.byref(gh),
                                 ctypes.byref(gl) if gl is not None else None, phi.ptr(), kappa,
@@ -387,14 +408,15 @@ class Context:
     def trajectory(self, L, U, P, eta, u, beta, kappa, tau, n_md, n_gauge, filter_k=0, n_t=0,
                    n_max=0, b=None, c=None, alpha=0.0, tol_md=1e-10, tol_action=1e-12,
                    inner_prec=F64, link_fmt_lo=LINK12, reliable_delta=0.1, U_end=None,
-                   P_end=None):
+                   P_end=None, force_prec=F64):
         """One HMC trajectory; U (F64/LINK18 gauge Field) is updated in place
         when accepted.  Returns the result as a dict."""
         self._stream()
         keep = []
         prm = TrajParams(beta=beta, kappa=kappa, tau=tau, n_md=n_md, n_gauge=n_gauge,
                          filter_k=filter_k, n_t=n_t, n_max=n_max, alpha=alpha, tol_md=tol_md,
-                         tol_action=tol_action, solver=SolverOpts(inner_prec, reliable_delta, 16),
+                         tol_action=tol_action,
+                         solver=SolverOpts(inner_prec, reliable_delta, 16, force_prec),
                          link_fmt_lo=link_fmt_lo)
         if b is not None:
             ab = np.ascontiguousarray(b, dtype=np.float64); keep.append(ab); prm.b = ab.ctypes.data
@@ -410,13 +432,14 @@ class Context:
 
     def md_evolve(self, L, U, P, phi, beta, kappa, tau, n_md, n_gauge, filter_k=0, n_t=0,
                   b=None, alpha=0.0, tol_md=1e-10, inner_prec=F64, link_fmt_lo=LINK12,
-                  reliable_delta=0.1):
+                  reliable_delta=0.1, force_prec=F64):
         """Molecular dynamics with phi fixed; U (F64/LINK18) and P updated in place."""
         self._stream()
         keep = []
         prm = TrajParams(beta=beta, kappa=kappa, tau=tau, n_md=n_md, n_gauge=n_gauge,
                          filter_k=filter_k, n_t=n_t, n_max=n_t, alpha=alpha, tol_md=tol_md,
-                         tol_action=tol_md, solver=SolverOpts(inner_prec, reliable_delta, 16),
+                         tol_action=tol_md,
+                         solver=SolverOpts(inner_prec, reliable_delta, 16, force_prec),
                          link_fmt_lo=link_fmt_lo)
         if b is not None:
             ab = np.ascontiguousarray(b, dtype=np.float64); keep.append(ab)

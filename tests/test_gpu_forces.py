@@ -153,3 +153,37 @@ def test_filter_coefficients_match_oracle(H):
         assert abs(alpha - ao) <= 1e-15
         assert np.allclose(b, bo, rtol=1e-13, atol=1e-300)
         assert np.allclose(c, co, rtol=1e-14, atol=0)
+
+
+def test_gauge_force_fp32(orc, ctx, H):
+    """FP32 links and arithmetic, FP64 accumulation: single-precision rounding
+    of 13 products of unit-norm matrices, <= 2e-6 of the largest component."""
+    L = (4, 6, 6, 8)
+    U = I.gauge_links(L, 0.3, 1)
+    for fmt in (18, 12):
+        F = ctx.new_algebra(L)
+        ctx.force_hopexp(L, ctx.pack_gauge(L, U, 1, fmt), BETA, KAPPA, 2, F, want_action=False)
+        want = orc.gauge_force(L, U, BETA) + orc.hopexp_force(L, U, KAPPA, 2)
+        assert _maxrel(_np(ctx.unpack_algebra(L, F)), want) <= 2e-6
+
+
+@pytest.mark.parametrize("filtered", [False, True])
+def test_pf_force_fp32_algebra(orc, ctx, H, filtered):
+    """force_prec = F32: solves still reach tol in FP64, the remaining Dslash
+    and the outer products run in FP32 (<= 2e-5 of the largest component)."""
+    L = (4, 6, 6, 8)
+    U = I.gauge_links(L, 0.3, 1)
+    phi = I.gaussian_half(L, 2)
+    Uh = ctx.pack_gauge(L, U, 0, 18)
+    Ul = ctx.pack_gauge(L, U, 1, 12)
+    F = ctx.new_algebra(L)
+    kw = {}
+    if filtered:
+        b, alpha, _ = C.filter_coeffs(2, 9)
+        kw = dict(b=b, alpha=alpha)
+        want = orc.filtered_force(L, U, KAPPA, b, alpha, phi, tol=1e-14)
+    else:
+        want = orc.pf_force(L, U, KAPPA, phi, tol=1e-14)
+    ctx.force_pf(L, Uh, ctx.pack_spinor(L, phi, 0), KAPPA, F, tol=1e-12, U_lo=Ul, inner_prec=1,
+                 force_prec=1, **kw)
+    assert _maxrel(_np(ctx.unpack_algebra(L, F)), want) <= 2e-5

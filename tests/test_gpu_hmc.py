@@ -144,3 +144,26 @@ def test_trajectory_rejected_leaves_U(ctx, H):
     if r["dH"] > 0:
         assert r["accepted"] == 0
         assert np.array_equal(_np(ctx.unpack_gauge(L, Ud)), before)
+
+
+def test_reversibility_fp32_forces(orc, ctx, H):
+    """FP32 molecular-dynamics forces are deterministic functions of U, so the
+    integrator stays reversible; only rounding differences in U between the
+    forward and backward passes can flip an FP32 rounding."""
+    L = (4, 6, 6, 8)
+    U = I.gauge_links(L, 0.3, 1)
+    P = I.momenta(L, 3)
+    eta = I.gaussian_half(L, 2)
+    kw = _traj_kw(2)
+    kw.pop("n_max", None)
+    kw.pop("c", None)
+    cc = C.heatbath_coeffs(2, 29)
+    phi = orc.mhat(L, U, KAPPA, orc.poly_K(L, U, KAPPA, cc, eta))
+    Ud = ctx.pack_gauge(L, U, 0, 18)
+    ph = ctx.pack_spinor(L, phi, 0)
+    Pd = ctx.pack_algebra(L, P)
+    ctx.md_evolve(L, Ud, Pd, ph, tol_md=1e-13, inner_prec=1, force_prec=1, **kw)
+    Pd.data.neg_()
+    ctx.md_evolve(L, Ud, Pd, ph, tol_md=1e-13, inner_prec=1, force_prec=1, **kw)
+    delta = np.sum(np.abs(_np(ctx.unpack_gauge(L, Ud)) - U) ** 2)
+    assert delta < 1e-14, delta
