@@ -50,6 +50,11 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--n-md", type=int, default=None,
+                    help="override the coarse steps (shortened trajectories for profiling)")
+    ap.add_argument("--timeline", action="store_true",
+                    help="after the timed steps, run one more trajectory with a per-launch "
+                         "event timeline and report its per-kernel shares")
     ap.add_argument("--inner", default="f32", choices=["f16", "f32"])
     ap.add_argument("--delta", type=float, default=1e-5, help="reliable-update threshold")
     ap.add_argument("--force-prec", default="f32", choices=["f32", "f64"])
@@ -223,7 +228,11 @@ def run_hmc(args):
     ed = ctx.pack_spinor(LAT, eta, hmc.F64)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     fprec = hmc.F32 if args.force_prec == "f32" else hmc.F64
-    kw = dict(WORK, b=b, c=c, alpha=alpha, inner_prec=inner, link_fmt_lo=hmc.LINK12,
+    work = dict(WORK)
+    if args.n_md:
+        work["tau"] = WORK["tau"] * args.n_md / WORK["n_md"]
+        work["n_md"] = args.n_md
+    kw = dict(work, b=b, c=c, alpha=alpha, inner_prec=inner, link_fmt_lo=hmc.LINK12,
               reliable_delta=args.delta, force_prec=fprec)
     stream = torch.cuda.current_stream()
 
@@ -289,7 +298,7 @@ def run_hmc(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.inner,
         "data": "synthetic (seeded exp(i 0.3 A) links, Gaussian momenta and sources)",
         "config": {"workload": "hmc-trajectory 24^3x48 kappa=0.1575 beta=5.6 kappa^4-filter",
-                   "lattice": "x".join(str(v) for v in LAT[::-1]), **{k: v for k, v in WORK.items()},
+                   "lattice": "x".join(str(v) for v in LAT[::-1]), **{k: v for k, v in work.items()},
                    "inner_prec": args.inner, "reliable_delta": args.delta,
                    "force_prec": args.force_prec, "links": "12-real (inner), 18-real FP64",
                    "l2": "flushed between timed steps (256 MB write)",
@@ -304,6 +313,16 @@ def run_hmc(args):
     }
     if clk:
         out["clocks"] = clk
+    # ---- per-kernel shares of one trajectory (launch timeline) ----------------------
+    if args.timeline:
+        ctx.set_timing(2)
+        one(kw)
+        tl = ctx.timing()
+        ctx.set_timing(0)
+        tot = sum(v[1] for v in tl.values())
+        out["timeline"] = {k: {"launches": v[0], "ms": round(v[1], 2),
+                               "share": round(v[1] / tot, 4)}
+                           for k, v in sorted(tl.items(), key=lambda kv: -kv[1][1])}
     # ---- plain FP64 GPU path, same trajectory ----------------------------------
     if not args.no_fp64:
         kw64 = dict(kw, inner_prec=hmc.F64, force_prec=hmc.F64)

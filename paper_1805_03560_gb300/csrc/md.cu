@@ -47,13 +47,22 @@ __device__ __forceinline__ void mm(const C a[9], const C b[9], C c[9]) {
 // scalar series is summed until its terms fall below 2^-60 of the leading
 // coefficient; matrices of norm above 1 are first scaled by a power of two and
 // squared back.  Cost: one 3x3 product for A^2 (plus one per squaring).
+// 1/n for the series terms (FP64 division is a long instruction sequence)
+__constant__ double c_inv[41] = {
+    0.0,        1.0,        1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,  1.0 / 7,  1.0 / 8,
+    1.0 / 9,    1.0 / 10,   1.0 / 11, 1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15, 1.0 / 16, 1.0 / 17,
+    1.0 / 18,   1.0 / 19,   1.0 / 20, 1.0 / 21, 1.0 / 22, 1.0 / 23, 1.0 / 24, 1.0 / 25, 1.0 / 26,
+    1.0 / 27,   1.0 / 28,   1.0 / 29, 1.0 / 30, 1.0 / 31, 1.0 / 32, 1.0 / 33, 1.0 / 34, 1.0 / 35,
+    1.0 / 36,   1.0 / 37,   1.0 / 38, 1.0 / 39, 1.0 / 40};
+
 __device__ __forceinline__ void expm_su3(const C A[9], C E[9]) {
+  // row-sum norm with |re| + |im| >= |z| per entry: an upper bound, no sqrt
   double nrm = 0.0;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     double r = 0.0;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) r += sqrt(norm2(A[i * 3 + j]));
+    for (int j = 0; j < 3; ++j) r += fabs(A[i * 3 + j].re) + fabs(A[i * 3 + j].im);
     nrm = fmax(nrm, r);
   }
   int sq = 0;
@@ -73,7 +82,7 @@ __device__ __forceinline__ void expm_su3(const C A[9], C E[9]) {
   C f0 = ta, f1 = tb, f2 = tc;
 #pragma unroll 1
   for (int n = 0; n < 40; ++n) {
-    const double inv = 1.0 / (n + 1);
+    const double inv = c_inv[n + 1];
     const C na = inv * (tc * d), nb = inv * (ta + tc * s), nc = inv * tb;
     ta = na;
     tb = nb;
@@ -103,7 +112,7 @@ __device__ __forceinline__ void expm_su3(const C A[9], C E[9]) {
 
 __device__ __forceinline__ void reunitarise(C u[9]) {
   double n0 = norm2(u[0]) + norm2(u[1]) + norm2(u[2]);
-  n0 = 1.0 / sqrt(n0);
+  n0 = rsqrt(n0);
 #pragma unroll
   for (int j = 0; j < 3; ++j) u[j] = n0 * u[j];
   C d = cjmul(u[0], u[3]);
@@ -112,7 +121,7 @@ __device__ __forceinline__ void reunitarise(C u[9]) {
 #pragma unroll
   for (int j = 0; j < 3; ++j) u[3 + j] = u[3 + j] - d * u[j];
   double n1 = norm2(u[3]) + norm2(u[4]) + norm2(u[5]);
-  n1 = 1.0 / sqrt(n1);
+  n1 = rsqrt(n1);
 #pragma unroll
   for (int j = 0; j < 3; ++j) u[3 + j] = n1 * u[3 + j];
   reconstruct_row2(u);
