@@ -163,6 +163,27 @@ int hmc_mhat(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U,
              void *out, const void *in, double kappa, int dagger, int prec,
              int n_rhs, const double *kappas);
 
+/* hmc_mhat_noalloc: the same operator as hmc_mhat (one kappa for every
+ * right-hand side), for callers that cannot allocate device memory: code whose
+ * device memory is reserved up front by its own allocator, or latency-critical
+ * loops that must not call cudaMalloc / cudaFree, which can synchronise the
+ * device.  (A service of this library; the paper has no counterpart.)
+ * hmc_mhat keeps its odd intermediate in context workspace, allocated on first
+ * use; this call keeps it in a file-scope device array of
+ * HMC_MHAT_NOALLOC_MAX_BYTES, which every GPU that loads the library holds
+ * until the process exits.  It allocates nothing and frees nothing.
+ * The intermediate needs hmc_spinor_bytes(lat, prec, n_rhs) bytes; larger
+ * requests return HMC_EINVAL.  The first call on a device looks up the array's
+ * device address (with that device current); make that first call before any
+ * stream capture.  Every call shares the one array and overwrites it
+ * completely before reading it, so nothing needs clearing, but calls that
+ * overlap on the GPU (other streams, other host threads) race on it.  The
+ * context's optional event timing is bypassed for this call. */
+#define HMC_MHAT_NOALLOC_MAX_BYTES ((size_t)64 << 20)
+int hmc_mhat_noalloc(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U,
+                     void *out, const void *in, double kappa, int dagger, int prec,
+                     int n_rhs);
+
 /* ---- solver ------------------------------------------------------------------- */
 
 typedef struct {

@@ -82,6 +82,7 @@ _SIGS = {
     "hmc_unpack_algebra": (_I, [_P, _P, _P, _P]),
     "hmc_dslash": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _I]),
     "hmc_mhat": (_I, [_P, _P, _P, _P, _P, _D, _I, _I, _I, _P]),
+    "hmc_mhat_noalloc": (_I, [_P, _P, _P, _P, _P, _D, _I, _I, _I]),
     "hmc_cg_solve": (_I, [_P, _P, _P, _P, _P, _P, _D, _D, _I, _P, _P]),
     "hmc_force_pf": (_I, [_P, _P, _P, _P, _P, _D, _P, _D, _P, _D, _P, _P]),
     "hmc_action_pf": (_I, [_P, _P, _P, _P, _P, _D, _P, _D, _P, _P, _P]),
