@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--kernel", default=None,
                     help="time one hemi-Dslash variant alone, e.g. f16-12 (for profiling)")
     ap.add_argument("--launches", type=int, default=20)
+    ap.add_argument("--variant", type=int, default=None, help="hemi-Dslash kernel variant 0..3")
     return ap.parse_args()
 
 
@@ -72,9 +73,36 @@ def run_kernel(args):
     from paper_1805_03560_gb300 import hmc
     from paper_1805_03560_gb300 import inputs as I
     pname, fmt = args.kernel.split("-")
+    ctx = hmc.Context(0)
+    if args.variant is not None:
+        ctx.set_dslash_variant(args.variant)
+    if pname == "cg":
+        # one CG solve of Mhat^dag Mhat on the benchmark lattice to 1e-10 with the
+        # given inner precision (FP64 reliable updates), all Dslash classes timed
+        inner = {"f64": hmc.F64, "f32": hmc.F32, "f16": hmc.F16}[fmt]
+        Ulat = I.gauge_links(LAT, EPS_LINKS, 1)
+        Uh = ctx.pack_gauge(LAT, Ulat, hmc.F64, hmc.LINK18)
+        Ul = ctx.pack_gauge(LAT, Ulat, inner, hmc.LINK12) if inner != hmc.F64 else None
+        b = ctx.pack_spinor(LAT, I.gaussian_half(LAT, 2), hmc.F64)
+        x = ctx.new_spinor(LAT, hmc.F64)
+        ctx.cg_solve(LAT, Uh, x, b, WORK["kappa"], 1e-10, U_lo=Ul, inner_prec=inner,
+                     reliable_delta=args.delta)
+        torch.cuda.synchronize()
+        ctx.set_timing(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = ctx.cg_solve(LAT, Uh, x, b, WORK["kappa"], 1e-10, U_lo=Ul, inner_prec=inner,
+                         reliable_delta=args.delta)
+        e1.record()
+        torch.cuda.synchronize()
+        st = ctx.timing()
+        print(json.dumps({"kernel": args.kernel, "solve_ms": round(e0.elapsed_time(e1), 3), **r,
+                          "classes": {k: {"launches": v[0], "us": round(v[1] / v[0] * 1e3, 2),
+                                          "GBs": round(v[2] / (v[1] * 1e-3) / 1e9, 1)}
+                                      for k, v in st.items()}}), flush=True)
+        return
     prec = {"f64": hmc.F64, "f32": hmc.F32, "f16": hmc.F16}[pname]
     fmt = int(fmt)
-    ctx = hmc.Context(0)
     U = ctx.pack_gauge(LAT, I.gauge_links(LAT, EPS_LINKS, 1), prec, fmt)
     srcs = [ctx.pack_spinor(LAT, I.gaussian_half(LAT, 2 + i), prec) for i in range(2)]
     out = ctx.new_spinor(LAT, prec)
@@ -87,7 +115,8 @@ def run_kernel(args):
     torch.cuda.synchronize()
     n, ms, byt = next(iter(ctx.timing().values()))
     Vh = int(np.prod(LAT)) // 2
-    print(json.dumps({"kernel": args.kernel, "launches": n, "us_per_launch": round(ms / n * 1e3, 2),
+    print(json.dumps({"kernel": args.kernel, "variant": args.variant,
+                      "launches": n, "us_per_launch": round(ms / n * 1e3, 2),
                       "GBs": round(byt / (ms * 1e-3) / 1e9, 1),
                       "TFLOPs": round(1320.0 * Vh * n / (ms * 1e-3) / 1e12, 3)}), flush=True)
 
@@ -116,8 +145,12 @@ def ncu_traffic(kclass):
     m = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
     if not m or m.group(1) != dslash_source_hash():
         return None
-    m = re.search(re.escape(kclass.split("/")[0]) + r"\s+traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    return float(m.group(1)) if m else None
+    for name in (kclass, kclass.split("/")[0]):
+        m = re.search(r"^" + re.escape(name) + r"\s+traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt,
+                      re.M)
+        if m:
+            return float(m.group(1))
+    return None
 
 
 class Clocks:

@@ -111,6 +111,15 @@ long long hmc_launch_count(hmc_ctx *ctx);
  * event (kernel time plus any idle gap before it) is charged to the launch.
  * Mode 0 switches timing off.  Any call clears the statistics. */
 int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
+/* Tuning options.  HMC_OPT_DSLASH_VARIANT selects the hemi-Dslash kernel
+ * variant: bit 0 maps each block of 128 threads onto four 32-site segments
+ * at the offsets {0, +x, +t, +x+t} (when Ly*Lz/2 is a multiple of 32 and
+ * n_rhs == 1; otherwise consecutive sites), bit 1 issues the loads of both
+ * hops of a direction before their arithmetic.  Every variant computes the
+ * same result bit for bit.  Default -1: paired loads for LINK18 only (the
+ * fastest choice measured on 24^3 x 48). */
+#define HMC_OPT_DSLASH_VARIANT 1
+int hmc_ctx_set_option(hmc_ctx *ctx, int option, int value);
 /* Statistics of the index-th kernel class seen since timing was enabled:
  * class name (e.g. "dslash_f16_12/cg"), launches, summed event time in ms and
  * summed algorithmic bytes.  Synchronises the stream.  HMC_EINVAL past the

@@ -245,6 +245,18 @@ int hmc_ctx_set_timing(hmc_ctx *ctx, int enable) {
   return HMC_OK;
 }
 
+int hmc_ctx_set_option(hmc_ctx *ctx, int option, int value) {
+  CTX_CHECK(ctx);
+  switch (option) {
+    case HMC_OPT_DSLASH_VARIANT:
+      if (value < -1 || value > 3) return fail(ctx, HMC_EINVAL, "dslash variant must be -1..3");
+      ctx->ds_variant = value;
+      return HMC_OK;
+    default:
+      return fail(ctx, HMC_EINVAL, "unknown option %d", option);
+  }
+}
+
 int hmc_timing_get(hmc_ctx *ctx, int index, char *name, int name_len, long long *launches,
                    double *total_ms, double *bytes) {
   CTX_CHECK(ctx);

@@ -129,14 +129,60 @@ __device__ __forceinline__ void hop_bwd(const DslashArgs &a, int r, int lex, con
   accumulate<MU, S>(acc, w);
 }
 
-template <int SP, int FMT, bool DAG>
+// Both hops of direction mu with all four loads (two spinors, two links)
+// issued before any arithmetic, doubling the loads in flight per thread.
+template <int SP, int FMT, int MU, int S>
+__device__ __forceinline__ void hop_pair(const DslashArgs &a, int h, int r, int lex,
+                                         const int c[4], Cx<typename SpinorIO<SP>::R> acc[12]) {
+  using SIO = SpinorIO<SP>;
+  using R = typename SIO::R;
+  using LIO = LinkIO<SP, FMT>;
+  const int Vh = a.g.Vh, S_ = Vh * a.n_rhs;
+  const int hf = nb_fwd(a.g, lex, c, MU), hb = nb_bwd(a.g, lex, c, MU);
+  Cx<R> pf[12], pb[12], uf[9], ub[9], hs[6], w[6];
+  SIO::load(a.in, S_, hf * a.n_rhs + r, pf);
+  LIO::load(link_base<SP, FMT>(a.gauge, Vh, a.p, MU), Vh, h, uf);
+  SIO::load(a.in, S_, hb * a.n_rhs + r, pb);
+  LIO::load(link_base<SP, FMT>(a.gauge, Vh, 1 - a.p, MU), Vh, hb, ub);
+  project<MU, S>(pf, hs);
+  if (MU == 0 && c[0] == a.g.L[0] - 1) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) hs[k] = -hs[k];
+  }
+  mul_link(uf, hs, w);
+  accumulate<MU, S>(acc, w);
+  project<MU, -S>(pb, hs);
+  if (MU == 0 && c[0] == 0) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) hs[k] = -hs[k];
+  }
+  mul_link_dag(ub, hs, w);
+  accumulate<MU, -S>(acc, w);
+}
+
+// Site of this thread.  Linear: consecutive threads take consecutive sites.
+// Tiled (a.tile_nseg > 0, one right-hand side): the four warps of a block take
+// 32 consecutive sites each at the offsets {0, +x, +t, +x+t}, so half of the
+// x and t neighbours a block reads are its own sites and can hit in L1.
+__device__ __forceinline__ int dslash_site(const DslashArgs &a) {
+  if (a.tile_nseg == 0) return blockIdx.x * DS_NT + threadIdx.x;
+  const int sx = a.g.L[2] * a.g.Lzh, st = a.g.L[1] * sx;
+  const int b = blockIdx.x;
+  const int seg = b % a.tile_nseg, xt = b / a.tile_nseg;
+  const int hx = a.g.L[1] >> 1;
+  const int xp = xt % hx, tp = xt / hx;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  return seg * 32 + lane + (2 * xp + (w & 1)) * sx + (2 * tp + (w >> 1)) * st;
+}
+
+template <int SP, int FMT, bool DAG, bool PAIR>
 __global__ void __launch_bounds__(DS_NT) k_dslash(const DslashArgs a) {
   using SIO = SpinorIO<SP>;
   using R = typename SIO::R;
   constexpr int SF = DAG ? -1 : 1;  // forwards: 1 - gamma (1 + gamma for the adjoint)
   if (a.gate && *a.gate == 0) return;
   const int S_ = a.g.Vh * a.n_rhs;
-  const int i = blockIdx.x * DS_NT + threadIdx.x;
+  const int i = dslash_site(a);
   double nrm = 0.0;
   if (i < S_) {
     const int h = a.n_rhs == 1 ? i : i / a.n_rhs;
@@ -146,14 +192,21 @@ __global__ void __launch_bounds__(DS_NT) k_dslash(const DslashArgs a) {
     Cx<R> acc[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = {R(0), R(0)};
-    hop_fwd<SP, FMT, 0, SF>(a, h, r, lex, c, acc);
-    hop_bwd<SP, FMT, 0, -SF>(a, r, lex, c, acc);
-    hop_fwd<SP, FMT, 1, SF>(a, h, r, lex, c, acc);
-    hop_bwd<SP, FMT, 1, -SF>(a, r, lex, c, acc);
-    hop_fwd<SP, FMT, 2, SF>(a, h, r, lex, c, acc);
-    hop_bwd<SP, FMT, 2, -SF>(a, r, lex, c, acc);
-    hop_fwd<SP, FMT, 3, SF>(a, h, r, lex, c, acc);
-    hop_bwd<SP, FMT, 3, -SF>(a, r, lex, c, acc);
+    if (PAIR) {
+      hop_pair<SP, FMT, 0, SF>(a, h, r, lex, c, acc);
+      hop_pair<SP, FMT, 1, SF>(a, h, r, lex, c, acc);
+      hop_pair<SP, FMT, 2, SF>(a, h, r, lex, c, acc);
+      hop_pair<SP, FMT, 3, SF>(a, h, r, lex, c, acc);
+    } else {
+      hop_fwd<SP, FMT, 0, SF>(a, h, r, lex, c, acc);
+      hop_bwd<SP, FMT, 0, -SF>(a, r, lex, c, acc);
+      hop_fwd<SP, FMT, 1, SF>(a, h, r, lex, c, acc);
+      hop_bwd<SP, FMT, 1, -SF>(a, r, lex, c, acc);
+      hop_fwd<SP, FMT, 2, SF>(a, h, r, lex, c, acc);
+      hop_bwd<SP, FMT, 2, -SF>(a, r, lex, c, acc);
+      hop_fwd<SP, FMT, 3, SF>(a, h, r, lex, c, acc);
+      hop_bwd<SP, FMT, 3, -SF>(a, r, lex, c, acc);
+    }
     const R cb = (R)(a.cb_rhs ? a.cb_rhs[r] : a.cb);
     if (a.x) {
       Cx<R> xv[12];
@@ -181,11 +234,18 @@ __global__ void __launch_bounds__(DS_NT) k_dslash(const DslashArgs a) {
 }
 
 template <int SP, int FMT>
-static void launch_sf(const DslashArgs &a, int dagger, int nb, cudaStream_t st) {
-  if (dagger)
-    k_dslash<SP, FMT, true><<<nb, DS_NT, 0, st>>>(a);
-  else
-    k_dslash<SP, FMT, false><<<nb, DS_NT, 0, st>>>(a);
+static void launch_sf(const DslashArgs &a, int dagger, bool pair, int nb, cudaStream_t st) {
+  if (pair) {
+    if (dagger)
+      k_dslash<SP, FMT, true, true><<<nb, DS_NT, 0, st>>>(a);
+    else
+      k_dslash<SP, FMT, false, true><<<nb, DS_NT, 0, st>>>(a);
+  } else {
+    if (dagger)
+      k_dslash<SP, FMT, true, false><<<nb, DS_NT, 0, st>>>(a);
+    else
+      k_dslash<SP, FMT, false, false><<<nb, DS_NT, 0, st>>>(a);
+  }
 }
 
 int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int dagger,
@@ -207,14 +267,25 @@ int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int
   snprintf(cls, sizeof(cls), "dslash_%s_%d%s%s",
            sprec == HMC_F64 ? "f64" : (sprec == HMC_F32 ? "f32" : "f16"), U.fmt, a.tag ? "/" : "",
            a.tag ? a.tag : "");
+  // kernel variant (hmc_ctx_set_option): bit 0 tiled site mapping, bit 1
+  // paired loads
+  // (default, -1: paired loads for 18-real links only; measured on 24^3 x 48,
+  // pairing helps the 18-real kernels and slows the 12-real ones, tiling
+  // helps neither)
+  DslashArgs aa = a;
+  aa.tile_nseg = 0;
+  const int var = ctx->ds_variant >= 0 ? ctx->ds_variant : (U.fmt == 18 ? 2 : 0);
+  const int sx = a.g.L[2] * a.g.Lzh;
+  if ((var & 1) && a.n_rhs == 1 && sx % 32 == 0) aa.tile_nseg = sx / 32;
+  const bool pair = (var & 2) != 0;
   TimedLaunch timer(ctx, cls, bytes);
   switch (sprec * 100 + U.fmt) {
-    case HMC_F64 * 100 + 18: launch_sf<HMC_F64, 18>(a, dagger, nb, st); break;
-    case HMC_F64 * 100 + 12: launch_sf<HMC_F64, 12>(a, dagger, nb, st); break;
-    case HMC_F32 * 100 + 18: launch_sf<HMC_F32, 18>(a, dagger, nb, st); break;
-    case HMC_F32 * 100 + 12: launch_sf<HMC_F32, 12>(a, dagger, nb, st); break;
-    case HMC_F16 * 100 + 18: launch_sf<HMC_F16, 18>(a, dagger, nb, st); break;
-    case HMC_F16 * 100 + 12: launch_sf<HMC_F16, 12>(a, dagger, nb, st); break;
+    case HMC_F64 * 100 + 18: launch_sf<HMC_F64, 18>(aa, dagger, pair, nb, st); break;
+    case HMC_F64 * 100 + 12: launch_sf<HMC_F64, 12>(aa, dagger, pair, nb, st); break;
+    case HMC_F32 * 100 + 18: launch_sf<HMC_F32, 18>(aa, dagger, pair, nb, st); break;
+    case HMC_F32 * 100 + 12: launch_sf<HMC_F32, 12>(aa, dagger, pair, nb, st); break;
+    case HMC_F16 * 100 + 18: launch_sf<HMC_F16, 18>(aa, dagger, pair, nb, st); break;
+    case HMC_F16 * 100 + 12: launch_sf<HMC_F16, 12>(aa, dagger, pair, nb, st); break;
     default:
       return fail(ctx, HMC_EINVAL, "dslash: unsupported precision %d / link format %d", sprec,
                   U.fmt);

@@ -25,6 +25,9 @@ struct hmc_ctx {
   // the time since the previous event to that launch (a launch timeline).
   int timing = 0;
   cudaEvent_t trace_prev = nullptr;
+  // hemi-Dslash kernel variant: bit 0 tiled site mapping, bit 1 paired loads;
+  // -1 chooses per link format
+  int ds_variant = -1;
   struct Pending {
     cudaEvent_t a, b;
     int cls;
@@ -96,6 +99,7 @@ struct DslashArgs {
   double *partials;
   const int *gate;  // device flag (nullable): the launch does nothing when *gate == 0
   const char *tag;  // timing class suffix (nullable)
+  int tile_nseg;    // set by the launcher: 32-site segments per (x, t) plane, 0 = linear
 };
 int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int dagger,
            int *nblocks);

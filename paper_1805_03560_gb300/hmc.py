@@ -70,6 +70,7 @@ _SIGS = {
     "hmc_last_error": (ctypes.c_char_p, [_P]),
     "hmc_launch_count": (ctypes.c_longlong, [_P]),
     "hmc_ctx_set_timing": (_I, [_P, _I]),
+    "hmc_ctx_set_option": (_I, [_P, _I, _I]),
     "hmc_timing_get": (_I, [_P, _I, ctypes.c_char_p, _I, _P, _P, _P]),
     "hmc_gauge_bytes": (_SZ, [_P, _I, _I]),
     "hmc_spinor_bytes": (_SZ, [_P, _I, _I]),
@@ -191,6 +192,9 @@ class Context:
 
     def launches(self):
         return lib().hmc_launch_count(self.h)
+
+    def set_dslash_variant(self, v):
+        self._check(lib().hmc_ctx_set_option(self.h, 1, int(v)), "hmc_ctx_set_option")
 
     def set_timing(self, enable):
         self._check(lib().hmc_ctx_set_timing(self.h, int(enable)), "hmc_ctx_set_timing")
