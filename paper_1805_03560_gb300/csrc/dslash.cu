@@ -223,13 +223,18 @@ __global__ void __launch_bounds__(DS_NT) k_dslash(const DslashArgs a) {
     }
     SIO::store(a.out, S_, i, acc);
     if (a.partials) {
+      // per-site sum in the arithmetic precision (FP64 adds are scarce on
+      // this GPU), cross-site sums in double
+      R n2 = R(0);
 #pragma unroll
-      for (int k = 0; k < 12; ++k) nrm += (double)norm2(acc[k]);
+      for (int k = 0; k < 12; ++k) n2 += norm2(acc[k]);
+      nrm = (double)n2;
     }
   }
   if (a.partials) {
     double s = block_sum<DS_NT>(nrm);
     if (threadIdx.x == 0) a.partials[blockIdx.x] = s;
+    if (a.total) last_block_total<DS_NT>(a.partials, a.counter, a.total);
   }
 }
 

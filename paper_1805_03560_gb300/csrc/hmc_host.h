@@ -100,6 +100,10 @@ struct DslashArgs {
   const int *gate;  // device flag (nullable): the launch does nothing when *gate == 0
   const char *tag;  // timing class suffix (nullable)
   int tile_nseg;    // set by the launcher: 32-site segments per (x, t) plane, 0 = linear
+  // with partials: the last block also sums them into *total (counter: a
+  // zeroed device int, returned to zero)
+  double *total;
+  unsigned int *counter;
 };
 int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int dagger,
            int *nblocks);

@@ -379,4 +379,27 @@ __device__ __forceinline__ double block_sum(double v) {
   return s;
 }
 
+// Called by every thread of every block after thread 0 of the block has
+// stored its partial sum in partials[blockIdx.x]: the last block to arrive
+// sums all partials in index order (the same order whichever block is last,
+// so the result is deterministic) into *total and resets *counter to 0.
+template <int NT>
+__device__ __forceinline__ void last_block_total(const double *partials, unsigned int *counter,
+                                                 double *total) {
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double s = 0.0;
+  for (unsigned int i = threadIdx.x; i < gridDim.x; i += NT) s += __ldcg(partials + i);
+  s = block_sum<NT>(s);
+  if (threadIdx.x == 0) {
+    *total = s;
+    *counter = 0u;
+  }
+}
+
 }  // namespace hmc

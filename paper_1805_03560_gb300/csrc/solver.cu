@@ -33,13 +33,15 @@
 namespace hmc {
 
 struct CGState {
-  double rr[2];  // |r|^2 at the start of iteration k is rr[k & 1]
+  double rr[2];   // |r|^2 at the start of iteration k is rr[k & 1]
   double b2, tol2;
-  double aux;    // scratch for one-off reductions
-  int done;      // 1 converged (recursive residual), 2 NaN/Inf
-  int active;    // !done
+  double aux;     // scratch for one-off reductions
+  double pap;     // p^dag A p of the current iteration (last block of the Mhat Dslash)
+  double rr_next; // |r|^2 after the update (last block of axpy)
+  int done;       // 1 converged (recursive residual), 2 NaN/Inf
+  int active;     // !done
   int iter;
-  int pad;
+  unsigned int cnt[2];  // arrival counters of the two last-block reductions
 };
 
 // ---- generic per-site helpers ------------------------------------------------
@@ -158,23 +160,17 @@ __global__ void __launch_bounds__(BL_NT) k_dot(const void *x, const void *y, int
 
 // ---- CG iteration kernels --------------------------------------------------------------
 
-// alpha = rr[par] / sum(pap_part);  x += alpha p;  r -= alpha Ap;  |r|^2 partials.
-// x in PX, the rest in PL.
+// alpha = rr[par] / pap;  x += alpha p;  r -= alpha Ap;  rr_next = |r|^2
+// (block partials, summed by the last block).  x in PX, the rest in PL.
 template <int PX, int PL>
 __global__ void __launch_bounds__(BL_NT) k_cg_axpy(void *x, void *r, const void *p, const void *Ap,
-                                                   int S, CGState *st, const double *pap_part,
-                                                   int n_pap, int par, double *partials) {
+                                                   int S, CGState *st, int par, double *partials) {
   if (!st->active) return;
   using R = RT<PL>;
-  __shared__ double s_alpha;
-  const double pap = block_sum_of<BL_NT>(pap_part, n_pap);
-  if (threadIdx.x == 0) {
-    const double a = st->rr[par] / pap;
-    s_alpha = a;
-    if (blockIdx.x == 0 && (!isfinite(a) || !(pap > 0.0))) st->done = 2;
-  }
-  __syncthreads();
-  const R alpha = (R)s_alpha;
+  const double pap = st->pap;
+  const double ad = st->rr[par] / pap;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (!isfinite(ad) || !(pap > 0.0))) st->done = 2;
+  const R alpha = (R)ad;
   int i = blockIdx.x * BL_NT + threadIdx.x;
   double s = 0.0;
   if (i < S) {
@@ -195,40 +191,39 @@ __global__ void __launch_bounds__(BL_NT) k_cg_axpy(void *x, void *r, const void 
       v[k].im = fma(-alpha, pv[k].im, v[k].im);
     }
     // norm of the updated residual from registers (reading it back through
-    // the read-only data path would return the value from before the store)
+    // the read-only data path would return the value from before the store);
+    // per-site sum in the field's arithmetic precision, cross-site in double
+    R n2 = R(0);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) s += (double)norm2(v[k]);
+    for (int k = 0; k < 12; ++k) n2 += norm2(v[k]);
+    s = (double)n2;
     store_as<PL>(r, S, i, v);
   }
   s = block_sum<BL_NT>(s);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  last_block_total<BL_NT>(partials, &st->cnt[1], &st->rr_next);
 }
 
-// beta = sum(rr_part) / rr[par];  p = r + beta p;  rr[par ^ 1] = new |r|^2.
+// beta = rr_next / rr[par];  p = r + beta p;  rr[par ^ 1] = rr_next.
 template <int PL>
 __global__ void __launch_bounds__(BL_NT) k_cg_xpay(void *p, const void *r, int S, CGState *st,
-                                                   const double *rr_part, int n_rr, int par,
-                                                   int plain) {
+                                                   int par, int plain) {
   if (!st->active) return;
   using R = RT<PL>;
-  __shared__ double s_beta;
-  const double rr_new = block_sum_of<BL_NT>(rr_part, n_rr);
-  if (threadIdx.x == 0) {
-    s_beta = rr_new / st->rr[par];
-    if (blockIdx.x == 0) {
-      st->rr[par ^ 1] = rr_new;
-      st->iter += 1;
-      if (!isfinite(rr_new) || st->done == 2) {
-        st->done = 2;
-        st->active = 0;
-      } else if (plain && rr_new <= st->tol2 * st->b2) {
-        st->done = 1;
-        st->active = 0;
-      }
+  const double rr_new = st->rr_next;
+  __syncthreads();  // every thread has read the scalars before block 0 updates the state
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->rr[par ^ 1] = rr_new;
+    st->iter += 1;
+    if (!isfinite(rr_new) || st->done == 2) {
+      st->done = 2;
+      st->active = 0;
+    } else if (plain && rr_new <= st->tol2 * st->b2) {
+      st->done = 1;
+      st->active = 0;
     }
   }
-  __syncthreads();
-  const R beta = (R)s_beta;
+  const R beta = (R)(rr_new / st->rr[par]);
   int i = blockIdx.x * BL_NT + threadIdx.x;
   if (i >= S) return;
   Cx<R> rv[12], pv[12];
@@ -291,6 +286,8 @@ __global__ void __launch_bounds__(FIN_NT) k_cg_init(CGState *st, const double *p
     st->b2 = s;
     st->tol2 = tol2;
     st->aux = 0.0;
+    st->pap = st->rr_next = 0.0;
+    st->cnt[0] = st->cnt[1] = 0u;
     st->iter = 0;
     st->done = (s == 0.0) ? 1 : (isfinite(s) ? 0 : 2);
     st->active = st->done == 0;
@@ -411,17 +408,17 @@ int apply_A64(Solve &s, const void *in, void *out) {
 template <int PL>
 void launch_axpy(Solve &s, void *x, int px, int par) {
   if (px == HMC_F64)
-    k_cg_axpy<HMC_F64, PL><<<s.nb_bl, BL_NT, 0, s.ctx->stream>>>(
-        x, s.rlo, s.p, s.Ap, s.S, s.st, s.pap_part, s.nb_ds, par, s.rr_part);
+    k_cg_axpy<HMC_F64, PL><<<s.nb_bl, BL_NT, 0, s.ctx->stream>>>(x, s.rlo, s.p, s.Ap, s.S, s.st,
+                                                                 par, s.rr_part);
   else
-    k_cg_axpy<HMC_F32, PL><<<s.nb_bl, BL_NT, 0, s.ctx->stream>>>(
-        x, s.rlo, s.p, s.Ap, s.S, s.st, s.pap_part, s.nb_ds, par, s.rr_part);
+    k_cg_axpy<HMC_F32, PL><<<s.nb_bl, BL_NT, 0, s.ctx->stream>>>(x, s.rlo, s.p, s.Ap, s.S, s.st,
+                                                                 par, s.rr_part);
 }
 
 template <int PL>
 void launch_xpay(Solve &s, int par) {
-  k_cg_xpay<PL><<<s.nb_bl, BL_NT, 0, s.ctx->stream>>>(s.p, s.rlo, s.S, s.st, s.rr_part, s.nb_bl,
-                                                      par, s.plo == HMC_F64 ? 1 : 0);
+  k_cg_xpay<PL><<<s.nb_bl, BL_NT, 0, s.ctx->stream>>>(s.p, s.rlo, s.S, s.st, par,
+                                                      s.plo == HMC_F64 ? 1 : 0);
 }
 
 int one_iteration(Solve &s, int k) {
@@ -440,8 +437,12 @@ int one_iteration(Solve &s, int k) {
   TRY(dslash(ctx, a, U, s.plo, 0, nullptr));
   a.p = 0; a.out = s.y; a.in = s.tlo; a.x = s.p; a.ca = 1.0; a.cb = -s.kappa * s.kappa;
   a.partials = s.pap_part;
+  a.total = &s.st->pap;
+  a.counter = &s.st->cnt[0];
   TRY(dslash(ctx, a, U, s.plo, 0, nullptr));
   a.partials = nullptr;
+  a.total = nullptr;
+  a.counter = nullptr;
   a.p = 1; a.out = s.tlo; a.in = s.y; a.x = nullptr; a.ca = 0.0; a.cb = 1.0;
   TRY(dslash(ctx, a, U, s.plo, 1, nullptr));
   a.p = 0; a.out = s.Ap; a.in = s.tlo; a.x = s.y; a.ca = 1.0; a.cb = -s.kappa * s.kappa;

@@ -467,8 +467,8 @@ int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj
     return convert_gauge(ctx, g, U1, Ulo, plo, fmt_lo);
   };
   const int k = prm->filter_k;
-  hmc_filter fmd{prm->b, prm->n_t, prm->alpha}, fact{prm->b, prm->n_max, prm->alpha};
-  const hmc_filter *filt_md = k ? &fmd : nullptr, *filt_act = k ? &fact : nullptr;
+  hmc_filter fact{prm->b, prm->n_max, prm->alpha};
+  const hmc_filter *filt_act = k ? &fact : nullptr;
   hmc_solve_stats acc{};
   // heatbath of the pseudo-fermion field and H0
   double kin0, sg0, spf0;
@@ -488,7 +488,6 @@ int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj
   TRY(gauge_action(ctx, g, Uh, prm->beta, prm->kappa, k, &sg0, &ps0));
   res->plaq0 = ps0 / (18.0 * 2.0 * g.Vh);
   res->H0 = kin0 + sg0 + spf0;
-  (void)filt_md;
   TRY(md_evolve(ctx, g, U1, Ulo, P, F, phi, prm, &res->solves, &acc));
   // H1 with the action solves
   double kin1, sg1, spf1, ps1;
