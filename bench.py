@@ -72,10 +72,40 @@ def run_kernel(args):
     import torch
     from paper_1805_03560_gb300 import hmc
     from paper_1805_03560_gb300 import inputs as I
-    pname, fmt = args.kernel.split("-")
+    parts = args.kernel.split("-")
+    pname, fmt = parts[0], parts[1]
     ctx = hmc.Context(0)
     if args.variant is not None:
         ctx.set_dslash_variant(args.variant)
+    if pname == "cgm":
+        # batched solve of n systems (kappas of mass-preconditioned
+        # pseudo-fermions) on the benchmark lattice, links shared per launch
+        inner = {"f64": hmc.F64, "f32": hmc.F32, "f16": hmc.F16}[fmt]
+        n = int(parts[2])
+        ks = ([0.150, 0.154, 0.1575] * 6)[:n]
+        Ulat = I.gauge_links(LAT, EPS_LINKS, 1)
+        Uh = ctx.pack_gauge(LAT, Ulat, hmc.F64, hmc.LINK18)
+        Ul = ctx.pack_gauge(LAT, Ulat, inner, hmc.LINK12) if inner != hmc.F64 else None
+        b = ctx.pack_spinor(LAT, I.gaussian_half(LAT, 2, n_rhs=n), hmc.F64)
+        x = ctx.new_spinor(LAT, hmc.F64, n)
+        ctx.cg_solve_multi(LAT, Uh, x, b, ks, 1e-10, U_lo=Ul, inner_prec=inner,
+                           reliable_delta=args.delta)
+        torch.cuda.synchronize()
+        ctx.set_timing(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = ctx.cg_solve_multi(LAT, Uh, x, b, ks, 1e-10, U_lo=Ul, inner_prec=inner,
+                               reliable_delta=args.delta)
+        e1.record()
+        torch.cuda.synchronize()
+        st = ctx.timing()
+        ms = e0.elapsed_time(e1)
+        print(json.dumps({"kernel": args.kernel, "solve_ms": round(ms, 3),
+                          "ms_per_rhs": round(ms / n, 3), **r,
+                          "classes": {k: {"launches": v[0], "us": round(v[1] / v[0] * 1e3, 2),
+                                          "GBs": round(v[2] / (v[1] * 1e-3) / 1e9, 1)}
+                                      for k, v in st.items()}}), flush=True)
+        return
     if pname == "cg":
         # one CG solve of Mhat^dag Mhat on the benchmark lattice to 1e-10 with the
         # given inner precision (FP64 reliable updates), all Dslash classes timed

@@ -227,6 +227,21 @@ int hmc_cg_solve(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
                  double tol, int max_iter, const hmc_solver_opts *opts,
                  hmc_solve_stats *stats);
 
+/* hmc_cg_solve_multi: n_rhs (1..16) systems Mhat_r^dag Mhat_r x_r = phi_r
+ * with per-system kappas[r] (host array), solved together: every hemi-Dslash
+ * launch serves all right-hand sides and loads each link once (the
+ * mass-preconditioned pseudo-fermions the paper motivates in Sec. I share the
+ * links but not kappa).  x and phi are F64 even fields with n_rhs right-hand
+ * sides (layout above); U_hi/U_lo and opts as for hmc_cg_solve.  Each system
+ * stops on its own FP64 true residual; converged systems are frozen while the
+ * others iterate, and in mixed precision a reliable update is applied to all
+ * systems when any of them needs one.  stats (nullable) is an array of n_rhs
+ * entries.  Blocks. */
+int hmc_cg_solve_multi(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
+                       const hmc_gauge *U_lo, void *x, const void *phi,
+                       const double *kappas, int n_rhs, double tol, int max_iter,
+                       const hmc_solver_opts *opts, hmc_solve_stats *stats);
+
 /* ---- actions and forces -------------------------------------------------------- */
 
 /* Filter of the pseudo-fermion action (Sec. II): with filt == NULL the plain

@@ -184,9 +184,11 @@ __global__ void __launch_bounds__(DS_NT) k_dslash(const DslashArgs a) {
   const int S_ = a.g.Vh * a.n_rhs;
   const int i = dslash_site(a);
   double nrm = 0.0;
+  int r_out = -1;
   if (i < S_) {
     const int h = a.n_rhs == 1 ? i : i / a.n_rhs;
     const int r = i - h * a.n_rhs;
+    r_out = r;
     int c[4];
     const int lex = site_coords(a.g, h, a.p, c);
     Cx<R> acc[12];
@@ -232,9 +234,15 @@ __global__ void __launch_bounds__(DS_NT) k_dslash(const DslashArgs a) {
     }
   }
   if (a.partials) {
-    double s = block_sum<DS_NT>(nrm);
-    if (threadIdx.x == 0) a.partials[blockIdx.x] = s;
-    if (a.total) last_block_total<DS_NT>(a.partials, a.counter, a.total);
+    if (a.n_rhs == 1) {
+      double s = block_sum<DS_NT>(nrm);
+      if (threadIdx.x == 0) a.partials[blockIdx.x] = s;
+      if (a.total) last_block_total<DS_NT>(a.partials, a.counter, a.total);
+    } else {
+      // one partial (and total) per right-hand side
+      block_partials_rhs<DS_NT>(nrm, r_out, a.n_rhs, a.partials);
+      if (a.total) last_block_totals_rhs<DS_NT>(a.partials, a.n_rhs, a.counter, a.total);
+    }
   }
 }
 

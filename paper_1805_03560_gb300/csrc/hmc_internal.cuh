@@ -379,6 +379,70 @@ __device__ __forceinline__ double block_sum(double v) {
   return s;
 }
 
+// ---- per-site conversion helpers -------------------------------------------------
+
+template <int P>
+using RT = typename SpinorIO<P>::R;
+
+// a site's spinor of storage precision P as complex values of type R
+template <int P, typename R>
+__device__ __forceinline__ void load_as(const void *base, int S, int s, Cx<R> v[12]) {
+  Cx<RT<P>> t[12];
+  SpinorIO<P>::load(base, S, s, t);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) v[k] = {(R)t[k].re, (R)t[k].im};
+}
+
+template <int P, typename R>
+__device__ __forceinline__ void store_as(void *base, int S, int s, const Cx<R> v[12]) {
+  Cx<RT<P>> t[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) t[k] = {(RT<P>)v[k].re, (RT<P>)v[k].im};
+  SpinorIO<P>::store(base, S, s, t);
+}
+
+// Per-right-hand-side block sums.  Each thread holds value v of right-hand
+// side r (r < 0: none); for every q < n_rhs the block writes
+// partials[blockIdx.x * n_rhs + q], summing its threads in index order.
+template <int NT>
+__device__ __forceinline__ void block_partials_rhs(double v, int r, int n_rhs, double *partials) {
+  __shared__ double sv[NT];
+  __shared__ int sr[NT];
+  sv[threadIdx.x] = v;
+  sr[threadIdx.x] = r;
+  __syncthreads();
+  for (int q = threadIdx.x; q < n_rhs; q += NT) {
+    double s = 0.0;
+    for (int j = 0; j < NT; ++j)
+      if (sr[j] == q) s += sv[j];
+    partials[(size_t)blockIdx.x * n_rhs + q] = s;
+  }
+  __syncthreads();
+}
+
+// Last block to arrive sums partials[b * n_rhs + q] over b (index order) into
+// totals[q] for every q, then resets *counter.
+template <int NT>
+__device__ __forceinline__ void last_block_totals_rhs(const double *partials, int n_rhs,
+                                                      unsigned int *counter, double *totals) {
+  __shared__ bool s_last_r;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last_r = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last_r) return;
+  __threadfence();
+  for (int q = 0; q < n_rhs; ++q) {
+    double s = 0.0;
+    for (unsigned int b = threadIdx.x; b < gridDim.x; b += NT)
+      s += __ldcg(partials + (size_t)b * n_rhs + q);
+    s = block_sum<NT>(s);
+    if (threadIdx.x == 0) totals[q] = s;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
 // Called by every thread of every block after thread 0 of the block has
 // stored its partial sum in partials[blockIdx.x]: the last block to arrive
 // sums all partials in index order (the same order whichever block is last,

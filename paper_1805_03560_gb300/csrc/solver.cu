@@ -44,27 +44,6 @@ struct CGState {
   unsigned int cnt[2];  // arrival counters of the two last-block reductions
 };
 
-// ---- generic per-site helpers ------------------------------------------------
-
-template <int P>
-using RT = typename SpinorIO<P>::R;
-
-template <int P, typename R>
-__device__ __forceinline__ void load_as(const void *base, int S, int s, Cx<R> v[12]) {
-  Cx<RT<P>> t[12];
-  SpinorIO<P>::load(base, S, s, t);
-#pragma unroll
-  for (int k = 0; k < 12; ++k) v[k] = {(R)t[k].re, (R)t[k].im};
-}
-
-template <int P, typename R>
-__device__ __forceinline__ void store_as(void *base, int S, int s, const Cx<R> v[12]) {
-  Cx<RT<P>> t[12];
-#pragma unroll
-  for (int k = 0; k < 12; ++k) t[k] = {(RT<P>)v[k].re, (RT<P>)v[k].im};
-  SpinorIO<P>::store(base, S, s, t);
-}
-
 // ---- reductions --------------------------------------------------------------------
 
 // Sum of p[0..n) by one block in a fixed order; valid in thread 0.

@@ -1,0 +1,522 @@
+// Batched conjugate gradients: n_rhs systems Mhat_r^dag Mhat_r x_r = phi_r,
+// each with its own kappa_r (the operators of mass-preconditioned
+// pseudo-fermions share the links but not kappa), solved in lock step so that
+// every hemi-Dslash launch loads each link once for all right-hand sides.
+//
+// The iteration is the single-RHS one with per-RHS scalars: the Mhat Dslash
+// writes per-RHS partials of |Mhat_r p_r|^2 whose last block forms p^dag A p
+// per RHS; axpy and xpay use alpha_r, beta_r.  A right-hand side that has
+// converged is frozen (alpha_r = 0, p_r no longer updated) while the others
+// continue.  Mixed precision: reliable updates are done for all right-hand
+// sides together (one multi-RHS FP64 operator application) whenever one of
+// them needs one, at batch boundaries; each restarts from its true residual.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "hmc_host.h"
+
+namespace hmc {
+
+constexpr int NR_MAX = 16;
+
+struct MState {
+  double rr[2][NR_MAX];
+  double b2[NR_MAX];
+  double pap[NR_MAX];
+  double rr_next[NR_MAX];
+  double aux[NR_MAX];
+  double tol2;
+  int done[NR_MAX];  // 1 converged, 2 NaN/Inf
+  int live[NR_MAX];  // iterating
+  int active;        // any live
+  int iter;
+  unsigned int cnt[2];
+};
+
+// alpha_q = rr_q / pap_q for live q (0 for frozen);  x += alpha p;  r -= alpha Ap
+template <int PX, int PL>
+__global__ void __launch_bounds__(BL_NT) k_mcg_axpy(void *x, void *r, const void *p, const void *Ap,
+                                                    int S, int n_rhs, MState *st, int par,
+                                                    double *partials) {
+  if (!st->active) return;
+  using R = RT<PL>;
+  int i = blockIdx.x * BL_NT + threadIdx.x;
+  double s = 0.0;
+  int q = -1;
+  if (i < S) {
+    q = i % n_rhs;
+    const double pap = st->pap[q];
+    double ad = st->live[q] ? st->rr[par][q] / pap : 0.0;
+    if (st->live[q] && (!isfinite(ad) || !(pap > 0.0))) {
+      st->done[q] = 2;
+      ad = 0.0;
+    }
+    const R alpha = (R)ad;
+    Cx<R> pv[12], v[12];
+    load_as<PL>(p, S, i, pv);
+    load_as<PX>(x, S, i, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      v[k].re = fma(alpha, pv[k].re, v[k].re);
+      v[k].im = fma(alpha, pv[k].im, v[k].im);
+    }
+    store_as<PX>(x, S, i, v);
+    load_as<PL>(Ap, S, i, pv);
+    load_as<PL>(r, S, i, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      v[k].re = fma(-alpha, pv[k].re, v[k].re);
+      v[k].im = fma(-alpha, pv[k].im, v[k].im);
+    }
+    R n2 = R(0);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) n2 += norm2(v[k]);
+    s = (double)n2;
+    store_as<PL>(r, S, i, v);
+  }
+  block_partials_rhs<BL_NT>(s, q, n_rhs, partials);
+  last_block_totals_rhs<BL_NT>(partials, n_rhs, &st->cnt[1], st->rr_next);
+}
+
+// beta_q = rr_next_q / rr_q;  p = r + beta p  (live q);  state advance
+template <int PL>
+__global__ void __launch_bounds__(BL_NT) k_mcg_xpay(void *p, const void *r, int S, int n_rhs,
+                                                    MState *st, int par, int plain) {
+  if (!st->active) return;
+  using R = RT<PL>;
+  int i = blockIdx.x * BL_NT + threadIdx.x;
+  if (i < S) {
+    const int q = i % n_rhs;
+    if (st->live[q]) {
+      const R beta = (R)(st->rr_next[q] / st->rr[par][q]);
+      Cx<R> rv[12], pv[12];
+      load_as<PL>(r, S, i, rv);
+      load_as<PL>(p, S, i, pv);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        pv[k].re = fma(beta, pv[k].re, rv[k].re);
+        pv[k].im = fma(beta, pv[k].im, rv[k].im);
+      }
+      store_as<PL>(p, S, i, pv);
+    }
+  }
+  // the state advances in the last block, after every block has used it
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&st->cnt[0], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  int any = 0;
+  for (int q = 0; q < n_rhs; ++q) {
+    if (st->live[q]) {
+      const double rn = st->rr_next[q];
+      st->rr[par ^ 1][q] = rn;
+      if (!isfinite(rn) || st->done[q] == 2) {
+        st->done[q] = 2;
+        st->live[q] = 0;
+      } else if (plain && rn <= st->tol2 * st->b2[q]) {
+        st->done[q] = 1;
+        st->live[q] = 0;
+      }
+    } else {
+      st->rr[par ^ 1][q] = st->rr[par][q];
+    }
+    any |= st->live[q];
+  }
+  st->active = any;
+  st->iter += 1;
+  st->cnt[0] = 0u;
+}
+
+// per-RHS |v|^2 partials of an F64 field
+__global__ void __launch_bounds__(BL_NT) k_mnorm(const void *v, int S, int n_rhs,
+                                                 double *partials) {
+  int i = blockIdx.x * BL_NT + threadIdx.x;
+  double s = 0.0;
+  int q = -1;
+  if (i < S) {
+    q = i % n_rhs;
+    Cx<double> a[12];
+    load_as<HMC_F64>(v, S, i, a);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) s += norm2(a[k]);
+  }
+  block_partials_rhs<BL_NT>(s, q, n_rhs, partials);
+}
+
+// r = b - q (F64), r_lo = p = r; per-RHS |r|^2 partials
+template <int PL>
+__global__ void __launch_bounds__(BL_NT) k_mresidual(void *r, const void *b, const void *qv,
+                                                     void *r_lo, void *p, int S, int n_rhs,
+                                                     double *partials) {
+  int i = blockIdx.x * BL_NT + threadIdx.x;
+  double s = 0.0;
+  int q = -1;
+  if (i < S) {
+    q = i % n_rhs;
+    Cx<double> bv[12], w[12];
+    load_as<HMC_F64>(b, S, i, bv);
+    load_as<HMC_F64>(qv, S, i, w);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      bv[k] = bv[k] - w[k];
+      s += norm2(bv[k]);
+    }
+    store_as<HMC_F64>(r, S, i, bv);
+    if (r_lo) store_as<PL>(r_lo, S, i, bv);
+    if (p) store_as<PL>(p, S, i, bv);
+  }
+  block_partials_rhs<BL_NT>(s, q, n_rhs, partials);
+}
+
+// per-RHS totals of partials (one block); mode 0: initialise from |b|^2,
+// mode 1: restart every not-failed RHS from its true residual
+__global__ void __launch_bounds__(FIN_NT) k_mstate(MState *st, const double *partials, int nb,
+                                                   int n_rhs, int par, double tol2, int mode) {
+  for (int q = 0; q < n_rhs; ++q) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += FIN_NT) s += partials[(size_t)b * n_rhs + q];
+    s = block_sum<FIN_NT>(s);
+    if (threadIdx.x == 0) {
+      st->aux[q] = s;
+      if (mode == 0) {
+        st->rr[0][q] = st->rr[1][q] = s;
+        st->b2[q] = s;
+        st->pap[q] = st->rr_next[q] = 0.0;
+        st->done[q] = s == 0.0 ? 1 : (isfinite(s) ? 0 : 2);
+        st->live[q] = st->done[q] == 0;
+      } else if (st->done[q] != 2) {
+        st->rr[par][q] = s;
+        const bool conv = s <= tol2 * st->b2[q];
+        st->done[q] = conv ? 1 : (isfinite(s) ? 0 : 2);
+        st->live[q] = st->done[q] == 0;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int any = 0;
+    for (int q = 0; q < n_rhs; ++q) any |= st->live[q];
+    st->active = any;
+    if (mode == 0) {
+      st->tol2 = tol2;
+      st->iter = 0;
+      st->cnt[0] = st->cnt[1] = 0u;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(BL_NT) k_mfold(void *x, void *y, int S) {
+  int i = blockIdx.x * BL_NT + threadIdx.x;
+  if (i >= S) return;
+  Cx<double> xv[12], yv[12];
+  load_as<HMC_F64>(x, S, i, xv);
+  load_as<HMC_F32>(y, S, i, yv);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) xv[k] = xv[k] + yv[k];
+  store_as<HMC_F64>(x, S, i, xv);
+  Cx<float> z[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) z[k] = {0.f, 0.f};
+  SpinorIO<HMC_F32>::store(y, S, i, z);
+}
+
+namespace {
+
+#define TRY(e)         \
+  do {                 \
+    int _s = (e);      \
+    if (_s) return _s; \
+  } while (0)
+
+struct MSolve {
+  hmc_ctx *ctx;
+  Geo g;
+  hmc_gauge Uh, Ul;
+  int plo, n;
+  int S;  // Vh * n
+  MState *st;
+  double *cb;  // -kappa_r^2 (device)
+  double *pap_part, *rr_part, *tmp_part;
+  void *x, *r, *q, *y64, *t64, *xlo, *rlo, *p, *y, *Ap, *tlo;
+  const void *b;
+  int nb_ds, nb_bl;
+};
+
+int m_apply_A64(MSolve &s, const void *in, void *out) {
+  TRY(mhat(s.ctx, s.g, s.Uh, HMC_F64, 0, s.n, s.y64, in, s.t64, 0.0, s.cb, nullptr, nullptr));
+  return mhat(s.ctx, s.g, s.Uh, HMC_F64, 1, s.n, out, s.y64, s.t64, 0.0, s.cb, nullptr, nullptr);
+}
+
+int m_iteration(MSolve &s, int k) {
+  hmc_ctx *ctx = s.ctx;
+  const bool mixed = s.plo != HMC_F64;
+  const hmc_gauge &U = mixed ? s.Ul : s.Uh;
+  const int par = k & 1;
+  DslashArgs a{};
+  a.g = s.g;
+  a.n_rhs = s.n;
+  a.gauge = U.data;
+  a.gate = &s.st->active;
+  a.tag = "cg_multi";
+  a.p = 1; a.out = s.tlo; a.in = s.p; a.cb = 1.0;
+  TRY(dslash(ctx, a, U, s.plo, 0, nullptr));
+  a.p = 0; a.out = s.y; a.in = s.tlo; a.x = s.p; a.ca = 1.0; a.cb_rhs = s.cb;
+  a.partials = s.pap_part; a.total = s.st->pap; a.counter = &s.st->cnt[0];
+  TRY(dslash(ctx, a, U, s.plo, 0, nullptr));
+  a.partials = nullptr; a.total = nullptr; a.counter = nullptr;
+  a.p = 1; a.out = s.tlo; a.in = s.y; a.x = nullptr; a.ca = 0.0; a.cb = 1.0; a.cb_rhs = nullptr;
+  TRY(dslash(ctx, a, U, s.plo, 1, nullptr));
+  a.p = 0; a.out = s.Ap; a.in = s.tlo; a.x = s.y; a.ca = 1.0; a.cb_rhs = s.cb;
+  TRY(dslash(ctx, a, U, s.plo, 1, nullptr));
+  cudaStream_t st = ctx->stream;
+  const int plain = mixed ? 0 : 1;
+  switch (s.plo) {
+    case HMC_F64:
+      k_mcg_axpy<HMC_F64, HMC_F64><<<s.nb_bl, BL_NT, 0, st>>>(s.x, s.rlo, s.p, s.Ap, s.S, s.n,
+                                                              s.st, par, s.rr_part);
+      break;
+    case HMC_F32:
+      k_mcg_axpy<HMC_F32, HMC_F32><<<s.nb_bl, BL_NT, 0, st>>>(s.xlo, s.rlo, s.p, s.Ap, s.S, s.n,
+                                                              s.st, par, s.rr_part);
+      break;
+    case HMC_F16:
+      k_mcg_axpy<HMC_F32, HMC_F16><<<s.nb_bl, BL_NT, 0, st>>>(s.xlo, s.rlo, s.p, s.Ap, s.S, s.n,
+                                                              s.st, par, s.rr_part);
+      break;
+  }
+  TRY(launched(ctx, "cg_multi_axpy"));
+  switch (s.plo) {
+    case HMC_F64:
+      k_mcg_xpay<HMC_F64><<<s.nb_bl, BL_NT, 0, st>>>(s.p, s.rlo, s.S, s.n, s.st, par, plain);
+      break;
+    case HMC_F32:
+      k_mcg_xpay<HMC_F32><<<s.nb_bl, BL_NT, 0, st>>>(s.p, s.rlo, s.S, s.n, s.st, par, plain);
+      break;
+    case HMC_F16:
+      k_mcg_xpay<HMC_F16><<<s.nb_bl, BL_NT, 0, st>>>(s.p, s.rlo, s.S, s.n, s.st, par, plain);
+      break;
+  }
+  return launched(ctx, "cg_multi_xpay");
+}
+
+int m_read(MSolve &s, MState *h) {
+  cudaError_t e = cudaMemcpyAsync(h, s.st, sizeof(MState), cudaMemcpyDeviceToHost, s.ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s.ctx->stream);
+  return cuda_ok(s.ctx, e, "cg_multi: reading solver state");
+}
+
+// r = b - A x for every RHS, restart the recursion from it (p = r_lo = r)
+int m_true_residual(MSolve &s, int par, double tol2) {
+  TRY(m_apply_A64(s, s.x, s.q));
+  const bool mixed = s.plo != HMC_F64;
+  cudaStream_t st = s.ctx->stream;
+  switch (s.plo) {
+    case HMC_F64:
+      k_mresidual<HMC_F64><<<s.nb_bl, BL_NT, 0, st>>>(s.r, s.b, s.q, nullptr, s.p, s.S, s.n,
+                                                      s.tmp_part);
+      break;
+    case HMC_F32:
+      k_mresidual<HMC_F32><<<s.nb_bl, BL_NT, 0, st>>>(s.r, s.b, s.q, s.rlo, s.p, s.S, s.n,
+                                                      s.tmp_part);
+      break;
+    case HMC_F16:
+      k_mresidual<HMC_F16><<<s.nb_bl, BL_NT, 0, st>>>(s.r, s.b, s.q, s.rlo, s.p, s.S, s.n,
+                                                      s.tmp_part);
+      break;
+  }
+  (void)mixed;
+  TRY(launched(s.ctx, "residual_multi"));
+  k_mstate<<<1, FIN_NT, 0, st>>>(s.st, s.tmp_part, s.nb_bl, s.n, par, tol2, 1);
+  return launched(s.ctx, "cg_multi_restart");
+}
+
+}  // namespace
+
+int cg_solve_multi(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul, void *x,
+                   const void *b, const double *kappas, int n_rhs, double tol, int max_iter,
+                   const hmc_solver_opts *opts, hmc_solve_stats *stats) {
+  if (n_rhs < 1 || n_rhs > NR_MAX)
+    return fail(ctx, HMC_EINVAL, "cg_multi: n_rhs must be 1..%d", NR_MAX);
+  MSolve s{};
+  s.ctx = ctx;
+  s.g = g;
+  s.Uh = Uh;
+  s.n = n_rhs;
+  s.plo = opts ? opts->inner_prec : HMC_F64;
+  if (s.plo != HMC_F64 && s.plo != HMC_F32 && s.plo != HMC_F16)
+    return fail(ctx, HMC_EINVAL, "cg_multi: bad inner precision %d", s.plo);
+  if (Uh.prec != HMC_F64) return fail(ctx, HMC_EINVAL, "cg_multi: U_hi must be F64");
+  const bool mixed = s.plo != HMC_F64;
+  if (mixed) {
+    if (!Ul || !Ul->data || Ul->prec != s.plo)
+      return fail(ctx, HMC_EINVAL, "cg_multi: U_lo must be given in the inner precision");
+    s.Ul = *Ul;
+  }
+  if (!(tol > 0.0)) return fail(ctx, HMC_EINVAL, "cg_multi: tol must be > 0");
+  const double delta = (opts && opts->reliable_delta > 0) ? opts->reliable_delta : 0.1;
+  const int check = (opts && opts->check_every > 0) ? opts->check_every : 16;
+  s.S = g.Vh * n_rhs;
+  s.nb_ds = blocks_for(s.S, DS_NT);
+  s.nb_bl = blocks_for(s.S, BL_NT);
+  const size_t f64 = spinor_bytes(g, HMC_F64, n_rhs);
+  s.st = (MState *)workspace(ctx, "cgm_state", sizeof(MState));
+  s.cb = (double *)workspace(ctx, "cgm_cb", sizeof(double) * NR_MAX);
+  double *parts = (double *)workspace(
+      ctx, "cgm_partials", sizeof(double) * ((size_t)(s.nb_ds + 2 * s.nb_bl) * n_rhs + 64));
+  s.r = workspace(ctx, "cgm_r64", f64);
+  s.q = workspace(ctx, "cgm_q64", f64);
+  s.y64 = workspace(ctx, "cgm_y64", f64);
+  s.t64 = workspace(ctx, "cgm_t64", f64);
+  s.p = workspace(ctx, "cgm_p", f64);
+  s.y = workspace(ctx, "cgm_y", f64);
+  s.Ap = workspace(ctx, "cgm_ap", f64);
+  s.tlo = workspace(ctx, "cgm_t", f64);
+  if (!s.st || !s.cb || !parts || !s.r || !s.q || !s.y64 || !s.t64 || !s.p || !s.y || !s.Ap ||
+      !s.tlo)
+    return HMC_ENOMEM;
+  if (mixed) {
+    s.xlo = workspace(ctx, "cgm_xlo", f64);
+    s.rlo = workspace(ctx, "cgm_rlo", f64);
+    if (!s.xlo || !s.rlo) return HMC_ENOMEM;
+  } else {
+    s.rlo = s.r;
+  }
+  s.pap_part = parts;
+  s.rr_part = parts + (size_t)s.nb_ds * n_rhs;
+  s.tmp_part = parts + (size_t)(s.nb_ds + s.nb_bl) * n_rhs;
+  s.x = x;
+  s.b = b;
+  double hcb[NR_MAX];
+  for (int q = 0; q < n_rhs; ++q) hcb[q] = -kappas[q] * kappas[q];
+  TRY(cuda_ok(ctx, cudaMemcpyAsync(s.cb, hcb, sizeof(double) * n_rhs, cudaMemcpyHostToDevice,
+                                   ctx->stream),
+              "cg_multi: kappas"));
+  // x = 0, r = b, p = r, per-RHS |b|^2
+  TRY(zero_field(ctx, HMC_F64, x, s.S));
+  TRY(copy_convert(ctx, HMC_F64, HMC_F64, s.r, b, s.S));
+  k_mnorm<<<s.nb_bl, BL_NT, 0, ctx->stream>>>(b, s.S, n_rhs, s.tmp_part);
+  TRY(launched(ctx, "norm_multi"));
+  k_mstate<<<1, FIN_NT, 0, ctx->stream>>>(s.st, s.tmp_part, s.nb_bl, n_rhs, 0, tol * tol, 0);
+  TRY(launched(ctx, "cg_multi_init"));
+  if (mixed) {
+    TRY(zero_field(ctx, HMC_F32, s.xlo, s.S));
+    TRY(copy_convert(ctx, s.plo, HMC_F64, s.rlo, b, s.S));
+    TRY(copy_convert(ctx, s.plo, HMC_F64, s.p, b, s.S));
+  } else {
+    TRY(copy_convert(ctx, HMC_F64, HMC_F64, s.p, b, s.S));
+  }
+  MState h{};
+  TRY(m_read(s, &h));
+  std::vector<double> maxr2(n_rhs), rr(n_rhs);
+  std::vector<int> reliable(n_rhs, 0);
+  for (int q = 0; q < n_rhs; ++q) maxr2[q] = rr[q] = h.b2[q];
+  int k = 0, restarts = 0;
+  bool nan = false;
+  double rate = 0.0;  // slowest observed log-decrease per iteration
+  while (h.active && k < max_iter) {
+    int todo = check;
+    if (rate < 0.0) {
+      double left = 0.0;
+      for (int q = 0; q < n_rhs; ++q) {
+        if (!h.live[q]) continue;
+        const double target =
+            mixed ? fmax(tol * tol * h.b2[q], delta * delta * maxr2[q]) : tol * tol * h.b2[q];
+        left = fmax(left, log(target / rr[q]) / rate);
+      }
+      if (left < todo) todo = left < 1.0 ? 1 : (int)ceil(left);
+    }
+    if (k + todo > max_iter) todo = max_iter - k;
+    for (int j = 0; j < todo; ++j) TRY(m_iteration(s, k + j));
+    std::vector<double> before(rr);
+    TRY(m_read(s, &h));
+    const int did = h.iter - k;
+    k = h.iter;
+    double worst = 0.0;
+    bool update = false;
+    for (int q = 0; q < n_rhs; ++q) {
+      if (h.done[q] == 2) nan = true;
+      const double now = h.rr[k & 1][q];
+      if (h.live[q] && did > 0 && now > 0.0 && now < before[q])
+        worst = worst == 0.0 ? log(now / before[q]) / did : fmax(worst, log(now / before[q]) / did);
+      rr[q] = now;
+      if (now > maxr2[q]) maxr2[q] = now;
+      if (mixed && h.live[q] &&
+          (now <= tol * tol * h.b2[q] || now < delta * delta * maxr2[q]))
+        update = true;
+    }
+    if (nan) break;
+    if (worst < 0.0) rate = worst;
+    if (mixed && update) {
+      // reliable update of every right-hand side at once
+      k_mfold<<<s.nb_bl, BL_NT, 0, ctx->stream>>>(s.x, s.xlo, s.S);
+      TRY(launched(ctx, "fold_multi"));
+      TRY(m_true_residual(s, k & 1, tol * tol));
+      TRY(m_read(s, &h));
+      for (int q = 0; q < n_rhs; ++q) {
+        ++reliable[q];
+        rr[q] = maxr2[q] = h.aux[q];
+      }
+      continue;
+    }
+    if (!mixed && !h.active) {
+      // every RHS converged on its recursive residual: confirm on the true one
+      TRY(m_true_residual(s, k & 1, tol * tol));
+      TRY(m_read(s, &h));
+      if (!h.active || ++restarts > 5) break;
+      for (int q = 0; q < n_rhs; ++q) rr[q] = h.aux[q];
+    }
+  }
+  if (mixed) {
+    k_mfold<<<s.nb_bl, BL_NT, 0, ctx->stream>>>(s.x, s.xlo, s.S);
+    TRY(launched(ctx, "fold_multi"));
+  }
+  // final true residuals
+  TRY(m_apply_A64(s, s.x, s.q));
+  k_mresidual<HMC_F32><<<s.nb_bl, BL_NT, 0, ctx->stream>>>(s.r, s.b, s.q, nullptr, nullptr, s.S,
+                                                           n_rhs, s.tmp_part);
+  TRY(launched(ctx, "residual_multi"));
+  MState hs = h;
+  k_mstate<<<1, FIN_NT, 0, ctx->stream>>>(s.st, s.tmp_part, s.nb_bl, n_rhs, k & 1, tol * tol, 1);
+  TRY(launched(ctx, "cg_multi_restart"));
+  TRY(m_read(s, &hs));
+  bool all = true;
+  double worst_rel = 0.0;
+  for (int q = 0; q < n_rhs; ++q) {
+    const double rel = hs.b2[q] > 0 ? sqrt(hs.aux[q] / hs.b2[q]) : 0.0;
+    if (stats) {
+      stats[q].iterations = k;
+      stats[q].reliable_updates = reliable[q];
+      stats[q].true_rel_res = rel;
+    }
+    if (!(rel <= tol)) all = false;
+    worst_rel = fmax(worst_rel, rel);
+  }
+  if (nan) return fail(ctx, HMC_ENAN, "cg_multi: NaN/Inf in a reduction");
+  if (!all)
+    return fail(ctx, HMC_ENOCONV, "cg_multi: not converged after %d iterations (worst %.3e)", k,
+                worst_rel);
+  return HMC_OK;
+}
+
+}  // namespace hmc
+
+using namespace hmc;
+
+extern "C" int hmc_cg_solve_multi(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
+                                  const hmc_gauge *U_lo, void *x, const void *phi,
+                                  const double *kappas, int n_rhs, double tol, int max_iter,
+                                  const hmc_solver_opts *opts, hmc_solve_stats *stats) {
+  if (!ctx) return HMC_EINVAL;
+  int st = check_lattice(ctx, lat);
+  if (st) return st;
+  if ((st = check_gauge(ctx, U_hi))) return st;
+  if (!x || !phi || !kappas || max_iter < 1) return fail(ctx, HMC_EINVAL, "cg_multi: bad arguments");
+  if (x == phi) return fail(ctx, HMC_EINVAL, "cg_multi: x must not alias phi");
+  if (opts && opts->inner_prec != HMC_F64 && (st = check_gauge(ctx, U_lo))) return st;
+  return cg_solve_multi(ctx, make_geo(*lat), *U_hi, U_lo, x, phi, kappas, n_rhs, tol, max_iter,
+                        opts, stats);
+}

@@ -85,6 +85,7 @@ _SIGS = {
     "hmc_mhat": (_I, [_P, _P, _P, _P, _P, _D, _I, _I, _I, _P]),
     "hmc_mhat_noalloc": (_I, [_P, _P, _P, _P, _P, _D, _I, _I, _I]),
     "hmc_cg_solve": (_I, [_P, _P, _P, _P, _P, _P, _D, _D, _I, _P, _P]),
+    "hmc_cg_solve_multi": (_I, [_P, _P, _P, _P, _P, _P, _P, _I, _D, _I, _P, _P]),
     "hmc_force_pf": (_I, [_P, _P, _P, _P, _P, _D, _P, _D, _P, _D, _P, _P]),
     "hmc_action_pf": (_I, [_P, _P, _P, _P, _P, _D, _P, _D, _P, _P, _P]),
     "hmc_force_hopexp": (_I, [_P, _P, _P, _D, _D, _I, _D, _P, _P]),
@@ -325,6 +326,27 @@ class Context:
         if st and st != ENOCONV:
             self._check(st, "hmc_cg_solve")
         return res
+
+    def cg_solve_multi(self, L, U_hi, x, phi, kappas, tol, max_iter=10000, U_lo=None,
+                       inner_prec=F64, reliable_delta=0.1, check_every=16):
+        """Batched solve of phi.n_rhs systems with per-system kappas."""
+        self._stream()
+        n = phi.n_rhs
+        gh = U_hi.gauge()
+        gl = U_lo.gauge() if U_lo is not None else None
+        ks = np.ascontiguousarray(kappas, dtype=np.float64)
+        assert len(ks) == n
+        opts = SolverOpts(inner_prec, reliable_delta, check_every, F64)
+        stats = (SolveStats * n)()
+        st = lib().hmc_cg_solve_multi(self.h, _ref(lattice(L)), ctypes.byref(gh),
+                                      ctypes.byref(gl) if gl is not None else None, x.ptr(),
+                                      phi.ptr(), ks.ctypes.data_as(_P), n, tol, max_iter,
+                                      ctypes.byref(opts), stats)
+        if st and st != ENOCONV:
+            self._check(st, "hmc_cg_solve_multi")
+        return {"status": st, "iterations": [s.iterations for s in stats],
+                "reliable_updates": [s.reliable_updates for s in stats],
+                "true_rel_res": [s.true_rel_res for s in stats]}
 
     # ---- actions and forces -------------------------------------------------------
     @staticmethod

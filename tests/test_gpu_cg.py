@@ -110,3 +110,44 @@ def test_cg_throughput_lattice(orc, ctx, H, inner):
     assert res["status"] == 0
     r = phi - orc.mdagm(L, U, kappa, x)
     assert np.linalg.norm(r) / np.linalg.norm(phi) <= 1.01e-10
+
+
+@pytest.mark.parametrize("inner", [0, 1, 2])
+def test_cg_multi_rhs_per_kappa(orc, ctx, H, inner):
+    """Three systems with the kappas of the mass-preconditioned pseudo-fermions
+    solved together: each matches the oracle's solve with its own kappa and
+    meets the tolerance on its FP64 true residual."""
+    L = (4, 6, 6, 10)
+    kappas = [0.150, 0.154, 0.1575]
+    U = I.gauge_links(L, 0.3, 1)
+    phi = I.gaussian_half(L, 2, n_rhs=3)
+    tol = 1e-12 if inner == 0 else 1e-10
+    Uh = ctx.pack_gauge(L, U, 0, 18)
+    Ul = ctx.pack_gauge(L, U, inner, 12) if inner else None
+    b = ctx.pack_spinor(L, phi, 0)
+    x = ctx.new_spinor(L, 0, 3)
+    res = ctx.cg_solve_multi(L, Uh, x, b, kappas, tol, U_lo=Ul, inner_prec=inner)
+    assert res["status"] == 0, res
+    xs = _np(ctx.unpack_spinor(L, x))
+    for r, k in enumerate(kappas):
+        assert res["true_rel_res"][r] <= tol
+        rr = phi[r] - orc.mdagm(L, U, k, xs[r])
+        assert np.linalg.norm(rr) / np.linalg.norm(phi[r]) <= tol * 1.01
+        xo, _, _ = orc.cg(L, U, k, phi[r], tol=1e-13)
+        assert np.abs(xs[r] - xo).max() / np.abs(xo).max() <= 50 * tol
+
+
+def test_cg_multi_matches_single(ctx, H):
+    """One right-hand side through the batched solver equals the single solve."""
+    L = (4, 4, 4, 8)
+    U = I.gauge_links(L, 0.3, 1)
+    phi = I.gaussian_half(L, 5)
+    Uh = ctx.pack_gauge(L, U, 0, 18)
+    b = ctx.pack_spinor(L, phi, 0)
+    x1 = ctx.new_spinor(L, 0)
+    x2 = ctx.new_spinor(L, 0)
+    r1 = ctx.cg_solve(L, Uh, x1, b, 0.156, 1e-12)
+    r2 = ctx.cg_solve_multi(L, Uh, x2, b, [0.156], 1e-12)
+    assert r1["iterations"] == r2["iterations"][0]
+    a1, a2 = _np(ctx.unpack_spinor(L, x1)), _np(ctx.unpack_spinor(L, x2))
+    assert np.abs(a1 - a2).max() <= 1e-14 * np.abs(a1).max()
