@@ -131,7 +131,7 @@ def run_kernel(args):
                                           "GBs": round(v[2] / (v[1] * 1e-3) / 1e9, 1)}
                                       for k, v in st.items()}}), flush=True)
         return
-    prec = {"f64": hmc.F64, "f32": hmc.F32, "f16": hmc.F16}[pname]
+    prec = {"f64": hmc.F64, "f32": hmc.F32, "f16": hmc.F16, "f64e": hmc.F64E}[pname]
     fmt = int(fmt)
     U = ctx.pack_gauge(LAT, I.gauge_links(LAT, EPS_LINKS, 1), prec, fmt)
     srcs = [ctx.pack_spinor(LAT, I.gaussian_half(LAT, 2 + i), prec) for i in range(2)]

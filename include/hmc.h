@@ -75,7 +75,13 @@ typedef enum {
   HMC_ECUDA = 6
 } hmc_status;
 
-typedef enum { HMC_F64 = 0, HMC_F32 = 1, HMC_F16 = 2 } hmc_prec;
+/* HMC_F64E: emulated FP64.  Each real is stored as the unevaluated sum of two
+ * floats (hi, lo), the same 8 bytes as a double, and arithmetic runs in
+ * double-float on the FP32 units (about 48 significant bits).  Used where
+ * FP64-accurate operator applications are needed on a GPU whose FP64 rate is
+ * a small fraction of its FP32 rate.  Layouts as FP64 with a float2 (hi, lo)
+ * in place of each double. */
+typedef enum { HMC_F64 = 0, HMC_F32 = 1, HMC_F16 = 2, HMC_F64E = 3 } hmc_prec;
 typedef enum { HMC_LINK18 = 18, HMC_LINK12 = 12 } hmc_link_fmt;
 
 typedef struct hmc_ctx hmc_ctx;

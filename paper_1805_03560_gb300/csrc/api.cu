@@ -139,7 +139,7 @@ int check_lattice(hmc_ctx *ctx, const hmc_lattice *lat) {
 }
 
 int check_prec(hmc_ctx *ctx, int prec) {
-  if (prec != HMC_F64 && prec != HMC_F32 && prec != HMC_F16)
+  if (prec != HMC_F64 && prec != HMC_F32 && prec != HMC_F16 && prec != HMC_F64E)
     return fail(ctx, HMC_EINVAL, "unsupported precision %d", prec);
   return HMC_OK;
 }
@@ -158,6 +158,7 @@ size_t spinor_bytes(const Geo &g, int prec, int n_rhs) {
     case HMC_F64: b = SpinorIO<HMC_F64>::bytes(S); break;
     case HMC_F32: b = SpinorIO<HMC_F32>::bytes(S); break;
     case HMC_F16: b = SpinorIO<HMC_F16>::bytes(S); break;
+    case HMC_F64E: b = SpinorIO<HMC_F64E>::bytes(S); break;
     default: return 0;
   }
   return (b + 255) & ~(size_t)255;
@@ -170,6 +171,7 @@ size_t gauge_bytes(const Geo &g, int prec, int fmt) {
     case HMC_F64: per = (size_t)fmt * 8; break;
     case HMC_F32: per = (size_t)fmt * 4; break;
     case HMC_F16: per = (size_t)fmt * 2; break;
+    case HMC_F64E: per = (size_t)fmt * 8; break;
     default: return 0;
   }
   return ((size_t)2 * 4 * g.Vh * per + 255) & ~(size_t)255;

@@ -175,8 +175,22 @@ __device__ __forceinline__ int dslash_site(const DslashArgs &a) {
   return seg * 32 + lane + (2 * xp + (w & 1)) * sx + (2 * tp + (w >> 1)) * st;
 }
 
+// Minimum resident blocks per SM asked of the register allocator, per
+// storage precision: the stencil is latency bound at the occupancy its
+// register count allows, so fewer registers (more warps in flight) win as
+// long as nothing spills.
+#ifndef HMC_DS_MINB32
+#define HMC_DS_MINB32 1
+#endif
+#ifndef HMC_DS_MINB64
+#define HMC_DS_MINB64 1
+#endif
+constexpr int ds_min_blocks(int sp) {
+  return (sp == HMC_F64 || sp == HMC_F64E) ? HMC_DS_MINB64 : HMC_DS_MINB32;
+}
+
 template <int SP, int FMT, bool DAG, bool PAIR>
-__global__ void __launch_bounds__(DS_NT) k_dslash(const DslashArgs a) {
+__global__ void __launch_bounds__(DS_NT, ds_min_blocks(SP)) k_dslash(const DslashArgs a) {
   using SIO = SpinorIO<SP>;
   using R = typename SIO::R;
   constexpr int SF = DAG ? -1 : 1;  // forwards: 1 - gamma (1 + gamma for the adjoint)
@@ -273,12 +287,13 @@ int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int
   // algorithmic bytes: every link once (8 per output site, shared by the
   // right-hand sides), the input and output spinors once, the epilogue field
   // once, and the per-site norms of half storage
-  const double rb = sprec == HMC_F64 ? 8.0 : (sprec == HMC_F32 ? 4.0 : 2.0);
+  const double rb = (sprec == HMC_F64 || sprec == HMC_F64E) ? 8.0 : (sprec == HMC_F32 ? 4.0 : 2.0);
   double bytes = (double)a.g.Vh * 8.0 * U.fmt * rb + (double)S * 24.0 * rb * (a.x ? 3.0 : 2.0);
   if (sprec == HMC_F16) bytes += (double)S * 4.0 * (a.x ? 3.0 : 2.0);
   char cls[64];
   snprintf(cls, sizeof(cls), "dslash_%s_%d%s%s",
-           sprec == HMC_F64 ? "f64" : (sprec == HMC_F32 ? "f32" : "f16"), U.fmt, a.tag ? "/" : "",
+           sprec == HMC_F64 ? "f64" : (sprec == HMC_F32 ? "f32" : (sprec == HMC_F16 ? "f16" : "f64e")),
+           U.fmt, a.tag ? "/" : "",
            a.tag ? a.tag : "");
   // kernel variant (hmc_ctx_set_option): bit 0 tiled site mapping, bit 1
   // paired loads
@@ -299,6 +314,8 @@ int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int
     case HMC_F32 * 100 + 12: launch_sf<HMC_F32, 12>(aa, dagger, pair, nb, st); break;
     case HMC_F16 * 100 + 18: launch_sf<HMC_F16, 18>(aa, dagger, pair, nb, st); break;
     case HMC_F16 * 100 + 12: launch_sf<HMC_F16, 12>(aa, dagger, pair, nb, st); break;
+    case HMC_F64E * 100 + 18: launch_sf<HMC_F64E, 18>(aa, dagger, pair, nb, st); break;
+    case HMC_F64E * 100 + 12: launch_sf<HMC_F64E, 12>(aa, dagger, pair, nb, st); break;
     default:
       return fail(ctx, HMC_EINVAL, "dslash: unsupported precision %d / link format %d", sprec,
                   U.fmt);

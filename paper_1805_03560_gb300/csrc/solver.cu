@@ -306,6 +306,9 @@ int copy_convert(hmc_ctx *ctx, int pd, int ps, void *d, const void *s, int S) {
     case HMC_F64 * 10 + HMC_F16: copy_l<HMC_F64, HMC_F16>(ctx, d, s, S); break;
     case HMC_F32 * 10 + HMC_F32: copy_l<HMC_F32, HMC_F32>(ctx, d, s, S); break;
     case HMC_F16 * 10 + HMC_F16: copy_l<HMC_F16, HMC_F16>(ctx, d, s, S); break;
+    case HMC_F64E * 10 + HMC_F64: copy_l<HMC_F64E, HMC_F64>(ctx, d, s, S); break;
+    case HMC_F64 * 10 + HMC_F64E: copy_l<HMC_F64, HMC_F64E>(ctx, d, s, S); break;
+    case HMC_F64E * 10 + HMC_F64E: copy_l<HMC_F64E, HMC_F64E>(ctx, d, s, S); break;
     default: return fail(ctx, HMC_EINVAL, "copy: unsupported precisions %d <- %d", pd, ps);
   }
   return launched(ctx, "copy");
@@ -317,6 +320,7 @@ int zero_field(hmc_ctx *ctx, int prec, void *d, int S) {
     case HMC_F64: k_zero<HMC_F64><<<nb, BL_NT, 0, ctx->stream>>>(d, S); break;
     case HMC_F32: k_zero<HMC_F32><<<nb, BL_NT, 0, ctx->stream>>>(d, S); break;
     case HMC_F16: k_zero<HMC_F16><<<nb, BL_NT, 0, ctx->stream>>>(d, S); break;
+    case HMC_F64E: k_zero<HMC_F64E><<<nb, BL_NT, 0, ctx->stream>>>(d, S); break;
     default: return fail(ctx, HMC_EINVAL, "zero: bad precision %d", prec);
   }
   return launched(ctx, "zero");
@@ -329,6 +333,7 @@ int norm_partials(hmc_ctx *ctx, int prec, const void *v, int S, double *partials
     case HMC_F64: k_norm<HMC_F64><<<nb, BL_NT, 0, ctx->stream>>>(v, S, partials); break;
     case HMC_F32: k_norm<HMC_F32><<<nb, BL_NT, 0, ctx->stream>>>(v, S, partials); break;
     case HMC_F16: k_norm<HMC_F16><<<nb, BL_NT, 0, ctx->stream>>>(v, S, partials); break;
+    case HMC_F64E: k_norm<HMC_F64E><<<nb, BL_NT, 0, ctx->stream>>>(v, S, partials); break;
     default: return fail(ctx, HMC_EINVAL, "norm: bad precision %d", prec);
   }
   return launched(ctx, "norm");
@@ -341,6 +346,7 @@ int axpby(hmc_ctx *ctx, int prec, void *out, double a, const void *x, double b, 
     case HMC_F64: k_axpby<HMC_F64><<<nb, BL_NT, 0, ctx->stream>>>(out, a, x, b, y, S); break;
     case HMC_F32: k_axpby<HMC_F32><<<nb, BL_NT, 0, ctx->stream>>>(out, a, x, b, y, S); break;
     case HMC_F16: k_axpby<HMC_F16><<<nb, BL_NT, 0, ctx->stream>>>(out, a, x, b, y, S); break;
+    case HMC_F64E: k_axpby<HMC_F64E><<<nb, BL_NT, 0, ctx->stream>>>(out, a, x, b, y, S); break;
     default: return fail(ctx, HMC_EINVAL, "axpby: bad precision %d", prec);
   }
   return launched(ctx, "axpby");

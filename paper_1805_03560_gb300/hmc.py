@@ -13,9 +13,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhmc.so")
 
-F64, F32, F16 = 0, 1, 2
+F64, F32, F16, F64E = 0, 1, 2, 3
 LINK18, LINK12 = 18, 12
-PREC_NAMES = {F64: "f64", F32: "f32", F16: "f16"}
+PREC_NAMES = {F64: "f64", F32: "f32", F16: "f16", F64E: "f64e"}
 
 OK, EINVAL, ENOMEM, ENOCONV, ETIMEOUT, ENAN, ECUDA = range(7)
 _STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ENOCONV", 4: "ETIMEOUT", 5: "ENAN", 6: "ECUDA"}

@@ -5,8 +5,11 @@ Tolerances: FP64 storage and arithmetic differ from the oracle only in the
 order of rounding, <= 1e-14 relative to the field's largest entry.  FP32
 storage with FP32 arithmetic: 8 hops of ~66 flops on unit-norm links give
 <= 1e-6.  FP16 storage (11-bit significand, power-of-two per-site scale) with
-FP32 arithmetic: <= 4e-3.  On links and spinors with small-integer entries
-every precision is exact: bit-for-bit equality.
+FP32 arithmetic: <= 4e-3.  Emulated FP64 (float pairs, about 48 significant
+bits, error-free sums and products of the halves): a unit roundoff near
+2^-47 over the same ~100 chained operations, <= 2e-13.  On links and
+spinors with small-integer entries every precision is exact: bit-for-bit
+equality.
 """
 import numpy as np
 import pytest
@@ -15,8 +18,8 @@ from paper_1805_03560_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-14, 1: 1e-6, 2: 4e-3}
-PRECS = [0, 1, 2]
+TOL = {0: 1e-14, 1: 1e-6, 2: 4e-3, 3: 2e-13}
+PRECS = [0, 1, 2, 3]
 FMTS = [18, 12]
 
 
@@ -52,7 +55,7 @@ def test_gauge_pack_roundtrip(ctx, H, prec, fmt):
     assert np.array_equal(back, U)  # exact: entries in {0, +-1, +-i}
     Ur = I.gauge_links(L, 0.3, 1)
     back = _np(ctx.unpack_gauge(L, ctx.pack_gauge(L, Ur, prec, fmt)))
-    assert _rel(back, Ur) <= {0: 1e-14, 1: 1e-6, 2: 2e-3}[prec]
+    assert _rel(back, Ur) <= {0: 1e-14, 1: 1e-6, 2: 2e-3, 3: 5e-14}[prec]
     if prec == 0 and fmt == 18:
         assert np.array_equal(back, Ur)
 
@@ -68,7 +71,7 @@ def test_spinor_pack_roundtrip(ctx, H, prec, n_rhs):
     assert np.array_equal(back, psi)
     g = I.gaussian_half(L, 2, n_rhs if n_rhs > 1 else None)
     back = _np(ctx.unpack_spinor(L, ctx.pack_spinor(L, g, prec)))
-    assert _rel(back, g) <= {0: 0, 1: 1e-7, 2: 1e-3}[prec]
+    assert _rel(back, g) <= {0: 0, 1: 1e-7, 2: 1e-3, 3: 4e-15}[prec]
 
 
 def test_algebra_pack_roundtrip(ctx, H):
@@ -169,12 +172,12 @@ def test_dslash_bench_lattice_parity(orc, ctx, H):
     U = I.gauge_links(L, 0.3, 1)
     psi = I.gaussian_half(L, 2)
     want = orc.hop_eo(L, U, 0, psi)
-    for prec, fmt in ((0, 18), (0, 12), (1, 12), (2, 12)):
+    for prec, fmt in ((0, 18), (0, 12), (1, 12), (2, 12), (3, 18), (3, 12)):
         Ud = ctx.pack_gauge(L, U, prec, fmt)
         out = ctx.new_spinor(L, prec)
         ctx.dslash(L, Ud, out, ctx.pack_spinor(L, psi, prec), 0)
         got = _np(ctx.unpack_spinor(L, out))
-        tol = {0: 1e-14, 1: 2e-6, 2: 6e-3}[prec]
+        tol = {0: 1e-14, 1: 2e-6, 2: 6e-3, 3: 2e-13}[prec]
         assert _rel(got, want) <= tol, (prec, fmt, _rel(got, want))
 
 
