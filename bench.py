@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--kernel", default=None,
                     help="time one hemi-Dslash variant alone, e.g. f16-12 (for profiling)")
     ap.add_argument("--launches", type=int, default=20)
+    ap.add_argument("--report", default=None, choices=["md"],
+                    help="md: leapfrog dH at dt = 1/10, 1/20, 1/40 and reversibility on "
+                         "16^3x32, kappa 0.156, plain pseudo-fermion action")
     ap.add_argument("--variant", type=int, default=None, help="hemi-Dslash kernel variant 0..3")
     return ap.parse_args()
 
@@ -513,9 +516,62 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_md_report(args):
+    """Leapfrog HMC trajectories (tau = 1, one time scale, plain S_PF) on
+    16^3 x 32 at beta 5.6, kappa 0.156 from fixed (U, Pi, eta): dH for
+    dt = 1/10, 1/20, 1/40 (dH ~ dt^2), and the reversibility
+    Delta = sum |U - U'|^2 of a forward and a momentum-flipped backward
+    run, for the plain FP64 and the mixed-precision paths."""
+    import numpy as np
+    import torch
+    from paper_1805_03560_gb300 import hmc
+    from paper_1805_03560_gb300 import inputs as I
+    L = (32, 16, 16, 16)
+    beta, kappa = 5.6, 0.156
+    ctx = hmc.Context(0)
+    U0 = I.gauge_links(L, EPS_LINKS, 1)
+    P0 = I.momenta(L, 3)
+    eta = ctx.pack_spinor(L, I.gaussian_half(L, 2), hmc.F64)
+    paths = {"fp64": dict(inner_prec=hmc.F64, force_prec=hmc.F64, tol_md=1e-12),
+             "mixed-f64force": dict(inner_prec=hmc.F32, force_prec=hmc.F64, tol_md=1e-10,
+                                    reliable_delta=args.delta),
+             "mixed": dict(inner_prec=hmc.F32, force_prec=hmc.F32, tol_md=1e-10,
+                           reliable_delta=args.delta)}
+    for name, kw in paths.items():
+        for n_md in (10, 20, 40):
+            U = ctx.pack_gauge(L, U0, hmc.F64, hmc.LINK18)
+            P = ctx.pack_algebra(L, P0)
+            t0 = time.time()
+            r = ctx.trajectory(L, U, P, eta, 0.0, beta, kappa, 1.0, n_md, 1,
+                               tol_action=1e-12, **kw)
+            torch.cuda.synchronize()
+            print(json.dumps({"report": "md", "lattice": "16^3x32", "path": name, "dt": 1.0 / n_md,
+                              "dH": r["dH"], "H0": r["H0"], "plaq0": r["plaq0"],
+                              "plaq1": r["plaq1"], "cg_iterations": r["cg_iterations"],
+                              "s": round(time.time() - t0, 3)}), flush=True)
+        # reversibility at dt = 1/10: phi = Mhat^dag eta fixed through both runs
+        U = ctx.pack_gauge(L, U0, hmc.F64, hmc.LINK18)
+        Ucopy = ctx.pack_gauge(L, U0, hmc.F64, hmc.LINK18)
+        Ud = ctx.pack_gauge(L, U0, hmc.F64, hmc.LINK18)
+        phi = ctx.new_spinor(L, hmc.F64)
+        ctx.mhat(L, Ud, phi, eta, kappa, True)
+        P = ctx.pack_algebra(L, P0)
+        mkw = {k: v for k, v in kw.items()}
+        ctx.md_evolve(L, U, P, phi, beta, kappa, 1.0, 10, 1, **mkw)
+        moved = float((ctx.unpack_gauge(L, U) - ctx.unpack_gauge(L, Ucopy)).abs().pow(2).sum())
+        P.data.neg_()
+        ctx.md_evolve(L, U, P, phi, beta, kappa, 1.0, 10, 1, **mkw)
+        delta = float((ctx.unpack_gauge(L, U) - ctx.unpack_gauge(L, Ucopy)).abs().pow(2).sum())
+        print(json.dumps({"report": "md", "lattice": "16^3x32", "path": name,
+                          "reversibility": {"dt": 0.1, "moved": moved, "Delta": delta}}),
+              flush=True)
+
+
 def main():
     args = parse()
-    if args.kernel:
+    if args.report == "md":
+        run_md_report(args)
+    elif args.kernel:
         run_kernel(args)
     elif args.impl == "reference":
         run_reference(args)

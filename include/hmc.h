@@ -298,6 +298,17 @@ int hmc_force_hopexp(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U,
 int hmc_plaquette(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U,
                   double *plaq);
 
+/* hmc_link_gradient: gradient of an action with respect to the complex link
+ * entries, from its Lie-algebra force F (an algebra field as filled by the
+ * force calls; (omega, F) = d/d eps S(exp(eps omega) U), Sec. I).  Writes
+ * G = scale * 2 F U per link, F = sum_a F_a T_a: the solution in the tangent
+ * space of SU(3) at U of dS = Re sum conj(G) dU for dU = omega U (the
+ * complex-gradient convention dS/dRe U + i dS/dIm U).  U_canon and G_canon:
+ * device arrays in the canonical gauge order (lex, mu, 3x3 complex, row
+ * major); G must not alias U.  Asynchronous. */
+int hmc_link_gradient(hmc_ctx *ctx, const hmc_lattice *lat, const double *U_canon,
+                      const double *F, double scale, double *G_canon);
+
 /* hmc_poly_apply: out = sum_{i=0}^{degree} c_i K^i in by Horner's scheme
  * (Sec. II), K = kappa^2 H_eo H_oe; in/out even fields of precision prec,
  * n_rhs = 1.  horner_store (nullable): device buffer of degree+1 fields of

@@ -90,6 +90,7 @@ _SIGS = {
     "hmc_action_pf": (_I, [_P, _P, _P, _P, _P, _D, _P, _D, _P, _P, _P]),
     "hmc_force_hopexp": (_I, [_P, _P, _P, _D, _D, _I, _D, _P, _P]),
     "hmc_plaquette": (_I, [_P, _P, _P, _P]),
+    "hmc_link_gradient": (_I, [_P, _P, _P, _P, _D, _P]),
     "hmc_poly_apply": (_I, [_P, _P, _P, _P, _P, _P, _I, _D, _I, _P]),
     "hmc_update_links": (_I, [_P, _P, _P, _P, _D]),
     "hmc_update_momenta": (_I, [_P, _P, _P, _P, _D]),
@@ -404,6 +405,19 @@ class Context:
         st = lib().hmc_plaquette(self.h, _ref(lattice(L)), ctypes.byref(g), ctypes.byref(out))
         self._check(st, "hmc_plaquette")
         return out.value
+
+    def link_gradient(self, L, U, F, scale=1.0):
+        """G = scale * 2 F U (complex [V,4,3,3]) from an algebra field F and
+        canonical links U (complex [V,4,3,3] on this device)."""
+        self._stream()
+        c = self._canon(U)
+        V = int(np.prod(L))
+        out = self.torch.empty((V, 4, 3, 3, 2), dtype=self.torch.float64,
+                               device=f"cuda:{self.device}")
+        st = lib().hmc_link_gradient(self.h, _ref(lattice(L)), _dp(c), _dp(F.data), float(scale),
+                                     _dp(out))
+        self._check(st, "hmc_link_gradient")
+        return self.torch.view_as_complex(out)
 
     def poly_apply(self, L, U, out, inp, coeffs, kappa, horner_store=None):
         self._stream()
