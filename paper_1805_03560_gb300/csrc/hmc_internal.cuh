@@ -544,22 +544,43 @@ __device__ __forceinline__ void block_partials_rhs(double v, int r, int n_rhs, d
   __syncthreads();
 }
 
-// Last block to arrive sums partials[b * n_rhs + q] over b (index order) into
-// totals[q] for every q, then resets *counter.
+// Strided sum of p[i * stride] for i = threadIdx.x, + NT, ... < n with four
+// independent accumulators, so four loads are in flight per thread (the
+// last block's pass is on the critical path of its kernel).  The assignment
+// of terms to accumulators depends only on n and NT: deterministic.
+template <int NT>
+__device__ __forceinline__ double strided_sum(const double *p, unsigned int n, size_t stride) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  unsigned int i = threadIdx.x;
+  for (; i + 3 * NT < n; i += 4 * NT) {
+    const double a = __ldcg(p + i * stride), b = __ldcg(p + (i + NT) * stride);
+    const double c = __ldcg(p + (i + 2 * NT) * stride), d = __ldcg(p + (i + 3 * NT) * stride);
+    s0 += a;
+    s1 += b;
+    s2 += c;
+    s3 += d;
+  }
+  for (; i < n; i += NT) s0 += __ldcg(p + i * stride);
+  return (s0 + s1) + (s2 + s3);
+}
+
+// Last block to arrive sums partials[b * n_rhs + q] over b into totals[q]
+// for every q, then resets *counter.  Precondition: threads q < n_rhs of the
+// block stored the block's partials (block_partials_rhs).  Only those
+// threads fence: a fence waits for all of the thread's earlier stores, and a
+// fence in every thread would hold every block for a store round trip.
 template <int NT>
 __device__ __forceinline__ void last_block_totals_rhs(const double *partials, int n_rhs,
                                                       unsigned int *counter, double *totals) {
   __shared__ bool s_last_r;
-  __threadfence();
+  if ((int)threadIdx.x < n_rhs) __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) s_last_r = atomicAdd(counter, 1u) == gridDim.x - 1;
   __syncthreads();
   if (!s_last_r) return;
   __threadfence();
   for (int q = 0; q < n_rhs; ++q) {
-    double s = 0.0;
-    for (unsigned int b = threadIdx.x; b < gridDim.x; b += NT)
-      s += __ldcg(partials + (size_t)b * n_rhs + q);
+    double s = strided_sum<NT>(partials + q, gridDim.x, (size_t)n_rhs);
     s = block_sum<NT>(s);
     if (threadIdx.x == 0) totals[q] = s;
     __syncthreads();
@@ -569,20 +590,21 @@ __device__ __forceinline__ void last_block_totals_rhs(const double *partials, in
 
 // Called by every thread of every block after thread 0 of the block has
 // stored its partial sum in partials[blockIdx.x]: the last block to arrive
-// sums all partials in index order (the same order whichever block is last,
-// so the result is deterministic) into *total and resets *counter to 0.
+// sums all partials (in an order fixed by the grid size, whichever block is
+// last, so the result is deterministic) into *total and resets *counter.
+// Only thread 0 fences before its arrival (see last_block_totals_rhs).
 template <int NT>
 __device__ __forceinline__ void last_block_total(const double *partials, unsigned int *counter,
                                                  double *total) {
   __shared__ bool s_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  double s = 0.0;
-  for (unsigned int i = threadIdx.x; i < gridDim.x; i += NT) s += __ldcg(partials + i);
+  double s = strided_sum<NT>(partials, gridDim.x, 1);
   s = block_sum<NT>(s);
   if (threadIdx.x == 0) {
     *total = s;

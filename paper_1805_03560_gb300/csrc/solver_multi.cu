@@ -102,8 +102,9 @@ __global__ void __launch_bounds__(BL_NT) k_mcg_xpay(void *p, const void *r, int 
     }
   }
   // the state advances in the last block, after every block has used it
+  // (each block's reads of the state are complete at the barrier; the
+  // values this kernel stores are not read by the last block, so no fence)
   __shared__ bool s_last;
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) s_last = atomicAdd(&st->cnt[0], 1u) == gridDim.x - 1;
   __syncthreads();
