@@ -91,6 +91,9 @@ def _declare(l):
         "or_gauge_force": (None, [_P, _P, _D, _D, _P]),
         "or_pf_action": (_D, [_P, _P, _D, _P, _D]),
         "or_pf_force": (None, [_P, _P, _D, _P, _D, _D, _P]),
+        "or_ratio_action": (_D, [_P, _P, _D, _D, _P, _D]),
+        "or_ratio_force": (None, [_P, _P, _D, _D, _P, _D, _D, _P]),
+        "or_ratio_heatbath": (None, [_P, _P, _D, _D, _P, _D, _P]),
         "or_hop_force": (None, [_P, _P, _D, _P, _P, _D, _P]),
         "or_trace_K_brute": (_D, [_P, _P, _D, _I]),
         "or_trace_H_paths": (_D, [_P, _P, _I]),
@@ -248,6 +251,26 @@ def pf_force(L, U, kappa, phi, tol=1e-13):
     F = _force_buf(L)
     lib().or_pf_force(_dims(L), _ptr(U), kappa, _ptr(phi), tol, 1.0, _ptr(F))
     return F
+
+
+def ratio_action(L, U, kappa_a, kappa_b, phi, tol=1e-13):
+    """Hasenbusch ratio term |Mhat_a^dag Mhat_b^{-dag} phi|^2 (kappa_a = 0: plain)."""
+    U = _c(U, np.complex128); phi = _c(phi, np.complex128)
+    return lib().or_ratio_action(_dims(L), _ptr(U), kappa_a, kappa_b, _ptr(phi), tol)
+
+
+def ratio_force(L, U, kappa_a, kappa_b, phi, tol=1e-13):
+    U = _c(U, np.complex128); phi = _c(phi, np.complex128)
+    F = _force_buf(L)
+    lib().or_ratio_force(_dims(L), _ptr(U), kappa_a, kappa_b, _ptr(phi), tol, 1.0, _ptr(F))
+    return F
+
+
+def ratio_heatbath(L, U, kappa_a, kappa_b, eta, tol=1e-13):
+    U = _c(U, np.complex128); eta = _c(eta, np.complex128)
+    out = np.zeros_like(eta)
+    lib().or_ratio_heatbath(_dims(L), _ptr(U), kappa_a, kappa_b, _ptr(eta), tol, _ptr(out))
+    return out
 
 
 def hop_force(L, U, kappa, W, Vf):

@@ -127,6 +127,20 @@ void or_filtered_force(const int L[4], const ocplx *U, double kappa,
                        const double *b, int n_t, double alpha,
                        const ocplx *phi, double tol, double coeff, double *F);
 
+/* ---- mass-preconditioned (Hasenbusch) terms (mp.c) ------------------------ */
+/* S_R = |Mhat(kappa_a)^dag Mhat(kappa_b)^{-dag} phi|^2; kappa_a = 0 means
+ * Mhat_a = 1 (the plain S_PF at kappa_b) */
+double or_ratio_action(const int L[4], const ocplx *U, double kappa_a,
+                       double kappa_b, const ocplx *phi, double tol);
+/* F += coeff * force of S_R */
+void or_ratio_force(const int L[4], const ocplx *U, double kappa_a,
+                    double kappa_b, const ocplx *phi, double tol, double coeff,
+                    double *F);
+/* phi = Mhat_b^dag Mhat_a^{-dag} eta, so that S_R(phi) = |eta|^2 */
+void or_ratio_heatbath(const int L[4], const ocplx *U, double kappa_a,
+                       double kappa_b, const ocplx *eta, double tol,
+                       ocplx *phi);
+
 /* ---- molecular dynamics (md.c) --------------------------------------------- */
 /* expo = exp(A) for a 3x3 complex matrix (scaling and squaring of Taylor) */
 void or_expm3(const ocplx A[9], ocplx expo[9]);
