@@ -119,8 +119,25 @@ double or_kinetic(const int L[4], const double *P) {
   return 0.5 * s;
 }
 
+/* hopping parameters (kappa_a, kappa_b) of pseudo-fermion term j of a
+ * mass-preconditioned chain (kappa_a = 0: the plain term) */
+static void mp_pair(const or_traj_params *p, int j, double *ka, double *kb) {
+  *ka = j == 0 ? 0.0 : p->kappa_mp[j - 1];
+  *kb = j < p->n_mp ? p->kappa_mp[j] : p->kappa;
+}
+
 static double fermion_action(const int L[4], const ocplx *U, const ocplx *phi,
                              const or_traj_params *p) {
+  if (p->n_mp > 0) {
+    long n12 = or_volume(L) / 2 * 12;
+    double s = 0;
+    for (int j = 0; j <= p->n_mp; ++j) {
+      double ka, kb;
+      mp_pair(p, j, &ka, &kb);
+      s += or_ratio_action(L, U, ka, kb, phi + j * n12, p->tol_action);
+    }
+    return s;
+  }
   if (p->filter_k == 0) return or_pf_action(L, U, p->kappa, phi, p->tol_action);
   return or_filtered_action(L, U, p->kappa, p->b, p->n_max, p->alpha, phi,
                             p->tol_action);
@@ -149,7 +166,14 @@ static void fermion_force(const int L[4], const ocplx *U, const ocplx *phi,
                           const or_traj_params *p, double *F) {
   long nP = or_volume(L) * 32;
   memset(F, 0, nP * sizeof(double));
-  if (p->filter_k == 0)
+  if (p->n_mp > 0) {
+    long n12 = or_volume(L) / 2 * 12;
+    for (int j = 0; j <= p->n_mp; ++j) {
+      double ka, kb;
+      mp_pair(p, j, &ka, &kb);
+      or_ratio_force(L, U, ka, kb, phi + j * n12, p->tol_md, 1.0, F);
+    }
+  } else if (p->filter_k == 0)
     or_pf_force(L, U, p->kappa, phi, p->tol_md, 1.0, F);
   else
     or_filtered_force(L, U, p->kappa, p->b, p->n_t, p->alpha, phi, p->tol_md,
@@ -182,14 +206,25 @@ int or_trajectory(const int L[4], ocplx *U, const double *P0, const ocplx *eta,
                   double u_metropolis, const or_traj_params *p,
                   or_traj_result *res, ocplx *U_out, double *P_out) {
   long V = or_volume(L), n12 = V / 2 * 12, nU = V * 4 * 9, nP = V * 32;
-  ocplx *phi = malloc(n12 * sizeof(ocplx));
+  const int n_terms = p->n_mp > 0 ? p->n_mp + 1 : 1;
+  ocplx *phi = malloc(n_terms * n12 * sizeof(ocplx));
   ocplx *U1 = malloc(nU * sizeof(ocplx));
   double *P = malloc(nP * sizeof(double));
   memcpy(U1, U, nU * sizeof(ocplx));
   memcpy(P, P0, nP * sizeof(double));
   /* heatbath of the pseudo-fermion field */
   double H0;
-  if (p->filter_k == 0) {
+  if (p->n_mp > 0) {
+    /* phi_j = Mhat_b^dag Mhat_a^{-dag} eta_j: S_j(phi_j) = |eta_j|^2 */
+    double e2 = 0;
+    for (int j = 0; j < n_terms; ++j) {
+      double ka, kb;
+      mp_pair(p, j, &ka, &kb);
+      or_ratio_heatbath(L, U, ka, kb, eta + j * n12, p->tol_action, phi + j * n12);
+    }
+    for (long i = 0; i < n_terms * n12; ++i) e2 += creal(conj(eta[i]) * eta[i]);
+    H0 = or_kinetic(L, P) + or_gauge_action(L, U, p->beta) + e2;
+  } else if (p->filter_k == 0) {
     or_mhat(L, U, p->kappa, 1, eta, phi); /* phi = Mhat^dag eta */
     double e2 = 0;
     for (long i = 0; i < n12; ++i) e2 += creal(conj(eta[i]) * eta[i]);

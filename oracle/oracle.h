@@ -166,6 +166,13 @@ typedef struct {
    * phi = Mtilde eta = Mhat sum c_n K^n eta */
   const double *b, *c;
   double alpha;
+  /* mass preconditioning (requires filter_k == 0): n_mp >= 1 heavier
+   * hopping parameters kappa_mp[0] < ... < kappa_mp[n_mp-1] < kappa split
+   * the pseudo-fermion action into n_mp + 1 terms, S_PF(kappa_mp[0]) +
+   * S_R(kappa_mp[j-1], kappa_mp[j]) + S_R(kappa_mp[n_mp-1], kappa); eta and
+   * phi then hold n_mp + 1 consecutive half fields.  n_mp = 0: one term. */
+  int n_mp;
+  const double *kappa_mp;
 } or_traj_params;
 
 typedef struct {

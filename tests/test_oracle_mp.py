@@ -97,3 +97,36 @@ def test_ratio_force_finite_differences(orc, ka, kb):
         fd = (-f(2 * e) + 8 * f(e) - 8 * f(-e) + f(-2 * e)) / (12 * e)
         got = float(np.dot(F[site, mu], om))
         assert abs(got - fd) <= 1e-6 * max(abs(fd), scale), (site, mu, got, fd)
+
+
+def _mp_kw(n_md=4):
+    return dict(beta=5.6, kappa=K, tau=0.5, n_md=n_md, n_gauge=2, tol_md=1e-13,
+                tol_action=1e-13, kappa_mp=[K1, K2])
+
+
+def test_mp_hamiltonian_at_start_equals_heatbath(orc):
+    """H(U, P, phi) with phi from the chain's heatbath is kinetic + S_G + |eta|^2."""
+    L = (4, 4, 4, 4)
+    U = I.gauge_links(L, 0.3, 1)
+    P = I.momenta(L, 3)
+    eta = np.stack([I.gaussian_half(L, 20 + j) for j in range(3)])
+    phi = np.stack([orc.ratio_heatbath(L, U, ka, kb, eta[j], tol=1e-14)
+                    for j, (ka, kb) in enumerate(((0.0, K1), (K1, K2), (K2, K)))])
+    h = orc.hamiltonian(L, U, P, phi, **_mp_kw())
+    want = orc.kinetic(L, P) + orc.gauge_action(L, U, 5.6) + np.sum(np.abs(eta) ** 2)
+    assert abs(h - want) <= 1e-10 * abs(want)
+
+
+def test_mp_trajectory_dt_scaling_and_reversibility(orc):
+    L = (4, 4, 4, 4)
+    U = I.gauge_links(L, 0.3, 1)
+    P = I.momenta(L, 3)
+    eta = np.stack([I.gaussian_half(L, 20 + j) for j in range(3)])
+    dH = [orc.trajectory(L, U, P, eta, 0.0, **_mp_kw(n))[1]["dH"] for n in (4, 8)]
+    assert 3.5 < dH[0] / dH[1] < 4.5, dH
+    phi = np.stack([orc.ratio_heatbath(L, U, ka, kb, eta[j], tol=1e-14)
+                    for j, (ka, kb) in enumerate(((0.0, K1), (K1, K2), (K2, K)))])
+    U1, P1 = orc.md_evolve(L, U, P, phi, **_mp_kw())
+    U2, _ = orc.md_evolve(L, U1, -P1, phi, **_mp_kw())
+    assert np.sum(np.abs(U1 - U) ** 2) > 1e-3
+    assert np.sum(np.abs(U2 - U) ** 2) < 1e-20
