@@ -318,6 +318,45 @@ int hmc_poly_apply(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U,
                    void *out, const void *in, const double *coeffs, int degree,
                    double kappa, int prec, void *horner_store);
 
+/* ---- mass preconditioning --------------------------------------------------------
+ * Sec. I motivates splitting det Mhat^dag Mhat over heavier auxiliary hopping
+ * parameters without writing the actions out.  Reading: the ratio form, in
+ * the gamma_5-equivalent convention of the plain action,
+ *   S_R(phi; kappa_a, kappa_b) = |Mhat(kappa_a)^dag Mhat(kappa_b)^{-dag} phi|^2,
+ * whose Gaussian integral over phi is det(Mhat_b^dag Mhat_b) /
+ * det(Mhat_a^dag Mhat_a); kappa_a = 0 means Mhat_a = 1 (the plain S_PF at
+ * kappa_b).  The calls below take n_terms (1..16) terms at once: phi / eta
+ * are n_terms consecutive F64 even fields (n_rhs = 1 layout, field j at byte
+ * offset j * hmc_spinor_bytes(lat, HMC_F64, 1)), kappa_a / kappa_b host
+ * arrays with 0 <= kappa_a[j] < kappa_b[j] (else HMC_EINVAL).  The terms
+ * share the links, so their solves run as multi-right-hand-side CGs (one per
+ * solve stage), every hemi-Dslash launch serving all terms.  U_hi, U_lo and
+ * opts as for hmc_cg_solve; stats (nullable) sums the stages (per stage the
+ * largest count over the batched systems).  Blocking. */
+
+/* F += coeff * sum_j force of S_R(phi_j): with chi = Mhat_b^{-dag} phi,
+ * psi = Mhat_a^dag chi, xi = Mhat_b^{-1} Mhat_a psi,
+ * delta S_R = 2 Re[chi^dag dMhat_a psi] - 2 Re[chi^dag dMhat_b xi].
+ * opts->force_prec as for hmc_force_pf. */
+int hmc_force_mp(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
+                 const hmc_gauge *U_lo, const void *phi, int n_terms,
+                 const double *kappa_a, const double *kappa_b, double coeff,
+                 double *F, double tol, const hmc_solver_opts *opts,
+                 hmc_solve_stats *stats);
+/* *action = sum_j S_R(phi_j) (host). */
+int hmc_action_mp(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
+                  const hmc_gauge *U_lo, const void *phi, int n_terms,
+                  const double *kappa_a, const double *kappa_b, double tol,
+                  const hmc_solver_opts *opts, double *action,
+                  hmc_solve_stats *stats);
+/* Heatbath: phi_j = Mhat_b^dag Mhat_a^{-dag} eta_j, so S_R(phi_j) = |eta_j|^2.
+ * phi must not alias eta. */
+int hmc_heatbath_mp(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
+                    const hmc_gauge *U_lo, const void *eta, int n_terms,
+                    const double *kappa_a, const double *kappa_b, double tol,
+                    const hmc_solver_opts *opts, void *phi,
+                    hmc_solve_stats *stats);
+
 /* ---- molecular dynamics -------------------------------------------------------- */
 
 /* hmc_update_links: U <- exp(eps Pi) U with Pi = sum_a P_a T_a (Sec. I, update
@@ -345,6 +384,15 @@ typedef struct {
   double tol_md, tol_action;
   hmc_solver_opts solver; /* inner precision of every solve */
   int link_fmt_lo;        /* format of the inner-precision gauge copy */
+  /* mass preconditioning (Sec. I; requires filter_k == 0): n_mp heavier
+   * hopping parameters kappa_mp[0] < ... < kappa_mp[n_mp-1] < kappa (host
+   * array) split the pseudo-fermion action into n_mp + 1 terms
+   * S_PF(kappa_mp[0]) + sum_j S_R(kappa_mp[j-1], kappa_mp[j]) +
+   * S_R(kappa_mp[n_mp-1], kappa) (see hmc_force_mp), all on the coarse
+   * time scale with their solves batched; eta then holds n_mp + 1
+   * consecutive F64 even fields.  n_mp = 0: one plain or filtered term. */
+  int n_mp;
+  const double *kappa_mp;
 } hmc_traj_params;
 
 typedef struct {
@@ -370,7 +418,9 @@ typedef struct {
  * params->solver.force_prec == HMC_F32 computes the molecular-dynamics forces
  * (gauge force on an F32 copy of the links, pseudo-fermion outer products and
  * filter polynomials) in FP32 with FP64 accumulation; the heatbath, the
- * actions of H0 and H1 and the link updates stay FP64.
+ * actions of H0 and H1 and the link updates stay FP64.  With
+ * params->n_mp > 0, eta holds n_mp + 1 consecutive F64 even fields and the
+ * heatbath is phi_j = Mhat_b^dag Mhat_a^{-dag} eta_j (hmc_heatbath_mp).
  * Blocks; *res is filled on the host. */
 int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U,
                    const hmc_traj_params *params, const double *P,
@@ -382,8 +432,9 @@ int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U,
  * pseudo-fermion field phi held fixed (the phi-algorithm, Sec. I).  With the
  * momenta flipped at the end this runs the trajectory backwards, which is the
  * reversibility test of Sec. IV.  U: F64/LINK18; P: algebra field; phi: F64
- * even field (the heatbath output); res (nullable) receives cg_iterations and
- * solves.  Blocks. */
+ * even field (the heatbath output; n_mp + 1 consecutive fields with mass
+ * preconditioning); res (nullable) receives cg_iterations and solves.
+ * Blocks. */
 int hmc_md_evolve(hmc_ctx *ctx, const hmc_lattice *lat, void *U, double *P,
                   const void *phi, const hmc_traj_params *params,
                   hmc_traj_result *res);

@@ -133,6 +133,24 @@ int cg_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
              const void *b, double kappa, double tol, int max_iter, const hmc_solver_opts *opts,
              hmc_solve_stats *stats);
 
+// batched CG of n_rhs systems with per-system kappas (host array); stats:
+// array of n_rhs (nullable)
+int cg_solve_multi(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul, void *x,
+                   const void *b, const double *kappas, int n_rhs, double tol, int max_iter,
+                   const hmc_solver_opts *opts, hmc_solve_stats *stats);
+
+// mass-preconditioned ratio terms (mp.cu); phi / eta: n consecutive F64 even
+// fields; acc (nullable) accumulates the solver statistics
+int force_mp(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
+             const void *phi, int n, const double *ka, const double *kb, double coeff, double *F,
+             double tol, const hmc_solver_opts *opts, hmc_solve_stats *acc);
+int action_mp(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
+              const void *phi, int n, const double *ka, const double *kb, double tol,
+              const hmc_solver_opts *opts, double *S, hmc_solve_stats *acc);
+int heatbath_mp(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
+                const void *eta, int n, const double *ka, const double *kb, double tol,
+                const hmc_solver_opts *opts, void *phi, hmc_solve_stats *acc);
+
 // dst[0] = sum of partials[0..n) in a fixed order (one block).
 int reduce_partials(hmc_ctx *ctx, const double *partials, int n, double *dst);
 

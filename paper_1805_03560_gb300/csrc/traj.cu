@@ -250,6 +250,17 @@ int action_pf(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *
   return norm2_host(ctx, g, HMC_F64, Z, S);
 }
 
+// Hopping parameters (kappa_a, kappa_b) of the n_mp + 1 terms of a
+// mass-preconditioned chain: (0, k_0), (k_0, k_1), ..., (k_{n-1}, kappa).
+static int mp_pairs(const hmc_traj_params *prm, double *ka, double *kb) {
+  const int n = prm->n_mp;
+  for (int j = 0; j <= n; ++j) {
+    ka[j] = j == 0 ? 0.0 : prm->kappa_mp[j - 1];
+    kb[j] = j < n ? prm->kappa_mp[j] : prm->kappa;
+  }
+  return n + 1;
+}
+
 // Leapfrog on two time scales (Sec. I; gauge on the fine scale, pseudo-fermion
 // on the coarse one, Sec. IV): per coarse step
 //   P_PF(dt/2) [P_G(dt0/2) T(dt0) P_G(dt0/2)]^n_gauge P_PF(dt/2),  dt0 = dt/n_gauge.
@@ -270,12 +281,21 @@ int md_evolve(hmc_ctx *ctx, const Geo &g, void *U1, void *Ulo, double *P, double
   const size_t fbytes = (size_t)g.Vh * 2 * 4 * 8 * sizeof(double);
   cudaStream_t st = ctx->stream;
   const double dt = prm->tau / prm->n_md, dt0 = dt / prm->n_gauge;
+  double ka[16], kb[16];
+  const int n_terms = prm->n_mp > 0 ? mp_pairs(prm, ka, kb) : 0;
   auto pf_step = [&](double eps) -> int {
     TRY(cuda_ok(ctx, cudaMemsetAsync(F, 0, fbytes, st), "md: zero F"));
     if (plo != HMC_F64) TRY(convert_gauge(ctx, g, U1, Ulo, plo, fmt_lo));
-    TRY(force_pf(ctx, g, Uh, Ulp, phi, prm->kappa, filt_md, 1.0, F, prm->tol_md, &prm->solver,
-                 acc));
-    *solves += k ? 2 : 1;
+    if (n_terms) {
+      // all terms of the chain at once: two batched solve stages
+      TRY(force_mp(ctx, g, Uh, Ulp, phi, n_terms, ka, kb, 1.0, F, prm->tol_md, &prm->solver,
+                   acc));
+      *solves += 2;
+    } else {
+      TRY(force_pf(ctx, g, Uh, Ulp, phi, prm->kappa, filt_md, 1.0, F, prm->tol_md, &prm->solver,
+                   acc));
+      *solves += k ? 2 : 1;
+    }
     return update_momenta(ctx, g, P, F, eps);
   };
   // with force_prec F32 the gauge force runs on an F32 copy of the links
@@ -312,6 +332,18 @@ static int check_traj_params(hmc_ctx *ctx, const hmc_traj_params *prm) {
     return fail(ctx, HMC_EINVAL, "trajectory: filter_k must be 0, 1 or 2");
   if (prm->filter_k > 0 && (!prm->b || !prm->c || prm->n_t < 0 || prm->n_max < prm->n_t))
     return fail(ctx, HMC_EINVAL, "trajectory: filter needs b, c and 0 <= n_t <= n_max");
+  if (prm->n_mp < 0 || prm->n_mp > 15)
+    return fail(ctx, HMC_EINVAL, "trajectory: n_mp must be 0..15");
+  if (prm->n_mp > 0) {
+    if (prm->filter_k != 0)
+      return fail(ctx, HMC_EINVAL, "trajectory: mass preconditioning needs filter_k == 0");
+    if (!prm->kappa_mp) return fail(ctx, HMC_EINVAL, "trajectory: kappa_mp is NULL");
+    for (int j = 0; j < prm->n_mp; ++j) {
+      const double nxt = j + 1 < prm->n_mp ? prm->kappa_mp[j + 1] : prm->kappa;
+      if (!(prm->kappa_mp[j] > 0.0) || !(prm->kappa_mp[j] < nxt))
+        return fail(ctx, HMC_EINVAL, "trajectory: need 0 < kappa_mp[0] < ... < kappa");
+    }
+  }
   return check_prec(ctx, prm->solver.inner_prec);
 }
 
@@ -453,7 +485,10 @@ int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj
   void *U1 = workspace(ctx, "tr_u1", gb);
   void *Ulo = plo != HMC_F64 ? workspace(ctx, "tr_ulo", gauge_bytes(g, plo, fmt_lo)) : nullptr;
   double *P = (double *)workspace(ctx, "tr_p", ab), *F = (double *)workspace(ctx, "tr_f", ab);
-  void *phi = workspace(ctx, "tr_phi", f64), *t1 = workspace(ctx, "tr_t1", f64);
+  double ka[16], kb[16];
+  const int n_terms = prm->n_mp > 0 ? mp_pairs(prm, ka, kb) : 0;
+  void *phi = workspace(ctx, "tr_phi", f64 * (n_terms ? n_terms : 1));
+  void *t1 = workspace(ctx, "tr_t1", f64);
   void *t2 = workspace(ctx, "tr_t2", f64);
   if (!U1 || (plo != HMC_F64 && !Ulo) || !P || !F || !phi || !t1 || !t2) return HMC_ENOMEM;
   cudaStream_t st = ctx->stream;
@@ -472,7 +507,19 @@ int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj
   hmc_solve_stats acc{};
   // heatbath of the pseudo-fermion field and H0
   double kin0, sg0, spf0;
-  if (k == 0) {
+  if (n_terms) {
+    // phi_j = Mhat_b^dag Mhat_a^{-dag} eta_j: the start action is sum |eta_j|^2
+    TRY(refresh_lo());
+    TRY(heatbath_mp(ctx, g, Uh, Ulp, eta, n_terms, ka, kb, prm->tol_action, &prm->solver, phi,
+                    &acc));
+    spf0 = 0.0;
+    for (int j = 0; j < n_terms; ++j) {
+      double e2;
+      TRY(norm2_host(ctx, g, HMC_F64, (const char *)eta + f64 * j, &e2));
+      spf0 += e2;
+    }
+    res->solves += 1;
+  } else if (k == 0) {
     TRY(mhat(ctx, g, Uh, HMC_F64, 1, 1, phi, eta, t1, prm->kappa, nullptr, nullptr, nullptr));
     TRY(norm2_host(ctx, g, HMC_F64, eta, &spf0));  // S_PF(Mhat^dag eta) = |eta|^2
   } else {
@@ -494,8 +541,12 @@ int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj
   TRY(hmc_kinetic(ctx, lat, P, &kin1));
   TRY(gauge_action(ctx, g, Uh, prm->beta, prm->kappa, k, &sg1, &ps1));
   TRY(refresh_lo());
-  TRY(action_pf(ctx, g, Uh, Ulp, phi, prm->kappa, filt_act, prm->tol_action, &prm->solver, &spf1,
-                &acc));
+  if (n_terms)
+    TRY(action_mp(ctx, g, Uh, Ulp, phi, n_terms, ka, kb, prm->tol_action, &prm->solver, &spf1,
+                  &acc));
+  else
+    TRY(action_pf(ctx, g, Uh, Ulp, phi, prm->kappa, filt_act, prm->tol_action, &prm->solver,
+                  &spf1, &acc));
   res->solves += 1;
   res->H1 = kin1 + sg1 + spf1;
   res->dH = res->H1 - res->H0;

@@ -49,7 +49,8 @@ class TrajParams(ctypes.Structure):
                 ("n_md", _I), ("n_gauge", _I), ("filter_k", _I), ("n_t", _I), ("n_max", _I),
                 ("b", _P), ("c", _P), ("alpha", _D),
                 ("tol_md", _D), ("tol_action", _D),
-                ("solver", SolverOpts), ("link_fmt_lo", _I)]
+                ("solver", SolverOpts), ("link_fmt_lo", _I),
+                ("n_mp", _I), ("kappa_mp", _P)]
 
 
 class TrajResult(ctypes.Structure):
@@ -97,6 +98,9 @@ _SIGS = {
     "hmc_kinetic": (_I, [_P, _P, _P, _P]),
     "hmc_trajectory": (_I, [_P, _P, _P, _P, _P, _P, _D, _P, _P, _P]),
     "hmc_filter_coeffs": (_I, [_I, _I, _P, _P, _P]),
+    "hmc_force_mp": (_I, [_P, _P, _P, _P, _P, _I, _P, _P, _D, _P, _D, _P, _P]),
+    "hmc_action_mp": (_I, [_P, _P, _P, _P, _P, _I, _P, _P, _D, _P, _P, _P]),
+    "hmc_heatbath_mp": (_I, [_P, _P, _P, _P, _P, _I, _P, _P, _D, _P, _P, _P]),
     "hmc_md_evolve": (_I, [_P, _P, _P, _P, _P, _P, _P]),
 }
 
@@ -406,6 +410,85 @@ class Context:
         self._check(st, "hmc_plaquette")
         return out.value
 
+    @staticmethod
+    def _mp(prm, kappa_mp, keep):
+        if kappa_mp:
+            km = np.ascontiguousarray(kappa_mp, dtype=np.float64)
+            keep.append(km)
+            prm.n_mp = len(km)
+            prm.kappa_mp = km.ctypes.data
+
+    def pack_spinors(self, L, fields):
+        """n F64 even fields stored one after another (not interleaved), the
+        layout of the pseudo-fermion fields of a mass-preconditioned chain."""
+        nb = int(lib().hmc_spinor_bytes(_ref(lattice(L)), F64, 1))
+        out = Field(self._bytes(nb * len(fields)), "spinor", F64, 1)
+        out.n_fields = len(fields)
+        for j, f in enumerate(fields):
+            one = self.pack_spinor(L, f, F64)
+            out.data[j * nb:(j + 1) * nb].copy_(one.data)
+        return out
+
+    def unpack_spinors(self, L, f):
+        nb = int(lib().hmc_spinor_bytes(_ref(lattice(L)), F64, 1))
+        res = []
+        for j in range(f.data.numel() // nb):
+            one = Field(f.data[j * nb:(j + 1) * nb], "spinor", F64, 1)
+            res.append(self.unpack_spinor(L, one))
+        return self.torch.stack(res)
+
+    def _mp_args(self, kappa_a, kappa_b, keep):
+        ka = np.ascontiguousarray(kappa_a, dtype=np.float64)
+        kb = np.ascontiguousarray(kappa_b, dtype=np.float64)
+        keep += [ka, kb]
+        return len(ka), ka.ctypes.data_as(_P), kb.ctypes.data_as(_P)
+
+    def force_mp(self, L, U_hi, phis, kappa_a, kappa_b, F, coeff=1.0, tol=1e-12, U_lo=None,
+                 inner_prec=F64, reliable_delta=0.1, force_prec=F64):
+        """F += coeff * sum_j force of |Mhat(ka_j)^dag Mhat(kb_j)^{-dag} phi_j|^2."""
+        self._stream()
+        keep = []
+        n, ka, kb = self._mp_args(kappa_a, kappa_b, keep)
+        gh = U_hi.gauge()
+        gl = U_lo.gauge() if U_lo is not None else None
+        opts = SolverOpts(inner_prec, reliable_delta, 16, force_prec)
+        stats = SolveStats()
+        st = lib().hmc_force_mp(self.h, _ref(lattice(L)), ctypes.byref(gh),
+                                ctypes.byref(gl) if gl is not None else None, phis.ptr(), n, ka,
+                                kb, coeff, _dp(F.data), tol, ctypes.byref(opts),
+                                ctypes.byref(stats))
+        self._check(st, "hmc_force_mp")
+        return {f: getattr(stats, f) for f, _ in SolveStats._fields_}
+
+    def action_mp(self, L, U_hi, phis, kappa_a, kappa_b, tol=1e-13, U_lo=None, inner_prec=F64):
+        self._stream()
+        keep = []
+        n, ka, kb = self._mp_args(kappa_a, kappa_b, keep)
+        gh = U_hi.gauge()
+        gl = U_lo.gauge() if U_lo is not None else None
+        opts = SolverOpts(inner_prec, 0.1, 16)
+        out = ctypes.c_double(0)
+        st = lib().hmc_action_mp(self.h, _ref(lattice(L)), ctypes.byref(gh),
+                                 ctypes.byref(gl) if gl is not None else None, phis.ptr(), n, ka,
+                                 kb, tol, ctypes.byref(opts), ctypes.byref(out), None)
+        self._check(st, "hmc_action_mp")
+        return out.value
+
+    def heatbath_mp(self, L, U_hi, etas, kappa_a, kappa_b, tol=1e-13, U_lo=None,
+                    inner_prec=F64):
+        self._stream()
+        keep = []
+        n, ka, kb = self._mp_args(kappa_a, kappa_b, keep)
+        gh = U_hi.gauge()
+        gl = U_lo.gauge() if U_lo is not None else None
+        opts = SolverOpts(inner_prec, 0.1, 16)
+        out = Field(self._bytes(etas.data.numel()), "spinor", F64, 1)
+        st = lib().hmc_heatbath_mp(self.h, _ref(lattice(L)), ctypes.byref(gh),
+                                   ctypes.byref(gl) if gl is not None else None, etas.ptr(), n,
+                                   ka, kb, tol, ctypes.byref(opts), out.ptr(), None)
+        self._check(st, "hmc_heatbath_mp")
+        return out
+
     def link_gradient(self, L, U, F, scale=1.0):
         """G = scale * 2 F U (complex [V,4,3,3]) from an algebra field F and
         canonical links U (complex [V,4,3,3] on this device)."""
@@ -449,9 +532,11 @@ class Context:
     def trajectory(self, L, U, P, eta, u, beta, kappa, tau, n_md, n_gauge, filter_k=0, n_t=0,
                    n_max=0, b=None, c=None, alpha=0.0, tol_md=1e-10, tol_action=1e-12,
                    inner_prec=F64, link_fmt_lo=LINK12, reliable_delta=0.1, U_end=None,
-                   P_end=None, force_prec=F64):
+                   P_end=None, force_prec=F64, kappa_mp=None):
         """One HMC trajectory; U (F64/LINK18 gauge Field) is updated in place
-        when accepted.  Returns the result as a dict."""
+        when accepted.  Returns the result as a dict.  kappa_mp: heavier
+        hopping parameters of a mass-preconditioned chain (eta then from
+        pack_spinors with len(kappa_mp) + 1 fields)."""
         self._stream()
         keep = []
         prm = TrajParams(beta=beta, kappa=kappa, tau=tau, n_md=n_md, n_gauge=n_gauge,
@@ -459,6 +544,7 @@ class Context:
                          tol_action=tol_action,
                          solver=SolverOpts(inner_prec, reliable_delta, 16, force_prec),
                          link_fmt_lo=link_fmt_lo)
+        self._mp(prm, kappa_mp, keep)
         if b is not None:
             ab = np.ascontiguousarray(b, dtype=np.float64); keep.append(ab); prm.b = ab.ctypes.data
         if c is not None:
@@ -473,7 +559,7 @@ class Context:
 
     def md_evolve(self, L, U, P, phi, beta, kappa, tau, n_md, n_gauge, filter_k=0, n_t=0,
                   b=None, alpha=0.0, tol_md=1e-10, inner_prec=F64, link_fmt_lo=LINK12,
-                  reliable_delta=0.1, force_prec=F64):
+                  reliable_delta=0.1, force_prec=F64, kappa_mp=None):
         """Molecular dynamics with phi fixed; U (F64/LINK18) and P updated in place."""
         self._stream()
         keep = []
@@ -482,6 +568,7 @@ class Context:
                          tol_action=tol_md,
                          solver=SolverOpts(inner_prec, reliable_delta, 16, force_prec),
                          link_fmt_lo=link_fmt_lo)
+        self._mp(prm, kappa_mp, keep)
         if b is not None:
             ab = np.ascontiguousarray(b, dtype=np.float64); keep.append(ab)
             prm.b = ab.ctypes.data
