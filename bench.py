@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--kernel", default=None,
                     help="time one hemi-Dslash variant alone, e.g. f16-12 (for profiling)")
     ap.add_argument("--launches", type=int, default=20)
+    ap.add_argument("--mp", action="store_true",
+                    help="mass-preconditioned workload: pseudo-fermions at kappa' = 0.150, "
+                         "0.154 and the target kappa (ratio terms, batched solves), no filter")
     ap.add_argument("--report", default=None, choices=["md"],
                     help="md: leapfrog dH at dt = 1/10, 1/20, 1/40 and reversibility on "
                          "16^3x32, kappa 0.156, plain pseudo-fermion action")
@@ -237,11 +240,18 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def build_inputs(rank):
+KAPPA_MP = [0.150, 0.154]
+
+
+def build_inputs(rank, n_eta=1):
     from paper_1805_03560_gb300 import inputs as I
+    import numpy as np
     U = I.gauge_links(LAT, EPS_LINKS, seed=1 + 100 * rank)
     P = I.momenta(LAT, seed=3 + 100 * rank)
-    eta = I.gaussian_half(LAT, seed=2 + 100 * rank)
+    if n_eta == 1:
+        eta = I.gaussian_half(LAT, seed=2 + 100 * rank)
+    else:
+        eta = np.stack([I.gaussian_half(LAT, seed=2 + 100 * rank + 1000 * j) for j in range(n_eta)])
     return U, P, eta
 
 
@@ -286,20 +296,26 @@ def run_hmc(args):
 
     inner = hmc.F16 if args.inner == "f16" else hmc.F32
     ctx = hmc.Context(local)
-    U, P, eta = build_inputs(rank)
+    n_eta = len(KAPPA_MP) + 1 if args.mp else 1
+    U, P, eta = build_inputs(rank, n_eta)
     b, alpha, c = coeffs()
     U0 = ctx.pack_gauge(LAT, U, hmc.F64, hmc.LINK18)
     Ud = ctx.new_gauge(LAT, hmc.F64, hmc.LINK18)
     Pd = ctx.pack_algebra(LAT, P)
-    ed = ctx.pack_spinor(LAT, eta, hmc.F64)
+    ed = ctx.pack_spinors(LAT, list(eta)) if args.mp else ctx.pack_spinor(LAT, eta, hmc.F64)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     fprec = hmc.F32 if args.force_prec == "f32" else hmc.F64
     work = dict(WORK)
     if args.n_md:
         work["tau"] = WORK["tau"] * args.n_md / WORK["n_md"]
         work["n_md"] = args.n_md
-    kw = dict(work, b=b, c=c, alpha=alpha, inner_prec=inner, link_fmt_lo=hmc.LINK12,
-              reliable_delta=args.delta, force_prec=fprec)
+    if args.mp:
+        work.update(filter_k=0, n_t=0, n_max=0)
+        kw = dict(work, kappa_mp=KAPPA_MP, inner_prec=inner, link_fmt_lo=hmc.LINK12,
+                  reliable_delta=args.delta, force_prec=fprec)
+    else:
+        kw = dict(work, b=b, c=c, alpha=alpha, inner_prec=inner, link_fmt_lo=hmc.LINK12,
+                  reliable_delta=args.delta, force_prec=fprec)
     stream = torch.cuda.current_stream()
 
     def one(kwargs):
@@ -363,7 +379,9 @@ def run_hmc(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.inner,
         "data": "synthetic (seeded exp(i 0.3 A) links, Gaussian momenta and sources)",
-        "config": {"workload": "hmc-trajectory 24^3x48 kappa=0.1575 beta=5.6 kappa^4-filter",
+        "config": {"workload": ("hmc-trajectory 24^3x48 kappa=0.1575 beta=5.6 mass-preconditioned "
+                                 "kappa'=0.150,0.154 (batched solves)" if args.mp else
+                                 "hmc-trajectory 24^3x48 kappa=0.1575 beta=5.6 kappa^4-filter"),
                    "lattice": "x".join(str(v) for v in LAT[::-1]), **{k: v for k, v in work.items()},
                    "inner_prec": args.inner, "reliable_delta": args.delta,
                    "force_prec": args.force_prec, "links": "12-real (inner), 18-real FP64",
@@ -418,7 +436,9 @@ def run_hmc(args):
         ecd = torch.empty(eh.shape, dtype=torch.float64, device="cuda")
         Ue = ctx.new_gauge(LAT, hmc.F64, hmc.LINK18)
         Pe = ctx.new_algebra(LAT)
-        ee = ctx.new_spinor(LAT, hmc.F64)
+        nb1 = int(hmc.lib().hmc_spinor_bytes(hmc._ref(hmc.lattice(LAT)), hmc.F64, 1))
+        ee = hmc.Field(torch.empty(nb1 * n_eta, dtype=torch.uint8, device="cuda"), "spinor",
+                       hmc.F64, 1)
         lat = hmc.lattice(LAT)
         lib = hmc.lib()
         import ctypes
@@ -432,8 +452,11 @@ def run_hmc(args):
                                           Ue.ptr(), hmc.F64, hmc.LINK18), "pack")
             ctx._check(lib.hmc_pack_algebra(ctx.h, ctypes.byref(lat), ctypes.c_void_p(Pcd.data_ptr()),
                                             ctypes.c_void_p(Pe.data.data_ptr())), "pack")
-            ctx._check(lib.hmc_pack_spinor(ctx.h, ctypes.byref(lat), ctypes.c_void_p(ecd.data_ptr()),
-                                           ee.ptr(), hmc.F64, 1), "pack")
+            for j in range(n_eta):  # one F64 field per pseudo-fermion term
+                src = ecd.data_ptr() + j * (ecd.numel() // n_eta) * 8
+                ctx._check(lib.hmc_pack_spinor(ctx.h, ctypes.byref(lat), ctypes.c_void_p(src),
+                                               ctypes.c_void_p(ee.data.data_ptr() + j * nb1),
+                                               hmc.F64, 1), "pack")
             r = ctx.trajectory(LAT, Ue, Pe, ee, 0.5, **kw)
             ctx._check(lib.hmc_unpack_gauge(ctx.h, ctypes.byref(lat), Ue.ptr(), hmc.F64, hmc.LINK18,
                                             ctypes.c_void_p(Ucd.data_ptr())), "unpack")

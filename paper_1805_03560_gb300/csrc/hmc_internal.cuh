@@ -527,9 +527,32 @@ __device__ __forceinline__ void store_as(void *base, int S, int s, const Cx<R> v
 
 // Per-right-hand-side block sums.  Each thread holds value v of right-hand
 // side r (r < 0: none); for every q < n_rhs the block writes
-// partials[blockIdx.x * n_rhs + q], summing its threads in index order.
+// partials[blockIdx.x * n_rhs + q].  Up to 16 right-hand sides: one masked
+// shuffle reduction per q and warp, then the warps' sums in warp order (a
+// fixed order, so the sums are deterministic); more: a serial pass over the
+// block's values in thread order.
 template <int NT>
 __device__ __forceinline__ void block_partials_rhs(double v, int r, int n_rhs, double *partials) {
+  constexpr int NW = NT / 32;
+  if (n_rhs <= 16) {
+    __shared__ double red[16][NW];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int q = 0; q < n_rhs; ++q) {
+      double x = r == q ? v : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (l == 0) red[q][w] = x;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < n_rhs) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < NW; ++k) s += red[threadIdx.x][k];
+      partials[(size_t)blockIdx.x * n_rhs + threadIdx.x] = s;
+    }
+    __syncthreads();
+    return;
+  }
   __shared__ double sv[NT];
   __shared__ int sr[NT];
   sv[threadIdx.x] = v;
@@ -544,72 +567,99 @@ __device__ __forceinline__ void block_partials_rhs(double v, int r, int n_rhs, d
   __syncthreads();
 }
 
-// Strided sum of p[i * stride] for i = threadIdx.x, + NT, ... < n with four
-// independent accumulators, so four loads are in flight per thread (the
-// last block's pass is on the critical path of its kernel).  The assignment
-// of terms to accumulators depends only on n and NT: deterministic.
-template <int NT>
-__device__ __forceinline__ double strided_sum(const double *p, unsigned int n, size_t stride) {
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  unsigned int i = threadIdx.x;
-  for (; i + 3 * NT < n; i += 4 * NT) {
-    const double a = __ldcg(p + i * stride), b = __ldcg(p + (i + NT) * stride);
-    const double c = __ldcg(p + (i + 2 * NT) * stride), d = __ldcg(p + (i + 3 * NT) * stride);
-    s0 += a;
-    s1 += b;
-    s2 += c;
-    s3 += d;
-  }
-  for (; i < n; i += NT) s0 += __ldcg(p + i * stride);
-  return (s0 + s1) + (s2 + s3);
+// ---- end-of-kernel totals: two-level deterministic reduction ----------------------
+//
+// Every block of a kernel stores its partial sums part[b * n + q] (q < n
+// quantities).  Blocks form groups of red_group_size(nb) consecutive blocks;
+// the last block of a group to arrive (per-group counter) sums the group's
+// partials in block order into part[nb * n + g * n + q]; the last group to
+// finish (counter 0) sums those in group order into totals[q].  Both orders
+// are fixed by the grid size, so the totals are bit-reproducible whichever
+// blocks finish last.  Two short passes replace one pass of a single block
+// over all partials, which is a serial tail of the kernel (one block cannot
+// keep enough loads in flight to read thousands of partials quickly).
+//
+// Storage: part holds red_part_len(nb, n) doubles; counters are
+// 1 + RED_MAX_GROUPS unsigned ints, zero on entry and reset by the finishers.
+
+constexpr int RED_MAX_GROUPS = 1024;
+constexpr int RED_CHUNK = 256;  // doubles staged in shared memory per pass
+
+__host__ __device__ inline int red_group_size(int nb) {
+  const int g = (nb + RED_MAX_GROUPS - 1) / RED_MAX_GROUPS;
+  return g > 64 ? g : 64;
+}
+__host__ __device__ inline size_t red_part_len(int nb, int n) {
+  const int gs = red_group_size(nb);
+  return ((size_t)nb + (nb + gs - 1) / gs) * n;
 }
 
-// Last block to arrive sums partials[b * n_rhs + q] over b into totals[q]
-// for every q, then resets *counter.  Precondition: threads q < n_rhs of the
-// block stored the block's partials (block_partials_rhs).  Only those
-// threads fence: a fence waits for all of the thread's earlier stores, and a
-// fence in every thread would hold every block for a store round trip.
+// out[q] = sum over rows r < m (in row order) of a[r * n + q], for q < n,
+// written by thread q.  a is staged through shared memory in chunks so every
+// thread keeps several loads in flight.
 template <int NT>
-__device__ __forceinline__ void last_block_totals_rhs(const double *partials, int n_rhs,
-                                                      unsigned int *counter, double *totals) {
-  __shared__ bool s_last_r;
-  if ((int)threadIdx.x < n_rhs) __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last_r = atomicAdd(counter, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!s_last_r) return;
-  __threadfence();
-  for (int q = 0; q < n_rhs; ++q) {
-    double s = strided_sum<NT>(partials + q, gridDim.x, (size_t)n_rhs);
-    s = block_sum<NT>(s);
-    if (threadIdx.x == 0) totals[q] = s;
+__device__ __forceinline__ void ordered_column_sums(const double *a, int m, int n, double *out,
+                                                    double *s_val) {
+  double acc = 0.0;
+  const int total = m * n;
+  for (int base = 0; base < total; base += RED_CHUNK) {
+    const int len = min(RED_CHUNK, total - base);
+#pragma unroll 8
+    for (int i = threadIdx.x; i < len; i += NT) s_val[i] = __ldcg(a + base + i);
+    __syncthreads();
+    if ((int)threadIdx.x < n) {
+      int i = ((int)threadIdx.x - base % n + n) % n;  // first element of column q in the chunk
+      for (; i < len; i += n) acc += s_val[i];
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) *counter = 0u;
+  if ((int)threadIdx.x < n) out[threadIdx.x] = acc;
 }
 
-// Called by every thread of every block after thread 0 of the block has
-// stored its partial sum in partials[blockIdx.x]: the last block to arrive
-// sums all partials (in an order fixed by the grid size, whichever block is
-// last, so the result is deterministic) into *total and resets *counter.
-// Only thread 0 fences before its arrival (see last_block_totals_rhs).
+// Precondition: threads q < n of the block stored part[blockIdx.x * n + q].
+// Only those threads fence: a fence waits for all of the thread's earlier
+// stores, and a fence in every thread would hold every block for a store
+// round trip.
 template <int NT>
-__device__ __forceinline__ void last_block_total(const double *partials, unsigned int *counter,
-                                                 double *total) {
-  __shared__ bool s_last;
+__device__ __forceinline__ void finish_totals(double *part, int n, unsigned int *cnt,
+                                              double *totals) {
+  __shared__ int s_flag;
+  __shared__ double s_val[RED_CHUNK];
+  const int nb = gridDim.x, gs = red_group_size(nb), grp = blockIdx.x / gs;
+  const int g0 = grp * gs, gsz = min(gs, nb - g0), ng = (nb + gs - 1) / gs;
+  double *part2 = part + (size_t)nb * n;
+  if ((int)threadIdx.x < n) __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_flag = atomicAdd(&cnt[1 + grp], 1u) == (unsigned)(gsz - 1);
+  __syncthreads();
+  if (!s_flag) return;
+  __threadfence();
+  ordered_column_sums<NT>(part + (size_t)g0 * n, gsz, n, part2 + (size_t)grp * n, s_val);
+  if ((int)threadIdx.x < n) __threadfence();
+  __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    cnt[1 + grp] = 0u;
+    s_flag = atomicAdd(&cnt[0], 1u) == (unsigned)(ng - 1);
   }
   __syncthreads();
-  if (!s_last) return;
+  if (!s_flag) return;
   __threadfence();
-  double s = strided_sum<NT>(partials, gridDim.x, 1);
-  s = block_sum<NT>(s);
-  if (threadIdx.x == 0) {
-    *total = s;
-    *counter = 0u;
-  }
+  ordered_column_sums<NT>(part2, ng, n, totals, s_val);
+  if (threadIdx.x == 0) cnt[0] = 0u;
+}
+
+// Single-quantity form: thread 0 of every block stored partials[blockIdx.x].
+template <int NT>
+__device__ __forceinline__ void last_block_total(double *partials, unsigned int *counters,
+                                                 double *total) {
+  finish_totals<NT>(partials, 1, counters, total);
+}
+
+// Per-right-hand-side form (block_partials_rhs stored the partials).
+template <int NT>
+__device__ __forceinline__ void last_block_totals_rhs(double *partials, int n_rhs,
+                                                      unsigned int *counters, double *totals) {
+  finish_totals<NT>(partials, n_rhs, counters, totals);
 }
 
 }  // namespace hmc

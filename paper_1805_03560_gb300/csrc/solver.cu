@@ -41,7 +41,9 @@ struct CGState {
   int done;       // 1 converged (recursive residual), 2 NaN/Inf
   int active;     // !done
   int iter;
-  unsigned int cnt[2];  // arrival counters of the two last-block reductions
+  // arrival counters of the two end-of-kernel reductions (Dslash p^dag A p,
+  // axpy |r|^2), each 1 + RED_MAX_GROUPS, zero between launches
+  unsigned int cnt[2][1 + RED_MAX_GROUPS];
 };
 
 // ---- reductions --------------------------------------------------------------------
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(BL_NT) k_cg_axpy(void *x, void *r, const void 
   }
   s = block_sum<BL_NT>(s);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
-  last_block_total<BL_NT>(partials, &st->cnt[1], &st->rr_next);
+  last_block_total<BL_NT>(partials, st->cnt[1], &st->rr_next);
 }
 
 // beta = rr_next / rr[par];  p = r + beta p;  rr[par ^ 1] = rr_next.
@@ -260,13 +262,13 @@ __global__ void __launch_bounds__(BL_NT) k_residual(void *r, const void *b, cons
 __global__ void __launch_bounds__(FIN_NT) k_cg_init(CGState *st, const double *partials, int n,
                                                     double tol2) {
   double s = block_sum_of<FIN_NT>(partials, n);
+  for (int i = threadIdx.x; i < 2 * (1 + RED_MAX_GROUPS); i += FIN_NT) (&st->cnt[0][0])[i] = 0u;
   if (threadIdx.x == 0) {
     st->rr[0] = st->rr[1] = s;
     st->b2 = s;
     st->tol2 = tol2;
     st->aux = 0.0;
     st->pap = st->rr_next = 0.0;
-    st->cnt[0] = st->cnt[1] = 0u;
     st->iter = 0;
     st->done = (s == 0.0) ? 1 : (isfinite(s) ? 0 : 2);
     st->active = st->done == 0;
@@ -423,7 +425,7 @@ int one_iteration(Solve &s, int k) {
   a.p = 0; a.out = s.y; a.in = s.tlo; a.x = s.p; a.ca = 1.0; a.cb = -s.kappa * s.kappa;
   a.partials = s.pap_part;
   a.total = &s.st->pap;
-  a.counter = &s.st->cnt[0];
+  a.counter = s.st->cnt[0];
   TRY(dslash(ctx, a, U, s.plo, 0, nullptr));
   a.partials = nullptr;
   a.total = nullptr;
@@ -516,9 +518,11 @@ int cg_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
   const size_t f64 = spinor_bytes(g, HMC_F64, 1);
   const size_t flo = spinor_bytes(g, s.plo, 1);
   const size_t f32 = spinor_bytes(g, HMC_F32, 1);
-  char *stbuf = (char *)workspace(ctx, "cg_state", 256);
+  char *stbuf = (char *)workspace(ctx, "cg_state", sizeof(CGState));
+  // end-of-kernel reductions need red_part_len entries (partials + group sums)
+  const size_t len_ds = red_part_len(s.nb_ds + 64, 1), len_bl = red_part_len(s.nb_bl, 1);
   double *parts = (double *)workspace(ctx, "cg_partials",
-                                      sizeof(double) * (s.nb_ds + 2 * s.nb_bl + 64));
+                                      sizeof(double) * (len_ds + len_bl + s.nb_bl + 64));
   s.r = workspace(ctx, "cg_r64", f64);
   s.q = workspace(ctx, "cg_q64", f64);
   s.y64 = workspace(ctx, "cg_y64", f64);
@@ -526,8 +530,8 @@ int cg_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
   if (!stbuf || !parts || !s.r || !s.q || !s.y64 || !s.t64) return HMC_ENOMEM;
   s.st = (CGState *)stbuf;
   s.pap_part = parts;
-  s.rr_part = parts + s.nb_ds;
-  s.tmp_part = parts + s.nb_ds + s.nb_bl;
+  s.rr_part = parts + len_ds;
+  s.tmp_part = parts + len_ds + len_bl;
   s.x = x;
   s.b = b;
   if (!mixed) {

@@ -31,7 +31,10 @@ struct MState {
   int live[NR_MAX];  // iterating
   int active;        // any live
   int iter;
-  unsigned int cnt[2];
+  // end-of-kernel reductions (Dslash p^dag A p, axpy |r|^2): 1 + RED_MAX_GROUPS
+  // counters each; adv: arrivals of the state-advancing xpay
+  unsigned int cnt[2][1 + RED_MAX_GROUPS];
+  unsigned int adv;
 };
 
 // alpha_q = rr_q / pap_q for live q (0 for frozen);  x += alpha p;  r -= alpha Ap
@@ -76,7 +79,7 @@ __global__ void __launch_bounds__(BL_NT) k_mcg_axpy(void *x, void *r, const void
     store_as<PL>(r, S, i, v);
   }
   block_partials_rhs<BL_NT>(s, q, n_rhs, partials);
-  last_block_totals_rhs<BL_NT>(partials, n_rhs, &st->cnt[1], st->rr_next);
+  last_block_totals_rhs<BL_NT>(partials, n_rhs, st->cnt[1], st->rr_next);
 }
 
 // beta_q = rr_next_q / rr_q;  p = r + beta p  (live q);  state advance
@@ -106,7 +109,7 @@ __global__ void __launch_bounds__(BL_NT) k_mcg_xpay(void *p, const void *r, int 
   // values this kernel stores are not read by the last block, so no fence)
   __shared__ bool s_last;
   __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(&st->cnt[0], 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) s_last = atomicAdd(&st->adv, 1u) == gridDim.x - 1;
   __syncthreads();
   if (!s_last || threadIdx.x != 0) return;
   __threadfence();
@@ -129,7 +132,7 @@ __global__ void __launch_bounds__(BL_NT) k_mcg_xpay(void *p, const void *r, int 
   }
   st->active = any;
   st->iter += 1;
-  st->cnt[0] = 0u;
+  st->adv = 0u;
 }
 
 // per-RHS |v|^2 partials of an F64 field
@@ -177,6 +180,8 @@ __global__ void __launch_bounds__(BL_NT) k_mresidual(void *r, const void *b, con
 // mode 1: restart every not-failed RHS from its true residual
 __global__ void __launch_bounds__(FIN_NT) k_mstate(MState *st, const double *partials, int nb,
                                                    int n_rhs, int par, double tol2, int mode) {
+  if (mode == 0)
+    for (int i = threadIdx.x; i < 2 * (1 + RED_MAX_GROUPS); i += FIN_NT) (&st->cnt[0][0])[i] = 0u;
   for (int q = 0; q < n_rhs; ++q) {
     double s = 0.0;
     for (int b = threadIdx.x; b < nb; b += FIN_NT) s += partials[(size_t)b * n_rhs + q];
@@ -205,7 +210,7 @@ __global__ void __launch_bounds__(FIN_NT) k_mstate(MState *st, const double *par
     if (mode == 0) {
       st->tol2 = tol2;
       st->iter = 0;
-      st->cnt[0] = st->cnt[1] = 0u;
+      st->adv = 0u;
     }
   }
 }
@@ -266,7 +271,7 @@ int m_iteration(MSolve &s, int k) {
   a.p = 1; a.out = s.tlo; a.in = s.p; a.cb = 1.0;
   TRY(dslash(ctx, a, U, s.plo, 0, nullptr));
   a.p = 0; a.out = s.y; a.in = s.tlo; a.x = s.p; a.ca = 1.0; a.cb_rhs = s.cb;
-  a.partials = s.pap_part; a.total = s.st->pap; a.counter = &s.st->cnt[0];
+  a.partials = s.pap_part; a.total = s.st->pap; a.counter = s.st->cnt[0];
   TRY(dslash(ctx, a, U, s.plo, 0, nullptr));
   a.partials = nullptr; a.total = nullptr; a.counter = nullptr;
   a.p = 1; a.out = s.tlo; a.in = s.y; a.x = nullptr; a.ca = 0.0; a.cb = 1.0; a.cb_rhs = nullptr;
@@ -366,8 +371,10 @@ int cg_solve_multi(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_ga
   const size_t f64 = spinor_bytes(g, HMC_F64, n_rhs);
   s.st = (MState *)workspace(ctx, "cgm_state", sizeof(MState));
   s.cb = (double *)workspace(ctx, "cgm_cb", sizeof(double) * NR_MAX);
+  // end-of-kernel reductions need red_part_len entries (partials + group sums)
+  const size_t len_ds = red_part_len(s.nb_ds + 64, n_rhs), len_bl = red_part_len(s.nb_bl, n_rhs);
   double *parts = (double *)workspace(
-      ctx, "cgm_partials", sizeof(double) * ((size_t)(s.nb_ds + 2 * s.nb_bl) * n_rhs + 64));
+      ctx, "cgm_partials", sizeof(double) * (len_ds + len_bl + (size_t)s.nb_bl * n_rhs + 64));
   s.r = workspace(ctx, "cgm_r64", f64);
   s.q = workspace(ctx, "cgm_q64", f64);
   s.y64 = workspace(ctx, "cgm_y64", f64);
@@ -387,8 +394,8 @@ int cg_solve_multi(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_ga
     s.rlo = s.r;
   }
   s.pap_part = parts;
-  s.rr_part = parts + (size_t)s.nb_ds * n_rhs;
-  s.tmp_part = parts + (size_t)(s.nb_ds + s.nb_bl) * n_rhs;
+  s.rr_part = parts + len_ds;
+  s.tmp_part = parts + len_ds + len_bl;
   s.x = x;
   s.b = b;
   double hcb[NR_MAX];
