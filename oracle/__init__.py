@@ -60,6 +60,7 @@ class TrajParams(ctypes.Structure):
         ("tol_md", _D), ("tol_action", _D),
         ("b", _P), ("c", _P), ("alpha", _D),
         ("n_mp", _I), ("kappa_mp", _P),
+        ("integrator", _I), ("lam", _D),
     ]
 
 
@@ -360,13 +361,15 @@ def kinetic(L, P):
 
 
 def _params(beta, kappa, tau, n_md, n_gauge, filter_k=0, n_t=0, n_max=0,
-            tol_md=1e-12, tol_action=1e-13, b=None, c=None, alpha=0.0, kappa_mp=None):
+            tol_md=1e-12, tol_action=1e-13, b=None, c=None, alpha=0.0, kappa_mp=None,
+            integrator=0, lam=1.0 / 6.0):
     """kappa_mp: heavier hopping parameters of a mass-preconditioned chain;
-    eta / phi then carry len(kappa_mp) + 1 half fields ([n, Vh, 4, 3])."""
+    eta / phi then carry len(kappa_mp) + 1 half fields ([n, Vh, 4, 3]).
+    integrator: 0 leapfrog, 1 Omelyan with parameter lam."""
     keep = []
     p = TrajParams(beta=beta, kappa=kappa, tau=tau, n_md=n_md, n_gauge=n_gauge,
                    filter_k=filter_k, n_t=n_t, n_max=n_max, tol_md=tol_md,
-                   tol_action=tol_action, alpha=alpha)
+                   tol_action=tol_action, alpha=alpha, integrator=integrator, lam=lam)
     if kappa_mp:
         km = _c(kappa_mp, np.float64); keep.append(km)
         p.n_mp = len(km)

@@ -180,10 +180,11 @@ static void fermion_force(const int L[4], const ocplx *U, const ocplx *phi,
                       1.0, F);
 }
 
-void or_md_evolve(const int L[4], ocplx *U, double *P, const ocplx *phi,
-                  const or_traj_params *p, int *cg_iters) {
+/* leapfrog T_L on two time scales, every force evaluated where the scheme
+ * places its momentum step (no merging) */
+static void md_leapfrog(const int L[4], ocplx *U, double *P, const ocplx *phi,
+                        const or_traj_params *p, double *F) {
   long nP = or_volume(L) * 32;
-  double *F = malloc(nP * sizeof(double));
   double dt = p->tau / p->n_md, dt0 = dt / p->n_gauge;
   for (int s = 0; s < p->n_md; ++s) {
     fermion_force(L, U, phi, p, F);
@@ -198,6 +199,50 @@ void or_md_evolve(const int L[4], ocplx *U, double *P, const ocplx *phi,
     fermion_force(L, U, phi, p, F);
     momentum_step(nP, P, F, 0.5 * dt);
   }
+}
+
+/* T_SW,0: the Omelyan step of the gauge force alone,
+ * P_0(lambda dt0) T(dt0/2) P_0((1-2 lambda) dt0) T(dt0/2) P_0(lambda dt0) */
+static void omelyan_fine(const int L[4], ocplx *U, double *P,
+                         const or_traj_params *p, double dt0, double *F) {
+  long nP = or_volume(L) * 32;
+  double lam = p->lambda;
+  gauge_force(L, U, p, F);
+  momentum_step(nP, P, F, lam * dt0);
+  or_update_links(L, U, P, 0.5 * dt0);
+  gauge_force(L, U, p, F);
+  momentum_step(nP, P, F, (1.0 - 2.0 * lam) * dt0);
+  or_update_links(L, U, P, 0.5 * dt0);
+  gauge_force(L, U, p, F);
+  momentum_step(nP, P, F, lam * dt0);
+}
+
+/* T_SW,1 = P_1(lambda dt) [T_SW,0]^m P_1((1-2 lambda) dt) [T_SW,0]^m
+ * P_1(lambda dt) with dt = 2 m dt0 (m = n_gauge) */
+static void md_omelyan(const int L[4], ocplx *U, double *P, const ocplx *phi,
+                       const or_traj_params *p, double *F) {
+  long nP = or_volume(L) * 32;
+  double lam = p->lambda, dt = p->tau / p->n_md, dt0 = dt / (2.0 * p->n_gauge);
+  for (int s = 0; s < p->n_md; ++s) {
+    fermion_force(L, U, phi, p, F);
+    momentum_step(nP, P, F, lam * dt);
+    for (int g = 0; g < p->n_gauge; ++g) omelyan_fine(L, U, P, p, dt0, F);
+    fermion_force(L, U, phi, p, F);
+    momentum_step(nP, P, F, (1.0 - 2.0 * lam) * dt);
+    for (int g = 0; g < p->n_gauge; ++g) omelyan_fine(L, U, P, p, dt0, F);
+    fermion_force(L, U, phi, p, F);
+    momentum_step(nP, P, F, lam * dt);
+  }
+}
+
+void or_md_evolve(const int L[4], ocplx *U, double *P, const ocplx *phi,
+                  const or_traj_params *p, int *cg_iters) {
+  long nP = or_volume(L) * 32;
+  double *F = malloc(nP * sizeof(double));
+  if (p->integrator == 1)
+    md_omelyan(L, U, P, phi, p, F);
+  else
+    md_leapfrog(L, U, P, phi, p, F);
   if (cg_iters) *cg_iters = 0;
   free(F);
 }

@@ -173,6 +173,13 @@ typedef struct {
    * phi then hold n_mp + 1 consecutive half fields.  n_mp = 0: one term. */
   int n_mp;
   const double *kappa_mp;
+  /* integrator (Sec. I): 0 leapfrog on two time scales, dt0 = dt / n_gauge;
+   * 1 the second-order Omelyan scheme T_O with parameter lambda on two time
+   * scales (Sexton-Weingarten nesting, pseudo-fermion force coarse, gauge
+   * force fine), dt0 = dt / (2 n_gauge), n_gauge fine steps in each of the
+   * two inner blocks of a coarse step. */
+  int integrator;
+  double lambda;
 } or_traj_params;
 
 typedef struct {
