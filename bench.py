@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--kernel", default=None,
                     help="time one hemi-Dslash variant alone, e.g. f16-12 (for profiling)")
     ap.add_argument("--launches", type=int, default=20)
+    ap.add_argument("--tau", type=float, default=None,
+                    help="trajectory length (applied after --n-md, which scales it)")
+    ap.add_argument("--integrator", default="leapfrog", choices=["leapfrog", "omelyan"],
+                    help="two-level leapfrog, or the second-order Omelyan scheme (lambda 1/6)")
     ap.add_argument("--mp", action="store_true",
                     help="mass-preconditioned workload: pseudo-fermions at kappa' = 0.150, "
                          "0.154 and the target kappa (ratio terms, batched solves), no filter")
@@ -309,6 +313,10 @@ def run_hmc(args):
     if args.n_md:
         work["tau"] = WORK["tau"] * args.n_md / WORK["n_md"]
         work["n_md"] = args.n_md
+    if args.tau:
+        work["tau"] = args.tau
+    if args.integrator == "omelyan":
+        work.update(integrator=hmc.OMELYAN, lam=1.0 / 6.0)
     if args.mp:
         work.update(filter_k=0, n_t=0, n_max=0)
         kw = dict(work, kappa_mp=KAPPA_MP, inner_prec=inner, link_fmt_lo=hmc.LINK12,

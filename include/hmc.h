@@ -393,7 +393,22 @@ typedef struct {
    * consecutive F64 even fields.  n_mp = 0: one plain or filtered term. */
   int n_mp;
   const double *kappa_mp;
+  /* integrator (Sec. I), both on the two time scales above with
+   * m = n_gauge: HMC_INTEGRATOR_LEAPFROG
+   *   T_L = P_1(dt/2) [P_0(dt0/2) T(dt0) P_0(dt0/2)]^m P_1(dt/2), dt0 = dt/m;
+   * HMC_INTEGRATOR_OMELYAN, the second-order scheme T_O with parameter
+   * lambda in (0, 1/2] nested as Sexton and Weingarten do:
+   *   P_1(l dt) [T_0]^m P_1((1-2l) dt) [T_0]^m P_1(l dt), dt0 = dt/(2m),
+   *   T_0 = P_0(l dt0) T(dt0/2) P_0((1-2l) dt0) T(dt0/2) P_0(l dt0);
+   * lambda = 1/6 is the paper's choice, lambda = 1/2 is the leapfrog with 2m
+   * fine steps.  dt = tau / n_md.  Adjacent momentum steps of one force at
+   * the same U are merged (one force evaluation). */
+  int integrator;
+  double lambda;
 } hmc_traj_params;
+
+#define HMC_INTEGRATOR_LEAPFROG 0
+#define HMC_INTEGRATOR_OMELYAN 1
 
 typedef struct {
   double H0, H1, dH;

@@ -261,13 +261,21 @@ static int mp_pairs(const hmc_traj_params *prm, double *ka, double *kb) {
   return n + 1;
 }
 
-// Leapfrog on two time scales (Sec. I; gauge on the fine scale, pseudo-fermion
-// on the coarse one, Sec. IV): per coarse step
-//   P_PF(dt/2) [P_G(dt0/2) T(dt0) P_G(dt0/2)]^n_gauge P_PF(dt/2),  dt0 = dt/n_gauge.
-// Adjacent momentum steps of the same force at the same U are merged (the sum
-// of the two half steps), which leaves the integrator unchanged.  U1 is the
-// F64/LINK18 field, Ulo its inner-precision copy (refreshed from U1 before
-// every pseudo-fermion force), F scratch for the force.
+// Molecular dynamics on two time scales (Sec. I; gauge force on the fine
+// scale, pseudo-fermion force on the coarse one, Sec. IV), with the
+// leapfrog or the second-order Omelyan integrator (parameter lambda) in the
+// Sexton-Weingarten nesting:
+//   leapfrog: P_1(dt/2) [P_0(dt0/2) T(dt0) P_0(dt0/2)]^m P_1(dt/2), dt0 = dt/m
+//   Omelyan:  P_1(l dt) [T_0]^m P_1((1-2l) dt) [T_0]^m P_1(l dt), dt0 = dt/(2m),
+//             T_0 = P_0(l dt0) T(dt0/2) P_0((1-2l) dt0) T(dt0/2) P_0(l dt0)
+// with m = n_gauge.  Momentum steps are deferred: a step only adds its
+// coefficient to the pending sum of its force, and the pending sums are
+// applied (one force evaluation each) just before the next link update and
+// at the end.  Adjacent steps of one force at the same U thereby merge into
+// one evaluation, and steps of different forces at the same U commute, so
+// the integrator is unchanged.  U1 is the F64/LINK18 field, Ulo its
+// inner-precision copy (refreshed from U1 before every pseudo-fermion
+// force), F scratch for the force.
 int md_evolve(hmc_ctx *ctx, const Geo &g, void *U1, void *Ulo, double *P, double *F,
               const void *phi, const hmc_traj_params *prm, int *solves, hmc_solve_stats *acc) {
   const int plo = prm->solver.inner_prec;
@@ -313,16 +321,47 @@ int md_evolve(hmc_ctx *ctx, const Geo &g, void *U1, void *Ulo, double *P, double
     }
     return update_momenta(ctx, g, P, F, eps);
   };
-  TRY(pf_step(0.5 * dt));
-  for (int s = 0; s < prm->n_md; ++s) {
-    TRY(gauge_step(0.5 * dt0));
-    for (int j = 0; j < prm->n_gauge; ++j) {
-      TRY(update_links(ctx, g, U1, P, dt0));
-      TRY(gauge_step(j + 1 < prm->n_gauge ? dt0 : 0.5 * dt0));
+  double pend_pf = 0.0, pend_g = 0.0;
+  auto flush = [&]() -> int {
+    if (pend_pf != 0.0) TRY(pf_step(pend_pf));
+    if (pend_g != 0.0) TRY(gauge_step(pend_g));
+    pend_pf = pend_g = 0.0;
+    return HMC_OK;
+  };
+  auto T = [&](double eps) -> int {
+    TRY(flush());
+    return update_links(ctx, g, U1, P, eps);
+  };
+  const int m = prm->n_gauge;
+  if (prm->integrator == HMC_INTEGRATOR_OMELYAN) {
+    const double lam = prm->lambda, dto = dt / (2.0 * m);
+    auto fine = [&]() -> int {
+      pend_g += lam * dto;
+      TRY(T(0.5 * dto));
+      pend_g += (1.0 - 2.0 * lam) * dto;
+      TRY(T(0.5 * dto));
+      pend_g += lam * dto;
+      return HMC_OK;
+    };
+    for (int s = 0; s < prm->n_md; ++s) {
+      pend_pf += lam * dt;
+      for (int j = 0; j < m; ++j) TRY(fine());
+      pend_pf += (1.0 - 2.0 * lam) * dt;
+      for (int j = 0; j < m; ++j) TRY(fine());
+      pend_pf += lam * dt;
     }
-    TRY(pf_step(s + 1 < prm->n_md ? dt : 0.5 * dt));
+  } else {
+    for (int s = 0; s < prm->n_md; ++s) {
+      pend_pf += 0.5 * dt;
+      for (int j = 0; j < m; ++j) {
+        pend_g += 0.5 * dt0;
+        TRY(T(dt0));
+        pend_g += 0.5 * dt0;
+      }
+      pend_pf += 0.5 * dt;
+    }
   }
-  return HMC_OK;
+  return flush();
 }
 
 static int check_traj_params(hmc_ctx *ctx, const hmc_traj_params *prm) {
@@ -332,6 +371,10 @@ static int check_traj_params(hmc_ctx *ctx, const hmc_traj_params *prm) {
     return fail(ctx, HMC_EINVAL, "trajectory: filter_k must be 0, 1 or 2");
   if (prm->filter_k > 0 && (!prm->b || !prm->c || prm->n_t < 0 || prm->n_max < prm->n_t))
     return fail(ctx, HMC_EINVAL, "trajectory: filter needs b, c and 0 <= n_t <= n_max");
+  if (prm->integrator != HMC_INTEGRATOR_LEAPFROG && prm->integrator != HMC_INTEGRATOR_OMELYAN)
+    return fail(ctx, HMC_EINVAL, "trajectory: unknown integrator %d", prm->integrator);
+  if (prm->integrator == HMC_INTEGRATOR_OMELYAN && !(prm->lambda > 0.0 && prm->lambda < 0.5 + 1e-15))
+    return fail(ctx, HMC_EINVAL, "trajectory: Omelyan lambda must be in (0, 1/2]");
   if (prm->n_mp < 0 || prm->n_mp > 15)
     return fail(ctx, HMC_EINVAL, "trajectory: n_mp must be 0..15");
   if (prm->n_mp > 0) {

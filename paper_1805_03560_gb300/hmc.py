@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libhmc.so")
 
 F64, F32, F16, F64E = 0, 1, 2, 3
 LINK18, LINK12 = 18, 12
+LEAPFROG, OMELYAN = 0, 1
 PREC_NAMES = {F64: "f64", F32: "f32", F16: "f16", F64E: "f64e"}
 
 OK, EINVAL, ENOMEM, ENOCONV, ETIMEOUT, ENAN, ECUDA = range(7)
@@ -50,7 +51,8 @@ class TrajParams(ctypes.Structure):
                 ("b", _P), ("c", _P), ("alpha", _D),
                 ("tol_md", _D), ("tol_action", _D),
                 ("solver", SolverOpts), ("link_fmt_lo", _I),
-                ("n_mp", _I), ("kappa_mp", _P)]
+                ("n_mp", _I), ("kappa_mp", _P),
+                ("integrator", _I), ("lam", _D)]
 
 
 class TrajResult(ctypes.Structure):
@@ -532,7 +534,8 @@ class Context:
     def trajectory(self, L, U, P, eta, u, beta, kappa, tau, n_md, n_gauge, filter_k=0, n_t=0,
                    n_max=0, b=None, c=None, alpha=0.0, tol_md=1e-10, tol_action=1e-12,
                    inner_prec=F64, link_fmt_lo=LINK12, reliable_delta=0.1, U_end=None,
-                   P_end=None, force_prec=F64, kappa_mp=None):
+                   P_end=None, force_prec=F64, kappa_mp=None, integrator=LEAPFROG,
+                   lam=1.0 / 6.0):
         """One HMC trajectory; U (F64/LINK18 gauge Field) is updated in place
         when accepted.  Returns the result as a dict.  kappa_mp: heavier
         hopping parameters of a mass-preconditioned chain (eta then from
@@ -543,7 +546,7 @@ class Context:
                          filter_k=filter_k, n_t=n_t, n_max=n_max, alpha=alpha, tol_md=tol_md,
                          tol_action=tol_action,
                          solver=SolverOpts(inner_prec, reliable_delta, 16, force_prec),
-                         link_fmt_lo=link_fmt_lo)
+                         link_fmt_lo=link_fmt_lo, integrator=integrator, lam=lam)
         self._mp(prm, kappa_mp, keep)
         if b is not None:
             ab = np.ascontiguousarray(b, dtype=np.float64); keep.append(ab); prm.b = ab.ctypes.data
@@ -559,7 +562,8 @@ class Context:
 
     def md_evolve(self, L, U, P, phi, beta, kappa, tau, n_md, n_gauge, filter_k=0, n_t=0,
                   b=None, alpha=0.0, tol_md=1e-10, inner_prec=F64, link_fmt_lo=LINK12,
-                  reliable_delta=0.1, force_prec=F64, kappa_mp=None):
+                  reliable_delta=0.1, force_prec=F64, kappa_mp=None, integrator=LEAPFROG,
+                  lam=1.0 / 6.0):
         """Molecular dynamics with phi fixed; U (F64/LINK18) and P updated in place."""
         self._stream()
         keep = []
@@ -567,7 +571,7 @@ class Context:
                          filter_k=filter_k, n_t=n_t, n_max=n_t, alpha=alpha, tol_md=tol_md,
                          tol_action=tol_md,
                          solver=SolverOpts(inner_prec, reliable_delta, 16, force_prec),
-                         link_fmt_lo=link_fmt_lo)
+                         link_fmt_lo=link_fmt_lo, integrator=integrator, lam=lam)
         self._mp(prm, kappa_mp, keep)
         if b is not None:
             ab = np.ascontiguousarray(b, dtype=np.float64); keep.append(ab)

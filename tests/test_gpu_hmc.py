@@ -195,3 +195,55 @@ def test_leapfrog_16x32_dt_scaling_and_reversibility(ctx, H):
     ctx.md_evolve(L, U, P, phi, BETA, KAPPA, 1.0, 10, 1, tol_md=1e-12)
     delta = np.sum(np.abs(_np(ctx.unpack_gauge(L, U)) - U0) ** 2)
     assert delta < 1e-20, delta
+
+
+@pytest.mark.parametrize("k,mp", [(0, False), (2, False), (0, True)])
+def test_omelyan_trajectory_matches_oracle(orc, ctx, H, k, mp):
+    """Second-order Omelyan scheme, lambda = 1/6, two time scales."""
+    L = (4, 4, 4, 4)
+    U = I.gauge_links(L, 0.3, 1)
+    P = I.momenta(L, 3)
+    kw = _traj_kw(k, n_md=2, integrator=1, lam=1.0 / 6)
+    if mp:
+        kw["kappa_mp"] = [0.150, 0.154]
+        eta = np.stack([I.gaussian_half(L, 20 + j) for j in range(3)])
+        ed = ctx.pack_spinors(L, list(eta))
+    else:
+        eta = I.gaussian_half(L, 2)
+        ed = ctx.pack_spinor(L, eta, 0)
+    _, ro, Uo_end, Po_end = orc.trajectory(L, U, P, eta, 0.5, tol_md=1e-13, tol_action=1e-14,
+                                           **kw)
+    Ue = ctx.new_gauge(L, 0, 18)
+    Pe = ctx.new_algebra(L)
+    r = ctx.trajectory(L, ctx.pack_gauge(L, U, 0, 18), ctx.pack_algebra(L, P), ed, 0.5,
+                       tol_md=1e-13, tol_action=1e-14, U_end=Ue, P_end=Pe, **kw)
+    assert abs(r["dH"] - ro["dH"]) <= 1e-7
+    assert np.abs(_np(ctx.unpack_gauge(L, Ue)) - Uo_end).max() <= 1e-9
+    assert np.abs(_np(ctx.unpack_algebra(L, Pe)) - Po_end).max() <= 1e-8
+
+
+def test_omelyan_half_equals_leapfrog_and_reverses(orc, ctx, H):
+    L = (4, 6, 6, 8)
+    U = I.gauge_links(L, 0.3, 1)
+    P = I.momenta(L, 3)
+    phi = ctx.pack_spinor(L, orc.mhat(L, U, KAPPA, I.gaussian_half(L, 2), dagger=True), 0)
+    base = dict(beta=BETA, kappa=KAPPA, tau=0.5, n_md=2, tol_md=1e-14)
+    out = []
+    for kw in (dict(n_gauge=2, integrator=1, lam=0.5), dict(n_gauge=4, integrator=0)):
+        Ud, Pd = ctx.pack_gauge(L, U, 0, 18), ctx.pack_algebra(L, P)
+        ctx.md_evolve(L, Ud, Pd, phi, **base, **kw)
+        out.append(_np(ctx.unpack_gauge(L, Ud)))
+    assert np.abs(out[0] - out[1]).max() < 1e-13
+    Ud, Pd = ctx.pack_gauge(L, U, 0, 18), ctx.pack_algebra(L, P)
+    ctx.md_evolve(L, Ud, Pd, phi, **base, n_gauge=2, integrator=1)
+    Pd.data.neg_()
+    ctx.md_evolve(L, Ud, Pd, phi, **base, n_gauge=2, integrator=1)
+    assert np.sum(np.abs(_np(ctx.unpack_gauge(L, Ud)) - U) ** 2) < 1e-20
+
+
+def test_bad_integrator_rejected(ctx, H):
+    L = (4, 4, 4, 4)
+    U = ctx.pack_gauge(L, I.unit_links(L), 0, 18)
+    with pytest.raises(H.HmcError):
+        ctx.trajectory(L, U, ctx.new_algebra(L), ctx.new_spinor(L, 0), 0.5, BETA, KAPPA, 0.5, 2,
+                       2, integrator=1, lam=0.7)
