@@ -58,6 +58,10 @@ def parse():
     ap.add_argument("--inner", default="f32", choices=["f16", "f32"])
     ap.add_argument("--delta", type=float, default=1e-5, help="reliable-update threshold")
     ap.add_argument("--force-prec", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--f64-emul", type=int, default=1, choices=[0, 1],
+                    help="FP64-accurate operator applications outside the inner solver "
+                         "(reliable updates, heatbath and action polynomials) in emulated "
+                         "FP64 (1) or native FP64 (0)")
     ap.add_argument("--kernel", default=None,
                     help="time one hemi-Dslash variant alone, e.g. f16-12 (for profiling)")
     ap.add_argument("--launches", type=int, default=20)
@@ -320,10 +324,10 @@ def run_hmc(args):
     if args.mp:
         work.update(filter_k=0, n_t=0, n_max=0)
         kw = dict(work, kappa_mp=KAPPA_MP, inner_prec=inner, link_fmt_lo=hmc.LINK12,
-                  reliable_delta=args.delta, force_prec=fprec)
+                  reliable_delta=args.delta, force_prec=fprec, f64_emul=args.f64_emul)
     else:
         kw = dict(work, b=b, c=c, alpha=alpha, inner_prec=inner, link_fmt_lo=hmc.LINK12,
-                  reliable_delta=args.delta, force_prec=fprec)
+                  reliable_delta=args.delta, force_prec=fprec, f64_emul=args.f64_emul)
     stream = torch.cuda.current_stream()
 
     def one(kwargs):
@@ -392,7 +396,8 @@ def run_hmc(args):
                                  "hmc-trajectory 24^3x48 kappa=0.1575 beta=5.6 kappa^4-filter"),
                    "lattice": "x".join(str(v) for v in LAT[::-1]), **{k: v for k, v in work.items()},
                    "inner_prec": args.inner, "reliable_delta": args.delta,
-                   "force_prec": args.force_prec, "links": "12-real (inner), 18-real FP64",
+                   "force_prec": args.force_prec, "f64_emul": args.f64_emul,
+                   "links": "12-real (inner), 18-real FP64",
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roof,
@@ -417,7 +422,7 @@ def run_hmc(args):
                            for k, v in sorted(tl.items(), key=lambda kv: -kv[1][1])}
     # ---- plain FP64 GPU path, same trajectory ----------------------------------
     if not args.no_fp64:
-        kw64 = dict(kw, inner_prec=hmc.F64, force_prec=hmc.F64)
+        kw64 = dict(kw, inner_prec=hmc.F64, force_prec=hmc.F64, f64_emul=0)
         one(kw64)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)

@@ -213,6 +213,14 @@ typedef struct {
                             products outside the solves (HMC_F64 or HMC_F32;
                             the solves always reach tol in FP64).  HMC_F32
                             needs U_lo in F32 or U_hi in LINK18. */
+  int f64_emul;          /* nonzero: the FP64-accurate operator applications
+                            outside the inner solver (true residuals of the
+                            reliable updates, heatbath and action
+                            polynomials, Mhat of the mass-preconditioned
+                            terms) run in emulated FP64 (HMC_F64E, about 48
+                            significant bits) on an F64E copy of U_hi made
+                            per call; needs U_hi in LINK18 (otherwise
+                            native FP64 is used).  0: native FP64. */
 } hmc_solver_opts;
 
 typedef struct {

@@ -160,6 +160,92 @@ __device__ __forceinline__ void hop_pair(const DslashArgs &a, int h, int r, int 
   accumulate<MU, -S>(acc, w);
 }
 
+// ---- runtime-direction forms ----------------------------------------------------
+// One copy of the hop code serves all eight hops.  The fully unrolled stencil
+// of the double-float kind is several times larger than the instruction
+// cache (its warps stall waiting for instructions); this form keeps one
+// projection, one link product of each kind and one accumulation in the
+// loop body.  mu is warp-uniform, so the switches do not diverge.
+// Same arithmetic as project / accumulate above, term for term.
+
+template <typename R>
+__device__ __forceinline__ Cx<R> sgn(int s, Cx<R> a) {
+  return s > 0 ? a : -a;
+}
+
+// h = u - S B_mu d  with S = +-1 at run time
+template <typename R>
+__device__ __forceinline__ void project_rt(int mu, int S, const Cx<R> p[12], Cx<R> h[6]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const Cx<R> u0 = p[a], u1 = p[3 + a], d0 = p[6 + a], d1 = p[9 + a];
+    Cx<R> t0, t1;
+    int c0, c1;
+    switch (mu) {
+      case 0: t0 = d0; c0 = -S; t1 = d1; c1 = -S; break;
+      case 1: t0 = ti(d1); c0 = S; t1 = ti(d0); c1 = S; break;
+      case 2: t0 = d1; c0 = S; t1 = d0; c1 = -S; break;
+      default: t0 = ti(d0); c0 = S; t1 = ti(d1); c1 = -S; break;
+    }
+    h[a] = u0 + sgn(c0, t0);
+    h[3 + a] = u1 + sgn(c1, t1);
+  }
+}
+
+// acc += (w, -S B_mu^dag w)
+template <typename R>
+__device__ __forceinline__ void accumulate_rt(int mu, int S, Cx<R> acc[12], const Cx<R> w[6]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const Cx<R> w0 = w[a], w1 = w[3 + a];
+    acc[a] = acc[a] + w0;
+    acc[3 + a] = acc[3 + a] + w1;
+    Cx<R> l0, l1;
+    int e0, e1;
+    switch (mu) {
+      case 0: l0 = w0; e0 = -S; l1 = w1; e1 = -S; break;
+      case 1: l0 = ti(w1); e0 = -S; l1 = ti(w0); e1 = -S; break;
+      case 2: l0 = w1; e0 = -S; l1 = w0; e1 = S; break;
+      default: l0 = ti(w0); e0 = -S; l1 = ti(w1); e1 = S; break;
+    }
+    acc[6 + a] = acc[6 + a] + sgn(e0, l0);
+    acc[9 + a] = acc[9 + a] + sgn(e1, l1);
+  }
+}
+
+// all eight hops of one site, directions in a run-time loop
+template <int SP, int FMT, int SF>
+__device__ __forceinline__ void hops_rt(const DslashArgs &a, int h, int r, int lex,
+                                        const int c[4], Cx<typename SpinorIO<SP>::R> acc[12]) {
+  using SIO = SpinorIO<SP>;
+  using R = typename SIO::R;
+  using LIO = LinkIO<SP, FMT>;
+  const int Vh = a.g.Vh, S_ = Vh * a.n_rhs;
+#pragma unroll 1
+  for (int k = 0; k < 8; ++k) {
+    const int mu = k >> 1;
+    const bool fwd = (k & 1) == 0;
+    const int hn = fwd ? nb_fwd(a.g, lex, c, mu) : nb_bwd(a.g, lex, c, mu);
+    Cx<R> psi[12], u[9], hs[6], w[6];
+    SIO::load(a.in, S_, hn * a.n_rhs + r, psi);
+    if (fwd)
+      LIO::load(link_base<SP, FMT>(a.gauge, Vh, a.p, mu), Vh, h, u);
+    else
+      LIO::load(link_base<SP, FMT>(a.gauge, Vh, 1 - a.p, mu), Vh, hn, u);
+    const int S = fwd ? SF : -SF;
+    project_rt(mu, S, psi, hs);
+    if (mu == 0 && c[0] == (fwd ? a.g.L[0] - 1 : 0)) {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) hs[q] = -hs[q];
+    }
+    if (fwd)
+      mul_link(u, hs, w);
+    else
+      mul_link_dag(u, hs, w);
+    accumulate_rt(mu, S, acc, w);
+  }
+}
+
 // Site of this thread.  Linear: consecutive threads take consecutive sites.
 // Tiled (a.tile_nseg > 0, one right-hand side): the four warps of a block take
 // 32 consecutive sites each at the offsets {0, +x, +t, +x+t}, so half of the
@@ -190,8 +276,14 @@ __device__ __forceinline__ int dslash_site(const DslashArgs &a) {
 #ifndef HMC_DS_MINB64
 #define HMC_DS_MINB64 1
 #endif
+#ifndef HMC_DS_MINB64E
+#define HMC_DS_MINB64E 3
+#endif
 constexpr int ds_min_blocks(int sp) {
-  return sp == HMC_F32 ? HMC_DS_MINB32 : (sp == HMC_F16 ? HMC_DS_MINB16 : HMC_DS_MINB64);
+  return sp == HMC_F32    ? HMC_DS_MINB32
+         : sp == HMC_F16  ? HMC_DS_MINB16
+         : sp == HMC_F64E ? HMC_DS_MINB64E
+                          : HMC_DS_MINB64;
 }
 
 template <int SP, int FMT, bool DAG, bool PAIR>
@@ -213,7 +305,9 @@ __global__ void __launch_bounds__(DS_NT, ds_min_blocks(SP)) k_dslash(const Dslas
     Cx<R> acc[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = {R(0), R(0)};
-    if (PAIR) {
+    if constexpr (SP == HMC_F64E) {
+      hops_rt<SP, FMT, SF>(a, h, r, lex, c, acc);
+    } else if (PAIR) {
       hop_pair<SP, FMT, 0, SF>(a, h, r, lex, c, acc);
       hop_pair<SP, FMT, 1, SF>(a, h, r, lex, c, acc);
       hop_pair<SP, FMT, 2, SF>(a, h, r, lex, c, acc);

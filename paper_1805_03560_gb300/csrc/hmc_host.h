@@ -133,6 +133,27 @@ int cg_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
              const void *b, double kappa, double tol, int max_iter, const hmc_solver_opts *opts,
              hmc_solve_stats *stats);
 
+// FP64-accurate operator applications, native or emulated (hiprec.cu).
+// hi_begin makes the F64E copy of the links when opts->f64_emul is set; tag
+// names the workspace (one tag per caller that may be active at a time).
+struct HiOps {
+  hmc_ctx *ctx;
+  Geo g;
+  hmc_gauge Uh, Ue;
+  bool emul;
+  const char *tag;
+};
+int hi_begin(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_solver_opts *opts,
+             HiOps *h, const char *tag);
+// F64 fields in and out; n_rhs right-hand sides with per-RHS -kappa^2 in
+// cb_rhs (device, nullable)
+int hi_mhat(const HiOps &h, int dagger, void *out, const void *in, double kappa, int n_rhs,
+            const double *cb_rhs);
+int hi_mdagm(const HiOps &h, void *out, const void *in, double kappa, int n_rhs,
+             const double *cb_rhs);
+// out = sum_{j<=n} c_j K^j in (Horner), out must not alias in
+int hi_poly_K(const HiOps &h, void *out, const void *in, const double *c, int n, double kappa);
+
 // batched CG of n_rhs systems with per-system kappas (host array); stats:
 // array of n_rhs (nullable)
 int cg_solve_multi(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul, void *x,

@@ -56,13 +56,10 @@ void *ws_j(hmc_ctx *ctx, const char *base, int j, size_t bytes) {
   return workspace(ctx, name, bytes);
 }
 
-// out = Mhat(kappa)^(dag) in, FP64; kappa == 0 copies
-int mhat64(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, int dagger, void *out,
-           const void *in, double kappa) {
-  if (kappa == 0.0) return copy_convert(ctx, HMC_F64, HMC_F64, out, in, g.Vh);
-  void *tmp = workspace(ctx, "mp_tmp", spinor_bytes(g, HMC_F64, 1));
-  if (!tmp) return HMC_ENOMEM;
-  return mhat(ctx, g, Uh, HMC_F64, dagger, 1, out, in, tmp, kappa, nullptr, nullptr, nullptr);
+// out = Mhat(kappa)^(dag) in, FP64-accurate (native or emulated); kappa == 0
+// copies
+int mhat64(const HiOps &h, int dagger, void *out, const void *in, double kappa) {
+  return hi_mhat(h, dagger, out, in, kappa, 1, nullptr);
 }
 
 void add_stats(hmc_solve_stats *acc, const hmc_solve_stats *s, int n) {
@@ -81,9 +78,11 @@ void add_stats(hmc_solve_stats *acc, const hmc_solve_stats *s, int n) {
 
 // X_j = (Mhat_b^dag Mhat_b)^{-1} phi_j for all j (batched), scattered into
 // single fields "mp_x<j>"; chi_j = Mhat_b X_j into "mp_chi<j>"
-int first_solves(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
-                 const void *phi, int n, const double *kb, double tol,
-                 const hmc_solver_opts *opts, hmc_solve_stats *acc) {
+int first_solves(const HiOps &hi, const hmc_gauge *Ul, const void *phi, int n, const double *kb,
+                 double tol, const hmc_solver_opts *opts, hmc_solve_stats *acc) {
+  hmc_ctx *ctx = hi.ctx;
+  const Geo &g = hi.g;
+  const hmc_gauge &Uh = hi.Uh;
   const size_t f64 = spinor_bytes(g, HMC_F64, 1);
   void *Phi = workspace(ctx, "mp_phim", f64 * n), *X = workspace(ctx, "mp_xm", f64 * n);
   if (!Phi || !X) return HMC_ENOMEM;
@@ -96,7 +95,7 @@ int first_solves(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gaug
     void *xj = ws_j(ctx, "mp_x", j, f64), *cj = ws_j(ctx, "mp_chi", j, f64);
     if (!xj || !cj) return HMC_ENOMEM;
     TRY(rhs_copy(ctx, g, X, xj, n, j, false));
-    TRY(mhat64(ctx, g, Uh, 0, cj, xj, kb[j]));
+    TRY(mhat64(hi, 0, cj, xj, kb[j]));
   }
   return HMC_OK;
 }
@@ -118,6 +117,8 @@ int force_mp(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
              const void *phi, int n, const double *ka, const double *kb, double coeff, double *F,
              double tol, const hmc_solver_opts *opts, hmc_solve_stats *acc) {
   TRY(check_terms(ctx, n, ka, kb));
+  HiOps hi;
+  TRY(hi_begin(ctx, g, Uh, opts, &hi, "mp"));
   const int fp = opts ? opts->force_prec : HMC_F64;
   if (fp != HMC_F64 && fp != HMC_F32)
     return fail(ctx, HMC_EINVAL, "force_mp: force_prec must be F64 or F32");
@@ -133,7 +134,7 @@ int force_mp(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
     }
   }
   const size_t f64 = spinor_bytes(g, HMC_F64, 1);
-  TRY(first_solves(ctx, g, Uh, Ul, phi, n, kb, tol, opts, acc));
+  TRY(first_solves(hi, Ul, phi, n, kb, tol, opts, acc));
   // second solves of the ratio terms, batched
   int m = 0;
   double kbr[16];
@@ -147,9 +148,9 @@ int force_mp(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
     if (slot[j] < 0) continue;
     void *cj = ws_j(ctx, "mp_chi", j, f64), *pj = ws_j(ctx, "mp_psi", j, f64);
     if (!pj) return HMC_ENOMEM;
-    TRY(mhat64(ctx, g, Uh, 1, pj, cj, ka[j]));  // psi = Mhat_a^dag chi
-    TRY(mhat64(ctx, g, Uh, 0, t, pj, ka[j]));   // Mhat_a psi
-    TRY(mhat64(ctx, g, Uh, 1, s, t, kb[j]));    // Mhat_b^dag Mhat_a psi
+    TRY(mhat64(hi, 1, pj, cj, ka[j]));  // psi = Mhat_a^dag chi
+    TRY(mhat64(hi, 0, t, pj, ka[j]));   // Mhat_a psi
+    TRY(mhat64(hi, 1, s, t, kb[j]));    // Mhat_b^dag Mhat_a psi
     TRY(rhs_copy(ctx, g, s, Sm, m, slot[j], true));
     kbr[slot[j]] = kb[j];
   }
@@ -202,14 +203,16 @@ int action_mp(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *
               const void *phi, int n, const double *ka, const double *kb, double tol,
               const hmc_solver_opts *opts, double *S, hmc_solve_stats *acc) {
   TRY(check_terms(ctx, n, ka, kb));
+  HiOps hi;
+  TRY(hi_begin(ctx, g, Uh, opts, &hi, "mp"));
   const size_t f64 = spinor_bytes(g, HMC_F64, 1);
-  TRY(first_solves(ctx, g, Uh, Ul, phi, n, kb, tol, opts, acc));
+  TRY(first_solves(hi, Ul, phi, n, kb, tol, opts, acc));
   void *pj = workspace(ctx, "mp_t", f64);
   double *part = (double *)workspace(ctx, "mp_part", sizeof(double) * (blocks_for(g.Vh, 256) + 64));
   double *dst = (double *)workspace(ctx, "mp_dst", sizeof(double) * 16);
   if (!pj || !part || !dst) return HMC_ENOMEM;
   for (int j = 0; j < n; ++j) {
-    TRY(mhat64(ctx, g, Uh, 1, pj, ws_j(ctx, "mp_chi", j, f64), ka[j]));  // psi
+    TRY(mhat64(hi, 1, pj, ws_j(ctx, "mp_chi", j, f64), ka[j]));  // psi
     int nb;
     TRY(norm_partials(ctx, HMC_F64, pj, g.Vh, part, &nb));
     TRY(reduce_partials(ctx, part, nb, dst + j));
@@ -231,6 +234,8 @@ int heatbath_mp(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge
                 const void *eta, int n, const double *ka, const double *kb, double tol,
                 const hmc_solver_opts *opts, void *phi, hmc_solve_stats *acc) {
   TRY(check_terms(ctx, n, ka, kb));
+  HiOps hi;
+  TRY(hi_begin(ctx, g, Uh, opts, &hi, "mp"));
   const size_t f64 = spinor_bytes(g, HMC_F64, 1);
   int m = 0;
   double kar[16];
@@ -254,10 +259,10 @@ int heatbath_mp(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge
     const void *zj = (const char *)eta + f64 * j;
     if (slot[j] >= 0) {
       TRY(rhs_copy(ctx, g, X, x1, m, slot[j], false));
-      TRY(mhat64(ctx, g, Uh, 0, z, x1, ka[j]));  // Mhat_a^{-dag} eta = Mhat_a X
+      TRY(mhat64(hi, 0, z, x1, ka[j]));  // Mhat_a^{-dag} eta = Mhat_a X
       zj = z;
     }
-    TRY(mhat64(ctx, g, Uh, 1, (char *)phi + f64 * j, zj, kb[j]));
+    TRY(mhat64(hi, 1, (char *)phi + f64 * j, zj, kb[j]));
   }
   return HMC_OK;
 }

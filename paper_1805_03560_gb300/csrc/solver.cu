@@ -383,13 +383,12 @@ struct Solve {
   const void *b;
   void *xlo, *rlo, *p, *y, *Ap, *tlo;
   int nb_ds, nb_bl;
+  HiOps hi;  // the FP64-accurate A x of the true residuals
 };
 
-// q = A in (FP64) via y64, t64
+// q = A in, FP64-accurate (native or emulated FP64)
 int apply_A64(Solve &s, const void *in, void *out) {
-  TRY(mhat(s.ctx, s.g, s.Uh, HMC_F64, 0, 1, s.y64, in, s.t64, s.kappa, nullptr, nullptr, nullptr));
-  return mhat(s.ctx, s.g, s.Uh, HMC_F64, 1, 1, out, s.y64, s.t64, s.kappa, nullptr, nullptr,
-              nullptr);
+  return hi_mdagm(s.hi, out, in, s.kappa, 1, nullptr);
 }
 
 template <int PL>
@@ -512,6 +511,7 @@ int cg_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
   const double delta = (opts && opts->reliable_delta > 0) ? opts->reliable_delta : 0.1;
   const int check = (opts && opts->check_every > 0) ? opts->check_every : 16;
   s.kappa = kappa;
+  TRY(hi_begin(ctx, g, Uh, opts, &s.hi, "cg"));
   s.S = g.Vh;
   s.nb_ds = blocks_for(g.Vh, DS_NT);
   s.nb_bl = blocks_for(g.Vh, BL_NT);

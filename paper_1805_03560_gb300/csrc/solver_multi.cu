@@ -250,11 +250,11 @@ struct MSolve {
   void *x, *r, *q, *y64, *t64, *xlo, *rlo, *p, *y, *Ap, *tlo;
   const void *b;
   int nb_ds, nb_bl;
+  HiOps hi;  // the FP64-accurate A x of the true residuals
 };
 
 int m_apply_A64(MSolve &s, const void *in, void *out) {
-  TRY(mhat(s.ctx, s.g, s.Uh, HMC_F64, 0, s.n, s.y64, in, s.t64, 0.0, s.cb, nullptr, nullptr));
-  return mhat(s.ctx, s.g, s.Uh, HMC_F64, 1, s.n, out, s.y64, s.t64, 0.0, s.cb, nullptr, nullptr);
+  return hi_mdagm(s.hi, out, in, 0.0, s.n, s.cb);
 }
 
 int m_iteration(MSolve &s, int k) {
@@ -363,6 +363,7 @@ int cg_solve_multi(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_ga
     s.Ul = *Ul;
   }
   if (!(tol > 0.0)) return fail(ctx, HMC_EINVAL, "cg_multi: tol must be > 0");
+  TRY(hi_begin(ctx, g, Uh, opts, &s.hi, "cgm"));
   const double delta = (opts && opts->reliable_delta > 0) ? opts->reliable_delta : 0.1;
   const int check = (opts && opts->check_every > 0) ? opts->check_every : 16;
   s.S = g.Vh * n_rhs;

@@ -122,14 +122,13 @@ static int pair_force(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U64, const hm
 }
 
 // y = Mhat^{-1} phi via the normal equations
-static int mhat_inverse(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
-                        void *y, const void *phi, double kappa, double tol,
-                        const hmc_solver_opts *opts, hmc_solve_stats *acc) {
-  size_t f64 = spinor_bytes(g, HMC_F64, 1);
-  void *src = workspace(ctx, "pf_src", f64), *tmp = workspace(ctx, "pf_tmp", f64);
-  if (!src || !tmp) return HMC_ENOMEM;
-  TRY(mhat(ctx, g, Uh, HMC_F64, 1, 1, src, phi, tmp, kappa, nullptr, nullptr, nullptr));
-  return solve(ctx, g, Uh, Ul, y, src, kappa, tol, opts, acc);
+static int mhat_inverse(const HiOps &h, const hmc_gauge *Ul, void *y, const void *phi,
+                        double kappa, double tol, const hmc_solver_opts *opts,
+                        hmc_solve_stats *acc) {
+  void *src = workspace(h.ctx, "pf_src", spinor_bytes(h.g, HMC_F64, 1));
+  if (!src) return HMC_ENOMEM;
+  TRY(hi_mhat(h, 1, src, phi, kappa, 1, nullptr));
+  return solve(h.ctx, h.g, h.Uh, Ul, y, src, kappa, tol, opts, acc);
 }
 
 // The pseudo-fermion force.  Solves always run to tol with their FP64
@@ -194,7 +193,9 @@ int force_pf(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
   for (int j = n; j >= 1; --j)
     TRY(apply_K(ctx, g, Uf, fp, 0, kappa, slot(j - 1), slot(j), phi_f, filt->b[j - 1], tmp));
   // Ytilde = alpha Mhat^{-1} phi (FP64 solve)
-  TRY(mhat_inverse(ctx, g, Uh, Ul, Yt, phi, kappa, tol, opts, acc));
+  HiOps hi;
+  TRY(hi_begin(ctx, g, Uh, opts, &hi, "tr"));
+  TRY(mhat_inverse(hi, Ul, Yt, phi, kappa, tol, opts, acc));
   TRY(axpby(ctx, HMC_F64, Yt, filt->alpha, Yt, 0.0, nullptr, g.Vh));
   const void *Yt_f = Yt;
   if (fp != HMC_F64) {
@@ -233,8 +234,7 @@ int action_pf(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *
               const hmc_solver_opts *opts, double *S, hmc_solve_stats *acc) {
   size_t f64 = spinor_bytes(g, HMC_F64, 1);
   void *X = workspace(ctx, "pa_x", f64), *Z = workspace(ctx, "pa_z", f64);
-  void *tmp = workspace(ctx, "pa_tmp", f64);
-  if (!X || !Z || !tmp) return HMC_ENOMEM;
+  if (!X || !Z) return HMC_ENOMEM;
   if (!filt) {
     TRY(solve(ctx, g, Uh, Ul, X, phi, kappa, tol, opts, acc));
     return dot_host(ctx, g, phi, X, S);
@@ -242,10 +242,10 @@ int action_pf(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *
   const int n = filt->n;
   if (n < 0 || !filt->b) return fail(ctx, HMC_EINVAL, "action_pf: bad filter");
   // Z = sum_j b_j K^j phi (Horner), then Z += alpha Mhat^{-1} phi
-  TRY(axpby(ctx, HMC_F64, Z, filt->b[n], phi, 0.0, nullptr, g.Vh));
-  for (int j = n - 1; j >= 0; --j)
-    TRY(apply_K(ctx, g, Uh, HMC_F64, 0, kappa, Z, Z, phi, filt->b[j], tmp));
-  TRY(mhat_inverse(ctx, g, Uh, Ul, X, phi, kappa, tol, opts, acc));
+  HiOps hi;
+  TRY(hi_begin(ctx, g, Uh, opts, &hi, "tr"));
+  TRY(hi_poly_K(hi, Z, phi, filt->b, n, kappa));
+  TRY(mhat_inverse(hi, Ul, X, phi, kappa, tol, opts, acc));
   TRY(axpby(ctx, HMC_F64, Z, 1.0, Z, filt->alpha, X, g.Vh));
   return norm2_host(ctx, g, HMC_F64, Z, S);
 }
@@ -563,11 +563,15 @@ int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj
     }
     res->solves += 1;
   } else if (k == 0) {
-    TRY(mhat(ctx, g, Uh, HMC_F64, 1, 1, phi, eta, t1, prm->kappa, nullptr, nullptr, nullptr));
+    HiOps hi;
+    TRY(hi_begin(ctx, g, Uh, &prm->solver, &hi, "tr"));
+    TRY(hi_mhat(hi, 1, phi, eta, prm->kappa, 1, nullptr));
     TRY(norm2_host(ctx, g, HMC_F64, eta, &spf0));  // S_PF(Mhat^dag eta) = |eta|^2
   } else {
-    TRY(hmc_poly_apply(ctx, lat, &Uh, t2, eta, prm->c, prm->n_max, prm->kappa, HMC_F64, nullptr));
-    TRY(mhat(ctx, g, Uh, HMC_F64, 0, 1, phi, t2, t1, prm->kappa, nullptr, nullptr, nullptr));
+    HiOps hi;
+    TRY(hi_begin(ctx, g, Uh, &prm->solver, &hi, "tr"));
+    TRY(hi_poly_K(hi, t2, eta, prm->c, prm->n_max, prm->kappa));
+    TRY(hi_mhat(hi, 0, phi, t2, prm->kappa, 1, nullptr));
     TRY(refresh_lo());
     TRY(action_pf(ctx, g, Uh, Ulp, phi, prm->kappa, filt_act, prm->tol_action, &prm->solver,
                   &spf0, &acc));

@@ -34,7 +34,7 @@ class Gauge(ctypes.Structure):
 
 class SolverOpts(ctypes.Structure):
     _fields_ = [("inner_prec", _I), ("reliable_delta", _D), ("check_every", _I),
-                ("force_prec", _I)]
+                ("force_prec", _I), ("f64_emul", _I)]
 
 
 class SolveStats(ctypes.Structure):
@@ -319,11 +319,11 @@ class Context:
         return out
 
     def cg_solve(self, L, U_hi, x, phi, kappa, tol, max_iter=10000, U_lo=None, inner_prec=F64,
-                 reliable_delta=0.1, check_every=16):
+                 reliable_delta=0.1, check_every=16, f64_emul=0):
         self._stream()
         gh = U_hi.gauge()
         gl = U_lo.gauge() if U_lo is not None else None
-        opts = SolverOpts(inner_prec, reliable_delta, check_every)
+        opts = SolverOpts(inner_prec, reliable_delta, check_every, F64, f64_emul)
         stats = SolveStats()
         st = lib().hmc_cg_solve(self.h, _ref(lattice(L)), ctypes.byref(gh),
                                 ctypes.byref(gl) if gl is not None else None, x.ptr(), phi.ptr(),
@@ -335,7 +335,7 @@ class Context:
         return res
 
     def cg_solve_multi(self, L, U_hi, x, phi, kappas, tol, max_iter=10000, U_lo=None,
-                       inner_prec=F64, reliable_delta=0.1, check_every=16):
+                       inner_prec=F64, reliable_delta=0.1, check_every=16, f64_emul=0):
         """Batched solve of phi.n_rhs systems with per-system kappas."""
         self._stream()
         n = phi.n_rhs
@@ -343,7 +343,7 @@ class Context:
         gl = U_lo.gauge() if U_lo is not None else None
         ks = np.ascontiguousarray(kappas, dtype=np.float64)
         assert len(ks) == n
-        opts = SolverOpts(inner_prec, reliable_delta, check_every, F64)
+        opts = SolverOpts(inner_prec, reliable_delta, check_every, F64, f64_emul)
         stats = (SolveStats * n)()
         st = lib().hmc_cg_solve_multi(self.h, _ref(lattice(L)), ctypes.byref(gh),
                                       ctypes.byref(gl) if gl is not None else None, x.ptr(),
@@ -364,13 +364,13 @@ class Context:
         return Filter(arr.ctypes.data, len(arr) - 1, alpha), arr
 
     def force_pf(self, L, U_hi, phi, kappa, F, coeff=1.0, tol=1e-12, U_lo=None, inner_prec=F64,
-                 b=None, alpha=0.0, reliable_delta=0.1, force_prec=F64):
+                 b=None, alpha=0.0, reliable_delta=0.1, force_prec=F64, f64_emul=0):
         """F += coeff * F_PF (plain action when b is None, else the filtered one)."""
         self._stream()
         gh = U_hi.gauge()
         gl = U_lo.gauge() if U_lo is not None else None
         flt, keep = self._filter(b, alpha)
-        opts = SolverOpts(inner_prec, reliable_delta, 16, force_prec)
+        opts = SolverOpts(inner_prec, reliable_delta, 16, force_prec, f64_emul)
         stats = SolveStats()
         st = lib().hmc_force_pf(self.h, _ref(lattice(L)), ctypes.byref(gh),
                                 ctypes.byref(gl) if gl is not None else None, phi.ptr(), kappa,
@@ -380,12 +380,12 @@ class Context:
         return {"iterations": stats.iterations, "true_rel_res": stats.true_rel_res}
 
     def action_pf(self, L, U_hi, phi, kappa, tol=1e-13, U_lo=None, inner_prec=F64, b=None,
-                  alpha=0.0):
+                  alpha=0.0, f64_emul=0):
         self._stream()
         gh = U_hi.gauge()
         gl = U_lo.gauge() if U_lo is not None else None
         flt, keep = self._filter(b, alpha)
-        opts = SolverOpts(inner_prec, 0.1, 16)
+        opts = SolverOpts(inner_prec, 0.1, 16, F64, f64_emul)
         out = ctypes.c_double(0)
         st = lib().hmc_action_pf(self.h, _ref(lattice(L)), ctypes.byref(gh),
                                  ctypes.byref(gl) if gl is not None else None, phi.ptr(), kappa,
@@ -446,14 +446,14 @@ class Context:
         return len(ka), ka.ctypes.data_as(_P), kb.ctypes.data_as(_P)
 
     def force_mp(self, L, U_hi, phis, kappa_a, kappa_b, F, coeff=1.0, tol=1e-12, U_lo=None,
-                 inner_prec=F64, reliable_delta=0.1, force_prec=F64):
+                 inner_prec=F64, reliable_delta=0.1, force_prec=F64, f64_emul=0):
         """F += coeff * sum_j force of |Mhat(ka_j)^dag Mhat(kb_j)^{-dag} phi_j|^2."""
         self._stream()
         keep = []
         n, ka, kb = self._mp_args(kappa_a, kappa_b, keep)
         gh = U_hi.gauge()
         gl = U_lo.gauge() if U_lo is not None else None
-        opts = SolverOpts(inner_prec, reliable_delta, 16, force_prec)
+        opts = SolverOpts(inner_prec, reliable_delta, 16, force_prec, f64_emul)
         stats = SolveStats()
         st = lib().hmc_force_mp(self.h, _ref(lattice(L)), ctypes.byref(gh),
                                 ctypes.byref(gl) if gl is not None else None, phis.ptr(), n, ka,
@@ -462,13 +462,13 @@ class Context:
         self._check(st, "hmc_force_mp")
         return {f: getattr(stats, f) for f, _ in SolveStats._fields_}
 
-    def action_mp(self, L, U_hi, phis, kappa_a, kappa_b, tol=1e-13, U_lo=None, inner_prec=F64):
+    def action_mp(self, L, U_hi, phis, kappa_a, kappa_b, tol=1e-13, U_lo=None, inner_prec=F64, f64_emul=0):
         self._stream()
         keep = []
         n, ka, kb = self._mp_args(kappa_a, kappa_b, keep)
         gh = U_hi.gauge()
         gl = U_lo.gauge() if U_lo is not None else None
-        opts = SolverOpts(inner_prec, 0.1, 16)
+        opts = SolverOpts(inner_prec, 0.1, 16, F64, f64_emul)
         out = ctypes.c_double(0)
         st = lib().hmc_action_mp(self.h, _ref(lattice(L)), ctypes.byref(gh),
                                  ctypes.byref(gl) if gl is not None else None, phis.ptr(), n, ka,
@@ -477,13 +477,13 @@ class Context:
         return out.value
 
     def heatbath_mp(self, L, U_hi, etas, kappa_a, kappa_b, tol=1e-13, U_lo=None,
-                    inner_prec=F64):
+                    inner_prec=F64, f64_emul=0):
         self._stream()
         keep = []
         n, ka, kb = self._mp_args(kappa_a, kappa_b, keep)
         gh = U_hi.gauge()
         gl = U_lo.gauge() if U_lo is not None else None
-        opts = SolverOpts(inner_prec, 0.1, 16)
+        opts = SolverOpts(inner_prec, 0.1, 16, F64, f64_emul)
         out = Field(self._bytes(etas.data.numel()), "spinor", F64, 1)
         st = lib().hmc_heatbath_mp(self.h, _ref(lattice(L)), ctypes.byref(gh),
                                    ctypes.byref(gl) if gl is not None else None, etas.ptr(), n,
@@ -535,7 +535,7 @@ class Context:
                    n_max=0, b=None, c=None, alpha=0.0, tol_md=1e-10, tol_action=1e-12,
                    inner_prec=F64, link_fmt_lo=LINK12, reliable_delta=0.1, U_end=None,
                    P_end=None, force_prec=F64, kappa_mp=None, integrator=LEAPFROG,
-                   lam=1.0 / 6.0):
+                   lam=1.0 / 6.0, f64_emul=0):
         """One HMC trajectory; U (F64/LINK18 gauge Field) is updated in place
         when accepted.  Returns the result as a dict.  kappa_mp: heavier
         hopping parameters of a mass-preconditioned chain (eta then from
@@ -545,7 +545,7 @@ class Context:
         prm = TrajParams(beta=beta, kappa=kappa, tau=tau, n_md=n_md, n_gauge=n_gauge,
                          filter_k=filter_k, n_t=n_t, n_max=n_max, alpha=alpha, tol_md=tol_md,
                          tol_action=tol_action,
-                         solver=SolverOpts(inner_prec, reliable_delta, 16, force_prec),
+                         solver=SolverOpts(inner_prec, reliable_delta, 16, force_prec, f64_emul),
                          link_fmt_lo=link_fmt_lo, integrator=integrator, lam=lam)
         self._mp(prm, kappa_mp, keep)
         if b is not None:
@@ -563,14 +563,14 @@ class Context:
     def md_evolve(self, L, U, P, phi, beta, kappa, tau, n_md, n_gauge, filter_k=0, n_t=0,
                   b=None, alpha=0.0, tol_md=1e-10, inner_prec=F64, link_fmt_lo=LINK12,
                   reliable_delta=0.1, force_prec=F64, kappa_mp=None, integrator=LEAPFROG,
-                  lam=1.0 / 6.0):
+                  lam=1.0 / 6.0, f64_emul=0):
         """Molecular dynamics with phi fixed; U (F64/LINK18) and P updated in place."""
         self._stream()
         keep = []
         prm = TrajParams(beta=beta, kappa=kappa, tau=tau, n_md=n_md, n_gauge=n_gauge,
                          filter_k=filter_k, n_t=n_t, n_max=n_t, alpha=alpha, tol_md=tol_md,
                          tol_action=tol_md,
-                         solver=SolverOpts(inner_prec, reliable_delta, 16, force_prec),
+                         solver=SolverOpts(inner_prec, reliable_delta, 16, force_prec, f64_emul),
                          link_fmt_lo=link_fmt_lo, integrator=integrator, lam=lam)
         self._mp(prm, kappa_mp, keep)
         if b is not None:
