@@ -127,7 +127,10 @@ int gauge_action_coeffs(hmc_ctx *ctx, const Geo &g, double beta, double kappa, i
                         double *beta_eff, double cline[4], bool *lines);
 int update_momenta(hmc_ctx *ctx, const Geo &g, double *P, const double *F, double eps);
 int kinetic_partials(hmc_ctx *ctx, const Geo &g, const double *P, double *partials, int *nb);
-int update_links(hmc_ctx *ctx, const Geo &g, void *U, const double *P, double eps);
+// U <- exp(eps Pi) U, reunitarised; emul: exponential and product in
+// emulated FP64 (the projection stays FP64)
+int update_links(hmc_ctx *ctx, const Geo &g, void *U, const double *P, double eps,
+                 bool emul = false);
 int convert_gauge(hmc_ctx *ctx, const Geo &g, const void *src, void *dst, int prec, int fmt);
 int cg_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul, void *x,
              const void *b, double kappa, double tol, int max_iter, const hmc_solver_opts *opts,

@@ -1,4 +1,5 @@
-// Molecular-dynamics update steps of Sec. I, all in FP64:
+// Molecular-dynamics update steps of Sec. I in FP64 (and the link update in
+// emulated FP64, below):
 //   P(eps): Pi <- Pi - eps F      (dPi/dtau = -F fixes the sign)
 //   T(eps): U  <- exp(eps Pi) U   (dU/dtau = Pi U, Pi antihermitian)
 // The kinetic term (1/2)(Pi, Pi) = (1/2) sum_a P_a^2 with Pi = sum_a P_a T_a,
@@ -163,6 +164,112 @@ __global__ void __launch_bounds__(128) k_update_links(Geo g, void *gauge, const 
   LinkIO<HMC_F64, 18>::store(base, g.Vh, h, w);
 }
 
+// ---- emulated-FP64 link update ---------------------------------------------
+// The same Cayley-Hamilton exponential and product exp(eps Pi) U in
+// double-float arithmetic (hmc_internal.cuh, about 48 significant bits) on
+// the FP32 units, then the projection back onto SU(3) in native FP64.  The
+// series is summed until its terms fall below 2^-50 of the leading
+// coefficient (the precision of the arithmetic).
+using E = Cx<df64>;
+
+__device__ __forceinline__ void mm_e(const E a[9], const E b[9], E c[9]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      E t = a[i * 3] * b[j];
+      t = fmac(t, a[i * 3 + 1], b[3 + j]);
+      t = fmac(t, a[i * 3 + 2], b[6 + j]);
+      c[i * 3 + j] = t;
+    }
+}
+
+__device__ __forceinline__ df64 scale2(df64 v, float s) { return {v.hi * s, v.lo * s}; }
+
+__device__ __forceinline__ void expm_su3_e(const E A[9], E Ex[9]) {
+  // row-sum norm bound from the leading parts (only a scaling decision)
+  float nrm = 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float r = 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) r += fabsf(A[i * 3 + j].re.hi) + fabsf(A[i * 3 + j].im.hi);
+    nrm = fmaxf(nrm, r);
+  }
+  int sq = 0;
+  while (nrm > 1.f && sq < 60) {
+    nrm *= 0.5f;
+    ++sq;
+  }
+  const float sc = ldexpf(1.f, -sq);  // exact power of two
+  E B[9], B2[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) B[k] = {scale2(A[k].re, sc), scale2(A[k].im, sc)};
+  mm_e(B, B, B2);
+  const df64 half(0.5f);
+  const E s = half * (B2[0] + B2[4] + B2[8]);
+  const E d = B[0] * (B[4] * B[8] - B[5] * B[7]) - B[1] * (B[3] * B[8] - B[5] * B[6]) +
+              B[2] * (B[3] * B[7] - B[4] * B[6]);
+  const df64 zero(0.f), one(1.f);
+  E ta = {one, zero}, tb = {zero, zero}, tc = {zero, zero};  // (a, b, c)_n / n!
+  E f0 = ta, f1 = tb, f2 = tc;
+#pragma unroll 1
+  for (int n = 0; n < 40; ++n) {
+    const df64 inv(c_inv[n + 1]);
+    const E na = inv * (tc * d), nb = inv * (ta + tc * s), nc = inv * tb;
+    ta = na;
+    tb = nb;
+    tc = nc;
+    f0 = f0 + ta;
+    f1 = f1 + tb;
+    f2 = f2 + tc;
+    const float m = fmaxf(ta.re.hi * ta.re.hi + ta.im.hi * ta.im.hi,
+                          fmaxf(tb.re.hi * tb.re.hi + tb.im.hi * tb.im.hi,
+                                tc.re.hi * tc.re.hi + tc.im.hi * tc.im.hi));
+    if (m < 7.9e-31f && n >= 2) break;  // (2^-50)^2
+  }
+  E R[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) R[k] = f1 * B[k] + f2 * B2[k];
+  R[0] = R[0] + f0;
+  R[4] = R[4] + f0;
+  R[8] = R[8] + f0;
+#pragma unroll 1
+  for (int k = 0; k < sq; ++k) {
+    E T[9];
+    mm_e(R, R, T);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) R[q] = T[q];
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Ex[k] = R[k];
+}
+
+__global__ void __launch_bounds__(128) k_update_links_e(Geo g, void *gauge, const double *P,
+                                                        double eps) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 8 * g.Vh) return;
+  const int pm = i / g.Vh, h = i - pm * g.Vh;
+  double p[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) p[a] = P[((size_t)pm * 8 + a) * g.Vh + h];
+  C A[9], u[9];
+  algebra_matrix(p, eps, A);
+  E Ae[9], Ee[9], ue[9], we[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Ae[k] = {df64(A[k].re), df64(A[k].im)};
+  expm_su3_e(Ae, Ee);
+  void *base = (char *)gauge + (size_t)pm * 9 * g.Vh * 16;
+  LinkIO<HMC_F64, 18>::load(base, g.Vh, h, u);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) ue[k] = {df64(u[k].re), df64(u[k].im)};
+  mm_e(Ee, ue, we);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) u[k] = {(double)we[k].re, (double)we[k].im};
+  reunitarise(u);
+  LinkIO<HMC_F64, 18>::store(base, g.Vh, h, u);
+}
+
 // F64/LINK18 -> any precision / format (same site order)
 template <int P, int FMT>
 __global__ void k_convert_gauge(Geo g, const void *src, void *dst) {
@@ -188,7 +295,11 @@ int kinetic_partials(hmc_ctx *ctx, const Geo &g, const double *P, double *partia
   return launched(ctx, "kinetic");
 }
 
-int update_links(hmc_ctx *ctx, const Geo &g, void *U, const double *P, double eps) {
+int update_links(hmc_ctx *ctx, const Geo &g, void *U, const double *P, double eps, bool emul) {
+  if (emul) {
+    k_update_links_e<<<blocks_for(8LL * g.Vh, 128), 128, 0, ctx->stream>>>(g, U, P, eps);
+    return launched(ctx, "update_links_f64e");
+  }
   k_update_links<<<blocks_for(8LL * g.Vh, 128), 128, 0, ctx->stream>>>(g, U, P, eps);
   return launched(ctx, "update_links");
 }

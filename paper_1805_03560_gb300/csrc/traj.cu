@@ -330,7 +330,7 @@ int md_evolve(hmc_ctx *ctx, const Geo &g, void *U1, void *Ulo, double *P, double
   };
   auto T = [&](double eps) -> int {
     TRY(flush());
-    return update_links(ctx, g, U1, P, eps);
+    return update_links(ctx, g, U1, P, eps, prm->solver.f64_emul != 0);
   };
   const int m = prm->n_gauge;
   if (prm->integrator == HMC_INTEGRATOR_OMELYAN) {

@@ -87,3 +87,23 @@ def test_trajectory_emulated_matches_oracle(orc, ctx, H, k, mp):
                        tol_md=1e-13, tol_action=1e-14, U_end=Ue, inner_prec=1, f64_emul=1, **kw)
     assert abs(r["dH"] - ro["dH"]) <= 1e-7
     assert np.abs(_np(ctx.unpack_gauge(L, Ue)) - Uo_end).max() <= 1e-9
+
+
+def test_md_reversible_with_emulated_link_update(orc, ctx, H):
+    """With f64_emul the exponential and product of the link update run in
+    double-float (projection in FP64).  Per update each entry carries ~1e-14
+    relative error, so over 16 updates of 4608 links Delta = sum |U - U'|^2
+    stays below ~1e-22; the bound 1e-18 still fails on any irreversible step
+    (a wrong sign or a skipped step moves U by O(1e-2))."""
+    L = (4, 6, 6, 8)
+    U = I.gauge_links(L, 0.3, 1)
+    P = I.momenta(L, 3)
+    phi = ctx.pack_spinor(L, orc.mhat(L, U, KAPPA, I.gaussian_half(L, 2), dagger=True), 0)
+    kw = dict(beta=5.6, kappa=KAPPA, tau=0.5, n_md=4, n_gauge=2, tol_md=1e-14, f64_emul=1)
+    Ud, Pd = ctx.pack_gauge(L, U, 0, 18), ctx.pack_algebra(L, P)
+    ctx.md_evolve(L, Ud, Pd, phi, **kw)
+    moved = np.sum(np.abs(_np(ctx.unpack_gauge(L, Ud)) - U) ** 2)
+    Pd.data.neg_()
+    ctx.md_evolve(L, Ud, Pd, phi, **kw)
+    delta = np.sum(np.abs(_np(ctx.unpack_gauge(L, Ud)) - U) ** 2)
+    assert moved > 1e-2 and delta < 1e-18, (moved, delta)
