@@ -292,6 +292,10 @@ __global__ void __launch_bounds__(DS_NT, ds_min_blocks(SP)) k_dslash(const Dslas
   using R = typename SIO::R;
   constexpr int SF = DAG ? -1 : 1;  // forwards: 1 - gamma (1 + gamma for the adjoint)
   if (a.gate && *a.gate == 0) return;
+  if (a.red_src && blockIdx.x == 0) {
+    const double t = block_sum_partials<DS_NT>(a.red_src, a.red_n);
+    if (threadIdx.x == 0) *a.red_dst = t;
+  }
   const int S_ = a.g.Vh * a.n_rhs;
   const int i = dslash_site(a);
   double nrm = 0.0;
@@ -336,14 +340,44 @@ __global__ void __launch_bounds__(DS_NT, ds_min_blocks(SP)) k_dslash(const Dslas
 #pragma unroll
       for (int k = 0; k < 12; ++k) acc[k] = cb * acc[k];
     }
-    SIO::store(a.out, S_, i, acc);
-    if (a.partials) {
-      // per-site sum in the arithmetic precision (FP64 adds are scarce on
-      // this GPU), cross-site sums in double
+    if (a.cg_x) {
+      // fused CG step: acc = A p is consumed here, x += alpha p, r -= alpha A p
+      constexpr int PX = (SP == HMC_F64 || SP == HMC_F64E) ? SP : HMC_F32;
+      const double pap = *a.cg_pap, ad = *a.cg_rr / pap;
+      if (blockIdx.x == 0 && threadIdx.x == 0 && (!isfinite(ad) || !(pap > 0.0)))
+        *a.cg_flag = 2;
+      const R alpha = (R)ad;
+      Cx<R> pv[12], v[12];
+      SIO::load(a.cg_p, S_, i, pv);
+      load_as<PX>(a.cg_x, S_, i, v);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        v[k].re = fma(alpha, pv[k].re, v[k].re);
+        v[k].im = fma(alpha, pv[k].im, v[k].im);
+      }
+      store_as<PX>(a.cg_x, S_, i, v);
+      SIO::load(a.cg_r, S_, i, v);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        v[k].re = fma(-alpha, acc[k].re, v[k].re);
+        v[k].im = fma(-alpha, acc[k].im, v[k].im);
+      }
+      // |r|^2 from registers, per-site sum in the arithmetic precision
       R n2 = R(0);
 #pragma unroll
-      for (int k = 0; k < 12; ++k) n2 += norm2(acc[k]);
+      for (int k = 0; k < 12; ++k) n2 += norm2(v[k]);
       nrm = (double)n2;
+      SIO::store(a.cg_r, S_, i, v);
+    } else {
+      SIO::store(a.out, S_, i, acc);
+      if (a.partials) {
+        // per-site sum in the arithmetic precision (FP64 adds are scarce on
+        // this GPU), cross-site sums in double
+        R n2 = R(0);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) n2 += norm2(acc[k]);
+        nrm = (double)n2;
+      }
     }
   }
   if (a.partials) {
@@ -389,6 +423,12 @@ int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int
   const double rb = (sprec == HMC_F64 || sprec == HMC_F64E) ? 8.0 : (sprec == HMC_F32 ? 4.0 : 2.0);
   double bytes = (double)a.g.Vh * 8.0 * U.fmt * rb + (double)S * 24.0 * rb * (a.x ? 3.0 : 2.0);
   if (sprec == HMC_F16) bytes += (double)S * 4.0 * (a.x ? 3.0 : 2.0);
+  if (a.cg_x) {
+    // fused CG update: p, x, r read and x, r written, A p not written
+    const double xb = sprec == HMC_F64 ? 8.0 : 4.0;
+    bytes += (double)S * 24.0 * (3.0 * rb + 2.0 * xb - rb);
+    if (sprec == HMC_F16) bytes += (double)S * 4.0 * 2.0;
+  }
   char cls[64];
   snprintf(cls, sizeof(cls), "dslash_%s_%d%s%s",
            sprec == HMC_F64 ? "f64" : (sprec == HMC_F32 ? "f32" : (sprec == HMC_F16 ? "f16" : "f64e")),

@@ -104,6 +104,21 @@ struct DslashArgs {
   // zeroed device int, returned to zero)
   double *total;
   unsigned int *counter;
+  // before its stencil work, block 0 sums red_src[0..red_n) (the block
+  // partials a previous launch left) in a fixed order into *red_dst
+  const double *red_src;
+  int red_n;
+  double *red_dst;
+  // fused CG update (n_rhs == 1): the epilogue result A p is not stored;
+  // with alpha = *cg_rr / *cg_pap the launch updates x += alpha p (cg_x, in
+  // FP64 for FP64 fields, F32 otherwise) and r -= alpha A p (cg_r), and the
+  // partials receive |r|^2.  *cg_flag = 2 when alpha is not finite.
+  void *cg_x;
+  void *cg_r;
+  const void *cg_p;
+  const double *cg_rr;
+  const double *cg_pap;
+  int *cg_flag;
 };
 int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int dagger,
            int *nblocks);

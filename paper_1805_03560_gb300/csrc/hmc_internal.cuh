@@ -567,6 +567,26 @@ __device__ __forceinline__ void block_partials_rhs(double v, int r, int n_rhs, d
   __syncthreads();
 }
 
+// Sum of p[0..n) over the threads of a block, each thread taking indices
+// threadIdx.x + k NT into eight independent accumulators so that its loads
+// are all in flight at once (the partials of a previous launch, read through
+// L2 at the start of a kernel).  The order depends only on n and NT, so every
+// block computes the same value.  Valid in thread 0 (block_sum).
+template <int NT>
+__device__ __forceinline__ double block_sum_partials(const double *p, int n) {
+  double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int j = threadIdx.x;
+  for (; j + 7 * NT < n; j += 8 * NT) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] += __ldcg(p + j + u * NT);
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+    if (j + u * NT < n) acc[u] += __ldcg(p + j + u * NT);
+  const double t = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+  return block_sum<NT>(t);
+}
+
 // ---- end-of-kernel totals: two-level deterministic reduction ----------------------
 //
 // Every block of a kernel stores its partial sums part[b * n + q] (q < n
