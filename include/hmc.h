@@ -125,6 +125,13 @@ int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
  * same result bit for bit.  Default -1: paired loads for LINK18 only (the
  * fastest choice measured on 24^3 x 48). */
 #define HMC_OPT_DSLASH_VARIANT 1
+/* HMC_OPT_CG_GRAPH: 1 (default) replays the CG iterations of hmc_cg_solve
+ * (and of every single-system solve inside the force, action and trajectory
+ * calls) from a CUDA graph of two iterations captured once per solve, on a
+ * stream of the library's own that is ordered after the caller's stream and
+ * before its next work; 0 launches every kernel on the caller's stream.
+ * Results are bit-identical.  Graphs are not used while timing is enabled. */
+#define HMC_OPT_CG_GRAPH 2
 int hmc_ctx_set_option(hmc_ctx *ctx, int option, int value);
 /* Statistics of the index-th kernel class seen since timing was enabled:
  * class name (e.g. "dslash_f16_12/cg"), launches, summed event time in ms and

@@ -220,6 +220,12 @@ int hmc_ctx_destroy(hmc_ctx *ctx) {
   for (auto &kv : ctx->ws)
     if (kv.second.p) cudaFree(kv.second.p);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  if (ctx->gstream) {
+    cudaStreamSynchronize(ctx->gstream);
+    cudaStreamDestroy(ctx->gstream);
+  }
+  for (cudaEvent_t e : ctx->gev)
+    if (e) cudaEventDestroy(e);
   delete ctx;
   return HMC_OK;
 }
@@ -253,6 +259,10 @@ int hmc_ctx_set_option(hmc_ctx *ctx, int option, int value) {
     case HMC_OPT_DSLASH_VARIANT:
       if (value < -1 || value > 3) return fail(ctx, HMC_EINVAL, "dslash variant must be -1..3");
       ctx->ds_variant = value;
+      return HMC_OK;
+    case HMC_OPT_CG_GRAPH:
+      if (value != 0 && value != 1) return fail(ctx, HMC_EINVAL, "cg graph option must be 0 or 1");
+      ctx->cg_graph = value;
       return HMC_OK;
     default:
       return fail(ctx, HMC_EINVAL, "unknown option %d", option);

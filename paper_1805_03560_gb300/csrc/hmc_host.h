@@ -28,6 +28,13 @@ struct hmc_ctx {
   // hemi-Dslash kernel variant: bit 0 tiled site mapping, bit 1 paired loads;
   // -1 chooses per link format
   int ds_variant = -1;
+  // CG iterations replayed from a captured CUDA graph (two iterations per
+  // graph, captured once per solve) when timing is off; gstream: the
+  // library's own non-blocking stream for capture and replay, ordered after
+  // and before the caller's stream by gev
+  int cg_graph = 1;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev[2] = {nullptr, nullptr};
   struct Pending {
     cudaEvent_t a, b;
     int cls;

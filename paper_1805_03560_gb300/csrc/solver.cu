@@ -350,6 +350,11 @@ struct Solve {
   void *xlo, *rlo, *p, *y, *tlo;
   int nb_ds, nb_bl;
   HiOps hi;  // the FP64-accurate A x of the true residuals
+  cudaGraphExec_t pair = nullptr;  // two captured iterations (enqueue_iterations)
+  int pair_nodes = 0;
+  ~Solve() {
+    if (pair) cudaGraphExecDestroy(pair);
+  }
 };
 
 // q = A in, FP64-accurate (native or emulated FP64)
@@ -411,6 +416,73 @@ int one_iteration(Solve &s, int k) {
     case HMC_F16: launch_xpay<HMC_F16>(s, par, nb_rr); break;
   }
   return launched(ctx, "cg_xpay");
+}
+
+// ---- CUDA-graph replay of the iterations ---------------------------------------------
+// Two iterations (parities 0 and 1) are captured once per solve on the
+// context's own stream and replayed for every even-aligned pair of a batch;
+// a single iteration fills an odd start or end.  The graph holds exactly the
+// launches one_iteration makes, so results are bit-identical to direct
+// launches.  The caller's stream and the graph stream are ordered by events
+// around every batch.
+
+int graph_stream(hmc_ctx *ctx) {
+  if (ctx->gstream) return HMC_OK;
+  TRY(cuda_ok(ctx, cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking),
+              "cg graph: stream"));
+  for (cudaEvent_t &e : ctx->gev)
+    TRY(cuda_ok(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cg graph: event"));
+  return HMC_OK;
+}
+
+int capture_pair(Solve &s) {
+  hmc_ctx *ctx = s.ctx;
+  cudaStream_t user = ctx->stream;
+  const long long n0 = ctx->launches;
+  ctx->stream = ctx->gstream;
+  cudaError_t e = cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal);
+  int st = e == cudaSuccess ? HMC_OK : cuda_ok(ctx, e, "cg graph: begin capture");
+  if (!st) st = one_iteration(s, 0);
+  if (!st) st = one_iteration(s, 1);
+  cudaGraph_t g = nullptr;
+  if (e == cudaSuccess) {
+    cudaError_t e2 = cudaStreamEndCapture(ctx->gstream, &g);
+    if (!st) st = cuda_ok(ctx, e2, "cg graph: end capture");
+  }
+  ctx->stream = user;
+  ctx->launches = n0;
+  size_t nodes = 0;
+  if (!st) st = cuda_ok(ctx, cudaGraphGetNodes(g, nullptr, &nodes), "cg graph: nodes");
+  if (!st) st = cuda_ok(ctx, cudaGraphInstantiate(&s.pair, g, 0), "cg graph: instantiate");
+  if (g) cudaGraphDestroy(g);
+  s.pair_nodes = (int)nodes;
+  return st;
+}
+
+// enqueue iterations k .. k + n - 1
+int enqueue_iterations(Solve &s, int k, int n) {
+  hmc_ctx *ctx = s.ctx;
+  if (!(ctx->cg_graph && ctx->timing == 0) || n < 2) {
+    for (int j = 0; j < n; ++j) TRY(one_iteration(s, k + j));
+    return HMC_OK;
+  }
+  TRY(graph_stream(ctx));
+  if (!s.pair) TRY(capture_pair(s));
+  cudaStream_t user = ctx->stream;
+  TRY(cuda_ok(ctx, cudaEventRecord(ctx->gev[0], user), "cg graph: order"));
+  TRY(cuda_ok(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->gev[0], 0), "cg graph: order"));
+  ctx->stream = ctx->gstream;
+  int st = HMC_OK, j = 0;
+  if (k & 1) st = one_iteration(s, k + j++);
+  for (; !st && j + 1 < n; j += 2) {
+    st = cuda_ok(ctx, cudaGraphLaunch(s.pair, ctx->gstream), "cg graph: launch");
+    ctx->launches += s.pair_nodes;
+  }
+  if (!st && j < n) st = one_iteration(s, k + j);
+  ctx->stream = user;
+  TRY(st);
+  TRY(cuda_ok(ctx, cudaEventRecord(ctx->gev[1], ctx->gstream), "cg graph: order"));
+  return cuda_ok(ctx, cudaStreamWaitEvent(user, ctx->gev[1], 0), "cg graph: order");
 }
 
 int read_state(Solve &s, CGState *h) {
@@ -551,7 +623,7 @@ int cg_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
       if (left < todo) todo = left < 1.0 ? 1 : (int)ceil(left);
     }
     if (k + todo > max_iter) todo = max_iter - k;
-    for (int j = 0; j < todo; ++j) TRY(one_iteration(s, k + j));
+    TRY(enqueue_iterations(s, k, todo));
     TRY(read_state(s, &h));
     if (h.done == 2) {
       nan = true;

@@ -204,6 +204,10 @@ class Context:
     def set_dslash_variant(self, v):
         self._check(lib().hmc_ctx_set_option(self.h, 1, int(v)), "hmc_ctx_set_option")
 
+    def set_cg_graph(self, on):
+        """Replay CG iterations from a captured CUDA graph (default on)."""
+        self._check(lib().hmc_ctx_set_option(self.h, 2, int(bool(on))), "hmc_ctx_set_option")
+
     def set_timing(self, enable):
         self._check(lib().hmc_ctx_set_timing(self.h, int(enable)), "hmc_ctx_set_timing")
 

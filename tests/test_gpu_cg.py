@@ -151,3 +151,28 @@ def test_cg_multi_matches_single(ctx, H):
     assert r1["iterations"] == r2["iterations"][0]
     a1, a2 = _np(ctx.unpack_spinor(L, x1)), _np(ctx.unpack_spinor(L, x2))
     assert np.abs(a1 - a2).max() <= 1e-14 * np.abs(a1).max()
+
+
+@pytest.mark.parametrize("inner", [0, 1])
+def test_cg_graph_replay_is_bit_identical(ctx, H, inner):
+    """The CG iterations replayed from the captured two-iteration graph are the
+    same launches as direct ones: identical solution bits and counts, on the
+    default stream and on a side stream."""
+    import torch
+    L = (4, 6, 6, 10)
+    U = I.gauge_links(L, 0.3, 1)
+    phi = I.gaussian_half(L, 2)
+    out = []
+    for graph, side in ((0, False), (1, False), (1, True)):
+        ctx.set_cg_graph(graph)
+        if side:
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                x, r = _solve(ctx, H, L, U, phi, 0.156, 1e-11, inner, check_every=5)
+            torch.cuda.synchronize()
+        else:
+            x, r = _solve(ctx, H, L, U, phi, 0.156, 1e-11, inner, check_every=5)
+        out.append((x, r["iterations"], r["reliable_updates"]))
+    ctx.set_cg_graph(1)
+    for x, it, ru in out[1:]:
+        assert np.array_equal(x, out[0][0]) and it == out[0][1] and ru == out[0][2]
