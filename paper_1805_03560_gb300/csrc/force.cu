@@ -56,13 +56,20 @@ __device__ __forceinline__ void im_tr_lambda(const Cx<R> q[9], double f[8]) {
   f[7] = ((double)q[0].im + (double)q[4].im - 2.0 * (double)q[8].im) * r3;
 }
 
+// Up to HF_MAX pairs (W_q, V_q) per launch: Q is linear in the pair, so the
+// kernel sums A and B over the pairs and multiplies by the link, projects and
+// updates F once (the filtered force of Sec. II is a sum of n_t + 1 pairs;
+// one launch reads the links and reads and writes F once for all of them).
+constexpr int HF_MAX = 32;
+
 struct HopForceArgs {
   Geo g;
-  const void *gauge;  // links in the precision of the fields
-  const void *W[2];   // W even, W odd   (F64 half fields)
-  const void *V[2];   // V even, V odd
-  double *F;          // algebra field
-  double c;           // F_a += c * (-Im Tr(lambda_a Q)) ; c = coeff * kappa^2
+  const void *gauge;      // links in the precision of the fields
+  int n;                  // pairs
+  const void *W[HF_MAX][2];  // W even, W odd
+  const void *V[HF_MAX][2];  // V even, V odd
+  double *F;              // algebra field
+  double c;               // F_a += c * (-Im Tr(lambda_a Q)) ; c = coeff * kappa^2
 };
 
 template <int FMT, int SP, int MU>
@@ -75,24 +82,31 @@ __device__ __forceinline__ void link_force(const HopForceArgs &a, int p, int h, 
   const double sg = (MU == 0 && c[0] == a.g.L[0] - 1) ? -1.0 : 1.0;
   Cx<R> s[12], hv[6], hw[6], u[9];
   Cx<R> A[9], B[9];
-  // A = sum_s P- V_{x+mu} (x) (P- W_x)^*   with P- = 1 - gamma_mu
-  SIO::load(a.V[1 - p], Vh, hn, s);
-  fproject<MU, +1>(s, hv);
-  SIO::load(a.W[p], Vh, h, s);
-  fproject<MU, +1>(s, hw);
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
+  for (int k = 0; k < 9; ++k) A[k] = B[k] = {R(0), R(0)};
+#pragma unroll 1
+  for (int q = 0; q < a.n; ++q) {
+    // A += sum_s P- V_{x+mu} (x) (P- W_x)^*   with P- = 1 - gamma_mu
+    SIO::load(a.V[q][1 - p], Vh, hn, s);
+    fproject<MU, +1>(s, hv);
+    SIO::load(a.W[q][p], Vh, h, s);
+    fproject<MU, +1>(s, hw);
 #pragma unroll
-    for (int j = 0; j < 3; ++j) A[i * 3 + j] = fmacj(cjmul(hw[j], hv[i]), hw[3 + j], hv[3 + i]);
-  // B = sum_s P+ V_x (x) (P+ W_{x+mu})^*   with P+ = 1 + gamma_mu
-  SIO::load(a.V[p], Vh, h, s);
-  fproject<MU, -1>(s, hv);
-  SIO::load(a.W[1 - p], Vh, hn, s);
-  fproject<MU, -1>(s, hw);
+    for (int i = 0; i < 3; ++i)
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        A[i * 3 + j] = fmacj(fmacj(A[i * 3 + j], hw[j], hv[i]), hw[3 + j], hv[3 + i]);
+    // B += sum_s P+ V_x (x) (P+ W_{x+mu})^*   with P+ = 1 + gamma_mu
+    SIO::load(a.V[q][p], Vh, h, s);
+    fproject<MU, -1>(s, hv);
+    SIO::load(a.W[q][1 - p], Vh, hn, s);
+    fproject<MU, -1>(s, hw);
 #pragma unroll
-    for (int j = 0; j < 3; ++j) B[i * 3 + j] = fmacj(cjmul(hw[j], hv[i]), hw[3 + j], hv[3 + i]);
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        B[i * 3 + j] = fmacj(fmacj(B[i * 3 + j], hw[j], hv[i]), hw[3 + j], hv[3 + i]);
+  }
   LinkIO<SP, FMT>::load(link_base<SP, FMT>(a.gauge, Vh, p, MU), Vh, h, u);
   // Q = U A - B U^dag
   Cx<R> Q[9];
@@ -133,17 +147,35 @@ __global__ void __launch_bounds__(128) k_hop_force(const HopForceArgs a) {
 
 int hop_force(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, const void *We, const void *Wo,
               const void *Ve, const void *Vo, double *F, double c, int sprec) {
+  const void *W[1][2] = {{We, Wo}}, *V[1][2] = {{Ve, Vo}};
+  return hop_force_multi(ctx, g, U, 1, W, V, F, c, sprec);
+}
+
+int hop_force_multi(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, int n, const void *const W[][2],
+                    const void *const V[][2], double *F, double c, int sprec) {
   if (sprec != HMC_F64 && sprec != HMC_F32)
     return fail(ctx, HMC_EINVAL, "force: spinor precision must be F64 or F32");
   if (U.prec != sprec)
     return fail(ctx, HMC_EINVAL, "force: gauge precision must match the fields");
+  if (n < 1) return HMC_OK;
+  if (n > HF_MAX) {
+    // in chunks of HF_MAX pairs
+    for (int q0 = 0; q0 < n; q0 += HF_MAX) {
+      int st = hop_force_multi(ctx, g, U, n - q0 < HF_MAX ? n - q0 : HF_MAX, W + q0, V + q0, F, c,
+                               sprec);
+      if (st) return st;
+    }
+    return HMC_OK;
+  }
   HopForceArgs a{};
   a.g = g;
   a.gauge = U.data;
-  a.W[0] = We;
-  a.W[1] = Wo;
-  a.V[0] = Ve;
-  a.V[1] = Vo;
+  a.n = n;
+  for (int q = 0; q < n; ++q)
+    for (int h = 0; h < 2; ++h) {
+      a.W[q][h] = W[q][h];
+      a.V[q][h] = V[q][h];
+    }
   a.F = F;
   a.c = c;
   int nb = blocks_for(2LL * g.Vh, 128);

@@ -141,6 +141,9 @@ int dot_partials(hmc_ctx *ctx, const void *x, const void *y, int S, double *part
 // F += c * (-Im Tr(lambda_a Q)) per link; W, V halves in precision sprec (F64 or F32)
 int hop_force(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, const void *We, const void *Wo,
               const void *Ve, const void *Vo, double *F, double c, int sprec);
+// the same for n pairs (W[q] = {even, odd}, V[q] likewise) summed in one pass
+int hop_force_multi(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, int n, const void *const W[][2],
+                    const void *const V[][2], double *F, double c, int sprec);
 int gauge_force(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, double beta, double kappa, int k,
                 double coeff, double *F);
 int gauge_action_sums(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, int with_lines,

@@ -159,13 +159,13 @@ int force_mp(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
     TRY(cg_solve_multi(ctx, g, Uh, Ul, Xi, Sm, kbr, m, tol, 100000, opts, st));
     add_stats(acc, st, m);
   }
-  // outer products: v = kappa_b^2 xi - kappa_a^2 psi
-  void *v = workspace(ctx, "mp_v", f64), *cf = workspace(ctx, "mp_chif", f64);
-  void *vf = workspace(ctx, "mp_vf", f64);
-  void *Wo = workspace(ctx, "mp_wo", f64), *Vo = workspace(ctx, "mp_vo", f64);
-  if (!v || !cf || !vf || !Wo || !Vo) return HMC_ENOMEM;
+  // outer products: v = kappa_b^2 xi - kappa_a^2 psi, all terms in one pass
+  const void *Wp[16][2], *Vp[16][2];
   for (int j = 0; j < n; ++j) {
-    void *cj = ws_j(ctx, "mp_chi", j, f64);
+    void *cj = ws_j(ctx, "mp_chi", j, f64), *v = ws_j(ctx, "mp_v", j, f64);
+    void *cf = ws_j(ctx, "mp_chif", j, f64), *vf = ws_j(ctx, "mp_vf", j, f64);
+    void *Wo = ws_j(ctx, "mp_wo", j, f64), *Vo = ws_j(ctx, "mp_vo", j, f64);
+    if (!v || !cf || !vf || !Wo || !Vo) return HMC_ENOMEM;
     const double kb2 = kb[j] * kb[j], ka2 = ka[j] * ka[j];
     if (slot[j] < 0) {
       TRY(axpby(ctx, HMC_F64, v, kb2, ws_j(ctx, "mp_x", j, f64), 0.0, nullptr, g.Vh));
@@ -193,9 +193,12 @@ int force_mp(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
     a.out = Vo;
     a.in = Vv;
     TRY(dslash(ctx, a, Uf, fp, 0, nullptr));
-    TRY(hop_force(ctx, g, Uf, W, Wo, Vv, Vo, F, coeff, fp));
+    Wp[j][0] = W;
+    Wp[j][1] = Wo;
+    Vp[j][0] = Vv;
+    Vp[j][1] = Vo;
   }
-  return HMC_OK;
+  return hop_force_multi(ctx, g, Uf, n, Wp, Vp, F, coeff, fp);
 }
 
 // *S = sum_j S_R(phi_j; ka[j], kb[j]) (FP64)

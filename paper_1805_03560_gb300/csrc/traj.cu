@@ -216,17 +216,32 @@ int force_pf(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
     Xs = Xf;
   }
   TRY(mhat(ctx, g, Uf, fp, 0, 1, Xt, Xs, tmp, kappa, nullptr, nullptr, nullptr));
-  TRY(pair_force(ctx, g, Uh, Uf, fp, kappa, Xt, Yt_f, coeff, F));
-  for (int i = 1; i <= n; ++i) {
-    TRY(pair_force(ctx, g, Uh, Uf, fp, kappa, Xi, slot(i), coeff, F));
-    if (i < n) {
-      TRY(apply_K(ctx, g, Uf, fp, 1, kappa, Xn, Xi, nullptr, 0.0, tmp));
-      void *t = Xi;
-      Xi = Xn;
-      Xn = t;
-    }
+  // The n + 1 pairs (Xtilde, Ytilde), (X_i, Y_i) go into one outer-product
+  // pass: X_1 .. X_n are kept (X_{i+1} = K^dag X_i), and for every pair the
+  // odd halves H_eo^dag A and H_oe B.  Buffers at FP64 size (never
+  // reallocated when the force precision changes).
+  char *Xs_all = (char *)workspace(ctx, "pf_xall", f64 * n);
+  char *Wodd = (char *)workspace(ctx, "pf_woall", f64 * (n + 1));
+  char *Vodd = (char *)workspace(ctx, "pf_voall", f64 * (n + 1));
+  if ((n && !Xs_all) || !Wodd || !Vodd) return HMC_ENOMEM;
+  auto xs = [&](int i) { return (void *)(Xs_all + f64 * (i - 1)); };
+  if (n >= 1) TRY(copy_convert(ctx, fp, fp, xs(1), Xi, g.Vh));
+  for (int i = 1; i < n; ++i) TRY(apply_K(ctx, g, Uf, fp, 1, kappa, xs(i + 1), xs(i), nullptr, 0.0, tmp));
+  std::vector<const void *> Wv(2 * (n + 1)), Vv(2 * (n + 1));
+  for (int q = 0; q <= n; ++q) {
+    const void *A = q == 0 ? Xt : xs(q);
+    const void *B = q == 0 ? Yt_f : slot(q);
+    void *wo = Wodd + f64 * q, *vo = Vodd + f64 * q;
+    TRY(hop(ctx, g, Uf, fp, 1, 1, wo, A, nullptr, 0.0, 1.0));  // H_eo^dag A
+    TRY(hop(ctx, g, Uf, fp, 1, 0, vo, B, nullptr, 0.0, 1.0));  // H_oe B
+    Wv[2 * q] = A;
+    Wv[2 * q + 1] = wo;
+    Vv[2 * q] = B;
+    Vv[2 * q + 1] = vo;
   }
-  return HMC_OK;
+  (void)Xn;
+  return hop_force_multi(ctx, g, Uf, n + 1, (const void *const(*)[2])Wv.data(),
+                         (const void *const(*)[2])Vv.data(), F, coeff * kappa * kappa, fp);
 }
 
 int action_pf(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
