@@ -75,7 +75,9 @@ def parse():
     ap.add_argument("--report", default=None, choices=["md"],
                     help="md: leapfrog dH at dt = 1/10, 1/20, 1/40 and reversibility on "
                          "16^3x32, kappa 0.156, plain pseudo-fermion action")
-    ap.add_argument("--variant", type=int, default=None, help="hemi-Dslash kernel variant 0..3")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="hemi-Dslash kernel variant 0..3, -1 built-in default, -2 autotuned "
+                         "(the trajectory benchmark autotunes by default)")
     return ap.parse_args()
 
 
@@ -318,6 +320,8 @@ def run_hmc(args):
 
     inner = hmc.F16 if args.inner == "f16" else hmc.F32
     ctx = hmc.Context(local)
+    # autotuned hemi-Dslash variants (tuned during the warm-up steps)
+    ctx.set_dslash_variant(-2 if args.variant is None else args.variant)
     n_eta = len(KAPPA_MP) + 1 if args.mp else 1
     U, P, eta = build_inputs(rank, n_eta)
     b, alpha, c = coeffs()
@@ -411,6 +415,7 @@ def run_hmc(args):
                    "lattice": "x".join(str(v) for v in LAT[::-1]), **{k: v for k, v in work.items()},
                    "inner_prec": args.inner, "reliable_delta": args.delta,
                    "force_prec": args.force_prec, "f64_emul": args.f64_emul,
+                   "dslash_variant": "autotuned" if args.variant is None else args.variant,
                    "links": "12-real (inner), 18-real FP64",
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

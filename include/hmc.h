@@ -123,7 +123,12 @@ int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
  * n_rhs == 1; otherwise consecutive sites), bit 1 issues the loads of both
  * hops of a direction before their arithmetic.  Every variant computes the
  * same result bit for bit.  Default -1: paired loads for LINK18 only (the
- * fastest choice measured on 24^3 x 48). */
+ * fastest choice measured on 24^3 x 48).  -2: autotune: the first launch of
+ * each class (precision, link format, dagger, n_rhs, lattice) that can be
+ * repeated without changing its result times every applicable variant (one
+ * warm-up and three timed launches each, synchronising the stream) and the
+ * class keeps the fastest; the solvers tune their classes on scratch fields
+ * before iterating.  Launches during stream capture are never tuned. */
 #define HMC_OPT_DSLASH_VARIANT 1
 /* HMC_OPT_CG_GRAPH: 1 (default) replays the CG iterations of hmc_cg_solve
  * (and of every single-system solve inside the force, action and trajectory

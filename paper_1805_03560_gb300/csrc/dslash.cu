@@ -408,6 +408,89 @@ static void launch_sf(const DslashArgs &a, int dagger, bool pair, int nb, cudaSt
   }
 }
 
+// Launch variant `var` (bit 0 tiled site mapping, bit 1 paired loads) of the
+// kernel for (sprec, fmt); false for an unsupported combination.
+static bool launch_variant(const DslashArgs &a, int sprec, int fmt, int dagger, int var, int nb,
+                           cudaStream_t st) {
+  DslashArgs aa = a;
+  aa.tile_nseg = 0;
+  const int sx = a.g.L[2] * a.g.Lzh;
+  if ((var & 1) && a.n_rhs == 1 && sx % 32 == 0) aa.tile_nseg = sx / 32;
+  const bool pair = (var & 2) != 0;
+  switch (sprec * 100 + fmt) {
+    case HMC_F64 * 100 + 18: launch_sf<HMC_F64, 18>(aa, dagger, pair, nb, st); break;
+    case HMC_F64 * 100 + 12: launch_sf<HMC_F64, 12>(aa, dagger, pair, nb, st); break;
+    case HMC_F32 * 100 + 18: launch_sf<HMC_F32, 18>(aa, dagger, pair, nb, st); break;
+    case HMC_F32 * 100 + 12: launch_sf<HMC_F32, 12>(aa, dagger, pair, nb, st); break;
+    case HMC_F16 * 100 + 18: launch_sf<HMC_F16, 18>(aa, dagger, pair, nb, st); break;
+    case HMC_F16 * 100 + 12: launch_sf<HMC_F16, 12>(aa, dagger, pair, nb, st); break;
+    case HMC_F64E * 100 + 18: launch_sf<HMC_F64E, 18>(aa, dagger, pair, nb, st); break;
+    case HMC_F64E * 100 + 12: launch_sf<HMC_F64E, 12>(aa, dagger, pair, nb, st); break;
+    default: return false;
+  }
+  return true;
+}
+
+// ---- autotuner (HMC_OPT_DSLASH_VARIANT = -2) ------------------------------------
+// The kernel variants compute bit-identical results and differ only in speed,
+// which depends on the lattice, the precision, the link format and the number
+// of right-hand sides.  The first launch of a (precision, format, dagger,
+// n_rhs, lattice) class that can be repeated without changing its result (no
+// gate, no fused CG update, no reductions) times every applicable variant
+// (one warm-up and three timed launches each, CUDA events on the context's
+// stream, which it synchronises) and keeps the fastest for the class; every
+// later launch of the class, with or without an epilogue, uses it.  Launches
+// of an untuned class that cannot be repeated, and launches while the stream
+// is being captured, use the built-in default.
+static std::string tune_key(const DslashArgs &a, int sprec, int fmt, int dagger) {
+  char k[96];
+  snprintf(k, sizeof k, "%d/%d/%d/%d/%d.%d.%d.%d", sprec, fmt, dagger, a.n_rhs, a.g.L[0], a.g.L[1],
+           a.g.L[2], a.g.L[3]);
+  return k;
+}
+
+static int default_variant(int fmt) { return fmt == 18 ? 2 : 0; }
+
+static int tune_variant(hmc_ctx *ctx, const DslashArgs &a, int sprec, int fmt, int dagger, int nb) {
+  const std::string key = tune_key(a, sprec, fmt, dagger);
+  auto it = ctx->ds_tuned.find(key);
+  if (it != ctx->ds_tuned.end()) return it->second;
+  const bool repeatable = !a.gate && !a.cg_x && !a.partials && !a.total && !a.red_src &&
+                          a.out != a.x && a.out != a.in;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(ctx->stream, &cs);
+  if (!repeatable || cs != cudaStreamCaptureStatusNone) return default_variant(fmt);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return default_variant(fmt);
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return default_variant(fmt);
+  }
+  const int sx = a.g.L[2] * a.g.Lzh;
+  const bool tiles = a.n_rhs == 1 && sx % 32 == 0;
+  int best = default_variant(fmt);
+  float best_ms = 1e30f;
+  for (int v = 0; v < 4; ++v) {
+    if ((v & 1) && !tiles) continue;
+    launch_variant(a, sprec, fmt, dagger, v, nb, ctx->stream);
+    cudaEventRecord(e0, ctx->stream);
+    for (int r = 0; r < 3; ++r) launch_variant(a, sprec, fmt, dagger, v, nb, ctx->stream);
+    cudaEventRecord(e1, ctx->stream);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+      continue;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->launches += tiles ? 16 : 8;
+  ctx->ds_tuned[key] = best;
+  return best;
+}
+
 int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int dagger,
            int *nblocks) {
   if (U.prec != sprec)
@@ -435,31 +518,35 @@ int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int
            U.fmt, a.tag ? "/" : "",
            a.tag ? a.tag : "");
   // kernel variant (hmc_ctx_set_option): bit 0 tiled site mapping, bit 1
-  // paired loads
-  // (default, -1: paired loads for 18-real links only; measured on 24^3 x 48,
-  // pairing helps the 18-real kernels and slows the 12-real ones, tiling
-  // helps neither)
-  DslashArgs aa = a;
-  aa.tile_nseg = 0;
-  const int var = ctx->ds_variant >= 0 ? ctx->ds_variant : (U.fmt == 18 ? 2 : 0);
-  const int sx = a.g.L[2] * a.g.Lzh;
-  if ((var & 1) && a.n_rhs == 1 && sx % 32 == 0) aa.tile_nseg = sx / 32;
-  const bool pair = (var & 2) != 0;
+  // paired loads.  Default -1: paired loads for 18-real links only (measured
+  // on 24^3 x 48, pairing helps the 18-real kernels and slows the 12-real
+  // ones, tiling helps neither); -2: autotuned per class.
+  int var = ctx->ds_variant >= 0 ? ctx->ds_variant : default_variant(U.fmt);
+  if (ctx->ds_variant == -2) var = tune_variant(ctx, a, sprec, U.fmt, dagger, nb);
   TimedLaunch timer(ctx, cls, bytes);
-  switch (sprec * 100 + U.fmt) {
-    case HMC_F64 * 100 + 18: launch_sf<HMC_F64, 18>(aa, dagger, pair, nb, st); break;
-    case HMC_F64 * 100 + 12: launch_sf<HMC_F64, 12>(aa, dagger, pair, nb, st); break;
-    case HMC_F32 * 100 + 18: launch_sf<HMC_F32, 18>(aa, dagger, pair, nb, st); break;
-    case HMC_F32 * 100 + 12: launch_sf<HMC_F32, 12>(aa, dagger, pair, nb, st); break;
-    case HMC_F16 * 100 + 18: launch_sf<HMC_F16, 18>(aa, dagger, pair, nb, st); break;
-    case HMC_F16 * 100 + 12: launch_sf<HMC_F16, 12>(aa, dagger, pair, nb, st); break;
-    case HMC_F64E * 100 + 18: launch_sf<HMC_F64E, 18>(aa, dagger, pair, nb, st); break;
-    case HMC_F64E * 100 + 12: launch_sf<HMC_F64E, 12>(aa, dagger, pair, nb, st); break;
-    default:
-      return fail(ctx, HMC_EINVAL, "dslash: unsupported precision %d / link format %d", sprec,
-                  U.fmt);
-  }
+  if (!launch_variant(a, sprec, U.fmt, dagger, var, nb, st))
+    return fail(ctx, HMC_EINVAL, "dslash: unsupported precision %d / link format %d", sprec,
+                U.fmt);
   return launched(ctx, cls);
+}
+
+// Tune the variant classes of (sprec, U.fmt, n_rhs) for both daggers on
+// scratch fields: out is overwritten, in only read (no-op unless the context
+// autotunes).
+int dslash_tune(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, int sprec, int n_rhs, void *out,
+                const void *in) {
+  if (ctx->ds_variant != -2 || U.prec != sprec) return HMC_OK;
+  DslashArgs a{};
+  a.g = g;
+  a.n_rhs = n_rhs;
+  a.gauge = U.data;
+  a.p = 1;
+  a.out = out;
+  a.in = in;
+  a.cb = 1.0;
+  const int nb = blocks_for((long long)g.Vh * n_rhs, DS_NT);
+  for (int d = 0; d < 2; ++d) tune_variant(ctx, a, sprec, U.fmt, d, nb);
+  return cuda_ok(ctx, cudaGetLastError(), "dslash autotune");
 }
 
 int mhat(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, int sprec, int dagger, int n_rhs,

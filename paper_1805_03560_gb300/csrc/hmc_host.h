@@ -33,6 +33,8 @@ struct hmc_ctx {
   // library's own non-blocking stream for capture and replay, ordered after
   // and before the caller's stream by gev
   int cg_graph = 1;
+  // autotuned hemi-Dslash variant per launch class (ds_variant == -2)
+  std::map<std::string, int> ds_tuned;
   cudaStream_t gstream = nullptr;
   cudaEvent_t gev[2] = {nullptr, nullptr};
   struct Pending {
@@ -129,6 +131,10 @@ struct DslashArgs {
 };
 int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int dagger,
            int *nblocks);
+// autotune the hemi-Dslash classes of (sprec, U.fmt, n_rhs) on scratch fields
+// (no-op unless HMC_OPT_DSLASH_VARIANT is -2)
+int dslash_tune(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, int sprec, int n_rhs, void *out,
+                const void *in);
 
 int zero_field(hmc_ctx *ctx, int prec, void *d, int S);
 int copy_convert(hmc_ctx *ctx, int pd, int ps, void *d, const void *s, int S);

@@ -602,6 +602,9 @@ int cg_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
     TRY(copy_convert(ctx, s.plo, HMC_F64, s.rlo, b, s.S));
     TRY(copy_convert(ctx, s.plo, HMC_F64, s.p, b, s.S));
   }
+  // autotuning contexts time the iteration's hemi-Dslash classes here, on
+  // scratch (t = H p), before any launch of the iteration exists
+  TRY(dslash_tune(ctx, g, mixed ? s.Ul : s.Uh, s.plo, 1, s.tlo, s.p));
   CGState h{};
   TRY(read_state(s, &h));
   const double b2 = h.b2, thr_tol = tol * tol * b2;

@@ -219,3 +219,33 @@ def test_dslash_variants_bit_identical(orc, ctx, H, prec):
     assert np.isfinite(outs[0]).all()
     Uq = _np(ctx.unpack_gauge(L, Ud))
     assert _rel(outs[0], orc.hop_eo(L, Uq, 0, _np(ctx.unpack_spinor(L, src)))) <= TOL[prec]
+
+
+def test_autotuned_variants_give_identical_results(orc, ctx, H):
+    """With the autotuner (variant -2) every launch class runs the variant it
+    timed fastest; the variants are bit-identical, so the Dslash, Mhat and a
+    mixed-precision CG return exactly what the default variants return."""
+    L = (4, 4, 8, 16)  # Ly * Lz/2 = 64: tiled variants apply
+    U = I.gauge_links(L, 0.3, 1)
+    psi = I.gaussian_half(L, 3)
+    res = []
+    for v in (-1, -2):
+        ctx.set_dslash_variant(v)
+        r = []
+        for prec, fmt in ((0, 18), (1, 12), (3, 18)):
+            Ud = ctx.pack_gauge(L, U, prec, fmt)
+            src = ctx.pack_spinor(L, psi, prec)
+            out = ctx.new_spinor(L, prec)
+            ctx.dslash(L, Ud, out, src, 0, False)
+            r.append(_np(ctx.unpack_spinor(L, out)))
+            ctx.mhat(L, Ud, out, src, 0.156, True)
+            r.append(_np(ctx.unpack_spinor(L, out)))
+        Uh = ctx.pack_gauge(L, U, 0, 18)
+        Ul = ctx.pack_gauge(L, U, 1, 12)
+        x = ctx.new_spinor(L, 0)
+        ctx.cg_solve(L, Uh, x, ctx.pack_spinor(L, psi, 0), 0.156, 1e-10, U_lo=Ul, inner_prec=1)
+        r.append(_np(ctx.unpack_spinor(L, x)))
+        res.append(r)
+    ctx.set_dslash_variant(-1)
+    for a, b in zip(res[0], res[1]):
+        assert np.array_equal(a, b)
