@@ -203,6 +203,9 @@ int hmc_ctx_create(int device, hmc_ctx **out) {
   if (cudaSetDevice(device) != cudaSuccess) return HMC_ECUDA;
   hmc_ctx *c = new hmc_ctx();
   c->device = device;
+  if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      c->sm_count < 1)
+    c->sm_count = 1;
   if (cudaMallocHost(&c->h_pinned, 64 * sizeof(double)) != cudaSuccess) {
     delete c;
     return HMC_ENOMEM;

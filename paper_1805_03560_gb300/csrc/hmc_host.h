@@ -28,6 +28,7 @@ struct hmc_ctx {
   // hemi-Dslash kernel variant: bit 0 tiled site mapping, bit 1 paired loads;
   // -1 chooses per link format
   int ds_variant = -1;
+  int sm_count = 1;  // streaming multiprocessors of the device
   // CG iterations replayed from a captured CUDA graph (two iterations per
   // graph, captured once per solve) when timing is off; gstream: the
   // library's own non-blocking stream for capture and replay, ordered after

@@ -172,17 +172,18 @@ __global__ void __launch_bounds__(BL_NT) k_cg_xpay(void *p, const void *r, int S
     }
   }
   const R beta = (R)(rr_new / st->rr[par]);
-  int i = blockIdx.x * BL_NT + threadIdx.x;
-  if (i >= S) return;
-  Cx<R> rv[12], pv[12];
-  load_as<PL>(r, S, i, rv);
-  load_as<PL>(p, S, i, pv);
+  // grid-stride: the grid is a few blocks per SM, so few blocks read the partials
+  for (int i = blockIdx.x * BL_NT + threadIdx.x; i < S; i += gridDim.x * BL_NT) {
+    Cx<R> rv[12], pv[12];
+    load_as<PL>(r, S, i, rv);
+    load_as<PL>(p, S, i, pv);
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    pv[k].re = fma(beta, pv[k].re, rv[k].re);
-    pv[k].im = fma(beta, pv[k].im, rv[k].im);
+    for (int k = 0; k < 12; ++k) {
+      pv[k].re = fma(beta, pv[k].re, rv[k].re);
+      pv[k].im = fma(beta, pv[k].im, rv[k].im);
+    }
+    store_as<PL>(p, S, i, pv);
   }
-  store_as<PL>(p, S, i, pv);
 }
 
 // x (F64) += y (F32); y = 0        (reliable update)
@@ -364,7 +365,8 @@ int apply_A64(Solve &s, const void *in, void *out) {
 
 template <int PL>
 void launch_xpay(Solve &s, int par, int n_part) {
-  k_cg_xpay<PL><<<s.nb_bl, BL_NT, 0, s.ctx->stream>>>(s.p, s.rlo, s.S, s.st, par,
+  const int nb = s.nb_bl < 2 * s.ctx->sm_count ? s.nb_bl : 2 * s.ctx->sm_count;
+  k_cg_xpay<PL><<<nb, BL_NT, 0, s.ctx->stream>>>(s.p, s.rlo, s.S, s.st, par,
                                                       s.plo == HMC_F64 ? 1 : 0, s.rr_part,
                                                       n_part);
 }
