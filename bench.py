@@ -69,12 +69,16 @@ def parse():
                     help="trajectory length (applied after --n-md, which scales it)")
     ap.add_argument("--integrator", default="leapfrog", choices=["leapfrog", "omelyan"],
                     help="two-level leapfrog, or the second-order Omelyan scheme (lambda 1/6)")
+    ap.add_argument("--thermal-kappa", type=float, default=0.156,
+                    help="hopping parameter of the --report thermal trajectories")
     ap.add_argument("--mp", action="store_true",
                     help="mass-preconditioned workload: pseudo-fermions at kappa' = 0.150, "
                          "0.154 and the target kappa (ratio terms, batched solves), no filter")
-    ap.add_argument("--report", default=None, choices=["md"],
+    ap.add_argument("--report", default=None, choices=["md", "thermal"],
                     help="md: leapfrog dH at dt = 1/10, 1/20, 1/40 and reversibility on "
-                         "16^3x32, kappa 0.156, plain pseudo-fermion action")
+                         "16^3x32, kappa 0.156, plain pseudo-fermion action; thermal: mixed "
+                         "vs plain FP64 trajectories (Omelyan, 20 steps) on a 16^3x32 field "
+                         "relaxed by pure-gauge HMC (dH, acceptance, time)")
     ap.add_argument("--variant", type=int, default=None,
                     help="hemi-Dslash kernel variant 0..3, -1 built-in default, -2 autotuned "
                          "(the trajectory benchmark autotunes by default)")
@@ -622,9 +626,106 @@ def run_md_report(args):
               flush=True)
 
 
+def quenched_hmc(ctx, L, Ud, beta, n_traj, n_steps, seed):
+    """Pure-gauge HMC (leapfrog, tau = 1) driven through the C ABI: gauge
+    force, momentum and link updates, Wilson action.  Relaxes the synthetic
+    start towards an equilibrium gauge field: the first half of the
+    trajectories are always kept (molecular-dynamics relaxation from a start
+    far from equilibrium), the second half pass a Metropolis test on the
+    host, whose acceptance rate is returned."""
+    import numpy as np
+    from paper_1805_03560_gb300 import hmc
+    from paper_1805_03560_gb300 import inputs as I
+    rng = np.random.default_rng(seed)
+    F = ctx.new_algebra(L)
+    Ub = ctx.new_gauge(L, hmc.F64, hmc.LINK18)
+    dt = 1.0 / n_steps
+    acc = 0
+    for t in range(n_traj):
+        P = ctx.pack_algebra(L, I.momenta(L, seed + 1000 + t))
+        Ub.data.copy_(Ud.data)
+        H0 = ctx.kinetic(L, P) + ctx.force_hopexp(L, Ud, beta, 0.0, 0)
+        F.data.zero_()
+        ctx.force_hopexp(L, Ud, beta, 0.0, 0, F=F, want_action=False)
+        ctx.update_momenta(L, P, F, 0.5 * dt)
+        for s in range(n_steps):
+            ctx.update_links(L, Ud, P, dt)
+            F.data.zero_()
+            ctx.force_hopexp(L, Ud, beta, 0.0, 0, F=F, want_action=False)
+            ctx.update_momenta(L, P, F, dt if s + 1 < n_steps else 0.5 * dt)
+        H1 = ctx.kinetic(L, P) + ctx.force_hopexp(L, Ud, beta, 0.0, 0)
+        if t < n_traj // 2:
+            continue
+        if rng.uniform() < np.exp(min(0.0, -(H1 - H0))):
+            acc += 1
+        else:
+            Ud.data.copy_(Ub.data)
+    return acc / max(n_traj - n_traj // 2, 1), ctx.plaquette(L, Ud)
+
+
+def run_thermal_report(args):
+    """Mixed-precision against plain FP64 HMC trajectories from a gauge field
+    relaxed by pure-gauge HMC (beta 5.85, which gives a plaquette near the
+    paper's dynamical beta = 5.6 ensembles), on 16^3 x 32 at beta 5.6,
+    kappa 0.156 (plain pseudo-fermion action, tau = 1, two-scale Omelyan):
+    dH, exp(-dH) acceptance, CG iterations and time per trajectory, each
+    trajectory with the same (Pi, eta) on both paths."""
+    import numpy as np
+    import torch
+    from paper_1805_03560_gb300 import hmc
+    from paper_1805_03560_gb300 import inputs as I
+    L = (32, 16, 16, 16)
+    ctx = hmc.Context(0)
+    Ud = ctx.pack_gauge(L, I.gauge_links(L, EPS_LINKS, 1), hmc.F64, hmc.LINK18)
+    t0 = time.time()
+    acc_q, plaq = quenched_hmc(ctx, L, Ud, 5.85, 40, 20, 11)
+    print(json.dumps({"report": "thermal", "stage": "pure-gauge HMC", "beta": 5.85, "trajectories": 40,
+                      "acceptance": acc_q, "plaquette": plaq, "s": round(time.time() - t0, 2)}),
+          flush=True)
+    U0 = ctx.new_gauge(L, hmc.F64, hmc.LINK18)
+    U0.data.copy_(Ud.data)
+    # second-order Omelyan, lambda = 1/6 (the paper's choice), 20 coarse steps:
+    # acceptance near 0.95 on this field (the leapfrog needs ~40 steps for 0.2)
+    base = dict(beta=5.6, kappa=args.thermal_kappa, tau=1.0, n_md=args.n_md or 20, n_gauge=4,
+                tol_md=1e-10, tol_action=1e-12, integrator=hmc.OMELYAN, lam=1.0 / 6.0)
+    paths = {"mixed": dict(inner_prec=hmc.F32, force_prec=hmc.F32, reliable_delta=args.delta,
+                           f64_emul=1)}
+    if not args.no_fp64:
+        paths["fp64"] = dict(inner_prec=hmc.F64, force_prec=hmc.F64, f64_emul=0)
+    res = {k: [] for k in paths}
+    for t in range(3):
+        P = ctx.pack_algebra(L, I.momenta(L, 500 + t))
+        eta = ctx.pack_spinor(L, I.gaussian_half(L, 600 + t), hmc.F64)
+        for name, kw in paths.items():
+            U = ctx.new_gauge(L, hmc.F64, hmc.LINK18)
+            U.data.copy_(U0.data)
+            torch.cuda.synchronize()
+            t1 = time.time()
+            r = ctx.trajectory(L, U, P, eta, 0.5, **base, **kw)
+            torch.cuda.synchronize()
+            res[name].append(dict(dH=r["dH"], cg_iterations=r["cg_iterations"],
+                                  s=time.time() - t1))
+    out = {"report": "thermal", "lattice": "16^3x32", "plaquette_start": plaq,
+           **{k: v for k, v in base.items()}}
+    for name, rs in res.items():
+        dH = np.array([r["dH"] for r in rs])
+        out[name] = {"dH": [round(float(x), 6) for x in dH],
+                     "acceptance_mean": round(float(np.mean(np.minimum(1.0, np.exp(-dH)))), 4),
+                     "cg_iterations": [r["cg_iterations"] for r in rs],
+                     "s_per_trajectory": round(float(np.mean([r["s"] for r in rs])), 3)}
+    if "fp64" in out:
+        out["dH_diff_max"] = float(np.max(np.abs(np.array(out["mixed"]["dH"]) -
+                                                 np.array(out["fp64"]["dH"]))))
+        out["speedup"] = round(out["fp64"]["s_per_trajectory"] / out["mixed"]["s_per_trajectory"],
+                               2)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
-    if args.report == "md":
+    if args.report == "thermal":
+        run_thermal_report(args)
+    elif args.report == "md":
         run_md_report(args)
     elif args.kernel:
         run_kernel(args)
