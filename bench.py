@@ -33,7 +33,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Dslash HBM GB/s (% of peak); s/trajectory mixed-batched vs plain FP64 at rr<=1e-10"
-LAT = (48, 24, 24, 24)  # Lt, Lx, Ly, Lz
+LAT = (48, 24, 24, 24)  # Lt, Lx, Ly, Lz (--lattice changes it)
+LATTICES = {"24x48": (48, 24, 24, 24), "32x64": (64, 32, 32, 32), "16x32": (32, 16, 16, 16)}
+
+
+def lat_name():
+    return f"{LAT[1]}^3x{LAT[0]}"
 WORK = dict(beta=5.6, kappa=0.1575, tau=1.0, n_md=10, n_gauge=4, filter_k=2, n_t=9, n_max=29,
             tol_md=1e-10, tol_action=1e-12)
 EPS_LINKS = 0.3
@@ -71,6 +76,8 @@ def parse():
                     help="two-level leapfrog, or the second-order Omelyan scheme (lambda 1/6)")
     ap.add_argument("--thermal-kappa", type=float, default=0.156,
                     help="hopping parameter of the --report thermal trajectories")
+    ap.add_argument("--lattice", default="24x48", choices=sorted(LATTICES),
+                    help="L^3 x T of the benchmark lattice (default 24^3 x 48)")
     ap.add_argument("--mp", action="store_true",
                     help="mass-preconditioned workload: pseudo-fermions at kappa' = 0.150, "
                          "0.154 and the target kappa (ratio terms, batched solves), no filter")
@@ -413,9 +420,10 @@ def run_hmc(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.inner,
         "data": "synthetic (seeded exp(i 0.3 A) links, Gaussian momenta and sources)",
-        "config": {"workload": ("hmc-trajectory 24^3x48 kappa=0.1575 beta=5.6 mass-preconditioned "
-                                 "kappa'=0.150,0.154 (batched solves)" if args.mp else
-                                 "hmc-trajectory 24^3x48 kappa=0.1575 beta=5.6 kappa^4-filter"),
+        "config": {"workload": (f"hmc-trajectory {lat_name()} kappa=0.1575 beta=5.6 "
+                                 "mass-preconditioned kappa'=0.150,0.154 (batched solves)"
+                                 if args.mp else
+                                 f"hmc-trajectory {lat_name()} kappa=0.1575 beta=5.6 kappa^4-filter"),
                    "lattice": "x".join(str(v) for v in LAT[::-1]), **{k: v for k, v in work.items()},
                    "inner_prec": args.inner, "reliable_delta": args.delta,
                    "force_prec": args.force_prec, "f64_emul": args.f64_emul,
@@ -544,7 +552,7 @@ def oracle_dslash_sample(n_apply):
 def cpu_baseline():
     gbs, dt = oracle_dslash_sample(4)
     return {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"4 hemi-Dslash applications of the FP64 C oracle on 24^3x48 "
+            "sample": f"4 hemi-Dslash applications of the FP64 C oracle on {lat_name()} "
                       f"({dt:.2f} s each, single thread), FP64 18-real algorithmic bytes"}
 
 
@@ -566,10 +574,10 @@ def run_reference(args):
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(dt * 1e3, 1), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "hmc-trajectory 24^3x48 kappa=0.1575 beta=5.6 kappa^4-filter",
+           "config": {"workload": f"hmc-trajectory {lat_name()} kappa=0.1575 beta=5.6 kappa^4-filter",
                       "sample": "one FP64 oracle hemi-Dslash of the lattice per step"},
            "cpu_baseline": {"value": round(val, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                            "sample": "one hemi-Dslash of 24^3x48 per step, single thread"},
+                            "sample": f"one hemi-Dslash of {lat_name()} per step, single thread"},
            "e2e": {"value": round(val, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -722,7 +730,9 @@ def run_thermal_report(args):
 
 
 def main():
+    global LAT
     args = parse()
+    LAT = LATTICES[args.lattice]
     if args.report == "thermal":
         run_thermal_report(args)
     elif args.report == "md":
