@@ -61,6 +61,7 @@ class TrajParams(ctypes.Structure):
         ("b", _P), ("c", _P), ("alpha", _D),
         ("n_mp", _I), ("kappa_mp", _P),
         ("integrator", _I), ("lam", _D),
+        ("root_levels", _I), ("root_N", _I), ("root_deg", _P), ("root_c", _P),
     ]
 
 
@@ -94,6 +95,7 @@ def _declare(l):
         "or_pf_action": (_D, [_P, _P, _D, _P, _D]),
         "or_pf_force": (None, [_P, _P, _D, _P, _D, _D, _P]),
         "or_ratio_action": (_D, [_P, _P, _D, _D, _P, _D]),
+        "or_poly_solve": (_I, [_P, _P, _D, _P, _I, _P, _P, _D, _I, _P]),
         "or_ratio_force": (None, [_P, _P, _D, _D, _P, _D, _D, _P]),
         "or_ratio_heatbath": (None, [_P, _P, _D, _D, _P, _D, _P]),
         "or_hop_force": (None, [_P, _P, _D, _P, _P, _D, _P]),
@@ -255,6 +257,16 @@ def pf_force(L, U, kappa, phi, tol=1e-13):
     return F
 
 
+def poly_solve(L, U, kappa, c, b, tol=1e-13):
+    """x = P(K)^{-1} b with P(K) = sum_i c_i K^i; returns (x, iterations, rel_res)."""
+    U = _c(U, np.complex128); b = _c(b, np.complex128); c = _c(c, np.float64)
+    x = np.zeros_like(b)
+    rel = ctypes.c_double(0)
+    it = lib().or_poly_solve(_dims(L), _ptr(U), kappa, _ptr(c), len(c) - 1, _ptr(b), _ptr(x),
+                             tol, 100000, ctypes.byref(rel))
+    return x, it, rel.value
+
+
 def ratio_action(L, U, kappa_a, kappa_b, phi, tol=1e-13):
     """Hasenbusch ratio term |Mhat_a^dag Mhat_b^{-dag} phi|^2 (kappa_a = 0: plain)."""
     U = _c(U, np.complex128); phi = _c(phi, np.complex128)
@@ -362,7 +374,7 @@ def kinetic(L, P):
 
 def _params(beta, kappa, tau, n_md, n_gauge, filter_k=0, n_t=0, n_max=0,
             tol_md=1e-12, tol_action=1e-13, b=None, c=None, alpha=0.0, kappa_mp=None,
-            integrator=0, lam=1.0 / 6.0):
+            integrator=0, lam=1.0 / 6.0, root_polys=None, root_N=0):
     """kappa_mp: heavier hopping parameters of a mass-preconditioned chain;
     eta / phi then carry len(kappa_mp) + 1 half fields ([n, Vh, 4, 3]).
     integrator: 0 leapfrog, 1 Omelyan with parameter lam."""
@@ -374,6 +386,15 @@ def _params(beta, kappa, tau, n_md, n_gauge, filter_k=0, n_t=0, n_max=0,
         km = _c(kappa_mp, np.float64); keep.append(km)
         p.n_mp = len(km)
         p.kappa_mp = km.ctypes.data
+    if root_polys:
+        arrs = [_c(c, np.float64) for c in root_polys]
+        deg = np.array([len(c) - 1 for c in root_polys], dtype=np.int32)
+        ptrs = (ctypes.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+        keep += arrs + [deg, ptrs]
+        p.root_levels = len(arrs)
+        p.root_N = root_N
+        p.root_deg = deg.ctypes.data
+        p.root_c = ctypes.cast(ptrs, ctypes.c_void_p)
     if b is not None:
         b = _c(b, np.float64); keep.append(b); p.b = b.ctypes.data
     if c is not None:

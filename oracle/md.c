@@ -128,6 +128,17 @@ static void mp_pair(const or_traj_params *p, int j, double *ka, double *kb) {
 
 static double fermion_action(const int L[4], const ocplx *U, const ocplx *phi,
                              const or_traj_params *p) {
+  if (p->root_levels > 0) {
+    long n12 = or_volume(L) / 2 * 12;
+    double s = 0;
+    int f = 0;
+    for (int j = 0; j < p->root_levels; ++j)
+      for (int i = 0; i < p->root_N; ++i, ++f)
+        s += or_filtered_action(L, U, p->kappa, p->root_c[j], p->root_deg[j], 0.0,
+                                phi + f * n12, p->tol_action);
+    return s + or_filtered_action(L, U, p->kappa, p->b, p->n_max, p->alpha, phi + f * n12,
+                                  p->tol_action);
+  }
   if (p->n_mp > 0) {
     long n12 = or_volume(L) / 2 * 12;
     double s = 0;
@@ -166,7 +177,15 @@ static void fermion_force(const int L[4], const ocplx *U, const ocplx *phi,
                           const or_traj_params *p, double *F) {
   long nP = or_volume(L) * 32;
   memset(F, 0, nP * sizeof(double));
-  if (p->n_mp > 0) {
+  if (p->root_levels > 0) {
+    long n12 = or_volume(L) / 2 * 12;
+    int f = 0;
+    for (int j = 0; j < p->root_levels; ++j)
+      for (int i = 0; i < p->root_N; ++i, ++f)
+        or_filtered_force(L, U, p->kappa, p->root_c[j], p->root_deg[j], 0.0, phi + f * n12,
+                          p->tol_md, 1.0, F);
+    or_filtered_force(L, U, p->kappa, p->b, p->n_t, p->alpha, phi + f * n12, p->tol_md, 1.0, F);
+  } else if (p->n_mp > 0) {
     long n12 = or_volume(L) / 2 * 12;
     for (int j = 0; j <= p->n_mp; ++j) {
       double ka, kb;
@@ -251,7 +270,8 @@ int or_trajectory(const int L[4], ocplx *U, const double *P0, const ocplx *eta,
                   double u_metropolis, const or_traj_params *p,
                   or_traj_result *res, ocplx *U_out, double *P_out) {
   long V = or_volume(L), n12 = V / 2 * 12, nU = V * 4 * 9, nP = V * 32;
-  const int n_terms = p->n_mp > 0 ? p->n_mp + 1 : 1;
+  const int n_terms = p->root_levels > 0 ? p->root_levels * p->root_N + 1
+                      : (p->n_mp > 0 ? p->n_mp + 1 : 1);
   ocplx *phi = malloc(n_terms * n12 * sizeof(ocplx));
   ocplx *U1 = malloc(nU * sizeof(ocplx));
   double *P = malloc(nP * sizeof(double));
@@ -259,7 +279,28 @@ int or_trajectory(const int L[4], ocplx *U, const double *P0, const ocplx *eta,
   memcpy(P, P0, nP * sizeof(double));
   /* heatbath of the pseudo-fermion field */
   double H0;
-  if (p->n_mp > 0) {
+  if (p->root_levels > 0) {
+    /* polynomial terms: phi = P_j^{-1} eta; remainder phi = M_{J+1} eta;
+     * H0 with the actions evaluated at the start (the remainder's heatbath
+     * series is truncated) */
+    int f = 0;
+    double rel;
+    for (int j = 0; j < p->root_levels; ++j)
+      for (int i = 0; i < p->root_N; ++i, ++f)
+        or_poly_solve(L, U, p->kappa, p->root_c[j], p->root_deg[j], eta + f * n12,
+                      phi + f * n12, p->tol_action, 100000, &rel);
+    ocplx *t = malloc(n12 * sizeof(ocplx)), *t2 = malloc(n12 * sizeof(ocplx));
+    or_poly_K(L, U, p->kappa, p->c, p->n_max, eta + f * n12, t);
+    or_mhat(L, U, p->kappa, 0, t, t2);
+    for (int j = 0; j < p->root_levels; ++j)
+      for (int q = 0; q < p->root_N; ++q) {
+        or_poly_K(L, U, p->kappa, p->root_c[j], p->root_deg[j], t2, t);
+        memcpy(t2, t, n12 * sizeof(ocplx));
+      }
+    memcpy(phi + f * n12, t2, n12 * sizeof(ocplx));
+    free(t); free(t2);
+    H0 = or_hamiltonian(L, U, P, phi, p);
+  } else if (p->n_mp > 0) {
     /* phi_j = Mhat_b^dag Mhat_a^{-dag} eta_j: S_j(phi_j) = |eta_j|^2 */
     double e2 = 0;
     for (int j = 0; j < n_terms; ++j) {

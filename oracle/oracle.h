@@ -141,6 +141,13 @@ void or_ratio_heatbath(const int L[4], const ocplx *U, double kappa_a,
                        double kappa_b, const ocplx *eta, double tol,
                        ocplx *phi);
 
+/* ---- rooted-polynomial pseudo-fermions (rooted.c) ------------------------- */
+/* x = P(K)^{-1} b, P(K) = sum_i c_i K^i, by CG on P^dag P stopping on the
+ * true residual |b - P x| / |b| <= tol; returns the iterations or -1 */
+int or_poly_solve(const int L[4], const ocplx *U, double kappa, const double *c,
+                  int deg, const ocplx *b, ocplx *x, double tol, int max_iter,
+                  double *rel_res);
+
 /* ---- molecular dynamics (md.c) --------------------------------------------- */
 /* expo = exp(A) for a 3x3 complex matrix (scaling and squaring of Taylor) */
 void or_expm3(const ocplx A[9], ocplx expo[9]);
@@ -180,6 +187,17 @@ typedef struct {
    * two inner blocks of a coarse step. */
   int integrator;
   double lambda;
+  /* rooted-polynomial hierarchy (Sec. II.A): root_levels > 0 polynomials
+   * P_j(K) (coefficients root_c[j][0..root_deg[j]]), root_N pseudo-fermions
+   * each with the action |P_j(K) phi|^2, plus the remainder
+   * |(alpha Mhat^{-1} + sum_{n<=n_max} b_n K^n) phi|^2 (force truncated at
+   * n_t) with b, alpha, c as for filtering; filter_k (0, 1, 2) is the order
+   * of Mtilde and of T_k in the gauge action.  eta / phi hold
+   * root_levels * root_N + 1 consecutive fields, the remainder last; its
+   * heatbath is phi = prod_j P_j^N Mhat sum c_n K^n eta.  Requires n_mp = 0. */
+  int root_levels, root_N;
+  const int *root_deg;
+  const double *const *root_c;
 } or_traj_params;
 
 typedef struct {
