@@ -377,6 +377,19 @@ int hmc_heatbath_mp(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
                     const hmc_solver_opts *opts, void *phi,
                     hmc_solve_stats *stats);
 
+/* hmc_poly_solve: x = P(K)^{-1} b with P(K) = sum_{i<=degree} coeffs[i] K^i
+ * (host coefficients), K = kappa^2 H_eo H_oe: the heatbath of a
+ * rooted-polynomial pseudo-fermion (Sec. II.A), whose action |P(K) phi|^2
+ * equals |b|^2 at phi = P^{-1} b.  CG on P^dag P with FP64-accurate
+ * polynomial applications (emulated FP64 when opts->f64_emul), stopping on
+ * the true residual |b - P x| / |b| <= tol; max_iter <= 0 means 100000.
+ * x and b: F64 even fields, x must not alias b.  stats (nullable) gets the
+ * iterations and the residual.  HMC_ENOCONV if not converged.  Blocking. */
+int hmc_poly_solve(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi, void *x,
+                   const void *b, const double *coeffs, int degree, double kappa,
+                   double tol, int max_iter, const hmc_solver_opts *opts,
+                   hmc_solve_stats *stats);
+
 /* ---- molecular dynamics -------------------------------------------------------- */
 
 /* hmc_update_links: U <- exp(eps Pi) U with Pi = sum_a P_a T_a (Sec. I, update
@@ -425,6 +438,20 @@ typedef struct {
    * the same U are merged (one force evaluation). */
   int integrator;
   double lambda;
+  /* rooted-polynomial hierarchy (Sec. II.A; requires n_mp == 0):
+   * root_levels > 0 polynomials P_j(K) = sum_i root_c[j][i] K^i
+   * (i = 0 .. root_deg[j], host arrays, e.g. truncated series of
+   * M_j^{-1/N}), each carried by root_N pseudo-fermions with the action
+   * |P_j(K) phi|^2, plus one remainder pseudo-fermion with
+   * |(alpha Mhat^{-1} + sum_{n<=n_max} b_n K^n) phi|^2 (force truncated at
+   * n_t; b, c, alpha as for filtering, even when filter_k == 0; filter_k
+   * fixes Mtilde and the T_k term of the gauge action).  eta then holds
+   * root_levels * root_N + 1 consecutive F64 even fields, the remainder
+   * last.  Heatbath: phi = P_j^{-1} eta (hmc_poly_solve) and
+   * phi = prod_j P_j^N Mhat sum c_n K^n eta; H0 and H1 evaluate the actions. */
+  int root_levels, root_N;
+  const int *root_deg;
+  const double *const *root_c;
 } hmc_traj_params;
 
 #define HMC_INTEGRATOR_LEAPFROG 0

@@ -78,8 +78,9 @@ int hi_mdagm(const HiOps &h, void *out, const void *in, double kappa, int n_rhs,
 }
 
 // out = sum_{j=0}^{n} c_j K^j in by Horner's scheme, K = kappa^2 H_eo H_oe
-// (out must not alias in)
-int hi_poly_K(const HiOps &h, void *out, const void *in, const double *c, int n, double kappa) {
+// (K^dag with dagger != 0; out must not alias in)
+int hi_poly_K(const HiOps &h, void *out, const void *in, const double *c, int n, double kappa,
+              int dagger) {
   const int p = h.emul ? HMC_F64E : HMC_F64;
   const hmc_gauge &U = h.emul ? h.Ue : h.Uh;
   void *tmp = hi_ws(h, "tmp", 1);
@@ -99,9 +100,9 @@ int hi_poly_K(const HiOps &h, void *out, const void *in, const double *c, int n,
   for (int j = n - 1; j >= 0; --j) {
     // y <- c_j x + K y: tmp (odd) = H_oe y; y = c_j x + kappa^2 H_eo tmp
     a.p = 1; a.out = tmp; a.in = y; a.x = nullptr; a.ca = 0.0; a.cb = 1.0;
-    TRY(dslash(h.ctx, a, U, p, 0, nullptr));
+    TRY(dslash(h.ctx, a, U, p, dagger, nullptr));
     a.p = 0; a.out = y; a.in = tmp; a.x = x; a.ca = c[j]; a.cb = kappa * kappa;
-    TRY(dslash(h.ctx, a, U, p, 0, nullptr));
+    TRY(dslash(h.ctx, a, U, p, dagger, nullptr));
   }
   if (h.emul) return copy_convert(h.ctx, HMC_F64, HMC_F64E, out, y, h.g.Vh);
   return HMC_OK;

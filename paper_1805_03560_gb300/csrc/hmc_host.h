@@ -186,8 +186,9 @@ int hi_mhat(const HiOps &h, int dagger, void *out, const void *in, double kappa,
             const double *cb_rhs);
 int hi_mdagm(const HiOps &h, void *out, const void *in, double kappa, int n_rhs,
              const double *cb_rhs);
-// out = sum_{j<=n} c_j K^j in (Horner), out must not alias in
-int hi_poly_K(const HiOps &h, void *out, const void *in, const double *c, int n, double kappa);
+// out = sum_{j<=n} c_j K^j in (Horner; K^dag with dagger), out must not alias in
+int hi_poly_K(const HiOps &h, void *out, const void *in, const double *c, int n, double kappa,
+              int dagger = 0);
 
 // batched CG of n_rhs systems with per-system kappas (host array); stats:
 // array of n_rhs (nullable)

@@ -192,11 +192,17 @@ int force_pf(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
   TRY(axpby(ctx, fp, slot(n), filt->b[n], phi_f, 0.0, nullptr, g.Vh));
   for (int j = n; j >= 1; --j)
     TRY(apply_K(ctx, g, Uf, fp, 0, kappa, slot(j - 1), slot(j), phi_f, filt->b[j - 1], tmp));
-  // Ytilde = alpha Mhat^{-1} phi (FP64 solve)
-  HiOps hi;
-  TRY(hi_begin(ctx, g, Uh, opts, &hi, "tr"));
-  TRY(mhat_inverse(hi, Ul, Yt, phi, kappa, tol, opts, acc));
-  TRY(axpby(ctx, HMC_F64, Yt, filt->alpha, Yt, 0.0, nullptr, g.Vh));
+  // Ytilde = alpha Mhat^{-1} phi (FP64 solve; zero for a pure polynomial,
+  // alpha == 0, whose Xtilde pair then vanishes too)
+  const bool has_inv = filt->alpha != 0.0;
+  if (has_inv) {
+    HiOps hi;
+    TRY(hi_begin(ctx, g, Uh, opts, &hi, "tr"));
+    TRY(mhat_inverse(hi, Ul, Yt, phi, kappa, tol, opts, acc));
+    TRY(axpby(ctx, HMC_F64, Yt, filt->alpha, Yt, 0.0, nullptr, g.Vh));
+  } else {
+    TRY(zero_field(ctx, HMC_F64, Yt, g.Vh));
+  }
   const void *Yt_f = Yt;
   if (fp != HMC_F64) {
     TRY(to_fp(Ytf, Yt));
@@ -209,13 +215,15 @@ int force_pf(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
     TRY(copy_convert(ctx, HMC_F64, fp, Y, Xi, g.Vh));
     x1_64 = Y;
   }
-  TRY(solve(ctx, g, Uh, Ul, X, x1_64, kappa, tol, opts, acc));
-  const void *Xs = X;
-  if (fp != HMC_F64) {
-    TRY(to_fp(Xf, X));
-    Xs = Xf;
+  if (has_inv) {
+    TRY(solve(ctx, g, Uh, Ul, X, x1_64, kappa, tol, opts, acc));
+    const void *Xs = X;
+    if (fp != HMC_F64) {
+      TRY(to_fp(Xf, X));
+      Xs = Xf;
+    }
+    TRY(mhat(ctx, g, Uf, fp, 0, 1, Xt, Xs, tmp, kappa, nullptr, nullptr, nullptr));
   }
-  TRY(mhat(ctx, g, Uf, fp, 0, 1, Xt, Xs, tmp, kappa, nullptr, nullptr, nullptr));
   // The n + 1 pairs (Xtilde, Ytilde), (X_i, Y_i) go into one outer-product
   // pass: X_1 .. X_n are kept (X_{i+1} = K^dag X_i), and for every pair the
   // odd halves H_eo^dag A and H_oe B.  Buffers at FP64 size (never
@@ -228,7 +236,7 @@ int force_pf(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
   if (n >= 1) TRY(copy_convert(ctx, fp, fp, xs(1), Xi, g.Vh));
   for (int i = 1; i < n; ++i) TRY(apply_K(ctx, g, Uf, fp, 1, kappa, xs(i + 1), xs(i), nullptr, 0.0, tmp));
   std::vector<const void *> Wv(2 * (n + 1)), Vv(2 * (n + 1));
-  for (int q = 0; q <= n; ++q) {
+  for (int q = has_inv ? 0 : 1; q <= n; ++q) {
     const void *A = q == 0 ? Xt : xs(q);
     const void *B = q == 0 ? Yt_f : slot(q);
     void *wo = Wodd + f64 * q, *vo = Vodd + f64 * q;
@@ -240,8 +248,10 @@ int force_pf(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
     Vv[2 * q + 1] = vo;
   }
   (void)Xn;
-  return hop_force_multi(ctx, g, Uf, n + 1, (const void *const(*)[2])Wv.data(),
-                         (const void *const(*)[2])Vv.data(), F, coeff * kappa * kappa, fp);
+  const int q0 = has_inv ? 0 : 1;
+  return hop_force_multi(ctx, g, Uf, n + 1 - q0, (const void *const(*)[2])(Wv.data() + 2 * q0),
+                         (const void *const(*)[2])(Vv.data() + 2 * q0), F, coeff * kappa * kappa,
+                         fp);
 }
 
 int action_pf(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
@@ -260,9 +270,96 @@ int action_pf(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *
   HiOps hi;
   TRY(hi_begin(ctx, g, Uh, opts, &hi, "tr"));
   TRY(hi_poly_K(hi, Z, phi, filt->b, n, kappa));
-  TRY(mhat_inverse(hi, Ul, X, phi, kappa, tol, opts, acc));
-  TRY(axpby(ctx, HMC_F64, Z, 1.0, Z, filt->alpha, X, g.Vh));
+  if (filt->alpha != 0.0) {
+    TRY(mhat_inverse(hi, Ul, X, phi, kappa, tol, opts, acc));
+    TRY(axpby(ctx, HMC_F64, Z, 1.0, Z, filt->alpha, X, g.Vh));
+  }
   return norm2_host(ctx, g, HMC_F64, Z, S);
+}
+
+// x = P(K)^{-1} b with P(K) = sum_i c_i K^i, by CG on the normal equations
+// P^dag P x = P^dag b (Sec. II.A: the heatbath of a rooted-polynomial
+// pseudo-fermion, phi = P^{-1} eta), FP64-accurate polynomial applications
+// (native or emulated).  Stops when the true residual |b - P x| / |b| <= tol
+// (checked when the normal-equation residual has fallen below tol).
+int poly_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, void *x, const void *b,
+               const double *c, int deg, double kappa, double tol, int max_iter,
+               const hmc_solver_opts *opts, int *iters, double *rel_out) {
+  const size_t f64 = spinor_bytes(g, HMC_F64, 1);
+  void *r = workspace(ctx, "ps_r", f64), *p = workspace(ctx, "ps_p", f64);
+  void *t = workspace(ctx, "ps_t", f64), *Ap = workspace(ctx, "ps_ap", f64);
+  if (!r || !p || !t || !Ap) return HMC_ENOMEM;
+  HiOps hi;
+  TRY(hi_begin(ctx, g, Uh, opts, &hi, "ps"));
+  double b2, rr, rhs2;
+  TRY(norm2_host(ctx, g, HMC_F64, b, &b2));
+  TRY(zero_field(ctx, HMC_F64, x, g.Vh));
+  int it = 0;
+  double rel = b2 > 0.0 ? 1.0 : 0.0;
+  bool conv = b2 == 0.0;
+  if (!conv) {
+    TRY(hi_poly_K(hi, r, b, c, deg, kappa, 1));  // r = P^dag b
+    TRY(copy_convert(ctx, HMC_F64, HMC_F64, p, r, g.Vh));
+    TRY(norm2_host(ctx, g, HMC_F64, r, &rr));
+    rhs2 = rr;
+  }
+  while (!conv && it < max_iter) {
+    TRY(hi_poly_K(hi, t, p, c, deg, kappa, 0));
+    TRY(hi_poly_K(hi, Ap, t, c, deg, kappa, 1));
+    double pap;
+    TRY(dot_host(ctx, g, p, Ap, &pap));
+    const double alpha = rr / pap;
+    if (!std::isfinite(alpha)) return fail(ctx, HMC_ENAN, "poly_solve: NaN/Inf");
+    TRY(axpby(ctx, HMC_F64, x, 1.0, x, alpha, p, g.Vh));
+    TRY(axpby(ctx, HMC_F64, r, 1.0, r, -alpha, Ap, g.Vh));
+    double rr_new;
+    TRY(norm2_host(ctx, g, HMC_F64, r, &rr_new));
+    ++it;
+    if (rr_new <= tol * tol * rhs2) {
+      TRY(hi_poly_K(hi, t, x, c, deg, kappa, 0));
+      TRY(axpby(ctx, HMC_F64, t, 1.0, b, -1.0, t, g.Vh));
+      double e2;
+      TRY(norm2_host(ctx, g, HMC_F64, t, &e2));
+      rel = sqrt(e2 / b2);
+      if (rel <= tol) {
+        conv = true;
+        break;
+      }
+    }
+    TRY(axpby(ctx, HMC_F64, p, 1.0, r, rr_new / rr, p, g.Vh));
+    rr = rr_new;
+  }
+  if (iters) *iters = it;
+  if (rel_out) *rel_out = rel;
+  if (!conv) return fail(ctx, HMC_ENOCONV, "poly_solve: not converged after %d iterations", it);
+  return HMC_OK;
+}
+
+// The rooted-polynomial pseudo-fermions (Sec. II.A): root_levels * root_N
+// polynomial terms |P_j(K) phi|^2 (the filtered form with alpha = 0) and the
+// remainder |(alpha Mhat^{-1} + sum b_n K^n) phi|^2, the fields consecutive.
+static int rooted_terms(const hmc_traj_params *prm) {
+  return prm->root_levels > 0 ? prm->root_levels * prm->root_N + 1 : 0;
+}
+static hmc_filter rooted_filter(const hmc_traj_params *prm, int f, bool action) {
+  const int j = f / prm->root_N;
+  if (j < prm->root_levels) return hmc_filter{prm->root_c[j], prm->root_deg[j], 0.0};
+  return hmc_filter{prm->b, action ? prm->n_max : prm->n_t, prm->alpha};
+}
+static int rooted_action(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
+                         const void *phi, const hmc_traj_params *prm, double *S,
+                         hmc_solve_stats *acc) {
+  const size_t f64 = spinor_bytes(g, HMC_F64, 1);
+  double s = 0.0;
+  for (int f = 0; f < rooted_terms(prm); ++f) {
+    const hmc_filter flt = rooted_filter(prm, f, true);
+    double sf;
+    TRY(action_pf(ctx, g, Uh, Ul, (const char *)phi + f64 * f, prm->kappa, &flt,
+                  prm->tol_action, &prm->solver, &sf, acc));
+    s += sf;
+  }
+  *S = s;
+  return HMC_OK;
 }
 
 // Hopping parameters (kappa_a, kappa_b) of the n_mp + 1 terms of a
@@ -309,7 +406,15 @@ int md_evolve(hmc_ctx *ctx, const Geo &g, void *U1, void *Ulo, double *P, double
   auto pf_step = [&](double eps) -> int {
     TRY(cuda_ok(ctx, cudaMemsetAsync(F, 0, fbytes, st), "md: zero F"));
     if (plo != HMC_F64) TRY(convert_gauge(ctx, g, U1, Ulo, plo, fmt_lo));
-    if (n_terms) {
+    if (rooted_terms(prm)) {
+      const size_t f64 = spinor_bytes(g, HMC_F64, 1);
+      for (int f = 0; f < rooted_terms(prm); ++f) {
+        const hmc_filter flt = rooted_filter(prm, f, false);
+        TRY(force_pf(ctx, g, Uh, Ulp, (const char *)phi + f64 * f, prm->kappa, &flt, 1.0, F,
+                     prm->tol_md, &prm->solver, acc));
+      }
+      *solves += 2;
+    } else if (n_terms) {
       // all terms of the chain at once: two batched solve stages
       TRY(force_mp(ctx, g, Uh, Ulp, phi, n_terms, ka, kb, 1.0, F, prm->tol_md, &prm->solver,
                    acc));
@@ -390,6 +495,20 @@ static int check_traj_params(hmc_ctx *ctx, const hmc_traj_params *prm) {
     return fail(ctx, HMC_EINVAL, "trajectory: unknown integrator %d", prm->integrator);
   if (prm->integrator == HMC_INTEGRATOR_OMELYAN && !(prm->lambda > 0.0 && prm->lambda < 0.5 + 1e-15))
     return fail(ctx, HMC_EINVAL, "trajectory: Omelyan lambda must be in (0, 1/2]");
+  if (prm->root_levels < 0 || prm->root_levels > 8)
+    return fail(ctx, HMC_EINVAL, "trajectory: root_levels must be 0..8");
+  if (prm->root_levels > 0) {
+    if (prm->n_mp != 0)
+      return fail(ctx, HMC_EINVAL, "trajectory: rooted polynomials need n_mp == 0");
+    if (prm->root_N < 1 || prm->root_levels * prm->root_N > 64 || !prm->root_deg || !prm->root_c)
+      return fail(ctx, HMC_EINVAL, "trajectory: root_N >= 1, at most 64 polynomial fields, "
+                                   "root_deg and root_c needed");
+    for (int j = 0; j < prm->root_levels; ++j)
+      if (prm->root_deg[j] < 0 || !prm->root_c[j])
+        return fail(ctx, HMC_EINVAL, "trajectory: bad root polynomial %d", j);
+    if (!prm->b || !prm->c || prm->n_t < 0 || prm->n_max < prm->n_t)
+      return fail(ctx, HMC_EINVAL, "trajectory: the remainder needs b, c and 0 <= n_t <= n_max");
+  }
   if (prm->n_mp < 0 || prm->n_mp > 15)
     return fail(ctx, HMC_EINVAL, "trajectory: n_mp must be 0..15");
   if (prm->n_mp > 0) {
@@ -495,6 +614,27 @@ int hmc_poly_apply(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U, voi
   return HMC_OK;
 }
 
+int hmc_poly_solve(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi, void *x,
+                   const void *b, const double *coeffs, int degree, double kappa, double tol,
+                   int max_iter, const hmc_solver_opts *opts, hmc_solve_stats *stats) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  TRY(check_gauge(ctx, U_hi));
+  if (U_hi->prec != HMC_F64) return fail(ctx, HMC_EINVAL, "poly_solve: U_hi must be F64");
+  if (!x || !b || !coeffs || degree < 0 || x == b || !(tol > 0.0))
+    return fail(ctx, HMC_EINVAL, "poly_solve: bad arguments");
+  int it = 0;
+  double rel = 0.0;
+  const int st = poly_solve(ctx, make_geo(*lat), *U_hi, x, b, coeffs, degree, kappa, tol,
+                            max_iter > 0 ? max_iter : 100000, opts, &it, &rel);
+  if (stats) {
+    stats->iterations = it;
+    stats->reliable_updates = 0;
+    stats->true_rel_res = rel;
+  }
+  return st;
+}
+
 int hmc_update_links(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const double *P, double eps) {
   CTX_CHECK(ctx);
   TRY(check_lattice(ctx, lat));
@@ -545,7 +685,9 @@ int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj
   double *P = (double *)workspace(ctx, "tr_p", ab), *F = (double *)workspace(ctx, "tr_f", ab);
   double ka[16], kb[16];
   const int n_terms = prm->n_mp > 0 ? mp_pairs(prm, ka, kb) : 0;
-  void *phi = workspace(ctx, "tr_phi", f64 * (n_terms ? n_terms : 1));
+  const int n_root = rooted_terms(prm);
+  const int n_fields = n_root ? n_root : (n_terms ? n_terms : 1);
+  void *phi = workspace(ctx, "tr_phi", f64 * n_fields);
   void *t1 = workspace(ctx, "tr_t1", f64);
   void *t2 = workspace(ctx, "tr_t2", f64);
   if (!U1 || (plo != HMC_F64 && !Ulo) || !P || !F || !phi || !t1 || !t2) return HMC_ENOMEM;
@@ -565,7 +707,32 @@ int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj
   hmc_solve_stats acc{};
   // heatbath of the pseudo-fermion field and H0
   double kin0, sg0, spf0;
-  if (n_terms) {
+  if (n_root) {
+    // polynomial terms: phi = P_j^{-1} eta; remainder: phi = prod_j P_j^N
+    // Mhat sum c_n K^n eta; H0 from the actions evaluated at the start
+    HiOps hi;
+    TRY(hi_begin(ctx, g, Uh, &prm->solver, &hi, "tr"));
+    for (int f = 0; f + 1 < n_root; ++f) {
+      const int j = f / prm->root_N;
+      int it;
+      double rel;
+      TRY(poly_solve(ctx, g, Uh, (char *)phi + f64 * f, (const char *)eta + f64 * f,
+                     prm->root_c[j], prm->root_deg[j], prm->kappa, prm->tol_action, 100000,
+                     &prm->solver, &it, &rel));
+    }
+    void *rem = (char *)phi + f64 * (n_root - 1);
+    TRY(hi_poly_K(hi, t2, (const char *)eta + f64 * (n_root - 1), prm->c, prm->n_max,
+                  prm->kappa));
+    TRY(hi_mhat(hi, 0, rem, t2, prm->kappa, 1, nullptr));
+    for (int j = 0; j < prm->root_levels; ++j)
+      for (int q = 0; q < prm->root_N; ++q) {
+        TRY(hi_poly_K(hi, t2, rem, prm->root_c[j], prm->root_deg[j], prm->kappa));
+        TRY(copy_convert(ctx, HMC_F64, HMC_F64, rem, t2, g.Vh));
+      }
+    TRY(refresh_lo());
+    TRY(rooted_action(ctx, g, Uh, Ulp, phi, prm, &spf0, &acc));
+    res->solves += 1;
+  } else if (n_terms) {
     // phi_j = Mhat_b^dag Mhat_a^{-dag} eta_j: the start action is sum |eta_j|^2
     TRY(refresh_lo());
     TRY(heatbath_mp(ctx, g, Uh, Ulp, eta, n_terms, ka, kb, prm->tol_action, &prm->solver, phi,
@@ -603,7 +770,9 @@ int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj
   TRY(hmc_kinetic(ctx, lat, P, &kin1));
   TRY(gauge_action(ctx, g, Uh, prm->beta, prm->kappa, k, &sg1, &ps1));
   TRY(refresh_lo());
-  if (n_terms)
+  if (n_root)
+    TRY(rooted_action(ctx, g, Uh, Ulp, phi, prm, &spf1, &acc));
+  else if (n_terms)
     TRY(action_mp(ctx, g, Uh, Ulp, phi, n_terms, ka, kb, prm->tol_action, &prm->solver, &spf1,
                   &acc));
   else

@@ -52,7 +52,8 @@ class TrajParams(ctypes.Structure):
                 ("tol_md", _D), ("tol_action", _D),
                 ("solver", SolverOpts), ("link_fmt_lo", _I),
                 ("n_mp", _I), ("kappa_mp", _P),
-                ("integrator", _I), ("lam", _D)]
+                ("integrator", _I), ("lam", _D),
+                ("root_levels", _I), ("root_N", _I), ("root_deg", _P), ("root_c", _P)]
 
 
 class TrajResult(ctypes.Structure):
@@ -100,6 +101,7 @@ _SIGS = {
     "hmc_kinetic": (_I, [_P, _P, _P, _P]),
     "hmc_trajectory": (_I, [_P, _P, _P, _P, _P, _P, _D, _P, _P, _P]),
     "hmc_filter_coeffs": (_I, [_I, _I, _P, _P, _P]),
+    "hmc_poly_solve": (_I, [_P, _P, _P, _P, _P, _P, _I, _D, _D, _I, _P, _P]),
     "hmc_force_mp": (_I, [_P, _P, _P, _P, _P, _I, _P, _P, _D, _P, _D, _P, _P]),
     "hmc_action_mp": (_I, [_P, _P, _P, _P, _P, _I, _P, _P, _D, _P, _P, _P]),
     "hmc_heatbath_mp": (_I, [_P, _P, _P, _P, _P, _I, _P, _P, _D, _P, _P, _P]),
@@ -417,6 +419,31 @@ class Context:
         return out.value
 
     @staticmethod
+    def _root(prm, root_polys, root_N, keep):
+        if root_polys:
+            arrs = [np.ascontiguousarray(c, dtype=np.float64) for c in root_polys]
+            deg = np.array([len(c) - 1 for c in root_polys], dtype=np.int32)
+            ptrs = (ctypes.c_void_p * len(arrs))(*[x.ctypes.data for x in arrs])
+            keep += arrs + [deg, ptrs]
+            prm.root_levels = len(arrs)
+            prm.root_N = int(root_N)
+            prm.root_deg = deg.ctypes.data
+            prm.root_c = ctypes.cast(ptrs, ctypes.c_void_p)
+
+    def poly_solve(self, L, U_hi, x, b, coeffs, kappa, tol=1e-12, max_iter=0, f64_emul=0):
+        """x = P(K)^{-1} b, P(K) = sum_i coeffs[i] K^i (F64 even fields)."""
+        self._stream()
+        c = np.ascontiguousarray(coeffs, dtype=np.float64)
+        gh = U_hi.gauge()
+        opts = SolverOpts(F64, 0.1, 16, F64, f64_emul)
+        stats = SolveStats()
+        st = lib().hmc_poly_solve(self.h, _ref(lattice(L)), ctypes.byref(gh), x.ptr(), b.ptr(),
+                                  c.ctypes.data_as(_P), len(c) - 1, kappa, tol, max_iter,
+                                  ctypes.byref(opts), ctypes.byref(stats))
+        self._check(st, "hmc_poly_solve")
+        return {f: getattr(stats, f) for f, _ in SolveStats._fields_}
+
+    @staticmethod
     def _mp(prm, kappa_mp, keep):
         if kappa_mp:
             km = np.ascontiguousarray(kappa_mp, dtype=np.float64)
@@ -539,7 +566,7 @@ class Context:
                    n_max=0, b=None, c=None, alpha=0.0, tol_md=1e-10, tol_action=1e-12,
                    inner_prec=F64, link_fmt_lo=LINK12, reliable_delta=0.1, U_end=None,
                    P_end=None, force_prec=F64, kappa_mp=None, integrator=LEAPFROG,
-                   lam=1.0 / 6.0, f64_emul=0):
+                   lam=1.0 / 6.0, f64_emul=0, root_polys=None, root_N=0):
         """One HMC trajectory; U (F64/LINK18 gauge Field) is updated in place
         when accepted.  Returns the result as a dict.  kappa_mp: heavier
         hopping parameters of a mass-preconditioned chain (eta then from
@@ -552,6 +579,7 @@ class Context:
                          solver=SolverOpts(inner_prec, reliable_delta, 16, force_prec, f64_emul),
                          link_fmt_lo=link_fmt_lo, integrator=integrator, lam=lam)
         self._mp(prm, kappa_mp, keep)
+        self._root(prm, root_polys, root_N, keep)
         if b is not None:
             ab = np.ascontiguousarray(b, dtype=np.float64); keep.append(ab); prm.b = ab.ctypes.data
         if c is not None:
@@ -567,7 +595,7 @@ class Context:
     def md_evolve(self, L, U, P, phi, beta, kappa, tau, n_md, n_gauge, filter_k=0, n_t=0,
                   b=None, alpha=0.0, tol_md=1e-10, inner_prec=F64, link_fmt_lo=LINK12,
                   reliable_delta=0.1, force_prec=F64, kappa_mp=None, integrator=LEAPFROG,
-                  lam=1.0 / 6.0, f64_emul=0):
+                  lam=1.0 / 6.0, f64_emul=0, root_polys=None, root_N=0):
         """Molecular dynamics with phi fixed; U (F64/LINK18) and P updated in place."""
         self._stream()
         keep = []
@@ -577,6 +605,7 @@ class Context:
                          solver=SolverOpts(inner_prec, reliable_delta, 16, force_prec, f64_emul),
                          link_fmt_lo=link_fmt_lo, integrator=integrator, lam=lam)
         self._mp(prm, kappa_mp, keep)
+        self._root(prm, root_polys, root_N, keep)
         if b is not None:
             ab = np.ascontiguousarray(b, dtype=np.float64); keep.append(ab)
             prm.b = ab.ctypes.data
