@@ -507,6 +507,16 @@ int hmc_md_evolve(hmc_ctx *ctx, const hmc_lattice *lat, void *U, double *P,
  * alpha = exp(-sum_{m<=k} 1/m) into *alpha, and (c nullable) the heatbath
  * series c_0..c_n of exp(sum_{m<=k} K^m/m) into c.  Computed in long double. */
 int hmc_filter_coeffs(int k, int n, double *b, double *alpha, double *c);
+/* Rooted-polynomial hierarchy of Sec. II.A for order k (powers of K) and
+ * root N: with M_1(x) = (1 - x) exp(sum_{m<=k} x^m/m) (Mtilde as a series in
+ * K), P_j = Taylor_{degrees[j]}[M_j^{-1/N}] and M_{j+1} = P_j^N M_j for
+ * j < levels (1..8); the remainder M_{levels+1}^{-1} = alpha Mhat^{-1} +
+ * sum b_m K^m with alpha = exp(-sum_{m<=k} 1/m) prod_j P_j(1)^{-N}.  Writes
+ * the coefficients of every P_j one after another into polys
+ * (sum_j (degrees[j] + 1) entries), b_0..b_{n_b} into b and alpha.  Host
+ * only, long double series arithmetic. */
+int hmc_rooted_coeffs(int k, int N, int levels, const int *degrees, int n_b,
+                      double *alpha, double *b, double *polys);
 
 #ifdef __cplusplus
 }

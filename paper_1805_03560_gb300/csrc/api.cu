@@ -5,6 +5,8 @@
 #include <cstdio>
 #include <cstring>
 
+#include <vector>
+
 #include "hmc_host.h"
 
 namespace hmc {
@@ -445,6 +447,81 @@ int hmc_filter_coeffs(int k, int n, double *b, double *alpha, double *c) {
   }
   delete[] e;
   delete[] bt;
+  return HMC_OK;
+}
+
+// Power-series helpers for hmc_rooted_coeffs (long double, truncated at n).
+static void ps_mul(const long double *a, const long double *b, long double *c, int n) {
+  for (int m = 0; m <= n; ++m) {
+    long double s = 0.0L;
+    for (int i = 0; i <= m; ++i) s += a[i] * b[m - i];
+    c[m] = s;
+  }
+}
+// g = f^r for f[0] == 1:  m g_m = sum_{j=1}^{m} ((r + 1) j - m) f_j g_{m-j}
+static void ps_pow(const long double *f, long double r, long double *g, int n) {
+  g[0] = 1.0L;
+  for (int m = 1; m <= n; ++m) {
+    long double s = 0.0L;
+    for (int j = 1; j <= m; ++j) s += ((r + 1.0L) * j - m) * f[j] * g[m - j];
+    g[m] = s / m;
+  }
+}
+
+int hmc_rooted_coeffs(int k, int N, int levels, const int *degrees, int n_b, double *alpha,
+                      double *b, double *polys) {
+  if (k < 0 || k > 8 || N < 1 || levels < 1 || levels > 8 || !degrees || n_b < 0 ||
+      n_b > 4096 || !alpha || !b || !polys)
+    return HMC_EINVAL;
+  int dmax = n_b;
+  for (int j = 0; j < levels; ++j) {
+    if (degrees[j] < 0 || degrees[j] > 4096) return HMC_EINVAL;
+    dmax = degrees[j] > dmax ? degrees[j] : dmax;
+  }
+  const int n = dmax + 200;
+  std::vector<long double> M(n + 1), E(n + 1), root(n + 1), P(n + 1), PN(n + 1), T(n + 1);
+  // M_1(x) = (1 - x) exp(sum_{m<=k} x^m / m):  m E_m = sum_{j=1}^{min(m,k)} E_{m-j}
+  E[0] = 1.0L;
+  for (int m = 1; m <= n; ++m) {
+    long double s = 0.0L;
+    for (int j = 1; j <= k && j <= m; ++j) s += E[m - j];
+    E[m] = s / m;
+  }
+  M[0] = E[0];
+  for (int m = 1; m <= n; ++m) M[m] = E[m] - E[m - 1];
+  long double hk = 0.0L;
+  for (int j = 1; j <= k; ++j) hk += 1.0L / j;
+  long double al = expl(-hk);
+  double *out = polys;
+  for (int j = 0; j < levels; ++j) {
+    // P_j = Taylor_{n_j}[M_j^{-1/N}],  M_{j+1} = P_j^N M_j
+    ps_pow(M.data(), -1.0L / N, root.data(), n);
+    long double p1 = 0.0L;
+    for (int m = 0; m <= n; ++m) P[m] = m <= degrees[j] ? root[m] : 0.0L;
+    for (int m = 0; m <= degrees[j]; ++m) {
+      out[m] = (double)P[m];
+      p1 += P[m];
+    }
+    out += degrees[j] + 1;
+    al /= powl(p1, (long double)N);
+    ps_pow(P.data(), (long double)N, PN.data(), n);
+    ps_mul(PN.data(), M.data(), T.data(), n);
+    M = T;
+  }
+  // R(x) = (1 - x) / M(x);  M^{-1} = R(1) / (1 - x) + sum b_m x^m with
+  // b_m = -sum_{i>m} R_i (summed from the far end)
+  ps_pow(M.data(), -1.0L, T.data(), n);
+  std::vector<long double> R(n + 1);
+  R[0] = T[0];
+  for (int m = 1; m <= n; ++m) R[m] = T[m] - T[m - 1];
+  long double acc = 0.0L;
+  std::vector<long double> bt(n + 1);
+  for (int m = n; m >= 0; --m) {
+    bt[m] = -acc;
+    acc += R[m];
+  }
+  for (int m = 0; m <= n_b; ++m) b[m] = (double)bt[m];
+  *alpha = (double)al;
   return HMC_OK;
 }
 

@@ -101,6 +101,7 @@ _SIGS = {
     "hmc_kinetic": (_I, [_P, _P, _P, _P]),
     "hmc_trajectory": (_I, [_P, _P, _P, _P, _P, _P, _D, _P, _P, _P]),
     "hmc_filter_coeffs": (_I, [_I, _I, _P, _P, _P]),
+    "hmc_rooted_coeffs": (_I, [_I, _I, _I, _P, _I, _P, _P, _P]),
     "hmc_poly_solve": (_I, [_P, _P, _P, _P, _P, _P, _I, _D, _D, _I, _P, _P]),
     "hmc_force_mp": (_I, [_P, _P, _P, _P, _P, _I, _P, _P, _D, _P, _D, _P, _P]),
     "hmc_action_mp": (_I, [_P, _P, _P, _P, _P, _I, _P, _P, _D, _P, _P, _P]),
@@ -150,6 +151,24 @@ def filter_coeffs(k, n, with_c=True):
     if st:
         raise HmcError(st, "hmc_filter_coeffs")
     return b, a.value, c
+
+
+def rooted_coeffs(k, N, degrees, n_b):
+    """Library-side rooted-polynomial hierarchy (host, long double):
+    (alpha, b_0..b_{n_b}, [P_1, P_2, ...])."""
+    deg = np.ascontiguousarray(degrees, dtype=np.int32)
+    polys = np.zeros(int(sum(d + 1 for d in degrees)))
+    b = np.zeros(n_b + 1)
+    a = ctypes.c_double(0)
+    st = lib().hmc_rooted_coeffs(k, N, len(deg), deg.ctypes.data_as(_P), n_b,
+                                 ctypes.byref(a), b.ctypes.data_as(_P), polys.ctypes.data_as(_P))
+    if st:
+        raise HmcError(st, "hmc_rooted_coeffs")
+    out, o = [], 0
+    for d in degrees:
+        out.append(polys[o:o + d + 1].copy())
+        o += d + 1
+    return a.value, b, out
 
 
 class Field:

@@ -71,3 +71,41 @@ def test_null_context_is_rejected(H):
     assert lib.hmc_dslash(None, ctypes.byref(L), None, None, None, 0, 0, 0, 1) == H.EINVAL
     assert lib.hmc_ctx_destroy(None) == H.EINVAL
     assert lib.hmc_last_error(None) == b"context is NULL"
+
+
+@pytest.mark.parametrize("k,N,degrees,n_b", [(0, 2, (4, 8), 16), (2, 8, (16, 42), 29),
+                                             (1, 4, (6,), 12)])
+def test_rooted_coeffs_match_exact_series(k, N, degrees, n_b):
+    """The library's long-double rooted-polynomial hierarchy (host only)
+    against the exact rational series of the oracle."""
+    from oracle import coeffs as C
+    from paper_1805_03560_gb300 import hmc
+    a, b, polys = hmc.rooted_coeffs(k, N, degrees, n_b)
+    wa, wb, wp = C.rooted_coeffs(k, N, degrees, n_b, tail=200)
+    assert abs(a - wa) <= 1e-14 * wa
+    assert np.abs(np.array(b) - np.array(wb)).max() <= 1e-13
+    for P, W in zip(polys, wp):
+        assert np.abs(np.array(P) - np.array(W)).max() <= 1e-13
+
+
+def test_rooted_coeffs_reproduce_table_iv():
+    """alpha of the printed rooted-polynomial table (Sec. IV, k = 0, n_1 = 8,
+    n_2 = 32) and the kappa^4 value (N = 8, n_1 = 16, n_2 = 42), from the
+    library's generator, to every printed digit."""
+    import json
+    from paper_1805_03560_gb300 import hmc
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_values.json")))
+    g = gold["rooted_alpha_table_IV"]
+    for N, txt in g["N"].items():
+        a, _, _ = hmc.rooted_coeffs(g["k"], int(N), (g["n1"], g["n2"]), 4)
+        assert _printed(a, txt), (N, a, txt)
+    g2 = gold["rooted_alpha_k4"]
+    a, _, _ = hmc.rooted_coeffs(g2["k"], g2["N"], (g2["n1"], g2["n2"]), 4)
+    assert _printed(a, g2["value"])
+
+
+def _printed(x, txt):
+    """x agrees with the printed value to its last digit (the table truncates
+    some entries and rounds others)."""
+    d = len(txt.split(".")[1])
+    return f"{x:.{d + 3}f}"[: len(txt)] == txt or abs(x - float(txt)) <= 0.5 * 10.0 ** -d
