@@ -78,6 +78,12 @@ def parse():
                     help="hopping parameter of the --report thermal trajectories")
     ap.add_argument("--lattice", default="24x48", choices=sorted(LATTICES),
                     help="L^3 x T of the benchmark lattice (default 24^3 x 48)")
+    ap.add_argument("--rooted", type=int, default=0,
+                    help="rooted-polynomial workload with this root N (kappa^4 Mtilde, "
+                         "P_1, P_2 of degrees 16 and 42, remainder n_t 15, n_max 29) on a "
+                         "field relaxed by pure-gauge HMC, kappa 0.156 unless --kappa")
+    ap.add_argument("--kappa", type=float, default=None,
+                    help="hopping parameter of the trajectory workload (default 0.1575)")
     ap.add_argument("--mp", action="store_true",
                     help="mass-preconditioned workload: pseudo-fermions at kappa' = 0.150, "
                          "0.154 and the target kappa (ratio terms, batched solves), no filter")
@@ -333,13 +339,24 @@ def run_hmc(args):
     ctx = hmc.Context(local)
     # autotuned hemi-Dslash variants (tuned during the warm-up steps)
     ctx.set_dslash_variant(-2 if args.variant is None else args.variant)
-    n_eta = len(KAPPA_MP) + 1 if args.mp else 1
+    n_eta = len(KAPPA_MP) + 1 if args.mp else (2 * args.rooted + 1 if args.rooted else 1)
     U, P, eta = build_inputs(rank, n_eta)
     b, alpha, c = coeffs()
     U0 = ctx.pack_gauge(LAT, U, hmc.F64, hmc.LINK18)
     Ud = ctx.new_gauge(LAT, hmc.F64, hmc.LINK18)
     Pd = ctx.pack_algebra(LAT, P)
-    ed = ctx.pack_spinors(LAT, list(eta)) if args.mp else ctx.pack_spinor(LAT, eta, hmc.F64)
+    ed = ctx.pack_spinors(LAT, list(eta)) if n_eta > 1 else ctx.pack_spinor(LAT, eta, hmc.F64)
+    start = None
+    if args.rooted:
+        # the roots' series in K approximate only where the spectrum of K lies
+        # inside the unit disk: on the synthetic start its radius is ~1.37 at
+        # kappa 0.1575 (the heatbath's P^dag P is then ill-conditioned), on a
+        # field relaxed by pure-gauge HMC ~0.98
+        t0 = time.time()
+        acc_q, plaq = quenched_hmc(ctx, LAT, U0, 5.85, 30, 20, 11 + rank)
+        U = ctx.unpack_gauge(LAT, U0).cpu().numpy()
+        start = {"relaxed": "pure-gauge HMC, beta 5.85, 30 trajectories", "plaquette": plaq,
+                 "acceptance": acc_q, "s": round(time.time() - t0, 1)}
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     fprec = hmc.F32 if args.force_prec == "f32" else hmc.F64
     work = dict(WORK)
@@ -350,7 +367,22 @@ def run_hmc(args):
         work["tau"] = args.tau
     if args.integrator == "omelyan":
         work.update(integrator=hmc.OMELYAN, lam=1.0 / 6.0)
-    if args.mp:
+    if args.kappa:
+        work["kappa"] = args.kappa
+    elif args.rooted:
+        # the relaxed field's critical kappa is ~0.1577 (spectral radius of K
+        # 0.998 at 0.1575 on 16 x 8^3), so the roots are taken at 0.156
+        work["kappa"] = 0.156
+    if args.rooted:
+        # Sec. II.A with kappa^4 filtering: M_1 = Mtilde (k = 2), P_1, P_2 of
+        # degrees 16 and 42, the remainder truncated at n_t = 15 / n_max = 29
+        ra, rb, rp = hmc.rooted_coeffs(2, args.rooted, (16, 42), 29)
+        _, _, rc = hmc.filter_coeffs(2, 29)
+        work.update(filter_k=2, n_t=15, n_max=29)
+        kw = dict(work, b=rb, c=rc, alpha=ra, root_polys=rp, root_N=args.rooted,
+                  inner_prec=inner, link_fmt_lo=hmc.LINK12, reliable_delta=args.delta,
+                  force_prec=fprec, f64_emul=args.f64_emul)
+    elif args.mp:
         work.update(filter_k=0, n_t=0, n_max=0)
         kw = dict(work, kappa_mp=KAPPA_MP, inner_prec=inner, link_fmt_lo=hmc.LINK12,
                   reliable_delta=args.delta, force_prec=fprec, f64_emul=args.f64_emul)
@@ -420,17 +452,21 @@ def run_hmc(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.inner,
         "data": "synthetic (seeded exp(i 0.3 A) links, Gaussian momenta and sources)",
-        "config": {"workload": (f"hmc-trajectory {lat_name()} kappa=0.1575 beta=5.6 "
+        "config": {"workload": (f"hmc-trajectory {lat_name()} kappa={work['kappa']} beta=5.6 "
                                  "mass-preconditioned kappa'=0.150,0.154 (batched solves)"
                                  if args.mp else
-                                 f"hmc-trajectory {lat_name()} kappa=0.1575 beta=5.6 kappa^4-filter"),
+                                 f"hmc-trajectory {lat_name()} kappa={work['kappa']} beta=5.6 kappa^4 "
+                                 f"rooted polynomials N={args.rooted} (degrees 16, 42)"
+                                 if args.rooted else
+                                 f"hmc-trajectory {lat_name()} kappa={work['kappa']} beta=5.6 kappa^4-filter"),
                    "lattice": "x".join(str(v) for v in LAT[::-1]), **{k: v for k, v in work.items()},
                    "inner_prec": args.inner, "reliable_delta": args.delta,
                    "force_prec": args.force_prec, "f64_emul": args.f64_emul,
                    "dslash_variant": "autotuned" if args.variant is None else args.variant,
                    "links": "12-real (inner), 18-real FP64",
                    "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   **({"start": start} if start else {})},
         "roofline": roof,
         "gpu_launches": launches,
         "kernels": kernels,

@@ -380,15 +380,24 @@ int hmc_heatbath_mp(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
 /* hmc_poly_solve: x = P(K)^{-1} b with P(K) = sum_{i<=degree} coeffs[i] K^i
  * (host coefficients), K = kappa^2 H_eo H_oe: the heatbath of a
  * rooted-polynomial pseudo-fermion (Sec. II.A), whose action |P(K) phi|^2
- * equals |b|^2 at phi = P^{-1} b.  CG on P^dag P with FP64-accurate
- * polynomial applications (emulated FP64 when opts->f64_emul), stopping on
- * the true residual |b - P x| / |b| <= tol; max_iter <= 0 means 100000.
+ * equals |b|^2 at phi = P^{-1} b.  Defect correction: passes of CG on
+ * P^dag P e = P^dag r, each followed by the FP64-accurate residual
+ * r = b - P x (emulated FP64 when opts->f64_emul).  U_lo (nullable, F32
+ * links of either format, the same field as U_hi) runs the passes on FP32
+ * fields to 1e-5 each; without it they are FP64-accurate.  Stops on
+ * |b - P x| / |b| <= tol, or when a pass no longer halves it (the rounding
+ * floor of the FP64-accurate application; converged then if within
+ * 10 tol); max_iter (all passes' CG iterations; <= 0 means 2000).  P must
+ * approximate a root of Mhat, i.e. the spectrum of K must lie inside the
+ * unit disk (kappa below the field's critical value); otherwise P^dag P is
+ * ill-conditioned and the result is HMC_ENOCONV.
  * x and b: F64 even fields, x must not alias b.  stats (nullable) gets the
- * iterations and the residual.  HMC_ENOCONV if not converged.  Blocking. */
-int hmc_poly_solve(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi, void *x,
-                   const void *b, const double *coeffs, int degree, double kappa,
-                   double tol, int max_iter, const hmc_solver_opts *opts,
-                   hmc_solve_stats *stats);
+ * iterations and the residual.  HMC_ENOCONV if not converged, HMC_EINVAL
+ * for U_lo of another precision.  Blocking. */
+int hmc_poly_solve(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
+                   const hmc_gauge *U_lo, void *x, const void *b, const double *coeffs,
+                   int degree, double kappa, double tol, int max_iter,
+                   const hmc_solver_opts *opts, hmc_solve_stats *stats);
 
 /* ---- molecular dynamics -------------------------------------------------------- */
 
@@ -447,8 +456,11 @@ typedef struct {
    * n_t; b, c, alpha as for filtering, even when filter_k == 0; filter_k
    * fixes Mtilde and the T_k term of the gauge action).  eta then holds
    * root_levels * root_N + 1 consecutive F64 even fields, the remainder
-   * last.  Heatbath: phi = P_j^{-1} eta (hmc_poly_solve) and
-   * phi = prod_j P_j^N Mhat sum c_n K^n eta; H0 and H1 evaluate the actions. */
+   * last.  Heatbath: phi = P_j^{-1} eta (hmc_poly_solve to tol_md, FP32
+   * correction passes when solver.inner_prec is F32) and
+   * phi = prod_j P_j^N Mhat sum c_n K^n eta; H0 and H1 evaluate the actions.
+   * The polynomials need the spectrum of K inside the unit disk (see
+   * hmc_poly_solve). */
   int root_levels, root_N;
   const int *root_deg;
   const double *const *root_c;

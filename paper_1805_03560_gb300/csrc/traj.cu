@@ -277,61 +277,113 @@ int action_pf(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *
   return norm2_host(ctx, g, HMC_F64, Z, S);
 }
 
-// x = P(K)^{-1} b with P(K) = sum_i c_i K^i, by CG on the normal equations
-// P^dag P x = P^dag b (Sec. II.A: the heatbath of a rooted-polynomial
-// pseudo-fermion, phi = P^{-1} eta), FP64-accurate polynomial applications
-// (native or emulated).  Stops when the true residual |b - P x| / |b| <= tol
-// (checked when the normal-equation residual has fallen below tol).
-int poly_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, void *x, const void *b,
-               const double *c, int deg, double kappa, double tol, int max_iter,
+// x = P(K)^{-1} b with P(K) = sum_i c_i K^i (Sec. II.A: the heatbath of a
+// rooted-polynomial pseudo-fermion, phi = P^{-1} eta), by defect correction:
+// each pass solves P^dag P e = P^dag r by CG for the current residual
+// r = b - P x and adds e to x; r is then recomputed with FP64-accurate
+// polynomial applications (native or emulated).  With FP32 links Ul the
+// passes apply P and P^dag on FP32 fields (CG vectors in FP64) to a relative
+// 1e-5 of their right-hand side; otherwise FP64-accurate.  Stops when
+// |r| / |b| <= tol, or when a pass no longer halves |r| (the rounding floor
+// of the FP64-accurate application, ~1e-14 times the degree in emulated
+// FP64), converged then if within 10 tol.  max_iter bounds the CG
+// iterations of all passes together.  P must be evaluated where its series
+// approximates a root of Mhat (spectrum of K inside the unit disk), else
+// P^dag P is ill-conditioned and the solve ends with HMC_ENOCONV.
+int poly_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul, void *x,
+               const void *b, const double *c, int deg, double kappa, double tol, int max_iter,
                const hmc_solver_opts *opts, int *iters, double *rel_out) {
-  const size_t f64 = spinor_bytes(g, HMC_F64, 1);
+  const bool lo = Ul && Ul->prec == HMC_F32;
+  const size_t f64 = spinor_bytes(g, HMC_F64, 1), f32 = spinor_bytes(g, HMC_F32, 1);
   void *r = workspace(ctx, "ps_r", f64), *p = workspace(ctx, "ps_p", f64);
   void *t = workspace(ctx, "ps_t", f64), *Ap = workspace(ctx, "ps_ap", f64);
-  if (!r || !p || !t || !Ap) return HMC_ENOMEM;
+  void *e = workspace(ctx, "ps_e", f64), *z = workspace(ctx, "ps_z", f64);
+  void *la = lo ? workspace(ctx, "ps_la", f32) : nullptr;
+  void *lb = lo ? workspace(ctx, "ps_lb", f32) : nullptr;
+  void *lc = lo ? workspace(ctx, "ps_lc", f32) : nullptr;
+  void *lt = lo ? workspace(ctx, "ps_lt", f32) : nullptr;
+  if (!r || !p || !t || !Ap || !e || !z || (lo && (!la || !lb || !lc || !lt))) return HMC_ENOMEM;
   HiOps hi;
   TRY(hi_begin(ctx, g, Uh, opts, &hi, "ps"));
-  double b2, rr, rhs2;
+  // FP32 Horner scheme: out = sum_i c_i K^i in (or K^dag), out != in
+  auto horner32 = [&](void *out, const void *in, int dagger) -> int {
+    TRY(axpby(ctx, HMC_F32, out, c[deg], in, 0.0, nullptr, g.Vh));
+    for (int j = deg - 1; j >= 0; --j)
+      TRY(apply_K(ctx, g, *Ul, HMC_F32, dagger, kappa, out, out, in, c[j], lt));
+    return HMC_OK;
+  };
+  // out = P^dag P in (both passes' operator), F64 fields
+  auto normal = [&](void *out, const void *in) -> int {
+    if (!lo) {
+      TRY(hi_poly_K(hi, t, in, c, deg, kappa, 0));
+      return hi_poly_K(hi, out, t, c, deg, kappa, 1);
+    }
+    TRY(copy_convert(ctx, HMC_F32, HMC_F64, la, in, g.Vh));
+    TRY(horner32(lb, la, 0));
+    TRY(horner32(lc, lb, 1));
+    return copy_convert(ctx, HMC_F64, HMC_F32, out, lc, g.Vh);
+  };
+  // out = P^dag in
+  auto dag = [&](void *out, const void *in) -> int {
+    if (!lo) return hi_poly_K(hi, out, in, c, deg, kappa, 1);
+    TRY(copy_convert(ctx, HMC_F32, HMC_F64, la, in, g.Vh));
+    TRY(horner32(lb, la, 1));
+    return copy_convert(ctx, HMC_F64, HMC_F32, out, lb, g.Vh);
+  };
+  double b2;
   TRY(norm2_host(ctx, g, HMC_F64, b, &b2));
   TRY(zero_field(ctx, HMC_F64, x, g.Vh));
   int it = 0;
   double rel = b2 > 0.0 ? 1.0 : 0.0;
   bool conv = b2 == 0.0;
-  if (!conv) {
-    TRY(hi_poly_K(hi, r, b, c, deg, kappa, 1));  // r = P^dag b
-    TRY(copy_convert(ctx, HMC_F64, HMC_F64, p, r, g.Vh));
-    TRY(norm2_host(ctx, g, HMC_F64, r, &rr));
-    rhs2 = rr;
-  }
+  if (!conv) TRY(copy_convert(ctx, HMC_F64, HMC_F64, r, b, g.Vh));
   while (!conv && it < max_iter) {
-    TRY(hi_poly_K(hi, t, p, c, deg, kappa, 0));
-    TRY(hi_poly_K(hi, Ap, t, c, deg, kappa, 1));
-    double pap;
-    TRY(dot_host(ctx, g, p, Ap, &pap));
-    const double alpha = rr / pap;
-    if (!std::isfinite(alpha)) return fail(ctx, HMC_ENAN, "poly_solve: NaN/Inf");
-    TRY(axpby(ctx, HMC_F64, x, 1.0, x, alpha, p, g.Vh));
-    TRY(axpby(ctx, HMC_F64, r, 1.0, r, -alpha, Ap, g.Vh));
-    double rr_new;
-    TRY(norm2_host(ctx, g, HMC_F64, r, &rr_new));
-    ++it;
-    if (rr_new <= tol * tol * rhs2) {
-      TRY(hi_poly_K(hi, t, x, c, deg, kappa, 0));
-      TRY(axpby(ctx, HMC_F64, t, 1.0, b, -1.0, t, g.Vh));
-      double e2;
-      TRY(norm2_host(ctx, g, HMC_F64, t, &e2));
-      rel = sqrt(e2 / b2);
-      if (rel <= tol) {
-        conv = true;
-        break;
-      }
+    // CG on P^dag P e = P^dag r, e from zero; z the normal-equation residual
+    const double delta = lo ? fmax(1e-5, 0.1 * tol / rel) : 0.1 * tol / rel;
+    double rr, rhs2;
+    TRY(dag(z, r));
+    TRY(zero_field(ctx, HMC_F64, e, g.Vh));
+    TRY(copy_convert(ctx, HMC_F64, HMC_F64, p, z, g.Vh));
+    TRY(norm2_host(ctx, g, HMC_F64, z, &rr));
+    rhs2 = rr;
+    while (rr > delta * delta * rhs2 && it < max_iter) {
+      TRY(normal(Ap, p));
+      double pap;
+      TRY(dot_host(ctx, g, p, Ap, &pap));
+      const double alpha = rr / pap;
+      if (!std::isfinite(alpha)) return fail(ctx, HMC_ENAN, "poly_solve: NaN/Inf");
+      TRY(axpby(ctx, HMC_F64, e, 1.0, e, alpha, p, g.Vh));
+      TRY(axpby(ctx, HMC_F64, z, 1.0, z, -alpha, Ap, g.Vh));
+      double rr_new;
+      TRY(norm2_host(ctx, g, HMC_F64, z, &rr_new));
+      ++it;
+      TRY(axpby(ctx, HMC_F64, p, 1.0, z, rr_new / rr, p, g.Vh));
+      rr = rr_new;
     }
-    TRY(axpby(ctx, HMC_F64, p, 1.0, r, rr_new / rr, p, g.Vh));
-    rr = rr_new;
+    // x += e, then the FP64-accurate residual r = b - P x
+    TRY(axpby(ctx, HMC_F64, x, 1.0, x, 1.0, e, g.Vh));
+    TRY(hi_poly_K(hi, t, x, c, deg, kappa, 0));
+    TRY(axpby(ctx, HMC_F64, r, 1.0, b, -1.0, t, g.Vh));
+    double r2;
+    TRY(norm2_host(ctx, g, HMC_F64, r, &r2));
+    const double rel_new = sqrt(r2 / b2);
+    if (!std::isfinite(rel_new)) return fail(ctx, HMC_ENAN, "poly_solve: NaN/Inf");
+    if (rel_new <= tol) {
+      rel = rel_new;
+      conv = true;
+    } else if (rel_new > 0.5 * rel) {  // stagnation at the rounding floor
+      rel = rel_new;
+      conv = rel <= 10.0 * tol;
+      break;
+    } else {
+      rel = rel_new;
+    }
   }
   if (iters) *iters = it;
   if (rel_out) *rel_out = rel;
-  if (!conv) return fail(ctx, HMC_ENOCONV, "poly_solve: not converged after %d iterations", it);
+  if (!conv)
+    return fail(ctx, HMC_ENOCONV, "poly_solve: not converged after %d iterations (residual %.3g)",
+                it, rel);
   return HMC_OK;
 }
 
@@ -614,19 +666,24 @@ int hmc_poly_apply(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U, voi
   return HMC_OK;
 }
 
-int hmc_poly_solve(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi, void *x,
-                   const void *b, const double *coeffs, int degree, double kappa, double tol,
-                   int max_iter, const hmc_solver_opts *opts, hmc_solve_stats *stats) {
+int hmc_poly_solve(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
+                   const hmc_gauge *U_lo, void *x, const void *b, const double *coeffs,
+                   int degree, double kappa, double tol, int max_iter,
+                   const hmc_solver_opts *opts, hmc_solve_stats *stats) {
   CTX_CHECK(ctx);
   TRY(check_lattice(ctx, lat));
   TRY(check_gauge(ctx, U_hi));
   if (U_hi->prec != HMC_F64) return fail(ctx, HMC_EINVAL, "poly_solve: U_hi must be F64");
+  if (U_lo) {
+    TRY(check_gauge(ctx, U_lo));
+    if (U_lo->prec != HMC_F32) return fail(ctx, HMC_EINVAL, "poly_solve: U_lo must be F32");
+  }
   if (!x || !b || !coeffs || degree < 0 || x == b || !(tol > 0.0))
     return fail(ctx, HMC_EINVAL, "poly_solve: bad arguments");
   int it = 0;
   double rel = 0.0;
-  const int st = poly_solve(ctx, make_geo(*lat), *U_hi, x, b, coeffs, degree, kappa, tol,
-                            max_iter > 0 ? max_iter : 100000, opts, &it, &rel);
+  const int st = poly_solve(ctx, make_geo(*lat), *U_hi, U_lo, x, b, coeffs, degree, kappa, tol,
+                            max_iter > 0 ? max_iter : 2000, opts, &it, &rel);
   if (stats) {
     stats->iterations = it;
     stats->reliable_updates = 0;
@@ -712,12 +769,15 @@ int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj
     // Mhat sum c_n K^n eta; H0 from the actions evaluated at the start
     HiOps hi;
     TRY(hi_begin(ctx, g, Uh, &prm->solver, &hi, "tr"));
+    TRY(refresh_lo());
     for (int f = 0; f + 1 < n_root; ++f) {
       const int j = f / prm->root_N;
       int it;
       double rel;
-      TRY(poly_solve(ctx, g, Uh, (char *)phi + f64 * f, (const char *)eta + f64 * f,
-                     prm->root_c[j], prm->root_deg[j], prm->kappa, prm->tol_action, 100000,
+      // to tol_md: H0 evaluates the actions at the start, so the heatbath's
+      // accuracy does not enter dH
+      TRY(poly_solve(ctx, g, Uh, Ulp, (char *)phi + f64 * f, (const char *)eta + f64 * f,
+                     prm->root_c[j], prm->root_deg[j], prm->kappa, prm->tol_md, 2000,
                      &prm->solver, &it, &rel));
     }
     void *rem = (char *)phi + f64 * (n_root - 1);
@@ -729,7 +789,6 @@ int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj
         TRY(hi_poly_K(hi, t2, rem, prm->root_c[j], prm->root_deg[j], prm->kappa));
         TRY(copy_convert(ctx, HMC_F64, HMC_F64, rem, t2, g.Vh));
       }
-    TRY(refresh_lo());
     TRY(rooted_action(ctx, g, Uh, Ulp, phi, prm, &spf0, &acc));
     res->solves += 1;
   } else if (n_terms) {

@@ -102,7 +102,7 @@ _SIGS = {
     "hmc_trajectory": (_I, [_P, _P, _P, _P, _P, _P, _D, _P, _P, _P]),
     "hmc_filter_coeffs": (_I, [_I, _I, _P, _P, _P]),
     "hmc_rooted_coeffs": (_I, [_I, _I, _I, _P, _I, _P, _P, _P]),
-    "hmc_poly_solve": (_I, [_P, _P, _P, _P, _P, _P, _I, _D, _D, _I, _P, _P]),
+    "hmc_poly_solve": (_I, [_P, _P, _P, _P, _P, _P, _P, _I, _D, _D, _I, _P, _P]),
     "hmc_force_mp": (_I, [_P, _P, _P, _P, _P, _I, _P, _P, _D, _P, _D, _P, _P]),
     "hmc_action_mp": (_I, [_P, _P, _P, _P, _P, _I, _P, _P, _D, _P, _P, _P]),
     "hmc_heatbath_mp": (_I, [_P, _P, _P, _P, _P, _I, _P, _P, _D, _P, _P, _P]),
@@ -449,14 +449,18 @@ class Context:
             prm.root_deg = deg.ctypes.data
             prm.root_c = ctypes.cast(ptrs, ctypes.c_void_p)
 
-    def poly_solve(self, L, U_hi, x, b, coeffs, kappa, tol=1e-12, max_iter=0, f64_emul=0):
-        """x = P(K)^{-1} b, P(K) = sum_i coeffs[i] K^i (F64 even fields)."""
+    def poly_solve(self, L, U_hi, x, b, coeffs, kappa, tol=1e-12, max_iter=0, f64_emul=0,
+                   U_lo=None):
+        """x = P(K)^{-1} b, P(K) = sum_i coeffs[i] K^i (F64 even fields); U_lo
+        (F32 links) runs the correction passes on FP32 fields."""
         self._stream()
         c = np.ascontiguousarray(coeffs, dtype=np.float64)
         gh = U_hi.gauge()
+        gl = U_lo.gauge() if U_lo is not None else None
         opts = SolverOpts(F64, 0.1, 16, F64, f64_emul)
         stats = SolveStats()
-        st = lib().hmc_poly_solve(self.h, _ref(lattice(L)), ctypes.byref(gh), x.ptr(), b.ptr(),
+        st = lib().hmc_poly_solve(self.h, _ref(lattice(L)), ctypes.byref(gh),
+                                  ctypes.byref(gl) if gl is not None else None, x.ptr(), b.ptr(),
                                   c.ctypes.data_as(_P), len(c) - 1, kappa, tol, max_iter,
                                   ctypes.byref(opts), ctypes.byref(stats))
         self._check(st, "hmc_poly_solve")

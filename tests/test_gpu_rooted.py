@@ -30,19 +30,27 @@ def _np(t):
     return t.cpu().numpy()
 
 
-@pytest.mark.parametrize("emul", [0, 1])
-def test_poly_solve_matches_oracle(orc, ctx, H, emul):
+@pytest.mark.parametrize("emul,lo,kappa", [(0, False, 0.156), (1, False, 0.156), (0, True, 0.12),
+                                           (1, True, 0.12)])
+def test_poly_solve_matches_oracle(orc, ctx, H, emul, lo, kappa):
+    """FP64-accurate passes, and FP32 passes (U_lo) corrected to the same
+    tolerance by the FP64-accurate residual (at kappa 0.12, where the spectrum
+    of K lies inside the unit disk on this field and the FP32 passes gain
+    five digits each)."""
     L = (4, 6, 6, 8)
     U = I.gauge_links(L, 0.3, 1)
     eta = I.gaussian_half(L, 2)
     _, _, polys = C.rooted_coeffs(0, 4, (6, 12), 4, tail=20)
     Uh = ctx.pack_gauge(L, U, 0, 18)
+    Ul = ctx.pack_gauge(L, U, 1, 12) if lo else None
     for P in polys:
         x = ctx.new_spinor(L, 0)
-        st = ctx.poly_solve(L, Uh, x, ctx.pack_spinor(L, eta, 0), P, 0.156, tol=1e-12,
-                            f64_emul=emul)
-        assert st["true_rel_res"] <= 1e-12 and st["iterations"] > 0
-        want, _, _ = orc.poly_solve(L, U, 0.156, P, eta, tol=1e-14)
+        st = ctx.poly_solve(L, Uh, x, ctx.pack_spinor(L, eta, 0), P, kappa, tol=1e-12,
+                            f64_emul=emul, U_lo=Ul)
+        # converged: below tol, or within 10 tol where the true residual
+        # stopped falling at the rounding floor of P(K)
+        assert st["true_rel_res"] <= 1e-11 and st["iterations"] > 0
+        want, _, _ = orc.poly_solve(L, U, kappa, P, eta, tol=1e-14)
         got = _np(ctx.unpack_spinor(L, x))
         assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
 
@@ -91,6 +99,24 @@ def test_rooted_trajectory_matches_oracle(orc, ctx, H):
     assert abs(r["dH"] - ro["dH"]) <= 1e-7
     assert np.abs(_np(ctx.unpack_gauge(L, Ue)) - Uo_end).max() <= 1e-9
     assert np.abs(_np(ctx.unpack_algebra(L, Pe)) - Po_end).max() <= 1e-8
+
+
+def test_rooted_trajectory_mixed_precision(orc, ctx, H):
+    """FP32 inner solves and FP32 polynomial passes of the heatbath (emulated
+    FP64 residuals), solves to 1e-10: dH within the 1e-6 target of the FP64
+    oracle's."""
+    L = (4, 4, 4, 4)
+    U = I.gauge_links(L, 0.3, 1)
+    P = I.momenta(L, 3)
+    eta = np.stack([I.gaussian_half(L, 30 + j) for j in range(5)])
+    kw = _rooted_kw()
+    _, ro, Uo_end, _ = orc.trajectory(L, U, P, eta, 0.5, tol_md=1e-13, tol_action=1e-13, **kw)
+    Ue = ctx.new_gauge(L, 0, 18)
+    r = ctx.trajectory(L, ctx.pack_gauge(L, U, 0, 18), ctx.pack_algebra(L, P),
+                       ctx.pack_spinors(L, list(eta)), 0.5, tol_md=1e-10, tol_action=1e-12,
+                       U_end=Ue, inner_prec=1, f64_emul=1, reliable_delta=1e-5, **kw)
+    assert abs(r["dH"] - ro["dH"]) <= 1e-6
+    assert np.abs(_np(ctx.unpack_gauge(L, Ue)) - Uo_end).max() <= 1e-8
 
 
 def test_rooted_md_reversible(ctx, H):
