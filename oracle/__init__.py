@@ -50,6 +50,7 @@ _P = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
 _L = ctypes.c_long
+_U64 = ctypes.c_uint64
 
 
 class TrajParams(ctypes.Structure):
@@ -114,6 +115,9 @@ def _declare(l):
         "or_trajectory": (_I, [_P, _P, _P, _P, _D, _P, _P, _P, _P]),
         "or_md_evolve": (None, [_P, _P, _P, _P, _P, _P]),
         "or_hamiltonian": (_D, [_P, _P, _P, _P, _P]),
+        "or_philox4x64": (None, [_P, _P, _P]),
+        "or_random_uniforms": (None, [_U64, _U64, _U64, _L, _P]),
+        "or_random_normals": (None, [_U64, _U64, _U64, _L, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(l, name)
@@ -431,3 +435,46 @@ def trajectory(L, U, P, eta, u, **kw):
                         ctypes.byref(p), ctypes.byref(res), _ptr(Uo), _ptr(Po))
     out = {f: getattr(res, f) for f, _ in TrajResult._fields_}
     return U, out, Uo, Po
+
+
+# ---- counter-based random numbers (rng.c) ---------------------------------------
+STREAM_MOMENTA, STREAM_SOURCES, STREAM_METROPOLIS = 0, 1, 2
+
+
+def philox(ctr, key):
+    """One Philox4x64-10 block (four uint64 words)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.zeros(4, np.uint64)
+    lib().or_philox4x64(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def random_uniforms(seed, stream, counter, n):
+    out = np.zeros(n, np.float64)
+    lib().or_random_uniforms(seed, stream, counter, n, _ptr(out))
+    return out
+
+
+def random_normals(seed, stream, counter, n):
+    out = np.zeros(n, np.float64)
+    lib().or_random_normals(seed, stream, counter, n, _ptr(out))
+    return out
+
+
+def random_momenta(L, seed, counter):
+    """Heatbath momenta, float64 [V, 4, 8], components N(0, 1)."""
+    V = volume(L)
+    return random_normals(seed, STREAM_MOMENTA, counter, V * 32).reshape(V, 4, 8)
+
+
+def random_sources(L, n, seed, counter):
+    """n pseudo-fermion sources, complex128 [n, V/2, 4, 3], density
+    exp(-|eta|^2) (E |eta_k|^2 = 1)."""
+    Vh = volume(L) // 2
+    z = random_normals(seed, STREAM_SOURCES, counter, n * Vh * 24).reshape(n, Vh, 4, 3, 2)
+    return (z[..., 0] + 1j * z[..., 1]) / np.sqrt(2.0)
+
+
+def metropolis_uniform(seed, counter):
+    return float(random_uniforms(seed, STREAM_METROPOLIS, counter, 1)[0])

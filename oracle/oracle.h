@@ -28,6 +28,7 @@
 #ifndef ORACLE_H
 #define ORACLE_H
 #include <complex.h>
+#include <stdint.h>
 #include <math.h>
 
 typedef double _Complex ocplx;
@@ -223,5 +224,12 @@ void or_md_evolve(const int L[4], ocplx *U, double *P, const ocplx *phi,
 /* H = kinetic + S_G (+ T_k) + pseudo-fermion action */
 double or_hamiltonian(const int L[4], const ocplx *U, const double *P,
                       const ocplx *phi, const or_traj_params *p);
+
+/* ---- counter-based random numbers (rng.c) ---------------------------------- */
+/* Philox4x64-10 block: out = philox(ctr, key) */
+void or_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
+/* the first n uniforms / normals of stream (seed, stream) at the counter */
+void or_random_uniforms(uint64_t seed, uint64_t stream, uint64_t counter, long n, double *out);
+void or_random_normals(uint64_t seed, uint64_t stream, uint64_t counter, long n, double *out);
 
 #endif
