@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--kernel", default=None,
                     help="time one hemi-Dslash variant alone, e.g. f16-12 (for profiling)")
     ap.add_argument("--launches", type=int, default=20)
+    ap.add_argument("--rhs", type=int, default=1,
+                    help="--kernel <prec>-<fmt>: right-hand sides per launch (links shared)")
     ap.add_argument("--tau", type=float, default=None,
                     help="trajectory length (applied after --n-md, which scales it)")
     ap.add_argument("--integrator", default="leapfrog", choices=["leapfrog", "omelyan"],
@@ -87,11 +89,17 @@ def parse():
     ap.add_argument("--mp", action="store_true",
                     help="mass-preconditioned workload: pseudo-fermions at kappa' = 0.150, "
                          "0.154 and the target kappa (ratio terms, batched solves), no filter")
-    ap.add_argument("--report", default=None, choices=["md", "thermal"],
+    ap.add_argument("--report", default=None, choices=["md", "thermal", "chain"],
                     help="md: leapfrog dH at dt = 1/10, 1/20, 1/40 and reversibility on "
                          "16^3x32, kappa 0.156, plain pseudo-fermion action; thermal: mixed "
                          "vs plain FP64 trajectories (Omelyan, 20 steps) on a 16^3x32 field "
-                         "relaxed by pure-gauge HMC (dH, acceptance, time)")
+                         "relaxed by pure-gauge HMC (dH, acceptance, time); chain: a Markov "
+                         "chain (hmc_chain, heatbath on the device) on that field with the "
+                         "Sec. III diagnostics")
+    ap.add_argument("--n-traj", type=int, default=20,
+                    help="trajectories of the --report chain run")
+    ap.add_argument("--jsonl", default=None,
+                    help="--report chain: append one JSON line per trajectory to this file")
     ap.add_argument("--variant", type=int, default=None,
                     help="hemi-Dslash kernel variant 0..3, -1 built-in default, -2 autotuned "
                          "(the trajectory benchmark autotunes by default)")
@@ -181,8 +189,10 @@ def run_kernel(args):
     prec = {"f64": hmc.F64, "f32": hmc.F32, "f16": hmc.F16, "f64e": hmc.F64E}[pname]
     fmt = int(fmt)
     U = ctx.pack_gauge(LAT, I.gauge_links(LAT, EPS_LINKS, 1), prec, fmt)
-    srcs = [ctx.pack_spinor(LAT, I.gaussian_half(LAT, 2 + i), prec) for i in range(2)]
-    out = ctx.new_spinor(LAT, prec)
+    nr = args.rhs
+    srcs = [ctx.pack_spinor(LAT, I.gaussian_half(LAT, 2 + i, n_rhs=nr) if nr > 1 else
+                            I.gaussian_half(LAT, 2 + i), prec) for i in range(2)]
+    out = ctx.new_spinor(LAT, prec, nr)
     for i in range(3):
         ctx.dslash(LAT, U, out, srcs[i % 2], i % 2)
     torch.cuda.synchronize()
@@ -192,10 +202,11 @@ def run_kernel(args):
     torch.cuda.synchronize()
     n, ms, byt = next(iter(ctx.timing().values()))
     Vh = int(np.prod(LAT)) // 2
-    print(json.dumps({"kernel": args.kernel, "variant": args.variant,
+    print(json.dumps({"kernel": args.kernel, "variant": args.variant, "rhs": nr,
                       "launches": n, "us_per_launch": round(ms / n * 1e3, 2),
+                      "us_per_rhs": round(ms / n * 1e3 / nr, 2),
                       "GBs": round(byt / (ms * 1e-3) / 1e9, 1),
-                      "TFLOPs": round(1320.0 * Vh * n / (ms * 1e-3) / 1e12, 3)}), flush=True)
+                      "TFLOPs": round(1320.0 * Vh * nr * n / (ms * 1e-3) / 1e12, 3)}), flush=True)
 
 
 def peaks():
@@ -444,6 +455,10 @@ def run_hmc(args):
                 "traffic": ncu_traffic(dom),
                 "bytes_per_launch": round(b_dom / n_dom),
                 "us_per_launch": round(ms_dom / n_dom * 1e3, 2),
+                # the standard 1320 flop per hemi-Dslash output site (one
+                # right-hand side per launch; the batched solves of --mp have more)
+                "gflops": None if args.mp else
+                round(1320.0 * (int(np.prod(LAT)) // 2) * n_dom / (ms_dom * 1e-3) / 1e9, 1),
                 "peak_source": "measured" if pk else "fallback"}
     kernels = {k: {"launches_per_step": v[0] // args.steps, "us": round(v[1] / v[0] * 1e3, 2),
                    "GBs": round(v[2] / (v[1] * 1e-3) / 1e9, 1)} for k, v in sorted(kst.items())}
@@ -765,6 +780,45 @@ def run_thermal_report(args):
     print(json.dumps(out), flush=True)
 
 
+def run_chain_report(args):
+    """A Markov chain through hmc_chain on the 16^3 x 32 field relaxed as in
+    the thermal report: kappa^4-filtered pseudo-fermion (n_t 9, n_max 29),
+    beta 5.6, kappa 0.156, tau 1, Omelyan (lambda 1/6) with 20 coarse steps
+    of 4 gauge steps, mixed precision; momenta, sources and Metropolis
+    uniforms drawn on the device; |F|^2 recorded for every force evaluation.
+    Prints the diagnostics of Sec. III: acceptance against
+    erfc(sqrt(Var(dH)/8)), <exp(-dH)>, spikes, Var(|F|^2)."""
+    import torch
+    from paper_1805_03560_gb300 import hmc, metrics
+    from paper_1805_03560_gb300 import inputs as I
+    L = (32, 16, 16, 16)
+    ctx = hmc.Context(0)
+    Ud = ctx.pack_gauge(L, I.gauge_links(L, EPS_LINKS, 1), hmc.F64, hmc.LINK18)
+    t0 = time.time()
+    acc_q, plaq = quenched_hmc(ctx, L, Ud, 5.85, 40, 20, 11)
+    relax_s = time.time() - t0
+    b, alpha, _ = hmc.filter_coeffs(2, 29, with_c=False)
+    _, _, c = hmc.filter_coeffs(2, 29)
+    kw = dict(beta=5.6, kappa=args.thermal_kappa, tau=1.0, n_md=args.n_md or 20, n_gauge=4,
+              filter_k=2, n_t=9, n_max=29, b=b, c=c, alpha=alpha, tol_md=1e-10,
+              tol_action=1e-12, integrator=hmc.OMELYAN, lam=1.0 / 6.0, inner_prec=hmc.F32,
+              force_prec=hmc.F32, reliable_delta=args.delta, f64_emul=1, measure_forces=True)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    res = ctx.chain(L, Ud, args.n_traj, 1234, counter0=0, spike_threshold=5.0, **kw)
+    torch.cuda.synchronize()
+    s = metrics.summarize(res)
+    if args.jsonl:
+        metrics.write_jsonl(args.jsonl, res, extra={"kappa": kw["kappa"], "beta": kw["beta"]})
+    out = {"report": "chain", "lattice": "16^3x32", "relax": {"beta": 5.85, "trajectories": 40,
+                                                             "plaquette": plaq,
+                                                             "s": round(relax_s, 1)},
+           **{k: v for k, v in kw.items() if k not in ("b", "c")},
+           "s_per_trajectory": round((time.time() - t1) / max(args.n_traj, 1), 3),
+           "dH": [round(r["dH"], 5) for r in res], **s}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     global LAT
     args = parse()
@@ -773,6 +827,8 @@ def main():
         run_thermal_report(args)
     elif args.report == "md":
         run_md_report(args)
+    elif args.report == "chain":
+        run_chain_report(args)
     elif args.kernel:
         run_kernel(args)
     elif args.impl == "reference":

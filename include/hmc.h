@@ -60,6 +60,7 @@
 #define HMC_H
 
 #include <stddef.h>
+#include <stdint.h>
 
 #ifdef __cplusplus
 extern "C" {
@@ -464,6 +465,11 @@ typedef struct {
   int root_levels, root_N;
   const int *root_deg;
   const double *const *root_c;
+  /* measure_forces != 0: record |F|^2 = (F, F) = sum_a F_a^2 over all links
+   * for every pseudo-fermion and every gauge force evaluation of the
+   * molecular dynamics (the force magnitudes whose variances govern
+   * Var(dH) in Sec. III); one extra reduction and host read per evaluation. */
+  int measure_forces;
 } hmc_traj_params;
 
 #define HMC_INTEGRATOR_LEAPFROG 0
@@ -475,6 +481,13 @@ typedef struct {
   int accepted;
   int cg_iterations;
   int solves;
+  /* with measure_forces: sums of |F|^2 and of |F|^4 over the n_f_pf
+   * pseudo-fermion (all terms together) and n_f_g gauge force evaluations
+   * of the molecular dynamics; zero otherwise */
+  int n_f_pf, n_f_g;
+  double f_pf2_sum, f_pf2_sq, f_g2_sum, f_g2_sq;
+  /* hmc_chain: |dH| above the chain's spike threshold (Sec. III) */
+  int spike;
 } hmc_traj_result;
 
 /* hmc_trajectory: one HMC trajectory (Sec. I): heatbath phi = Mhat^dag eta
@@ -512,6 +525,85 @@ int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U,
 int hmc_md_evolve(hmc_ctx *ctx, const hmc_lattice *lat, void *U, double *P,
                   const void *phi, const hmc_traj_params *params,
                   hmc_traj_result *res);
+
+/* ---- counter-based random numbers (heatbath and Metropolis test) ----------- */
+
+/* Philox4x64 with 10 rounds (Salmon et al., SC'11) with key (seed, stream)
+ * and counter (block q, counter, 0, 0); streams HMC_STREAM_*.  Element e of a
+ * stream is output word e % 4 of block e / 4; a word x gives the uniform
+ * ((x >> 12) + 1/2) 2^-52 in (0, 1); normals come by Box-Muller from the word
+ * pairs (x0, x1), (x2, x3) of a block: r (cos 2 pi u1, sin 2 pi u1),
+ * r = sqrt(-2 ln u0).  Results depend only on (seed, counter) and the
+ * canonical element order, not on the launch configuration.  All calls are
+ * asynchronous on the context's stream; pointers are device pointers. */
+#define HMC_STREAM_MOMENTA 0
+#define HMC_STREAM_SOURCES 1
+#define HMC_STREAM_METROPOLIS 2
+
+/* Momenta of the heatbath (Sec. I, Pi = sum_a P_a T_a with P_a ~ N(0, 1)):
+ * normal e = (x * 4 + mu) * 8 + a of stream HMC_STREAM_MOMENTA (x the
+ * lexicographic site) is component a of link (x, mu), written into the
+ * algebra field P (device layout). */
+int hmc_random_momenta(hmc_ctx *ctx, const hmc_lattice *lat, double *P, uint64_t seed,
+                       uint64_t counter);
+/* n_fields consecutive F64 even pseudo-fermion sources with density
+ * exp(-|eta|^2) (E |eta_k|^2 = 1): normal e = ((j * Vh + h) * 12 + k) * 2 +
+ * part of stream HMC_STREAM_SOURCES, times 1/sqrt(2), is part (0 real,
+ * 1 imaginary) of spin-colour component k (= s * 3 + c) at half site h of
+ * field j. */
+int hmc_random_sources(hmc_ctx *ctx, const hmc_lattice *lat, void *eta, int n_fields,
+                       uint64_t seed, uint64_t counter);
+/* u[0..n) = the first n uniforms of (seed, stream) at the counter (device
+ * array). */
+int hmc_random_uniforms(hmc_ctx *ctx, double *u, int n, uint64_t seed, uint64_t stream,
+                        uint64_t counter);
+
+/* ---- Markov chain ------------------------------------------------------------ */
+
+typedef struct {
+  uint64_t seed;
+  /* RNG counter of the first trajectory; trajectory t uses counter0 + t for
+   * its momenta, sources and Metropolis uniform */
+  uint64_t counter0;
+  int n_traj;
+  /* |dH| > spike_threshold marks a spike (Sec. III); <= 0: none marked */
+  double spike_threshold;
+} hmc_chain_params;
+
+/* hmc_chain: n_traj HMC trajectories (hmc_trajectory) with the heatbath and
+ * the Metropolis uniform drawn on the device: trajectory t takes its momenta
+ * from hmc_random_momenta, its sources from hmc_random_sources (as many
+ * fields as hmc_trajectory's eta needs for params) and u from the first
+ * uniform of HMC_STREAM_METROPOLIS, all at counter counter0 + t.  U (F64,
+ * LINK18) advances in place on every accept.  results: host array of n_traj
+ * entries.  The chain is reproducible: the same (U, seed, counter0) give the
+ * same chain bit for bit.  Blocks; stops at the first failing trajectory
+ * (its status returned, U then the last accepted field). */
+int hmc_chain(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj_params *params,
+              const hmc_chain_params *chain, hmc_traj_result *results);
+
+/* ---- checkpoints (host, no GPU needed) ---------------------------------------- */
+
+typedef struct {
+  int L[4];
+  double beta, kappa;
+  uint64_t seed, trajectory, rng_counter;
+  double plaquette; /* the caller's plaquette of the stored field */
+} hmc_checkpoint_info;
+
+/* File: the 8 bytes "HMCCKPT1", the info fields (int32 L[4], float64 beta,
+ * kappa, uint64 seed, trajectory, rng_counter, float64 plaquette), the uint32
+ * CRC-32 (IEEE 802.3 polynomial, reflected) of the link bytes, 4 zero bytes,
+ * then the links as complex128 [V, 4, 3, 3] in the canonical order, all
+ * little-endian.  Written to a temporary file renamed over path.  U_canon:
+ * host array of V * 72 doubles.  ctx (nullable) only receives the message. */
+int hmc_checkpoint_write(hmc_ctx *ctx, const char *path, const hmc_checkpoint_info *info,
+                         const double *U_canon);
+/* Reads the header into *info and, when U_canon is non-NULL, the links
+ * (n_doubles must be V * 72 for the stored L).  HMC_EINVAL for a missing or
+ * short file, a wrong magic, a size mismatch or a CRC mismatch. */
+int hmc_checkpoint_read(hmc_ctx *ctx, const char *path, hmc_checkpoint_info *info,
+                        double *U_canon, size_t n_doubles);
 
 /* ---- host helpers (no GPU needed) -------------------------------------------- */
 

@@ -217,4 +217,27 @@ int mhat(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, int sprec, int dagger, 
          void *out, const void *in, void *tmp, double kappa, const double *cb_rhs,
          double *partials, int *nblocks);
 
+// |F|^2 of the molecular-dynamics force evaluations (hmc_traj_params.measure_forces)
+struct ForceStats {
+  int n_pf = 0, n_g = 0;
+  double pf_sum = 0.0, pf_sq = 0.0, g_sum = 0.0, g_sq = 0.0;
+  void store(hmc_traj_result *r) const {
+    r->n_f_pf = n_pf;
+    r->n_f_g = n_g;
+    r->f_pf2_sum = pf_sum;
+    r->f_pf2_sq = pf_sq;
+    r->f_g2_sum = g_sum;
+    r->f_g2_sq = g_sq;
+  }
+};
+// number of F64 even fields of hmc_trajectory's eta for these parameters
+int traj_eta_fields(const hmc_traj_params *prm);
+
+// counter-based random numbers (rng.cu)
+int random_momenta(hmc_ctx *ctx, const Geo &g, double *P, uint64_t seed, uint64_t counter);
+int random_sources(hmc_ctx *ctx, const Geo &g, void *eta, int n_fields, uint64_t seed,
+                   uint64_t counter);
+int random_uniforms(hmc_ctx *ctx, double *u, int n, uint64_t seed, uint64_t stream,
+                    uint64_t counter);
+
 }  // namespace hmc

@@ -425,6 +425,22 @@ static int mp_pairs(const hmc_traj_params *prm, double *ka, double *kb) {
   return n + 1;
 }
 
+// Number of F64 even fields of hmc_trajectory's eta (and of phi).
+int traj_eta_fields(const hmc_traj_params *prm) {
+  if (rooted_terms(prm)) return rooted_terms(prm);
+  return prm->n_mp > 0 ? prm->n_mp + 1 : 1;
+}
+
+// (F, F) = sum over links and components of F_a^2 (host)
+static int algebra_norm2(hmc_ctx *ctx, const Geo &g, const double *F, double *out) {
+  double *part = partials_buf(ctx, g), *dst = scalars(ctx);
+  if (!part || !dst) return HMC_ENOMEM;
+  int nb;
+  TRY(kinetic_partials(ctx, g, F, part, &nb));
+  TRY(reduce_partials(ctx, part, nb, dst));
+  return read_dev(ctx, dst, 1, out);
+}
+
 // Molecular dynamics on two time scales (Sec. I; gauge force on the fine
 // scale, pseudo-fermion force on the coarse one, Sec. IV), with the
 // leapfrog or the second-order Omelyan integrator (parameter lambda) in the
@@ -439,9 +455,11 @@ static int mp_pairs(const hmc_traj_params *prm, double *ka, double *kb) {
 // one evaluation, and steps of different forces at the same U commute, so
 // the integrator is unchanged.  U1 is the F64/LINK18 field, Ulo its
 // inner-precision copy (refreshed from U1 before every pseudo-fermion
-// force), F scratch for the force.
+// force), F scratch for the force.  fs (nullable) receives |F|^2 of every
+// force evaluation.
 int md_evolve(hmc_ctx *ctx, const Geo &g, void *U1, void *Ulo, double *P, double *F,
-              const void *phi, const hmc_traj_params *prm, int *solves, hmc_solve_stats *acc) {
+              const void *phi, const hmc_traj_params *prm, int *solves, hmc_solve_stats *acc,
+              ForceStats *fs) {
   const int plo = prm->solver.inner_prec;
   const int fmt_lo = prm->link_fmt_lo ? prm->link_fmt_lo : HMC_LINK12;
   const int k = prm->filter_k;
@@ -476,6 +494,13 @@ int md_evolve(hmc_ctx *ctx, const Geo &g, void *U1, void *Ulo, double *P, double
                    acc));
       *solves += k ? 2 : 1;
     }
+    if (fs) {
+      double f2;
+      TRY(algebra_norm2(ctx, g, F, &f2));
+      fs->n_pf += 1;
+      fs->pf_sum += f2;
+      fs->pf_sq += f2 * f2;
+    }
     return update_momenta(ctx, g, P, F, eps);
   };
   // with force_prec F32 the gauge force runs on an F32 copy of the links
@@ -490,6 +515,13 @@ int md_evolve(hmc_ctx *ctx, const Geo &g, void *U1, void *Ulo, double *P, double
       TRY(gauge_force(ctx, g, Ug32, prm->beta, prm->kappa, k, 1.0, F));
     } else {
       TRY(gauge_force(ctx, g, Uh, prm->beta, prm->kappa, k, 1.0, F));
+    }
+    if (fs) {
+      double f2;
+      TRY(algebra_norm2(ctx, g, F, &f2));
+      fs->n_g += 1;
+      fs->g_sum += f2;
+      fs->g_sq += f2 * f2;
     }
     return update_momenta(ctx, g, P, F, eps);
   };
@@ -823,7 +855,10 @@ int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj
   TRY(gauge_action(ctx, g, Uh, prm->beta, prm->kappa, k, &sg0, &ps0));
   res->plaq0 = ps0 / (18.0 * 2.0 * g.Vh);
   res->H0 = kin0 + sg0 + spf0;
-  TRY(md_evolve(ctx, g, U1, Ulo, P, F, phi, prm, &res->solves, &acc));
+  ForceStats fst{};
+  TRY(md_evolve(ctx, g, U1, Ulo, P, F, phi, prm, &res->solves, &acc,
+                prm->measure_forces ? &fst : nullptr));
+  fst.store(res);
   // H1 with the action solves
   double kin1, sg1, spf1, ps1;
   TRY(hmc_kinetic(ctx, lat, P, &kin1));
@@ -867,11 +902,14 @@ extern "C" int hmc_md_evolve(hmc_ctx *ctx, const hmc_lattice *lat, void *U, doub
   if ((plo != HMC_F64 && !Ulo) || !F) return HMC_ENOMEM;
   hmc_solve_stats acc{};
   int solves = 0;
-  TRY(md_evolve(ctx, g, U, Ulo, P, F, phi, prm, &solves, &acc));
+  ForceStats fst{};
+  TRY(md_evolve(ctx, g, U, Ulo, P, F, phi, prm, &solves, &acc,
+                prm->measure_forces ? &fst : nullptr));
   if (res) {
     memset(res, 0, sizeof(*res));
     res->cg_iterations = acc.iterations;
     res->solves = solves;
+    fst.store(res);
   }
   return cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), "md_evolve");
 }

@@ -22,6 +22,8 @@ OK, EINVAL, ENOMEM, ENOCONV, ETIMEOUT, ENAN, ECUDA = range(7)
 _STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ENOCONV", 4: "ETIMEOUT", 5: "ENAN", 6: "ECUDA"}
 
 _P, _I, _D, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+_U64 = ctypes.c_uint64
+STREAM_MOMENTA, STREAM_SOURCES, STREAM_METROPOLIS = 0, 1, 2
 
 
 class Lat(ctypes.Structure):
@@ -53,12 +55,25 @@ class TrajParams(ctypes.Structure):
                 ("solver", SolverOpts), ("link_fmt_lo", _I),
                 ("n_mp", _I), ("kappa_mp", _P),
                 ("integrator", _I), ("lam", _D),
-                ("root_levels", _I), ("root_N", _I), ("root_deg", _P), ("root_c", _P)]
+                ("root_levels", _I), ("root_N", _I), ("root_deg", _P), ("root_c", _P),
+                ("measure_forces", _I)]
 
 
 class TrajResult(ctypes.Structure):
     _fields_ = [("H0", _D), ("H1", _D), ("dH", _D), ("plaq0", _D), ("plaq1", _D),
-                ("accepted", _I), ("cg_iterations", _I), ("solves", _I)]
+                ("accepted", _I), ("cg_iterations", _I), ("solves", _I),
+                ("n_f_pf", _I), ("n_f_g", _I),
+                ("f_pf2_sum", _D), ("f_pf2_sq", _D), ("f_g2_sum", _D), ("f_g2_sq", _D),
+                ("spike", _I)]
+
+
+class ChainParams(ctypes.Structure):
+    _fields_ = [("seed", _U64), ("counter0", _U64), ("n_traj", _I), ("spike_threshold", _D)]
+
+
+class CheckpointInfo(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int * 4), ("beta", _D), ("kappa", _D), ("seed", _U64),
+                ("trajectory", _U64), ("rng_counter", _U64), ("plaquette", _D)]
 
 
 class HmcError(RuntimeError):
@@ -107,6 +122,12 @@ _SIGS = {
     "hmc_action_mp": (_I, [_P, _P, _P, _P, _P, _I, _P, _P, _D, _P, _P, _P]),
     "hmc_heatbath_mp": (_I, [_P, _P, _P, _P, _P, _I, _P, _P, _D, _P, _P, _P]),
     "hmc_md_evolve": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "hmc_random_momenta": (_I, [_P, _P, _P, _U64, _U64]),
+    "hmc_random_sources": (_I, [_P, _P, _P, _I, _U64, _U64]),
+    "hmc_random_uniforms": (_I, [_P, _P, _I, _U64, _U64, _U64]),
+    "hmc_chain": (_I, [_P, _P, _P, _P, _P, _P]),
+    "hmc_checkpoint_write": (_I, [_P, ctypes.c_char_p, _P, _P]),
+    "hmc_checkpoint_read": (_I, [_P, ctypes.c_char_p, _P, _P, _SZ]),
 }
 
 _lib = None
@@ -589,24 +610,20 @@ class Context:
                    n_max=0, b=None, c=None, alpha=0.0, tol_md=1e-10, tol_action=1e-12,
                    inner_prec=F64, link_fmt_lo=LINK12, reliable_delta=0.1, U_end=None,
                    P_end=None, force_prec=F64, kappa_mp=None, integrator=LEAPFROG,
-                   lam=1.0 / 6.0, f64_emul=0, root_polys=None, root_N=0):
+                   lam=1.0 / 6.0, f64_emul=0, root_polys=None, root_N=0, measure_forces=False):
         """One HMC trajectory; U (F64/LINK18 gauge Field) is updated in place
         when accepted.  Returns the result as a dict.  kappa_mp: heavier
         hopping parameters of a mass-preconditioned chain (eta then from
         pack_spinors with len(kappa_mp) + 1 fields)."""
         self._stream()
         keep = []
-        prm = TrajParams(beta=beta, kappa=kappa, tau=tau, n_md=n_md, n_gauge=n_gauge,
-                         filter_k=filter_k, n_t=n_t, n_max=n_max, alpha=alpha, tol_md=tol_md,
-                         tol_action=tol_action,
-                         solver=SolverOpts(inner_prec, reliable_delta, 16, force_prec, f64_emul),
-                         link_fmt_lo=link_fmt_lo, integrator=integrator, lam=lam)
-        self._mp(prm, kappa_mp, keep)
-        self._root(prm, root_polys, root_N, keep)
-        if b is not None:
-            ab = np.ascontiguousarray(b, dtype=np.float64); keep.append(ab); prm.b = ab.ctypes.data
-        if c is not None:
-            ac = np.ascontiguousarray(c, dtype=np.float64); keep.append(ac); prm.c = ac.ctypes.data
+        prm = self._traj_params(
+            keep, beta=beta, kappa=kappa, tau=tau, n_md=n_md, n_gauge=n_gauge, filter_k=filter_k,
+            n_t=n_t, n_max=n_max, b=b, c=c, alpha=alpha, tol_md=tol_md, tol_action=tol_action,
+            inner_prec=inner_prec, link_fmt_lo=link_fmt_lo, reliable_delta=reliable_delta,
+            force_prec=force_prec, kappa_mp=kappa_mp, integrator=integrator, lam=lam,
+            f64_emul=f64_emul, root_polys=root_polys, root_N=root_N,
+            measure_forces=measure_forces)
         res = TrajResult()
         st = lib().hmc_trajectory(self.h, _ref(lattice(L)), U.ptr(), ctypes.byref(prm),
                                   _dp(P.data), eta.ptr(), u, ctypes.byref(res),
@@ -615,10 +632,90 @@ class Context:
         self._check(st, "hmc_trajectory")
         return {f: getattr(res, f) for f, _ in TrajResult._fields_}
 
+    def _traj_params(self, keep, beta, kappa, tau, n_md, n_gauge, filter_k=0, n_t=0, n_max=0,
+                     b=None, c=None, alpha=0.0, tol_md=1e-10, tol_action=1e-12, inner_prec=F64,
+                     link_fmt_lo=LINK12, reliable_delta=0.1, force_prec=F64, kappa_mp=None,
+                     integrator=LEAPFROG, lam=1.0 / 6.0, f64_emul=0, root_polys=None, root_N=0,
+                     measure_forces=False):
+        """hmc_traj_params; arrays it points to are appended to keep."""
+        prm = TrajParams(beta=beta, kappa=kappa, tau=tau, n_md=n_md, n_gauge=n_gauge,
+                         filter_k=filter_k, n_t=n_t, n_max=n_max, alpha=alpha, tol_md=tol_md,
+                         tol_action=tol_action,
+                         solver=SolverOpts(inner_prec, reliable_delta, 16, force_prec, f64_emul),
+                         link_fmt_lo=link_fmt_lo, integrator=integrator, lam=lam,
+                         measure_forces=int(bool(measure_forces)))
+        self._mp(prm, kappa_mp, keep)
+        self._root(prm, root_polys, root_N, keep)
+        if b is not None:
+            ab = np.ascontiguousarray(b, dtype=np.float64); keep.append(ab); prm.b = ab.ctypes.data
+        if c is not None:
+            ac = np.ascontiguousarray(c, dtype=np.float64); keep.append(ac); prm.c = ac.ctypes.data
+        return prm
+
+    # ---- heatbath random numbers and the Markov chain ---------------------------
+    def random_momenta(self, L, seed, counter, P=None):
+        """Momenta with N(0,1) components from (seed, counter) (hmc_random_momenta)."""
+        self._stream()
+        P = P if P is not None else self.new_algebra(L)
+        st = lib().hmc_random_momenta(self.h, _ref(lattice(L)), _dp(P.data), seed, counter)
+        self._check(st, "hmc_random_momenta")
+        return P
+
+    def random_sources(self, L, n, seed, counter):
+        """n consecutive F64 even sources, density exp(-|eta|^2) (hmc_random_sources)."""
+        self._stream()
+        nb = int(lib().hmc_spinor_bytes(_ref(lattice(L)), F64, 1))
+        out = Field(self._bytes(nb * n), "spinor", F64, 1)
+        out.n_fields = n
+        st = lib().hmc_random_sources(self.h, _ref(lattice(L)), out.ptr(), n, seed, counter)
+        self._check(st, "hmc_random_sources")
+        return out
+
+    def random_uniforms(self, n, seed, stream, counter):
+        self._stream()
+        u = self.torch.empty(n, dtype=self.torch.float64, device=f"cuda:{self.device}")
+        st = lib().hmc_random_uniforms(self.h, _dp(u), n, seed, stream, counter)
+        self._check(st, "hmc_random_uniforms")
+        return u
+
+    def chain(self, L, U, n_traj, seed, counter0=0, spike_threshold=0.0, **traj):
+        """n_traj trajectories with the heatbath drawn on the device
+        (hmc_chain); U (F64/LINK18) advances in place.  traj: the keyword
+        arguments of trajectory().  Returns one result dict per trajectory."""
+        self._stream()
+        keep = []
+        prm = self._traj_params(keep, **traj)
+        cp = ChainParams(seed, counter0, n_traj, spike_threshold)
+        res = (TrajResult * max(n_traj, 1))()
+        st = lib().hmc_chain(self.h, _ref(lattice(L)), U.ptr(), ctypes.byref(prm),
+                             ctypes.byref(cp), res)
+        self._check(st, "hmc_chain")
+        return [{f: getattr(res[t], f) for f, _ in TrajResult._fields_} for t in range(n_traj)]
+
+    def save_checkpoint(self, path, L, U, beta, kappa, seed, trajectory, rng_counter):
+        """Write U (F64/LINK18 Field) with its plaquette (hmc_checkpoint_write)."""
+        Uc = self.unpack_gauge(L, U).cpu().numpy()
+        info = dict(L=list(L), beta=beta, kappa=kappa, seed=seed, trajectory=trajectory,
+                    rng_counter=rng_counter, plaquette=self.plaquette(L, U))
+        write_checkpoint(path, info, Uc, ctx=self)
+        return info
+
+    def load_checkpoint(self, path):
+        """(info dict, U as an F64/LINK18 Field); raises when the plaquette
+        recomputed on the device differs from the stored one."""
+        info, Uc = read_checkpoint(path, ctx=self)
+        L = tuple(info["L"])
+        U = self.pack_gauge(L, Uc, F64, LINK18)
+        plaq = self.plaquette(L, U)
+        if abs(plaq - info["plaquette"]) > 1e-14 * max(1.0, abs(info["plaquette"])):
+            raise HmcError(EINVAL, f"checkpoint {path}: plaquette {plaq} != stored "
+                                   f"{info['plaquette']}")
+        return info, U
+
     def md_evolve(self, L, U, P, phi, beta, kappa, tau, n_md, n_gauge, filter_k=0, n_t=0,
                   b=None, alpha=0.0, tol_md=1e-10, inner_prec=F64, link_fmt_lo=LINK12,
                   reliable_delta=0.1, force_prec=F64, kappa_mp=None, integrator=LEAPFROG,
-                  lam=1.0 / 6.0, f64_emul=0, root_polys=None, root_N=0):
+                  lam=1.0 / 6.0, f64_emul=0, root_polys=None, root_N=0, measure_forces=False):
         """Molecular dynamics with phi fixed; U (F64/LINK18) and P updated in place."""
         self._stream()
         keep = []
@@ -626,7 +723,8 @@ class Context:
                          filter_k=filter_k, n_t=n_t, n_max=n_t, alpha=alpha, tol_md=tol_md,
                          tol_action=tol_md,
                          solver=SolverOpts(inner_prec, reliable_delta, 16, force_prec, f64_emul),
-                         link_fmt_lo=link_fmt_lo, integrator=integrator, lam=lam)
+                         link_fmt_lo=link_fmt_lo, integrator=integrator, lam=lam,
+                         measure_forces=int(bool(measure_forces)))
         self._mp(prm, kappa_mp, keep)
         self._root(prm, root_polys, root_N, keep)
         if b is not None:
@@ -637,4 +735,40 @@ class Context:
         st = lib().hmc_md_evolve(self.h, _ref(lattice(L)), U.ptr(), _dp(P.data), phi.ptr(),
                                  ctypes.byref(prm), ctypes.byref(res))
         self._check(st, "hmc_md_evolve")
-        return {"cg_iterations": res.cg_iterations, "solves": res.solves}
+        return {f: getattr(res, f) for f, _ in TrajResult._fields_ if f not in
+                ("H0", "H1", "dH", "plaq0", "plaq1", "accepted", "spike")}
+
+
+# ---- checkpoints (host only) ---------------------------------------------------------
+def write_checkpoint(path, info, U_canon, ctx=None):
+    """hmc_checkpoint_write: info = dict(L, beta, kappa, seed, trajectory,
+    rng_counter, plaquette); U_canon complex128 [V, 4, 3, 3]."""
+    U = np.ascontiguousarray(U_canon, dtype=np.complex128)
+    ci = CheckpointInfo((ctypes.c_int * 4)(*[int(v) for v in info["L"]]), info["beta"],
+                        info["kappa"], int(info["seed"]), int(info["trajectory"]),
+                        int(info["rng_counter"]), info["plaquette"])
+    st = lib().hmc_checkpoint_write(ctx.h if ctx else None, os.fsencode(path), ctypes.byref(ci),
+                                    U.ctypes.data)
+    if st:
+        msg = lib().hmc_last_error(ctx.h).decode() if ctx else path
+        raise HmcError(st, f"hmc_checkpoint_write: {msg}")
+
+
+def read_checkpoint(path, links=True, ctx=None):
+    """hmc_checkpoint_read: (info dict, links complex128 [V, 4, 3, 3] or None)."""
+    ci = CheckpointInfo()
+    st = lib().hmc_checkpoint_read(ctx.h if ctx else None, os.fsencode(path), ctypes.byref(ci),
+                                   None, 0)
+    if not st and links:
+        V = int(np.prod(list(ci.L)))
+        U = np.empty((V, 4, 3, 3), np.complex128)
+        st = lib().hmc_checkpoint_read(ctx.h if ctx else None, os.fsencode(path),
+                                       ctypes.byref(ci), U.ctypes.data, V * 72)
+    else:
+        U = None
+    if st:
+        msg = lib().hmc_last_error(ctx.h).decode() if ctx else path
+        raise HmcError(st, f"hmc_checkpoint_read: {msg}")
+    info = {f: getattr(ci, f) for f, _ in CheckpointInfo._fields_}
+    info["L"] = list(ci.L)
+    return info, U

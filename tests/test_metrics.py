@@ -1,0 +1,71 @@
+"""Host chain diagnostics (Sec. III), on synthetic dH samples.
+
+* the acceptance formula P_acc = erfc(sqrt(Var(dH)/8)) is pinned by numerical
+  integration of <min(1, exp(-dH))> over a Gaussian dH of mean Var/2 (the mean
+  that <exp(-dH)> = 1 forces on a Gaussian);
+* summarize() estimates <min(1, e^-dH)>, <e^-dH> = 1 and the erfc prediction
+  consistently on large Gaussian samples, counts spikes, and forms the force
+  variances from the per-trajectory sums.
+"""
+import json
+import math
+
+import numpy as np
+import pytest
+
+from paper_1805_03560_gb300 import metrics
+
+integrate = pytest.importorskip("scipy.integrate")
+
+
+@pytest.mark.parametrize("sigma", [0.1, 0.3, 0.7, 1.2])
+def test_erfc_formula_by_integration(sigma):
+    mu = sigma * sigma / 2
+
+    def dens(x):
+        return math.exp(-(x - mu) ** 2 / (2 * sigma * sigma)) / (sigma * math.sqrt(2 * math.pi))
+
+    lo, hi = mu - 12 * sigma, mu + 12 * sigma
+    p = integrate.quad(lambda x: dens(x), lo, 0.0)[0] + \
+        integrate.quad(lambda x: math.exp(-x) * dens(x), 0.0, hi)[0]
+    assert abs(p - math.erfc(math.sqrt(sigma * sigma / 8))) < 1e-10
+    e = integrate.quad(lambda x: math.exp(-x) * dens(x), lo, hi)[0]
+    assert abs(e - 1.0) < 1e-10
+
+
+def _fake(dH, rng, spike_at=()):
+    out = []
+    for i, d in enumerate(dH):
+        u = rng.uniform()
+        out.append(dict(dH=float(d), accepted=int(u < math.exp(-d)), plaq0=0.5, plaq1=0.6,
+                        cg_iterations=100, spike=int(i in spike_at), n_f_pf=2, n_f_g=4,
+                        f_pf2_sum=2.0 * (3.0 + i % 2), f_pf2_sq=2.0 * (3.0 + i % 2) ** 2,
+                        f_g2_sum=4.0, f_g2_sq=4.0))
+    return out
+
+
+def test_summarize_gaussian_chain():
+    rng = np.random.default_rng(5)
+    sigma = 0.5
+    dH = rng.normal(sigma * sigma / 2, sigma, 200000)
+    s = metrics.summarize(_fake(dH, rng, spike_at=(3, 17)))
+    want = math.erfc(sigma / math.sqrt(8))
+    assert abs(s["acceptance"] - want) < 5 * s["acceptance_err"]
+    assert abs(s["acceptance_counted"] - want) < 5 * math.sqrt(want * (1 - want) / dH.size)
+    assert abs(s["exp_minus_dH"] - 1.0) < 5 * s["exp_minus_dH_err"]
+    assert abs(s["acceptance_erfc"] - want) < 1e-2
+    assert s["spikes"] == 2
+    # |F|^2 alternates 3, 4 per trajectory: mean 3.5, variance 0.25 (n / (n - 1))
+    assert abs(s["force_pf2_mean"] - 3.5) < 1e-12
+    n = s["force_pf_evaluations"]
+    assert abs(s["force_pf2_var"] - 0.25 * n / (n - 1)) < 1e-9
+    assert s["force_g2_var"] == 0.0
+    # plaquette of the field left behind: 0.6 when accepted, else 0.5
+    assert abs(s["plaquette"] - (0.5 + 0.1 * s["acceptance_counted"])) < 1e-12
+
+
+def test_write_jsonl(tmp_path):
+    p = tmp_path / "chain.jsonl"
+    metrics.write_jsonl(p, [{"dH": 0.1, "accepted": 1}], extra={"beta": 5.6})
+    rec = json.loads(p.read_text().strip())
+    assert rec == {"dH": 0.1, "accepted": 1, "beta": 5.6, "index": 0}
