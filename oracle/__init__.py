@@ -90,6 +90,7 @@ def _declare(l):
         "or_K": (None, [_P, _P, _D, _I, _P, _P]),
         "or_cg": (_I, [_P, _P, _D, _P, _P, _D, _I, _P]),
         "or_mhat_inverse": (_I, [_P, _P, _D, _P, _P, _D, _I]),
+        "or_bicgstab": (_I, [_P, _P, _D, _I, _P, _P, _D, _I, _P]),
         "or_plaquette_sum": (_D, [_P, _P]),
         "or_gauge_action": (_D, [_P, _P, _D]),
         "or_gauge_force": (None, [_P, _P, _D, _D, _P]),
@@ -217,6 +218,17 @@ def cg(L, U, kappa, phi, tol=1e-12, max_iter=10000):
     rel = ctypes.c_double(0)
     it = lib().or_cg(_dims(L), _ptr(U), kappa, _ptr(phi), _ptr(x), tol,
                      max_iter, ctypes.byref(rel))
+    return x, it, rel.value
+
+
+def bicgstab(L, U, kappa, b, dagger=False, tol=1e-12, max_iter=10000):
+    """BiCGstab on Mhat x = b (or Mhat^dag x = b).  Returns (x, iterations,
+    true relative residual); iterations = -1 when max_iter was reached."""
+    U = _c(U, np.complex128); b = _c(b, np.complex128)
+    x = np.zeros_like(b)
+    rel = ctypes.c_double(0)
+    it = lib().or_bicgstab(_dims(L), _ptr(U), kappa, int(dagger), _ptr(b), _ptr(x), tol,
+                           max_iter, ctypes.byref(rel))
     return x, it, rel.value
 
 

@@ -78,6 +78,10 @@ void or_K(const int L[4], const ocplx *U, double kappa, int dagger,
  * -1 if max_iter was reached; *rel_res receives the true relative residual. */
 int or_cg(const int L[4], const ocplx *U, double kappa, const ocplx *phi,
           ocplx *x, double tol, int max_iter, double *rel_res);
+/* BiCGstab on Mhat x = b (dagger = 0) or Mhat^dag x = b (bicgstab.c);
+ * returns the iterations, -1 when max_iter was reached */
+int or_bicgstab(const int L[4], const ocplx *U, double kappa, int dagger, const ocplx *b,
+                ocplx *x, double tol, int max_iter, double *rel_res);
 /* y = Mhat^{-1} phi via the normal equations */
 int or_mhat_inverse(const int L[4], const ocplx *U, double kappa,
                     const ocplx *phi, ocplx *y, double tol, int max_iter);
