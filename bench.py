@@ -96,6 +96,8 @@ def parse():
                          "relaxed by pure-gauge HMC (dH, acceptance, time); chain: a Markov "
                          "chain (hmc_chain, heatbath on the device) on that field with the "
                          "Sec. III diagnostics")
+    ap.add_argument("--solver", default="cg", choices=["cg", "bicgstab"],
+                    help="solves of Mhat^dag Mhat: CG, or two BiCGstab solves (the paper's)")
     ap.add_argument("--n-traj", type=int, default=20,
                     help="trajectories of the --report chain run")
     ap.add_argument("--jsonl", default=None,
@@ -384,6 +386,7 @@ def run_hmc(args):
         # the relaxed field's critical kappa is ~0.1577 (spectral radius of K
         # 0.998 at 0.1575 on 16 x 8^3), so the roots are taken at 0.156
         work["kappa"] = 0.156
+    solver = hmc.SOLVER_BICGSTAB if args.solver == "bicgstab" else hmc.SOLVER_CG
     if args.rooted:
         # Sec. II.A with kappa^4 filtering: M_1 = Mtilde (k = 2), P_1, P_2 of
         # degrees 16 and 42, the remainder truncated at n_t = 15 / n_max = 29
@@ -392,14 +395,16 @@ def run_hmc(args):
         work.update(filter_k=2, n_t=15, n_max=29)
         kw = dict(work, b=rb, c=rc, alpha=ra, root_polys=rp, root_N=args.rooted,
                   inner_prec=inner, link_fmt_lo=hmc.LINK12, reliable_delta=args.delta,
-                  force_prec=fprec, f64_emul=args.f64_emul)
+                  force_prec=fprec, f64_emul=args.f64_emul, solver=solver)
     elif args.mp:
         work.update(filter_k=0, n_t=0, n_max=0)
         kw = dict(work, kappa_mp=KAPPA_MP, inner_prec=inner, link_fmt_lo=hmc.LINK12,
-                  reliable_delta=args.delta, force_prec=fprec, f64_emul=args.f64_emul)
+                  reliable_delta=args.delta, force_prec=fprec, f64_emul=args.f64_emul,
+                  solver=solver)
     else:
         kw = dict(work, b=b, c=c, alpha=alpha, inner_prec=inner, link_fmt_lo=hmc.LINK12,
-                  reliable_delta=args.delta, force_prec=fprec, f64_emul=args.f64_emul)
+                  reliable_delta=args.delta, force_prec=fprec, f64_emul=args.f64_emul,
+                  solver=solver)
     stream = torch.cuda.current_stream()
 
     def one(kwargs):
@@ -477,6 +482,7 @@ def run_hmc(args):
                    "lattice": "x".join(str(v) for v in LAT[::-1]), **{k: v for k, v in work.items()},
                    "inner_prec": args.inner, "reliable_delta": args.delta,
                    "force_prec": args.force_prec, "f64_emul": args.f64_emul,
+                   "solver": args.solver,
                    "dslash_variant": "autotuned" if args.variant is None else args.variant,
                    "links": "12-real (inner), 18-real FP64",
                    "l2": "flushed between timed steps (256 MB write)",
@@ -802,7 +808,8 @@ def run_chain_report(args):
     kw = dict(beta=5.6, kappa=args.thermal_kappa, tau=1.0, n_md=args.n_md or 20, n_gauge=4,
               filter_k=2, n_t=9, n_max=29, b=b, c=c, alpha=alpha, tol_md=1e-10,
               tol_action=1e-12, integrator=hmc.OMELYAN, lam=1.0 / 6.0, inner_prec=hmc.F32,
-              force_prec=hmc.F32, reliable_delta=args.delta, f64_emul=1, measure_forces=True)
+              force_prec=hmc.F32, reliable_delta=args.delta, f64_emul=1, measure_forces=True,
+              solver=hmc.SOLVER_BICGSTAB if args.solver == "bicgstab" else hmc.SOLVER_CG)
     torch.cuda.synchronize()
     t1 = time.time()
     res = ctx.chain(L, Ud, args.n_traj, 1234, counter0=0, spike_threshold=5.0, **kw)
@@ -810,7 +817,7 @@ def run_chain_report(args):
     s = metrics.summarize(res)
     if args.jsonl:
         metrics.write_jsonl(args.jsonl, res, extra={"kappa": kw["kappa"], "beta": kw["beta"]})
-    out = {"report": "chain", "lattice": "16^3x32", "relax": {"beta": 5.85, "trajectories": 40,
+    out = {"report": "chain", "lattice": "16^3x32", "solver_name": args.solver, "relax": {"beta": 5.85, "trajectories": 40,
                                                              "plaquette": plaq,
                                                              "s": round(relax_s, 1)},
            **{k: v for k, v in kw.items() if k not in ("b", "c")},

@@ -234,7 +234,14 @@ typedef struct {
                             significant bits) on an F64E copy of U_hi made
                             per call; needs U_hi in LINK18 (otherwise
                             native FP64 is used).  0: native FP64. */
+  int solver;            /* solves of Mhat^dag Mhat inside forces, actions
+                            and trajectories: HMC_SOLVER_CG (default) or
+                            HMC_SOLVER_BICGSTAB (two BiCGstab solves,
+                            Mhat^dag then Mhat, the paper's solver) */
 } hmc_solver_opts;
+
+#define HMC_SOLVER_CG 0
+#define HMC_SOLVER_BICGSTAB 1
 
 typedef struct {
   int iterations;       /* CG iterations */
@@ -377,6 +384,27 @@ int hmc_heatbath_mp(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
                     const double *kappa_a, const double *kappa_b, double tol,
                     const hmc_solver_opts *opts, void *phi,
                     hmc_solve_stats *stats);
+
+/* hmc_bicgstab_solve: x = Mhat^{-1} b (dagger = 0) or Mhat^{-dag} b
+ * (dagger = 1) by BiCGstab (van der Vorst 1992; Sec. IV: the paper's solver,
+ * run to machine precision there).  Defect correction: passes of BiCGstab
+ * in the inner precision (FP32 fields on U_lo when U_lo is given, F32 links
+ * of either format; FP64 on U_hi otherwise) from e = 0 with shadow residual
+ * r, each followed by the FP64-accurate true residual r = b - A x (emulated
+ * FP64 when opts->f64_emul).  Stops when |b - A x| / |b| <= tol; HMC_ENOCONV
+ * when a pass no longer halves it or max_iter (iterations of all passes; <= 0
+ * means 100000) runs out, x then the last iterate.  One iteration applies
+ * Mhat twice (four hemi-Dslash).  BiCGstab needs the spectrum of Mhat in the
+ * right half-plane (spectral radius of K below 1); where it surrounds the
+ * origin (kappa above the field's critical value) a pass diverges and the
+ * result is HMC_ENOCONV, while CG on Mhat^dag Mhat still converges.
+ * x, b: F64 even fields, x must not alias b.
+ * opts (nullable) only for f64_emul.  stats: iterations, passes (in
+ * reliable_updates), true residual.  Blocking. */
+int hmc_bicgstab_solve(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
+                       const hmc_gauge *U_lo, void *x, const void *b, double kappa, int dagger,
+                       double tol, int max_iter, const hmc_solver_opts *opts,
+                       hmc_solve_stats *stats);
 
 /* hmc_poly_solve: x = P(K)^{-1} b with P(K) = sum_{i<=degree} coeffs[i] K^i
  * (host coefficients), K = kappa^2 H_eo H_oe: the heatbath of a

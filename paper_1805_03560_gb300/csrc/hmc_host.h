@@ -168,6 +168,15 @@ int cg_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
              const void *b, double kappa, double tol, int max_iter, const hmc_solver_opts *opts,
              hmc_solve_stats *stats);
 
+// BiCGstab on Mhat (dagger 0) or Mhat^dag, and (Mhat^dag Mhat)^{-1} as two
+// such solves (bicgstab.cu)
+int bicgstab_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul, void *x,
+                   const void *b, double kappa, int dagger, double tol, int max_iter,
+                   const hmc_solver_opts *opts, hmc_solve_stats *stats);
+int bicgstab_normal(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul, void *X,
+                    const void *phi, double kappa, double tol, int max_iter,
+                    const hmc_solver_opts *opts, hmc_solve_stats *stats);
+
 // FP64-accurate operator applications, native or emulated (hiprec.cu).
 // hi_begin makes the F64E copy of the links when opts->f64_emul is set; tag
 // names the workspace (one tag per caller that may be active at a time).

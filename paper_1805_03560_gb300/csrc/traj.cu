@@ -100,7 +100,9 @@ static int solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gaug
                  const void *b, double kappa, double tol, const hmc_solver_opts *opts,
                  hmc_solve_stats *acc) {
   hmc_solve_stats s{};
-  int st = cg_solve(ctx, g, Uh, Ul, x, b, kappa, tol, 100000, opts, &s);
+  int st = opts && opts->solver == HMC_SOLVER_BICGSTAB
+               ? bicgstab_normal(ctx, g, Uh, Ul, x, b, kappa, tol, 100000, opts, &s)
+               : cg_solve(ctx, g, Uh, Ul, x, b, kappa, tol, 100000, opts, &s);
   add_stats(acc, s);
   return st;
 }

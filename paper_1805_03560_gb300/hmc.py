@@ -36,7 +36,10 @@ class Gauge(ctypes.Structure):
 
 class SolverOpts(ctypes.Structure):
     _fields_ = [("inner_prec", _I), ("reliable_delta", _D), ("check_every", _I),
-                ("force_prec", _I), ("f64_emul", _I)]
+                ("force_prec", _I), ("f64_emul", _I), ("solver", _I)]
+
+
+SOLVER_CG, SOLVER_BICGSTAB = 0, 1
 
 
 class SolveStats(ctypes.Structure):
@@ -122,6 +125,7 @@ _SIGS = {
     "hmc_action_mp": (_I, [_P, _P, _P, _P, _P, _I, _P, _P, _D, _P, _P, _P]),
     "hmc_heatbath_mp": (_I, [_P, _P, _P, _P, _P, _I, _P, _P, _D, _P, _P, _P]),
     "hmc_md_evolve": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "hmc_bicgstab_solve": (_I, [_P, _P, _P, _P, _P, _P, _D, _I, _D, _I, _P, _P]),
     "hmc_random_momenta": (_I, [_P, _P, _P, _U64, _U64]),
     "hmc_random_sources": (_I, [_P, _P, _P, _I, _U64, _U64]),
     "hmc_random_uniforms": (_I, [_P, _P, _I, _U64, _U64, _U64]),
@@ -364,6 +368,23 @@ class Context:
         self._check(st, "hmc_mhat")
         return out
 
+    def bicgstab_solve(self, L, U_hi, x, b, kappa, tol, dagger=False, max_iter=0, U_lo=None,
+                       f64_emul=0):
+        """x = Mhat^{-1} b (or Mhat^{-dag} b) by BiCGstab; U_lo (F32 links)
+        runs the passes in FP32.  Returns the solve statistics."""
+        self._stream()
+        gh = U_hi.gauge()
+        gl = U_lo.gauge() if U_lo is not None else None
+        opts = SolverOpts(F64, 0.1, 16, F64, f64_emul, SOLVER_BICGSTAB)
+        stats = SolveStats()
+        st = lib().hmc_bicgstab_solve(self.h, _ref(lattice(L)), ctypes.byref(gh),
+                                      ctypes.byref(gl) if gl is not None else None, x.ptr(),
+                                      b.ptr(), kappa, int(bool(dagger)), tol, max_iter,
+                                      ctypes.byref(opts), ctypes.byref(stats))
+        self._check(st, "hmc_bicgstab_solve")
+        return {"iterations": stats.iterations, "passes": stats.reliable_updates,
+                "true_rel_res": stats.true_rel_res}
+
     def cg_solve(self, L, U_hi, x, phi, kappa, tol, max_iter=10000, U_lo=None, inner_prec=F64,
                  reliable_delta=0.1, check_every=16, f64_emul=0):
         self._stream()
@@ -410,13 +431,14 @@ class Context:
         return Filter(arr.ctypes.data, len(arr) - 1, alpha), arr
 
     def force_pf(self, L, U_hi, phi, kappa, F, coeff=1.0, tol=1e-12, U_lo=None, inner_prec=F64,
-                 b=None, alpha=0.0, reliable_delta=0.1, force_prec=F64, f64_emul=0):
+                 b=None, alpha=0.0, reliable_delta=0.1, force_prec=F64, f64_emul=0,
+                 solver=SOLVER_CG):
         """F += coeff * F_PF (plain action when b is None, else the filtered one)."""
         self._stream()
         gh = U_hi.gauge()
         gl = U_lo.gauge() if U_lo is not None else None
         flt, keep = self._filter(b, alpha)
-        opts = SolverOpts(inner_prec, reliable_delta, 16, force_prec, f64_emul)
+        opts = SolverOpts(inner_prec, reliable_delta, 16, force_prec, f64_emul, solver)
         stats = SolveStats()
         st = lib().hmc_force_pf(self.h, _ref(lattice(L)), ctypes.byref(gh),
                                 ctypes.byref(gl) if gl is not None else None, phi.ptr(), kappa,
@@ -426,12 +448,12 @@ class Context:
         return {"iterations": stats.iterations, "true_rel_res": stats.true_rel_res}
 
     def action_pf(self, L, U_hi, phi, kappa, tol=1e-13, U_lo=None, inner_prec=F64, b=None,
-                  alpha=0.0, f64_emul=0):
+                  alpha=0.0, f64_emul=0, solver=SOLVER_CG):
         self._stream()
         gh = U_hi.gauge()
         gl = U_lo.gauge() if U_lo is not None else None
         flt, keep = self._filter(b, alpha)
-        opts = SolverOpts(inner_prec, 0.1, 16, F64, f64_emul)
+        opts = SolverOpts(inner_prec, 0.1, 16, F64, f64_emul, solver)
         out = ctypes.c_double(0)
         st = lib().hmc_action_pf(self.h, _ref(lattice(L)), ctypes.byref(gh),
                                  ctypes.byref(gl) if gl is not None else None, phi.ptr(), kappa,
@@ -610,7 +632,8 @@ class Context:
                    n_max=0, b=None, c=None, alpha=0.0, tol_md=1e-10, tol_action=1e-12,
                    inner_prec=F64, link_fmt_lo=LINK12, reliable_delta=0.1, U_end=None,
                    P_end=None, force_prec=F64, kappa_mp=None, integrator=LEAPFROG,
-                   lam=1.0 / 6.0, f64_emul=0, root_polys=None, root_N=0, measure_forces=False):
+                   lam=1.0 / 6.0, f64_emul=0, root_polys=None, root_N=0, measure_forces=False,
+                   solver=SOLVER_CG):
         """One HMC trajectory; U (F64/LINK18 gauge Field) is updated in place
         when accepted.  Returns the result as a dict.  kappa_mp: heavier
         hopping parameters of a mass-preconditioned chain (eta then from
@@ -623,7 +646,7 @@ class Context:
             inner_prec=inner_prec, link_fmt_lo=link_fmt_lo, reliable_delta=reliable_delta,
             force_prec=force_prec, kappa_mp=kappa_mp, integrator=integrator, lam=lam,
             f64_emul=f64_emul, root_polys=root_polys, root_N=root_N,
-            measure_forces=measure_forces)
+            measure_forces=measure_forces, solver=solver)
         res = TrajResult()
         st = lib().hmc_trajectory(self.h, _ref(lattice(L)), U.ptr(), ctypes.byref(prm),
                                   _dp(P.data), eta.ptr(), u, ctypes.byref(res),
@@ -636,12 +659,13 @@ class Context:
                      b=None, c=None, alpha=0.0, tol_md=1e-10, tol_action=1e-12, inner_prec=F64,
                      link_fmt_lo=LINK12, reliable_delta=0.1, force_prec=F64, kappa_mp=None,
                      integrator=LEAPFROG, lam=1.0 / 6.0, f64_emul=0, root_polys=None, root_N=0,
-                     measure_forces=False):
+                     measure_forces=False, solver=SOLVER_CG):
         """hmc_traj_params; arrays it points to are appended to keep."""
         prm = TrajParams(beta=beta, kappa=kappa, tau=tau, n_md=n_md, n_gauge=n_gauge,
                          filter_k=filter_k, n_t=n_t, n_max=n_max, alpha=alpha, tol_md=tol_md,
                          tol_action=tol_action,
-                         solver=SolverOpts(inner_prec, reliable_delta, 16, force_prec, f64_emul),
+                         solver=SolverOpts(inner_prec, reliable_delta, 16, force_prec, f64_emul,
+                                           solver),
                          link_fmt_lo=link_fmt_lo, integrator=integrator, lam=lam,
                          measure_forces=int(bool(measure_forces)))
         self._mp(prm, kappa_mp, keep)
@@ -715,14 +739,16 @@ class Context:
     def md_evolve(self, L, U, P, phi, beta, kappa, tau, n_md, n_gauge, filter_k=0, n_t=0,
                   b=None, alpha=0.0, tol_md=1e-10, inner_prec=F64, link_fmt_lo=LINK12,
                   reliable_delta=0.1, force_prec=F64, kappa_mp=None, integrator=LEAPFROG,
-                  lam=1.0 / 6.0, f64_emul=0, root_polys=None, root_N=0, measure_forces=False):
+                  lam=1.0 / 6.0, f64_emul=0, root_polys=None, root_N=0, measure_forces=False,
+                  solver=SOLVER_CG):
         """Molecular dynamics with phi fixed; U (F64/LINK18) and P updated in place."""
         self._stream()
         keep = []
         prm = TrajParams(beta=beta, kappa=kappa, tau=tau, n_md=n_md, n_gauge=n_gauge,
                          filter_k=filter_k, n_t=n_t, n_max=n_t, alpha=alpha, tol_md=tol_md,
                          tol_action=tol_md,
-                         solver=SolverOpts(inner_prec, reliable_delta, 16, force_prec, f64_emul),
+                         solver=SolverOpts(inner_prec, reliable_delta, 16, force_prec, f64_emul,
+                                           solver),
                          link_fmt_lo=link_fmt_lo, integrator=integrator, lam=lam,
                          measure_forces=int(bool(measure_forces)))
         self._mp(prm, kappa_mp, keep)
