@@ -321,32 +321,14 @@ def run_hmc(args):
     import torch
     from paper_1805_03560_gb300 import hmc
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1805_03560_gb300.replicas import Replicas
+
+    # replicas only: one independent chain per GPU, no collective on the data
+    # path; barrier, max-over-ranks time and summed work for the measurement
+    rep = Replicas("nccl")
+    world, rank, local = rep.world, rep.rank, rep.local
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def allmax(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def allsum(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    barrier, allmax, allsum = rep.barrier, rep.allmax, rep.allsum
 
     inner = hmc.F16 if args.inner == "f16" else hmc.F32
     ctx = hmc.Context(local)
@@ -584,8 +566,7 @@ def run_hmc(args):
         if not args.no_cpu:
             out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    rep.close()
 
 
 def oracle_dslash_sample(n_apply):
