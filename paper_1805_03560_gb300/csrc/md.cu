@@ -165,12 +165,59 @@ __global__ void __launch_bounds__(128) k_update_links(Geo g, void *gauge, const 
 }
 
 // ---- emulated-FP64 link update ---------------------------------------------
-// The same Cayley-Hamilton exponential and product exp(eps Pi) U in
-// double-float arithmetic (hmc_internal.cuh, about 48 significant bits) on
-// the FP32 units, then the projection back onto SU(3) in native FP64.  The
-// series is summed until its terms fall below 2^-50 of the leading
+// The same Cayley-Hamilton exponential, product exp(eps Pi) U and projection
+// back onto SU(3) in double-float arithmetic (hmc_internal.cuh, about 48
+// significant bits) on the FP32 units; native FP64 only converts the stored
+// link and momenta (the FP64 units of this GPU are the bottleneck otherwise).
+// The series is summed until its terms fall below 2^-50 of the leading
 // coefficient (the precision of the arithmetic).
 using E = Cx<df64>;
+
+// (i/2) sum_a p_a lambda_a, scaled by eps, in double-float
+__device__ __forceinline__ void algebra_matrix_e(const double p[8], double eps, E A[9]) {
+  df64 q[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) q[a] = df64(p[a]);
+  const df64 h(0.5 * eps), r3(0.57735026918962576451), z(0.f);
+  const df64 s = q[7] * r3;
+  A[0] = {z, h * (q[2] + s)};
+  A[4] = {z, h * (s - q[2])};
+  A[8] = {z, -(h * (s + s))};
+  A[1] = {h * q[1], h * q[0]};
+  A[3] = {-(h * q[1]), h * q[0]};
+  A[2] = {h * q[4], h * q[3]};
+  A[6] = {-(h * q[4]), h * q[3]};
+  A[5] = {h * q[6], h * q[5]};
+  A[7] = {-(h * q[6]), h * q[5]};
+}
+
+// a^{-1/2} in double-float: the FP32 estimate refined by two Newton-Raphson
+// steps y <- y + y (1 - a y^2) / 2 (each doubles the correct bits, up to the
+// precision of the arithmetic)
+__device__ __forceinline__ df64 rsqrt_e(df64 a) {
+  df64 y(rsqrtf(a.hi));
+  const df64 one(1.f), half(0.5f);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) y = y + y * (half * (one - a * (y * y)));
+  return y;
+}
+
+// Gram-Schmidt on the first two rows, third row conj(row0 x row1): the
+// same projection as reunitarise, in double-float
+__device__ __forceinline__ void reunitarise_e(E u[9]) {
+  const df64 n0 = rsqrt_e(norm2(u[0]) + norm2(u[1]) + norm2(u[2]));
+#pragma unroll
+  for (int j = 0; j < 3; ++j) u[j] = {n0 * u[j].re, n0 * u[j].im};
+  E d = cjmul(u[0], u[3]);
+  d = fmacj(d, u[1], u[4]);
+  d = fmacj(d, u[2], u[5]);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) u[3 + j] = u[3 + j] - d * u[j];
+  const df64 n1 = rsqrt_e(norm2(u[3]) + norm2(u[4]) + norm2(u[5]));
+#pragma unroll
+  for (int j = 0; j < 3; ++j) u[3 + j] = {n1 * u[3 + j].re, n1 * u[3 + j].im};
+  reconstruct_row2(u);
+}
 
 __device__ __forceinline__ void mm_e(const E a[9], const E b[9], E c[9]) {
 #pragma unroll
@@ -253,20 +300,18 @@ __global__ void __launch_bounds__(128) k_update_links_e(Geo g, void *gauge, cons
   double p[8];
 #pragma unroll
   for (int a = 0; a < 8; ++a) p[a] = P[((size_t)pm * 8 + a) * g.Vh + h];
-  C A[9], u[9];
-  algebra_matrix(p, eps, A);
+  C u[9];
   E Ae[9], Ee[9], ue[9], we[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) Ae[k] = {df64(A[k].re), df64(A[k].im)};
+  algebra_matrix_e(p, eps, Ae);
   expm_su3_e(Ae, Ee);
   void *base = (char *)gauge + (size_t)pm * 9 * g.Vh * 16;
   LinkIO<HMC_F64, 18>::load(base, g.Vh, h, u);
 #pragma unroll
   for (int k = 0; k < 9; ++k) ue[k] = {df64(u[k].re), df64(u[k].im)};
   mm_e(Ee, ue, we);
+  reunitarise_e(we);
 #pragma unroll
   for (int k = 0; k < 9; ++k) u[k] = {(double)we[k].re, (double)we[k].im};
-  reunitarise(u);
   LinkIO<HMC_F64, 18>::store(base, g.Vh, h, u);
 }
 
