@@ -673,40 +673,10 @@ def run_md_report(args):
 
 
 def quenched_hmc(ctx, L, Ud, beta, n_traj, n_steps, seed):
-    """Pure-gauge HMC (leapfrog, tau = 1) driven through the C ABI: gauge
-    force, momentum and link updates, Wilson action.  Relaxes the synthetic
-    start towards an equilibrium gauge field: the first half of the
-    trajectories are always kept (molecular-dynamics relaxation from a start
-    far from equilibrium), the second half pass a Metropolis test on the
-    host, whose acceptance rate is returned."""
-    import numpy as np
-    from paper_1805_03560_gb300 import hmc
-    from paper_1805_03560_gb300 import inputs as I
-    rng = np.random.default_rng(seed)
-    F = ctx.new_algebra(L)
-    Ub = ctx.new_gauge(L, hmc.F64, hmc.LINK18)
-    dt = 1.0 / n_steps
-    acc = 0
-    for t in range(n_traj):
-        P = ctx.pack_algebra(L, I.momenta(L, seed + 1000 + t))
-        Ub.data.copy_(Ud.data)
-        H0 = ctx.kinetic(L, P) + ctx.force_hopexp(L, Ud, beta, 0.0, 0)
-        F.data.zero_()
-        ctx.force_hopexp(L, Ud, beta, 0.0, 0, F=F, want_action=False)
-        ctx.update_momenta(L, P, F, 0.5 * dt)
-        for s in range(n_steps):
-            ctx.update_links(L, Ud, P, dt)
-            F.data.zero_()
-            ctx.force_hopexp(L, Ud, beta, 0.0, 0, F=F, want_action=False)
-            ctx.update_momenta(L, P, F, dt if s + 1 < n_steps else 0.5 * dt)
-        H1 = ctx.kinetic(L, P) + ctx.force_hopexp(L, Ud, beta, 0.0, 0)
-        if t < n_traj // 2:
-            continue
-        if rng.uniform() < np.exp(min(0.0, -(H1 - H0))):
-            acc += 1
-        else:
-            Ud.data.copy_(Ub.data)
-    return acc / max(n_traj - n_traj // 2, 1), ctx.plaquette(L, Ud)
+    """Relax the synthetic start by pure-gauge HMC (the package's runner
+    does the same before a production chain)."""
+    from paper_1805_03560_gb300.run import relax_pure_gauge
+    return relax_pure_gauge(ctx, L, Ud, beta, n_traj, n_steps, seed)
 
 
 def run_thermal_report(args):

@@ -1,0 +1,69 @@
+"""The production runner's run file (host side, no GPU): validation and the
+trajectory arguments it builds, coefficients from the library's host code
+checked against the oracle's exact series."""
+import json
+
+import numpy as np
+import pytest
+
+from oracle import coeffs as C
+from paper_1805_03560_gb300 import run
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_1805_03560_gb300 import build, hmc
+    build.build()
+    return hmc
+
+
+BASE = {"lattice": [8, 4, 4, 4], "beta": 5.6, "kappa": 0.156}
+
+
+def test_defaults_and_round_trip(tmp_path):
+    p = tmp_path / "run.json"
+    p.write_text(json.dumps(BASE))
+    cfg = run.load_config(str(p))
+    assert cfg["integrator"]["type"] == "leapfrog" and cfg["solver"]["type"] == "cg"
+    assert cfg["chain"]["block"] == 10 and cfg["start"]["eps"] == 0.3
+    assert run.load_config(cfg) == cfg  # idempotent
+
+
+@pytest.mark.parametrize("bad", [
+    {"lattice": [8, 4, 4, 3]}, {"lattice": [8, 4, 4]}, {"extra": 1},
+    {"integrator": {"type": "rk4"}}, {"solver": {"type": "gmres"}}, {"solver": {"inner": "bf16"}},
+    {"action": {"mass_preconditioning": [0.15], "filter_k": 2}}, {"action": {"roots": 2}},
+    {"chain": {"block": 0}}])
+def test_rejected(bad):
+    with pytest.raises(ValueError):
+        run.load_config({**BASE, **bad})
+    with pytest.raises(ValueError):
+        run.load_config({"beta": 5.6, "kappa": 0.15})
+
+
+def test_filtered_kwargs(H):
+    cfg = run.load_config({**BASE, "action": {"filter_k": 2, "n_t": 9, "n_max": 29},
+                           "integrator": {"type": "omelyan", "n_md": 20},
+                           "solver": {"type": "bicgstab", "inner": "f16"}})
+    kw = run.traj_kwargs(cfg, H)
+    assert kw["integrator"] == H.OMELYAN and kw["n_md"] == 20 and abs(kw["lam"] - 1 / 6) < 1e-15
+    assert kw["solver"] == H.SOLVER_BICGSTAB and kw["inner_prec"] == H.F16
+    b, alpha, _ = C.filter_coeffs(2, 29)
+    assert np.allclose(kw["b"], b, rtol=1e-14, atol=1e-300) and abs(kw["alpha"] - alpha) < 1e-15
+    assert np.allclose(kw["c"], C.heatbath_coeffs(2, 29), rtol=1e-14, atol=1e-300)
+    assert kw["n_t"] == 9 and kw["n_max"] == 29 and kw["filter_k"] == 2
+
+
+def test_rooted_and_mp_kwargs(H):
+    cfg = run.load_config({**BASE, "action": {"rooted": {"N": 2, "degrees": [6, 12], "n_b": 20,
+                                                         "n_t": 10, "filter_k": 2}}})
+    kw = run.traj_kwargs(cfg, H)
+    alpha, b, polys = C.rooted_coeffs(2, 2, (6, 12), 20)
+    assert kw["root_N"] == 2 and [len(p) for p in kw["root_polys"]] == [7, 13]
+    for got, want in zip(kw["root_polys"], polys):
+        # long-double residue (~1e-20) where the exact coefficient vanishes
+        assert np.allclose(got, want, rtol=1e-13, atol=1e-16)
+    assert abs(kw["alpha"] - alpha) <= 1e-13 * abs(alpha)
+    cfg = run.load_config({**BASE, "action": {"mass_preconditioning": [0.150, 0.154]}})
+    kw = run.traj_kwargs(cfg, H)
+    assert kw["kappa_mp"] == [0.150, 0.154] and "b" not in kw
