@@ -44,3 +44,22 @@ def test_resume_reproduces_run(H, tmp_path):
     lines = (tmp_path / "whole.jsonl").read_text().splitlines()
     assert len(lines) == 4 and json.loads(lines[3])["trajectory"] == 3
     assert s_all["n"] == 4 and "acceptance_erfc" in s_all
+
+
+def test_relaxed_start(H):
+    """Pure-gauge HMC relaxation from the synthetic start (plaquette ~0.78 at
+    eps 0.3) moves the plaquette towards its beta 5.85 equilibrium (~0.58)."""
+    from paper_1805_03560_gb300 import inputs as I
+    from paper_1805_03560_gb300 import run
+    L = (4, 4, 4, 4)
+    ctx = H.Context(0)
+    U = ctx.pack_gauge(L, I.gauge_links(L, 0.3, 1), H.F64, H.LINK18)
+    p0 = ctx.plaquette(L, U)
+    acc, p1 = run.relax_pure_gauge(ctx, L, U, 5.85, 6, 20, 11)
+    assert p0 > 0.75 and p1 < p0 - 0.05 and 0.0 <= acc <= 1.0
+    res, summ = run.run({"lattice": list(L), "beta": 5.6, "kappa": 0.12,
+                         "start": {"eps": 0.3, "seed": 1,
+                                   "relax": {"beta": 5.85, "trajectories": 6}},
+                         "integrator": {"tau": 0.5, "n_md": 4, "n_gauge": 2},
+                         "chain": {"seed": 1, "n_traj": 1, "block": 1}}, log=lambda m: None)
+    assert len(res) == 1 and summ["n"] == 1
