@@ -233,7 +233,10 @@ typedef struct {
                             terms) run in emulated FP64 (HMC_F64E, about 48
                             significant bits) on an F64E copy of U_hi made
                             per call; needs U_hi in LINK18 (otherwise
-                            native FP64 is used).  0: native FP64. */
+                            native FP64 is used).  In trajectories it also
+                            selects the emulated-FP64 link update
+                            (exponential, product and SU(3) projection in
+                            double-float).  0: native FP64. */
   int solver;            /* solves of Mhat^dag Mhat inside forces, actions
                             and trajectories: HMC_SOLVER_CG (default) or
                             HMC_SOLVER_BICGSTAB (two BiCGstab solves,
@@ -533,7 +536,8 @@ typedef struct {
  * params->solver.force_prec == HMC_F32 computes the molecular-dynamics forces
  * (gauge force on an F32 copy of the links, pseudo-fermion outer products and
  * filter polynomials) in FP32 with FP64 accumulation; the heatbath, the
- * actions of H0 and H1 and the link updates stay FP64.  With
+ * actions of H0 and H1 and the link updates stay FP64-accurate (native, or
+ * emulated with solver.f64_emul).  With
  * params->n_mp > 0, eta holds n_mp + 1 consecutive F64 even fields and the
  * heatbath is phi_j = Mhat_b^dag Mhat_a^{-dag} eta_j (hmc_heatbath_mp).
  * Blocks; *res is filled on the host. */
