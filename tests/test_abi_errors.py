@@ -83,3 +83,31 @@ def test_host_entry_points_reject_bad_arguments(H):
     assert lib.hmc_checkpoint_write(None, b"/tmp/never-written.ckpt", ctypes.byref(bad),
                                     buf) == H.EINVAL
     assert not os.path.exists("/tmp/never-written.ckpt")
+
+
+def test_coefficient_entry_points_validate(H):
+    import numpy as np
+    lib = H.lib()
+    b = np.zeros(64)
+    a = ctypes.c_double(0)
+    P = ctypes.c_void_p
+    for k, n in ((-1, 4), (9, 4), (2, -1), (2, 5000)):
+        assert lib.hmc_filter_coeffs(k, n, b.ctypes.data_as(P), ctypes.byref(a), None) == H.EINVAL
+    assert lib.hmc_filter_coeffs(2, 4, None, ctypes.byref(a), None) == H.EINVAL
+    assert lib.hmc_filter_coeffs(2, 4, b.ctypes.data_as(P), ctypes.byref(a), None) == H.OK
+    deg = np.array([4, 8], dtype=np.int32)
+    polys = np.zeros(64)
+    good = (2, 2, 2, deg.ctypes.data_as(P), 10, ctypes.byref(a), b.ctypes.data_as(P),
+            polys.ctypes.data_as(P))
+    assert lib.hmc_rooted_coeffs(*good) == H.OK
+    for pos, val in ((1, 0), (2, 0), (2, 9), (0, 9)):  # N = 0, levels 0 and 9, k = 9
+        args = list(good)
+        args[pos] = val
+        assert lib.hmc_rooted_coeffs(*args) == H.EINVAL, (pos, val)
+    neg = np.array([4, -1], dtype=np.int32)
+    args = list(good)
+    args[3] = neg.ctypes.data_as(P)
+    assert lib.hmc_rooted_coeffs(*args) == H.EINVAL
+    args = list(good)
+    args[4] = -1
+    assert lib.hmc_rooted_coeffs(*args) == H.EINVAL

@@ -69,3 +69,12 @@ def test_write_jsonl(tmp_path):
     metrics.write_jsonl(p, [{"dH": 0.1, "accepted": 1}], extra={"beta": 5.6})
     rec = json.loads(p.read_text().strip())
     assert rec == {"dH": 0.1, "accepted": 1, "beta": 5.6, "index": 0}
+
+
+def test_summarize_edge_cases():
+    assert metrics.summarize([]) == {"n": 0}
+    one = dict(dH=0.3, accepted=1, plaq0=0.5, plaq1=0.6, cg_iterations=7)
+    s = metrics.summarize([one])
+    assert s["n"] == 1 and s["var_dH"] == 0.0 and s["acceptance_erfc"] == 1.0
+    assert abs(s["acceptance"] - math.exp(-0.3)) < 1e-15 and s["plaquette"] == 0.6
+    assert math.isnan(s["acceptance_err"]) and "force_pf2_mean" not in s
