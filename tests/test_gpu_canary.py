@@ -158,3 +158,20 @@ def test_random_fields_link_update_trajectory(ctx, H, L):
                    inner_prec=H.F32, reliable_delta=1e-3, f64_emul=1, **kw)
     ctx.torch.cuda.synchronize()
     assert cU.intact() and cUe.intact() and cPe.intact()
+
+
+@pytest.mark.parametrize("L", LATTICES)
+def test_batched_cg_and_ratio_terms(ctx, H, L):
+    U = I.gauge_links(L, 0.3, 1)
+    Uh = ctx.pack_gauge(L, U, H.F64, 18)
+    Ul = ctx.pack_gauge(L, U, H.F32, 12)
+    phi3 = ctx.pack_spinor(L, I.gaussian_half(L, 2, n_rhs=3), H.F64)
+    cx, x = _spinor(ctx, H, L, H.F64, 3)
+    ctx.cg_solve_multi(L, Uh, x, phi3, [0.12, 0.13, 0.14], 1e-10, U_lo=Ul, inner_prec=H.F32,
+                       reliable_delta=1e-3)
+    phis = ctx.pack_spinors(L, [I.gaussian_half(L, 30 + j) for j in range(3)])
+    cF, F = _algebra(ctx, H, L)
+    ctx.force_mp(L, Uh, phis, [0.0, 0.12, 0.13], [0.12, 0.13, 0.14], F, tol=1e-10, U_lo=Ul,
+                 inner_prec=H.F32, reliable_delta=1e-3)
+    ctx.torch.cuda.synchronize()
+    assert cx.intact() and cF.intact()

@@ -84,6 +84,27 @@ def test_chain_matches_oracle(orc, ctx, H):
     assert np.abs(_np(ctx.unpack_gauge(L, Ud)) - Uo).max() <= 1e-10
 
 
+def test_mass_preconditioned_chain_matches_oracle(orc, ctx, H):
+    """Three pseudo-fermion fields per trajectory (kappa' = 0.150, 0.154 and
+    the target 0.1575): the chain draws them as consecutive source fields."""
+    L = (4, 4, 4, 4)
+    U = I.gauge_links(L, 0.3, 1)
+    kw = dict(beta=5.6, kappa=0.1575, tau=0.5, n_md=4, n_gauge=2, kappa_mp=[0.150, 0.154])
+    seed, c0, n = 5, 2, 2
+    Ud = ctx.pack_gauge(L, U, 0, 18)
+    res = ctx.chain(L, Ud, n, seed, counter0=c0, tol_md=1e-13, tol_action=1e-14, **kw)
+    Uo = U
+    for t in range(n):
+        c = c0 + t
+        P = orc.random_momenta(L, seed, c)
+        eta = orc.random_sources(L, 3, seed, c)
+        u = orc.metropolis_uniform(seed, c)
+        Uo, ro, _, _ = orc.trajectory(L, Uo, P, eta, u, tol_md=1e-13, tol_action=1e-14, **kw)
+        assert abs(res[t]["dH"] - ro["dH"]) <= 1e-7
+        assert res[t]["accepted"] == ro["accepted"]
+    assert np.abs(_np(ctx.unpack_gauge(L, Ud)) - Uo).max() <= 1e-9
+
+
 def test_checkpoint_resume_bit_identical(ctx, H, tmp_path):
     L = (4, 4, 4, 6)
     U = I.gauge_links(L, 0.3, 2)
