@@ -67,3 +67,54 @@ def test_rooted_and_mp_kwargs(H):
     cfg = run.load_config({**BASE, "action": {"mass_preconditioning": [0.150, 0.154]}})
     kw = run.traj_kwargs(cfg, H)
     assert kw["kappa_mp"] == [0.150, 0.154] and "b" not in kw
+
+
+class _FakeCtx:
+    """Stands in for hmc.Context: records the chain blocks and checkpoints."""
+
+    calls = []
+
+    def __init__(self, device=0):
+        self.saved = None
+
+    def pack_gauge(self, L, U, prec, fmt):
+        return ("U", tuple(L))
+
+    def plaquette(self, L, U):
+        return 0.5
+
+    def load_checkpoint(self, path):
+        _FakeCtx.calls.append(("load", path))
+        return {"L": [8, 4, 4, 4], "rng_counter": 7, "trajectory": 7, "plaquette": 0.5}, ("U", 0)
+
+    def chain(self, L, U, n, seed, counter0=0, spike_threshold=0.0, **kw):
+        _FakeCtx.calls.append(("chain", n, seed, counter0, spike_threshold, kw["kappa"]))
+        return [dict(dH=0.01 * (counter0 + i), accepted=1, plaq0=0.5, plaq1=0.5,
+                     cg_iterations=10, spike=0, n_f_pf=0, n_f_g=0, f_pf2_sum=0.0, f_pf2_sq=0.0,
+                     f_g2_sum=0.0, f_g2_sq=0.0) for i in range(n)]
+
+    def save_checkpoint(self, path, L, U, beta, kappa, seed, trajectory, rng_counter):
+        _FakeCtx.calls.append(("save", path, trajectory, rng_counter))
+
+
+def test_runner_blocks_counters_and_resume(H, monkeypatch, tmp_path):
+    monkeypatch.setattr(H, "Context", _FakeCtx)
+    _FakeCtx.calls = []
+    cfg = {**BASE, "chain": {"seed": 4, "n_traj": 5, "block": 2, "spike_threshold": 3.0},
+           "output": {"checkpoint": str(tmp_path / "c.ckpt"), "jsonl": str(tmp_path / "r.jsonl")}}
+    res, summ = run.run(cfg, log=lambda m: None)
+    chains = [c for c in _FakeCtx.calls if c[0] == "chain"]
+    assert [(c[1], c[3]) for c in chains] == [(2, 0), (2, 2), (1, 4)]
+    assert all(c[2] == 4 and c[4] == 3.0 and c[5] == 0.156 for c in chains)
+    saves = [c for c in _FakeCtx.calls if c[0] == "save"]
+    assert [(s[2], s[3]) for s in saves] == [(2, 2), (4, 4), (5, 5)]
+    lines = [json.loads(l) for l in (tmp_path / "r.jsonl").read_text().splitlines()]
+    assert [l["trajectory"] for l in lines] == [0, 1, 2, 3, 4]
+    assert summ["n"] == 5 and [r["trajectory"] for r in res] == [0, 1, 2, 3, 4]
+    # resume: the counter continues from the checkpoint
+    _FakeCtx.calls = []
+    run.run({**BASE, "start": {"checkpoint": "x.ckpt"}, "chain": {"seed": 4, "n_traj": 3,
+                                                                  "block": 3}},
+            log=lambda m: None)
+    assert _FakeCtx.calls[0] == ("load", "x.ckpt")
+    assert [(c[1], c[3]) for c in _FakeCtx.calls if c[0] == "chain"] == [(3, 7)]
