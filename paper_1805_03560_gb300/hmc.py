@@ -224,6 +224,7 @@ class Context:
         self.h = h
 
     def close(self):
+        """Destroy the library context (its workspace and streams)."""
         if getattr(self, "h", None):
             lib().hmc_ctx_destroy(self.h)
             self.h = None
@@ -245,9 +246,12 @@ class Context:
             raise HmcError(st, f"{what}: {msg}")
 
     def launches(self):
+        """Number of kernels this context has launched so far."""
         return lib().hmc_launch_count(self.h)
 
     def set_dslash_variant(self, v):
+        """Hemi-Dslash kernel variant: 0..3 fixed, -1 built-in default, -2 autotuned per launch
+        class."""
         self._check(lib().hmc_ctx_set_option(self.h, 1, int(v)), "hmc_ctx_set_option")
 
     def set_cg_graph(self, on):
@@ -255,6 +259,7 @@ class Context:
         self._check(lib().hmc_ctx_set_option(self.h, 2, int(bool(on))), "hmc_ctx_set_option")
 
     def set_timing(self, enable):
+        """Per-launch timing: 0 off, 1 event-timed Dslash classes, 2 timeline of every launch."""
         self._check(lib().hmc_ctx_set_timing(self.h, int(enable)), "hmc_ctx_set_timing")
 
     def timing(self):
@@ -277,14 +282,17 @@ class Context:
 
     # ---- allocation ---------------------------------------------------------
     def new_spinor(self, L, prec, n_rhs=1):
+        """Uninitialised half-spinor field of precision prec, n_rhs right-hand sides."""
         n = lib().hmc_spinor_bytes(_ref(lattice(L)), prec, n_rhs)
         return Field(self._bytes(n), "spinor", prec, n_rhs)
 
     def new_gauge(self, L, prec, fmt):
+        """Uninitialised gauge field of precision prec and link format fmt (LINK18 or LINK12)."""
         n = lib().hmc_gauge_bytes(_ref(lattice(L)), prec, fmt)
         return Field(self._bytes(n), "gauge", prec, fmt=fmt)
 
     def new_algebra(self, L):
+        """Zeroed algebra field (momenta or forces: 8 FP64 components per link)."""
         n = lib().hmc_algebra_bytes(_ref(lattice(L)))
         t = self.torch.zeros(int(n) // 8, dtype=self.torch.float64, device=f"cuda:{self.device}")
         return Field(t, "algebra", F64)
@@ -297,6 +305,7 @@ class Context:
         return t.to(dtype=self.torch.float64, device=f"cuda:{self.device}").contiguous()
 
     def pack_gauge(self, L, U, prec=F64, fmt=LINK18):
+        """Device gauge field from canonical links complex [V, 4, 3, 3] (sites t, x, y, z)."""
         self._stream()
         Uc = self._canon(U)
         f = self.new_gauge(L, prec, fmt)
@@ -305,6 +314,7 @@ class Context:
         return f
 
     def unpack_gauge(self, L, f):
+        """Canonical links complex128 [V, 4, 3, 3] of a device gauge field (on the device)."""
         self._stream()
         V = int(np.prod(L))
         out = self.torch.empty((V, 4, 3, 3, 2), dtype=self.torch.float64, device=f"cuda:{self.device}")
@@ -323,6 +333,7 @@ class Context:
         return f
 
     def unpack_spinor(self, L, f):
+        """Canonical half spinor complex128 [Vh, 4, 3] (or [n_rhs, Vh, 4, 3]) of a device field."""
         self._stream()
         Vh = int(np.prod(L)) // 2
         shape = (Vh, 4, 3, 2) if f.n_rhs == 1 else (f.n_rhs, Vh, 4, 3, 2)
@@ -332,6 +343,7 @@ class Context:
         return self.torch.view_as_complex(out)
 
     def pack_algebra(self, L, A):
+        """Device algebra field from canonical float64 [V, 4, 8] components."""
         self._stream()
         c = self._canon(A)
         f = self.new_algebra(L)
@@ -340,6 +352,7 @@ class Context:
         return f
 
     def unpack_algebra(self, L, f):
+        """Canonical float64 [V, 4, 8] components of a device algebra field."""
         self._stream()
         V = int(np.prod(L))
         out = self.torch.empty((V, 4, 8), dtype=self.torch.float64, device=f"cuda:{self.device}")
@@ -349,6 +362,7 @@ class Context:
 
     # ---- operators ---------------------------------------------------------------
     def dslash(self, L, U, out, inp, out_parity, dagger=False):
+        """out (parity out_parity) = H_{p,1-p} inp, or gamma_5 H gamma_5 with dagger."""
         self._stream()
         g = U.gauge()
         st = lib().hmc_dslash(self.h, _ref(lattice(L)), ctypes.byref(g), out.ptr(), inp.ptr(),
@@ -357,6 +371,8 @@ class Context:
         return out
 
     def mhat(self, L, U, out, inp, kappa, dagger=False, kappas=None):
+        """out = Mhat inp = inp - kappa^2 H_eo H_oe inp (or Mhat^dag); kappas: one per right-hand
+        side."""
         self._stream()
         g = U.gauge()
         ks = None
@@ -387,6 +403,8 @@ class Context:
 
     def cg_solve(self, L, U_hi, x, phi, kappa, tol, max_iter=10000, U_lo=None, inner_prec=F64,
                  reliable_delta=0.1, check_every=16, f64_emul=0):
+        """x = (Mhat^dag Mhat)^{-1} phi to the true relative residual tol (hmc_cg_solve); returns
+        the statistics."""
         self._stream()
         gh = U_hi.gauge()
         gl = U_lo.gauge() if U_lo is not None else None
@@ -449,6 +467,8 @@ class Context:
 
     def action_pf(self, L, U_hi, phi, kappa, tol=1e-13, U_lo=None, inner_prec=F64, b=None,
                   alpha=0.0, f64_emul=0, solver=SOLVER_CG):
+        """Pseudo-fermion action: plain phi^dag (Mhat^dag Mhat)^{-1} phi, or the filtered |(alpha
+        Mhat^{-1} + sum b_n K^n) phi|^2 when b is given."""
         self._stream()
         gh = U_hi.gauge()
         gl = U_lo.gauge() if U_lo is not None else None
@@ -463,6 +483,8 @@ class Context:
         return out.value
 
     def force_hopexp(self, L, U, beta, kappa, k, F=None, coeff=1.0, want_action=True):
+        """Gauge action with the kappa^k hopping-expansion term (returned) and, when F is given, F
+        += coeff * its force."""
         self._stream()
         g = U.gauge()
         act = ctypes.c_double(0)
@@ -473,6 +495,7 @@ class Context:
         return act.value
 
     def plaquette(self, L, U):
+        """Average plaquette Re Tr U_p / 3 of a gauge field."""
         self._stream()
         g = U.gauge()
         out = ctypes.c_double(0)
@@ -529,6 +552,7 @@ class Context:
         return out
 
     def unpack_spinors(self, L, f):
+        """The consecutive F64 fields of pack_spinors, stacked as complex128 [n, Vh, 4, 3]."""
         nb = int(lib().hmc_spinor_bytes(_ref(lattice(L)), F64, 1))
         res = []
         for j in range(f.data.numel() // nb):
@@ -560,6 +584,8 @@ class Context:
         return {f: getattr(stats, f) for f, _ in SolveStats._fields_}
 
     def action_mp(self, L, U_hi, phis, kappa_a, kappa_b, tol=1e-13, U_lo=None, inner_prec=F64, f64_emul=0):
+        """Sum of the ratio actions |Mhat(ka_j)^dag Mhat(kb_j)^{-dag} phi_j|^2 (mass
+        preconditioning)."""
         self._stream()
         keep = []
         n, ka, kb = self._mp_args(kappa_a, kappa_b, keep)
@@ -575,6 +601,8 @@ class Context:
 
     def heatbath_mp(self, L, U_hi, etas, kappa_a, kappa_b, tol=1e-13, U_lo=None,
                     inner_prec=F64, f64_emul=0):
+        """phi_j = Mhat(kb_j)^dag Mhat(ka_j)^{-dag} eta_j, so that each ratio action equals
+        |eta_j|^2."""
         self._stream()
         keep = []
         n, ka, kb = self._mp_args(kappa_a, kappa_b, keep)
@@ -602,6 +630,8 @@ class Context:
         return self.torch.view_as_complex(out)
 
     def poly_apply(self, L, U, out, inp, coeffs, kappa, horner_store=None):
+        """out = sum_i coeffs[i] K^i inp by the Horner scheme; horner_store (optional) keeps the
+        partial sums."""
         self._stream()
         g = U.gauge()
         c = np.ascontiguousarray(coeffs, dtype=np.float64)
@@ -612,16 +642,19 @@ class Context:
         return out
 
     def update_links(self, L, U, P, eps):
+        """U <- exp(eps Pi) U with Pi from the algebra field P, reunitarised (native FP64)."""
         self._stream()
         st = lib().hmc_update_links(self.h, _ref(lattice(L)), U.ptr(), _dp(P.data), eps)
         self._check(st, "hmc_update_links")
 
     def update_momenta(self, L, P, F, eps):
+        """P <- P - eps F."""
         self._stream()
         st = lib().hmc_update_momenta(self.h, _ref(lattice(L)), _dp(P.data), _dp(F.data), eps)
         self._check(st, "hmc_update_momenta")
 
     def kinetic(self, L, P):
+        """Kinetic term (1/2)(Pi, Pi) = (1/2) sum_a P_a^2 of an algebra field."""
         self._stream()
         out = ctypes.c_double(0)
         st = lib().hmc_kinetic(self.h, _ref(lattice(L)), _dp(P.data), ctypes.byref(out))
@@ -696,6 +729,7 @@ class Context:
         return out
 
     def random_uniforms(self, n, seed, stream, counter):
+        """n uniforms in (0, 1) of (seed, stream) at the counter (device tensor)."""
         self._stream()
         u = self.torch.empty(n, dtype=self.torch.float64, device=f"cuda:{self.device}")
         st = lib().hmc_random_uniforms(self.h, _dp(u), n, seed, stream, counter)
