@@ -138,6 +138,8 @@ int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
  * before its next work; 0 launches every kernel on the caller's stream.
  * Results are bit-identical.  Graphs are not used while timing is enabled. */
 #define HMC_OPT_CG_GRAPH 2
+/* Sets option (HMC_OPT_DSLASH_VARIANT: -2..3, HMC_OPT_CG_GRAPH: 0 or 1) for
+ * every later call on ctx.  HMC_EINVAL for an unknown option or value. */
 int hmc_ctx_set_option(hmc_ctx *ctx, int option, int value);
 /* Statistics of the index-th kernel class seen since timing was enabled:
  * class name (e.g. "dslash_f16_12/cg"), launches, summed event time in ms and
@@ -148,8 +150,14 @@ int hmc_timing_get(hmc_ctx *ctx, int index, char *name, int name_len,
 
 /* ---- sizes (host-only, no GPU needed) ---------------------------------------- */
 
+/* Bytes of a gauge field (both parities, four directions) in precision prec
+ * and link format fmt; 0 for a lattice with an odd or < 2 extent or an
+ * unsupported precision / format. */
 size_t hmc_gauge_bytes(const hmc_lattice *lat, int prec, int fmt);
+/* Bytes of a half-lattice (one parity) spinor field of precision prec with
+ * n_rhs right-hand sides; 0 as above. */
 size_t hmc_spinor_bytes(const hmc_lattice *lat, int prec, int n_rhs);
+/* Bytes of an algebra field (momenta or forces: 8 doubles per link). */
 size_t hmc_algebra_bytes(const hmc_lattice *lat);
 
 /* ---- layout conversion --------------------------------------------------------
@@ -161,12 +169,21 @@ int hmc_pack_gauge(hmc_ctx *ctx, const hmc_lattice *lat, const double *U_canon,
 /* Inverse of hmc_pack_gauge (LINK12 rebuilds row 2). */
 int hmc_unpack_gauge(hmc_ctx *ctx, const hmc_lattice *lat, const void *U_dev,
                      int prec, int fmt, double *U_canon);
+/* Canonical half spinor (n_rhs fields one after another, each Vh sites in
+ * lexicographic order of their parity x 4 spins x 3 colours of complex
+ * doubles (re, im)) to the device layout of precision prec, right-hand sides
+ * innermost. */
 int hmc_pack_spinor(hmc_ctx *ctx, const hmc_lattice *lat,
                     const double *psi_canon, void *psi_dev, int prec, int n_rhs);
+/* Inverse of hmc_pack_spinor. */
 int hmc_unpack_spinor(hmc_ctx *ctx, const hmc_lattice *lat, const void *psi_dev,
                       int prec, int n_rhs, double *psi_canon);
+/* Canonical algebra field ([V, 4, 8] doubles: site, direction, component a
+ * of Pi = sum_a P_a T_a) to the device layout (per parity, direction and
+ * component, sites innermost). */
 int hmc_pack_algebra(hmc_ctx *ctx, const hmc_lattice *lat, const double *A_canon,
                      double *A_dev);
+/* Inverse of hmc_pack_algebra. */
 int hmc_unpack_algebra(hmc_ctx *ctx, const hmc_lattice *lat, const double *A_dev,
                        double *A_canon);
 

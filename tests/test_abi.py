@@ -109,3 +109,19 @@ def _printed(x, txt):
     some entries and rounds others)."""
     d = len(txt.split(".")[1])
     return f"{x:.{d + 3}f}"[: len(txt)] == txt or abs(x - float(txt)) <= 0.5 * 10.0 ** -d
+
+
+def test_every_declaration_documented():
+    """Each entry point of include/hmc.h carries its own comment block (the
+    passage it implements, layout, ownership, errors), possibly separated
+    from the declaration by #define lines."""
+    src = open(os.path.join(ROOT, "include", "hmc.h")).read()
+    bare = []
+    for m in re.finditer(r"^(?:int|const char \*|long long|size_t|void)\s+(hmc_[a-z0-9_]+)\s*\(",
+                         src, re.M):
+        lines = src[:m.start()].rstrip().split("\n")
+        while lines and lines[-1].startswith("#define"):
+            lines.pop()
+        if not "\n".join(lines).rstrip().endswith("*/"):
+            bare.append(m.group(1))
+    assert not bare, bare
