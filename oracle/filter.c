@@ -42,13 +42,13 @@ double or_filtered_action(const int L[4], const ocplx *U, double kappa,
   ocplx *z = malloc(n12 * sizeof(ocplx)), *y = malloc(n12 * sizeof(ocplx));
   or_poly_K(L, U, kappa, b, n, phi, z);
   or_mhat_inverse(L, U, kappa, phi, y, tol, 100000);
-  double s = 0;
+  or_sum s = {0, 0};
   for (long i = 0; i < n12; ++i) {
     ocplx v = z[i] + alpha * y[i];
-    s += creal(conj(v) * v);
+    or_sum_add(&s, creal(conj(v) * v));
   }
   free(z); free(y);
-  return s;
+  return or_sum_total(&s);
 }
 
 static void join_halves(const int L[4], const ocplx *even, const ocplx *odd,

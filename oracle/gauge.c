@@ -34,7 +34,7 @@ static const ocplx *link(const ocplx *U, long x, int mu) {
 
 double or_plaquette_sum(const int L[4], const ocplx *U) {
   long V = or_volume(L);
-  double sum = 0;
+  or_sum sum = {0, 0};
   for (long x = 0; x < V; ++x)
     for (int mu = 0; mu < 4; ++mu)
       for (int nu = mu + 1; nu < 4; ++nu) {
@@ -46,9 +46,9 @@ double or_plaquette_sum(const int L[4], const ocplx *U) {
         mul3(a, b, a);
         dag3(link(U, x, nu), c);
         mul3(a, c, a);
-        sum += creal(a[0] + a[4] + a[8]);
+        or_sum_add(&sum, creal(a[0] + a[4] + a[8]));
       }
-  return sum;
+  return or_sum_total(&sum);
 }
 
 double or_gauge_action(const int L[4], const ocplx *U, double beta) {
@@ -58,6 +58,8 @@ double or_gauge_action(const int L[4], const ocplx *U, double beta) {
 void or_gauge_force(const int L[4], const ocplx *U, double beta, double coeff,
                     double *F) {
   long V = or_volume(L);
+  /* every (x, mu) writes only its own link's components */
+#pragma omp parallel for schedule(static)
   for (long x = 0; x < V; ++x)
     for (int mu = 0; mu < 4; ++mu) {
       /* staple sum A with S_G = -(beta/3) Re Tr(U_{x,mu} A) + (U-free) */

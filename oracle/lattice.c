@@ -7,6 +7,19 @@
  */
 #include "oracle.h"
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* threads of the parallel site loops (1 without OpenMP) */
+int or_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 long or_volume(const int L[4]) {
   return (long)L[0] * L[1] * L[2] * L[3];
 }

@@ -94,6 +94,7 @@ static void algebra_matrix(const double *p, double eps, ocplx A[9]) {
 
 void or_update_links(const int L[4], ocplx *U, const double *P, double eps) {
   long n = or_volume(L) * 4;
+#pragma omp parallel for schedule(static)
   for (long l = 0; l < n; ++l) {
     ocplx A[9], E[9];
     algebra_matrix(P + l * 8, eps, A);
@@ -114,9 +115,9 @@ void or_rotate_link(const int L[4], ocplx *U, long site, int mu,
 
 double or_kinetic(const int L[4], const double *P) {
   long n = or_volume(L) * 4 * 8;
-  double s = 0;
-  for (long i = 0; i < n; ++i) s += P[i] * P[i];
-  return 0.5 * s;
+  or_sum s = {0, 0};
+  for (long i = 0; i < n; ++i) or_sum_add(&s, P[i] * P[i]);
+  return 0.5 * or_sum_total(&s);
 }
 
 /* hopping parameters (kappa_a, kappa_b) of pseudo-fermion term j of a
@@ -302,19 +303,19 @@ int or_trajectory(const int L[4], ocplx *U, const double *P0, const ocplx *eta,
     H0 = or_hamiltonian(L, U, P, phi, p);
   } else if (p->n_mp > 0) {
     /* phi_j = Mhat_b^dag Mhat_a^{-dag} eta_j: S_j(phi_j) = |eta_j|^2 */
-    double e2 = 0;
+    or_sum e2 = {0, 0};
     for (int j = 0; j < n_terms; ++j) {
       double ka, kb;
       mp_pair(p, j, &ka, &kb);
       or_ratio_heatbath(L, U, ka, kb, eta + j * n12, p->tol_action, phi + j * n12);
     }
-    for (long i = 0; i < n_terms * n12; ++i) e2 += creal(conj(eta[i]) * eta[i]);
-    H0 = or_kinetic(L, P) + or_gauge_action(L, U, p->beta) + e2;
+    for (long i = 0; i < n_terms * n12; ++i) or_sum_add(&e2, creal(conj(eta[i]) * eta[i]));
+    H0 = or_kinetic(L, P) + or_gauge_action(L, U, p->beta) + or_sum_total(&e2);
   } else if (p->filter_k == 0) {
     or_mhat(L, U, p->kappa, 1, eta, phi); /* phi = Mhat^dag eta */
-    double e2 = 0;
-    for (long i = 0; i < n12; ++i) e2 += creal(conj(eta[i]) * eta[i]);
-    H0 = or_kinetic(L, P) + or_gauge_action(L, U, p->beta) + e2;
+    or_sum e2 = {0, 0};
+    for (long i = 0; i < n12; ++i) or_sum_add(&e2, creal(conj(eta[i]) * eta[i]));
+    H0 = or_kinetic(L, P) + or_gauge_action(L, U, p->beta) + or_sum_total(&e2);
   } else {
     ocplx *t = malloc(n12 * sizeof(ocplx));
     or_poly_K(L, U, p->kappa, p->c, p->n_max, eta, t);

@@ -57,11 +57,11 @@ double or_ratio_action(const int L[4], const ocplx *U, double kappa_a,
   ocplx *chi = malloc(n * sizeof(ocplx)), *psi = malloc(n * sizeof(ocplx));
   inv_dag(L, U, kappa_b, phi, tol, chi);
   mhat_or_one(L, U, kappa_a, 1, chi, psi);
-  double s = 0;
-  for (long i = 0; i < n; ++i) s += creal(conj(psi[i]) * psi[i]);
+  or_sum s = {0, 0};
+  for (long i = 0; i < n; ++i) or_sum_add(&s, creal(conj(psi[i]) * psi[i]));
   free(chi);
   free(psi);
-  return s;
+  return or_sum_total(&s);
 }
 
 void or_ratio_heatbath(const int L[4], const ocplx *U, double kappa_a,

@@ -33,7 +33,25 @@
 
 typedef double _Complex ocplx;
 
+/* Compensated summation (Neumaier, ZAMM 54 (1974) 39): the running sum s and
+ * the running correction c of its rounding errors; the total s + c is within
+ * about one rounding of the exact sum whatever the number of terms, so the
+ * Hamiltonian of a large lattice (H ~ 1e7) resolves dH to 1e-7 and better. */
+typedef struct {
+  double s, c;
+} or_sum;
+static inline void or_sum_add(or_sum *a, double x) {
+  double t = a->s + x;
+  if (fabs(a->s) >= fabs(x))
+    a->c += (a->s - t) + x;
+  else
+    a->c += (x - t) + a->s;
+  a->s = t;
+}
+static inline double or_sum_total(const or_sum *a) { return a->s + a->c; }
+
 /* ---- geometry (lattice.c) ------------------------------------------------ */
+int or_threads(void);
 long or_volume(const int L[4]);
 void or_coords(const int L[4], long site, int c[4]);
 long or_site(const int L[4], const int c[4]);

@@ -23,10 +23,10 @@ double or_pf_action(const int L[4], const ocplx *U, double kappa,
   ocplx *X = malloc(n * sizeof(ocplx));
   double rel;
   or_cg(L, U, kappa, phi, X, tol, 100000, &rel);
-  double s = 0;
-  for (long i = 0; i < n; ++i) s += creal(conj(phi[i]) * X[i]);
+  or_sum s = {0, 0};
+  for (long i = 0; i < n; ++i) or_sum_add(&s, creal(conj(phi[i]) * X[i]));
   free(X);
-  return s;
+  return or_sum_total(&s);
 }
 
 /* the 4x4 spin factor of the hop x -> x + dir*mu */
@@ -59,6 +59,8 @@ void or_hop_force(const int L[4], const ocplx *U, double kappa,
     hop_spin(mu, +1, Gf[mu]);
     hop_spin(mu, -1, Gb[mu]);
   }
+  /* every (x, mu) writes only its own link's components */
+#pragma omp parallel for schedule(static)
   for (long x = 0; x < Vol; ++x)
     for (int mu = 0; mu < 4; ++mu) {
       int s;

@@ -68,6 +68,8 @@ static void apply_block_adj(const ocplx G[16], const ocplx C[9], double s,
 void or_hop(const int L[4], const ocplx *U, const ocplx *in, ocplx *out) {
   long V = or_volume(L);
   memset(out, 0, (size_t)V * 12 * sizeof(ocplx));
+  /* output sites are independent: OpenMP only splits the site loop */
+#pragma omp parallel for schedule(static)
   for (long x = 0; x < V; ++x)
     for (int mu = 0; mu < 4; ++mu)
       for (int dir = 1; dir >= -1; dir -= 2) {
@@ -84,6 +86,7 @@ void or_hop_eo(const int L[4], const ocplx *U, int out_parity,
                const ocplx *in, ocplx *out) {
   long Vh = or_volume(L) / 2;
   memset(out, 0, (size_t)Vh * 12 * sizeof(ocplx));
+#pragma omp parallel for schedule(static)
   for (long h = 0; h < Vh; ++h) {
     long x = or_site_of_half(L, out_parity, h);
     for (int mu = 0; mu < 4; ++mu)
@@ -98,22 +101,27 @@ void or_hop_eo(const int L[4], const ocplx *U, int out_parity,
   }
 }
 
-/* out (parity p) = (H_{1-p,p})^dagger in (parity 1-p): scatter the adjoint of
- * every block of the rows of H that belong to parity 1-p */
+/* out (parity p) = (H_{1-p,p})^dagger in (parity 1-p): the adjoint of every
+ * block of the rows of H that belong to parity 1-p.  The block of row x and
+ * column y = x + dir mu sends its adjoint to output site y; for each output
+ * site y the eight rows x = y - dir mu that reach it are gathered (crossing
+ * the time boundary between x and y gives the same sign either way), so
+ * output sites are independent. */
 void or_hop_eo_dag(const int L[4], const ocplx *U, int out_parity,
                    const ocplx *in, ocplx *out) {
   long Vh = or_volume(L) / 2;
   memset(out, 0, (size_t)Vh * 12 * sizeof(ocplx));
+#pragma omp parallel for schedule(static)
   for (long h = 0; h < Vh; ++h) {
-    long x = or_site_of_half(L, 1 - out_parity, h);
+    long y = or_site_of_half(L, out_parity, h);
     for (int mu = 0; mu < 4; ++mu)
       for (int dir = 1; dir >= -1; dir -= 2) {
         int s;
-        long y = or_neighbour(L, x, mu, dir, &s);
+        long x = or_neighbour(L, y, mu, -dir, &s);
         ocplx G[16], C[9];
         hop_spin(mu, dir, G);
         hop_colour(L, U, x, mu, dir, C);
-        apply_block_adj(G, C, s, in + h * 12, out + (y >> 1) * 12);
+        apply_block_adj(G, C, s, in + (x >> 1) * 12, out + h * 12);
       }
   }
 }
