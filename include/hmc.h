@@ -223,7 +223,11 @@ int hmc_mhat(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U,
  * stream capture.  Every call shares the one array and overwrites it
  * completely before reading it, so nothing needs clearing, but calls that
  * overlap on the GPU (other streams, other host threads) race on it.  The
- * context's optional event timing is bypassed for this call. */
+ * context's optional event timing and the Dslash autotuner (option
+ * HMC_OPT_DSLASH_VARIANT = -2) are bypassed for this call: it creates no
+ * events, never synchronises the stream, and an autotuning context runs the
+ * built-in default variant (every variant computes the same result bit for
+ * bit, so the output equals hmc_mhat's). */
 #define HMC_MHAT_NOALLOC_MAX_BYTES ((size_t)64 << 20)
 int hmc_mhat_noalloc(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U,
                      void *out, const void *in, double kappa, int dagger, int prec,
@@ -238,11 +242,15 @@ typedef struct {
                             its maximum since the last update (0: 0.1) */
   int check_every;       /* iterations between host convergence checks
                             (0: 16); does not change the result */
-  int force_prec;        /* hmc_force_pf only: precision of the Dslash
+  int force_prec;        /* forces only: precision of the Dslash
                             applications, filter polynomials and outer
-                            products outside the solves (HMC_F64 or HMC_F32;
-                            the solves always reach tol in FP64).  HMC_F32
-                            needs U_lo in F32 or U_hi in LINK18. */
+                            products outside the solves (the solves always
+                            reach tol in FP64): HMC_F64 (native), HMC_F32
+                            (needs U_lo in F32 or U_hi in LINK18; about 1e-6
+                            relative) or HMC_F64E (emulated FP64 on an F64E
+                            copy of U_hi made per call, about 1e-14
+                            relative).  In trajectories it also selects the
+                            precision of the gauge force. */
   int f64_emul;          /* nonzero: the FP64-accurate operator applications
                             outside the inner solver (true residuals of the
                             reliable updates, heatbath and action
@@ -552,9 +560,10 @@ typedef struct {
  * for the reversibility test of Sec. IV: flip P_end and run back).
  * params->solver.force_prec == HMC_F32 computes the molecular-dynamics forces
  * (gauge force on an F32 copy of the links, pseudo-fermion outer products and
- * filter polynomials) in FP32 with FP64 accumulation; the heatbath, the
- * actions of H0 and H1 and the link updates stay FP64-accurate (native, or
- * emulated with solver.f64_emul).  With
+ * filter polynomials) in FP32 with FP64 accumulation, HMC_F64E in emulated
+ * FP64 (double-float on the FP32 units, on an F64E copy of the links); the
+ * heatbath, the actions of H0 and H1 and the link updates stay FP64-accurate
+ * (native, or emulated with solver.f64_emul).  With
  * params->n_mp > 0, eta holds n_mp + 1 consecutive F64 even fields and the
  * heatbath is phi_j = Mhat_b^dag Mhat_a^{-dag} eta_j (hmc_heatbath_mp).
  * Blocks; *res is filled on the host. */

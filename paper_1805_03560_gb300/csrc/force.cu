@@ -153,8 +153,8 @@ int hop_force(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, const void *We, co
 
 int hop_force_multi(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, int n, const void *const W[][2],
                     const void *const V[][2], double *F, double c, int sprec) {
-  if (sprec != HMC_F64 && sprec != HMC_F32)
-    return fail(ctx, HMC_EINVAL, "force: spinor precision must be F64 or F32");
+  if (sprec != HMC_F64 && sprec != HMC_F32 && sprec != HMC_F64E)
+    return fail(ctx, HMC_EINVAL, "force: spinor precision must be F64, F32 or F64E");
   if (U.prec != sprec)
     return fail(ctx, HMC_EINVAL, "force: gauge precision must match the fields");
   if (n < 1) return HMC_OK;
@@ -179,15 +179,19 @@ int hop_force_multi(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, int n, const
   a.F = F;
   a.c = c;
   int nb = blocks_for(2LL * g.Vh, 128);
-  const bool d = sprec == HMC_F64;
-  if (U.fmt == 18) {
-    if (d) k_hop_force<18, HMC_F64><<<nb, 128, 0, ctx->stream>>>(a);
-    else k_hop_force<18, HMC_F32><<<nb, 128, 0, ctx->stream>>>(a);
-  } else {
-    if (d) k_hop_force<12, HMC_F64><<<nb, 128, 0, ctx->stream>>>(a);
-    else k_hop_force<12, HMC_F32><<<nb, 128, 0, ctx->stream>>>(a);
+  cudaStream_t st = ctx->stream;
+  switch (sprec * 100 + U.fmt) {
+    case HMC_F64 * 100 + 18: k_hop_force<18, HMC_F64><<<nb, 128, 0, st>>>(a); break;
+    case HMC_F64 * 100 + 12: k_hop_force<12, HMC_F64><<<nb, 128, 0, st>>>(a); break;
+    case HMC_F32 * 100 + 18: k_hop_force<18, HMC_F32><<<nb, 128, 0, st>>>(a); break;
+    case HMC_F32 * 100 + 12: k_hop_force<12, HMC_F32><<<nb, 128, 0, st>>>(a); break;
+    // emulated FP64: the outer products and Q = U A - B U^dag in double-float
+    case HMC_F64E * 100 + 18: k_hop_force<18, HMC_F64E><<<nb, 128, 0, st>>>(a); break;
+    case HMC_F64E * 100 + 12: k_hop_force<12, HMC_F64E><<<nb, 128, 0, st>>>(a); break;
+    default: return fail(ctx, HMC_EINVAL, "force: bad link format %d", U.fmt);
   }
-  return launched(ctx, d ? "hop_force_f64" : "hop_force_f32");
+  return launched(ctx, sprec == HMC_F64 ? "hop_force_f64"
+                       : sprec == HMC_F32 ? "hop_force_f32" : "hop_force_f64e");
 }
 
 }  // namespace hmc

@@ -252,9 +252,13 @@ int gauge_force(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, double beta, dou
     case HMC_F64 * 100 + 12: k_gauge_force<HMC_F64, 12><<<nb, 128, 0, strm>>>(a); break;
     case HMC_F32 * 100 + 18: k_gauge_force<HMC_F32, 18><<<nb, 128, 0, strm>>>(a); break;
     case HMC_F32 * 100 + 12: k_gauge_force<HMC_F32, 12><<<nb, 128, 0, strm>>>(a); break;
-    default: return fail(ctx, HMC_EINVAL, "gauge_force: links must be F64 or F32");
+    // emulated FP64: staples and U A in double-float, F accumulated in FP64
+    case HMC_F64E * 100 + 18: k_gauge_force<HMC_F64E, 18><<<nb, 128, 0, strm>>>(a); break;
+    case HMC_F64E * 100 + 12: k_gauge_force<HMC_F64E, 12><<<nb, 128, 0, strm>>>(a); break;
+    default: return fail(ctx, HMC_EINVAL, "gauge_force: links must be F64, F32 or F64E");
   }
-  return launched(ctx, U.prec == HMC_F64 ? "gauge_force_f64" : "gauge_force_f32");
+  return launched(ctx, U.prec == HMC_F64 ? "gauge_force_f64"
+                       : U.prec == HMC_F32 ? "gauge_force_f32" : "gauge_force_f64e");
 }
 
 // Enqueues the action reduction: dst[0] = plaquette sum, dst[1] = signed line

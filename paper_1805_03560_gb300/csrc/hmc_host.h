@@ -177,6 +177,14 @@ int bicgstab_normal(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_g
                     const void *phi, double kappa, double tol, int max_iter,
                     const hmc_solver_opts *opts, hmc_solve_stats *stats);
 
+// Links in the precision fp of the force algebra (hmc_solver_opts.force_prec):
+// U_hi itself for F64; for F32 the inner-precision copy U_lo when it is F32,
+// otherwise an F32/LINK12 copy of U_hi made in workspace; for F64E an
+// emulated-FP64 copy of U_hi (same format) made in workspace.  who names the
+// caller in error messages.
+int force_links(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul, int fp,
+                hmc_gauge *Uf, const char *who);
+
 // FP64-accurate operator applications, native or emulated (hiprec.cu).
 // hi_begin makes the F64E copy of the links when opts->f64_emul is set; tag
 // names the workspace (one tag per caller that may be active at a time).

@@ -120,19 +120,8 @@ int force_mp(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
   HiOps hi;
   TRY(hi_begin(ctx, g, Uh, opts, &hi, "mp"));
   const int fp = opts ? opts->force_prec : HMC_F64;
-  if (fp != HMC_F64 && fp != HMC_F32)
-    return fail(ctx, HMC_EINVAL, "force_mp: force_prec must be F64 or F32");
-  hmc_gauge Uf = Uh;
-  if (fp == HMC_F32) {
-    if (Ul && Ul->prec == HMC_F32) {
-      Uf = *Ul;
-    } else {
-      void *u32 = workspace(ctx, "pf_u32", gauge_bytes(g, HMC_F32, HMC_LINK12));
-      if (!u32) return HMC_ENOMEM;
-      TRY(convert_gauge(ctx, g, Uh.data, u32, HMC_F32, HMC_LINK12));
-      Uf = hmc_gauge{u32, HMC_F32, HMC_LINK12};
-    }
-  }
+  hmc_gauge Uf;
+  TRY(force_links(ctx, g, Uh, Ul, fp, &Uf, "force_mp"));
   const size_t f64 = spinor_bytes(g, HMC_F64, 1);
   TRY(first_solves(hi, Ul, phi, n, kb, tol, opts, acc));
   // second solves of the ratio terms, batched

@@ -51,11 +51,15 @@ extern "C" int hmc_mhat_noalloc(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_
                   cudaGetErrorString(e));
     g_scratch_addr[dev] = tmp;
   }
-  // the optional per-launch event timing may create CUDA events, so it is
-  // bypassed for this call
-  const int saved = ctx->timing;
+  // the optional per-launch event timing and the autotuner create CUDA
+  // events (and the autotuner synchronises the stream and relaunches), so
+  // both are bypassed for this call: an autotuning context runs the built-in
+  // default variant, which computes the same result bit for bit
+  const int saved_timing = ctx->timing, saved_variant = ctx->ds_variant;
   ctx->timing = 0;
+  if (ctx->ds_variant == -2) ctx->ds_variant = -1;
   st = mhat(ctx, g, *U, prec, dagger, n_rhs, out, in, tmp, kappa, nullptr, nullptr, nullptr);
-  ctx->timing = saved;
+  ctx->timing = saved_timing;
+  ctx->ds_variant = saved_variant;
   return st;
 }

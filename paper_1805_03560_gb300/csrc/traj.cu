@@ -133,30 +133,44 @@ static int mhat_inverse(const HiOps &h, const hmc_gauge *Ul, void *y, const void
   return solve(h.ctx, h.g, h.Uh, Ul, y, src, kappa, tol, opts, acc);
 }
 
+int force_links(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul, int fp,
+                hmc_gauge *Uf, const char *who) {
+  *Uf = Uh;
+  if (fp == HMC_F64) return HMC_OK;
+  if (fp == HMC_F32) {
+    if (Ul && Ul->prec == HMC_F32) {
+      *Uf = *Ul;
+      return HMC_OK;
+    }
+    if (Uh.fmt != HMC_LINK18)
+      return fail(ctx, HMC_EINVAL, "%s: F32 force needs U_lo in F32 or U_hi in LINK18", who);
+    void *u32 = workspace(ctx, "pf_u32", gauge_bytes(g, HMC_F32, HMC_LINK12));
+    if (!u32) return HMC_ENOMEM;
+    TRY(convert_gauge(ctx, g, Uh.data, u32, HMC_F32, HMC_LINK12));
+    *Uf = hmc_gauge{u32, HMC_F32, HMC_LINK12};
+    return HMC_OK;
+  }
+  if (fp == HMC_F64E) {
+    void *ue = workspace(ctx, "pf_ue", gauge_bytes(g, HMC_F64E, Uh.fmt));
+    if (!ue) return HMC_ENOMEM;
+    TRY(convert_gauge(ctx, g, Uh.data, ue, HMC_F64E, Uh.fmt));
+    *Uf = hmc_gauge{ue, HMC_F64E, Uh.fmt};
+    return HMC_OK;
+  }
+  return fail(ctx, HMC_EINVAL, "%s: force_prec must be F64, F32 or F64E", who);
+}
+
 // The pseudo-fermion force.  Solves always run to tol with their FP64
-// residual; with opts->force_prec == HMC_F32 every other Dslash, the filter
-// polynomials (Horner chain Y_i, the chain X_i = K^dag X_{i-1}) and the spin
-// projections of the outer products run on F32 fields; the outer products and
-// the force accumulate in FP64 on the FP64 links.
+// residual; with opts->force_prec == HMC_F32 (or HMC_F64E) every other
+// Dslash, the filter polynomials (Horner chain Y_i, the chain
+// X_i = K^dag X_{i-1}), the spin projections and the outer products run on
+// F32 (emulated-FP64) fields and links; the force accumulates in FP64.
 int force_pf(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
              const void *phi, double kappa, const hmc_filter *filt, double coeff, double *F,
              double tol, const hmc_solver_opts *opts, hmc_solve_stats *acc) {
   const int fp = opts ? opts->force_prec : HMC_F64;
-  if (fp != HMC_F64 && fp != HMC_F32)
-    return fail(ctx, HMC_EINVAL, "force_pf: force_prec must be F64 or F32");
-  hmc_gauge Uf = Uh;
-  if (fp == HMC_F32) {
-    if (Ul && Ul->prec == HMC_F32) {
-      Uf = *Ul;
-    } else if (Uh.fmt == HMC_LINK18) {
-      void *u32 = workspace(ctx, "pf_u32", gauge_bytes(g, HMC_F32, HMC_LINK12));
-      if (!u32) return HMC_ENOMEM;
-      TRY(convert_gauge(ctx, g, Uh.data, u32, HMC_F32, HMC_LINK12));
-      Uf = hmc_gauge{u32, HMC_F32, HMC_LINK12};
-    } else {
-      return fail(ctx, HMC_EINVAL, "force_pf: F32 force needs U_lo in F32 or U_hi in LINK18");
-    }
-  }
+  hmc_gauge Uf;
+  TRY(force_links(ctx, g, Uh, Ul, fp, &Uf, "force_pf"));
   const size_t f64 = spinor_bytes(g, HMC_F64, 1);
   void *X = workspace(ctx, "pf_x", f64), *Y = workspace(ctx, "pf_y", f64);
   void *tmp = workspace(ctx, "pf_tmp", f64), *Xf = workspace(ctx, "pf_xf", f64);
@@ -505,16 +519,20 @@ int md_evolve(hmc_ctx *ctx, const Geo &g, void *U1, void *Ulo, double *P, double
     }
     return update_momenta(ctx, g, P, F, eps);
   };
-  // with force_prec F32 the gauge force runs on an F32 copy of the links
-  const bool g32 = prm->solver.force_prec == HMC_F32;
-  void *U32 = g32 ? workspace(ctx, "tr_u32", gauge_bytes(g, HMC_F32, HMC_LINK12)) : nullptr;
-  if (g32 && !U32) return HMC_ENOMEM;
-  const hmc_gauge Ug32{U32, HMC_F32, HMC_LINK12};
+  // with force_prec F32 (F64E) the gauge force runs on an F32/LINK12
+  // (emulated-FP64/LINK18) copy of the links
+  const int gfp = prm->solver.force_prec;
+  const bool glo = gfp == HMC_F32 || gfp == HMC_F64E;
+  const int gfmt = gfp == HMC_F32 ? HMC_LINK12 : HMC_LINK18;
+  void *Ug = glo ? workspace(ctx, gfp == HMC_F32 ? "tr_u32" : "tr_ug", gauge_bytes(g, gfp, gfmt))
+                 : nullptr;
+  if (glo && !Ug) return HMC_ENOMEM;
+  const hmc_gauge Ugl{Ug, gfp, gfmt};
   auto gauge_step = [&](double eps) -> int {
     TRY(cuda_ok(ctx, cudaMemsetAsync(F, 0, fbytes, st), "md: zero F"));
-    if (g32) {
-      TRY(convert_gauge(ctx, g, U1, U32, HMC_F32, HMC_LINK12));
-      TRY(gauge_force(ctx, g, Ug32, prm->beta, prm->kappa, k, 1.0, F));
+    if (glo) {
+      TRY(convert_gauge(ctx, g, U1, Ug, gfp, gfmt));
+      TRY(gauge_force(ctx, g, Ugl, prm->beta, prm->kappa, k, 1.0, F));
     } else {
       TRY(gauge_force(ctx, g, Uh, prm->beta, prm->kappa, k, 1.0, F));
     }

@@ -70,7 +70,7 @@ def test_null_context_utilities(H):
     assert lib.hmc_launch_count(None) == 0
 
 
-def test_host_entry_points_reject_bad_arguments(H):
+def test_host_entry_points_reject_bad_arguments(H, tmp_path):
     lib = H.lib()
     assert lib.hmc_checkpoint_write(None, None, None, None) == H.EINVAL
     assert lib.hmc_checkpoint_read(None, None, None, None, 0) == H.EINVAL
@@ -80,9 +80,10 @@ def test_host_entry_points_reject_bad_arguments(H):
     # a checkpoint with a non-positive extent is refused before any I/O
     bad = H.CheckpointInfo((ctypes.c_int * 4)(4, 4, 0, 4), 5.6, 0.15, 1, 0, 0, 0.5)
     buf = (ctypes.c_double * 8)()
-    assert lib.hmc_checkpoint_write(None, b"/tmp/never-written.ckpt", ctypes.byref(bad),
+    path = tmp_path / "never-written.ckpt"
+    assert lib.hmc_checkpoint_write(None, str(path).encode(), ctypes.byref(bad),
                                     buf) == H.EINVAL
-    assert not os.path.exists("/tmp/never-written.ckpt")
+    assert not path.exists()
 
 
 def test_coefficient_entry_points_validate(H):
