@@ -1,13 +1,21 @@
 #!/usr/bin/env python3
 """Benchmark of the GB300 hot path: one HMC trajectory per step.
 
-Workload: 24^3 x 48 lattice, beta = 5.6, kappa = 0.1575, synthetic links
-U = exp(i 0.3 A) (seeded), kappa^4 filtering (n_t = 9 in the force, n_max = 29
-in the action), leapfrog on two time scales (tau = 1, 10 coarse steps,
-4 gauge steps each), pseudo-fermion solves to relative residual 1e-10 (MD) and
-1e-12 (action) with FP16-storage / FP32-arithmetic CG and FP64 reliable
-updates.  One step = the whole path: heatbath, every force, every solve, the
-filter polynomials, link updates, the Hamiltonian and the Metropolis test.
+Workload: 24^3 x 48 lattice, beta = 5.6, kappa = 0.1575, kappa^4 filtering
+(n_t = 9 in the force, n_max = 29 in the action), the second-order Omelyan
+integrator (lambda = 1/6) on two time scales (tau = 1, 10 coarse steps of 4
+gauge steps), pseudo-fermion solves to relative residual 1e-10 (MD) and 1e-12
+(action) with FP32 CG on 12-real FP32 links and emulated-FP64 reliable
+updates, the force algebra and the link update in emulated FP64.  One step =
+the whole path: heatbath, every force, every solve, the filter polynomials,
+link updates, the Hamiltonian and the Metropolis test.
+
+Start: the seeded synthetic links U = exp(i 0.3 A), relaxed by pure-gauge HMC
+on the device (the synthetic field itself is far from equilibrium at beta 5.6,
+with dH of O(10^3) and acceptance zero).  Timed step t starts from that field
+with momenta and sources drawn by the library's counter-based generator at
+counter t; the plain-FP64 GPU path then runs the first trajectories with the
+same inputs, so dH, acceptance and time compare like for like.
 
 Prints one JSON line.  value = hemi-Dslash algorithmic bytes per trajectory
 (each link and spinor of every launch counted once) over the device time of
@@ -15,8 +23,8 @@ the trajectory, i.e. the whole job expressed in the metric's unit.  The
 roofline object gives the dominant Dslash kernel alone, timed with CUDA events
 on its launch stream during the timed steps.
 
---impl reference runs the FP64 CPU oracle instead (bounded sample: one
-hemi-Dslash of the same lattice per step, on the host cores).
+--impl reference runs the FP64 CPU oracle instead (bounded sample: oracle
+hemi-Dslash applications of the same lattice on all host cores).
 """
 import argparse
 import hashlib
@@ -44,6 +52,8 @@ WORK = dict(beta=5.6, kappa=0.1575, tau=1.0, n_md=10, n_gauge=4, filter_k=2, n_t
 EPS_LINKS = 0.3
 FLUSH_BYTES = 256 << 20  # > 129 MB L2
 FP64_PEAK_GFLOPS = 1250.0  # nominal dense FP64 of GB300 (no measured figure in the peaks file)
+FP64_PEAK_SOURCE = "nominal FP64 rate of GB300 (recipe table)"
+RELAX_BETA = 5.85  # pure-gauge beta of the relaxation (plaquette ~0.577, near beta 5.6 dynamical)
 
 
 def parse():
@@ -62,7 +72,11 @@ def parse():
                          "event timeline and report its per-kernel shares")
     ap.add_argument("--inner", default="f32", choices=["f16", "f32"])
     ap.add_argument("--delta", type=float, default=1e-5, help="reliable-update threshold")
-    ap.add_argument("--force-prec", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--force-prec", default="f64e", choices=["f32", "f64", "f64e"],
+                    help="precision of the molecular-dynamics force algebra (Dslash "
+                         "applications outside the solves, filter polynomials, outer products, "
+                         "gauge force): emulated FP64 (default; forces within 1e-8 of FP64), "
+                         "native FP64, or FP32 (about 1e-6)")
     ap.add_argument("--f64-emul", type=int, default=1, choices=[0, 1],
                     help="FP64-accurate operator applications outside the inner solver "
                          "(reliable updates, heatbath and action polynomials) in emulated "
@@ -74,8 +88,19 @@ def parse():
                     help="--kernel <prec>-<fmt>: right-hand sides per launch (links shared)")
     ap.add_argument("--tau", type=float, default=None,
                     help="trajectory length (applied after --n-md, which scales it)")
-    ap.add_argument("--integrator", default="leapfrog", choices=["leapfrog", "omelyan"],
-                    help="two-level leapfrog, or the second-order Omelyan scheme (lambda 1/6)")
+    ap.add_argument("--integrator", default="omelyan", choices=["leapfrog", "omelyan"],
+                    help="two-level second-order Omelyan scheme (lambda 1/6, the paper's "
+                         "choice), or the two-level leapfrog")
+    ap.add_argument("--no-relax", action="store_true",
+                    help="start the trajectories from the synthetic field itself (far from "
+                         "equilibrium: dH of O(10^3), acceptance zero)")
+    ap.add_argument("--relax-beta", type=float, default=RELAX_BETA,
+                    help="beta of the pure-gauge HMC that relaxes the synthetic start")
+    ap.add_argument("--relax-traj", type=int, default=30,
+                    help="pure-gauge trajectories of the relaxation")
+    ap.add_argument("--fp64-traj", type=int, default=2,
+                    help="trajectories of the plain-FP64 comparison (the first ones of the "
+                         "timed steps, same momenta and sources)")
     ap.add_argument("--thermal-kappa", type=float, default=0.156,
                     help="hopping parameter of the --report thermal trajectories")
     ap.add_argument("--lattice", default="24x48", choices=sorted(LATTICES),
@@ -297,23 +322,34 @@ class Clocks:
 KAPPA_MP = [0.150, 0.154]
 
 
-def build_inputs(rank, n_eta=1):
-    from paper_1805_03560_gb300 import inputs as I
-    import numpy as np
-    U = I.gauge_links(LAT, EPS_LINKS, seed=1 + 100 * rank)
-    P = I.momenta(LAT, seed=3 + 100 * rank)
-    if n_eta == 1:
-        eta = I.gaussian_half(LAT, seed=2 + 100 * rank)
-    else:
-        eta = np.stack([I.gaussian_half(LAT, seed=2 + 100 * rank + 1000 * j) for j in range(n_eta)])
-    return U, P, eta
-
-
 def coeffs():
     from paper_1805_03560_gb300 import hmc
     b, alpha, _ = hmc.filter_coeffs(WORK["filter_k"], WORK["n_max"], with_c=False)
     _, _, c = hmc.filter_coeffs(WORK["filter_k"], WORK["n_max"])
     return b, alpha, c
+
+
+def relax_start(ctx, Ud, args, rank):
+    """Relax the synthetic start towards an equilibrium gauge field by
+    pure-gauge HMC on the device (momenta from the library's counter-based
+    generator), so that the benchmark trajectories start from a field whose
+    acceptance is not zero.  Returns the description of the start."""
+    from paper_1805_03560_gb300.run import relax_pure_gauge
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.time()
+    acc, plaq = relax_pure_gauge(ctx, LAT, Ud, args.relax_beta, args.relax_traj, 20,
+                                 11 + rank, device_rng=True)
+    torch.cuda.synchronize()
+    return {"relaxed": f"pure-gauge HMC, beta {args.relax_beta}, {args.relax_traj} trajectories "
+                       "of 20 leapfrog steps (tau 1)",
+            "plaquette": round(plaq, 6), "acceptance": acc, "s": round(time.time() - t0, 1)}
+
+
+def acceptance(dHs):
+    import numpy as np
+    d = np.asarray(dHs, dtype=np.float64)
+    return float(np.mean(np.minimum(1.0, np.exp(-d)))) if d.size else None
 
 
 def run_hmc(args):
@@ -335,25 +371,31 @@ def run_hmc(args):
     # autotuned hemi-Dslash variants (tuned during the warm-up steps)
     ctx.set_dslash_variant(-2 if args.variant is None else args.variant)
     n_eta = len(KAPPA_MP) + 1 if args.mp else (2 * args.rooted + 1 if args.rooted else 1)
-    U, P, eta = build_inputs(rank, n_eta)
-    b, alpha, c = coeffs()
-    U0 = ctx.pack_gauge(LAT, U, hmc.F64, hmc.LINK18)
+    from paper_1805_03560_gb300 import inputs as I
+    U0 = ctx.pack_gauge(LAT, I.gauge_links(LAT, EPS_LINKS, seed=1 + 100 * rank), hmc.F64,
+                        hmc.LINK18)
     Ud = ctx.new_gauge(LAT, hmc.F64, hmc.LINK18)
-    Pd = ctx.pack_algebra(LAT, P)
-    ed = ctx.pack_spinors(LAT, list(eta)) if n_eta > 1 else ctx.pack_spinor(LAT, eta, hmc.F64)
+    b, alpha, c = coeffs()
     start = None
-    if args.rooted:
-        # the roots' series in K approximate only where the spectrum of K lies
-        # inside the unit disk: on the synthetic start its radius is ~1.37 at
-        # kappa 0.1575 (the heatbath's P^dag P is then ill-conditioned), on a
-        # field relaxed by pure-gauge HMC ~0.98
-        t0 = time.time()
-        acc_q, plaq = quenched_hmc(ctx, LAT, U0, 5.85, 30, 20, 11 + rank)
-        U = ctx.unpack_gauge(LAT, U0).cpu().numpy()
-        start = {"relaxed": "pure-gauge HMC, beta 5.85, 30 trajectories", "plaquette": plaq,
-                 "acceptance": acc_q, "s": round(time.time() - t0, 1)}
+    if args.rooted or not args.no_relax:
+        # the synthetic start is far from equilibrium at beta 5.6 (dH of
+        # O(10^3), acceptance zero); the roots' series in K also need the
+        # spectrum of K inside the unit disk, which holds on a relaxed field
+        if args.rooted and args.no_relax:
+            args.relax_beta = 5.85
+        start = relax_start(ctx, U0, args, rank)
+    # per-step random inputs, drawn on the device from (seed, counter) and
+    # resident before the timed region: warm-up steps use counters
+    # 1000 + w, timed step t counter t
+    seed = 7 + 100 * rank
+
+    def inputs_for(counter):
+        P = ctx.random_momenta(LAT, seed, counter)
+        eta = ctx.random_sources(LAT, n_eta, seed, counter)
+        return P, eta
+
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    fprec = hmc.F32 if args.force_prec == "f32" else hmc.F64
+    fprec = {"f32": hmc.F32, "f64": hmc.F64, "f64e": hmc.F64E}[args.force_prec]
     work = dict(WORK)
     if args.n_md:
         work["tau"] = WORK["tau"] * args.n_md / WORK["n_md"]
@@ -389,12 +431,13 @@ def run_hmc(args):
                   solver=solver)
     stream = torch.cuda.current_stream()
 
-    def one(kwargs):
+    def one(kwargs, P, eta):
         Ud.data.copy_(U0.data)
-        return ctx.trajectory(LAT, Ud, Pd, ed, 0.5, **kwargs)
+        return ctx.trajectory(LAT, Ud, P, eta, 0.5, **kwargs)
 
-    for _ in range(args.warmup):
-        one(kw)
+    for w in range(args.warmup):
+        one(kw, *inputs_for(1000 + w))
+    steps_in = [inputs_for(t) for t in range(args.steps)]
     torch.cuda.synchronize()
     # ---- timed region --------------------------------------------------------
     clocks = Clocks(local)
@@ -404,13 +447,13 @@ def run_hmc(args):
     torch.cuda.synchronize()
     clocks.start()
     times, results = [], []
-    for _ in range(args.steps):
+    for t in range(args.steps):
         Ud.data.copy_(U0.data)
         flush.zero_()  # L2 flush between timed steps (outside the events)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        results.append(ctx.trajectory(LAT, Ud, Pd, ed, 0.5, **kw))
+        results.append(ctx.trajectory(LAT, Ud, steps_in[t][0], steps_in[t][1], 0.5, **kw))
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -422,18 +465,22 @@ def run_hmc(args):
     ctx.set_timing(False)
     ms_step = allmax(sum(times) / len(times))
     ds_bytes = sum(v[2] for k, v in kst.items() if k.startswith("dslash")) / args.steps
+    Vh = int(np.prod(LAT)) // 2
+    # hemi-Dslash output-site applications per trajectory (n_rhs = 1 except in
+    # the batched solves of --mp, whose launches count once per right-hand side
+    # through their bytes, so the count is a lower bound there)
+    ds_sites = sum(v[0] for k, v in kst.items() if k.startswith("dslash")) * Vh / args.steps
     value = allsum(ds_bytes) / (ms_step * 1e-3) / 1e9
     # dominant Dslash class by time
     dom = max((k for k in kst if k.startswith("dslash")), key=lambda k: kst[k][1])
     n_dom, ms_dom, b_dom = kst[dom]
     pk = peaks()
     if dom.startswith("dslash_f64"):
-        Vh = int(np.prod(LAT)) // 2
         achieved = 1320.0 * Vh * n_dom / (ms_dom * 1e-3) / 1e9
         roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 1),
                 "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                 "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": None,
-                "peak_source": "nominal FP64 rate of GB300 (recipe table)"}
+                "peak_source": FP64_PEAK_SOURCE}
     else:
         achieved = b_dom / (ms_dom * 1e-3) / 1e9
         peak = pk["hbm_gbs"] if pk else 6800.0
@@ -445,23 +492,30 @@ def run_hmc(args):
                 # the standard 1320 flop per hemi-Dslash output site (one
                 # right-hand side per launch; the batched solves of --mp have more)
                 "gflops": None if args.mp else
-                round(1320.0 * (int(np.prod(LAT)) // 2) * n_dom / (ms_dom * 1e-3) / 1e9, 1),
+                round(1320.0 * Vh * n_dom / (ms_dom * 1e-3) / 1e9, 1),
                 "peak_source": "measured" if pk else "fallback"}
     kernels = {k: {"launches_per_step": v[0] // args.steps, "us": round(v[1] / v[0] * 1e3, 2),
                    "GBs": round(v[2] / (v[1] * 1e-3) / 1e9, 1)} for k, v in sorted(kst.items())}
+    dHs = [r["dH"] for r in results]
+    if args.mp:
+        wl = (f"hmc-trajectory {lat_name()} kappa={work['kappa']} beta=5.6 "
+              "mass-preconditioned kappa'=0.150,0.154 (batched solves)")
+    elif args.rooted:
+        wl = (f"hmc-trajectory {lat_name()} kappa={work['kappa']} beta=5.6 kappa^4 "
+              f"rooted polynomials N={args.rooted} (degrees 16, 42)")
+    else:
+        wl = f"hmc-trajectory {lat_name()} kappa={work['kappa']} beta=5.6 kappa^4-filter"
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.inner,
-        "data": "synthetic (seeded exp(i 0.3 A) links, Gaussian momenta and sources)",
-        "config": {"workload": (f"hmc-trajectory {lat_name()} kappa={work['kappa']} beta=5.6 "
-                                 "mass-preconditioned kappa'=0.150,0.154 (batched solves)"
-                                 if args.mp else
-                                 f"hmc-trajectory {lat_name()} kappa={work['kappa']} beta=5.6 kappa^4 "
-                                 f"rooted polynomials N={args.rooted} (degrees 16, 42)"
-                                 if args.rooted else
-                                 f"hmc-trajectory {lat_name()} kappa={work['kappa']} beta=5.6 kappa^4-filter"),
-                   "lattice": "x".join(str(v) for v in LAT[::-1]), **{k: v for k, v in work.items()},
+        "data": ("synthetic (seeded exp(i 0.3 A) links" +
+                 (", relaxed by pure-gauge HMC" if start else "") +
+                 "; momenta and sources from the library's counter-based generator)"),
+        "config": {"workload": wl,
+                   "lattice": "x".join(str(v) for v in LAT[::-1]),
+                   **{k: v for k, v in work.items()},
+                   "integrator": args.integrator,
                    "inner_prec": args.inner, "reliable_delta": args.delta,
                    "force_prec": args.force_prec, "f64_emul": args.f64_emul,
                    "solver": args.solver,
@@ -473,63 +527,81 @@ def run_hmc(args):
         "roofline": roof,
         "gpu_launches": launches,
         "kernels": kernels,
-        "trajectory": {"s": round(ms_step / 1e3, 4), "dH": results[-1]["dH"],
-                       "accepted": results[-1]["accepted"],
-                       "cg_iterations": results[-1]["cg_iterations"],
-                       "solves": results[-1]["solves"]},
+        "trajectory": {"s": round(ms_step / 1e3, 4), "s_each": [round(x / 1e3, 4) for x in times],
+                       "dH": dHs, "acceptance": acceptance(dHs),
+                       "accepted": [r["accepted"] for r in results],
+                       "cg_iterations": [r["cg_iterations"] for r in results],
+                       "solves": results[-1]["solves"],
+                       "dslash_site_applications": int(ds_sites)},
     }
     if clk:
         out["clocks"] = clk
     # ---- per-kernel shares of one trajectory (launch timeline) ----------------------
     if args.timeline:
         ctx.set_timing(2)
-        one(kw)
+        one(kw, *steps_in[0])
         tl = ctx.timing()
         ctx.set_timing(0)
         tot = sum(v[1] for v in tl.values())
         out["timeline"] = {k: {"launches": v[0], "ms": round(v[1], 2),
                                "share": round(v[1] / tot, 4)}
                            for k, v in sorted(tl.items(), key=lambda kv: -kv[1][1])}
-    # ---- plain FP64 GPU path, same trajectory ----------------------------------
-    if not args.no_fp64:
+    # ---- plain FP64 GPU path, the same trajectories ----------------------------
+    if not args.no_fp64 and world == 1:
+        # at N = 1 only (a replica run would hold every GPU for it)
+        n_cmp = max(1, min(args.steps, args.fp64_traj))
         kw64 = dict(kw, inner_prec=hmc.F64, force_prec=hmc.F64, f64_emul=0)
-        one(kw64)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        Ud.data.copy_(U0.data)
-        flush.zero_()
-        e0.record(stream)
-        r64 = ctx.trajectory(LAT, Ud, Pd, ed, 0.5, **kw64)
-        e1.record(stream)
-        e1.synchronize()
-        s64 = allmax(e0.elapsed_time(e1)) / 1e3
-        out["fp64_path"] = {"s_per_trajectory": round(s64, 4), "dH": r64["dH"],
-                            "accepted": r64["accepted"], "cg_iterations": r64["cg_iterations"]}
-        out["speedup_vs_fp64"] = round(s64 / (ms_step / 1e3), 3)
-        out["dH_diff_vs_fp64"] = abs(r64["dH"] - results[-1]["dH"])
+        s64, r64 = [], []
+        for t in range(n_cmp):
+            Ud.data.copy_(U0.data)
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r64.append(ctx.trajectory(LAT, Ud, steps_in[t][0], steps_in[t][1], 0.5, **kw64))
+            e1.record(stream)
+            e1.synchronize()
+            s64.append(e0.elapsed_time(e1) / 1e3)
+        s64_mean = allmax(sum(s64) / n_cmp)
+        mixed_mean = allmax(sum(times[:n_cmp]) / n_cmp / 1e3)
+        dH64 = [r["dH"] for r in r64]
+        out["fp64_path"] = {"s_per_trajectory": round(s64_mean, 4),
+                            "s_each": [round(x, 4) for x in s64], "dH": dH64,
+                            "acceptance": acceptance(dH64),
+                            "accepted": [r["accepted"] for r in r64],
+                            "cg_iterations": [r["cg_iterations"] for r in r64],
+                            "trajectories": n_cmp}
+        out["mixed_same_trajectories"] = {"s_per_trajectory": round(mixed_mean, 4),
+                                          "acceptance": acceptance(dHs[:n_cmp])}
+        out["speedup_vs_fp64"] = round(s64_mean / mixed_mean, 3)
+        out["dH_diff_vs_fp64"] = max(abs(a - b) for a, b in zip(dH64, dHs))
     # ---- end to end through the public API with host buffers ----------------------
     if not args.no_e2e:
-        Uh = torch.view_as_real(torch.from_numpy(U)).pin_memory()
-        Ph = torch.from_numpy(P).pin_memory()
-        eh = torch.view_as_real(torch.from_numpy(eta)).pin_memory()
+        import ctypes
+        Uh = torch.view_as_real(ctx.unpack_gauge(LAT, U0).cpu()).contiguous().pin_memory()
+        Phs = [ctx.unpack_algebra(LAT, P).cpu().contiguous().pin_memory() for P, _ in steps_in]
+        nb1 = int(hmc.lib().hmc_spinor_bytes(hmc._ref(hmc.lattice(LAT)), hmc.F64, 1))
+        ehs = []
+        for _, eta in steps_in:
+            fields = ctx.unpack_spinors(LAT, eta) if n_eta > 1 else [ctx.unpack_spinor(LAT, eta)]
+            ehs.append(torch.view_as_real(torch.stack([f.reshape(-1) for f in fields]).cpu())
+                       .contiguous().pin_memory())
         Uout = torch.empty_like(Uh).pin_memory()
         Ucd = torch.empty(Uh.shape, dtype=torch.float64, device="cuda")
-        Pcd = torch.empty(Ph.shape, dtype=torch.float64, device="cuda")
-        ecd = torch.empty(eh.shape, dtype=torch.float64, device="cuda")
+        Pcd = torch.empty(Phs[0].shape, dtype=torch.float64, device="cuda")
+        ecd = torch.empty(ehs[0].shape, dtype=torch.float64, device="cuda")
         Ue = ctx.new_gauge(LAT, hmc.F64, hmc.LINK18)
         Pe = ctx.new_algebra(LAT)
-        nb1 = int(hmc.lib().hmc_spinor_bytes(hmc._ref(hmc.lattice(LAT)), hmc.F64, 1))
         ee = hmc.Field(torch.empty(nb1 * n_eta, dtype=torch.uint8, device="cuda"), "spinor",
                        hmc.F64, 1)
         lat = hmc.lattice(LAT)
         lib = hmc.lib()
-        import ctypes
 
-        def e2e_step():
+        def e2e_step(t):
             Ucd.copy_(Uh, non_blocking=True)
-            Pcd.copy_(Ph, non_blocking=True)
-            ecd.copy_(eh, non_blocking=True)
+            Pcd.copy_(Phs[t], non_blocking=True)
+            ecd.copy_(ehs[t], non_blocking=True)
             ctx._stream()
             ctx._check(lib.hmc_pack_gauge(ctx.h, ctypes.byref(lat), ctypes.c_void_p(Ucd.data_ptr()),
                                           Ue.ptr(), hmc.F64, hmc.LINK18), "pack")
@@ -546,76 +618,113 @@ def run_hmc(args):
             Uout.copy_(Ucd, non_blocking=True)
             return r
 
-        e2e_step()
         torch.cuda.synchronize()
         barrier()
         tt = []
-        for _ in range(args.steps):
+        for t in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            e2e_step()
+            e2e_step(t)
             torch.cuda.synchronize()
             tt.append(time.perf_counter() - t0)
         t_e2e = allmax(sum(tt) / len(tt))
         out["e2e"] = {"value": round(allsum(ds_bytes) / t_e2e / 1e9, 1), "unit": "GB/s",
                       "s_per_trajectory": round(t_e2e, 4),
-                      "h2d_bytes_per_step": int(Uh.numel() * 8 + Ph.numel() * 8 + eh.numel() * 8),
+                      "h2d_bytes_per_step": int(Uh.numel() * 8 + Phs[0].numel() * 8 +
+                                                ehs[0].numel() * 8),
                       "d2h_bytes_per_step": int(Uout.numel() * 8 + 8 * 8)}
     if rank == 0:
-        if not args.no_cpu:
-            out["cpu_baseline"] = cpu_baseline()
+        if not args.no_cpu and world == 1:
+            out["cpu_baseline"] = cpu_baseline(ds_bytes / max(ds_sites, 1), ds_sites)
         print(json.dumps(out), flush=True)
     rep.close()
 
 
-def oracle_dslash_sample(n_apply):
-    """The FP64 oracle hemi-Dslash on the benchmark lattice, n_apply times."""
+def oracle_sample(threads, n_hop=3, cg_iters=3):
+    """The FP64 C oracle on the benchmark lattice with `threads` threads:
+    seconds per hemi-Dslash, per Mhat and per CG iteration (a CG on
+    Mhat^dag Mhat stopped after cg_iters iterations, its final true residual
+    included)."""
     import numpy as np
     import oracle
     from paper_1805_03560_gb300 import inputs as I
     oracle.build()
+    oracle.set_threads(threads)
     U = I.gauge_links(LAT, EPS_LINKS, seed=1)
     psi = I.gaussian_half(LAT, seed=2)
     oracle.hop_eo(LAT, U, 0, psi)  # warm
     t0 = time.perf_counter()
-    for i in range(n_apply):
+    for i in range(n_hop):
         oracle.hop_eo(LAT, U, i % 2, psi)
-    dt = (time.perf_counter() - t0) / n_apply
-    Vh = int(np.prod(LAT)) // 2
-    byt = Vh * (8 * 18 * 8 + 24 * 8 * 2)  # FP64, 18-real links: the oracle's own data
-    return byt / dt / 1e9, dt
+    t_hop = (time.perf_counter() - t0) / n_hop
+    t0 = time.perf_counter()
+    oracle.mhat(LAT, U, WORK["kappa"], psi)
+    t_mhat = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.cg(LAT, U, WORK["kappa"], psi, tol=1e-30, max_iter=cg_iters)
+    t_cg = time.perf_counter() - t0
+    return {"threads": oracle.threads(), "s_per_hemi_dslash": round(t_hop, 4),
+            "s_per_mhat": round(t_mhat, 4),
+            # cg_iters iterations plus the final FP64 true residual (one more
+            # Mhat^dag Mhat)
+            "s_cg_sample": round(t_cg, 4), "cg_sample_iterations": cg_iters,
+            "site_applications_per_s": round((int(np.prod(LAT)) // 2) / t_hop, 1)}
 
 
-def cpu_baseline():
-    gbs, dt = oracle_dslash_sample(4)
-    return {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"4 hemi-Dslash applications of the FP64 C oracle on {lat_name()} "
-                      f"({dt:.2f} s each, single thread), FP64 18-real algorithmic bytes"}
+def cpu_baseline(bytes_per_site, sites_per_traj):
+    """The oracle as it stands on the host cores (all of them, and one),
+    expressed in the benchmark's unit: the trajectory's hemi-Dslash site
+    applications at the oracle's rate, each counted with the trajectory's own
+    algorithmic bytes per site application."""
+    ncores = os.cpu_count() or 1
+    allc = oracle_sample(ncores)
+    one = oracle_sample(1, n_hop=1, cg_iters=1)
+    gbs = allc["site_applications_per_s"] * bytes_per_site / 1e9
+    return {"value": round(gbs, 3), "unit": "GB/s", "cores": allc["threads"], "kind": "oracle",
+            "nproc": ncores,
+            "sample": (f"FP64 C oracle on {lat_name()}: hemi-Dslash, Mhat and CG iterations, "
+                       f"{allc['threads']} threads (OpenMP over sites) and 1 thread; value = "
+                       f"the trajectory's {int(sites_per_traj)} hemi-Dslash site applications "
+                       f"at the oracle's all-core rate, {bytes_per_site:.0f} B each (the "
+                       "trajectory's algorithmic bytes per site application)"),
+            "all_cores": allc, "single_thread": one,
+            "s_per_trajectory_dslash_only": round(sites_per_traj /
+                                                  allc["site_applications_per_s"], 1)}
+
+
+REF_BYTES_PER_SITE = 576  # FP32-12 hemi-Dslash: 8 x 12 x 4 (links) + 2 x 24 x 4 (spinors)
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    ncores = os.cpu_count() or 1
     for _ in range(args.warmup):
-        oracle_dslash_sample(1)
+        oracle_sample(ncores, n_hop=1, cg_iters=1)
     t = []
     for _ in range(args.steps):
-        g, dt = oracle_dslash_sample(1)
-        t.append(dt)
+        s = oracle_sample(ncores, n_hop=2, cg_iters=1)
+        t.append(s["s_per_hemi_dslash"])
     dt = sum(t) / len(t)
     import numpy as np
     Vh = int(np.prod(LAT)) // 2
-    val = Vh * (8 * 18 * 8 + 24 * 8 * 2) / dt / 1e9
+    val = Vh * REF_BYTES_PER_SITE / dt / 1e9
     out = {"impl": "reference", "metric": METRIC, "value": round(val, 3), "unit": "GB/s",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(dt * 1e3, 1), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"hmc-trajectory {lat_name()} kappa=0.1575 beta=5.6 kappa^4-filter",
-                      "sample": "one FP64 oracle hemi-Dslash of the lattice per step"},
-           "cpu_baseline": {"value": round(val, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                            "sample": f"one hemi-Dslash of {lat_name()} per step, single thread"},
+           "config": {"workload": (f"FP64 oracle hemi-Dslash applications on {lat_name()} "
+                                   f"({s['threads']} host threads), counted at "
+                                   f"{REF_BYTES_PER_SITE} B per output site (the FP32-12 "
+                                   "hemi-Dslash's algorithmic bytes)"),
+                      "sample": "per step: two oracle hemi-Dslash applications, one Mhat "
+                                "and one CG iteration"},
+           "cpu_baseline": {"value": round(val, 3), "unit": "GB/s", "cores": s["threads"],
+                            "kind": "oracle", "nproc": ncores,
+                            "sample": f"hemi-Dslash applications of {lat_name()}, "
+                                      f"{s['threads']} threads"},
            "e2e": {"value": round(val, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)

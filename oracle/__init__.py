@@ -45,6 +45,11 @@ def threads():
     return int(l.or_threads())
 
 
+def set_threads(n):
+    """Use n threads in the oracle's parallel loops from now on."""
+    lib().or_set_threads(int(n))
+
+
 _lib = None
 
 
@@ -89,6 +94,7 @@ def _declare(l):
     sig = {
         "or_volume": (_L, [_P]),
         "or_threads": (_I, []),
+        "or_set_threads": (None, [_I]),
         "or_neighbour": (_L, [_P, _L, _I, _I, _P]),
         "or_site_of_half": (_L, [_P, _I, _L]),
         "or_gamma": (None, [_I, _P]),

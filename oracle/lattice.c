@@ -20,6 +20,15 @@ int or_threads(void) {
 #endif
 }
 
+/* use n threads in later parallel loops (no effect without OpenMP) */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 long or_volume(const int L[4]) {
   return (long)L[0] * L[1] * L[2] * L[3];
 }

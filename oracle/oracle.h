@@ -52,6 +52,7 @@ static inline double or_sum_total(const or_sum *a) { return a->s + a->c; }
 
 /* ---- geometry (lattice.c) ------------------------------------------------ */
 int or_threads(void);
+void or_set_threads(int n);
 long or_volume(const int L[4]);
 void or_coords(const int L[4], long site, int c[4]);
 long or_site(const int L[4], const int c[4]);

@@ -118,23 +118,28 @@ def traj_kwargs(cfg, hmc):
     return kw
 
 
-def relax_pure_gauge(ctx, L, Ud, beta, n_traj, n_steps, seed):
+def relax_pure_gauge(ctx, L, Ud, beta, n_traj, n_steps, seed, device_rng=False):
     """Pure-gauge HMC (leapfrog, tau = 1) through the C ABI: gauge force,
     momentum and link updates, Wilson action.  Relaxes a synthetic start
     towards an equilibrium gauge field: the first half of the trajectories
     are always kept (molecular-dynamics relaxation from far out of
     equilibrium), the second half pass a Metropolis test on the host.
-    Momenta from the seeded host generator.  Returns (acceptance of the
-    second half, plaquette)."""
+    Momenta from the seeded host generator, or with device_rng from the
+    library's counter-based generator (key seed, counter = trajectory).
+    Returns (acceptance of the second half, plaquette)."""
     from . import hmc
     from . import inputs as I
     rng = np.random.default_rng(seed)
     F = ctx.new_algebra(L)
     Ub = ctx.new_gauge(L, hmc.F64, hmc.LINK18)
+    Pd = ctx.new_algebra(L) if device_rng else None
     dt = 1.0 / n_steps
     acc = 0
     for t in range(n_traj):
-        P = ctx.pack_algebra(L, I.momenta(L, seed + 1000 + t))
+        if device_rng:
+            P = ctx.random_momenta(L, seed, t, P=Pd)
+        else:
+            P = ctx.pack_algebra(L, I.momenta(L, seed + 1000 + t))
         Ub.data.copy_(Ud.data)
         H0 = ctx.kinetic(L, P) + ctx.force_hopexp(L, Ud, beta, 0.0, 0)
         F.data.zero_()

@@ -53,9 +53,13 @@ def test_mhat_noalloc_matches_mhat(H, prec, variant):
         for call, dagger in enumerate((False, True)):
             psi = I.gaussian_half(L, 20 + call, n_rhs if n_rhs > 1 else None)
             src = ctx.pack_spinor(L, psi, prec)
+            # both outputs zeroed first: the padding after a field's last
+            # chunk (half storage rounds its size up) is never written
             want_f = ctx.new_spinor(L, prec, n_rhs)
+            want_f.data.zero_()
             ctx.mhat(L, Ud, want_f, src, kappa, dagger)
             got_f = ctx.new_spinor(L, prec, n_rhs)
+            got_f.data.zero_()
             launches = ctx.launches()
             st = _noalloc(H, ctx, L, Ud, got_f, src, kappa, dagger)
             assert st == 0, H.lib().hmc_last_error(ctx.h)
