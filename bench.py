@@ -51,8 +51,6 @@ WORK = dict(beta=5.6, kappa=0.1575, tau=1.0, n_md=10, n_gauge=4, filter_k=2, n_t
             tol_md=1e-10, tol_action=1e-12)
 EPS_LINKS = 0.3
 FLUSH_BYTES = 256 << 20  # > 129 MB L2
-FP64_PEAK_GFLOPS = 1250.0  # nominal dense FP64 of GB300 (no measured figure in the peaks file)
-FP64_PEAK_SOURCE = "nominal FP64 rate of GB300 (recipe table)"
 RELAX_BETA = 5.85  # pure-gauge beta of the relaxation (plaquette ~0.577, near beta 5.6 dynamical)
 
 
@@ -229,11 +227,17 @@ def run_kernel(args):
     torch.cuda.synchronize()
     n, ms, byt = next(iter(ctx.timing().values()))
     Vh = int(np.prod(LAT)) // 2
+    pk = peaks()
+    gbs = byt / (ms * 1e-3) / 1e9
     print(json.dumps({"kernel": args.kernel, "variant": args.variant, "rhs": nr,
                       "launches": n, "us_per_launch": round(ms / n * 1e3, 2),
                       "us_per_rhs": round(ms / n * 1e3 / nr, 2),
-                      "GBs": round(byt / (ms * 1e-3) / 1e9, 1),
-                      "TFLOPs": round(1320.0 * Vh * nr * n / (ms * 1e-3) / 1e12, 3)}), flush=True)
+                      "GBs": round(gbs, 1),
+                      "hbm_frac": round(gbs / pk["hbm_gbs"], 4) if pk else None,
+                      "TFLOPs": round(1320.0 * Vh * nr * n / (ms * 1e-3) / 1e12, 3),
+                      "fma_peaks_tflops": {k: round(ctx.fma_peak(i), 2) for i, k in
+                                           enumerate(("fp64", "fp32", "fp32x2"))}}),
+          flush=True)
 
 
 def peaks():
@@ -368,6 +372,8 @@ def run_hmc(args):
 
     inner = hmc.F16 if args.inner == "f16" else hmc.F32
     ctx = hmc.Context(local)
+    # measured CUDA-core FMA ceilings (the arithmetic rooflines)
+    fma = {k: round(ctx.fma_peak(i), 2) for i, k in enumerate(("fp64", "fp32", "fp32x2"))}
     # autotuned hemi-Dslash variants (tuned during the warm-up steps)
     ctx.set_dslash_variant(-2 if args.variant is None else args.variant)
     n_eta = len(KAPPA_MP) + 1 if args.mp else (2 * args.rooted + 1 if args.rooted else 1)
@@ -477,10 +483,13 @@ def run_hmc(args):
     pk = peaks()
     if dom.startswith("dslash_f64"):
         achieved = 1320.0 * Vh * n_dom / (ms_dom * 1e-3) / 1e9
+        # native FP64 against the measured FP64 FMA rate, emulated FP64 (on the
+        # FP32 pipe) against the measured FP32 rate
+        pk64 = fma["fp32" if dom.startswith("dslash_f64e") else "fp64"] * 1e3
         roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 1),
-                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": None,
-                "peak_source": FP64_PEAK_SOURCE}
+                "peak": pk64, "unit": "GFLOP/s",
+                "frac": round(achieved / pk64, 4), "traffic": None,
+                "peak_source": "measured (hmc_measure_fma_peak)"}
     else:
         achieved = b_dom / (ms_dom * 1e-3) / 1e9
         peak = pk["hbm_gbs"] if pk else 6800.0
@@ -525,6 +534,7 @@ def run_hmc(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    **({"start": start} if start else {})},
         "roofline": roof,
+        "fma_peaks_tflops": fma,
         "gpu_launches": launches,
         "kernels": kernels,
         "trajectory": {"s": round(ms_step / 1e3, 4), "s_each": [round(x / 1e3, 4) for x in times],

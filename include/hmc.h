@@ -122,9 +122,17 @@ int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
  * variant: bit 0 maps each block of 128 threads onto four 32-site segments
  * at the offsets {0, +x, +t, +x+t} (when Ly*Lz/2 is a multiple of 32 and
  * n_rhs == 1; otherwise consecutive sites), bit 1 issues the loads of both
- * hops of a direction before their arithmetic.  Every variant computes the
- * same result bit for bit.  Default -1: paired loads for LINK18 only (the
- * fastest choice measured on 24^3 x 48).  -2: autotune: the first launch of
+ * hops of a direction before their arithmetic.  Variants 0..3 compute the
+ * same result bit for bit.  Values 4, 5, 6 select, for n_rhs > 1 and FP32 or
+ * FP16 storage, the multi-right-hand-side kernel with 2, 3 or 4 right-hand
+ * sides per thread (each link loaded, rebuilt and indexed once for them,
+ * packed paired-FP32 arithmetic; exact on exactly representable inputs,
+ * otherwise within FP32 rounding of the other variants); where the count
+ * does not divide n_rhs the built-in default is used.  Default -1: for
+ * n_rhs > 1 in FP32/FP16 the multi-right-hand-side kernel with 2 (else 3)
+ * per thread where that divides n_rhs, otherwise paired loads for LINK18
+ * only (the fastest choice measured on 24^3 x 48).  -2: autotune: the first
+ * launch of
  * each class (precision, link format, dagger, n_rhs, lattice) that can be
  * repeated without changing its result times every applicable variant (one
  * warm-up and three timed launches each, synchronising the stream) and the
@@ -138,7 +146,7 @@ int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
  * before its next work; 0 launches every kernel on the caller's stream.
  * Results are bit-identical.  Graphs are not used while timing is enabled. */
 #define HMC_OPT_CG_GRAPH 2
-/* Sets option (HMC_OPT_DSLASH_VARIANT: -2..3, HMC_OPT_CG_GRAPH: 0 or 1) for
+/* Sets option (HMC_OPT_DSLASH_VARIANT: -2..6, HMC_OPT_CG_GRAPH: 0 or 1) for
  * every later call on ctx.  HMC_EINVAL for an unknown option or value. */
 int hmc_ctx_set_option(hmc_ctx *ctx, int option, int value);
 /* Statistics of the index-th kernel class seen since timing was enabled:
@@ -147,6 +155,18 @@ int hmc_ctx_set_option(hmc_ctx *ctx, int option, int value);
  * last class. */
 int hmc_timing_get(hmc_ctx *ctx, int index, char *name, int name_len,
                    long long *launches, double *total_ms, double *bytes);
+
+/* hmc_measure_fma_peak: measured CUDA-core multiply-add throughput of the
+ * context's device in TFLOP/s (2 flops per FMA, 4 per paired FMA), for the
+ * arithmetic rooflines of the kernels that are not bound by memory: kind 0
+ * FP64 (the native-FP64 hemi-Dslash of the plain FP64 path), 1 FP32 (the
+ * double-float kernels of emulated FP64), 2 paired FP32 (fma.rn.f32x2, the
+ * packed arithmetic of the multi-right-hand-side hemi-Dslash).  A
+ * measurement utility with no counterpart in the paper: independent FMA
+ * chains on every SM, event-timed on the context's stream, best of three
+ * launches after one warm-up (~10 ms).  Synchronises the stream.
+ * HMC_EINVAL for another kind. */
+int hmc_measure_fma_peak(hmc_ctx *ctx, int kind, double *tflops);
 
 /* ---- sizes (host-only, no GPU needed) ---------------------------------------- */
 
@@ -225,9 +245,11 @@ int hmc_mhat(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U,
  * overlap on the GPU (other streams, other host threads) race on it.  The
  * context's optional event timing and the Dslash autotuner (option
  * HMC_OPT_DSLASH_VARIANT = -2) are bypassed for this call: it creates no
- * events, never synchronises the stream, and an autotuning context runs the
- * built-in default variant (every variant computes the same result bit for
- * bit, so the output equals hmc_mhat's). */
+ * events and never synchronises the stream; an autotuning context runs the
+ * variant already tuned for the launch class, else the built-in default, so
+ * the output equals hmc_mhat's bit for bit once hmc_mhat has run the same
+ * class (before that, a multi-right-hand-side class may differ from it by
+ * FP32 rounding). */
 #define HMC_MHAT_NOALLOC_MAX_BYTES ((size_t)64 << 20)
 int hmc_mhat_noalloc(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U,
                      void *out, const void *in, double kappa, int dagger, int prec,

@@ -79,6 +79,7 @@ class TrajParams(ctypes.Structure):
         ("n_mp", _I), ("kappa_mp", _P),
         ("integrator", _I), ("lam", _D),
         ("root_levels", _I), ("root_N", _I), ("root_deg", _P), ("root_c", _P),
+        ("n_levels", _I), ("level_steps", _I * 8), ("term_level", _P),
     ]
 
 
@@ -94,6 +95,9 @@ def _declare(l):
     sig = {
         "or_volume": (_L, [_P]),
         "or_threads": (_I, []),
+        "or_fratio_action": (_D, [_P, _P, _D, _P, _I, _D, _D, _P, _D]),
+        "or_fratio_force": (None, [_P, _P, _D, _P, _I, _D, _D, _P, _D, _D, _P]),
+        "or_fratio_heatbath": (None, [_P, _P, _D, _P, _I, _D, _P, _D, _P]),
         "or_set_threads": (None, [_I]),
         "or_neighbour": (_L, [_P, _L, _I, _I, _P]),
         "or_site_of_half": (_L, [_P, _I, _L]),
@@ -408,14 +412,26 @@ def kinetic(L, P):
 
 def _params(beta, kappa, tau, n_md, n_gauge, filter_k=0, n_t=0, n_max=0,
             tol_md=1e-12, tol_action=1e-13, b=None, c=None, alpha=0.0, kappa_mp=None,
-            integrator=0, lam=1.0 / 6.0, root_polys=None, root_N=0):
+            integrator=0, lam=1.0 / 6.0, root_polys=None, root_N=0, level_steps=None,
+            term_level=None):
     """kappa_mp: heavier hopping parameters of a mass-preconditioned chain;
-    eta / phi then carry len(kappa_mp) + 1 half fields ([n, Vh, 4, 3]).
-    integrator: 0 leapfrog, 1 Omelyan with parameter lam."""
+    eta / phi then carry the heavy terms' fields and the target group's
+    ([n, Vh, 4, 3]).  integrator: 0 leapfrog, 1 Omelyan with parameter lam.
+    level_steps: m_0 .. m_{J-2} of a J-level Sexton-Weingarten scheme (gauge
+    on level 0; None: two levels with m_0 = n_gauge); term_level: the level
+    of each pseudo-fermion field (None: the outermost)."""
     keep = []
     p = TrajParams(beta=beta, kappa=kappa, tau=tau, n_md=n_md, n_gauge=n_gauge,
                    filter_k=filter_k, n_t=n_t, n_max=n_max, tol_md=tol_md,
                    tol_action=tol_action, alpha=alpha, integrator=integrator, lam=lam)
+    if level_steps is not None:
+        assert 1 <= len(level_steps) <= 7
+        p.n_levels = len(level_steps) + 1
+        for i, m in enumerate(level_steps):
+            p.level_steps[i] = int(m)
+    if term_level is not None:
+        tl = np.ascontiguousarray(term_level, dtype=np.int32); keep.append(tl)
+        p.term_level = tl.ctypes.data
     if kappa_mp:
         km = _c(kappa_mp, np.float64); keep.append(km)
         p.n_mp = len(km)
@@ -434,6 +450,33 @@ def _params(beta, kappa, tau, n_md, n_gauge, filter_k=0, n_t=0, n_max=0,
     if c is not None:
         c = _c(c, np.float64); keep.append(c); p.c = c.ctypes.data
     return p, keep
+
+
+def fratio_action(L, U, kappa, b, alpha, kappa_a, phi, tol=1e-13, n=None):
+    """|Z Mhat(kappa_a) phi|^2 with Z = alpha Mhat^{-1} + sum_{j<=n} b_j K^j."""
+    U = _c(U, np.complex128); phi = _c(phi, np.complex128); b = _c(b, np.float64)
+    n = len(b) - 1 if n is None else n
+    return lib().or_fratio_action(_dims(L), _ptr(U), kappa, _ptr(b), n, alpha, kappa_a,
+                                  _ptr(phi), tol)
+
+
+def fratio_force(L, U, kappa, b, alpha, kappa_a, phi, tol=1e-13, n_t=None, coeff=1.0):
+    """Force of the filtered ratio term (truncation n_t), canonical [V, 4, 8]."""
+    U = _c(U, np.complex128); phi = _c(phi, np.complex128); b = _c(b, np.float64)
+    n_t = len(b) - 1 if n_t is None else n_t
+    F = np.zeros((volume(L), 4, 8))
+    lib().or_fratio_force(_dims(L), _ptr(U), kappa, _ptr(b), n_t, alpha, kappa_a, _ptr(phi),
+                          tol, coeff, _ptr(F))
+    return F
+
+
+def fratio_heatbath(L, U, kappa, c, kappa_a, eta, tol=1e-13):
+    """phi = Mhat(kappa_a)^{-1} Mhat sum_n c_n K^n eta."""
+    U = _c(U, np.complex128); eta = _c(eta, np.complex128); c = _c(c, np.float64)
+    phi = np.zeros_like(eta)
+    lib().or_fratio_heatbath(_dims(L), _ptr(U), kappa, _ptr(c), len(c) - 1, kappa_a, _ptr(eta),
+                             tol, _ptr(phi))
+    return phi
 
 
 def hamiltonian(L, U, P, phi, **kw):

@@ -120,39 +120,73 @@ double or_kinetic(const int L[4], const double *P) {
   return 0.5 * or_sum_total(&s);
 }
 
-/* hopping parameters (kappa_a, kappa_b) of pseudo-fermion term j of a
- * mass-preconditioned chain (kappa_a = 0: the plain term) */
-static void mp_pair(const or_traj_params *p, int j, double *ka, double *kb) {
-  *ka = j == 0 ? 0.0 : p->kappa_mp[j - 1];
-  *kb = j < p->n_mp ? p->kappa_mp[j] : p->kappa;
+/* ---- the pseudo-fermion terms, in the order of eta's fields -------------
+ * f < n_mp: the heavy terms of the mass-preconditioning chain, S_PF(k_0)
+ * and S_R(k_{f-1}, k_f); then the target group at kappa with
+ * kappa_a = k_{n_mp-1} (0 without mass preconditioning): the ratio term
+ * S_R(kappa_a, kappa), or the filtered ratio term (filter_k > 0), or the
+ * rooted polynomials |P_j phi|^2 (root_N fields each) and the remainder in
+ * the filtered ratio form. */
+static int n_target(const or_traj_params *p) {
+  return p->root_levels > 0 ? p->root_levels * p->root_N + 1 : 1;
+}
+static int n_terms(const or_traj_params *p) { return p->n_mp + n_target(p); }
+static double target_ka(const or_traj_params *p) {
+  return p->n_mp > 0 ? p->kappa_mp[p->n_mp - 1] : 0.0;
+}
+/* kinds: 0 ratio (ka, kb), 1 rooted polynomial j, 2 filtered ratio */
+static int term_kind(const or_traj_params *p, int f, double *ka, double *kb, int *j) {
+  if (f < p->n_mp) {
+    *ka = f == 0 ? 0.0 : p->kappa_mp[f - 1];
+    *kb = p->kappa_mp[f];
+    return 0;
+  }
+  const int t = f - p->n_mp;
+  *ka = target_ka(p);
+  *kb = p->kappa;
+  if (p->root_levels > 0 && t < p->root_levels * p->root_N) {
+    *j = t / p->root_N;
+    return 1;
+  }
+  return (p->root_levels > 0 || p->filter_k > 0) ? 2 : 0;
+}
+
+static double term_action(const int L[4], const ocplx *U, const ocplx *phi,
+                          const or_traj_params *p, int f) {
+  double ka, kb;
+  int j = 0;
+  switch (term_kind(p, f, &ka, &kb, &j)) {
+    case 0: return or_ratio_action(L, U, ka, kb, phi, p->tol_action);
+    case 1:
+      return or_filtered_action(L, U, p->kappa, p->root_c[j], p->root_deg[j], 0.0, phi,
+                                p->tol_action);
+    default:
+      return or_fratio_action(L, U, p->kappa, p->b, p->n_max, p->alpha, ka, phi,
+                              p->tol_action);
+  }
+}
+
+static void term_force(const int L[4], const ocplx *U, const ocplx *phi,
+                       const or_traj_params *p, int f, double *F) {
+  double ka, kb;
+  int j = 0;
+  switch (term_kind(p, f, &ka, &kb, &j)) {
+    case 0: or_ratio_force(L, U, ka, kb, phi, p->tol_md, 1.0, F); break;
+    case 1:
+      or_filtered_force(L, U, p->kappa, p->root_c[j], p->root_deg[j], 0.0, phi, p->tol_md, 1.0,
+                        F);
+      break;
+    default:
+      or_fratio_force(L, U, p->kappa, p->b, p->n_t, p->alpha, ka, phi, p->tol_md, 1.0, F);
+  }
 }
 
 static double fermion_action(const int L[4], const ocplx *U, const ocplx *phi,
                              const or_traj_params *p) {
-  if (p->root_levels > 0) {
-    long n12 = or_volume(L) / 2 * 12;
-    double s = 0;
-    int f = 0;
-    for (int j = 0; j < p->root_levels; ++j)
-      for (int i = 0; i < p->root_N; ++i, ++f)
-        s += or_filtered_action(L, U, p->kappa, p->root_c[j], p->root_deg[j], 0.0,
-                                phi + f * n12, p->tol_action);
-    return s + or_filtered_action(L, U, p->kappa, p->b, p->n_max, p->alpha, phi + f * n12,
-                                  p->tol_action);
-  }
-  if (p->n_mp > 0) {
-    long n12 = or_volume(L) / 2 * 12;
-    double s = 0;
-    for (int j = 0; j <= p->n_mp; ++j) {
-      double ka, kb;
-      mp_pair(p, j, &ka, &kb);
-      s += or_ratio_action(L, U, ka, kb, phi + j * n12, p->tol_action);
-    }
-    return s;
-  }
-  if (p->filter_k == 0) return or_pf_action(L, U, p->kappa, phi, p->tol_action);
-  return or_filtered_action(L, U, p->kappa, p->b, p->n_max, p->alpha, phi,
-                            p->tol_action);
+  long n12 = or_volume(L) / 2 * 12;
+  double s = 0;
+  for (int f = 0; f < n_terms(p); ++f) s += term_action(L, U, phi + f * n12, p, f);
+  return s;
 }
 
 double or_hamiltonian(const int L[4], const ocplx *U, const double *P,
@@ -166,103 +200,83 @@ static void momentum_step(long nP, double *P, const double *F, double dt) {
   for (long i = 0; i < nP; ++i) P[i] -= dt * F[i];
 }
 
-static void gauge_force(const int L[4], const ocplx *U,
-                        const or_traj_params *p, double *F) {
-  long nP = or_volume(L) * 32;
+/* ---- Sexton-Weingarten levels ------------------------------------------- */
+static int n_level(const or_traj_params *p) { return p->n_levels > 0 ? p->n_levels : 2; }
+static int level_m(const or_traj_params *p, int i) {
+  return p->n_levels > 0 ? p->level_steps[i] : p->n_gauge;
+}
+static int term_level(const or_traj_params *p, int f) {
+  return p->term_level ? p->term_level[f] : n_level(p) - 1;
+}
+
+/* F = the force of the action terms on level l (0: gauge with T_k) */
+static void level_force(const int L[4], const ocplx *U, const ocplx *phi,
+                        const or_traj_params *p, int l, double *F) {
+  long nP = or_volume(L) * 32, n12 = or_volume(L) / 2 * 12;
   memset(F, 0, nP * sizeof(double));
-  or_gauge_force(L, U, p->beta, 1.0, F);
-  if (p->filter_k > 0) or_hopexp_force(L, U, p->kappa, p->filter_k, 1.0, F);
-}
-
-static void fermion_force(const int L[4], const ocplx *U, const ocplx *phi,
-                          const or_traj_params *p, double *F) {
-  long nP = or_volume(L) * 32;
-  memset(F, 0, nP * sizeof(double));
-  if (p->root_levels > 0) {
-    long n12 = or_volume(L) / 2 * 12;
-    int f = 0;
-    for (int j = 0; j < p->root_levels; ++j)
-      for (int i = 0; i < p->root_N; ++i, ++f)
-        or_filtered_force(L, U, p->kappa, p->root_c[j], p->root_deg[j], 0.0, phi + f * n12,
-                          p->tol_md, 1.0, F);
-    or_filtered_force(L, U, p->kappa, p->b, p->n_t, p->alpha, phi + f * n12, p->tol_md, 1.0, F);
-  } else if (p->n_mp > 0) {
-    long n12 = or_volume(L) / 2 * 12;
-    for (int j = 0; j <= p->n_mp; ++j) {
-      double ka, kb;
-      mp_pair(p, j, &ka, &kb);
-      or_ratio_force(L, U, ka, kb, phi + j * n12, p->tol_md, 1.0, F);
-    }
-  } else if (p->filter_k == 0)
-    or_pf_force(L, U, p->kappa, phi, p->tol_md, 1.0, F);
-  else
-    or_filtered_force(L, U, p->kappa, p->b, p->n_t, p->alpha, phi, p->tol_md,
-                      1.0, F);
-}
-
-/* leapfrog T_L on two time scales, every force evaluated where the scheme
- * places its momentum step (no merging) */
-static void md_leapfrog(const int L[4], ocplx *U, double *P, const ocplx *phi,
-                        const or_traj_params *p, double *F) {
-  long nP = or_volume(L) * 32;
-  double dt = p->tau / p->n_md, dt0 = dt / p->n_gauge;
-  for (int s = 0; s < p->n_md; ++s) {
-    fermion_force(L, U, phi, p, F);
-    momentum_step(nP, P, F, 0.5 * dt);
-    for (int g = 0; g < p->n_gauge; ++g) {
-      gauge_force(L, U, p, F);
-      momentum_step(nP, P, F, 0.5 * dt0);
-      or_update_links(L, U, P, dt0);
-      gauge_force(L, U, p, F);
-      momentum_step(nP, P, F, 0.5 * dt0);
-    }
-    fermion_force(L, U, phi, p, F);
-    momentum_step(nP, P, F, 0.5 * dt);
+  if (l == 0) {
+    or_gauge_force(L, U, p->beta, 1.0, F);
+    if (p->filter_k > 0) or_hopexp_force(L, U, p->kappa, p->filter_k, 1.0, F);
+    return;
   }
+  for (int f = 0; f < n_terms(p); ++f)
+    if (term_level(p, f) == l) term_force(L, U, phi + f * n12, p, f, F);
 }
 
-/* T_SW,0: the Omelyan step of the gauge force alone,
- * P_0(lambda dt0) T(dt0/2) P_0((1-2 lambda) dt0) T(dt0/2) P_0(lambda dt0) */
-static void omelyan_fine(const int L[4], ocplx *U, double *P,
-                         const or_traj_params *p, double dt0, double *F) {
-  long nP = or_volume(L) * 32;
-  double lam = p->lambda;
-  gauge_force(L, U, p, F);
-  momentum_step(nP, P, F, lam * dt0);
-  or_update_links(L, U, P, 0.5 * dt0);
-  gauge_force(L, U, p, F);
-  momentum_step(nP, P, F, (1.0 - 2.0 * lam) * dt0);
-  or_update_links(L, U, P, 0.5 * dt0);
-  gauge_force(L, U, p, F);
-  momentum_step(nP, P, F, lam * dt0);
+/* P_l(eps): the momentum step of level l, its force evaluated at U */
+static void p_step(const int L[4], const ocplx *U, double *P, const ocplx *phi,
+                   const or_traj_params *p, int l, double eps, double *F) {
+  level_force(L, U, phi, p, l, F);
+  momentum_step(or_volume(L) * 32, P, F, eps);
 }
 
-/* T_SW,1 = P_1(lambda dt) [T_SW,0]^m P_1((1-2 lambda) dt) [T_SW,0]^m
- * P_1(lambda dt) with dt = 2 m dt0 (m = n_gauge) */
-static void md_omelyan(const int L[4], ocplx *U, double *P, const ocplx *phi,
-                       const or_traj_params *p, double *F) {
-  long nP = or_volume(L) * 32;
-  double lam = p->lambda, dt = p->tau / p->n_md, dt0 = dt / (2.0 * p->n_gauge);
-  for (int s = 0; s < p->n_md; ++s) {
-    fermion_force(L, U, phi, p, F);
-    momentum_step(nP, P, F, lam * dt);
-    for (int g = 0; g < p->n_gauge; ++g) omelyan_fine(L, U, P, p, dt0, F);
-    fermion_force(L, U, phi, p, F);
-    momentum_step(nP, P, F, (1.0 - 2.0 * lam) * dt);
-    for (int g = 0; g < p->n_gauge; ++g) omelyan_fine(L, U, P, p, dt0, F);
-    fermion_force(L, U, phi, p, F);
-    momentum_step(nP, P, F, lam * dt);
+/* one step T_SW,l of size dt, every force evaluated where the scheme places
+ * its momentum step (no merging).  Leapfrog:
+ *   T_0 = P_0(dt/2) T(dt) P_0(dt/2),  T_l = P_l(dt/2) [T_{l-1}]^m P_l(dt/2);
+ * Omelyan (parameter lambda):
+ *   T_0 = P_0(l dt) T(dt/2) P_0((1-2l) dt) T(dt/2) P_0(l dt),
+ *   T_l = P_l(l dt) [T_{l-1}]^m P_l((1-2l) dt) [T_{l-1}]^m P_l(l dt),
+ * m = m_{l-1}, the inner step dt / m (leapfrog) or dt / (2 m) (Omelyan). */
+static void sw_step(const int L[4], ocplx *U, double *P, const ocplx *phi,
+                    const or_traj_params *p, int l, double dt, double *F) {
+  if (p->integrator == 1) {
+    const double lam = p->lambda;
+    if (l == 0) {
+      p_step(L, U, P, phi, p, 0, lam * dt, F);
+      or_update_links(L, U, P, 0.5 * dt);
+      p_step(L, U, P, phi, p, 0, (1.0 - 2.0 * lam) * dt, F);
+      or_update_links(L, U, P, 0.5 * dt);
+      p_step(L, U, P, phi, p, 0, lam * dt, F);
+      return;
+    }
+    const int m = level_m(p, l - 1);
+    const double di = dt / (2.0 * m);
+    p_step(L, U, P, phi, p, l, lam * dt, F);
+    for (int g = 0; g < m; ++g) sw_step(L, U, P, phi, p, l - 1, di, F);
+    p_step(L, U, P, phi, p, l, (1.0 - 2.0 * lam) * dt, F);
+    for (int g = 0; g < m; ++g) sw_step(L, U, P, phi, p, l - 1, di, F);
+    p_step(L, U, P, phi, p, l, lam * dt, F);
+    return;
   }
+  if (l == 0) {
+    p_step(L, U, P, phi, p, 0, 0.5 * dt, F);
+    or_update_links(L, U, P, dt);
+    p_step(L, U, P, phi, p, 0, 0.5 * dt, F);
+    return;
+  }
+  const int m = level_m(p, l - 1);
+  const double di = dt / m;
+  p_step(L, U, P, phi, p, l, 0.5 * dt, F);
+  for (int g = 0; g < m; ++g) sw_step(L, U, P, phi, p, l - 1, di, F);
+  p_step(L, U, P, phi, p, l, 0.5 * dt, F);
 }
 
 void or_md_evolve(const int L[4], ocplx *U, double *P, const ocplx *phi,
                   const or_traj_params *p, int *cg_iters) {
   long nP = or_volume(L) * 32;
   double *F = malloc(nP * sizeof(double));
-  if (p->integrator == 1)
-    md_omelyan(L, U, P, phi, p, F);
-  else
-    md_leapfrog(L, U, P, phi, p, F);
+  const double dt = p->tau / p->n_md;
+  for (int s = 0; s < p->n_md; ++s) sw_step(L, U, P, phi, p, n_level(p) - 1, dt, F);
   if (cg_iters) *cg_iters = 0;
   free(F);
 }
@@ -271,58 +285,57 @@ int or_trajectory(const int L[4], ocplx *U, const double *P0, const ocplx *eta,
                   double u_metropolis, const or_traj_params *p,
                   or_traj_result *res, ocplx *U_out, double *P_out) {
   long V = or_volume(L), n12 = V / 2 * 12, nU = V * 4 * 9, nP = V * 32;
-  const int n_terms = p->root_levels > 0 ? p->root_levels * p->root_N + 1
-                      : (p->n_mp > 0 ? p->n_mp + 1 : 1);
-  ocplx *phi = malloc(n_terms * n12 * sizeof(ocplx));
+  const int nt = n_terms(p);
+  ocplx *phi = malloc(nt * n12 * sizeof(ocplx));
   ocplx *U1 = malloc(nU * sizeof(ocplx));
   double *P = malloc(nP * sizeof(double));
   memcpy(U1, U, nU * sizeof(ocplx));
   memcpy(P, P0, nP * sizeof(double));
-  /* heatbath of the pseudo-fermion field */
-  double H0;
-  if (p->root_levels > 0) {
-    /* polynomial terms: phi = P_j^{-1} eta; remainder phi = M_{J+1} eta;
-     * H0 with the actions evaluated at the start (the remainder's heatbath
-     * series is truncated) */
-    int f = 0;
-    double rel;
-    for (int j = 0; j < p->root_levels; ++j)
-      for (int i = 0; i < p->root_N; ++i, ++f)
-        or_poly_solve(L, U, p->kappa, p->root_c[j], p->root_deg[j], eta + f * n12,
-                      phi + f * n12, p->tol_action, 100000, &rel);
-    ocplx *t = malloc(n12 * sizeof(ocplx)), *t2 = malloc(n12 * sizeof(ocplx));
-    or_poly_K(L, U, p->kappa, p->c, p->n_max, eta + f * n12, t);
-    or_mhat(L, U, p->kappa, 0, t, t2);
-    for (int j = 0; j < p->root_levels; ++j)
-      for (int q = 0; q < p->root_N; ++q) {
-        or_poly_K(L, U, p->kappa, p->root_c[j], p->root_deg[j], t2, t);
-        memcpy(t2, t, n12 * sizeof(ocplx));
-      }
-    memcpy(phi + f * n12, t2, n12 * sizeof(ocplx));
-    free(t); free(t2);
-    H0 = or_hamiltonian(L, U, P, phi, p);
-  } else if (p->n_mp > 0) {
-    /* phi_j = Mhat_b^dag Mhat_a^{-dag} eta_j: S_j(phi_j) = |eta_j|^2 */
-    or_sum e2 = {0, 0};
-    for (int j = 0; j < n_terms; ++j) {
-      double ka, kb;
-      mp_pair(p, j, &ka, &kb);
-      or_ratio_heatbath(L, U, ka, kb, eta + j * n12, p->tol_action, phi + j * n12);
+  /* heatbath of every pseudo-fermion field; H0 takes |eta_f|^2 for the
+   * terms whose heatbath is exact (ratio terms, the plain action) and the
+   * action itself, evaluated at the start, for the filtered and rooted
+   * ones (their heatbath series is truncated) */
+  or_sum h0 = {0, 0};
+  for (int f = 0; f < nt; ++f) {
+    const ocplx *e = eta + f * n12;
+    ocplx *ph = phi + f * n12;
+    double ka, kb;
+    int j = 0;
+    const int kind = term_kind(p, f, &ka, &kb, &j);
+    if (kind == 0) {
+      or_ratio_heatbath(L, U, ka, kb, e, p->tol_action, ph);
+      for (long i = 0; i < n12; ++i) or_sum_add(&h0, creal(conj(e[i]) * e[i]));
+      continue;
     }
-    for (long i = 0; i < n_terms * n12; ++i) or_sum_add(&e2, creal(conj(eta[i]) * eta[i]));
-    H0 = or_kinetic(L, P) + or_gauge_action(L, U, p->beta) + or_sum_total(&e2);
-  } else if (p->filter_k == 0) {
-    or_mhat(L, U, p->kappa, 1, eta, phi); /* phi = Mhat^dag eta */
-    or_sum e2 = {0, 0};
-    for (long i = 0; i < n12; ++i) or_sum_add(&e2, creal(conj(eta[i]) * eta[i]));
-    H0 = or_kinetic(L, P) + or_gauge_action(L, U, p->beta) + or_sum_total(&e2);
-  } else {
-    ocplx *t = malloc(n12 * sizeof(ocplx));
-    or_poly_K(L, U, p->kappa, p->c, p->n_max, eta, t);
-    or_mhat(L, U, p->kappa, 0, t, phi); /* phi = Mhat sum c_n K^n eta */
-    free(t);
-    H0 = or_hamiltonian(L, U, P, phi, p);
+    if (kind == 1) {
+      double rel;
+      or_poly_solve(L, U, p->kappa, p->root_c[j], p->root_deg[j], e, ph, p->tol_action, 100000,
+                    &rel);
+    } else if (p->root_levels == 0) {
+      or_fratio_heatbath(L, U, p->kappa, p->c, p->n_max, ka, e, p->tol_action, ph);
+    } else {
+      /* remainder: phi = Mhat_a^{-1} prod_j P_j^N Mhat sum c_n K^n eta */
+      ocplx *t = malloc(n12 * sizeof(ocplx)), *t2 = malloc(n12 * sizeof(ocplx));
+      or_poly_K(L, U, p->kappa, p->c, p->n_max, e, t);
+      or_mhat(L, U, p->kappa, 0, t, t2);
+      for (int q = 0; q < p->root_levels; ++q)
+        for (int r = 0; r < p->root_N; ++r) {
+          or_poly_K(L, U, p->kappa, p->root_c[q], p->root_deg[q], t2, t);
+          memcpy(t2, t, n12 * sizeof(ocplx));
+        }
+      if (ka == 0.0) {
+        memcpy(ph, t2, n12 * sizeof(ocplx));
+      } else {
+        double rel;
+        or_mhat(L, U, ka, 1, t2, t);
+        or_cg(L, U, ka, t, ph, p->tol_action, 100000, &rel);
+      }
+      free(t); free(t2);
+    }
+    or_sum_add(&h0, term_action(L, U, ph, p, f));
   }
+  double H0 = or_kinetic(L, P) + or_gauge_action(L, U, p->beta) + or_sum_total(&h0);
+  if (p->filter_k > 0) H0 += or_hopexp_action(L, U, p->kappa, p->filter_k);
   res->plaq0 = or_plaquette_sum(L, U) / (18.0 * V);
   or_md_evolve(L, U1, P, phi, p, &res->cg_iters);
   double H1 = or_hamiltonian(L, U1, P, phi, p);

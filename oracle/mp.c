@@ -87,10 +87,9 @@ static void join(const int L[4], const ocplx *even, const ocplx *odd,
   }
 }
 
-/* F += coeff * sign * force of Re[chi^dag delta Mhat(kappa) v] */
-static void mhat_force(const int L[4], const ocplx *U, double kappa,
-                       const ocplx *chi, const ocplx *v, double coeff,
-                       double *F) {
+/* F += coeff * force of Re[chi^dag delta Mhat(kappa) v] */
+void or_mhat_force(const int L[4], const ocplx *U, double kappa, const ocplx *chi,
+                   const ocplx *v, double coeff, double *F) {
   long V = or_volume(L), n = half_len(L);
   ocplx *co = malloc(n * sizeof(ocplx)), *vo = malloc(n * sizeof(ocplx));
   ocplx *W = malloc(V * 12 * sizeof(ocplx)), *Vf = malloc(V * 12 * sizeof(ocplx));
@@ -119,7 +118,7 @@ void or_ratio_force(const int L[4], const ocplx *U, double kappa_a,
   or_mhat(L, U, kappa_b, 1, t, b);
   or_cg(L, U, kappa_b, b, xi, tol, 100000, &rel);
   /* 2 Re[chi^dag dMhat_a psi] - 2 Re[chi^dag dMhat_b xi] */
-  if (kappa_a != 0.0) mhat_force(L, U, kappa_a, chi, psi, 2.0 * coeff, F);
-  mhat_force(L, U, kappa_b, chi, xi, -2.0 * coeff, F);
+  if (kappa_a != 0.0) or_mhat_force(L, U, kappa_a, chi, psi, 2.0 * coeff, F);
+  or_mhat_force(L, U, kappa_b, chi, xi, -2.0 * coeff, F);
   free(chi); free(psi); free(t); free(xi); free(b);
 }

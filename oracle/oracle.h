@@ -165,6 +165,22 @@ void or_ratio_heatbath(const int L[4], const ocplx *U, double kappa_a,
                        double kappa_b, const ocplx *eta, double tol,
                        ocplx *phi);
 
+/* F += coeff * force of Re[chi^dag delta Mhat(kappa) v] (mp.c) */
+void or_mhat_force(const int L[4], const ocplx *U, double kappa, const ocplx *chi,
+                   const ocplx *v, double coeff, double *F);
+
+/* ---- filtered ratio term (fratio.c) ------------------------------------------
+ * S~_R(phi) = |Z Mhat(kappa_a) phi|^2, Z = alpha Mhat^{-1} + sum_{j<=n} b_j K^j
+ * (kappa_a = 0: the filtered action).  The force uses the truncation n_t. */
+double or_fratio_action(const int L[4], const ocplx *U, double kappa, const double *b, int n,
+                        double alpha, double kappa_a, const ocplx *phi, double tol);
+void or_fratio_force(const int L[4], const ocplx *U, double kappa, const double *b, int n_t,
+                     double alpha, double kappa_a, const ocplx *phi, double tol, double coeff,
+                     double *F);
+/* phi = Mhat_a^{-1} Mhat sum_{n<=n_max} c_n K^n eta */
+void or_fratio_heatbath(const int L[4], const ocplx *U, double kappa, const double *c,
+                        int n_max, double kappa_a, const ocplx *eta, double tol, ocplx *phi);
+
 /* ---- rooted-polynomial pseudo-fermions (rooted.c) ------------------------- */
 /* x = P(K)^{-1} b, P(K) = sum_i c_i K^i, by CG on P^dag P stopping on the
  * true residual |b - P x| / |b| <= tol; returns the iterations or -1 */
@@ -197,11 +213,16 @@ typedef struct {
    * phi = Mtilde eta = Mhat sum c_n K^n eta */
   const double *b, *c;
   double alpha;
-  /* mass preconditioning (requires filter_k == 0): n_mp >= 1 heavier
-   * hopping parameters kappa_mp[0] < ... < kappa_mp[n_mp-1] < kappa split
-   * the pseudo-fermion action into n_mp + 1 terms, S_PF(kappa_mp[0]) +
-   * S_R(kappa_mp[j-1], kappa_mp[j]) + S_R(kappa_mp[n_mp-1], kappa); eta and
-   * phi then hold n_mp + 1 consecutive half fields.  n_mp = 0: one term. */
+  /* mass preconditioning: n_mp >= 1 heavier hopping parameters
+   * kappa_mp[0] < ... < kappa_mp[n_mp-1] < kappa split the pseudo-fermion
+   * action into the heavy terms S_PF(kappa_mp[0]) + S_R(kappa_mp[j-1],
+   * kappa_mp[j]) (j < n_mp) and the target term at kappa with
+   * kappa_a = kappa_mp[n_mp-1]: S_R(kappa_a, kappa) when neither filtered
+   * nor rooted, the filtered ratio term S~_R (fratio.c) with filter_k > 0,
+   * and with root_levels > 0 the polynomial terms plus the remainder in the
+   * filtered ratio form.  eta and phi hold the heavy terms' fields first,
+   * then the target group's.  n_mp = 0: kappa_a = 0 (the plain, filtered or
+   * rooted action alone). */
   int n_mp;
   const double *kappa_mp;
   /* integrator (Sec. I): 0 leapfrog on two time scales, dt0 = dt / n_gauge;
@@ -218,10 +239,22 @@ typedef struct {
    * n_t) with b, alpha, c as for filtering; filter_k (0, 1, 2) is the order
    * of Mtilde and of T_k in the gauge action.  eta / phi hold
    * root_levels * root_N + 1 consecutive fields, the remainder last; its
-   * heatbath is phi = prod_j P_j^N Mhat sum c_n K^n eta.  Requires n_mp = 0. */
+   * heatbath is phi = Mhat_a^{-1} prod_j P_j^N Mhat sum c_n K^n eta
+   * (kappa_a from the mass-preconditioning chain, 0 without it). */
   int root_levels, root_N;
   const int *root_deg;
   const double *const *root_c;
+  /* Sexton-Weingarten levels (Sec. I): n_levels = J >= 2 levels, the gauge
+   * action (with T_k) on level 0; level_steps[i-1] = m_{i-1} steps of level
+   * i-1 inside one step of level i (i = 1 .. J-1); the outermost level
+   * J-1 takes n_md steps of dt = tau / n_md.  Leapfrog: dt_{i-1} =
+   * dt_i / m_{i-1}; Omelyan: dt_{i-1} = dt_i / (2 m_{i-1}).  term_level
+   * (nullable: every term on J-1) gives the level 1 .. J-1 of each
+   * pseudo-fermion field in eta's order.  n_levels = 0: J = 2 with
+   * m_0 = n_gauge and every pseudo-fermion term on level 1. */
+  int n_levels;
+  int level_steps[8];
+  const int *term_level;
 } or_traj_params;
 
 typedef struct {

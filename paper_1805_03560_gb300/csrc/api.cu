@@ -262,7 +262,7 @@ int hmc_ctx_set_option(hmc_ctx *ctx, int option, int value) {
   CTX_CHECK(ctx);
   switch (option) {
     case HMC_OPT_DSLASH_VARIANT:
-      if (value < -2 || value > 3) return fail(ctx, HMC_EINVAL, "dslash variant must be -2..3");
+      if (value < -2 || value > 6) return fail(ctx, HMC_EINVAL, "dslash variant must be -2..6");
       ctx->ds_variant = value;
       return HMC_OK;
     case HMC_OPT_CG_GRAPH:

@@ -449,7 +449,30 @@ static std::string tune_key(const DslashArgs &a, int sprec, int fmt, int dagger)
   return k;
 }
 
-static int default_variant(int fmt) { return fmt == 18 ? 2 : 0; }
+// Right-hand sides per thread of the multi-right-hand-side kernel by
+// default (variants 4..6 are that kernel with 2..4 per thread): 2 when it
+// divides n_rhs, else 3; 0 where it does not apply (one right-hand side, FP64
+// kinds, n_rhs not a multiple of 2 or 3).
+static int mr_default(int sprec, int n_rhs) {
+  if (n_rhs < 2) return 0;
+  if (dslash_mr_supported(sprec, n_rhs, 2)) return 2;
+  if (dslash_mr_supported(sprec, n_rhs, 3)) return 3;
+  return 0;
+}
+
+static int default_variant(int fmt, int sprec, int n_rhs) {
+  const int nr = mr_default(sprec, n_rhs);
+  if (nr) return 2 + nr;
+  return fmt == 18 ? 2 : 0;
+}
+
+// variant v of the class, launched: 0..3 the single-site kernel (bit 0 tiled
+// site mapping, bit 1 paired loads), 4..6 the multi-right-hand-side kernel
+static bool launch_any(const DslashArgs &a, int sprec, int fmt, int dagger, int v, int nb,
+                       cudaStream_t st) {
+  if (v >= 4) return launch_dslash_mr(a, sprec, fmt, dagger, v - 2, st);
+  return launch_variant(a, sprec, fmt, dagger, v, nb, st);
+}
 
 static int tune_variant(hmc_ctx *ctx, const DslashArgs &a, int sprec, int fmt, int dagger, int nb) {
   const std::string key = tune_key(a, sprec, fmt, dagger);
@@ -459,22 +482,26 @@ static int tune_variant(hmc_ctx *ctx, const DslashArgs &a, int sprec, int fmt, i
                           a.out != a.x && a.out != a.in;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(ctx->stream, &cs);
-  if (!repeatable || cs != cudaStreamCaptureStatusNone) return default_variant(fmt);
+  const int dflt = default_variant(fmt, sprec, a.n_rhs);
+  if (!repeatable || cs != cudaStreamCaptureStatusNone || ctx->tune_frozen) return dflt;
   cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess) return default_variant(fmt);
+  if (cudaEventCreate(&e0) != cudaSuccess) return dflt;
   if (cudaEventCreate(&e1) != cudaSuccess) {
     cudaEventDestroy(e0);
-    return default_variant(fmt);
+    return dflt;
   }
   const int sx = a.g.L[2] * a.g.Lzh;
   const bool tiles = a.n_rhs == 1 && sx % 32 == 0;
-  int best = default_variant(fmt);
+  int best = dflt;
   float best_ms = 1e30f;
-  for (int v = 0; v < 4; ++v) {
-    if ((v & 1) && !tiles) continue;
-    launch_variant(a, sprec, fmt, dagger, v, nb, ctx->stream);
+  int tried = 0;
+  for (int v = 0; v < 7; ++v) {
+    if ((v & 1) && v < 4 && !tiles) continue;
+    if (v >= 4 && !dslash_mr_supported(sprec, a.n_rhs, v - 2)) continue;
+    ++tried;
+    launch_any(a, sprec, fmt, dagger, v, nb, ctx->stream);
     cudaEventRecord(e0, ctx->stream);
-    for (int r = 0; r < 3; ++r) launch_variant(a, sprec, fmt, dagger, v, nb, ctx->stream);
+    for (int r = 0; r < 3; ++r) launch_any(a, sprec, fmt, dagger, v, nb, ctx->stream);
     cudaEventRecord(e1, ctx->stream);
     float ms = 0.f;
     if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
@@ -486,9 +513,24 @@ static int tune_variant(hmc_ctx *ctx, const DslashArgs &a, int sprec, int fmt, i
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  ctx->launches += tiles ? 16 : 8;
+  ctx->launches += 4 * tried;
   ctx->ds_tuned[key] = best;
   return best;
+}
+
+int dslash_mr_nr(hmc_ctx *ctx, const Geo &g, int sprec, int fmt, int n_rhs) {
+  const int dflt = mr_default(sprec, n_rhs);
+  if (!dflt) return 0;
+  int v = ctx->ds_variant;
+  if (v == -2) {
+    DslashArgs a{};
+    a.g = g;
+    a.n_rhs = n_rhs;
+    auto it = ctx->ds_tuned.find(tune_key(a, sprec, fmt, 1));
+    v = it != ctx->ds_tuned.end() ? it->second : -1;
+  }
+  if (v >= 4 && dslash_mr_supported(sprec, n_rhs, v - 2)) return v - 2;
+  return dflt;
 }
 
 int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int dagger,
@@ -521,10 +563,20 @@ int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int
   // paired loads.  Default -1: paired loads for 18-real links only (measured
   // on 24^3 x 48, pairing helps the 18-real kernels and slows the 12-real
   // ones, tiling helps neither); -2: autotuned per class.
-  int var = ctx->ds_variant >= 0 ? ctx->ds_variant : default_variant(U.fmt);
+  int var = ctx->ds_variant >= 0 ? ctx->ds_variant : default_variant(U.fmt, sprec, a.n_rhs);
   if (ctx->ds_variant == -2) var = tune_variant(ctx, a, sprec, U.fmt, dagger, nb);
+  if (var >= 4 && !dslash_mr_supported(sprec, a.n_rhs, var - 2)) var = U.fmt == 18 ? 2 : 0;
+  if (a.mr_force > 0 && var < 4) {
+    if (!dslash_mr_supported(sprec, a.n_rhs, a.mr_force))
+      return fail(ctx, HMC_EINVAL, "dslash: no multi-right-hand-side kernel for %d x %d",
+                  a.n_rhs, a.mr_force);
+    var = 2 + a.mr_force;
+  }
+  if (a.cg_x && a.n_rhs > 1 && var < 4)
+    return fail(ctx, HMC_EINVAL, "dslash: the fused batched update needs the multi-rhs kernel");
+  if (var >= 4 && nblocks) *nblocks = blocks_for((long long)a.g.Vh * (a.n_rhs / (var - 2)), DS_NT);
   TimedLaunch timer(ctx, cls, bytes);
-  if (!launch_variant(a, sprec, U.fmt, dagger, var, nb, st))
+  if (!launch_any(a, sprec, U.fmt, dagger, var, nb, st))
     return fail(ctx, HMC_EINVAL, "dslash: unsupported precision %d / link format %d", sprec,
                 U.fmt);
   return launched(ctx, cls);

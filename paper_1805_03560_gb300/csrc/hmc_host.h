@@ -34,8 +34,10 @@ struct hmc_ctx {
   // library's own non-blocking stream for capture and replay, ordered after
   // and before the caller's stream by gev
   int cg_graph = 1;
-  // autotuned hemi-Dslash variant per launch class (ds_variant == -2)
+  // autotuned hemi-Dslash variant per launch class (ds_variant == -2);
+  // tune_frozen: use tuned classes, never tune (untuned: built-in default)
   std::map<std::string, int> ds_tuned;
+  int tune_frozen = 0;
   cudaStream_t gstream = nullptr;
   cudaEvent_t gev[2] = {nullptr, nullptr};
   struct Pending {
@@ -129,7 +131,27 @@ struct DslashArgs {
   const double *cg_rr;
   const double *cg_pap;
   int *cg_flag;
+  // fused update of the batched CG (n_rhs > 1, multi-right-hand-side
+  // kernel only): per system alpha_r = mcg_rr[r] / mcg_pap[r] when
+  // mcg_live[r] (0 otherwise; mcg_done[r] = 2 when not finite), x_r +=
+  // alpha_r p_r (cg_x in F32), r_r -= alpha_r A p_r (cg_r), |r_r|^2
+  // partials and totals (partials, total, counter)
+  const double *mcg_rr;
+  const double *mcg_pap;
+  const int *mcg_live;
+  int *mcg_done;
+  // > 0: launch the multi-right-hand-side kernel with this many right-hand
+  // sides per thread (set by callers that need its fused epilogue)
+  int mr_force;
 };
+// Multi-right-hand-side hemi-Dslash with nr right-hand sides per thread
+// (dslash_mr.cu): FP32 or FP16 storage, 2 <= nr <= 4 dividing n_rhs <= 16.
+bool dslash_mr_supported(int sprec, int n_rhs, int nr);
+bool launch_dslash_mr(const DslashArgs &a, int sprec, int fmt, int dagger, int nr,
+                      cudaStream_t st);
+// right-hand sides per thread the multi-right-hand-side kernel uses for this
+// class (tuned or default); 0 when it does not apply
+int dslash_mr_nr(hmc_ctx *ctx, const Geo &g, int sprec, int fmt, int n_rhs);
 int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int dagger,
            int *nblocks);
 // autotune the hemi-Dslash classes of (sprec, U.fmt, n_rhs) on scratch fields

@@ -53,13 +53,13 @@ extern "C" int hmc_mhat_noalloc(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_
   }
   // the optional per-launch event timing and the autotuner create CUDA
   // events (and the autotuner synchronises the stream and relaunches), so
-  // both are bypassed for this call: an autotuning context runs the built-in
-  // default variant, which computes the same result bit for bit
-  const int saved_timing = ctx->timing, saved_variant = ctx->ds_variant;
+  // both are bypassed for this call: an autotuning context runs the variant
+  // already tuned for the class, else the built-in default
+  const int saved_timing = ctx->timing, saved_frozen = ctx->tune_frozen;
   ctx->timing = 0;
-  if (ctx->ds_variant == -2) ctx->ds_variant = -1;
+  ctx->tune_frozen = 1;
   st = mhat(ctx, g, *U, prec, dagger, n_rhs, out, in, tmp, kappa, nullptr, nullptr, nullptr);
   ctx->timing = saved_timing;
-  ctx->ds_variant = saved_variant;
+  ctx->tune_frozen = saved_frozen;
   return st;
 }

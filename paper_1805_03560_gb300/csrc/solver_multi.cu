@@ -243,6 +243,7 @@ struct MSolve {
   Geo g;
   hmc_gauge Uh, Ul;
   int plo, n;
+  int mr;  // right-hand sides per thread of the fused last hop (0: separate axpy)
   int S;  // Vh * n
   MState *st;
   double *cb;  // -kappa_r^2 (device)
@@ -277,10 +278,20 @@ int m_iteration(MSolve &s, int k) {
   a.p = 1; a.out = s.tlo; a.in = s.y; a.x = nullptr; a.ca = 0.0; a.cb = 1.0; a.cb_rhs = nullptr;
   TRY(dslash(ctx, a, U, s.plo, 1, nullptr));
   a.p = 0; a.out = s.Ap; a.in = s.tlo; a.x = s.y; a.ca = 1.0; a.cb_rhs = s.cb;
-  TRY(dslash(ctx, a, U, s.plo, 1, nullptr));
   cudaStream_t st = ctx->stream;
   const int plain = mixed ? 0 : 1;
-  switch (s.plo) {
+  if (s.mr) {
+    // the x and r updates fused into the last hemi-Dslash (A p not stored)
+    a.mr_force = s.mr;
+    a.cg_x = s.xlo; a.cg_r = s.rlo; a.cg_p = s.p;
+    a.mcg_rr = s.st->rr[par]; a.mcg_pap = s.st->pap; a.mcg_live = s.st->live;
+    a.mcg_done = s.st->done;
+    a.partials = s.rr_part; a.total = s.st->rr_next; a.counter = s.st->cnt[1];
+    TRY(dslash(ctx, a, U, s.plo, 1, nullptr));
+  } else {
+    TRY(dslash(ctx, a, U, s.plo, 1, nullptr));
+  }
+  if (!s.mr) switch (s.plo) {
     case HMC_F64:
       k_mcg_axpy<HMC_F64, HMC_F64><<<s.nb_bl, BL_NT, 0, st>>>(s.x, s.rlo, s.p, s.Ap, s.S, s.n,
                                                               s.st, par, s.rr_part);
@@ -294,7 +305,7 @@ int m_iteration(MSolve &s, int k) {
                                                               s.st, par, s.rr_part);
       break;
   }
-  TRY(launched(ctx, "cg_multi_axpy"));
+  if (!s.mr) TRY(launched(ctx, "cg_multi_axpy"));
   switch (s.plo) {
     case HMC_F64:
       k_mcg_xpay<HMC_F64><<<s.nb_bl, BL_NT, 0, st>>>(s.p, s.rlo, s.S, s.n, s.st, par, plain);
@@ -417,6 +428,13 @@ int cg_solve_multi(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_ga
     TRY(copy_convert(ctx, s.plo, HMC_F64, s.p, b, s.S));
   } else {
     TRY(copy_convert(ctx, HMC_F64, HMC_F64, s.p, b, s.S));
+  }
+  // autotuning contexts time the iteration's hemi-Dslash classes here, on
+  // scratch (t = H p); the fused last hop then runs the multi-right-hand-side
+  // kernel with the tuned (or default) right-hand sides per thread
+  if (mixed) {
+    TRY(dslash_tune(ctx, g, s.Ul, s.plo, n_rhs, s.tlo, s.p));
+    s.mr = dslash_mr_nr(ctx, g, s.plo, s.Ul.fmt, n_rhs);
   }
   MState h{};
   TRY(m_read(s, &h));

@@ -93,6 +93,7 @@ _SIGS = {
     "hmc_launch_count": (ctypes.c_longlong, [_P]),
     "hmc_ctx_set_timing": (_I, [_P, _I]),
     "hmc_ctx_set_option": (_I, [_P, _I, _I]),
+    "hmc_measure_fma_peak": (_I, [_P, _I, _P]),
     "hmc_timing_get": (_I, [_P, _I, ctypes.c_char_p, _I, _P, _P, _P]),
     "hmc_gauge_bytes": (_SZ, [_P, _I, _I]),
     "hmc_spinor_bytes": (_SZ, [_P, _I, _I]),
@@ -250,9 +251,18 @@ class Context:
         return lib().hmc_launch_count(self.h)
 
     def set_dslash_variant(self, v):
-        """Hemi-Dslash kernel variant: 0..3 fixed, -1 built-in default, -2 autotuned per launch
-        class."""
+        """Hemi-Dslash kernel variant: 0..3 the single-site kernel, 4..6 the
+        multi-right-hand-side kernel with 2..4 right-hand sides per thread,
+        -1 built-in default, -2 autotuned per launch class."""
         self._check(lib().hmc_ctx_set_option(self.h, 1, int(v)), "hmc_ctx_set_option")
+
+    def fma_peak(self, kind):
+        """Measured multiply-add throughput in TFLOP/s: kind 0 FP64, 1 FP32, 2 paired FP32."""
+        self._stream()
+        out = ctypes.c_double(0)
+        self._check(lib().hmc_measure_fma_peak(self.h, int(kind), ctypes.byref(out)),
+                    "hmc_measure_fma_peak")
+        return out.value
 
     def set_cg_graph(self, on):
         """Replay CG iterations from a captured CUDA graph (default on)."""

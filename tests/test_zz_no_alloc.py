@@ -6,8 +6,8 @@ synchronise the device).  hmc_mhat_noalloc serves them by keeping Mhat's odd
 intermediate in a static device array.  It runs the same kernels on the same
 inputs as hmc_mhat, the allocating entry point, so its output must equal
 hmc_mhat's bit for bit, on consecutive calls that reuse the shared array, and
-also on a context that autotunes its Dslash variant (the call bypasses the
-autotuner; every variant computes the same bits).
+also on a context that autotunes its Dslash variant (the call never tunes; it
+runs the variant hmc_mhat tuned for the class just before).
 
 This file is collected last so that, in a run that stops at the first
 failure, every other test has run already.
