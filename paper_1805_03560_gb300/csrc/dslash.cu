@@ -294,7 +294,14 @@ __global__ void __launch_bounds__(DS_NT, ds_min_blocks(SP)) k_dslash(const Dslas
   if (a.gate && *a.gate == 0) return;
   if (a.red_src && blockIdx.x == 0) {
     const double t = block_sum_partials<DS_NT>(a.red_src, a.red_n);
-    if (threadIdx.x == 0) *a.red_dst = t;
+    if (threadIdx.x == 0) {
+      *a.red_dst = t;
+      if (a.red_alpha) {
+        const double al = *a.red_rr / t;
+        *a.red_alpha = al;
+        if (!isfinite(al) || !(t > 0.0)) *a.red_flag = 2;
+      }
+    }
   }
   const int S_ = a.g.Vh * a.n_rhs;
   const int i = dslash_site(a);
@@ -343,9 +350,15 @@ __global__ void __launch_bounds__(DS_NT, ds_min_blocks(SP)) k_dslash(const Dslas
     if (a.cg_x) {
       // fused CG step: acc = A p is consumed here, x += alpha p, r -= alpha A p
       constexpr int PX = (SP == HMC_F64 || SP == HMC_F64E) ? SP : HMC_F32;
-      const double pap = *a.cg_pap, ad = *a.cg_rr / pap;
-      if (blockIdx.x == 0 && threadIdx.x == 0 && (!isfinite(ad) || !(pap > 0.0)))
-        *a.cg_flag = 2;
+      double ad;
+      if (a.cg_alpha) {
+        ad = *a.cg_alpha;  // formed once (and checked) by the launch before
+      } else {
+        const double pap = *a.cg_pap;
+        ad = *a.cg_rr / pap;
+        if (blockIdx.x == 0 && threadIdx.x == 0 && (!isfinite(ad) || !(pap > 0.0)))
+          *a.cg_flag = 2;
+      }
       const R alpha = (R)ad;
       Cx<R> pv[12], v[12];
       SIO::load(a.cg_p, S_, i, pv);

@@ -121,6 +121,11 @@ struct DslashArgs {
   const double *red_src;
   int red_n;
   double *red_dst;
+  // with red_alpha: block 0 also stores *red_alpha = *red_rr / (the sum),
+  // *red_flag = 2 when that is not finite or the sum is not positive
+  const double *red_rr;
+  double *red_alpha;
+  int *red_flag;
   // fused CG update (n_rhs == 1): the epilogue result A p is not stored;
   // with alpha = *cg_rr / *cg_pap the launch updates x += alpha p (cg_x, in
   // FP64 for FP64 fields, F32 otherwise) and r -= alpha A p (cg_r), and the
@@ -131,6 +136,9 @@ struct DslashArgs {
   const double *cg_rr;
   const double *cg_pap;
   int *cg_flag;
+  // nullable: alpha precomputed by an earlier launch (red_alpha); the fused
+  // update then reads it instead of dividing cg_rr by cg_pap
+  const double *cg_alpha;
   // fused update of the batched CG (n_rhs > 1, multi-right-hand-side
   // kernel only): per system alpha_r = mcg_rr[r] / mcg_pap[r] when
   // mcg_live[r] (0 otherwise; mcg_done[r] = 2 when not finite), x_r +=

@@ -38,6 +38,7 @@ struct CGState {
   double aux;     // scratch for one-off reductions
   double pap;     // p^dag A p of the current iteration (last block of the Mhat Dslash)
   double rr_next; // |r|^2 after the update (set by xpay)
+  double alpha;   // rr / pap of the current iteration (block 0 of the H_eo^dag launch)
   int done;       // 1 converged (recursive residual), 2 NaN/Inf
   int active;     // !done
   int iter;
@@ -373,8 +374,9 @@ void launch_xpay(Solve &s, int par, int n_part) {
 
 // One iteration, five launches: y = Mhat p (the second hemi-Dslash leaves
 // block partials of |y|^2 = p^dag A p), t = H_eo^dag y (its block 0 sums
-// those partials into pap), then the second hemi-Dslash of Mhat^dag with the
-// fused update x += alpha p, r -= alpha A p (A p is never stored; it leaves
+// those partials into pap and forms alpha = rr / pap once), then the second
+// hemi-Dslash of Mhat^dag with the fused update x += alpha p,
+// r -= alpha A p (A p is never stored; it leaves
 // block partials of |r|^2), then xpay (every block sums the |r|^2 partials:
 // beta = |r|^2 / rr; p = r + beta p; block 0 advances the state).
 int one_iteration(Solve &s, int k) {
@@ -399,8 +401,10 @@ int one_iteration(Solve &s, int k) {
   // t = H_eo^dag y, block 0 finishing p^dag A p
   a.p = 1; a.out = s.tlo; a.in = s.y; a.x = nullptr; a.ca = 0.0; a.cb = 1.0;
   a.red_src = s.pap_part; a.red_n = nb_pap; a.red_dst = &s.st->pap;
+  a.red_rr = &s.st->rr[par]; a.red_alpha = &s.st->alpha; a.red_flag = &s.st->done;
   TRY(dslash(ctx, a, U, s.plo, 1, nullptr));
   a.red_src = nullptr; a.red_dst = nullptr; a.red_n = 0;
+  a.red_rr = nullptr; a.red_alpha = nullptr; a.red_flag = nullptr;
   // A p = y - kappa^2 H_oe^dag t consumed by the fused update
   a.p = 0; a.out = nullptr; a.in = s.tlo; a.x = s.y; a.ca = 1.0; a.cb = -s.kappa * s.kappa;
   a.cg_x = mixed ? s.xlo : s.x;
@@ -409,6 +413,7 @@ int one_iteration(Solve &s, int k) {
   a.cg_rr = &s.st->rr[par];
   a.cg_pap = &s.st->pap;
   a.cg_flag = &s.st->done;
+  a.cg_alpha = &s.st->alpha;
   a.partials = s.rr_part;
   int nb_rr = 0;
   TRY(dslash(ctx, a, U, s.plo, 1, &nb_rr));
