@@ -109,6 +109,12 @@ def parse():
                          "field relaxed by pure-gauge HMC, kappa 0.156 unless --kappa")
     ap.add_argument("--kappa", type=float, default=None,
                     help="hopping parameter of the trajectory workload (default 0.1575)")
+    ap.add_argument("--c5", action="store_true",
+                    help="the combined workload on 32^3x64 at kappa 0.1575: kappa^4 filtering, "
+                         "rooted polynomials (N 2, degrees 16 and 42, remainder n_t 15 / n_max "
+                         "29) on the target term of a 2-level mass-preconditioning chain "
+                         "(kappa' 0.150, 0.154), Omelyan on four Sexton-Weingarten levels "
+                         "(gauge; P_1; P_2 and the heavy terms; the remainder)")
     ap.add_argument("--mp", action="store_true",
                     help="mass-preconditioned workload: pseudo-fermions at kappa' = 0.150, "
                          "0.154 and the target kappa (ratio terms, batched solves), no filter")
@@ -324,6 +330,8 @@ class Clocks:
 
 
 KAPPA_MP = [0.150, 0.154]
+C5_ROOT_N = 2
+C5_LEVEL_STEPS = (2, 2, 2)  # m_0 (gauge), m_1 (P_1), m_2 (P_2, heavy ratio terms)
 
 
 def coeffs():
@@ -376,14 +384,17 @@ def run_hmc(args):
     fma = {k: round(ctx.fma_peak(i), 2) for i, k in enumerate(("fp64", "fp32", "fp32x2"))}
     # autotuned hemi-Dslash variants (tuned during the warm-up steps)
     ctx.set_dslash_variant(-2 if args.variant is None else args.variant)
-    n_eta = len(KAPPA_MP) + 1 if args.mp else (2 * args.rooted + 1 if args.rooted else 1)
+    if args.c5:
+        n_eta = len(KAPPA_MP) + 2 * C5_ROOT_N + 1
+    else:
+        n_eta = len(KAPPA_MP) + 1 if args.mp else (2 * args.rooted + 1 if args.rooted else 1)
     from paper_1805_03560_gb300 import inputs as I
     U0 = ctx.pack_gauge(LAT, I.gauge_links(LAT, EPS_LINKS, seed=1 + 100 * rank), hmc.F64,
                         hmc.LINK18)
     Ud = ctx.new_gauge(LAT, hmc.F64, hmc.LINK18)
     b, alpha, c = coeffs()
     start = None
-    if args.rooted or not args.no_relax:
+    if args.rooted or args.c5 or not args.no_relax:
         # the synthetic start is far from equilibrium at beta 5.6 (dH of
         # O(10^3), acceptance zero); the roots' series in K also need the
         # spectrum of K inside the unit disk, which holds on a relaxed field
@@ -417,7 +428,23 @@ def run_hmc(args):
         # 0.998 at 0.1575 on 16 x 8^3), so the roots are taken at 0.156
         work["kappa"] = 0.156
     solver = hmc.SOLVER_BICGSTAB if args.solver == "bicgstab" else hmc.SOLVER_CG
-    if args.rooted:
+    if args.c5:
+        # kappa^4 Mtilde, P_1 and P_2 (degrees 16, 42, root N) on the target
+        # term of the chain kappa' = 0.150, 0.154 -> kappa; remainder n_t 15 /
+        # n_max 29; Omelyan (lambda 1/6) on four levels: gauge (m_0 steps per
+        # level-1 step), P_1 (m_1), P_2 with the heavy ratio terms (m_2), the
+        # remainder on the outermost level (n_md steps)
+        ra, rb, rp = hmc.rooted_coeffs(2, C5_ROOT_N, (16, 42), 29)
+        _, _, rc = hmc.filter_coeffs(2, 29)
+        work.update(filter_k=2, n_t=15, n_max=29, n_md=args.n_md or 4, n_gauge=1,
+                    integrator=hmc.OMELYAN, lam=1.0 / 6.0, tau=args.tau or 1.0)
+        nk = len(KAPPA_MP)
+        levels = [2] * nk + [1] * C5_ROOT_N + [2] * C5_ROOT_N + [3]
+        kw = dict(work, b=rb, c=rc, alpha=ra, root_polys=rp, root_N=C5_ROOT_N,
+                  kappa_mp=KAPPA_MP, level_steps=list(C5_LEVEL_STEPS), term_level=levels,
+                  inner_prec=inner, link_fmt_lo=hmc.LINK12, reliable_delta=args.delta,
+                  force_prec=fprec, f64_emul=args.f64_emul, solver=solver)
+    elif args.rooted:
         # Sec. II.A with kappa^4 filtering: M_1 = Mtilde (k = 2), P_1, P_2 of
         # degrees 16 and 42, the remainder truncated at n_t = 15 / n_max = 29
         ra, rb, rp = hmc.rooted_coeffs(2, args.rooted, (16, 42), 29)
@@ -506,7 +533,12 @@ def run_hmc(args):
     kernels = {k: {"launches_per_step": v[0] // args.steps, "us": round(v[1] / v[0] * 1e3, 2),
                    "GBs": round(v[2] / (v[1] * 1e-3) / 1e9, 1)} for k, v in sorted(kst.items())}
     dHs = [r["dH"] for r in results]
-    if args.mp:
+    if args.c5:
+        wl = (f"hmc-trajectory {lat_name()} kappa={work['kappa']} beta=5.6 kappa^4 rooted "
+              f"polynomials N={C5_ROOT_N} (degrees 16, 42) on the target of the chain "
+              "kappa'=0.150,0.154; Omelyan on 4 levels m=" +
+              ",".join(str(m) for m in C5_LEVEL_STEPS) + f",{work['n_md']}")
+    elif args.mp:
         wl = (f"hmc-trajectory {lat_name()} kappa={work['kappa']} beta=5.6 "
               "mass-preconditioned kappa'=0.150,0.154 (batched solves)")
     elif args.rooted:
@@ -899,7 +931,7 @@ def run_chain_report(args):
 def main():
     global LAT
     args = parse()
-    LAT = LATTICES[args.lattice]
+    LAT = LATTICES["32x64" if args.c5 and args.lattice == "24x48" else args.lattice]
     if args.report == "thermal":
         run_thermal_report(args)
     elif args.report == "md":

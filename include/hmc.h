@@ -358,6 +358,32 @@ int hmc_action_pf(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
                   const hmc_solver_opts *opts, double *action,
                   hmc_solve_stats *stats);
 
+/* hmc_action_fratio / hmc_force_fratio: the filtered ratio term, the filter
+ * of Sec. II combined with the mass preconditioning of Sec. I (the paper's
+ * Conclusion notes that the two combine; the action is not written out
+ * there).  Reading: the target term of a mass-preconditioned chain with the
+ * target operator replaced by Mtilde,
+ *   S~_R(phi) = |Z Mhat(kappa_a) phi|^2,
+ *   Z = alpha Mhat^{-1} + sum_{n=0}^{filt->n} b_n K^n  (K at kappa),
+ * whose Gaussian integral is det(Mtilde Mtilde^dag) / det(Mhat_a^dag Mhat_a)
+ * (the T_k term of hmc_force_hopexp at kappa cancels the filter).
+ * kappa_a = 0 (Mhat_a = 1) is the filtered action of hmc_action_pf.  The
+ * force: 2 Re[z^dag (delta Z) chi] + 2 Re[(Z^dag z)^dag delta Mhat_a phi] with
+ * chi = Mhat_a phi, z = Z chi; the second part reuses the Horner fields of the
+ * first (no further solve).  Arguments as for hmc_force_pf / hmc_action_pf
+ * (filt required); the rooted-polynomial remainder of Sec. II.A takes the same
+ * form.  Blocking; the action is written to *action (host). */
+int hmc_action_fratio(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
+                      const hmc_gauge *U_lo, const void *phi, double kappa,
+                      const hmc_filter *filt, double kappa_a, double tol,
+                      const hmc_solver_opts *opts, double *action, hmc_solve_stats *stats);
+/* F += coeff * force of S~_R (filt->n the truncation n_t of the force);
+ * performs its own solves (tolerance tol, options opts, stats summed). */
+int hmc_force_fratio(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
+                     const hmc_gauge *U_lo, const void *phi, double kappa, const hmc_filter *filt,
+                     double kappa_a, double coeff, double *F, double tol,
+                     const hmc_solver_opts *opts, hmc_solve_stats *stats);
+
 /* hmc_force_hopexp: gauge part of the action, S_G (Sec. I) plus the
  * hopping-expansion term T_k = 2 sum_{n=1}^{k} (1/n) Tr_e K^n (eq. ModGauge in
  * even/odd form), k in {0, 1, 2} counting powers of K.  For every extent >= 6
@@ -505,13 +531,21 @@ typedef struct {
   double tol_md, tol_action;
   hmc_solver_opts solver; /* inner precision of every solve */
   int link_fmt_lo;        /* format of the inner-precision gauge copy */
-  /* mass preconditioning (Sec. I; requires filter_k == 0): n_mp heavier
-   * hopping parameters kappa_mp[0] < ... < kappa_mp[n_mp-1] < kappa (host
-   * array) split the pseudo-fermion action into n_mp + 1 terms
-   * S_PF(kappa_mp[0]) + sum_j S_R(kappa_mp[j-1], kappa_mp[j]) +
-   * S_R(kappa_mp[n_mp-1], kappa) (see hmc_force_mp), all on the coarse
-   * time scale with their solves batched; eta then holds n_mp + 1
-   * consecutive F64 even fields.  n_mp = 0: one plain or filtered term. */
+  /* mass preconditioning (Sec. I): n_mp heavier hopping parameters
+   * kappa_mp[0] < ... < kappa_mp[n_mp-1] < kappa (host array) give the heavy
+   * terms S_PF(kappa_mp[0]) + sum_{j<n_mp} S_R(kappa_mp[j-1], kappa_mp[j])
+   * (see hmc_force_mp) and set kappa_a = kappa_mp[n_mp-1] for the target
+   * group at kappa (kappa_a = 0 when n_mp = 0):
+   *   plain (filter_k = 0, no roots): S_R(kappa_a, kappa);
+   *   filtered (filter_k > 0): |Z Mhat(kappa_a) phi|^2 with
+   *     Z = alpha Mhat^{-1} + sum_{n<=n_max} b_n K^n (Sec. II's filtered
+   *     action of the field Mhat_a phi; its Gaussian integral is
+   *     det(Mtilde Mtilde^dag) / det(Mhat_a^dag Mhat_a), and T_k at kappa
+   *     cancels the filter: the filter and mass preconditioning combined);
+   *   rooted (root_levels > 0): the polynomial terms below and the
+   *     remainder in that filtered form.
+   * eta holds the heavy terms' fields first, then the target group's.
+   * Ratio terms on one level have their solves batched. */
   int n_mp;
   const double *kappa_mp;
   /* integrator (Sec. I), both on the two time scales above with
@@ -526,18 +560,19 @@ typedef struct {
    * the same U are merged (one force evaluation). */
   int integrator;
   double lambda;
-  /* rooted-polynomial hierarchy (Sec. II.A; requires n_mp == 0):
+  /* rooted-polynomial hierarchy (Sec. II.A):
    * root_levels > 0 polynomials P_j(K) = sum_i root_c[j][i] K^i
    * (i = 0 .. root_deg[j], host arrays, e.g. truncated series of
    * M_j^{-1/N}), each carried by root_N pseudo-fermions with the action
    * |P_j(K) phi|^2, plus one remainder pseudo-fermion with
-   * |(alpha Mhat^{-1} + sum_{n<=n_max} b_n K^n) phi|^2 (force truncated at
-   * n_t; b, c, alpha as for filtering, even when filter_k == 0; filter_k
-   * fixes Mtilde and the T_k term of the gauge action).  eta then holds
-   * root_levels * root_N + 1 consecutive F64 even fields, the remainder
-   * last.  Heatbath: phi = P_j^{-1} eta (hmc_poly_solve to tol_md, FP32
-   * correction passes when solver.inner_prec is F32) and
-   * phi = prod_j P_j^N Mhat sum c_n K^n eta; H0 and H1 evaluate the actions.
+   * |(alpha Mhat^{-1} + sum_{n<=n_max} b_n K^n) Mhat(kappa_a) phi|^2 (force
+   * truncated at n_t; b, c, alpha as for filtering, even when
+   * filter_k == 0; filter_k fixes Mtilde and the T_k term of the gauge
+   * action).  The target group then holds root_levels * root_N + 1 F64 even
+   * fields, the remainder last.  Heatbath: phi = P_j^{-1} eta
+   * (hmc_poly_solve to tol_md, FP32 correction passes when
+   * solver.inner_prec is F32) and phi = Mhat_a^{-1} prod_j P_j^N Mhat
+   * sum c_n K^n eta; H0 and H1 evaluate the actions.
    * The polynomials need the spectrum of K inside the unit disk (see
    * hmc_poly_solve). */
   int root_levels, root_N;
@@ -548,6 +583,21 @@ typedef struct {
    * molecular dynamics (the force magnitudes whose variances govern
    * Var(dH) in Sec. III); one extra reduction and host read per evaluation. */
   int measure_forces;
+  /* Sexton-Weingarten levels (Sec. I): n_levels = J in 2..8 levels, the
+   * gauge action (with T_k) on level 0 and every pseudo-fermion field on
+   * level term_level[f] in 1..J-1 (term_level: host array in eta's order,
+   * nullable: all on J-1); level_steps[i-1] = m_{i-1} steps of level i-1
+   * inside one step of level i, the outermost level J-1 taking n_md steps of
+   * dt = tau / n_md.  With the integrator above on every level: leapfrog
+   * T_i = P_i(dt_i/2) [T_{i-1}]^{m_{i-1}} P_i(dt_i/2), dt_{i-1} = dt_i / m_{i-1}
+   * (the paper's leapfrog convention); Omelyan T_i = P_i(l dt_i)
+   * [T_{i-1}]^m P_i((1-2l) dt_i) [T_{i-1}]^m P_i(l dt_i), dt_{i-1} =
+   * dt_i / (2 m_{i-1}); T_0 the gauge step with the link updates.
+   * n_levels = 0: the two time scales above (level_steps and term_level
+   * ignored, m_0 = n_gauge). */
+  int n_levels;
+  int level_steps[8];
+  const int *term_level;
 } hmc_traj_params;
 
 #define HMC_INTEGRATOR_LEAPFROG 0

@@ -2,6 +2,7 @@
 // molecular-dynamics steps and the HMC trajectory (Sec. I and Sec. II).
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <vector>
 
 #include "hmc_host.h"
@@ -165,9 +166,28 @@ int force_links(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge
 // Dslash, the filter polynomials (Horner chain Y_i, the chain
 // X_i = K^dag X_{i-1}), the spin projections and the outer products run on
 // F32 (emulated-FP64) fields and links; the force accumulates in FP64.
+//
+// With kappa_a != 0 (filtered ratio term |Z Mhat_a phi_a|^2, phi the source
+// chi = Mhat_a phi_a) the force also gets 2 Re[w^dag delta Mhat_a phi_a] with
+// w = Z^dag Z chi: Z chi = Y_0 + Ytilde = X_1, so
+// w = alpha Mhat^{-dag} X_1 + sum_m b_m K^dag^m X_1 = alpha Xtilde + sum_m b_m X_{m+1},
+// from the fields the Horner force already holds (one more K^dag for
+// X_{n+1}) and no further solve.
+static int force_filt(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
+                      const void *phi, double kappa, const hmc_filter *filt, double coeff,
+                      double *F, double tol, const hmc_solver_opts *opts, hmc_solve_stats *acc,
+                      double kappa_a, const void *phi_a);
+
 int force_pf(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
              const void *phi, double kappa, const hmc_filter *filt, double coeff, double *F,
              double tol, const hmc_solver_opts *opts, hmc_solve_stats *acc) {
+  return force_filt(ctx, g, Uh, Ul, phi, kappa, filt, coeff, F, tol, opts, acc, 0.0, nullptr);
+}
+
+static int force_filt(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
+                      const void *phi, double kappa, const hmc_filter *filt, double coeff,
+                      double *F, double tol, const hmc_solver_opts *opts, hmc_solve_stats *acc,
+                      double kappa_a, const void *phi_a) {
   const int fp = opts ? opts->force_prec : HMC_F64;
   hmc_gauge Uf;
   TRY(force_links(ctx, g, Uh, Ul, fp, &Uf, "force_pf"));
@@ -263,11 +283,30 @@ int force_pf(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
     Vv[2 * q] = B;
     Vv[2 * q + 1] = vo;
   }
-  (void)Xn;
   const int q0 = has_inv ? 0 : 1;
-  return hop_force_multi(ctx, g, Uf, n + 1 - q0, (const void *const(*)[2])(Wv.data() + 2 * q0),
-                         (const void *const(*)[2])(Vv.data() + 2 * q0), F, coeff * kappa * kappa,
-                         fp);
+  TRY(hop_force_multi(ctx, g, Uf, n + 1 - q0, (const void *const(*)[2])(Wv.data() + 2 * q0),
+                      (const void *const(*)[2])(Vv.data() + 2 * q0), F, coeff * kappa * kappa,
+                      fp));
+  if (kappa_a == 0.0 || !phi_a) return HMC_OK;
+  // w = alpha Xtilde + sum_{m<=n} b_m X_{m+1}  (X_{n+1} = K^dag X_n; X_1 = Xi)
+  void *w = workspace(ctx, "pf_w", f64);
+  if (!w) return HMC_ENOMEM;
+  const void *xlast = Xi;
+  if (n >= 1) {
+    TRY(apply_K(ctx, g, Uf, fp, 1, kappa, Xn, xs(n), nullptr, 0.0, tmp));
+    xlast = Xn;
+  }
+  auto xm = [&](int m) -> const void * { return m == 0 ? Xi : (m < n ? xs(m + 1) : xlast); };
+  TRY(axpby(ctx, fp, w, filt->b[0], xm(0), has_inv ? filt->alpha : 0.0, has_inv ? Xt : nullptr,
+            g.Vh));
+  for (int m = 1; m <= n; ++m) TRY(axpby(ctx, fp, w, 1.0, w, filt->b[m], xm(m), g.Vh));
+  // 2 Re[w^dag delta Mhat_a phi_a] = -2 Re[w^dag delta K_a phi_a]
+  const void *pa = phi_a;
+  if (fp != HMC_F64) {
+    TRY(to_fp(phf, phi_a));
+    pa = phf;
+  }
+  return pair_force(ctx, g, Uh, Uf, fp, kappa_a, w, pa, -coeff, F);
 }
 
 int action_pf(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
@@ -403,48 +442,180 @@ int poly_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge 
   return HMC_OK;
 }
 
-// The rooted-polynomial pseudo-fermions (Sec. II.A): root_levels * root_N
-// polynomial terms |P_j(K) phi|^2 (the filtered form with alpha = 0) and the
-// remainder |(alpha Mhat^{-1} + sum b_n K^n) phi|^2, the fields consecutive.
-static int rooted_terms(const hmc_traj_params *prm) {
-  return prm->root_levels > 0 ? prm->root_levels * prm->root_N + 1 : 0;
+// ---- the pseudo-fermion terms of a trajectory, in the order of eta's fields
+// f < n_mp: the heavy terms of the mass-preconditioning chain (Sec. I),
+// S_PF(k_0) and S_R(k_{f-1}, k_f) (ratio terms); then the target group at
+// kappa with kappa_a = k_{n_mp-1} (0 without mass preconditioning): the ratio
+// term S_R(kappa_a, kappa); or, with the filter of Sec. II (filter_k > 0),
+// the filtered ratio term |Z Mhat_a phi|^2, Z = alpha Mhat^{-1} + sum b_n K^n
+// (kappa_a = 0: the filtered action itself); or, with the rooted polynomials
+// of Sec. II.A, root_levels * root_N terms |P_j(K) phi|^2 and the remainder
+// in the filtered ratio form.
+enum TermKind { TERM_RATIO = 0, TERM_POLY = 1, TERM_FRATIO = 2 };
+
+static int n_target(const hmc_traj_params *prm) {
+  return prm->root_levels > 0 ? prm->root_levels * prm->root_N + 1 : 1;
 }
-static hmc_filter rooted_filter(const hmc_traj_params *prm, int f, bool action) {
-  const int j = f / prm->root_N;
-  if (j < prm->root_levels) return hmc_filter{prm->root_c[j], prm->root_deg[j], 0.0};
+static int n_terms(const hmc_traj_params *prm) { return prm->n_mp + n_target(prm); }
+static double target_ka(const hmc_traj_params *prm) {
+  return prm->n_mp > 0 ? prm->kappa_mp[prm->n_mp - 1] : 0.0;
+}
+static TermKind term_kind(const hmc_traj_params *prm, int f, double *ka, double *kb, int *j) {
+  if (f < prm->n_mp) {
+    *ka = f == 0 ? 0.0 : prm->kappa_mp[f - 1];
+    *kb = prm->kappa_mp[f];
+    return TERM_RATIO;
+  }
+  const int t = f - prm->n_mp;
+  *ka = target_ka(prm);
+  *kb = prm->kappa;
+  if (prm->root_levels > 0 && t < prm->root_levels * prm->root_N) {
+    *j = t / prm->root_N;
+    return TERM_POLY;
+  }
+  return (prm->root_levels > 0 || prm->filter_k > 0) ? TERM_FRATIO : TERM_RATIO;
+}
+// the ratio terms are the first n_ratio fields
+static int n_ratio(const hmc_traj_params *prm) {
+  double ka, kb;
+  int j = 0;
+  return prm->n_mp + (term_kind(prm, prm->n_mp, &ka, &kb, &j) == TERM_RATIO ? 1 : 0);
+}
+static void ratio_pairs(const hmc_traj_params *prm, double *ka, double *kb) {
+  int j = 0;
+  for (int f = 0; f < n_ratio(prm); ++f) term_kind(prm, f, &ka[f], &kb[f], &j);
+}
+static hmc_filter term_filter(const hmc_traj_params *prm, int j, bool action, bool poly) {
+  if (poly) return hmc_filter{prm->root_c[j], prm->root_deg[j], 0.0};
   return hmc_filter{prm->b, action ? prm->n_max : prm->n_t, prm->alpha};
 }
-static int rooted_action(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
-                         const void *phi, const hmc_traj_params *prm, double *S,
+
+// Number of F64 even fields of hmc_trajectory's eta (and of phi).
+int traj_eta_fields(const hmc_traj_params *prm) { return n_terms(prm); }
+
+// Sexton-Weingarten levels (Sec. I): J levels, gauge on level 0; m_{i-1}
+// steps of level i-1 per step of level i.
+static int n_level(const hmc_traj_params *prm) { return prm->n_levels > 0 ? prm->n_levels : 2; }
+static int level_m(const hmc_traj_params *prm, int i) {
+  return prm->n_levels > 0 ? prm->level_steps[i] : prm->n_gauge;
+}
+static int term_level(const hmc_traj_params *prm, int f) {
+  return prm->term_level ? prm->term_level[f] : n_level(prm) - 1;
+}
+
+// S~_R = |Z Mhat_a phi|^2: the filtered action of the source Mhat_a phi
+static int action_fratio(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
+                         const void *phi, double kappa, const hmc_filter &filt, double ka,
+                         double tol, const hmc_solver_opts *opts, double *S,
                          hmc_solve_stats *acc) {
+  const void *chi = phi;
+  if (ka != 0.0) {
+    void *c = workspace(ctx, "fr_chi", spinor_bytes(g, HMC_F64, 1));
+    if (!c) return HMC_ENOMEM;
+    HiOps hi;
+    TRY(hi_begin(ctx, g, Uh, opts, &hi, "fr"));
+    TRY(hi_mhat(hi, 0, c, phi, ka, 1, nullptr));
+    chi = c;
+  }
+  return action_pf(ctx, g, Uh, Ul, chi, kappa, &filt, tol, opts, S, acc);
+}
+
+static int force_fratio(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
+                        const void *phi, double kappa, const hmc_filter &filt, double ka,
+                        double coeff, double *F, double tol, const hmc_solver_opts *opts,
+                        hmc_solve_stats *acc) {
+  if (ka == 0.0) return force_pf(ctx, g, Uh, Ul, phi, kappa, &filt, coeff, F, tol, opts, acc);
+  void *c = workspace(ctx, "fr_chi", spinor_bytes(g, HMC_F64, 1));
+  if (!c) return HMC_ENOMEM;
+  HiOps hi;
+  TRY(hi_begin(ctx, g, Uh, opts, &hi, "fr"));
+  TRY(hi_mhat(hi, 0, c, phi, ka, 1, nullptr));
+  return force_filt(ctx, g, Uh, Ul, c, kappa, &filt, coeff, F, tol, opts, acc, ka, phi);
+}
+
+// Sum of the actions of the terms f in [f0, f1) (ratio terms batched)
+static int terms_action(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
+                        const void *phi, const hmc_traj_params *prm, int f0, int f1,
+                        double *S, hmc_solve_stats *acc) {
   const size_t f64 = spinor_bytes(g, HMC_F64, 1);
   double s = 0.0;
-  for (int f = 0; f < rooted_terms(prm); ++f) {
-    const hmc_filter flt = rooted_filter(prm, f, true);
-    double sf;
-    TRY(action_pf(ctx, g, Uh, Ul, (const char *)phi + f64 * f, prm->kappa, &flt,
-                  prm->tol_action, &prm->solver, &sf, acc));
+  const int nr = n_ratio(prm);
+  if (f0 < nr) {
+    double ka[80], kb[80], sr;
+    ratio_pairs(prm, ka, kb);
+    const int e = f1 < nr ? f1 : nr;
+    const void *ph = (const char *)phi + f64 * f0;
+    if (e - f0 == 1 && ka[f0] == 0.0)
+      TRY(action_pf(ctx, g, Uh, Ul, ph, kb[f0], nullptr, prm->tol_action, &prm->solver, &sr,
+                    acc));
+    else
+      TRY(action_mp(ctx, g, Uh, Ul, ph, e - f0, ka + f0, kb + f0, prm->tol_action,
+                    &prm->solver, &sr, acc));
+    s += sr;
+    f0 = e;
+  }
+  for (int f = f0; f < f1; ++f) {
+    double ka, kb, sf;
+    int j = 0;
+    const TermKind kd = term_kind(prm, f, &ka, &kb, &j);
+    const hmc_filter flt = term_filter(prm, j, true, kd == TERM_POLY);
+    const void *ph = (const char *)phi + f64 * f;
+    if (kd == TERM_POLY)
+      TRY(action_pf(ctx, g, Uh, Ul, ph, prm->kappa, &flt, prm->tol_action, &prm->solver, &sf,
+                    acc));
+    else
+      TRY(action_fratio(ctx, g, Uh, Ul, ph, prm->kappa, flt, ka, prm->tol_action, &prm->solver,
+                        &sf, acc));
     s += sf;
   }
   *S = s;
   return HMC_OK;
 }
 
-// Hopping parameters (kappa_a, kappa_b) of the n_mp + 1 terms of a
-// mass-preconditioned chain: (0, k_0), (k_0, k_1), ..., (k_{n-1}, kappa).
-static int mp_pairs(const hmc_traj_params *prm, double *ka, double *kb) {
-  const int n = prm->n_mp;
-  for (int j = 0; j <= n; ++j) {
-    ka[j] = j == 0 ? 0.0 : prm->kappa_mp[j - 1];
-    kb[j] = j < n ? prm->kappa_mp[j] : prm->kappa;
+// F += forces of the terms on level l (ratio terms of consecutive fields on
+// the same level batched into one call)
+static int level_forces(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
+                        const void *phi, const hmc_traj_params *prm, int l, double *F,
+                        hmc_solve_stats *acc, int *solves) {
+  const size_t f64 = spinor_bytes(g, HMC_F64, 1);
+  const int nr = n_ratio(prm), nt = n_terms(prm);
+  double ka_r[80], kb_r[80];
+  ratio_pairs(prm, ka_r, kb_r);
+  for (int f = 0; f < nr;) {
+    if (term_level(prm, f) != l) {
+      ++f;
+      continue;
+    }
+    int e = f + 1;
+    while (e < nr && term_level(prm, e) == l) ++e;
+    const void *ph = (const char *)phi + f64 * f;
+    if (e - f == 1 && ka_r[f] == 0.0) {
+      // a plain S_PF alone: the single-system solver
+      TRY(force_pf(ctx, g, Uh, Ul, ph, kb_r[f], nullptr, 1.0, F, prm->tol_md, &prm->solver, acc));
+      *solves += 1;
+    } else {
+      TRY(force_mp(ctx, g, Uh, Ul, ph, e - f, ka_r + f, kb_r + f, 1.0, F, prm->tol_md,
+                   &prm->solver, acc));
+      *solves += 2;
+    }
+    f = e;
   }
-  return n + 1;
-}
-
-// Number of F64 even fields of hmc_trajectory's eta (and of phi).
-int traj_eta_fields(const hmc_traj_params *prm) {
-  if (rooted_terms(prm)) return rooted_terms(prm);
-  return prm->n_mp > 0 ? prm->n_mp + 1 : 1;
+  for (int f = nr; f < nt; ++f) {
+    if (term_level(prm, f) != l) continue;
+    double ka, kb;
+    int j = 0;
+    const TermKind kd = term_kind(prm, f, &ka, &kb, &j);
+    const hmc_filter flt = term_filter(prm, j, false, kd == TERM_POLY);
+    const void *ph = (const char *)phi + f64 * f;
+    if (kd == TERM_POLY)
+      TRY(force_pf(ctx, g, Uh, Ul, ph, prm->kappa, &flt, 1.0, F, prm->tol_md, &prm->solver,
+                   acc));
+    else
+      TRY(force_fratio(ctx, g, Uh, Ul, ph, prm->kappa, flt, ka, 1.0, F, prm->tol_md,
+                       &prm->solver, acc));
+    *solves += kd == TERM_POLY ? 0 : 2;
+  }
+  return HMC_OK;
 }
 
 // (F, F) = sum over links and components of F_a^2 (host)
@@ -457,22 +628,25 @@ static int algebra_norm2(hmc_ctx *ctx, const Geo &g, const double *F, double *ou
   return read_dev(ctx, dst, 1, out);
 }
 
-// Molecular dynamics on two time scales (Sec. I; gauge force on the fine
-// scale, pseudo-fermion force on the coarse one, Sec. IV), with the
-// leapfrog or the second-order Omelyan integrator (parameter lambda) in the
-// Sexton-Weingarten nesting:
-//   leapfrog: P_1(dt/2) [P_0(dt0/2) T(dt0) P_0(dt0/2)]^m P_1(dt/2), dt0 = dt/m
-//   Omelyan:  P_1(l dt) [T_0]^m P_1((1-2l) dt) [T_0]^m P_1(l dt), dt0 = dt/(2m),
-//             T_0 = P_0(l dt0) T(dt0/2) P_0((1-2l) dt0) T(dt0/2) P_0(l dt0)
-// with m = n_gauge.  Momentum steps are deferred: a step only adds its
-// coefficient to the pending sum of its force, and the pending sums are
-// applied (one force evaluation each) just before the next link update and
-// at the end.  Adjacent steps of one force at the same U thereby merge into
-// one evaluation, and steps of different forces at the same U commute, so
-// the integrator is unchanged.  U1 is the F64/LINK18 field, Ulo its
+// Molecular dynamics in the Sexton-Weingarten scheme of Sec. I with J levels
+// (default two: gauge force with the hopping-expansion term on the fine
+// level 0, every pseudo-fermion term on level 1, m_0 = n_gauge), the
+// leapfrog or the second-order Omelyan integrator (parameter lambda):
+//   leapfrog: T_0 = P_0(dt/2) T(dt) P_0(dt/2),
+//             T_l = P_l(dt/2) [T_{l-1}]^m P_l(dt/2),             inner dt / m
+//   Omelyan:  T_0 = P_0(l dt) T(dt/2) P_0((1-2l) dt) T(dt/2) P_0(l dt),
+//             T_l = P_l(l dt) [T_{l-1}]^m P_l((1-2l) dt) [T_{l-1}]^m P_l(l dt),
+//             inner dt / (2m)
+// with m = m_{l-1}; the outermost level takes n_md steps of dt = tau / n_md.
+// Momentum steps are deferred: a step only adds its coefficient to the
+// pending sum of its level, and the pending sums are applied (one force
+// evaluation each, outermost level first) just before the next link update
+// and at the end.  Adjacent steps of one level at the same U thereby merge
+// into one evaluation, and steps of different levels at the same U commute,
+// so the integrator is unchanged.  U1 is the F64/LINK18 field, Ulo its
 // inner-precision copy (refreshed from U1 before every pseudo-fermion
 // force), F scratch for the force.  fs (nullable) receives |F|^2 of every
-// force evaluation.
+// force evaluation (all the pseudo-fermion terms of a level count as one).
 int md_evolve(hmc_ctx *ctx, const Geo &g, void *U1, void *Ulo, double *P, double *F,
               const void *phi, const hmc_traj_params *prm, int *solves, hmc_solve_stats *acc,
               ForceStats *fs) {
@@ -482,34 +656,13 @@ int md_evolve(hmc_ctx *ctx, const Geo &g, void *U1, void *Ulo, double *P, double
   hmc_gauge Uh{U1, HMC_F64, HMC_LINK18};
   hmc_gauge Ul{Ulo, plo, fmt_lo};
   const hmc_gauge *Ulp = plo != HMC_F64 ? &Ul : nullptr;
-  hmc_filter fmd{prm->b, prm->n_t, prm->alpha};
-  const hmc_filter *filt_md = k ? &fmd : nullptr;
   const size_t fbytes = (size_t)g.Vh * 2 * 4 * 8 * sizeof(double);
   cudaStream_t st = ctx->stream;
-  const double dt = prm->tau / prm->n_md, dt0 = dt / prm->n_gauge;
-  double ka[16], kb[16];
-  const int n_terms = prm->n_mp > 0 ? mp_pairs(prm, ka, kb) : 0;
-  auto pf_step = [&](double eps) -> int {
+  const double dt = prm->tau / prm->n_md;
+  auto pf_step = [&](int l, double eps) -> int {
     TRY(cuda_ok(ctx, cudaMemsetAsync(F, 0, fbytes, st), "md: zero F"));
     if (plo != HMC_F64) TRY(convert_gauge(ctx, g, U1, Ulo, plo, fmt_lo));
-    if (rooted_terms(prm)) {
-      const size_t f64 = spinor_bytes(g, HMC_F64, 1);
-      for (int f = 0; f < rooted_terms(prm); ++f) {
-        const hmc_filter flt = rooted_filter(prm, f, false);
-        TRY(force_pf(ctx, g, Uh, Ulp, (const char *)phi + f64 * f, prm->kappa, &flt, 1.0, F,
-                     prm->tol_md, &prm->solver, acc));
-      }
-      *solves += 2;
-    } else if (n_terms) {
-      // all terms of the chain at once: two batched solve stages
-      TRY(force_mp(ctx, g, Uh, Ulp, phi, n_terms, ka, kb, 1.0, F, prm->tol_md, &prm->solver,
-                   acc));
-      *solves += 2;
-    } else {
-      TRY(force_pf(ctx, g, Uh, Ulp, phi, prm->kappa, filt_md, 1.0, F, prm->tol_md, &prm->solver,
-                   acc));
-      *solves += k ? 2 : 1;
-    }
+    TRY(level_forces(ctx, g, Uh, Ulp, phi, prm, l, F, acc, solves));
     if (fs) {
       double f2;
       TRY(algebra_norm2(ctx, g, F, &f2));
@@ -545,46 +698,57 @@ int md_evolve(hmc_ctx *ctx, const Geo &g, void *U1, void *Ulo, double *P, double
     }
     return update_momenta(ctx, g, P, F, eps);
   };
-  double pend_pf = 0.0, pend_g = 0.0;
+  const int J = n_level(prm);
+  double pend[8] = {0.0};
   auto flush = [&]() -> int {
-    if (pend_pf != 0.0) TRY(pf_step(pend_pf));
-    if (pend_g != 0.0) TRY(gauge_step(pend_g));
-    pend_pf = pend_g = 0.0;
+    for (int l = J - 1; l >= 1; --l)
+      if (pend[l] != 0.0) {
+        TRY(pf_step(l, pend[l]));
+        pend[l] = 0.0;
+      }
+    if (pend[0] != 0.0) TRY(gauge_step(pend[0]));
+    pend[0] = 0.0;
     return HMC_OK;
   };
   auto T = [&](double eps) -> int {
     TRY(flush());
     return update_links(ctx, g, U1, P, eps, prm->solver.f64_emul != 0);
   };
-  const int m = prm->n_gauge;
-  if (prm->integrator == HMC_INTEGRATOR_OMELYAN) {
-    const double lam = prm->lambda, dto = dt / (2.0 * m);
-    auto fine = [&]() -> int {
-      pend_g += lam * dto;
-      TRY(T(0.5 * dto));
-      pend_g += (1.0 - 2.0 * lam) * dto;
-      TRY(T(0.5 * dto));
-      pend_g += lam * dto;
-      return HMC_OK;
-    };
-    for (int s = 0; s < prm->n_md; ++s) {
-      pend_pf += lam * dt;
-      for (int j = 0; j < m; ++j) TRY(fine());
-      pend_pf += (1.0 - 2.0 * lam) * dt;
-      for (int j = 0; j < m; ++j) TRY(fine());
-      pend_pf += lam * dt;
-    }
-  } else {
-    for (int s = 0; s < prm->n_md; ++s) {
-      pend_pf += 0.5 * dt;
-      for (int j = 0; j < m; ++j) {
-        pend_g += 0.5 * dt0;
-        TRY(T(dt0));
-        pend_g += 0.5 * dt0;
+  const bool omelyan = prm->integrator == HMC_INTEGRATOR_OMELYAN;
+  const double lam = prm->lambda;
+  // one step T_l of size h
+  std::function<int(int, double)> step = [&](int l, double h) -> int {
+    if (l == 0) {
+      if (omelyan) {
+        pend[0] += lam * h;
+        TRY(T(0.5 * h));
+        pend[0] += (1.0 - 2.0 * lam) * h;
+        TRY(T(0.5 * h));
+        pend[0] += lam * h;
+      } else {
+        pend[0] += 0.5 * h;
+        TRY(T(h));
+        pend[0] += 0.5 * h;
       }
-      pend_pf += 0.5 * dt;
+      return HMC_OK;
     }
-  }
+    const int m = level_m(prm, l - 1);
+    if (omelyan) {
+      const double hi = h / (2.0 * m);
+      pend[l] += lam * h;
+      for (int j = 0; j < m; ++j) TRY(step(l - 1, hi));
+      pend[l] += (1.0 - 2.0 * lam) * h;
+      for (int j = 0; j < m; ++j) TRY(step(l - 1, hi));
+      pend[l] += lam * h;
+    } else {
+      const double hi = h / m;
+      pend[l] += 0.5 * h;
+      for (int j = 0; j < m; ++j) TRY(step(l - 1, hi));
+      pend[l] += 0.5 * h;
+    }
+    return HMC_OK;
+  };
+  for (int s = 0; s < prm->n_md; ++s) TRY(step(J - 1, dt));
   return flush();
 }
 
@@ -602,8 +766,6 @@ static int check_traj_params(hmc_ctx *ctx, const hmc_traj_params *prm) {
   if (prm->root_levels < 0 || prm->root_levels > 8)
     return fail(ctx, HMC_EINVAL, "trajectory: root_levels must be 0..8");
   if (prm->root_levels > 0) {
-    if (prm->n_mp != 0)
-      return fail(ctx, HMC_EINVAL, "trajectory: rooted polynomials need n_mp == 0");
     if (prm->root_N < 1 || prm->root_levels * prm->root_N > 64 || !prm->root_deg || !prm->root_c)
       return fail(ctx, HMC_EINVAL, "trajectory: root_N >= 1, at most 64 polynomial fields, "
                                    "root_deg and root_c needed");
@@ -616,8 +778,6 @@ static int check_traj_params(hmc_ctx *ctx, const hmc_traj_params *prm) {
   if (prm->n_mp < 0 || prm->n_mp > 15)
     return fail(ctx, HMC_EINVAL, "trajectory: n_mp must be 0..15");
   if (prm->n_mp > 0) {
-    if (prm->filter_k != 0)
-      return fail(ctx, HMC_EINVAL, "trajectory: mass preconditioning needs filter_k == 0");
     if (!prm->kappa_mp) return fail(ctx, HMC_EINVAL, "trajectory: kappa_mp is NULL");
     for (int j = 0; j < prm->n_mp; ++j) {
       const double nxt = j + 1 < prm->n_mp ? prm->kappa_mp[j + 1] : prm->kappa;
@@ -625,6 +785,18 @@ static int check_traj_params(hmc_ctx *ctx, const hmc_traj_params *prm) {
         return fail(ctx, HMC_EINVAL, "trajectory: need 0 < kappa_mp[0] < ... < kappa");
     }
   }
+  if (prm->n_levels != 0 && (prm->n_levels < 2 || prm->n_levels > 8))
+    return fail(ctx, HMC_EINVAL, "trajectory: n_levels must be 0 or 2..8");
+  const int J = n_level(prm);
+  if (prm->n_levels)
+    for (int i = 0; i + 1 < J; ++i)
+      if (prm->level_steps[i] < 1)
+        return fail(ctx, HMC_EINVAL, "trajectory: level_steps[%d] must be >= 1", i);
+  if (prm->term_level)
+    for (int f = 0; f < n_terms(prm); ++f)
+      if (prm->term_level[f] < 1 || prm->term_level[f] > J - 1)
+        return fail(ctx, HMC_EINVAL, "trajectory: term_level[%d] = %d not in 1..%d", f,
+                    prm->term_level[f], J - 1);
   return check_prec(ctx, prm->solver.inner_prec);
 }
 
@@ -667,6 +839,36 @@ int hmc_action_pf(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
   if (!phi || !action) return fail(ctx, HMC_EINVAL, "action_pf: NULL argument");
   if (stats) memset(stats, 0, sizeof(*stats));
   return action_pf(ctx, make_geo(*lat), *U_hi, U_lo, phi, kappa, filt, tol, opts, action, stats);
+}
+
+int hmc_force_fratio(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
+                     const hmc_gauge *U_lo, const void *phi, double kappa, const hmc_filter *filt,
+                     double kappa_a, double coeff, double *F, double tol,
+                     const hmc_solver_opts *opts, hmc_solve_stats *stats) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  TRY(check_solver_args(ctx, U_hi, U_lo, opts));
+  if (!phi || !F || !filt || !filt->b || filt->n < 0)
+    return fail(ctx, HMC_EINVAL, "force_fratio: NULL field or bad filter");
+  if (!(kappa_a >= 0.0)) return fail(ctx, HMC_EINVAL, "force_fratio: kappa_a must be >= 0");
+  if (stats) memset(stats, 0, sizeof(*stats));
+  return force_fratio(ctx, make_geo(*lat), *U_hi, U_lo, phi, kappa, *filt, kappa_a, coeff, F, tol,
+                      opts, stats);
+}
+
+int hmc_action_fratio(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
+                      const hmc_gauge *U_lo, const void *phi, double kappa,
+                      const hmc_filter *filt, double kappa_a, double tol,
+                      const hmc_solver_opts *opts, double *action, hmc_solve_stats *stats) {
+  CTX_CHECK(ctx);
+  TRY(check_lattice(ctx, lat));
+  TRY(check_solver_args(ctx, U_hi, U_lo, opts));
+  if (!phi || !action || !filt || !filt->b || filt->n < 0)
+    return fail(ctx, HMC_EINVAL, "action_fratio: NULL argument or bad filter");
+  if (!(kappa_a >= 0.0)) return fail(ctx, HMC_EINVAL, "action_fratio: kappa_a must be >= 0");
+  if (stats) memset(stats, 0, sizeof(*stats));
+  return action_fratio(ctx, make_geo(*lat), *U_hi, U_lo, phi, kappa, *filt, kappa_a, tol, opts,
+                       action, stats);
 }
 
 int hmc_force_hopexp(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U, double beta,
@@ -792,11 +994,8 @@ int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj
   void *U1 = workspace(ctx, "tr_u1", gb);
   void *Ulo = plo != HMC_F64 ? workspace(ctx, "tr_ulo", gauge_bytes(g, plo, fmt_lo)) : nullptr;
   double *P = (double *)workspace(ctx, "tr_p", ab), *F = (double *)workspace(ctx, "tr_f", ab);
-  double ka[16], kb[16];
-  const int n_terms = prm->n_mp > 0 ? mp_pairs(prm, ka, kb) : 0;
-  const int n_root = rooted_terms(prm);
-  const int n_fields = n_root ? n_root : (n_terms ? n_terms : 1);
-  void *phi = workspace(ctx, "tr_phi", f64 * n_fields);
+  const int nt = n_terms(prm), nr = n_ratio(prm);
+  void *phi = workspace(ctx, "tr_phi", f64 * nt);
   void *t1 = workspace(ctx, "tr_t1", f64);
   void *t2 = workspace(ctx, "tr_t2", f64);
   if (!U1 || (plo != HMC_F64 && !Ulo) || !P || !F || !phi || !t1 || !t2) return HMC_ENOMEM;
@@ -811,64 +1010,67 @@ int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj
     return convert_gauge(ctx, g, U1, Ulo, plo, fmt_lo);
   };
   const int k = prm->filter_k;
-  hmc_filter fact{prm->b, prm->n_max, prm->alpha};
-  const hmc_filter *filt_act = k ? &fact : nullptr;
   hmc_solve_stats acc{};
-  // heatbath of the pseudo-fermion field and H0
-  double kin0, sg0, spf0;
-  if (n_root) {
-    // polynomial terms: phi = P_j^{-1} eta; remainder: phi = prod_j P_j^N
-    // Mhat sum c_n K^n eta; H0 from the actions evaluated at the start
-    HiOps hi;
-    TRY(hi_begin(ctx, g, Uh, &prm->solver, &hi, "tr"));
-    TRY(refresh_lo());
-    for (int f = 0; f + 1 < n_root; ++f) {
-      const int j = f / prm->root_N;
-      int it;
-      double rel;
-      // to tol_md: H0 evaluates the actions at the start, so the heatbath's
-      // accuracy does not enter dH
-      TRY(poly_solve(ctx, g, Uh, Ulp, (char *)phi + f64 * f, (const char *)eta + f64 * f,
-                     prm->root_c[j], prm->root_deg[j], prm->kappa, prm->tol_md, 2000,
-                     &prm->solver, &it, &rel));
+  // heatbath of every pseudo-fermion field and H0: the ratio terms' heatbath
+  // is exact (S = |eta|^2); the filtered and rooted terms' heatbath series is
+  // truncated, so their actions are evaluated at the start (Sec. II)
+  double kin0, sg0, spf0 = 0.0;
+  HiOps hi;
+  TRY(hi_begin(ctx, g, Uh, &prm->solver, &hi, "tr"));
+  TRY(refresh_lo());
+  if (nr > 0) {
+    double ka[80], kb[80];
+    ratio_pairs(prm, ka, kb);
+    if (nr == 1 && ka[0] == 0.0) {
+      TRY(hi_mhat(hi, 1, phi, eta, kb[0], 1, nullptr));  // phi = Mhat^dag eta
+    } else {
+      // phi_j = Mhat_b^dag Mhat_a^{-dag} eta_j
+      TRY(heatbath_mp(ctx, g, Uh, Ulp, eta, nr, ka, kb, prm->tol_action, &prm->solver, phi,
+                      &acc));
+      res->solves += 1;
     }
-    void *rem = (char *)phi + f64 * (n_root - 1);
-    TRY(hi_poly_K(hi, t2, (const char *)eta + f64 * (n_root - 1), prm->c, prm->n_max,
-                  prm->kappa));
-    TRY(hi_mhat(hi, 0, rem, t2, prm->kappa, 1, nullptr));
-    for (int j = 0; j < prm->root_levels; ++j)
-      for (int q = 0; q < prm->root_N; ++q) {
-        TRY(hi_poly_K(hi, t2, rem, prm->root_c[j], prm->root_deg[j], prm->kappa));
-        TRY(copy_convert(ctx, HMC_F64, HMC_F64, rem, t2, g.Vh));
-      }
-    TRY(rooted_action(ctx, g, Uh, Ulp, phi, prm, &spf0, &acc));
-    res->solves += 1;
-  } else if (n_terms) {
-    // phi_j = Mhat_b^dag Mhat_a^{-dag} eta_j: the start action is sum |eta_j|^2
-    TRY(refresh_lo());
-    TRY(heatbath_mp(ctx, g, Uh, Ulp, eta, n_terms, ka, kb, prm->tol_action, &prm->solver, phi,
-                    &acc));
-    spf0 = 0.0;
-    for (int j = 0; j < n_terms; ++j) {
+    for (int f = 0; f < nr; ++f) {
       double e2;
-      TRY(norm2_host(ctx, g, HMC_F64, (const char *)eta + f64 * j, &e2));
+      TRY(norm2_host(ctx, g, HMC_F64, (const char *)eta + f64 * f, &e2));
       spf0 += e2;
     }
+  }
+  for (int f = nr; f < nt; ++f) {
+    double ka, kb;
+    int j = 0;
+    const TermKind kd = term_kind(prm, f, &ka, &kb, &j);
+    void *ph = (char *)phi + f64 * f;
+    const void *e = (const char *)eta + f64 * f;
+    if (kd == TERM_POLY) {
+      // phi = P_j^{-1} eta to tol_md: H0 evaluates the action at the start,
+      // so the heatbath's accuracy does not enter dH
+      int it;
+      double rel;
+      TRY(poly_solve(ctx, g, Uh, Ulp, ph, e, prm->root_c[j], prm->root_deg[j], prm->kappa,
+                     prm->tol_md, 2000, &prm->solver, &it, &rel));
+      continue;
+    }
+    // filtered ratio term: phi = Mhat_a^{-1} [prod_j P_j^N] Mhat sum c_n K^n eta
+    void *y = ka != 0.0 ? t1 : ph;
+    TRY(hi_poly_K(hi, t2, e, prm->c, prm->n_max, prm->kappa));
+    TRY(hi_mhat(hi, 0, y, t2, prm->kappa, 1, nullptr));
+    for (int q = 0; q < prm->root_levels; ++q)
+      for (int r = 0; r < prm->root_N; ++r) {
+        TRY(hi_poly_K(hi, t2, y, prm->root_c[q], prm->root_deg[q], prm->kappa));
+        TRY(copy_convert(ctx, HMC_F64, HMC_F64, y, t2, g.Vh));
+      }
+    if (ka != 0.0) {
+      // Mhat_a^{-1} y = (Mhat_a^dag Mhat_a)^{-1} Mhat_a^dag y
+      TRY(hi_mhat(hi, 1, t2, y, ka, 1, nullptr));
+      TRY(solve(ctx, g, Uh, Ulp, ph, t2, ka, prm->tol_action, &prm->solver, &acc));
+      res->solves += 1;
+    }
+  }
+  if (nr < nt) {
+    double sa;
+    TRY(terms_action(ctx, g, Uh, Ulp, phi, prm, nr, nt, &sa, &acc));
+    spf0 += sa;
     res->solves += 1;
-  } else if (k == 0) {
-    HiOps hi;
-    TRY(hi_begin(ctx, g, Uh, &prm->solver, &hi, "tr"));
-    TRY(hi_mhat(hi, 1, phi, eta, prm->kappa, 1, nullptr));
-    TRY(norm2_host(ctx, g, HMC_F64, eta, &spf0));  // S_PF(Mhat^dag eta) = |eta|^2
-  } else {
-    HiOps hi;
-    TRY(hi_begin(ctx, g, Uh, &prm->solver, &hi, "tr"));
-    TRY(hi_poly_K(hi, t2, eta, prm->c, prm->n_max, prm->kappa));
-    TRY(hi_mhat(hi, 0, phi, t2, prm->kappa, 1, nullptr));
-    TRY(refresh_lo());
-    TRY(action_pf(ctx, g, Uh, Ulp, phi, prm->kappa, filt_act, prm->tol_action, &prm->solver,
-                  &spf0, &acc));
-    res->solves += 2;
   }
   TRY(hmc_kinetic(ctx, lat, P, &kin0));
   double ps0;
@@ -884,14 +1086,7 @@ int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj
   TRY(hmc_kinetic(ctx, lat, P, &kin1));
   TRY(gauge_action(ctx, g, Uh, prm->beta, prm->kappa, k, &sg1, &ps1));
   TRY(refresh_lo());
-  if (n_root)
-    TRY(rooted_action(ctx, g, Uh, Ulp, phi, prm, &spf1, &acc));
-  else if (n_terms)
-    TRY(action_mp(ctx, g, Uh, Ulp, phi, n_terms, ka, kb, prm->tol_action, &prm->solver, &spf1,
-                  &acc));
-  else
-    TRY(action_pf(ctx, g, Uh, Ulp, phi, prm->kappa, filt_act, prm->tol_action, &prm->solver,
-                  &spf1, &acc));
+  TRY(terms_action(ctx, g, Uh, Ulp, phi, prm, 0, nt, &spf1, &acc));
   res->solves += 1;
   res->H1 = kin1 + sg1 + spf1;
   res->dH = res->H1 - res->H0;

@@ -59,7 +59,8 @@ class TrajParams(ctypes.Structure):
                 ("n_mp", _I), ("kappa_mp", _P),
                 ("integrator", _I), ("lam", _D),
                 ("root_levels", _I), ("root_N", _I), ("root_deg", _P), ("root_c", _P),
-                ("measure_forces", _I)]
+                ("measure_forces", _I),
+                ("n_levels", _I), ("level_steps", _I * 8), ("term_level", _P)]
 
 
 class TrajResult(ctypes.Structure):
@@ -110,6 +111,8 @@ _SIGS = {
     "hmc_cg_solve": (_I, [_P, _P, _P, _P, _P, _P, _D, _D, _I, _P, _P]),
     "hmc_cg_solve_multi": (_I, [_P, _P, _P, _P, _P, _P, _P, _I, _D, _I, _P, _P]),
     "hmc_force_pf": (_I, [_P, _P, _P, _P, _P, _D, _P, _D, _P, _D, _P, _P]),
+    "hmc_force_fratio": (_I, [_P, _P, _P, _P, _P, _D, _P, _D, _D, _P, _D, _P, _P]),
+    "hmc_action_fratio": (_I, [_P, _P, _P, _P, _P, _D, _P, _D, _D, _P, _P, _P]),
     "hmc_action_pf": (_I, [_P, _P, _P, _P, _P, _D, _P, _D, _P, _P, _P]),
     "hmc_force_hopexp": (_I, [_P, _P, _P, _D, _D, _I, _D, _P, _P]),
     "hmc_plaquette": (_I, [_P, _P, _P, _P]),
@@ -475,6 +478,39 @@ class Context:
         self._check(st, "hmc_force_pf")
         return {"iterations": stats.iterations, "true_rel_res": stats.true_rel_res}
 
+    def force_fratio(self, L, U_hi, phi, kappa, b, alpha, kappa_a, F, coeff=1.0, tol=1e-12,
+                     U_lo=None, inner_prec=F64, reliable_delta=0.1, force_prec=F64, f64_emul=0,
+                     solver=SOLVER_CG):
+        """F += coeff * force of |Z Mhat(kappa_a) phi|^2, Z = alpha Mhat^{-1} + sum b_n K^n."""
+        self._stream()
+        gh = U_hi.gauge()
+        gl = U_lo.gauge() if U_lo is not None else None
+        flt, keep = self._filter(b, alpha)
+        opts = SolverOpts(inner_prec, reliable_delta, 16, force_prec, f64_emul, solver)
+        stats = SolveStats()
+        st = lib().hmc_force_fratio(self.h, _ref(lattice(L)), ctypes.byref(gh),
+                                    ctypes.byref(gl) if gl is not None else None, phi.ptr(),
+                                    kappa, ctypes.byref(flt), kappa_a, coeff, _dp(F.data), tol,
+                                    ctypes.byref(opts), ctypes.byref(stats))
+        self._check(st, "hmc_force_fratio")
+        return {"iterations": stats.iterations, "true_rel_res": stats.true_rel_res}
+
+    def action_fratio(self, L, U_hi, phi, kappa, b, alpha, kappa_a, tol=1e-13, U_lo=None,
+                      inner_prec=F64, f64_emul=0, solver=SOLVER_CG):
+        """|Z Mhat(kappa_a) phi|^2 with Z = alpha Mhat^{-1} + sum b_n K^n."""
+        self._stream()
+        gh = U_hi.gauge()
+        gl = U_lo.gauge() if U_lo is not None else None
+        flt, keep = self._filter(b, alpha)
+        opts = SolverOpts(inner_prec, 0.1, 16, F64, f64_emul, solver)
+        out = ctypes.c_double(0)
+        st = lib().hmc_action_fratio(self.h, _ref(lattice(L)), ctypes.byref(gh),
+                                     ctypes.byref(gl) if gl is not None else None, phi.ptr(),
+                                     kappa, ctypes.byref(flt), kappa_a, tol, ctypes.byref(opts),
+                                     ctypes.byref(out), None)
+        self._check(st, "hmc_action_fratio")
+        return out.value
+
     def action_pf(self, L, U_hi, phi, kappa, tol=1e-13, U_lo=None, inner_prec=F64, b=None,
                   alpha=0.0, f64_emul=0, solver=SOLVER_CG):
         """Pseudo-fermion action: plain phi^dag (Mhat^dag Mhat)^{-1} phi, or the filtered |(alpha
@@ -676,7 +712,7 @@ class Context:
                    inner_prec=F64, link_fmt_lo=LINK12, reliable_delta=0.1, U_end=None,
                    P_end=None, force_prec=F64, kappa_mp=None, integrator=LEAPFROG,
                    lam=1.0 / 6.0, f64_emul=0, root_polys=None, root_N=0, measure_forces=False,
-                   solver=SOLVER_CG):
+                   solver=SOLVER_CG, level_steps=None, term_level=None):
         """One HMC trajectory; U (F64/LINK18 gauge Field) is updated in place
         when accepted.  Returns the result as a dict.  kappa_mp: heavier
         hopping parameters of a mass-preconditioned chain (eta then from
@@ -689,7 +725,8 @@ class Context:
             inner_prec=inner_prec, link_fmt_lo=link_fmt_lo, reliable_delta=reliable_delta,
             force_prec=force_prec, kappa_mp=kappa_mp, integrator=integrator, lam=lam,
             f64_emul=f64_emul, root_polys=root_polys, root_N=root_N,
-            measure_forces=measure_forces, solver=solver)
+            measure_forces=measure_forces, solver=solver, level_steps=level_steps,
+            term_level=term_level)
         res = TrajResult()
         st = lib().hmc_trajectory(self.h, _ref(lattice(L)), U.ptr(), ctypes.byref(prm),
                                   _dp(P.data), eta.ptr(), u, ctypes.byref(res),
@@ -702,8 +739,11 @@ class Context:
                      b=None, c=None, alpha=0.0, tol_md=1e-10, tol_action=1e-12, inner_prec=F64,
                      link_fmt_lo=LINK12, reliable_delta=0.1, force_prec=F64, kappa_mp=None,
                      integrator=LEAPFROG, lam=1.0 / 6.0, f64_emul=0, root_polys=None, root_N=0,
-                     measure_forces=False, solver=SOLVER_CG):
-        """hmc_traj_params; arrays it points to are appended to keep."""
+                     measure_forces=False, solver=SOLVER_CG, level_steps=None, term_level=None):
+        """hmc_traj_params; arrays it points to are appended to keep.
+        level_steps: m_0 .. m_{J-2} of a J-level Sexton-Weingarten scheme
+        (None: two levels with m_0 = n_gauge); term_level: the level of each
+        pseudo-fermion field in eta's order (None: the outermost)."""
         prm = TrajParams(beta=beta, kappa=kappa, tau=tau, n_md=n_md, n_gauge=n_gauge,
                          filter_k=filter_k, n_t=n_t, n_max=n_max, alpha=alpha, tol_md=tol_md,
                          tol_action=tol_action,
@@ -713,11 +753,24 @@ class Context:
                          measure_forces=int(bool(measure_forces)))
         self._mp(prm, kappa_mp, keep)
         self._root(prm, root_polys, root_N, keep)
+        self._levels(prm, level_steps, term_level, keep)
         if b is not None:
             ab = np.ascontiguousarray(b, dtype=np.float64); keep.append(ab); prm.b = ab.ctypes.data
         if c is not None:
             ac = np.ascontiguousarray(c, dtype=np.float64); keep.append(ac); prm.c = ac.ctypes.data
         return prm
+
+    @staticmethod
+    def _levels(prm, level_steps, term_level, keep):
+        if level_steps is not None:
+            if not 1 <= len(level_steps) <= 7:
+                raise ValueError("level_steps: 1..7 entries (2..8 levels)")
+            prm.n_levels = len(level_steps) + 1
+            for i, m in enumerate(level_steps):
+                prm.level_steps[i] = int(m)
+        if term_level is not None:
+            tl = np.ascontiguousarray(term_level, dtype=np.int32); keep.append(tl)
+            prm.term_level = tl.ctypes.data
 
     # ---- heatbath random numbers and the Markov chain ---------------------------
     def random_momenta(self, L, seed, counter, P=None):
@@ -784,7 +837,7 @@ class Context:
                   b=None, alpha=0.0, tol_md=1e-10, inner_prec=F64, link_fmt_lo=LINK12,
                   reliable_delta=0.1, force_prec=F64, kappa_mp=None, integrator=LEAPFROG,
                   lam=1.0 / 6.0, f64_emul=0, root_polys=None, root_N=0, measure_forces=False,
-                  solver=SOLVER_CG):
+                  solver=SOLVER_CG, level_steps=None, term_level=None, n_max=None, c=None):
         """Molecular dynamics with phi fixed; U (F64/LINK18) and P updated in place."""
         self._stream()
         keep = []
@@ -797,10 +850,15 @@ class Context:
                          measure_forces=int(bool(measure_forces)))
         self._mp(prm, kappa_mp, keep)
         self._root(prm, root_polys, root_N, keep)
+        self._levels(prm, level_steps, term_level, keep)
+        if n_max is not None:
+            prm.n_max = n_max
         if b is not None:
             ab = np.ascontiguousarray(b, dtype=np.float64); keep.append(ab)
             prm.b = ab.ctypes.data
             prm.c = ab.ctypes.data  # unused by the MD step; satisfies the filter check
+        if c is not None:
+            ac = np.ascontiguousarray(c, dtype=np.float64); keep.append(ac); prm.c = ac.ctypes.data
         res = TrajResult()
         st = lib().hmc_md_evolve(self.h, _ref(lattice(L)), U.ptr(), _dp(P.data), phi.ptr(),
                                  ctypes.byref(prm), ctypes.byref(res))
