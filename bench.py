@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--timeline", action="store_true",
                     help="after the timed steps, run one more trajectory with a per-launch "
                          "event timeline and report its per-kernel shares")
-    ap.add_argument("--inner", default="f32", choices=["f16", "f32"])
+    ap.add_argument("--inner", default="f32", choices=["f16", "bf16", "f32"])
     ap.add_argument("--delta", type=float, default=1e-5, help="reliable-update threshold")
     ap.add_argument("--force-prec", default="f64e", choices=["f32", "f64", "f64e"],
                     help="precision of the molecular-dynamics force algebra (Dslash "
@@ -152,7 +152,7 @@ def run_kernel(args):
     if pname == "cgm":
         # batched solve of n systems (kappas of mass-preconditioned
         # pseudo-fermions) on the benchmark lattice, links shared per launch
-        inner = {"f64": hmc.F64, "f32": hmc.F32, "f16": hmc.F16}[fmt]
+        inner = {"f64": hmc.F64, "f32": hmc.F32, "f16": hmc.F16, "bf16": hmc.BF16}[fmt]
         n = int(parts[2])
         ks = ([0.150, 0.154, 0.1575] * 6)[:n]
         Ulat = I.gauge_links(LAT, EPS_LINKS, 1)
@@ -181,7 +181,7 @@ def run_kernel(args):
     if pname == "cg":
         # one CG solve of Mhat^dag Mhat on the benchmark lattice to 1e-10 with the
         # given inner precision (FP64 reliable updates), all Dslash classes timed
-        inner = {"f64": hmc.F64, "f32": hmc.F32, "f16": hmc.F16}[fmt]
+        inner = {"f64": hmc.F64, "f32": hmc.F32, "f16": hmc.F16, "bf16": hmc.BF16}[fmt]
         Ulat = I.gauge_links(LAT, EPS_LINKS, 1)
         Uh = ctx.pack_gauge(LAT, Ulat, hmc.F64, hmc.LINK18)
         Ul = ctx.pack_gauge(LAT, Ulat, inner, hmc.LINK12) if inner != hmc.F64 else None
@@ -217,7 +217,8 @@ def run_kernel(args):
                                           "GBs": round(v[2] / (v[1] * 1e-3) / 1e9, 1)}
                                       for k, v in st.items()}}), flush=True)
         return
-    prec = {"f64": hmc.F64, "f32": hmc.F32, "f16": hmc.F16, "f64e": hmc.F64E}[pname]
+    prec = {"f64": hmc.F64, "f32": hmc.F32, "f16": hmc.F16, "f64e": hmc.F64E,
+            "bf16": hmc.BF16}[pname]
     fmt = int(fmt)
     U = ctx.pack_gauge(LAT, I.gauge_links(LAT, EPS_LINKS, 1), prec, fmt)
     nr = args.rhs
@@ -378,7 +379,7 @@ def run_hmc(args):
     torch.cuda.set_device(local)
     barrier, allmax, allsum = rep.barrier, rep.allmax, rep.allsum
 
-    inner = hmc.F16 if args.inner == "f16" else hmc.F32
+    inner = {"f16": hmc.F16, "bf16": hmc.BF16, "f32": hmc.F32}[args.inner]
     ctx = hmc.Context(local)
     # measured CUDA-core FMA ceilings (the arithmetic rooflines)
     fma = {k: round(ctx.fma_peak(i), 2) for i, k in enumerate(("fp64", "fp32", "fp32x2"))}

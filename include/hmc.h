@@ -82,7 +82,11 @@ typedef enum {
  * FP64-accurate operator applications are needed on a GPU whose FP64 rate is
  * a small fraction of its FP32 rate.  Layouts as FP64 with a float2 (hi, lo)
  * in place of each double. */
-typedef enum { HMC_F64 = 0, HMC_F32 = 1, HMC_F16 = 2, HMC_F64E = 3 } hmc_prec;
+/* HMC_BF16: bfloat16 storage (8 significant bits, the float exponent range,
+ * so no per-site norm), float arithmetic; rounded to nearest even on store.
+ * Layouts as F16 without the norm array: spinor 8 bfloat16 [3][S]; links
+ * LINK18 bfloat162 x 9 per link, LINK12 4 bfloat16 x 3. */
+typedef enum { HMC_F64 = 0, HMC_F32 = 1, HMC_F16 = 2, HMC_F64E = 3, HMC_BF16 = 4 } hmc_prec;
 typedef enum { HMC_LINK18 = 18, HMC_LINK12 = 12 } hmc_link_fmt;
 
 typedef struct hmc_ctx hmc_ctx;
@@ -146,9 +150,21 @@ int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
  * before its next work; 0 launches every kernel on the caller's stream.
  * Results are bit-identical.  Graphs are not used while timing is enabled. */
 #define HMC_OPT_CG_GRAPH 2
-/* Sets option (HMC_OPT_DSLASH_VARIANT: -2..6, HMC_OPT_CG_GRAPH: 0 or 1) for
+/* HMC_OPT_WORKSPACE_GUARD: 1 frees the context's workspace and gives every
+ * buffer allocated afterwards a 4 KiB guard region of the byte 0xA5 after its
+ * end; hmc_workspace_check then reports any buffer whose guard was written (a
+ * bounds check of the library's internal buffers for tests; compute-sanitizer
+ * is not used).  0 (default): no guards. */
+#define HMC_OPT_WORKSPACE_GUARD 3
+/* Sets option (HMC_OPT_DSLASH_VARIANT: -2..6, HMC_OPT_CG_GRAPH: 0 or 1,
+ * HMC_OPT_WORKSPACE_GUARD: 0 or 1) for
  * every later call on ctx.  HMC_EINVAL for an unknown option or value. */
 int hmc_ctx_set_option(hmc_ctx *ctx, int option, int value);
+/* hmc_workspace_check: synchronises the context's streams and checks the
+ * guard regions of its workspace buffers (HMC_OPT_WORKSPACE_GUARD); *n_bad
+ * receives the number of buffers written past their end, whose names
+ * hmc_last_error lists.  Returns HMC_OK unless the check itself fails. */
+int hmc_workspace_check(hmc_ctx *ctx, int *n_bad);
 /* Statistics of the index-th kernel class seen since timing was enabled:
  * class name (e.g. "dslash_f16_12/cg"), launches, summed event time in ms and
  * summed algorithmic bytes.  Synchronises the stream.  HMC_EINVAL past the

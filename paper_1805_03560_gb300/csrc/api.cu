@@ -49,7 +49,8 @@ void *workspace(hmc_ctx *ctx, const char *name, size_t bytes) {
     b.p = nullptr;
     b.n = 0;
   }
-  cudaError_t e = cudaMalloc(&b.p, bytes);
+  const size_t extra = ctx->ws_guard ? WS_GUARD_BYTES : 0;
+  cudaError_t e = cudaMalloc(&b.p, bytes + extra);
   if (e != cudaSuccess) {
     b.p = nullptr;
     fail(ctx, HMC_ENOMEM, "workspace %s: cudaMalloc(%zu) failed: %s", name, bytes,
@@ -57,7 +58,24 @@ void *workspace(hmc_ctx *ctx, const char *name, size_t bytes) {
     return nullptr;
   }
   b.n = bytes;
+  b.guard = extra != 0;
+  if (b.guard) {
+    e = cudaMemsetAsync((char *)b.p + bytes, WS_GUARD_BYTE, extra, ctx->stream);
+    if (e != cudaSuccess) {
+      fail(ctx, HMC_ECUDA, "workspace %s: guard fill failed: %s", name, cudaGetErrorString(e));
+      return nullptr;
+    }
+  }
   return b.p;
+}
+
+// frees every workspace buffer (after the context's streams are idle)
+static void release_workspace(hmc_ctx *ctx) {
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->gstream) cudaStreamSynchronize(ctx->gstream);
+  for (auto &kv : ctx->ws)
+    if (kv.second.p) cudaFree(kv.second.p);
+  ctx->ws.clear();
 }
 
 static cudaEvent_t take_event(hmc_ctx *ctx) {
@@ -141,7 +159,8 @@ int check_lattice(hmc_ctx *ctx, const hmc_lattice *lat) {
 }
 
 int check_prec(hmc_ctx *ctx, int prec) {
-  if (prec != HMC_F64 && prec != HMC_F32 && prec != HMC_F16 && prec != HMC_F64E)
+  if (prec != HMC_F64 && prec != HMC_F32 && prec != HMC_F16 && prec != HMC_F64E &&
+      prec != HMC_BF16)
     return fail(ctx, HMC_EINVAL, "unsupported precision %d", prec);
   return HMC_OK;
 }
@@ -160,6 +179,7 @@ size_t spinor_bytes(const Geo &g, int prec, int n_rhs) {
     case HMC_F64: b = SpinorIO<HMC_F64>::bytes(S); break;
     case HMC_F32: b = SpinorIO<HMC_F32>::bytes(S); break;
     case HMC_F16: b = SpinorIO<HMC_F16>::bytes(S); break;
+    case HMC_BF16: b = SpinorIO<HMC_BF16>::bytes(S); break;
     case HMC_F64E: b = SpinorIO<HMC_F64E>::bytes(S); break;
     default: return 0;
   }
@@ -173,6 +193,7 @@ size_t gauge_bytes(const Geo &g, int prec, int fmt) {
     case HMC_F64: per = (size_t)fmt * 8; break;
     case HMC_F32: per = (size_t)fmt * 4; break;
     case HMC_F16: per = (size_t)fmt * 2; break;
+    case HMC_BF16: per = (size_t)fmt * 2; break;
     case HMC_F64E: per = (size_t)fmt * 8; break;
     default: return 0;
   }
@@ -213,6 +234,33 @@ int hmc_ctx_create(int device, hmc_ctx **out) {
     return HMC_ENOMEM;
   }
   *out = c;
+  return HMC_OK;
+}
+
+int hmc_workspace_check(hmc_ctx *ctx, int *n_bad) {
+  CTX_CHECK(ctx);
+  if (!n_bad) return fail(ctx, HMC_EINVAL, "workspace_check: n_bad is NULL");
+  *n_bad = 0;
+  int st = cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), "workspace_check: sync");
+  if (!st && ctx->gstream)
+    st = cuda_ok(ctx, cudaStreamSynchronize(ctx->gstream), "workspace_check: sync");
+  if (st) return st;
+  std::vector<unsigned char> h(WS_GUARD_BYTES);
+  std::string bad;
+  for (auto &kv : ctx->ws) {
+    const hmc_ctx::Buf &b = kv.second;
+    if (!b.p || !b.guard) continue;
+    st = cuda_ok(ctx, cudaMemcpy(h.data(), (char *)b.p + b.n, WS_GUARD_BYTES,
+                                 cudaMemcpyDeviceToHost), "workspace_check: read");
+    if (st) return st;
+    for (size_t i = 0; i < WS_GUARD_BYTES; ++i)
+      if (h[i] != WS_GUARD_BYTE) {
+        ++*n_bad;
+        bad += (bad.empty() ? "" : ", ") + kv.first;
+        break;
+      }
+  }
+  if (*n_bad) fail(ctx, HMC_OK, "workspace written past its end: %s", bad.c_str());
   return HMC_OK;
 }
 
@@ -268,6 +316,12 @@ int hmc_ctx_set_option(hmc_ctx *ctx, int option, int value) {
     case HMC_OPT_CG_GRAPH:
       if (value != 0 && value != 1) return fail(ctx, HMC_EINVAL, "cg graph option must be 0 or 1");
       ctx->cg_graph = value;
+      return HMC_OK;
+    case HMC_OPT_WORKSPACE_GUARD:
+      if (value != 0 && value != 1)
+        return fail(ctx, HMC_EINVAL, "workspace guard option must be 0 or 1");
+      if (value != ctx->ws_guard) release_workspace(ctx);
+      ctx->ws_guard = value;
       return HMC_OK;
     default:
       return fail(ctx, HMC_EINVAL, "unknown option %d", option);

@@ -282,6 +282,7 @@ __device__ __forceinline__ int dslash_site(const DslashArgs &a) {
 constexpr int ds_min_blocks(int sp) {
   return sp == HMC_F32    ? HMC_DS_MINB32
          : sp == HMC_F16  ? HMC_DS_MINB16
+         : sp == HMC_BF16 ? HMC_DS_MINB32
          : sp == HMC_F64E ? HMC_DS_MINB64E
                           : HMC_DS_MINB64;
 }
@@ -437,6 +438,8 @@ static bool launch_variant(const DslashArgs &a, int sprec, int fmt, int dagger, 
     case HMC_F32 * 100 + 12: launch_sf<HMC_F32, 12>(aa, dagger, pair, nb, st); break;
     case HMC_F16 * 100 + 18: launch_sf<HMC_F16, 18>(aa, dagger, pair, nb, st); break;
     case HMC_F16 * 100 + 12: launch_sf<HMC_F16, 12>(aa, dagger, pair, nb, st); break;
+    case HMC_BF16 * 100 + 18: launch_sf<HMC_BF16, 18>(aa, dagger, pair, nb, st); break;
+    case HMC_BF16 * 100 + 12: launch_sf<HMC_BF16, 12>(aa, dagger, pair, nb, st); break;
     case HMC_F64E * 100 + 18: launch_sf<HMC_F64E, 18>(aa, dagger, pair, nb, st); break;
     case HMC_F64E * 100 + 12: launch_sf<HMC_F64E, 12>(aa, dagger, pair, nb, st); break;
     default: return false;
@@ -559,6 +562,7 @@ int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int
   // right-hand sides), the input and output spinors once, the epilogue field
   // once, and the per-site norms of half storage
   const double rb = (sprec == HMC_F64 || sprec == HMC_F64E) ? 8.0 : (sprec == HMC_F32 ? 4.0 : 2.0);
+  // (BF16 storage: 2 bytes per real like F16, no norms)
   double bytes = (double)a.g.Vh * 8.0 * U.fmt * rb + (double)S * 24.0 * rb * (a.x ? 3.0 : 2.0);
   if (sprec == HMC_F16) bytes += (double)S * 4.0 * (a.x ? 3.0 : 2.0);
   if (a.cg_x) {
@@ -569,7 +573,8 @@ int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int
   }
   char cls[64];
   snprintf(cls, sizeof(cls), "dslash_%s_%d%s%s",
-           sprec == HMC_F64 ? "f64" : (sprec == HMC_F32 ? "f32" : (sprec == HMC_F16 ? "f16" : "f64e")),
+           sprec == HMC_F64 ? "f64" : sprec == HMC_F32 ? "f32" : sprec == HMC_F16 ? "f16"
+           : sprec == HMC_BF16 ? "bf16" : "f64e",
            U.fmt, a.tag ? "/" : "",
            a.tag ? a.tag : "");
   // kernel variant (hmc_ctx_set_option): bit 0 tiled site mapping, bit 1

@@ -359,7 +359,8 @@ bool launch_fmt(const DslashArgs &a, int dagger, int nr, cudaStream_t st) {
 }  // namespace
 
 bool dslash_mr_supported(int sprec, int n_rhs, int nr) {
-  return (sprec == HMC_F32 || sprec == HMC_F16) && nr >= 2 && nr <= 4 && n_rhs % nr == 0 &&
+  return (sprec == HMC_F32 || sprec == HMC_F16 || sprec == HMC_BF16) && nr >= 2 && nr <= 4 &&
+         n_rhs % nr == 0 &&
          n_rhs <= 16;
 }
 
@@ -371,6 +372,8 @@ bool launch_dslash_mr(const DslashArgs &a, int sprec, int fmt, int dagger, int n
     case HMC_F32 * 100 + 12: return launch_fmt<HMC_F32, 12>(a, dagger, nr, st);
     case HMC_F16 * 100 + 18: return launch_fmt<HMC_F16, 18>(a, dagger, nr, st);
     case HMC_F16 * 100 + 12: return launch_fmt<HMC_F16, 12>(a, dagger, nr, st);
+    case HMC_BF16 * 100 + 18: return launch_fmt<HMC_BF16, 18>(a, dagger, nr, st);
+    case HMC_BF16 * 100 + 12: return launch_fmt<HMC_BF16, 12>(a, dagger, nr, st);
     default: return false;
   }
 }

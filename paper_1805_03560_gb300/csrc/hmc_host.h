@@ -17,7 +17,10 @@ struct hmc_ctx {
   struct Buf {
     void *p = nullptr;
     size_t n = 0;
+    bool guard = false;  // WS_GUARD_BYTES of 0xA5 follow the n usable bytes
   };
+  // HMC_OPT_WORKSPACE_GUARD: new workspace buffers carry a guard region
+  int ws_guard = 0;
   std::map<std::string, Buf> ws;
   double *h_pinned = nullptr;  // small pinned host buffer for scalar reads
   // optional per-kernel-class timing: mode 1 brackets every hemi-Dslash with
@@ -77,6 +80,9 @@ int timing_resolve(hmc_ctx *ctx);
 constexpr int DS_NT = 128;   // threads per block, stencil kernels
 constexpr int BL_NT = 256;   // threads per block, BLAS kernels
 constexpr int FIN_NT = 1024; // threads of the single-block finalisers
+
+constexpr size_t WS_GUARD_BYTES = 4096;
+constexpr unsigned char WS_GUARD_BYTE = 0xA5;
 
 int fail(hmc_ctx *ctx, int code, const char *fmt, ...);
 // Checks the launch that just happened and counts it.

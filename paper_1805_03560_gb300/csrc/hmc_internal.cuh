@@ -2,6 +2,7 @@
 // geometry, and the load/store traits of the spinor and gauge layouts that
 // include/hmc.h documents.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -293,6 +294,39 @@ struct SpinorIO<HMC_F16> {
   }
 };
 
+// BF16 storage: 24 bfloat16 values per site in three 16-byte chunks, no
+// per-site norm (bfloat16 keeps the float exponent range; 8 significant bits).
+// Rounding to nearest even on store.
+template <>
+struct SpinorIO<HMC_BF16> {
+  using R = float;
+  static size_t bytes(size_t S) { return S * 3 * sizeof(uint4); }
+  static __device__ __forceinline__ void load(const void *base, int S, int s, Cx<float> v[12]) {
+    const uint4 *b = (const uint4 *)base;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 t = __ldg(b + (size_t)k * S + s);
+      const __nv_bfloat162 *hp = reinterpret_cast<const __nv_bfloat162 *>(&t);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float2 f = __bfloat1622float2(hp[j]);
+        v[4 * k + j] = {f.x, f.y};
+      }
+    }
+  }
+  static __device__ __forceinline__ void store(void *base, int S, int s, const Cx<float> v[12]) {
+    uint4 *b = (uint4 *)base;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 t;
+      __nv_bfloat162 *hp = reinterpret_cast<__nv_bfloat162 *>(&t);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) hp[j] = __floats2bfloat162_rn(v[4 * k + j].re, v[4 * k + j].im);
+      b[(size_t)k * S + s] = t;
+    }
+  }
+};
+
 // Emulated FP64: each real as a (hi, lo) float pair, one complex per float4;
 // the same 16 bytes per complex as FP64.
 template <>
@@ -442,6 +476,57 @@ struct LinkIO<HMC_F16, 18> {
 #pragma unroll
     for (int c = 0; c < 9; ++c)
       b[(size_t)c * Vh + h] = __floats2half2_rn((float)u[c].re, (float)u[c].im);
+  }
+};
+
+template <>
+struct LinkIO<HMC_BF16, 18> {
+  using R = float;
+  static constexpr int NC = 9;
+  static constexpr size_t chunk = 4;
+  static __device__ __forceinline__ void load(const void *base, int Vh, int h, Cx<float> u[9]) {
+    const __nv_bfloat162 *b = (const __nv_bfloat162 *)base;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      float2 t = __bfloat1622float2(b[(size_t)c * Vh + h]);
+      u[c] = {t.x, t.y};
+    }
+  }
+  static __device__ __forceinline__ void store(void *base, int Vh, int h, const Cx<double> u[9]) {
+    __nv_bfloat162 *b = (__nv_bfloat162 *)base;
+#pragma unroll
+    for (int c = 0; c < 9; ++c)
+      b[(size_t)c * Vh + h] = __floats2bfloat162_rn((float)u[c].re, (float)u[c].im);
+  }
+};
+
+template <>
+struct LinkIO<HMC_BF16, 12> {
+  using R = float;
+  static constexpr int NC = 3;
+  static constexpr size_t chunk = 8;
+  static __device__ __forceinline__ void load(const void *base, int Vh, int h, Cx<float> u[9]) {
+    const uint2 *b = (const uint2 *)base;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      uint2 t = __ldg(b + (size_t)c * Vh + h);
+      const __nv_bfloat162 *hp = reinterpret_cast<const __nv_bfloat162 *>(&t);
+      float2 a = __bfloat1622float2(hp[0]), d = __bfloat1622float2(hp[1]);
+      u[2 * c] = {a.x, a.y};
+      u[2 * c + 1] = {d.x, d.y};
+    }
+    reconstruct_row2(u);
+  }
+  static __device__ __forceinline__ void store(void *base, int Vh, int h, const Cx<double> u[9]) {
+    uint2 *b = (uint2 *)base;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      uint2 t;
+      __nv_bfloat162 *hp = reinterpret_cast<__nv_bfloat162 *>(&t);
+      hp[0] = __floats2bfloat162_rn((float)u[2 * c].re, (float)u[2 * c].im);
+      hp[1] = __floats2bfloat162_rn((float)u[2 * c + 1].re, (float)u[2 * c + 1].im);
+      b[(size_t)c * Vh + h] = t;
+    }
   }
 };
 

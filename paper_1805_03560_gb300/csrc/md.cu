@@ -359,6 +359,8 @@ int convert_gauge(hmc_ctx *ctx, const Geo &g, const void *src, void *dst, int pr
     case HMC_F32 * 100 + 12: k_convert_gauge<HMC_F32, 12><<<nb, 256, 0, st>>>(g, src, dst); break;
     case HMC_F16 * 100 + 18: k_convert_gauge<HMC_F16, 18><<<nb, 256, 0, st>>>(g, src, dst); break;
     case HMC_F16 * 100 + 12: k_convert_gauge<HMC_F16, 12><<<nb, 256, 0, st>>>(g, src, dst); break;
+    case HMC_BF16 * 100 + 18: k_convert_gauge<HMC_BF16, 18><<<nb, 256, 0, st>>>(g, src, dst); break;
+    case HMC_BF16 * 100 + 12: k_convert_gauge<HMC_BF16, 12><<<nb, 256, 0, st>>>(g, src, dst); break;
     case HMC_F64E * 100 + 18: k_convert_gauge<HMC_F64E, 18><<<nb, 256, 0, st>>>(g, src, dst); break;
     case HMC_F64E * 100 + 12: k_convert_gauge<HMC_F64E, 12><<<nb, 256, 0, st>>>(g, src, dst); break;
     default: return fail(ctx, HMC_EINVAL, "convert_gauge: bad precision/format %d/%d", prec, fmt);

@@ -104,6 +104,8 @@ int pack_gauge(hmc_ctx *ctx, const Geo &g, const double *Uc, void *Ud, int prec,
     case HMC_F32 * 100 + 12: gauge_l<HMC_F32, 12>(ctx, g, Uc, Ud, pack); break;
     case HMC_F16 * 100 + 18: gauge_l<HMC_F16, 18>(ctx, g, Uc, Ud, pack); break;
     case HMC_F16 * 100 + 12: gauge_l<HMC_F16, 12>(ctx, g, Uc, Ud, pack); break;
+    case HMC_BF16 * 100 + 18: gauge_l<HMC_BF16, 18>(ctx, g, Uc, Ud, pack); break;
+    case HMC_BF16 * 100 + 12: gauge_l<HMC_BF16, 12>(ctx, g, Uc, Ud, pack); break;
     case HMC_F64E * 100 + 18: gauge_l<HMC_F64E, 18>(ctx, g, Uc, Ud, pack); break;
     case HMC_F64E * 100 + 12: gauge_l<HMC_F64E, 12>(ctx, g, Uc, Ud, pack); break;
     default: return fail(ctx, HMC_EINVAL, "gauge: unsupported precision %d / format %d", prec, fmt);
@@ -127,6 +129,10 @@ int pack_spinor(hmc_ctx *ctx, const Geo &g, const double *c, void *d, int prec, 
     case HMC_F16:
       if (pack) k_pack_spinor<HMC_F16><<<nb, 256, 0, st>>>(g.Vh, n_rhs, c, d);
       else k_unpack_spinor<HMC_F16><<<nb, 256, 0, st>>>(g.Vh, n_rhs, d, (double *)c);
+      break;
+    case HMC_BF16:
+      if (pack) k_pack_spinor<HMC_BF16><<<nb, 256, 0, st>>>(g.Vh, n_rhs, c, d);
+      else k_unpack_spinor<HMC_BF16><<<nb, 256, 0, st>>>(g.Vh, n_rhs, d, (double *)c);
       break;
     case HMC_F64E:
       if (pack) k_pack_spinor<HMC_F64E><<<nb, 256, 0, st>>>(g.Vh, n_rhs, c, d);

@@ -276,6 +276,9 @@ int copy_convert(hmc_ctx *ctx, int pd, int ps, void *d, const void *s, int S) {
     case HMC_F64 * 10 + HMC_F16: copy_l<HMC_F64, HMC_F16>(ctx, d, s, S); break;
     case HMC_F32 * 10 + HMC_F32: copy_l<HMC_F32, HMC_F32>(ctx, d, s, S); break;
     case HMC_F16 * 10 + HMC_F16: copy_l<HMC_F16, HMC_F16>(ctx, d, s, S); break;
+    case HMC_BF16 * 10 + HMC_F64: copy_l<HMC_BF16, HMC_F64>(ctx, d, s, S); break;
+    case HMC_F64 * 10 + HMC_BF16: copy_l<HMC_F64, HMC_BF16>(ctx, d, s, S); break;
+    case HMC_BF16 * 10 + HMC_BF16: copy_l<HMC_BF16, HMC_BF16>(ctx, d, s, S); break;
     case HMC_F64E * 10 + HMC_F64: copy_l<HMC_F64E, HMC_F64>(ctx, d, s, S); break;
     case HMC_F64 * 10 + HMC_F64E: copy_l<HMC_F64, HMC_F64E>(ctx, d, s, S); break;
     case HMC_F64E * 10 + HMC_F64E: copy_l<HMC_F64E, HMC_F64E>(ctx, d, s, S); break;
@@ -290,6 +293,7 @@ int zero_field(hmc_ctx *ctx, int prec, void *d, int S) {
     case HMC_F64: k_zero<HMC_F64><<<nb, BL_NT, 0, ctx->stream>>>(d, S); break;
     case HMC_F32: k_zero<HMC_F32><<<nb, BL_NT, 0, ctx->stream>>>(d, S); break;
     case HMC_F16: k_zero<HMC_F16><<<nb, BL_NT, 0, ctx->stream>>>(d, S); break;
+    case HMC_BF16: k_zero<HMC_BF16><<<nb, BL_NT, 0, ctx->stream>>>(d, S); break;
     case HMC_F64E: k_zero<HMC_F64E><<<nb, BL_NT, 0, ctx->stream>>>(d, S); break;
     default: return fail(ctx, HMC_EINVAL, "zero: bad precision %d", prec);
   }
@@ -303,6 +307,7 @@ int norm_partials(hmc_ctx *ctx, int prec, const void *v, int S, double *partials
     case HMC_F64: k_norm<HMC_F64><<<nb, BL_NT, 0, ctx->stream>>>(v, S, partials); break;
     case HMC_F32: k_norm<HMC_F32><<<nb, BL_NT, 0, ctx->stream>>>(v, S, partials); break;
     case HMC_F16: k_norm<HMC_F16><<<nb, BL_NT, 0, ctx->stream>>>(v, S, partials); break;
+    case HMC_BF16: k_norm<HMC_BF16><<<nb, BL_NT, 0, ctx->stream>>>(v, S, partials); break;
     case HMC_F64E: k_norm<HMC_F64E><<<nb, BL_NT, 0, ctx->stream>>>(v, S, partials); break;
     default: return fail(ctx, HMC_EINVAL, "norm: bad precision %d", prec);
   }
@@ -316,6 +321,7 @@ int axpby(hmc_ctx *ctx, int prec, void *out, double a, const void *x, double b, 
     case HMC_F64: k_axpby<HMC_F64><<<nb, BL_NT, 0, ctx->stream>>>(out, a, x, b, y, S); break;
     case HMC_F32: k_axpby<HMC_F32><<<nb, BL_NT, 0, ctx->stream>>>(out, a, x, b, y, S); break;
     case HMC_F16: k_axpby<HMC_F16><<<nb, BL_NT, 0, ctx->stream>>>(out, a, x, b, y, S); break;
+    case HMC_BF16: k_axpby<HMC_BF16><<<nb, BL_NT, 0, ctx->stream>>>(out, a, x, b, y, S); break;
     case HMC_F64E: k_axpby<HMC_F64E><<<nb, BL_NT, 0, ctx->stream>>>(out, a, x, b, y, S); break;
     default: return fail(ctx, HMC_EINVAL, "axpby: bad precision %d", prec);
   }
@@ -421,6 +427,7 @@ int one_iteration(Solve &s, int k) {
     case HMC_F64: launch_xpay<HMC_F64>(s, par, nb_rr); break;
     case HMC_F32: launch_xpay<HMC_F32>(s, par, nb_rr); break;
     case HMC_F16: launch_xpay<HMC_F16>(s, par, nb_rr); break;
+    case HMC_BF16: launch_xpay<HMC_BF16>(s, par, nb_rr); break;
   }
   return launched(ctx, "cg_xpay");
 }
@@ -521,6 +528,10 @@ int true_residual_restart(Solve &s, int par, bool restart_lo, double *rr) {
       k_residual<HMC_F16><<<s.nb_bl, BL_NT, 0, s.ctx->stream>>>(s.r, s.b, s.q, rl, pl, s.S,
                                                                 s.tmp_part);
       break;
+    case HMC_BF16:
+      k_residual<HMC_BF16><<<s.nb_bl, BL_NT, 0, s.ctx->stream>>>(s.r, s.b, s.q, rl, pl, s.S,
+                                                                 s.tmp_part);
+      break;
   }
   TRY(launched(s.ctx, "residual"));
   k_cg_restart<<<1, FIN_NT, 0, s.ctx->stream>>>(s.st, s.tmp_part, s.nb_bl, par);
@@ -541,7 +552,7 @@ int cg_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
   s.g = g;
   s.Uh = Uh;
   s.plo = opts ? opts->inner_prec : HMC_F64;
-  if (s.plo != HMC_F64 && s.plo != HMC_F32 && s.plo != HMC_F16)
+  if (s.plo != HMC_F64 && s.plo != HMC_F32 && s.plo != HMC_F16 && s.plo != HMC_BF16)
     return fail(ctx, HMC_EINVAL, "cg: bad inner precision %d", s.plo);
   if (Uh.prec != HMC_F64) return fail(ctx, HMC_EINVAL, "cg: U_hi must be F64");
   if (s.plo != HMC_F64) {

@@ -304,6 +304,10 @@ int m_iteration(MSolve &s, int k) {
       k_mcg_axpy<HMC_F32, HMC_F16><<<s.nb_bl, BL_NT, 0, st>>>(s.xlo, s.rlo, s.p, s.Ap, s.S, s.n,
                                                               s.st, par, s.rr_part);
       break;
+    case HMC_BF16:
+      k_mcg_axpy<HMC_F32, HMC_BF16><<<s.nb_bl, BL_NT, 0, st>>>(s.xlo, s.rlo, s.p, s.Ap, s.S,
+                                                               s.n, s.st, par, s.rr_part);
+      break;
   }
   if (!s.mr) TRY(launched(ctx, "cg_multi_axpy"));
   switch (s.plo) {
@@ -315,6 +319,9 @@ int m_iteration(MSolve &s, int k) {
       break;
     case HMC_F16:
       k_mcg_xpay<HMC_F16><<<s.nb_bl, BL_NT, 0, st>>>(s.p, s.rlo, s.S, s.n, s.st, par, plain);
+      break;
+    case HMC_BF16:
+      k_mcg_xpay<HMC_BF16><<<s.nb_bl, BL_NT, 0, st>>>(s.p, s.rlo, s.S, s.n, s.st, par, plain);
       break;
   }
   return launched(ctx, "cg_multi_xpay");
@@ -344,6 +351,10 @@ int m_true_residual(MSolve &s, int par, double tol2) {
       k_mresidual<HMC_F16><<<s.nb_bl, BL_NT, 0, st>>>(s.r, s.b, s.q, s.rlo, s.p, s.S, s.n,
                                                       s.tmp_part);
       break;
+    case HMC_BF16:
+      k_mresidual<HMC_BF16><<<s.nb_bl, BL_NT, 0, st>>>(s.r, s.b, s.q, s.rlo, s.p, s.S, s.n,
+                                                       s.tmp_part);
+      break;
   }
   (void)mixed;
   TRY(launched(s.ctx, "residual_multi"));
@@ -364,7 +375,7 @@ int cg_solve_multi(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_ga
   s.Uh = Uh;
   s.n = n_rhs;
   s.plo = opts ? opts->inner_prec : HMC_F64;
-  if (s.plo != HMC_F64 && s.plo != HMC_F32 && s.plo != HMC_F16)
+  if (s.plo != HMC_F64 && s.plo != HMC_F32 && s.plo != HMC_F16 && s.plo != HMC_BF16)
     return fail(ctx, HMC_EINVAL, "cg_multi: bad inner precision %d", s.plo);
   if (Uh.prec != HMC_F64) return fail(ctx, HMC_EINVAL, "cg_multi: U_hi must be F64");
   const bool mixed = s.plo != HMC_F64;

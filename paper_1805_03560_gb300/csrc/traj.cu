@@ -27,8 +27,13 @@ static int read_dev(hmc_ctx *ctx, const double *dev, int n, double *host) {
 static double *scalars(hmc_ctx *ctx) { return (double *)workspace(ctx, "tr_scalars", 64 * 8); }
 
 static double *partials_buf(hmc_ctx *ctx, const Geo &g) {
-  // enough for two reductions over 8 Vh elements in blocks of 128
-  return (double *)workspace(ctx, "tr_partials", sizeof(double) * (2 * (8LL * g.Vh / 128 + 2) + 64));
+  // block partials of the largest reduction that uses it: the kinetic term
+  // and |F|^2 over the 64 Vh components of an algebra field in blocks of
+  // BL_NT (the gauge action needs two arrays of 2 Vh / 128, the spinor
+  // norms and dots Vh / BL_NT)
+  const long long kin = (64LL * g.Vh + BL_NT - 1) / BL_NT;
+  const long long act = 2 * ((2LL * g.Vh + 127) / 128);
+  return (double *)workspace(ctx, "tr_partials", sizeof(double) * ((kin > act ? kin : act) + 64));
 }
 
 // S_G + T_k on the host

@@ -13,7 +13,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhmc.so")
 
-F64, F32, F16, F64E = 0, 1, 2, 3
+F64, F32, F16, F64E, BF16 = 0, 1, 2, 3, 4
 LINK18, LINK12 = 18, 12
 LEAPFROG, OMELYAN = 0, 1
 PREC_NAMES = {F64: "f64", F32: "f32", F16: "f16", F64E: "f64e"}
@@ -95,6 +95,7 @@ _SIGS = {
     "hmc_ctx_set_timing": (_I, [_P, _I]),
     "hmc_ctx_set_option": (_I, [_P, _I, _I]),
     "hmc_measure_fma_peak": (_I, [_P, _I, _P]),
+    "hmc_workspace_check": (_I, [_P, _P]),
     "hmc_timing_get": (_I, [_P, _I, ctypes.c_char_p, _I, _P, _P, _P]),
     "hmc_gauge_bytes": (_SZ, [_P, _I, _I]),
     "hmc_spinor_bytes": (_SZ, [_P, _I, _I]),
@@ -266,6 +267,20 @@ class Context:
         self._check(lib().hmc_measure_fma_peak(self.h, int(kind), ctypes.byref(out)),
                     "hmc_measure_fma_peak")
         return out.value
+
+    def set_workspace_guard(self, on):
+        """Guard regions after every workspace buffer allocated from now on
+        (frees the current workspace)."""
+        self._check(lib().hmc_ctx_set_option(self.h, 3, int(bool(on))), "hmc_ctx_set_option")
+
+    def workspace_check(self):
+        """Names of workspace buffers written past their end ([] when none)."""
+        n = ctypes.c_int(0)
+        self._check(lib().hmc_workspace_check(self.h, ctypes.byref(n)), "hmc_workspace_check")
+        if n.value == 0:
+            return []
+        msg = lib().hmc_last_error(self.h).decode()
+        return msg.split(": ", 1)[-1].split(", ")
 
     def set_cg_graph(self, on):
         """Replay CG iterations from a captured CUDA graph (default on)."""
