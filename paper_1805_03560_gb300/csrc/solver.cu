@@ -151,6 +151,14 @@ __global__ void __launch_bounds__(BL_NT) k_cg_xpay(void *p, const void *r, int S
                                                    int n_part) {
   if (!st->active) return;
   using R = RT<PL>;
+  // the first grid-stride element's r and p are loaded before the sum of the
+  // partials, so that their DRAM latency overlaps the reduction
+  const int i0 = blockIdx.x * BL_NT + threadIdx.x;
+  Cx<R> rv[12], pv[12];
+  if (i0 < S) {
+    load_as<PL>(r, S, i0, rv);
+    load_as<PL>(p, S, i0, pv);
+  }
   __shared__ double s_rr;
   {
     double t = 0.0;
@@ -173,17 +181,28 @@ __global__ void __launch_bounds__(BL_NT) k_cg_xpay(void *p, const void *r, int S
     }
   }
   const R beta = (R)(rr_new / st->rr[par]);
-  // grid-stride: the grid is a few blocks per SM, so few blocks read the partials
-  for (int i = blockIdx.x * BL_NT + threadIdx.x; i < S; i += gridDim.x * BL_NT) {
-    Cx<R> rv[12], pv[12];
-    load_as<PL>(r, S, i, rv);
-    load_as<PL>(p, S, i, pv);
+  // grid-stride: the grid is a few blocks per SM, so few blocks read the
+  // partials; the next element's loads are issued before the current one is
+  // updated, two elements in flight per thread
+  const int stride = gridDim.x * BL_NT;
+  for (int i = i0; i < S; i += stride) {
+    Cx<R> rn[12], pn[12];
+    const int in = i + stride;
+    if (in < S) {
+      load_as<PL>(r, S, in, rn);
+      load_as<PL>(p, S, in, pn);
+    }
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       pv[k].re = fma(beta, pv[k].re, rv[k].re);
       pv[k].im = fma(beta, pv[k].im, rv[k].im);
     }
     store_as<PL>(p, S, i, pv);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      rv[k] = rn[k];
+      pv[k] = pn[k];
+    }
   }
 }
 

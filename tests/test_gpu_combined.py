@@ -168,3 +168,33 @@ def test_level_parameters_validated(ctx, H):
         with pytest.raises(H.HmcError) as e:
             ctx.trajectory(L, U, P, eta, 0.5, **base, **bad)
         assert e.value.status == H.EINVAL
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_rooted_kappa4_paper_parameter_set(ctx, H, mixed):
+    """The parameter set of the paper's rooted kappa^4 run (Sec. IV.B): root
+    N = 8, polynomials of degrees 16 and 42, remainder force to n_t = 160,
+    leapfrog on four levels with m_0 = 40, m_1 = 3, m_2 = 2 and m = 4 outer
+    steps, tau = sqrt(2) (kappa 0.12 on the synthetic 4^4 field, where the
+    roots' series converge), against the oracle's trajectory stored by
+    tests/golden/make_rooted_paper_set.py (the oracle takes ~4 minutes)."""
+    import json
+    import os
+    ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                      "rooted_paper_set.json")))
+    L = tuple(ref["lattice"])
+    kw = dict(ref["params"])
+    U = I.gauge_links(L, 0.3, 1)
+    P = I.momenta(L, 3)
+    eta = [I.gaussian_half(L, 40 + j) for j in range(2 * kw["root_N"] + 1)]
+    Ue = ctx.new_gauge(L, F64, 18)
+    extra = dict(MIXED, tol_md=1e-10, tol_action=1e-12) if mixed else \
+        dict(tol_md=ref["tol_md"], tol_action=ref["tol_action"])
+    r = ctx.trajectory(L, ctx.pack_gauge(L, U, F64, 18), ctx.pack_algebra(L, P),
+                       ctx.pack_spinors(L, eta), 0.5, U_end=Ue, **extra, **kw)
+    assert abs(r["H0"] - ref["H0"]) <= 1e-9 * abs(ref["H0"])
+    assert abs(r["dH"] - ref["dH"]) <= 1e-7, (r["dH"], ref["dH"])
+    Ug = _np(ctx.unpack_gauge(L, Ue))
+    for s, mu, m in ref["U_end_sample"]:
+        want = np.array([complex(a, b) for a, b in m]).reshape(3, 3)
+        assert np.abs(Ug[s, mu] - want).max() <= (1e-8 if mixed else 1e-10), (s, mu)
