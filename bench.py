@@ -509,11 +509,10 @@ def run_hmc(args):
     dom = max((k for k in kst if k.startswith("dslash")), key=lambda k: kst[k][1])
     n_dom, ms_dom, b_dom = kst[dom]
     pk = peaks()
-    if dom.startswith("dslash_f64"):
+    if dom.startswith("dslash_f64_"):
+        # native FP64: bound by the FP64 units (measured FMA rate)
         achieved = 1320.0 * Vh * n_dom / (ms_dom * 1e-3) / 1e9
-        # native FP64 against the measured FP64 FMA rate, emulated FP64 (on the
-        # FP32 pipe) against the measured FP32 rate
-        pk64 = fma["fp32" if dom.startswith("dslash_f64e") else "fp64"] * 1e3
+        pk64 = fma["fp64"] * 1e3
         roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 1),
                 "peak": pk64, "unit": "GFLOP/s",
                 "frac": round(achieved / pk64, 4), "traffic": None,

@@ -126,7 +126,8 @@ int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
  * variant: bit 0 maps each block of 128 threads onto four 32-site segments
  * at the offsets {0, +x, +t, +x+t} (when Ly*Lz/2 is a multiple of 32 and
  * n_rhs == 1; otherwise consecutive sites), bit 1 issues the loads of both
- * hops of a direction before their arithmetic.  Variants 0..3 compute the
+ * hops of a direction before their arithmetic (for F16/BF16 storage with
+ * 12-real links: of the four hops of two directions).  Variants 0..3 compute the
  * same result bit for bit.  Values 4, 5, 6 select, for n_rhs > 1 and FP32 or
  * FP16 storage, the multi-right-hand-side kernel with 2, 3 or 4 right-hand
  * sides per thread (each link loaded, rebuilt and indexed once for them,

@@ -160,6 +160,111 @@ __device__ __forceinline__ void hop_pair(const DslashArgs &a, int h, int r, int 
   accumulate<MU, -S>(acc, w);
 }
 
+// ---- half storage: the loads of two directions (four hops) in flight ------------
+// F16 and BF16 spinors are 48 bytes (+ a 4-byte norm for F16) and 12-real links
+// 24 bytes, so the raw chunks of four hops fit in the registers that two
+// FP32 hops' values take.  The loads of both hops of directions MU0 and MU1
+// are issued first, then converted and applied; the bytes in flight per
+// thread double against the paired form.  Same arithmetic as hop_fwd/hop_bwd.
+template <int SP>
+struct HalfRaw {
+  uint4 c[3];
+  float n;
+};
+template <int SP>
+__device__ __forceinline__ void half_load_raw(const void *base, int S, int s, HalfRaw<SP> &v) {
+  const uint4 *b = (const uint4 *)base;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v.c[k] = __ldg(b + (size_t)k * S + s);
+  if (SP == HMC_F16) v.n = __ldg((const float *)(b + (size_t)3 * S) + s);
+}
+template <int SP>
+__device__ __forceinline__ void half_convert(const HalfRaw<SP> &v, Cx<float> p[12]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const unsigned w = j == 0 ? v.c[k].x : j == 1 ? v.c[k].y : j == 2 ? v.c[k].z : v.c[k].w;
+      float2 f;
+      if (SP == HMC_F16) {
+        const __half2 hh = *reinterpret_cast<const __half2 *>(&w);
+        f = __half22float2(hh);
+        f.x *= v.n;
+        f.y *= v.n;
+      } else {
+        const __nv_bfloat162 hh = *reinterpret_cast<const __nv_bfloat162 *>(&w);
+        f = __bfloat1622float2(hh);
+      }
+      p[4 * k + j] = {f.x, f.y};
+    }
+  }
+}
+// 12-real half links: three 8-byte chunks (rows 0 and 1), row 2 rebuilt
+template <int SP>
+__device__ __forceinline__ void half_link_raw(const void *base, int Vh, int h, uint2 v[3]) {
+  const uint2 *b = (const uint2 *)base;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) v[c] = __ldg(b + (size_t)c * Vh + h);
+}
+template <int SP>
+__device__ __forceinline__ void half_link_convert(const uint2 v[3], Cx<float> u[9]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float2 a, d;
+    if (SP == HMC_F16) {
+      a = __half22float2(*reinterpret_cast<const __half2 *>(&v[c].x));
+      d = __half22float2(*reinterpret_cast<const __half2 *>(&v[c].y));
+    } else {
+      a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v[c].x));
+      d = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v[c].y));
+    }
+    u[2 * c] = {a.x, a.y};
+    u[2 * c + 1] = {d.x, d.y};
+  }
+  reconstruct_row2(u);
+}
+
+template <int SP, int MU, int S>
+__device__ __forceinline__ void half_apply(const HalfRaw<SP> &pr, const uint2 lr[3], bool fwd,
+                                           bool wrap, Cx<float> acc[12]) {
+  Cx<float> psi[12], u[9], hs[6], w[6];
+  half_convert<SP>(pr, psi);
+  half_link_convert<SP>(lr, u);
+  project<MU, S>(psi, hs);
+  if (wrap) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) hs[k] = -hs[k];
+  }
+  if (fwd)
+    mul_link(u, hs, w);
+  else
+    mul_link_dag(u, hs, w);
+  accumulate<MU, S>(acc, w);
+}
+
+template <int SP, int MU0, int MU1, int SF>
+__device__ __forceinline__ void hop_quad(const DslashArgs &a, int h, int r, int lex,
+                                         const int c[4], Cx<float> acc[12]) {
+  const int Vh = a.g.Vh, S_ = Vh * a.n_rhs, n = a.n_rhs;
+  const int f0 = nb_fwd(a.g, lex, c, MU0), b0 = nb_bwd(a.g, lex, c, MU0);
+  const int f1 = nb_fwd(a.g, lex, c, MU1), b1 = nb_bwd(a.g, lex, c, MU1);
+  HalfRaw<SP> p[4];
+  uint2 l[4][3];
+  half_load_raw<SP>(a.in, S_, f0 * n + r, p[0]);
+  half_link_raw<SP>(link_base<SP, 12>(a.gauge, Vh, a.p, MU0), Vh, h, l[0]);
+  half_load_raw<SP>(a.in, S_, b0 * n + r, p[1]);
+  half_link_raw<SP>(link_base<SP, 12>(a.gauge, Vh, 1 - a.p, MU0), Vh, b0, l[1]);
+  half_load_raw<SP>(a.in, S_, f1 * n + r, p[2]);
+  half_link_raw<SP>(link_base<SP, 12>(a.gauge, Vh, a.p, MU1), Vh, h, l[2]);
+  half_load_raw<SP>(a.in, S_, b1 * n + r, p[3]);
+  half_link_raw<SP>(link_base<SP, 12>(a.gauge, Vh, 1 - a.p, MU1), Vh, b1, l[3]);
+  const bool tlast = MU0 == 0 && c[0] == a.g.L[0] - 1, tfirst = MU0 == 0 && c[0] == 0;
+  half_apply<SP, MU0, SF>(p[0], l[0], true, tlast, acc);
+  half_apply<SP, MU0, -SF>(p[1], l[1], false, tfirst, acc);
+  half_apply<SP, MU1, SF>(p[2], l[2], true, false, acc);
+  half_apply<SP, MU1, -SF>(p[3], l[3], false, false, acc);
+}
+
 // ---- runtime-direction forms ----------------------------------------------------
 // One copy of the hop code serves all eight hops.  The fully unrolled stencil
 // of the double-float kind is several times larger than the instruction
@@ -266,12 +371,13 @@ __device__ __forceinline__ int dslash_site(const DslashArgs &a) {
 // register count allows, so fewer registers (more warps in flight) win as
 // long as nothing spills.  Measured on 24^3x48: FP32 storage at 6 blocks
 // (80 registers, no spills) 39.1 us against 41.4 us at 5 blocks (100
-// registers); FP16 storage and the FP64 kinds gain nothing.
+// registers); the FP64 kinds gain nothing.  Half storage (F16, BF16) at 4
+// blocks: its four-hop load form then fits in 128 registers without spills.
 #ifndef HMC_DS_MINB32
 #define HMC_DS_MINB32 6
 #endif
 #ifndef HMC_DS_MINB16
-#define HMC_DS_MINB16 1
+#define HMC_DS_MINB16 4
 #endif
 #ifndef HMC_DS_MINB64
 #define HMC_DS_MINB64 1
@@ -279,10 +385,13 @@ __device__ __forceinline__ int dslash_site(const DslashArgs &a) {
 #ifndef HMC_DS_MINB64E
 #define HMC_DS_MINB64E 3
 #endif
+#ifndef HMC_DS_MINBBF16
+#define HMC_DS_MINBBF16 4
+#endif
 constexpr int ds_min_blocks(int sp) {
   return sp == HMC_F32    ? HMC_DS_MINB32
          : sp == HMC_F16  ? HMC_DS_MINB16
-         : sp == HMC_BF16 ? HMC_DS_MINB32
+         : sp == HMC_BF16 ? HMC_DS_MINBBF16
          : sp == HMC_F64E ? HMC_DS_MINB64E
                           : HMC_DS_MINB64;
 }
@@ -319,6 +428,9 @@ __global__ void __launch_bounds__(DS_NT, ds_min_blocks(SP)) k_dslash(const Dslas
     for (int k = 0; k < 12; ++k) acc[k] = {R(0), R(0)};
     if constexpr (SP == HMC_F64E) {
       hops_rt<SP, FMT, SF>(a, h, r, lex, c, acc);
+    } else if constexpr ((SP == HMC_F16 || SP == HMC_BF16) && FMT == 12 && PAIR) {
+      hop_quad<SP, 0, 1, SF>(a, h, r, lex, c, acc);
+      hop_quad<SP, 2, 3, SF>(a, h, r, lex, c, acc);
     } else if (PAIR) {
       hop_pair<SP, FMT, 0, SF>(a, h, r, lex, c, acc);
       hop_pair<SP, FMT, 1, SF>(a, h, r, lex, c, acc);

@@ -19,7 +19,7 @@ from paper_1805_03560_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 # FP64, FP32, FP16 storage, emulated FP64, BF16 storage (8 significant bits:
-# inputs and output each rounded to 2^-9 relative, eight hops: 3e-2)
+# inputs and output each rounded to within 2^-8 relative, eight hops: 3e-2)
 TOL = {0: 1e-14, 1: 1e-6, 2: 4e-3, 3: 2e-13, 4: 3e-2}
 PRECS = [0, 1, 2, 3, 4]
 FMTS = [18, 12]
@@ -73,7 +73,7 @@ def test_spinor_pack_roundtrip(ctx, H, prec, n_rhs):
     assert np.array_equal(back, psi)
     g = I.gaussian_half(L, 2, n_rhs if n_rhs > 1 else None)
     back = _np(ctx.unpack_spinor(L, ctx.pack_spinor(L, g, prec)))
-    assert _rel(back, g) <= {0: 0, 1: 1e-7, 2: 1e-3, 3: 4e-15, 4: 2.5e-3}[prec]
+    assert _rel(back, g) <= {0: 0, 1: 1e-7, 2: 1e-3, 3: 4e-15, 4: 4e-3}[prec]
 
 
 def test_algebra_pack_roundtrip(ctx, H):
