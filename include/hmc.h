@@ -115,6 +115,11 @@ int hmc_ctx_set_stream(hmc_ctx *ctx, void *stream);
 const char *hmc_last_error(hmc_ctx *ctx);
 /* Number of kernels this context has launched so far. */
 long long hmc_launch_count(hmc_ctx *ctx);
+/* Number of times this context's calls have made the host wait for the
+ * device so far: every stream synchronisation inside a call (a solver reading
+ * its convergence state, a trajectory reading an action, the final wait of a
+ * synchronous call), the autotuner's and timing mode's waits included. */
+long long hmc_host_sync_count(hmc_ctx *ctx);
 /* Per-kernel-class timing.  Mode 1: every hemi-Dslash launch is bracketed by
  * two CUDA events on the context's stream and its algorithmic bytes (links,
  * input, output and epilogue spinors, each once) are counted.  Mode 2 (launch

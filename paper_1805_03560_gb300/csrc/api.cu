@@ -38,6 +38,11 @@ int launched(hmc_ctx *ctx, const char *what) {
   return HMC_OK;
 }
 
+int host_sync(hmc_ctx *ctx, const char *what) {
+  ctx->host_syncs += 1;
+  return cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), what);
+}
+
 void *workspace(hmc_ctx *ctx, const char *name, size_t bytes) {
   bytes = (bytes + 255) & ~(size_t)255;
   hmc_ctx::Buf &b = ctx->ws[name];
@@ -126,8 +131,8 @@ TimedLaunch::~TimedLaunch() {
 
 int timing_resolve(hmc_ctx *ctx) {
   if (ctx->pending.empty()) return HMC_OK;
-  cudaError_t e = cudaStreamSynchronize(ctx->stream);
-  if (e != cudaSuccess) return cuda_ok(ctx, e, "timing: synchronise");
+  const int sst = host_sync(ctx, "timing: synchronise");
+  if (sst) return sst;
   for (auto &p : ctx->pending) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
@@ -292,6 +297,8 @@ int hmc_ctx_set_stream(hmc_ctx *ctx, void *stream) {
 const char *hmc_last_error(hmc_ctx *ctx) { return ctx ? ctx->err.c_str() : "context is NULL"; }
 
 long long hmc_launch_count(hmc_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+long long hmc_host_sync_count(hmc_ctx *ctx) { return ctx ? ctx->host_syncs : 0; }
 
 int hmc_ctx_set_timing(hmc_ctx *ctx, int enable) {
   CTX_CHECK(ctx);

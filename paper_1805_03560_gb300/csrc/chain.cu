@@ -80,7 +80,7 @@ int hmc_chain(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj_para
     double uh = 0.0;
     TRY(cuda_ok(ctx, cudaMemcpyAsync(&uh, u, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
                 "chain: Metropolis uniform"));
-    TRY(cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), "chain: Metropolis uniform"));
+    TRY(host_sync(ctx, "chain: Metropolis uniform"));
     TRY(hmc_trajectory(ctx, lat, U, prm, P, eta, uh, &results[t], nullptr, nullptr));
     results[t].spike =
         cp->spike_threshold > 0.0 && std::fabs(results[t].dH) > cp->spike_threshold ? 1 : 0;

@@ -14,6 +14,7 @@ struct hmc_ctx {
   cudaStream_t stream = nullptr;
   std::string err;
   long long launches = 0;
+  long long host_syncs = 0;  // host waits on the device (stream syncs and event waits)
   struct Buf {
     void *p = nullptr;
     size_t n = 0;
@@ -88,6 +89,8 @@ int fail(hmc_ctx *ctx, int code, const char *fmt, ...);
 // Checks the launch that just happened and counts it.
 int launched(hmc_ctx *ctx, const char *what);
 int cuda_ok(hmc_ctx *ctx, cudaError_t e, const char *what);
+// cudaStreamSynchronize(ctx->stream), counted in ctx->host_syncs
+int host_sync(hmc_ctx *ctx, const char *what);
 // Device workspace owned by the context, grown on demand; nullptr on failure
 // (ctx->err set).  Contents are undefined on return.
 void *workspace(hmc_ctx *ctx, const char *name, size_t bytes);
@@ -206,6 +209,9 @@ int cg_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
 
 // BiCGstab on Mhat (dagger 0) or Mhat^dag, and (Mhat^dag Mhat)^{-1} as two
 // such solves (bicgstab.cu)
+// the context's graph-replay stream and its two ordering events, created on
+// first use
+int graph_stream(hmc_ctx *ctx);
 int bicgstab_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul, void *x,
                    const void *b, double kappa, int dagger, double tol, int max_iter,
                    const hmc_solver_opts *opts, hmc_solve_stats *stats);

@@ -212,7 +212,7 @@ int action_mp(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *
   double h[16];
   TRY(cuda_ok(ctx, cudaMemcpyAsync(h, dst, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream),
               "action_mp: read"));
-  TRY(cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), "action_mp: sync"));
+  TRY(host_sync(ctx, "action_mp: sync"));
   double s = 0.0;
   for (int j = 0; j < n; ++j) s += h[j];
   *S = s;

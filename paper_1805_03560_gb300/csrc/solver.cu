@@ -459,14 +459,19 @@ int one_iteration(Solve &s, int k) {
 // launches.  The caller's stream and the graph stream are ordered by events
 // around every batch.
 
+}  // namespace
+
 int graph_stream(hmc_ctx *ctx) {
   if (ctx->gstream) return HMC_OK;
   TRY(cuda_ok(ctx, cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking),
-              "cg graph: stream"));
+              "graph replay: stream"));
   for (cudaEvent_t &e : ctx->gev)
-    TRY(cuda_ok(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cg graph: event"));
+    TRY(cuda_ok(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming),
+                "graph replay: event"));
   return HMC_OK;
 }
+
+namespace {
 
 int capture_pair(Solve &s) {
   hmc_ctx *ctx = s.ctx;
@@ -520,8 +525,8 @@ int enqueue_iterations(Solve &s, int k, int n) {
 
 int read_state(Solve &s, CGState *h) {
   cudaError_t e = cudaMemcpyAsync(h, s.st, sizeof(CGState), cudaMemcpyDeviceToHost, s.ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s.ctx->stream);
-  return cuda_ok(s.ctx, e, "cg: reading solver state");
+  if (e != cudaSuccess) return cuda_ok(s.ctx, e, "cg: reading solver state");
+  return host_sync(s.ctx, "cg: reading solver state");
 }
 
 // r = b - A x in FP64 (and r_lo = p_lo = r in the mixed solver), restart the

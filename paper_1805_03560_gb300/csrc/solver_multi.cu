@@ -329,8 +329,8 @@ int m_iteration(MSolve &s, int k) {
 
 int m_read(MSolve &s, MState *h) {
   cudaError_t e = cudaMemcpyAsync(h, s.st, sizeof(MState), cudaMemcpyDeviceToHost, s.ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s.ctx->stream);
-  return cuda_ok(s.ctx, e, "cg_multi: reading solver state");
+  if (e != cudaSuccess) return cuda_ok(s.ctx, e, "cg_multi: reading solver state");
+  return host_sync(s.ctx, "cg_multi: reading solver state");
 }
 
 // r = b - A x for every RHS, restart the recursion from it (p = r_lo = r)

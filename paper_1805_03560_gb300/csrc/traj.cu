@@ -18,8 +18,8 @@ namespace hmc {
 static int read_dev(hmc_ctx *ctx, const double *dev, int n, double *host) {
   cudaError_t e =
       cudaMemcpyAsync(ctx->h_pinned, dev, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   TRY(cuda_ok(ctx, e, "reading a device scalar"));
+  TRY(host_sync(ctx, "reading a device scalar"));
   for (int i = 0; i < n; ++i) host[i] = ctx->h_pinned[i];
   return HMC_OK;
 }
@@ -1102,7 +1102,7 @@ int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj
   if (U_end) TRY(cuda_ok(ctx, cudaMemcpyAsync(U_end, U1, gb, cudaMemcpyDeviceToDevice, st), "U_end"));
   if (P_end) TRY(cuda_ok(ctx, cudaMemcpyAsync(P_end, P, ab, cudaMemcpyDeviceToDevice, st), "P_end"));
   if (res->accepted) TRY(cuda_ok(ctx, cudaMemcpyAsync(U, U1, gb, cudaMemcpyDeviceToDevice, st), "U"));
-  return cuda_ok(ctx, cudaStreamSynchronize(st), "trajectory");
+  return host_sync(ctx, "trajectory");
 }
 
 }  // extern "C"
@@ -1131,5 +1131,5 @@ extern "C" int hmc_md_evolve(hmc_ctx *ctx, const hmc_lattice *lat, void *U, doub
     res->solves = solves;
     fst.store(res);
   }
-  return cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), "md_evolve");
+  return host_sync(ctx, "md_evolve");
 }

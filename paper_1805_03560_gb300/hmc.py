@@ -92,6 +92,7 @@ _SIGS = {
     "hmc_ctx_set_stream": (_I, [_P, _P]),
     "hmc_last_error": (ctypes.c_char_p, [_P]),
     "hmc_launch_count": (ctypes.c_longlong, [_P]),
+    "hmc_host_sync_count": (ctypes.c_longlong, [_P]),
     "hmc_ctx_set_timing": (_I, [_P, _I]),
     "hmc_ctx_set_option": (_I, [_P, _I, _I]),
     "hmc_measure_fma_peak": (_I, [_P, _I, _P]),
@@ -253,6 +254,10 @@ class Context:
     def launches(self):
         """Number of kernels this context has launched so far."""
         return lib().hmc_launch_count(self.h)
+
+    def host_syncs(self):
+        """Number of host waits on the device this context's calls have made."""
+        return lib().hmc_host_sync_count(self.h)
 
     def set_dslash_variant(self, v):
         """Hemi-Dslash kernel variant: 0..3 the single-site kernel, 4..6 the

@@ -50,7 +50,8 @@ def test_null_context_rejected(H):
     for name, params in _prototypes():
         if not params or not params[0].startswith("hmc_ctx *"):
             continue
-        if name in ("hmc_ctx_destroy", "hmc_last_error", "hmc_launch_count"):
+        if name in ("hmc_ctx_destroy", "hmc_last_error", "hmc_launch_count",
+                    "hmc_host_sync_count"):
             continue
         if name in ("hmc_checkpoint_write", "hmc_checkpoint_read"):
             continue  # ctx is optional there; covered below
@@ -68,6 +69,7 @@ def test_null_context_utilities(H):
     assert lib.hmc_ctx_destroy(None) == H.EINVAL
     assert lib.hmc_last_error(None) == b"context is NULL"
     assert lib.hmc_launch_count(None) == 0
+    assert lib.hmc_host_sync_count(None) == 0
 
 
 def test_host_entry_points_reject_bad_arguments(H, tmp_path):
