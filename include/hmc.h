@@ -118,13 +118,21 @@ long long hmc_launch_count(hmc_ctx *ctx);
 /* Number of times this context's calls have made the host wait for the
  * device so far: every stream synchronisation inside a call (a solver reading
  * its convergence state, a trajectory reading an action, the final wait of a
- * synchronous call), the autotuner's and timing mode's waits included. */
+ * synchronous call) and timing mode's waits; the autotuner's one-time waits
+ * on its timing events are not counted. */
 long long hmc_host_sync_count(hmc_ctx *ctx);
 /* Per-kernel-class timing.  Mode 1: every hemi-Dslash launch is bracketed by
  * two CUDA events on the context's stream and its algorithmic bytes (links,
  * input, output and epilogue spinors, each once) are counted.  Mode 2 (launch
  * timeline): one event after every kernel launch; the time since the previous
  * event (kernel time plus any idle gap before it) is charged to the launch.
+ * Mode 3 (sampled): every hemi-Dslash launch is counted with its bytes,
+ * those replayed from the CUDA graph of a CG solve included, but only one CG
+ * solve in eight (the first of every eight since timing was enabled, run with
+ * direct launches) and the hemi-Dslash launches outside CG solves are
+ * bracketed by events; the other solves run as in mode 0.  The average
+ * duration of a class is its summed time over its event-timed launches
+ * (hmc_timing_get_timed).  Modes 1 and 2 launch every kernel directly.
  * Mode 0 switches timing off.  Any call clears the statistics. */
 int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
 /* Tuning options.  HMC_OPT_DSLASH_VARIANT selects the hemi-Dslash kernel
@@ -149,12 +157,18 @@ int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
  * class keeps the fastest; the solvers tune their classes on scratch fields
  * before iterating.  Launches during stream capture are never tuned. */
 #define HMC_OPT_DSLASH_VARIANT 1
-/* HMC_OPT_CG_GRAPH: 1 (default) replays the CG iterations of hmc_cg_solve
- * (and of every single-system solve inside the force, action and trajectory
- * calls) from a CUDA graph of two iterations captured once per solve, on a
- * stream of the library's own that is ordered after the caller's stream and
- * before its next work; 0 launches every kernel on the caller's stream.
- * Results are bit-identical.  Graphs are not used while timing is enabled. */
+/* HMC_OPT_CG_GRAPH: 1 (default) runs every CG solve of hmc_cg_solve (and
+ * every single-system solve inside the force, action and trajectory calls)
+ * as one CUDA graph captured per solve: a while node over the loop body (two
+ * iterations and a decision kernel), the reliable update in an if node, the
+ * convergence, reliable-update and iteration-limit decisions taken on the
+ * device, the host reading the solver state once at the end.  The graph runs
+ * on a stream of the library's own that is ordered after the caller's stream
+ * and before its next work.  BiCGstab passes replay one captured iteration
+ * in batches of 16, reading the state after each batch.  0 launches every
+ * kernel on the caller's stream, the CG in batches of loop bodies with the
+ * state read after each (the same kernels on the same data: results are
+ * bit-identical).  Graphs are not used in timing modes 1 and 2. */
 #define HMC_OPT_CG_GRAPH 2
 /* HMC_OPT_WORKSPACE_GUARD: 1 frees the context's workspace and gives every
  * buffer allocated afterwards a 4 KiB guard region of the byte 0xA5 after its
@@ -177,6 +191,10 @@ int hmc_workspace_check(hmc_ctx *ctx, int *n_bad);
  * last class. */
 int hmc_timing_get(hmc_ctx *ctx, int index, char *name, int name_len,
                    long long *launches, double *total_ms, double *bytes);
+/* Number of the index-th class's launches that were bracketed by events
+ * (equal to its launches except in timing mode 3).  Synchronises the stream.
+ * HMC_EINVAL past the last class or for a NULL timed. */
+int hmc_timing_get_timed(hmc_ctx *ctx, int index, long long *timed);
 
 /* hmc_measure_fma_peak: measured CUDA-core multiply-add throughput of the
  * context's device in TFLOP/s (2 flops per FMA, 4 per paired FMA), for the

@@ -104,8 +104,18 @@ static int class_index(hmc_ctx *ctx, const char *cls) {
 
 TimedLaunch::TimedLaunch(hmc_ctx *ctx, const char *cls, double bytes)
     : ctx_(ctx), cls_(-1), bytes_(bytes) {
-  if (ctx->timing != 1) return;
+  if (ctx->timing != 1 && ctx->timing != 3) return;
   cls_ = class_index(ctx, cls);
+  if (ctx->timing == 3 && (ctx->tally || !ctx->sample_on)) {
+    // counted only: captured into a graph (counted per replay) or untimed
+    if (ctx->tally) {
+      ctx->tally->push_back({cls_, bytes});
+    } else {
+      ctx->kstats[cls_].n += 1;
+      ctx->kstats[cls_].bytes += bytes;
+    }
+    return;
+  }
   a_ = take_event(ctx);
   if (a_) cudaEventRecord(a_, ctx->stream);
 }
@@ -138,6 +148,7 @@ int timing_resolve(hmc_ctx *ctx) {
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       hmc_ctx::KStat &k = ctx->kstats[p.cls];
       k.n += 1;
+      k.timed += 1;
       k.ms += ms;
       k.bytes += p.bytes;
     }
@@ -148,6 +159,13 @@ int timing_resolve(hmc_ctx *ctx) {
   }
   ctx->pending.clear();
   return HMC_OK;
+}
+
+void tally_add(hmc_ctx *ctx, const std::vector<std::pair<int, double>> &t, long long reps) {
+  for (const auto &e : t) {
+    ctx->kstats[e.first].n += reps;
+    ctx->kstats[e.first].bytes += e.second * (double)reps;
+  }
 }
 
 int check_lattice(hmc_ctx *ctx, const hmc_lattice *lat) {
@@ -202,7 +220,8 @@ size_t gauge_bytes(const Geo &g, int prec, int fmt) {
     case HMC_F64E: per = (size_t)fmt * 8; break;
     default: return 0;
   }
-  return ((size_t)2 * 4 * g.Vh * per + 255) & ~(size_t)255;
+  const size_t n = (prec == HMC_F32 && fmt == 12) ? f32_sites(g.Vh) : (size_t)g.Vh;
+  return ((size_t)2 * 4 * n * per + 255) & ~(size_t)255;
 }
 
 int pack_gauge(hmc_ctx *ctx, const Geo &g, const double *Uc, void *Ud, int prec, int fmt,
@@ -282,6 +301,8 @@ int hmc_ctx_destroy(hmc_ctx *ctx) {
     cudaStreamSynchronize(ctx->gstream);
     cudaStreamDestroy(ctx->gstream);
   }
+  for (cudaStream_t b : ctx->bstream)
+    if (b) cudaStreamDestroy(b);
   for (cudaEvent_t e : ctx->gev)
     if (e) cudaEventDestroy(e);
   delete ctx;
@@ -302,7 +323,7 @@ long long hmc_host_sync_count(hmc_ctx *ctx) { return ctx ? ctx->host_syncs : 0; 
 
 int hmc_ctx_set_timing(hmc_ctx *ctx, int enable) {
   CTX_CHECK(ctx);
-  if (enable < 0 || enable > 2) return fail(ctx, HMC_EINVAL, "timing mode must be 0, 1 or 2");
+  if (enable < 0 || enable > 3) return fail(ctx, HMC_EINVAL, "timing mode must be 0..3");
   TRY(timing_resolve(ctx));
   if (ctx->trace_prev) {
     ctx->ev_free.push_back(ctx->trace_prev);
@@ -310,6 +331,8 @@ int hmc_ctx_set_timing(hmc_ctx *ctx, int enable) {
   }
   ctx->kstats.clear();
   ctx->timing = enable;
+  ctx->solve_seq = 0;
+  ctx->sample_on = 1;
   return HMC_OK;
 }
 
@@ -348,6 +371,14 @@ int hmc_timing_get(hmc_ctx *ctx, int index, char *name, int name_len, long long 
   if (launches) *launches = k.n;
   if (total_ms) *total_ms = k.ms;
   if (bytes) *bytes = k.bytes;
+  return HMC_OK;
+}
+
+int hmc_timing_get_timed(hmc_ctx *ctx, int index, long long *timed) {
+  CTX_CHECK(ctx);
+  TRY(timing_resolve(ctx));
+  if (index < 0 || index >= (int)ctx->kstats.size() || !timed) return HMC_EINVAL;
+  *timed = ctx->kstats[index].timed;
   return HMC_OK;
 }
 

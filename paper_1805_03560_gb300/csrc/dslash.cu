@@ -632,7 +632,6 @@ static int tune_variant(hmc_ctx *ctx, const DslashArgs &a, int sprec, int fmt, i
     for (int r = 0; r < 3; ++r) launch_any(a, sprec, fmt, dagger, v, nb, ctx->stream);
     cudaEventRecord(e1, ctx->stream);
     float ms = 0.f;
-    ctx->host_syncs += 1;
     if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
       continue;
     if (ms < best_ms) {

@@ -157,7 +157,7 @@ __device__ __forceinline__ void load_pk(const void *base, int S, int s, float2 v
     const float4 *b = (const float4 *)base;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      const float4 t = __ldg(b + (size_t)k * S + s);
+      const float4 t = __ldg(b + f32_chunk<6>(S, k, s));
       v[2 * k] = make_float2(t.x, t.y);
       v[2 * k + 1] = make_float2(t.z, t.w);
     }

@@ -44,6 +44,14 @@ struct hmc_ctx {
   int tune_frozen = 0;
   cudaStream_t gstream = nullptr;
   cudaEvent_t gev[2] = {nullptr, nullptr};
+  // streams on which the bodies of conditional graph nodes are captured
+  cudaStream_t bstream[2] = {nullptr, nullptr};
+  // timing mode 3: solves counted (one in kTimingSample is event-timed),
+  // whether launches outside graphs are event-timed now, and the classes of
+  // the launches being captured into a graph (class, bytes per launch)
+  long long solve_seq = 0;
+  int sample_on = 1;
+  std::vector<std::pair<int, double>> *tally = nullptr;
   struct Pending {
     cudaEvent_t a, b;
     int cls;
@@ -51,7 +59,7 @@ struct hmc_ctx {
   };
   struct KStat {
     std::string name;
-    long long n = 0;
+    long long n = 0, timed = 0;  // launches, event-timed launches
     double ms = 0.0, bytes = 0.0;
   };
   std::vector<cudaEvent_t> ev_free;
@@ -77,6 +85,11 @@ class TimedLaunch {
 };
 // Sync the stream and fold pending event pairs into ctx->kstats.
 int timing_resolve(hmc_ctx *ctx);
+// timing mode 3: add `reps` launches of each (class, bytes) entry to the
+// statistics (launches replayed from a graph, counted when it was captured)
+void tally_add(hmc_ctx *ctx, const std::vector<std::pair<int, double>> &t, long long reps);
+// timing mode 3 event-times one CG solve in this many
+constexpr int kTimingSample = 8;
 
 constexpr int DS_NT = 128;   // threads per block, stencil kernels
 constexpr int BL_NT = 256;   // threads per block, BLAS kernels
@@ -241,6 +254,7 @@ int hi_begin(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_solver_o
              HiOps *h, const char *tag);
 // F64 fields in and out; n_rhs right-hand sides with per-RHS -kappa^2 in
 // cb_rhs (device, nullable)
+int hi_prepare(const HiOps &h);
 int hi_mhat(const HiOps &h, int dagger, void *out, const void *in, double kappa, int n_rhs,
             const double *cb_rhs);
 int hi_mdagm(const HiOps &h, void *out, const void *in, double kappa, int n_rhs,

@@ -203,6 +203,28 @@ __device__ __forceinline__ int nb_bwd(const Geo &g, int lex, const int c[4], int
 
 // ---- spinor storage -----------------------------------------------------------
 
+// Position of 16-byte chunk k of site s in an FP32 field of S sites with NK
+// chunks per site.  Plane layout: chunk-major planes of S chunks.  Blocked
+// layout (HMC_BLOCKED_F32): blocks of 32 consecutive sites, each block
+// holding its NK chunk planes of 32 one after another, so that a warp's
+// loads of one site range stay within one contiguous NK x 512-byte region.
+#ifdef HMC_BLOCKED_F32
+constexpr bool kBlockedF32 = true;
+#else
+constexpr bool kBlockedF32 = false;
+#endif
+template <int NK>
+__device__ __forceinline__ size_t f32_chunk(int S, int k, int s) {
+  if constexpr (kBlockedF32)
+    return (size_t)(s >> 5) * (NK * 32) + (size_t)k * 32 + (s & 31);
+  else
+    return (size_t)k * S + s;
+}
+// sites an FP32 field of S sites is allocated for
+__host__ __device__ __forceinline__ size_t f32_sites(size_t S) {
+  return kBlockedF32 ? (S + 31) & ~(size_t)31 : S;
+}
+
 template <int P>
 struct SpinorIO;
 
@@ -228,12 +250,12 @@ struct SpinorIO<HMC_F64> {
 template <>
 struct SpinorIO<HMC_F32> {
   using R = float;
-  static size_t bytes(size_t S) { return S * 6 * sizeof(float4); }
+  static size_t bytes(size_t S) { return f32_sites(S) * 6 * sizeof(float4); }
   static __device__ __forceinline__ void load(const void *base, int S, int s, Cx<float> v[12]) {
     const float4 *b = (const float4 *)base;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      float4 t = __ldg(b + (size_t)k * S + s);
+      float4 t = __ldg(b + f32_chunk<6>(S, k, s));
       v[2 * k] = {t.x, t.y};
       v[2 * k + 1] = {t.z, t.w};
     }
@@ -242,7 +264,8 @@ struct SpinorIO<HMC_F32> {
     float4 *b = (float4 *)base;
 #pragma unroll
     for (int k = 0; k < 6; ++k)
-      b[(size_t)k * S + s] = make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im);
+      b[f32_chunk<6>(S, k, s)] =
+          make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im);
   }
 };
 
@@ -443,7 +466,7 @@ struct LinkIO<HMC_F32, 12> {
     const float4 *b = (const float4 *)base;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      float4 t = __ldg(b + (size_t)c * Vh + h);
+      float4 t = __ldg(b + f32_chunk<3>(Vh, c, h));
       u[2 * c] = {t.x, t.y};
       u[2 * c + 1] = {t.z, t.w};
     }
@@ -453,7 +476,7 @@ struct LinkIO<HMC_F32, 12> {
     float4 *b = (float4 *)base;
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-      b[(size_t)c * Vh + h] = make_float4((float)u[2 * c].re, (float)u[2 * c].im,
+      b[f32_chunk<3>(Vh, c, h)] = make_float4((float)u[2 * c].re, (float)u[2 * c].im,
                                           (float)u[2 * c + 1].re, (float)u[2 * c + 1].im);
   }
 };
@@ -564,7 +587,8 @@ struct LinkIO<HMC_F16, 12> {
 template <int P, int FMT>
 __device__ __forceinline__ const void *link_base(const void *gauge, int Vh, int p, int mu) {
   using IO = LinkIO<P, FMT>;
-  return (const char *)gauge + (size_t)(p * 4 + mu) * IO::NC * Vh * IO::chunk;
+  const size_t n = (P == HMC_F32 && FMT == 12) ? f32_sites(Vh) : (size_t)Vh;
+  return (const char *)gauge + (size_t)(p * 4 + mu) * IO::NC * n * IO::chunk;
 }
 
 // ---- block reductions -----------------------------------------------------------

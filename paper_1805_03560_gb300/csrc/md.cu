@@ -323,8 +323,7 @@ __global__ void k_convert_gauge(Geo g, const void *src, void *dst) {
   const int pm = i / g.Vh, h = i - pm * g.Vh;
   C u[9];
   LinkIO<HMC_F64, 18>::load((const char *)src + (size_t)pm * 9 * g.Vh * 16, g.Vh, h, u);
-  using IO = LinkIO<P, FMT>;
-  LinkIO<P, FMT>::store((char *)dst + (size_t)pm * IO::NC * g.Vh * IO::chunk, g.Vh, h, u);
+  LinkIO<P, FMT>::store((void *)link_base<P, FMT>(dst, g.Vh, pm >> 2, pm & 3), g.Vh, h, u);
 }
 
 int update_momenta(hmc_ctx *ctx, const Geo &g, double *P, const double *F, double eps) {

@@ -42,6 +42,17 @@ struct CGState {
   int done;       // 1 converged (recursive residual), 2 NaN/Inf
   int active;     // !done
   int iter;
+  int iter_cap;   // xpay clears `active` once iter reaches it
+  // iteration control on the device (k_cg_control_init, k_cg_decide, k_cg_ru_end)
+  double thr;     // tol^2 |b|^2
+  double maxr2;   // largest |r|^2 since the last reliable update
+  double delta2;  // reliable-update threshold delta^2
+  int mixed;      // reliable updates (else true-residual checks of plain CG)
+  int max_iter;
+  int ru;         // a reliable update (or true-residual check) follows
+  int stop;       // 0 running, 1 converged, 2 NaN/Inf, 3 iteration or restart limit
+  int reliable, restarts;
+  int bodies, max_bodies;  // loop bodies run (graph while loop) and their bound
 };
 
 // ---- reductions --------------------------------------------------------------------
@@ -179,6 +190,7 @@ __global__ void __launch_bounds__(BL_NT) k_cg_xpay(void *p, const void *r, int S
       st->done = 1;
       st->active = 0;
     }
+    if (st->iter >= st->iter_cap) st->active = 0;
   }
   const R beta = (R)(rr_new / st->rr[par]);
   // grid-stride: the grid is a few blocks per SM, so few blocks read the
@@ -257,9 +269,101 @@ __global__ void __launch_bounds__(FIN_NT) k_cg_init(CGState *st, const double *p
     st->aux = 0.0;
     st->pap = st->rr_next = 0.0;
     st->iter = 0;
+    st->iter_cap = 0x7fffffff;
     st->done = (s == 0.0) ? 1 : (isfinite(s) ? 0 : 2);
     st->active = st->done == 0;
   }
+}
+
+// ---- iteration control on the device ----------------------------------------------
+// A solve is a loop of bodies: two iterations (parities 0 and 1), then
+// k_cg_decide.  When that asks for a reliable update (mixed precision: |r|^2
+// below the tolerance or below delta^2 times its largest value since the
+// last update) or for a true-residual check (plain FP64: the recursive
+// residual has converged), the update follows: fold the low-precision iterate
+// into x, r = b - A x in FP64-accurate arithmetic, and k_cg_ru_end restarts
+// the recursion from it.  Every decision is taken on the device from the
+// state, so the same sequence of kernels runs either as one CUDA graph (a
+// while node over the body, the update in an if node) or as direct launches
+// in batches whose state the host reads between batches; iterations after a
+// stop or before a pending update are gated off.  The results of the two are
+// bit-identical.
+
+__global__ void k_cg_control_init(CGState *st, double delta2, int max_iter, int mixed,
+                                  int max_bodies) {
+  st->thr = st->tol2 * st->b2;
+  st->maxr2 = st->b2;
+  st->delta2 = delta2;
+  st->mixed = mixed;
+  st->max_iter = max_iter;
+  st->iter_cap = max_iter;
+  st->ru = 0;
+  st->reliable = st->restarts = 0;
+  st->bodies = 0;
+  st->max_bodies = max_bodies;
+  st->stop = st->done == 1 ? 1 : (st->done == 2 ? 2 : (max_iter > 0 ? 0 : 3));
+  if (st->stop) st->active = 0;
+}
+
+// after each pair of iterations: NaN, a pending reliable update or check, the
+// iteration limit; `handle` (in a graph) receives whether the update runs
+__global__ void k_cg_decide(CGState *st, cudaGraphConditionalHandle handle, int in_graph) {
+  int ru = 0;
+  if (st->stop == 0) {
+    if (st->done == 2) {
+      st->stop = 2;
+      st->active = 0;
+    } else if (!st->mixed) {
+      ru = st->done == 1;
+    } else {
+      const double rr = st->rr[st->iter & 1];
+      if (rr > st->maxr2) st->maxr2 = rr;
+      ru = rr <= st->thr || rr < st->delta2 * st->maxr2;
+    }
+    if (!ru && st->stop == 0 && st->iter >= st->max_iter) {
+      st->stop = 3;
+      st->active = 0;
+    }
+  }
+  if (ru) st->active = 0;
+  st->ru = ru;
+  if (in_graph) cudaGraphSetConditional(handle, ru ? 1u : 0u);
+}
+
+// end of a reliable update: restart the recursion from the true |r|^2
+// (block partials of k_residual), or stop
+__global__ void __launch_bounds__(FIN_NT) k_cg_ru_end(CGState *st, const double *partials,
+                                                      int n) {
+  const double s = block_sum_of<FIN_NT>(partials, n);
+  if (threadIdx.x) return;
+  st->rr[0] = st->rr[1] = s;
+  st->aux = s;
+  st->maxr2 = s;
+  st->ru = 0;
+  if (st->mixed)
+    st->reliable += 1;
+  else
+    st->restarts += 1;
+  if (!isfinite(s)) {
+    st->done = 2;
+    st->active = 0;
+    st->stop = 2;
+  } else if (s <= st->thr) {
+    st->active = 0;
+    st->stop = 1;
+  } else if ((!st->mixed && st->restarts > 5) || st->iter >= st->max_iter) {
+    st->active = 0;
+    st->stop = 3;
+  } else {
+    st->done = 0;
+    st->active = 1;
+  }
+}
+
+// end of a loop body in a graph: continue while running, within the bound
+__global__ void k_cg_continue(CGState *st, cudaGraphConditionalHandle handle) {
+  st->bodies += 1;
+  cudaGraphSetConditional(handle, st->stop == 0 && st->bodies < st->max_bodies ? 1u : 0u);
 }
 
 // restart of the recursion from a true residual: rr[par] = sum(partials)
@@ -268,6 +372,7 @@ __global__ void __launch_bounds__(FIN_NT) k_cg_restart(CGState *st, const double
   double s = block_sum_of<FIN_NT>(partials, n);
   if (threadIdx.x == 0) {
     st->rr[par] = s;
+    st->rr[par ^ 1] = s;
     st->aux = s;
     if (!isfinite(s)) {
       st->done = 2;
@@ -377,10 +482,9 @@ struct Solve {
   void *xlo, *rlo, *p, *y, *tlo;
   int nb_ds, nb_bl;
   HiOps hi;  // the FP64-accurate A x of the true residuals
-  cudaGraphExec_t pair = nullptr;  // two captured iterations (enqueue_iterations)
-  int pair_nodes = 0;
+  cudaGraphExec_t whole = nullptr;  // the whole solve (capture_solve)
   ~Solve() {
-    if (pair) cudaGraphExecDestroy(pair);
+    if (whole) cudaGraphExecDestroy(whole);
   }
 };
 
@@ -451,87 +555,15 @@ int one_iteration(Solve &s, int k) {
   return launched(ctx, "cg_xpay");
 }
 
-// ---- CUDA-graph replay of the iterations ---------------------------------------------
-// Two iterations (parities 0 and 1) are captured once per solve on the
-// context's own stream and replayed for every even-aligned pair of a batch;
-// a single iteration fills an odd start or end.  The graph holds exactly the
-// launches one_iteration makes, so results are bit-identical to direct
-// launches.  The caller's stream and the graph stream are ordered by events
-// around every batch.
-
-}  // namespace
-
-int graph_stream(hmc_ctx *ctx) {
-  if (ctx->gstream) return HMC_OK;
-  TRY(cuda_ok(ctx, cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking),
-              "graph replay: stream"));
-  for (cudaEvent_t &e : ctx->gev)
-    TRY(cuda_ok(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming),
-                "graph replay: event"));
-  return HMC_OK;
-}
-
-namespace {
-
-int capture_pair(Solve &s) {
-  hmc_ctx *ctx = s.ctx;
-  cudaStream_t user = ctx->stream;
-  const long long n0 = ctx->launches;
-  ctx->stream = ctx->gstream;
-  cudaError_t e = cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal);
-  int st = e == cudaSuccess ? HMC_OK : cuda_ok(ctx, e, "cg graph: begin capture");
-  if (!st) st = one_iteration(s, 0);
-  if (!st) st = one_iteration(s, 1);
-  cudaGraph_t g = nullptr;
-  if (e == cudaSuccess) {
-    cudaError_t e2 = cudaStreamEndCapture(ctx->gstream, &g);
-    if (!st) st = cuda_ok(ctx, e2, "cg graph: end capture");
-  }
-  ctx->stream = user;
-  ctx->launches = n0;
-  size_t nodes = 0;
-  if (!st) st = cuda_ok(ctx, cudaGraphGetNodes(g, nullptr, &nodes), "cg graph: nodes");
-  if (!st) st = cuda_ok(ctx, cudaGraphInstantiate(&s.pair, g, 0), "cg graph: instantiate");
-  if (g) cudaGraphDestroy(g);
-  s.pair_nodes = (int)nodes;
-  return st;
-}
-
-// enqueue iterations k .. k + n - 1
-int enqueue_iterations(Solve &s, int k, int n) {
-  hmc_ctx *ctx = s.ctx;
-  if (!(ctx->cg_graph && ctx->timing == 0) || n < 2) {
-    for (int j = 0; j < n; ++j) TRY(one_iteration(s, k + j));
-    return HMC_OK;
-  }
-  TRY(graph_stream(ctx));
-  if (!s.pair) TRY(capture_pair(s));
-  cudaStream_t user = ctx->stream;
-  TRY(cuda_ok(ctx, cudaEventRecord(ctx->gev[0], user), "cg graph: order"));
-  TRY(cuda_ok(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->gev[0], 0), "cg graph: order"));
-  ctx->stream = ctx->gstream;
-  int st = HMC_OK, j = 0;
-  if (k & 1) st = one_iteration(s, k + j++);
-  for (; !st && j + 1 < n; j += 2) {
-    st = cuda_ok(ctx, cudaGraphLaunch(s.pair, ctx->gstream), "cg graph: launch");
-    ctx->launches += s.pair_nodes;
-  }
-  if (!st && j < n) st = one_iteration(s, k + j);
-  ctx->stream = user;
-  TRY(st);
-  TRY(cuda_ok(ctx, cudaEventRecord(ctx->gev[1], ctx->gstream), "cg graph: order"));
-  return cuda_ok(ctx, cudaStreamWaitEvent(user, ctx->gev[1], 0), "cg graph: order");
-}
-
 int read_state(Solve &s, CGState *h) {
   cudaError_t e = cudaMemcpyAsync(h, s.st, sizeof(CGState), cudaMemcpyDeviceToHost, s.ctx->stream);
   if (e != cudaSuccess) return cuda_ok(s.ctx, e, "cg: reading solver state");
   return host_sync(s.ctx, "cg: reading solver state");
 }
 
-// r = b - A x in FP64 (and r_lo = p_lo = r in the mixed solver), restart the
-// recursion at iteration parity `par`; returns |r|^2 on the host.
-int true_residual_restart(Solve &s, int par, bool restart_lo, double *rr) {
+// q = A x in FP64-accurate arithmetic, r = b - q with block partials of
+// |r|^2 (and, with restart_lo, the low-precision r and p set to r)
+int residual_launch(Solve &s, bool restart_lo) {
   TRY(apply_A64(s, s.x, s.q));
   void *rl = nullptr, *pl = nullptr;
   if (restart_lo) {
@@ -557,7 +589,13 @@ int true_residual_restart(Solve &s, int par, bool restart_lo, double *rr) {
                                                                  s.tmp_part);
       break;
   }
-  TRY(launched(s.ctx, "residual"));
+  return launched(s.ctx, "residual");
+}
+
+// r = b - A x in FP64 (and r_lo = p_lo = r in the mixed solver), restart the
+// recursion; returns |r|^2 on the host.
+int true_residual_restart(Solve &s, int par, bool restart_lo, double *rr) {
+  TRY(residual_launch(s, restart_lo));
   k_cg_restart<<<1, FIN_NT, 0, s.ctx->stream>>>(s.st, s.tmp_part, s.nb_bl, par);
   TRY(launched(s.ctx, "cg_restart"));
   CGState h;
@@ -566,7 +604,176 @@ int true_residual_restart(Solve &s, int par, bool restart_lo, double *rr) {
   return 0;
 }
 
+// the loop body: two iterations and the decision (`handle` receives it in a graph)
+int body_pair(Solve &s, cudaGraphConditionalHandle handle, int in_graph) {
+  TRY(one_iteration(s, 0));
+  TRY(one_iteration(s, 1));
+  k_cg_decide<<<1, 1, 0, s.ctx->stream>>>(s.st, handle, in_graph);
+  return launched(s.ctx, "cg_decide");
+}
+
+// the reliable update (plain CG: the true-residual check and restart)
+int body_update(Solve &s) {
+  if (s.plo != HMC_F64) {
+    k_fold<<<s.nb_bl, BL_NT, 0, s.ctx->stream>>>(s.x, s.xlo, s.S);
+    TRY(launched(s.ctx, "fold"));
+  }
+  TRY(residual_launch(s, true));
+  k_cg_ru_end<<<1, FIN_NT, 0, s.ctx->stream>>>(s.st, s.tmp_part, s.nb_bl);
+  return launched(s.ctx, "cg_ru_end");
+}
+
+// ---- the whole solve as one CUDA graph -------------------------------------------------
+// top: while (handle `loop`, initially 1) { body_pair; if (handle `upd`)
+// { body_update }; k_cg_continue }.  The body graphs are captured on the
+// context's two body streams into the graphs that the conditional nodes own.
+
+int graph_of_capture(hmc_ctx *ctx, cudaStream_t cs, cudaGraph_t *g, const cudaGraphNode_t **deps,
+                     size_t *nd) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  TRY(cuda_ok(ctx, cudaStreamGetCaptureInfo(cs, &st, nullptr, g, deps, nullptr, nd),
+              "cg graph: capture info"));
+  if (st != cudaStreamCaptureStatusActive) return fail(ctx, HMC_ECUDA, "cg graph: not capturing");
+  return HMC_OK;
+}
+
+// append a conditional node (handle h) to the work captured on cs; *body
+// receives its body graph
+int add_conditional(hmc_ctx *ctx, cudaStream_t cs, cudaGraphConditionalNodeType type,
+                    cudaGraphConditionalHandle h, cudaGraph_t *body) {
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  TRY(graph_of_capture(ctx, cs, &g, &deps, &nd));
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = type;
+  p.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  TRY(cuda_ok(ctx, cudaGraphAddNode(&node, g, deps, nullptr, nd, &p), "cg graph: conditional node"));
+  *body = p.conditional.phGraph_out[0];
+  return cuda_ok(ctx, cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1,
+                                                         cudaStreamSetCaptureDependencies),
+                 "cg graph: capture dependencies");
+}
+
+struct Tally {
+  long long body = 0, update = 0;  // launches per body and per update
+  // timing mode 3: the classes of one iteration's and of one update's
+  // hemi-Dslash launches (counted per iteration and per update that ran)
+  std::vector<std::pair<int, double>> t_iter, t_update, t_rest;
+};
+
+int capture_solve(Solve &s, Tally *t) {
+  hmc_ctx *ctx = s.ctx;
+  TRY(graph_stream(ctx));
+  cudaStream_t user = ctx->stream, top = ctx->gstream, bs = ctx->bstream[0], us = ctx->bstream[1];
+  const long long n0 = ctx->launches;
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  bool c_top = false, c_body = false, c_upd = false;
+  cudaGraph_t g_top = nullptr, g_body = nullptr, g_upd = nullptr, done = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  cudaGraphConditionalHandle h_loop = 0, h_upd = 0;
+  int st = cuda_ok(ctx, cudaStreamBeginCapture(top, mode), "cg graph: begin capture");
+  c_top = !st;
+  if (!st) st = graph_of_capture(ctx, top, &g_top, &deps, &nd);
+  if (!st)
+    st = cuda_ok(ctx, cudaGraphConditionalHandleCreate(&h_loop, g_top, 1, cudaGraphCondAssignDefault),
+                 "cg graph: loop handle");
+  if (!st) st = add_conditional(ctx, top, cudaGraphCondTypeWhile, h_loop, &g_body);
+  if (!st) {
+    st = cuda_ok(ctx, cudaStreamBeginCaptureToGraph(bs, g_body, nullptr, nullptr, 0, mode),
+                 "cg graph: body capture");
+    c_body = !st;
+  }
+  if (!st)
+    st = cuda_ok(ctx, cudaGraphConditionalHandleCreate(&h_upd, g_body, 0, 0),
+                 "cg graph: update handle");
+  const long long nb0 = ctx->launches;
+  ctx->stream = bs;
+  ctx->tally = &t->t_iter;
+  if (!st) st = one_iteration(s, 0);
+  ctx->tally = &t->t_rest;
+  if (!st) st = one_iteration(s, 1);
+  if (!st) {
+    k_cg_decide<<<1, 1, 0, bs>>>(s.st, h_upd, 1);
+    st = launched(ctx, "cg_decide");
+  }
+  if (!st) st = add_conditional(ctx, bs, cudaGraphCondTypeIf, h_upd, &g_upd);
+  if (!st) {
+    st = cuda_ok(ctx, cudaStreamBeginCaptureToGraph(us, g_upd, nullptr, nullptr, 0, mode),
+                 "cg graph: update capture");
+    c_upd = !st;
+  }
+  const long long nu0 = ctx->launches;
+  ctx->stream = us;
+  ctx->tally = &t->t_update;
+  if (!st) st = body_update(s);
+  t->update = ctx->launches - nu0;
+  if (c_upd) {
+    cudaError_t e = cudaStreamEndCapture(us, &done);
+    if (!st) st = cuda_ok(ctx, e, "cg graph: end update capture");
+  }
+  ctx->stream = bs;
+  ctx->tally = &t->t_rest;
+  if (!st) {
+    k_cg_continue<<<1, 1, 0, bs>>>(s.st, h_loop);
+    st = launched(ctx, "cg_continue");
+  }
+  t->body = ctx->launches - nb0 - t->update;
+  if (c_body) {
+    cudaError_t e = cudaStreamEndCapture(bs, &done);
+    if (!st) st = cuda_ok(ctx, e, "cg graph: end body capture");
+  }
+  ctx->stream = user;
+  ctx->tally = nullptr;
+  cudaGraph_t g = nullptr;
+  if (c_top) {
+    cudaError_t e = cudaStreamEndCapture(top, &g);
+    if (!st) st = cuda_ok(ctx, e, "cg graph: end capture");
+  }
+  ctx->launches = n0;
+  if (!st) st = cuda_ok(ctx, cudaGraphInstantiate(&s.whole, g, 0), "cg graph: instantiate");
+  if (g) cudaGraphDestroy(g);
+  return st;
+}
+
+// run the captured solve after the caller's stream's work, then order the
+// caller's stream after it; count its launches from the loop bodies and
+// updates that ran (in timing mode 3 the hemi-Dslash launches from the
+// iterations and updates that ran, gated-off ones excluded)
+int run_solve(Solve &s, const Tally &t, CGState *h) {
+  hmc_ctx *ctx = s.ctx;
+  cudaStream_t user = ctx->stream;
+  TRY(cuda_ok(ctx, cudaEventRecord(ctx->gev[0], user), "cg graph: order"));
+  TRY(cuda_ok(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->gev[0], 0), "cg graph: order"));
+  TRY(cuda_ok(ctx, cudaGraphLaunch(s.whole, ctx->gstream), "cg graph: launch"));
+  TRY(cuda_ok(ctx, cudaEventRecord(ctx->gev[1], ctx->gstream), "cg graph: order"));
+  TRY(cuda_ok(ctx, cudaStreamWaitEvent(user, ctx->gev[1], 0), "cg graph: order"));
+  TRY(read_state(s, h));
+  const long long nu = h->reliable + h->restarts;
+  ctx->launches += t.body * h->bodies + t.update * nu;
+  tally_add(ctx, t.t_iter, h->iter);
+  tally_add(ctx, t.t_update, nu);
+  return HMC_OK;
+}
+
 }  // namespace
+
+int graph_stream(hmc_ctx *ctx) {
+  if (ctx->gstream) return HMC_OK;
+  for (cudaStream_t &b : ctx->bstream)
+    TRY(cuda_ok(ctx, cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking),
+                "graph capture: body stream"));
+  TRY(cuda_ok(ctx, cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking),
+              "graph replay: stream"));
+  for (cudaEvent_t &e : ctx->gev)
+    TRY(cuda_ok(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming),
+                "graph replay: event"));
+  return HMC_OK;
+}
 
 int cg_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul, void *x,
              const void *b, double kappa, double tol, int max_iter, const hmc_solver_opts *opts,
@@ -644,91 +851,87 @@ int cg_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
     TRY(copy_convert(ctx, s.plo, HMC_F64, s.rlo, b, s.S));
     TRY(copy_convert(ctx, s.plo, HMC_F64, s.p, b, s.S));
   }
-  // autotuning contexts time the iteration's hemi-Dslash classes here, on
-  // scratch (t = H p), before any launch of the iteration exists
+  // autotuning contexts time the iteration's hemi-Dslash classes (and those
+  // of the FP64-accurate A x) here, on scratch, before any launch of the
+  // solve exists; the scratch of A x is allocated before any capture
   TRY(dslash_tune(ctx, g, mixed ? s.Ul : s.Uh, s.plo, 1, s.tlo, s.p));
+  TRY(hi_prepare(s.hi));
+  const int cap = max_iter > 0 ? max_iter : 0;
+  // bound of the graph's loop: every body but the last runs an iteration or
+  // an update
+  const long long bodies = 2LL * cap + 16;
+  k_cg_control_init<<<1, 1, 0, ctx->stream>>>(s.st, delta * delta, cap, mixed ? 1 : 0,
+                                              bodies < 0x7fffffff ? (int)bodies : 0x7fffffff);
+  TRY(launched(ctx, "cg_control"));
+  // timing mode 3 event-times one solve in kTimingSample (directly launched);
+  // the others run as graphs with their launches counted
+  bool sampled = false;
+  if (ctx->timing == 3) sampled = (ctx->solve_seq++ % kTimingSample) == 0;
+  const bool whole = ctx->cg_graph && (ctx->timing == 0 || (ctx->timing == 3 && !sampled));
+  const int sample_prev = ctx->sample_on;
+  if (ctx->timing == 3) ctx->sample_on = sampled ? 1 : 0;
   CGState h{};
-  TRY(read_state(s, &h));
-  const double b2 = h.b2, thr_tol = tol * tol * b2;
-  if (h.done == 2) return fail(ctx, HMC_ENAN, "cg: source has NaN/Inf");
-  int k = 0;              // iterations enqueued
-  int reliable = 0, restarts = 0;
-  double rr = b2;         // latest recursive |r|^2 seen by the host
-  double maxr2 = b2;      // largest |r|^2 since the last reliable update
-  double rate = 0.0;      // observed log-decrease of |r|^2 per iteration
-  double rel2 = b2 > 0 ? 1.0 : 0.0;
-  bool converged = h.done == 1;
-  bool nan = false;
-  while (!converged && k < max_iter) {
-    // size the batch so that it ends near the next reliable update or convergence
-    int todo = check;
-    if (rate < 0.0) {
-      const double target = mixed ? fmax(thr_tol, delta * delta * maxr2) : thr_tol;
-      const double left = log(target / rr) / rate;
-      if (left < todo) todo = left < 1.0 ? 1 : (int)ceil(left);
-    }
-    if (k + todo > max_iter) todo = max_iter - k;
-    TRY(enqueue_iterations(s, k, todo));
-    TRY(read_state(s, &h));
-    if (h.done == 2) {
-      nan = true;
-      break;
-    }
-    const int did = h.iter - k;  // iterations that ran (plain CG stops early when done)
-    k = h.iter;
-    const double rr_now = h.rr[k & 1];
-    if (did > 0 && rr_now > 0.0 && rr_now < rr) rate = log(rr_now / rr) / did;
-    rr = rr_now;
-    if (!mixed) {
-      if (h.done != 1) continue;
-      // confirm on the true residual, restart from it if needed
-      double rt;
-      TRY(true_residual_restart(s, k & 1, true, &rt));
-      rel2 = b2 > 0 ? rt / b2 : 0.0;
-      if (rt <= thr_tol || restarts >= 5) {
-        converged = rt <= thr_tol;
-        break;
+  int st = HMC_OK;
+  if (whole) {
+    Tally t;
+    st = capture_solve(s, &t);
+    if (!st) st = run_solve(s, t, &h);
+  } else {
+    // batches of loop bodies sized from the observed convergence rate to end
+    // before the next update or convergence (single bodies near it), the
+    // state read after each batch, so that bodies gated off by a pending
+    // update are rare
+    st = read_state(s, &h);
+    double rr = h.b2, rate = 0.0;
+    while (!st && h.stop == 0) {
+      if (h.ru) {
+        st = body_update(s);
+        if (!st) st = read_state(s, &h);
+        rr = h.aux;
+        continue;
       }
-      ++restarts;
-      rr = rt;
-      continue;
-    }
-    if (rr > maxr2) maxr2 = rr;
-    if (rr <= thr_tol || rr < delta * delta * maxr2) {
-      // reliable update: fold, FP64 true residual, restart the recursion
-      k_fold<<<s.nb_bl, BL_NT, 0, ctx->stream>>>(s.x, s.xlo, s.S);
-      TRY(launched(ctx, "fold"));
-      double rt;
-      TRY(true_residual_restart(s, k & 1, true, &rt));
-      ++reliable;
-      rel2 = b2 > 0 ? rt / b2 : 0.0;
-      if (!std::isfinite(rt)) {
-        nan = true;
-        break;
+      int pairs = check > 1 ? check / 2 : 1;
+      if (rate < 0.0) {
+        const double target = mixed ? fmax(h.thr, h.delta2 * h.maxr2) : h.thr;
+        const double left = log(target / rr) / rate;  // iterations to the next decision
+        const int whole_pairs = left < 2.0 * pairs ? (int)floor(0.5 * left) : pairs;
+        pairs = whole_pairs < 1 ? 1 : whole_pairs;
       }
-      if (rt <= thr_tol) converged = true;
-      rr = rt;
-      maxr2 = rt;
+      const int k0 = h.iter;
+      for (int j = 0; !st && j < pairs; ++j) st = body_pair(s, 0, 0);
+      if (!st) st = read_state(s, &h);
+      const double rr_now = h.rr[h.iter & 1];
+      const int did = h.iter - k0;
+      if (did > 0 && rr_now > 0.0 && rr_now < rr) rate = log(rr_now / rr) / did;
+      rr = rr_now;
     }
   }
-  if (mixed && !converged && !nan) {
-    // fold the last low-precision iterate so x holds it
-    k_fold<<<s.nb_bl, BL_NT, 0, ctx->stream>>>(s.x, s.xlo, s.S);
-    TRY(launched(ctx, "fold"));
-    double rt;
-    TRY(true_residual_restart(s, k & 1, false, &rt));
-    rel2 = b2 > 0 ? rt / b2 : 0.0;
-  } else if (!mixed && !converged && !nan) {
+  ctx->sample_on = sample_prev;
+  TRY(st);
+  const double b2 = h.b2;
+  const int k = h.iter;
+  const bool nan = h.stop == 2;
+  const bool converged = h.stop == 1;
+  double rel2 = b2 > 0 ? h.aux / b2 : 0.0;
+  if (h.reliable + h.restarts == 0) rel2 = b2 > 0 ? 1.0 : 0.0;
+  if (!converged && !nan) {
+    // iteration limit: fold the last low-precision iterate so x holds it, and
+    // report the true residual
+    if (mixed) {
+      k_fold<<<s.nb_bl, BL_NT, 0, ctx->stream>>>(s.x, s.xlo, s.S);
+      TRY(launched(ctx, "fold"));
+    }
     double rt;
     TRY(true_residual_restart(s, k & 1, false, &rt));
     rel2 = b2 > 0 ? rt / b2 : 0.0;
   }
   if (stats) {
     stats->iterations = k;
-    stats->reliable_updates = reliable;
+    stats->reliable_updates = h.reliable;
     stats->true_rel_res = sqrt(rel2);
   }
-  if (nan) return fail(ctx, HMC_ENAN, "cg: NaN/Inf in a reduction");
+  if (nan) return fail(ctx, HMC_ENAN, h.iter ? "cg: NaN/Inf in a reduction"
+                                             : "cg: source has NaN/Inf");
   if (!converged && !(sqrt(rel2) <= tol))
     return fail(ctx, HMC_ENOCONV, "cg: not converged after %d iterations (rel. residual %.3e)", k,
                 sqrt(rel2));

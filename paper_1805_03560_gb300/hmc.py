@@ -92,6 +92,7 @@ _SIGS = {
     "hmc_ctx_set_stream": (_I, [_P, _P]),
     "hmc_last_error": (ctypes.c_char_p, [_P]),
     "hmc_launch_count": (ctypes.c_longlong, [_P]),
+    "hmc_timing_get_timed": (_I, [_P, _I, _P]),
     "hmc_host_sync_count": (ctypes.c_longlong, [_P]),
     "hmc_ctx_set_timing": (_I, [_P, _I]),
     "hmc_ctx_set_option": (_I, [_P, _I, _I]),
@@ -292,11 +293,14 @@ class Context:
         self._check(lib().hmc_ctx_set_option(self.h, 2, int(bool(on))), "hmc_ctx_set_option")
 
     def set_timing(self, enable):
-        """Per-launch timing: 0 off, 1 event-timed Dslash classes, 2 timeline of every launch."""
+        """Per-launch timing: 0 off, 1 event-timed Dslash classes, 2 timeline of
+        every launch, 3 sampled (every Dslash launch counted, one CG solve in
+        eight event-timed, the others run as graphs)."""
         self._check(lib().hmc_ctx_set_timing(self.h, int(enable)), "hmc_ctx_set_timing")
 
     def timing(self):
-        """{class: (launches, total_ms, algorithmic_bytes)} since timing was enabled."""
+        """{class: (launches, total_ms, algorithmic_bytes, timed_launches)} since
+        timing was enabled (total_ms is summed over the timed launches)."""
         out = {}
         i = 0
         while True:
@@ -306,7 +310,10 @@ class Context:
                                       ctypes.byref(b))
             if st:
                 break
-            out[name.value.decode()] = (n.value, ms.value, b.value)
+            t = ctypes.c_longlong(0)
+            self._check(lib().hmc_timing_get_timed(self.h, i, ctypes.byref(t)),
+                        "hmc_timing_get_timed")
+            out[name.value.decode()] = (n.value, ms.value, b.value, t.value)
             i += 1
         return out
 

@@ -155,9 +155,10 @@ def test_cg_multi_matches_single(ctx, H):
 
 @pytest.mark.parametrize("inner", [0, 1])
 def test_cg_graph_replay_is_bit_identical(ctx, H, inner):
-    """The CG iterations replayed from the captured two-iteration graph are the
-    same launches as direct ones: identical solution bits and counts, on the
-    default stream and on a side stream."""
+    """The whole solve as one CUDA graph (while node over the loop body,
+    reliable update in an if node, decisions on the device) runs the same
+    kernels on the same data as direct launches in batches: identical
+    solution bits and counts, on the default stream and on a side stream."""
     import torch
     L = (4, 6, 6, 10)
     U = I.gauge_links(L, 0.3, 1)
@@ -176,3 +177,82 @@ def test_cg_graph_replay_is_bit_identical(ctx, H, inner):
     ctx.set_cg_graph(1)
     for x, it, ru in out[1:]:
         assert np.array_equal(x, out[0][0]) and it == out[0][1] and ru == out[0][2]
+
+
+@pytest.mark.parametrize("inner", [0, 1, 4])
+def test_cg_whole_solve_graph_syncs_and_bits(ctx, H, inner):
+    """A 16^3 x 32 solve to 1e-12 (~50 iterations on this synthetic field, one
+    or more reliable updates): the graph path makes at most three host waits
+    per solve (the solver state at the end, none in between) against one per
+    batch and per update for direct launches, and gives the same bits and
+    statistics."""
+    L = (32, 16, 16, 16)
+    U = I.gauge_links(L, 0.3, 1)
+    phi = I.gaussian_half(L, 2)
+    got = {}
+    for graph in (1, 0):
+        ctx.set_cg_graph(graph)
+        _solve(ctx, H, L, U, phi, 0.1575, 1e-12, inner)  # warm (allocation, capture)
+        y0 = ctx.host_syncs()
+        x, r = _solve(ctx, H, L, U, phi, 0.1575, 1e-12, inner)
+        got[graph] = (x, r, ctx.host_syncs() - y0)
+    ctx.set_cg_graph(1)
+    (xg, rg, yg), (xd, rd, yd) = got[1], got[0]
+    assert rg["status"] == 0 and rg["true_rel_res"] <= 1e-12
+    assert rg["iterations"] > 30
+    assert np.array_equal(xg, xd)
+    assert (rg["iterations"], rg["reliable_updates"]) == (rd["iterations"], rd["reliable_updates"])
+    assert yg <= 3, yg
+    assert yd >= rd["iterations"] // 16 + rd["reliable_updates"] and yd > yg, (yd, yg)
+
+
+@pytest.mark.parametrize("inner", [0, 1])
+def test_cg_iteration_limit_on_device(ctx, H, inner):
+    """max_iter ends the device-driven loop at exactly max_iter iterations
+    (ENOCONV with the true residual of the last iterate), with and without the
+    graph, identically."""
+    L = (4, 6, 6, 10)
+    U = I.gauge_links(L, 0.3, 1)
+    phi = I.gaussian_half(L, 2)
+    Uh = ctx.pack_gauge(L, U, 0, 18)
+    Ul = ctx.pack_gauge(L, U, inner, 12) if inner else None
+    b = ctx.pack_spinor(L, phi, 0)
+    out = []
+    for graph in (1, 0):
+        ctx.set_cg_graph(graph)
+        x = ctx.new_spinor(L, 0)
+        r = ctx.cg_solve(L, Uh, x, b, 0.156, 1e-14, max_iter=7, U_lo=Ul, inner_prec=inner)
+        out.append((_np(ctx.unpack_spinor(L, x)), r))
+    ctx.set_cg_graph(1)
+    for x, r in out:
+        assert r["status"] == H.ENOCONV and r["iterations"] == 7, r
+        assert 0.0 < r["true_rel_res"] < 1.0
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1]["true_rel_res"] == out[1][1]["true_rel_res"]
+
+
+def test_sampled_timing_counts_graph_launches(ctx, H):
+    """Timing mode 3 counts every hemi-Dslash launch of the graph-replayed
+    solves (4 per iteration) with its bytes, and event-times the first solve
+    in eight: the counts equal those of mode 1 (every launch direct and
+    timed) on the same solves, the timed launches are those of one solve."""
+    L = (16, 8, 8, 8)
+    U = I.gauge_links(L, 0.3, 1)
+    phi = I.gaussian_half(L, 2)
+    stats = {}
+    for mode in (1, 3):
+        ctx.set_timing(mode)
+        its = [_solve(ctx, H, L, U, phi, 0.156, 1e-10, 1)[1]["iterations"] for _ in range(3)]
+        stats[mode] = (its, ctx.timing())
+    ctx.set_timing(0)
+    (it1, t1), (it3, t3) = stats[1], stats[3]
+    assert it1 == it3
+    cls = "dslash_f32_12/cg"
+    n1, ms1, b1, timed1 = t1[cls]
+    n3, ms3, b3, timed3 = t3[cls]
+    # direct launches are counted as issued: a body gated off by a pending
+    # update (rare: batches end before the predicted decision) counts too
+    assert timed1 == n1 and n1 >= 4 * sum(it1)
+    assert timed3 >= 4 * it3[0] and n3 - timed3 == 4 * (it3[1] + it3[2])
+    assert b3 / n3 == b1 / n1
+    assert ms3 > 0.0 and ms3 / timed3 == pytest.approx(ms1 / timed1, rel=0.5)
