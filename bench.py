@@ -134,6 +134,8 @@ def parse():
     ap.add_argument("--variant", type=int, default=None,
                     help="hemi-Dslash kernel variant 0..3, -1 built-in default, -2 autotuned "
                          "(the trajectory benchmark autotunes by default)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="--kernel cg-*: launch the CG kernels directly (no CUDA graphs)")
     return ap.parse_args()
 
 
@@ -149,6 +151,8 @@ def run_kernel(args):
     ctx = hmc.Context(0)
     if args.variant is not None:
         ctx.set_dslash_variant(args.variant)
+    if args.no_graph:
+        ctx.set_cg_graph(0)
     if pname == "cgm":
         # batched solve of n systems (kappas of mass-preconditioned
         # pseudo-fermions) on the benchmark lattice, links shared per launch
@@ -193,7 +197,7 @@ def run_kernel(args):
         # solve time with and without the CUDA-graph replay of the iterations
         # (kernel timing off), then per-class kernel times (timing on)
         graph_ms = {}
-        for graph in (1, 0):
+        for graph in ((0,) if args.no_graph else (1, 0)):
             ctx.set_cg_graph(graph)
             t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             t0.record()
@@ -202,7 +206,7 @@ def run_kernel(args):
             t1.record()
             torch.cuda.synchronize()
             graph_ms["graph" if graph else "direct"] = round(t0.elapsed_time(t1), 3)
-        ctx.set_cg_graph(1)
+        ctx.set_cg_graph(0 if args.no_graph else 1)
         ctx.set_timing(True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -749,7 +753,11 @@ def cpu_baseline(bytes_per_site, sites_per_traj):
                                                   allc["site_applications_per_s"], 1)}
 
 
-REF_BYTES_PER_SITE = 576  # FP32-12 hemi-Dslash: 8 x 12 x 4 (links) + 2 x 24 x 4 (spinors)
+# algorithmic bytes per hemi-Dslash site application of the benchmark
+# trajectory (its mix of CG hops with fused epilogues and emulated-FP64 hops:
+# the GPU arm's value / its site applications per second, 730 B on 24^3 x 48),
+# so that both arms express the same site applications in the same unit
+REF_BYTES_PER_SITE = 730
 
 
 def run_reference(args):
@@ -773,8 +781,9 @@ def run_reference(args):
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": (f"FP64 oracle hemi-Dslash applications on {lat_name()} "
                                    f"({s['threads']} host threads), counted at "
-                                   f"{REF_BYTES_PER_SITE} B per output site (the FP32-12 "
-                                   "hemi-Dslash's algorithmic bytes)"),
+                                   f"{REF_BYTES_PER_SITE} B per output site (the "
+                                   "benchmark trajectory's algorithmic bytes per hemi-Dslash "
+                                   "site application)"),
                       "sample": "per step: two oracle hemi-Dslash applications, one Mhat "
                                 "and one CG iteration"},
            "cpu_baseline": {"value": round(val, 3), "unit": "GB/s", "cores": s["threads"],

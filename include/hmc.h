@@ -24,11 +24,14 @@
  *
  * Device layouts (what every compute call reads and writes):
  *   gauge   for parity p of the base site, direction mu, chunk c, site h:
- *           chunk index ((p*4 + mu)*NC + c)*Vh + h.  A chunk is 16 bytes
- *           where the format allows it:
+ *           chunk index ((p*4 + mu)*NC + c)*Vh + h, except F32/LINK12 (below).
+ *           A chunk is 16 bytes where the format allows it:
  *             F64/LINK18: double2 (1 complex) x 9    F64/LINK12: double2 x 6
  *             F32/LINK18: float2  (1 complex) x 9    F32/LINK12: float4 (2 complex) x 3
  *             F16/LINK18: half2   (1 complex) x 9    F16/LINK12: 4 halves (2 complex) x 3
+ *           F32/LINK12 is blocked by 32 sites: with Vp = Vh rounded up to a
+ *           multiple of 32, chunk index (p*4 + mu)*3*Vp + (h/32)*96 + c*32 +
+ *           h%32.
  *           Complex entries are row-major; LINK12 stores rows 0 and 1 and the
  *           kernels rebuild row 2 = conj(row0 x row1) (exact for SU(3)).  The
  *           fermion time-boundary sign is applied by the kernels, never folded
@@ -36,13 +39,17 @@
  *   spinor  one parity, n_rhs right-hand sides, element s = h*n_rhs + r,
  *           S = Vh*n_rhs:
  *             F64: double2 [12][S]   (chunk = spin*3 + colour)
- *             F32: float4  [6][S]    (chunk k holds complexes 2k, 2k+1)
+ *             F32: float4, blocked by 32 elements: chunk k (complexes 2k,
+ *                  2k+1) of element s at (s/32)*192 + k*32 + s%32; S
+ *                  rounded up to a multiple of 32 elements are allocated
  *             F16: 8 halves [3][S] followed by float norm[S]; value = half *
  *                  norm, norm a power of two >= the site's largest |real|.
  *   algebra double [2][4][8][Vh]: ((p*4 + mu)*8 + a)*Vh + h.
  *
  * Memory and streams.  Every field pointer is a caller-owned DEVICE pointer,
- * 256-byte aligned, of the size the *_bytes helpers return.  The library
+ * 256-byte aligned, of the size the *_bytes helpers return (for spinors of
+ * every precision: S rounded up to a multiple of 32 elements, then to 256
+ * bytes).  The library
  * never frees or reallocates caller memory; it owns only workspace inside the
  * context, released by hmc_ctx_destroy.  Calls are asynchronous on the
  * context's stream (hmc_ctx_set_stream) unless stated otherwise; calls that
@@ -146,7 +153,11 @@ int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
  * sides per thread (each link loaded, rebuilt and indexed once for them,
  * packed paired-FP32 arithmetic; exact on exactly representable inputs,
  * otherwise within FP32 rounding of the other variants); where the count
- * does not divide n_rhs the built-in default is used.  Default -1: for
+ * does not divide n_rhs the built-in default is used.  Values 7 and 8 are
+ * variants 0 and 2 (linear site mapping) whose blocks first ask for a bulk
+ * L2 prefetch of the links they will read (12-real FP32, F16 and BF16
+ * links, one right-hand side; bit-identical results; elsewhere variant 0 or
+ * 2 runs).  Default -1: for
  * n_rhs > 1 in FP32/FP16 the multi-right-hand-side kernel with 2 (else 3)
  * per thread where that divides n_rhs, otherwise paired loads for LINK18
  * only (the fastest choice measured on 24^3 x 48).  -2: autotune: the first
@@ -176,7 +187,7 @@ int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
  * bounds check of the library's internal buffers for tests; compute-sanitizer
  * is not used).  0 (default): no guards. */
 #define HMC_OPT_WORKSPACE_GUARD 3
-/* Sets option (HMC_OPT_DSLASH_VARIANT: -2..6, HMC_OPT_CG_GRAPH: 0 or 1,
+/* Sets option (HMC_OPT_DSLASH_VARIANT: -2..8, HMC_OPT_CG_GRAPH: 0 or 1,
  * HMC_OPT_WORKSPACE_GUARD: 0 or 1) for
  * every later call on ctx.  HMC_EINVAL for an unknown option or value. */
 int hmc_ctx_set_option(hmc_ctx *ctx, int option, int value);

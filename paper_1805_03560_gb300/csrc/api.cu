@@ -197,7 +197,9 @@ int check_gauge(hmc_ctx *ctx, const hmc_gauge *U) {
 }
 
 size_t spinor_bytes(const Geo &g, int prec, int n_rhs) {
-  size_t S = (size_t)g.Vh * n_rhs, b = 0;
+  // every precision sized for at least the blocked FP32 field's padded
+  // element count, so scratch of one precision's size holds any lower one
+  size_t S = f32_sites((size_t)g.Vh * n_rhs), b = 0;
   switch (prec) {
     case HMC_F64: b = SpinorIO<HMC_F64>::bytes(S); break;
     case HMC_F32: b = SpinorIO<HMC_F32>::bytes(S); break;
@@ -340,7 +342,7 @@ int hmc_ctx_set_option(hmc_ctx *ctx, int option, int value) {
   CTX_CHECK(ctx);
   switch (option) {
     case HMC_OPT_DSLASH_VARIANT:
-      if (value < -2 || value > 6) return fail(ctx, HMC_EINVAL, "dslash variant must be -2..6");
+      if (value < -2 || value > 8) return fail(ctx, HMC_EINVAL, "dslash variant must be -2..8");
       ctx->ds_variant = value;
       return HMC_OK;
     case HMC_OPT_CG_GRAPH:

@@ -178,6 +178,7 @@ __device__ __forceinline__ void half_load_raw(const void *base, int S, int s, Ha
   for (int k = 0; k < 3; ++k) v.c[k] = __ldg(b + (size_t)k * S + s);
   if (SP == HMC_F16) v.n = __ldg((const float *)(b + (size_t)3 * S) + s);
 }
+// the stored values, without the F16 norm (applied by half_apply)
 template <int SP>
 __device__ __forceinline__ void half_convert(const HalfRaw<SP> &v, Cx<float> p[12]) {
 #pragma unroll
@@ -189,8 +190,6 @@ __device__ __forceinline__ void half_convert(const HalfRaw<SP> &v, Cx<float> p[1
       if (SP == HMC_F16) {
         const __half2 hh = *reinterpret_cast<const __half2 *>(&w);
         f = __half22float2(hh);
-        f.x *= v.n;
-        f.y *= v.n;
       } else {
         const __nv_bfloat162 hh = *reinterpret_cast<const __nv_bfloat162 *>(&w);
         f = __bfloat1622float2(hh);
@@ -224,6 +223,43 @@ __device__ __forceinline__ void half_link_convert(const uint2 v[3], Cx<float> u[
   reconstruct_row2(u);
 }
 
+// acc += f (w, -S B_mu^dag w) by multiply-adds (f a scalar)
+template <int MU, int S>
+__device__ __forceinline__ void accumulate_scaled(Cx<float> acc[12], const Cx<float> w[6],
+                                                  float f) {
+  auto add = [f](Cx<float> &a, Cx<float> v) {
+    a.re = fmaf(f, v.re, a.re);
+    a.im = fmaf(f, v.im, a.im);
+  };
+  auto sub = [f](Cx<float> &a, Cx<float> v) {
+    a.re = fmaf(-f, v.re, a.re);
+    a.im = fmaf(-f, v.im, a.im);
+  };
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const Cx<float> w0 = w[a], w1 = w[3 + a];
+    add(acc[a], w0);
+    add(acc[3 + a], w1);
+    if (MU == 0) {
+      if (S > 0) { sub(acc[6 + a], w0); sub(acc[9 + a], w1); }
+      else { add(acc[6 + a], w0); add(acc[9 + a], w1); }
+    } else if (MU == 1) {
+      if (S > 0) { sub(acc[6 + a], ti(w1)); sub(acc[9 + a], ti(w0)); }
+      else { add(acc[6 + a], ti(w1)); add(acc[9 + a], ti(w0)); }
+    } else if (MU == 2) {
+      if (S > 0) { sub(acc[6 + a], w1); add(acc[9 + a], w0); }
+      else { add(acc[6 + a], w1); sub(acc[9 + a], w0); }
+    } else {
+      if (S > 0) { sub(acc[6 + a], ti(w0)); add(acc[9 + a], ti(w1)); }
+      else { add(acc[6 + a], ti(w0)); sub(acc[9 + a], ti(w1)); }
+    }
+  }
+}
+
+// The F16 norm (a power of two) and the time-boundary sign are applied once,
+// as the factor of the accumulating multiply-adds: scaling by a power of two
+// is exact, so the result equals scaling the stored values before the
+// projection, bit for bit (barring underflow to subnormals).
 template <int SP, int MU, int S>
 __device__ __forceinline__ void half_apply(const HalfRaw<SP> &pr, const uint2 lr[3], bool fwd,
                                            bool wrap, Cx<float> acc[12]) {
@@ -231,15 +267,12 @@ __device__ __forceinline__ void half_apply(const HalfRaw<SP> &pr, const uint2 lr
   half_convert<SP>(pr, psi);
   half_link_convert<SP>(lr, u);
   project<MU, S>(psi, hs);
-  if (wrap) {
-#pragma unroll
-    for (int k = 0; k < 6; ++k) hs[k] = -hs[k];
-  }
   if (fwd)
     mul_link(u, hs, w);
   else
     mul_link_dag(u, hs, w);
-  accumulate<MU, S>(acc, w);
+  const float n = SP == HMC_F16 ? pr.n : 1.0f;
+  accumulate_scaled<MU, S>(acc, w, wrap ? -n : n);
 }
 
 template <int SP, int MU0, int MU1, int SF>
@@ -263,6 +296,51 @@ __device__ __forceinline__ void hop_quad(const DslashArgs &a, int h, int r, int 
   half_apply<SP, MU0, -SF>(p[1], l[1], false, tfirst, acc);
   half_apply<SP, MU1, SF>(p[2], l[2], true, false, acc);
   half_apply<SP, MU1, -SF>(p[3], l[3], false, false, acc);
+}
+
+// ---- bulk L2 prefetch of a block's links (variants 7 and 8) -----------------------
+// The links are 2/3 of a 12-real FP32 or half hemi-Dslash's bytes and are read
+// once, so every link load waits for DRAM.  With `prefetch`, threads 0..7 of
+// a block (linear site mapping, one right-hand side) first ask the copy
+// engine to bring the links of hop t into L2 (cp.async.bulk.prefetch: no
+// destination, no completion to wait for): the forward links of the block's
+// own sites, and the backward links of the block's sites shifted by the
+// direction's half-site stride (plus one site for z, whose neighbours are h
+// and h - 1).  Ranges are clamped to the field; the wrapped boundary sites'
+// links are left out.  The loads that follow are unchanged, so the result is
+// bit-identical to variants 0 and 2.
+__device__ __forceinline__ void l2_prefetch(const void *p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+template <int SP, int FMT>
+__device__ __forceinline__ void prefetch_block_links(const DslashArgs &a) {
+  const int t = threadIdx.x;
+  if (t >= 8) return;
+  const int Vh = a.g.Vh, h0 = blockIdx.x * DS_NT, mu = t >> 1;
+  const bool fwd = (t & 1) == 0;
+  const int sh = fwd ? 0 : (mu == 3 ? 1 : a.g.st[mu] >> 1);
+  int lo = h0 - sh, hi = h0 + DS_NT - sh + (!fwd && mu == 3 ? 1 : 0);
+  lo = lo < 0 ? 0 : lo;
+  hi = hi > Vh ? Vh : hi;
+  if (lo >= hi) return;
+  const char *base = (const char *)link_base<SP, FMT>(a.gauge, Vh, fwd ? a.p : 1 - a.p, mu);
+  if constexpr (SP == HMC_F32 && FMT == 12) {
+    // blocks of 32 sites, 3 chunks of 16 bytes each (or planes, HMC_PLANE_F32)
+    if constexpr (kBlockedF32) {
+      const size_t b0 = (size_t)(lo >> 5) * 96 * 16, b1 = (size_t)(((hi - 1) >> 5) + 1) * 96 * 16;
+      l2_prefetch(base + b0, (unsigned)(b1 - b0));
+    } else {
+      for (int c = 0; c < 3; ++c)
+        l2_prefetch(base + ((size_t)c * Vh + lo) * 16, (unsigned)(hi - lo) * 16);
+    }
+  } else if constexpr ((SP == HMC_F16 || SP == HMC_BF16) && FMT == 12) {
+    // three planes of 8-byte chunks; 16-byte aligned ends (Vh is even)
+    lo &= ~1;
+    hi = (hi + 1) & ~1;
+    for (int c = 0; c < 3; ++c)
+      l2_prefetch(base + ((size_t)c * Vh + lo) * 8, (unsigned)(hi - lo) * 8);
+  }
 }
 
 // ---- runtime-direction forms ----------------------------------------------------
@@ -413,6 +491,8 @@ __global__ void __launch_bounds__(DS_NT, ds_min_blocks(SP)) k_dslash(const Dslas
       }
     }
   }
+  if constexpr ((SP == HMC_F32 || SP == HMC_F16 || SP == HMC_BF16) && FMT == 12)
+    if (a.prefetch) prefetch_block_links<SP, FMT>(a);
   const int S_ = a.g.Vh * a.n_rhs;
   const int i = dslash_site(a);
   double nrm = 0.0;
@@ -540,6 +620,7 @@ static bool launch_variant(const DslashArgs &a, int sprec, int fmt, int dagger, 
                            cudaStream_t st) {
   DslashArgs aa = a;
   aa.tile_nseg = 0;
+  aa.prefetch = 0;
   const int sx = a.g.L[2] * a.g.Lzh;
   if ((var & 1) && a.n_rhs == 1 && sx % 32 == 0) aa.tile_nseg = sx / 32;
   const bool pair = (var & 2) != 0;
@@ -594,10 +675,29 @@ static int default_variant(int fmt, int sprec, int n_rhs) {
   return fmt == 18 ? 2 : 0;
 }
 
+// whether variants 7 and 8 (links prefetched into L2) apply
+static bool prefetch_applies(const DslashArgs &a, int sprec, int fmt) {
+  return a.n_rhs == 1 && fmt == 12 &&
+         (sprec == HMC_F32 || sprec == HMC_F16 || sprec == HMC_BF16);
+}
+
 // variant v of the class, launched: 0..3 the single-site kernel (bit 0 tiled
-// site mapping, bit 1 paired loads), 4..6 the multi-right-hand-side kernel
+// site mapping, bit 1 paired loads), 4..6 the multi-right-hand-side kernel,
+// 7 and 8 variants 0 and 2 with the block's links prefetched into L2
 static bool launch_any(const DslashArgs &a, int sprec, int fmt, int dagger, int v, int nb,
                        cudaStream_t st) {
+  if (v >= 7) {
+    if (!prefetch_applies(a, sprec, fmt)) return launch_variant(a, sprec, fmt, dagger, 0, nb, st);
+    DslashArgs aa = a;
+    aa.tile_nseg = 0;
+    aa.prefetch = 1;
+    switch (sprec * 100 + fmt) {
+      case HMC_F32 * 100 + 12: launch_sf<HMC_F32, 12>(aa, dagger, v == 8, nb, st); break;
+      case HMC_F16 * 100 + 12: launch_sf<HMC_F16, 12>(aa, dagger, v == 8, nb, st); break;
+      case HMC_BF16 * 100 + 12: launch_sf<HMC_BF16, 12>(aa, dagger, v == 8, nb, st); break;
+    }
+    return true;
+  }
   if (v >= 4) return launch_dslash_mr(a, sprec, fmt, dagger, v - 2, st);
   return launch_variant(a, sprec, fmt, dagger, v, nb, st);
 }
@@ -623,9 +723,10 @@ static int tune_variant(hmc_ctx *ctx, const DslashArgs &a, int sprec, int fmt, i
   int best = dflt;
   float best_ms = 1e30f;
   int tried = 0;
-  for (int v = 0; v < 7; ++v) {
+  for (int v = 0; v < 9; ++v) {
     if ((v & 1) && v < 4 && !tiles) continue;
-    if (v >= 4 && !dslash_mr_supported(sprec, a.n_rhs, v - 2)) continue;
+    if (v >= 4 && v < 7 && !dslash_mr_supported(sprec, a.n_rhs, v - 2)) continue;
+    if (v >= 7 && !prefetch_applies(a, sprec, fmt)) continue;
     ++tried;
     launch_any(a, sprec, fmt, dagger, v, nb, ctx->stream);
     cudaEventRecord(e0, ctx->stream);
@@ -657,7 +758,7 @@ int dslash_mr_nr(hmc_ctx *ctx, const Geo &g, int sprec, int fmt, int n_rhs) {
     auto it = ctx->ds_tuned.find(tune_key(a, sprec, fmt, 1));
     v = it != ctx->ds_tuned.end() ? it->second : -1;
   }
-  if (v >= 4 && dslash_mr_supported(sprec, n_rhs, v - 2)) return v - 2;
+  if (v >= 4 && v < 7 && dslash_mr_supported(sprec, n_rhs, v - 2)) return v - 2;
   return dflt;
 }
 
@@ -695,16 +796,20 @@ int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int
   // ones, tiling helps neither); -2: autotuned per class.
   int var = ctx->ds_variant >= 0 ? ctx->ds_variant : default_variant(U.fmt, sprec, a.n_rhs);
   if (ctx->ds_variant == -2) var = tune_variant(ctx, a, sprec, U.fmt, dagger, nb);
-  if (var >= 4 && !dslash_mr_supported(sprec, a.n_rhs, var - 2)) var = U.fmt == 18 ? 2 : 0;
-  if (a.mr_force > 0 && var < 4) {
+  if (var >= 4 && var < 7 && !dslash_mr_supported(sprec, a.n_rhs, var - 2))
+    var = U.fmt == 18 ? 2 : 0;
+  if (var >= 7 && !prefetch_applies(a, sprec, U.fmt)) var = var == 8 ? 2 : 0;
+  const bool mr = var >= 4 && var < 7;
+  if (a.mr_force > 0 && !mr) {
     if (!dslash_mr_supported(sprec, a.n_rhs, a.mr_force))
       return fail(ctx, HMC_EINVAL, "dslash: no multi-right-hand-side kernel for %d x %d",
                   a.n_rhs, a.mr_force);
     var = 2 + a.mr_force;
   }
-  if (a.cg_x && a.n_rhs > 1 && var < 4)
+  if (a.cg_x && a.n_rhs > 1 && !(var >= 4 && var < 7))
     return fail(ctx, HMC_EINVAL, "dslash: the fused batched update needs the multi-rhs kernel");
-  if (var >= 4 && nblocks) *nblocks = blocks_for((long long)a.g.Vh * (a.n_rhs / (var - 2)), DS_NT);
+  if (var >= 4 && var < 7 && nblocks)
+    *nblocks = blocks_for((long long)a.g.Vh * (a.n_rhs / (var - 2)), DS_NT);
   TimedLaunch timer(ctx, cls, bytes);
   if (!launch_any(a, sprec, U.fmt, dagger, var, nb, st))
     return fail(ctx, HMC_EINVAL, "dslash: unsupported precision %d / link format %d", sprec,

@@ -134,6 +134,7 @@ struct DslashArgs {
   const int *gate;  // device flag (nullable): the launch does nothing when *gate == 0
   const char *tag;  // timing class suffix (nullable)
   int tile_nseg;    // set by the launcher: 32-site segments per (x, t) plane, 0 = linear
+  int prefetch;     // set by the launcher: bulk L2 prefetch of the block's links (variants 7, 8)
   // with partials: the last block also sums them into *total (counter: a
   // zeroed device int, returned to zero)
   double *total;

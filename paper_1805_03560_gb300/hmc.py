@@ -263,7 +263,8 @@ class Context:
     def set_dslash_variant(self, v):
         """Hemi-Dslash kernel variant: 0..3 the single-site kernel, 4..6 the
         multi-right-hand-side kernel with 2..4 right-hand sides per thread,
-        -1 built-in default, -2 autotuned per launch class."""
+        7 and 8 variants 0 and 2 with a bulk L2 prefetch of each block's
+        links, -1 built-in default, -2 autotuned per launch class."""
         self._check(lib().hmc_ctx_set_option(self.h, 1, int(v)), "hmc_ctx_set_option")
 
     def fma_peak(self, kind):

@@ -46,6 +46,12 @@ def test_sizes(H):
     assert lib.hmc_gauge_bytes(ctypes.byref(L), H.F32, 12) == 2 * Vh * 4 * 48
     assert lib.hmc_gauge_bytes(ctypes.byref(L), H.F16, 12) == 2 * Vh * 4 * 24
     assert lib.hmc_algebra_bytes(ctypes.byref(L)) == 2 * Vh * 4 * 8 * 8
+    # FP32 fields are blocked by 32 elements: Vh = 8 on 2^4 takes 32 slots,
+    # and the other precisions are sized for as many
+    T = H.lattice((2, 2, 2, 2))
+    assert lib.hmc_spinor_bytes(ctypes.byref(T), H.F32, 1) == 32 * 96
+    assert lib.hmc_spinor_bytes(ctypes.byref(T), H.F64, 1) == 32 * 192
+    assert lib.hmc_gauge_bytes(ctypes.byref(T), H.F32, 12) == 2 * 4 * 32 * 48
     bad = H.lattice((4, 4, 4, 3))
     assert lib.hmc_spinor_bytes(ctypes.byref(bad), H.F64, 1) == 0
     assert lib.hmc_gauge_bytes(ctypes.byref(L), 7, 18) == 0

@@ -197,9 +197,10 @@ def test_bad_arguments_are_rejected(ctx, H):
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_dslash_variants_bit_identical(orc, ctx, H, prec):
-    """The kernel variants (tiled site mapping, paired loads) change only the
-    thread-to-site assignment and the load order: outputs are bit-identical,
-    and the tiled mapping covers every site exactly once."""
+    """The kernel variants (tiled site mapping, paired loads, and 7, 8: the
+    links of each block prefetched into L2 first) change only the
+    thread-to-site assignment, the load order and what is in L2: outputs are
+    bit-identical, and the tiled mapping covers every site exactly once."""
     L = (4, 4, 8, 16)  # Ly * Lz/2 = 64: the tiled mapping applies
     fmt = 18 if prec == 0 else 12
     U = I.gauge_links(L, 0.3, 1)
@@ -207,7 +208,8 @@ def test_dslash_variants_bit_identical(orc, ctx, H, prec):
     psi = I.gaussian_half(L, 3)
     src = ctx.pack_spinor(L, psi, prec)
     outs = []
-    for v in range(4):
+    variants = (0, 1, 2, 3, 7, 8)
+    for v in variants:
         ctx.set_dslash_variant(v)
         for dagger in (False, True):
             out = ctx.new_spinor(L, prec)
@@ -215,9 +217,9 @@ def test_dslash_variants_bit_identical(orc, ctx, H, prec):
             ctx.dslash(L, Ud, out, src, 0, dagger)
             outs.append(_np(ctx.unpack_spinor(L, out)))
     ctx.set_dslash_variant(-1)
-    for v in range(1, 4):
+    for j in range(1, len(variants)):
         for d in range(2):
-            assert np.array_equal(outs[2 * v + d], outs[d])
+            assert np.array_equal(outs[2 * j + d], outs[d]), (variants[j], d)
     assert np.isfinite(outs[0]).all()
     Uq = _np(ctx.unpack_gauge(L, Ud))
     assert _rel(outs[0], orc.hop_eo(L, Uq, 0, _np(ctx.unpack_spinor(L, src)))) <= TOL[prec]
