@@ -135,7 +135,8 @@ def parse():
                     help="hemi-Dslash kernel variant 0..3, -1 built-in default, -2 autotuned "
                          "(the trajectory benchmark autotunes by default)")
     ap.add_argument("--no-graph", action="store_true",
-                    help="--kernel cg-*: launch the CG kernels directly (no CUDA graphs)")
+                    help="launch the CG kernels directly (no CUDA graphs), e.g. for an ncu "
+                         "launch list")
     return ap.parse_args()
 
 
@@ -385,6 +386,8 @@ def run_hmc(args):
 
     inner = {"f16": hmc.F16, "bf16": hmc.BF16, "f32": hmc.F32}[args.inner]
     ctx = hmc.Context(local)
+    if args.no_graph:
+        ctx.set_cg_graph(0)  # every kernel a direct launch (e.g. for an ncu launch list)
     # measured CUDA-core FMA ceilings (the arithmetic rooflines)
     fma = {k: round(ctx.fma_peak(i), 2) for i, k in enumerate(("fp64", "fp32", "fp32x2"))}
     # autotuned hemi-Dslash variants (tuned during the warm-up steps)
@@ -575,6 +578,8 @@ def run_hmc(args):
                    "force_prec": args.force_prec, "f64_emul": args.f64_emul,
                    "solver": args.solver,
                    "dslash_variant": "autotuned" if args.variant is None else args.variant,
+                   "cg_graph": "direct launches" if args.no_graph else
+                   "one CUDA graph per solve (one solve in eight direct and event-timed)",
                    "links": "12-real (inner), 18-real FP64",
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
