@@ -27,8 +27,31 @@ namespace {
     if (_s) return _s; \
   } while (0)
 
+// <a, b> of one site (re, im) in the arithmetic precision R: per-site sums
+// of the FP32 solver stay on the FP32 units (the FP64 units are a small
+// fraction of them on this GPU); cross-site sums are double
+template <typename R>
+__device__ __forceinline__ void site_dot(const Cx<R> a[12], const Cx<R> b[12], double &re,
+                                         double &im) {
+  R x = R(0), y = R(0);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    x += a[k].re * b[k].re + a[k].im * b[k].im;
+    y += a[k].re * b[k].im - a[k].im * b[k].re;
+  }
+  re += (double)x;
+  im += (double)y;
+}
+template <typename R>
+__device__ __forceinline__ double site_norm(const Cx<R> a[12]) {
+  R x = R(0);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) x += a[k].re * a[k].re + a[k].im * a[k].im;
+  return (double)x;
+}
+
 // partials[c * gridDim.x + block], c = 0..3: Re, Im <a1, b1>, Re, Im <a2, b2>
-// (a2 nullable: zeros), accumulated in double
+// (a2 nullable: zeros), per-site sums in the arithmetic precision
 template <int P>
 __global__ void __launch_bounds__(BL_NT) k_cdot2(const void *a1, const void *b1, const void *a2,
                                                  const void *b2, int S, double *partials) {
@@ -39,19 +62,11 @@ __global__ void __launch_bounds__(BL_NT) k_cdot2(const void *a1, const void *b1,
     Cx<R> a[12], b[12];
     load_as<P>(a1, S, i, a);
     load_as<P>(b1, S, i, b);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      s0 += (double)a[k].re * b[k].re + (double)a[k].im * b[k].im;
-      s1 += (double)a[k].re * b[k].im - (double)a[k].im * b[k].re;
-    }
+    site_dot<R>(a, b, s0, s1);
     if (a2) {
       load_as<P>(a2, S, i, a);
       load_as<P>(b2, S, i, b);
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        s2 += (double)a[k].re * b[k].re + (double)a[k].im * b[k].im;
-        s3 += (double)a[k].re * b[k].im - (double)a[k].im * b[k].re;
-      }
+      site_dot<R>(a, b, s2, s3);
     }
   }
   const double t0 = block_sum<BL_NT>(s0), t1 = block_sum<BL_NT>(s1);
@@ -278,12 +293,8 @@ __global__ void __launch_bounds__(BL_NT) k_bicg_xr(void *x, void *r, const void 
     }
     store_as<P>(r, S, i, b);
     load_as<P>(r0, S, i, a);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      s0 += (double)a[k].re * b[k].re + (double)a[k].im * b[k].im;
-      s1 += (double)a[k].re * b[k].im - (double)a[k].im * b[k].re;
-      s2 += (double)b[k].re * b[k].re + (double)b[k].im * b[k].im;
-    }
+    site_dot<R>(a, b, s0, s1);
+    s2 += site_norm<R>(b);
   }
   const double t0 = block_sum<BL_NT>(s0), t1 = block_sum<BL_NT>(s1), t2 = block_sum<BL_NT>(s2);
   if (threadIdx.x == 0) {
@@ -307,19 +318,11 @@ __global__ void __launch_bounds__(BL_NT) k_cdot2_gated(const void *a1, const voi
     Cx<R> a[12], b[12];
     load_as<P>(a1, S, i, a);
     load_as<P>(b1, S, i, b);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      s0 += (double)a[k].re * b[k].re + (double)a[k].im * b[k].im;
-      s1 += (double)a[k].re * b[k].im - (double)a[k].im * b[k].re;
-    }
+    site_dot<R>(a, b, s0, s1);
     if (a2) {
       load_as<P>(a2, S, i, a);
       load_as<P>(b2, S, i, b);
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        s2 += (double)a[k].re * b[k].re + (double)a[k].im * b[k].im;
-        s3 += (double)a[k].re * b[k].im - (double)a[k].im * b[k].re;
-      }
+      site_dot<R>(a, b, s2, s3);
     }
   }
   const double t0 = block_sum<BL_NT>(s0), t1 = block_sum<BL_NT>(s1);
