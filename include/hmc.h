@@ -168,12 +168,13 @@ int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
  * class keeps the fastest; the solvers tune their classes on scratch fields
  * before iterating.  Launches during stream capture are never tuned. */
 #define HMC_OPT_DSLASH_VARIANT 1
-/* HMC_OPT_CG_GRAPH: 1 (default) runs every CG solve of hmc_cg_solve (and
- * every single-system solve inside the force, action and trajectory calls)
- * as one CUDA graph captured per solve: a while node over the loop body (two
+/* HMC_OPT_CG_GRAPH: 1 (default) runs every CG solve of hmc_cg_solve and
+ * hmc_cg_solve_multi (and every solve inside the force, action and
+ * trajectory calls) as one CUDA graph captured per solve: a while node over the loop body (two
  * iterations and a decision kernel), the reliable update in an if node, the
  * convergence, reliable-update and iteration-limit decisions taken on the
- * device, the host reading the solver state once at the end.  The graph runs
+ * device (for a batched solve: for all systems together), the host reading
+ * the solver state once at the end.  The graph runs
  * on a stream of the library's own that is ordered after the caller's stream
  * and before its next work.  BiCGstab passes replay one captured iteration
  * in batches of 16, reading the state after each batch.  0 launches every

@@ -58,18 +58,18 @@ int hi_mhat(const HiOps &h, int dagger, void *out, const void *in, double kappa,
   return copy_convert(h.ctx, HMC_F64, HMC_F64E, out, eo, S);
 }
 
-// Before a capture of these operators (one right-hand side): allocate their
+// Before a capture of these operators (n_rhs right-hand sides): allocate their
 // scratch fields (no allocation may happen while a stream is captured) and,
 // in autotuning contexts, tune their hemi-Dslash classes on scratch (zeroed
 // input), so that the captured launches use the tuned variants.
-int hi_prepare(const HiOps &h) {
-  void *in = hi_ws(h, "in", 1), *out = hi_ws(h, "out", 1);
-  void *tmp = hi_ws(h, "tmp", 1), *mid = hi_ws(h, "mid", 1);
+int hi_prepare(const HiOps &h, int n_rhs) {
+  void *in = hi_ws(h, "in", n_rhs), *out = hi_ws(h, "out", n_rhs);
+  void *tmp = hi_ws(h, "tmp", n_rhs), *mid = hi_ws(h, "mid", n_rhs);
   if (!in || !out || !tmp || !mid) return HMC_ENOMEM;
   if (h.ctx->ds_variant != -2) return HMC_OK;
   const int p = h.emul ? HMC_F64E : HMC_F64;
-  TRY(zero_field(h.ctx, p, in, h.g.Vh));
-  return dslash_tune(h.ctx, h.g, h.emul ? h.Ue : h.Uh, p, 1, tmp, in);
+  TRY(zero_field(h.ctx, p, in, h.g.Vh * n_rhs));
+  return dslash_tune(h.ctx, h.g, h.emul ? h.Ue : h.Uh, p, n_rhs, tmp, in);
 }
 
 // out = Mhat^dag Mhat in

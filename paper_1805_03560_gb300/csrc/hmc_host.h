@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -223,9 +224,33 @@ int cg_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
 
 // BiCGstab on Mhat (dagger 0) or Mhat^dag, and (Mhat^dag Mhat)^{-1} as two
 // such solves (bicgstab.cu)
-// the context's graph-replay stream and its two ordering events, created on
-// first use
+// the context's graph-replay stream, its two ordering events and the two
+// streams on which conditional bodies are captured, created on first use
 int graph_stream(hmc_ctx *ctx);
+// the graph being captured on stream cs and its current leaf nodes
+int graph_of_capture(hmc_ctx *ctx, cudaStream_t cs, cudaGraph_t *g, const cudaGraphNode_t **deps,
+                     size_t *nd);
+// append a conditional node (handle h) to the work captured on cs; *body
+// receives its body graph
+int add_conditional(hmc_ctx *ctx, cudaStream_t cs, cudaGraphConditionalNodeType type,
+                    cudaGraphConditionalHandle h, cudaGraph_t *body);
+// A solver loop captured as one CUDA graph (capture_loop): while (loop) {
+// iter(); rest(upd, loop) (ends in the decision kernel, which sets both
+// handles); if (upd) update() }.  Each callback enqueues on ctx->stream.
+struct LoopParts {
+  std::function<int()> iter;
+  std::function<int(cudaGraphConditionalHandle, cudaGraphConditionalHandle)> rest;
+  std::function<int()> update;
+};
+// launches per loop body and per update; timing mode 3: the classes of one
+// iteration's and of one update's hemi-Dslash launches
+struct LoopTally {
+  long long body = 0, update = 0;
+  std::vector<std::pair<int, double>> t_iter, t_update, t_rest;
+};
+int capture_loop(hmc_ctx *ctx, const LoopParts &L, LoopTally *t, cudaGraphExec_t *exec);
+// launch a captured loop after the work on ctx->stream, ordering ctx->stream after it
+int run_loop(hmc_ctx *ctx, cudaGraphExec_t exec);
 int bicgstab_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul, void *x,
                    const void *b, double kappa, int dagger, double tol, int max_iter,
                    const hmc_solver_opts *opts, hmc_solve_stats *stats);
@@ -255,7 +280,7 @@ int hi_begin(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_solver_o
              HiOps *h, const char *tag);
 // F64 fields in and out; n_rhs right-hand sides with per-RHS -kappa^2 in
 // cb_rhs (device, nullable)
-int hi_prepare(const HiOps &h);
+int hi_prepare(const HiOps &h, int n_rhs = 1);
 int hi_mhat(const HiOps &h, int dagger, void *out, const void *in, double kappa, int n_rhs,
             const double *cb_rhs);
 int hi_mdagm(const HiOps &h, void *out, const void *in, double kappa, int n_rhs,

@@ -306,8 +306,12 @@ __global__ void k_cg_control_init(CGState *st, double delta2, int max_iter, int 
 }
 
 // after each pair of iterations: NaN, a pending reliable update or check, the
-// iteration limit; `handle` (in a graph) receives whether the update runs
-__global__ void k_cg_decide(CGState *st, cudaGraphConditionalHandle handle, int in_graph) {
+// iteration limit.  In a graph, `upd` receives whether the update runs and
+// `loop` whether the loop goes on: it does while the solve runs (after an
+// update that stops it, the next body's launches are gated off and its
+// decision ends the loop), within the body bound.
+__global__ void k_cg_decide(CGState *st, cudaGraphConditionalHandle upd,
+                            cudaGraphConditionalHandle loop, int in_graph) {
   int ru = 0;
   if (st->stop == 0) {
     if (st->done == 2) {
@@ -327,7 +331,11 @@ __global__ void k_cg_decide(CGState *st, cudaGraphConditionalHandle handle, int 
   }
   if (ru) st->active = 0;
   st->ru = ru;
-  if (in_graph) cudaGraphSetConditional(handle, ru ? 1u : 0u);
+  st->bodies += 1;
+  if (in_graph) {
+    cudaGraphSetConditional(upd, ru ? 1u : 0u);
+    cudaGraphSetConditional(loop, st->stop == 0 && st->bodies < st->max_bodies ? 1u : 0u);
+  }
 }
 
 // end of a reliable update: restart the recursion from the true |r|^2
@@ -360,11 +368,7 @@ __global__ void __launch_bounds__(FIN_NT) k_cg_ru_end(CGState *st, const double 
   }
 }
 
-// end of a loop body in a graph: continue while running, within the bound
-__global__ void k_cg_continue(CGState *st, cudaGraphConditionalHandle handle) {
-  st->bodies += 1;
-  cudaGraphSetConditional(handle, st->stop == 0 && st->bodies < st->max_bodies ? 1u : 0u);
-}
+
 
 // restart of the recursion from a true residual: rr[par] = sum(partials)
 __global__ void __launch_bounds__(FIN_NT) k_cg_restart(CGState *st, const double *partials, int n,
@@ -482,7 +486,7 @@ struct Solve {
   void *xlo, *rlo, *p, *y, *tlo;
   int nb_ds, nb_bl;
   HiOps hi;  // the FP64-accurate A x of the true residuals
-  cudaGraphExec_t whole = nullptr;  // the whole solve (capture_solve)
+  cudaGraphExec_t whole = nullptr;  // the whole solve (capture_loop)
   ~Solve() {
     if (whole) cudaGraphExecDestroy(whole);
   }
@@ -608,7 +612,7 @@ int true_residual_restart(Solve &s, int par, bool restart_lo, double *rr) {
 int body_pair(Solve &s, cudaGraphConditionalHandle handle, int in_graph) {
   TRY(one_iteration(s, 0));
   TRY(one_iteration(s, 1));
-  k_cg_decide<<<1, 1, 0, s.ctx->stream>>>(s.st, handle, in_graph);
+  k_cg_decide<<<1, 1, 0, s.ctx->stream>>>(s.st, handle, 0, in_graph);
   return launched(s.ctx, "cg_decide");
 }
 
@@ -623,10 +627,48 @@ int body_update(Solve &s) {
   return launched(s.ctx, "cg_ru_end");
 }
 
-// ---- the whole solve as one CUDA graph -------------------------------------------------
-// top: while (handle `loop`, initially 1) { body_pair; if (handle `upd`)
-// { body_update }; k_cg_continue }.  The body graphs are captured on the
-// context's two body streams into the graphs that the conditional nodes own.
+// ---- the whole solve as one CUDA graph (capture_loop) -----------------------------------
+// body of the loop for capture_loop: iteration 0 (tallied), iteration 1 and
+// the decision, the update, the continue kernel
+LoopParts solve_parts(Solve &s) {
+  LoopParts L;
+  L.iter = [&s]() { return one_iteration(s, 0); };
+  L.rest = [&s](cudaGraphConditionalHandle upd, cudaGraphConditionalHandle loop) {
+    TRY(one_iteration(s, 1));
+    k_cg_decide<<<1, 1, 0, s.ctx->stream>>>(s.st, upd, loop, 1);
+    return launched(s.ctx, "cg_decide");
+  };
+  L.update = [&s]() { return body_update(s); };
+  return L;
+}
+
+// run the captured solve, read the state, count its launches (and, in
+// timing mode 3, the hemi-Dslash launches of the iterations and updates that
+// ran, gated-off ones excluded)
+int run_solve(Solve &s, const LoopTally &t, CGState *h) {
+  TRY(run_loop(s.ctx, s.whole));
+  TRY(read_state(s, h));
+  const long long nu = h->reliable + h->restarts;
+  s.ctx->launches += t.body * h->bodies + t.update * nu;
+  tally_add(s.ctx, t.t_iter, h->iter);
+  tally_add(s.ctx, t.t_update, nu);
+  return HMC_OK;
+}
+
+}  // namespace
+
+int graph_stream(hmc_ctx *ctx) {
+  if (ctx->gstream) return HMC_OK;
+  for (cudaStream_t &b : ctx->bstream)
+    TRY(cuda_ok(ctx, cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking),
+                "graph capture: body stream"));
+  TRY(cuda_ok(ctx, cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking),
+              "graph replay: stream"));
+  for (cudaEvent_t &e : ctx->gev)
+    TRY(cuda_ok(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming),
+                "graph replay: event"));
+  return HMC_OK;
+}
 
 int graph_of_capture(hmc_ctx *ctx, cudaStream_t cs, cudaGraph_t *g, const cudaGraphNode_t **deps,
                      size_t *nd) {
@@ -658,15 +700,14 @@ int add_conditional(hmc_ctx *ctx, cudaStream_t cs, cudaGraphConditionalNodeType 
                  "cg graph: capture dependencies");
 }
 
-struct Tally {
-  long long body = 0, update = 0;  // launches per body and per update
-  // timing mode 3: the classes of one iteration's and of one update's
-  // hemi-Dslash launches (counted per iteration and per update that ran)
-  std::vector<std::pair<int, double>> t_iter, t_update, t_rest;
-};
-
-int capture_solve(Solve &s, Tally *t) {
-  hmc_ctx *ctx = s.ctx;
+// ---- a solver loop as one CUDA graph ------------------------------------------------
+// top: while (handle `loop`, initially 1) { iter; rest (ending in the decision
+// kernel, which sets the handles `upd` and `loop`); if (upd) { update } }.
+// The bodies are captured on the context's two body streams into the graphs
+// that the conditional nodes own; ctx->stream points at the capturing stream
+// while the callbacks enqueue, and ctx->tally collects the timed classes of
+// each part (timing mode 3).
+int capture_loop(hmc_ctx *ctx, const LoopParts &L, LoopTally *t, cudaGraphExec_t *exec) {
   TRY(graph_stream(ctx));
   cudaStream_t user = ctx->stream, top = ctx->gstream, bs = ctx->bstream[0], us = ctx->bstream[1];
   const long long n0 = ctx->launches;
@@ -676,103 +717,69 @@ int capture_solve(Solve &s, Tally *t) {
   const cudaGraphNode_t *deps = nullptr;
   size_t nd = 0;
   cudaGraphConditionalHandle h_loop = 0, h_upd = 0;
-  int st = cuda_ok(ctx, cudaStreamBeginCapture(top, mode), "cg graph: begin capture");
+  int st = cuda_ok(ctx, cudaStreamBeginCapture(top, mode), "graph: begin capture");
   c_top = !st;
   if (!st) st = graph_of_capture(ctx, top, &g_top, &deps, &nd);
   if (!st)
     st = cuda_ok(ctx, cudaGraphConditionalHandleCreate(&h_loop, g_top, 1, cudaGraphCondAssignDefault),
-                 "cg graph: loop handle");
+                 "graph: loop handle");
   if (!st) st = add_conditional(ctx, top, cudaGraphCondTypeWhile, h_loop, &g_body);
   if (!st) {
     st = cuda_ok(ctx, cudaStreamBeginCaptureToGraph(bs, g_body, nullptr, nullptr, 0, mode),
-                 "cg graph: body capture");
+                 "graph: body capture");
     c_body = !st;
   }
   if (!st)
-    st = cuda_ok(ctx, cudaGraphConditionalHandleCreate(&h_upd, g_body, 0, 0),
-                 "cg graph: update handle");
+    st = cuda_ok(ctx, cudaGraphConditionalHandleCreate(&h_upd, g_body, 0, 0), "graph: update handle");
   const long long nb0 = ctx->launches;
   ctx->stream = bs;
   ctx->tally = &t->t_iter;
-  if (!st) st = one_iteration(s, 0);
+  if (!st) st = L.iter();
   ctx->tally = &t->t_rest;
-  if (!st) st = one_iteration(s, 1);
-  if (!st) {
-    k_cg_decide<<<1, 1, 0, bs>>>(s.st, h_upd, 1);
-    st = launched(ctx, "cg_decide");
-  }
+  if (!st) st = L.rest(h_upd, h_loop);
   if (!st) st = add_conditional(ctx, bs, cudaGraphCondTypeIf, h_upd, &g_upd);
   if (!st) {
     st = cuda_ok(ctx, cudaStreamBeginCaptureToGraph(us, g_upd, nullptr, nullptr, 0, mode),
-                 "cg graph: update capture");
+                 "graph: update capture");
     c_upd = !st;
   }
   const long long nu0 = ctx->launches;
   ctx->stream = us;
   ctx->tally = &t->t_update;
-  if (!st) st = body_update(s);
+  if (!st) st = L.update();
   t->update = ctx->launches - nu0;
   if (c_upd) {
     cudaError_t e = cudaStreamEndCapture(us, &done);
-    if (!st) st = cuda_ok(ctx, e, "cg graph: end update capture");
+    if (!st) st = cuda_ok(ctx, e, "graph: end update capture");
   }
   ctx->stream = bs;
-  ctx->tally = &t->t_rest;
-  if (!st) {
-    k_cg_continue<<<1, 1, 0, bs>>>(s.st, h_loop);
-    st = launched(ctx, "cg_continue");
-  }
   t->body = ctx->launches - nb0 - t->update;
   if (c_body) {
     cudaError_t e = cudaStreamEndCapture(bs, &done);
-    if (!st) st = cuda_ok(ctx, e, "cg graph: end body capture");
+    if (!st) st = cuda_ok(ctx, e, "graph: end body capture");
   }
   ctx->stream = user;
   ctx->tally = nullptr;
   cudaGraph_t g = nullptr;
   if (c_top) {
     cudaError_t e = cudaStreamEndCapture(top, &g);
-    if (!st) st = cuda_ok(ctx, e, "cg graph: end capture");
+    if (!st) st = cuda_ok(ctx, e, "graph: end capture");
   }
   ctx->launches = n0;
-  if (!st) st = cuda_ok(ctx, cudaGraphInstantiate(&s.whole, g, 0), "cg graph: instantiate");
+  if (!st) st = cuda_ok(ctx, cudaGraphInstantiate(exec, g, 0), "graph: instantiate");
   if (g) cudaGraphDestroy(g);
   return st;
 }
 
-// run the captured solve after the caller's stream's work, then order the
-// caller's stream after it; count its launches from the loop bodies and
-// updates that ran (in timing mode 3 the hemi-Dslash launches from the
-// iterations and updates that ran, gated-off ones excluded)
-int run_solve(Solve &s, const Tally &t, CGState *h) {
-  hmc_ctx *ctx = s.ctx;
+// launch the loop graph after the caller's stream's work and order the
+// caller's stream after it
+int run_loop(hmc_ctx *ctx, cudaGraphExec_t exec) {
   cudaStream_t user = ctx->stream;
-  TRY(cuda_ok(ctx, cudaEventRecord(ctx->gev[0], user), "cg graph: order"));
-  TRY(cuda_ok(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->gev[0], 0), "cg graph: order"));
-  TRY(cuda_ok(ctx, cudaGraphLaunch(s.whole, ctx->gstream), "cg graph: launch"));
-  TRY(cuda_ok(ctx, cudaEventRecord(ctx->gev[1], ctx->gstream), "cg graph: order"));
-  TRY(cuda_ok(ctx, cudaStreamWaitEvent(user, ctx->gev[1], 0), "cg graph: order"));
-  TRY(read_state(s, h));
-  const long long nu = h->reliable + h->restarts;
-  ctx->launches += t.body * h->bodies + t.update * nu;
-  tally_add(ctx, t.t_iter, h->iter);
-  tally_add(ctx, t.t_update, nu);
-  return HMC_OK;
-}
-
-}  // namespace
-
-int graph_stream(hmc_ctx *ctx) {
-  if (ctx->gstream) return HMC_OK;
-  for (cudaStream_t &b : ctx->bstream)
-    TRY(cuda_ok(ctx, cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking),
-                "graph capture: body stream"));
-  TRY(cuda_ok(ctx, cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking),
-              "graph replay: stream"));
-  for (cudaEvent_t &e : ctx->gev)
-    TRY(cuda_ok(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming),
-                "graph replay: event"));
-  return HMC_OK;
+  TRY(cuda_ok(ctx, cudaEventRecord(ctx->gev[0], user), "graph: order"));
+  TRY(cuda_ok(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->gev[0], 0), "graph: order"));
+  TRY(cuda_ok(ctx, cudaGraphLaunch(exec, ctx->gstream), "graph: launch"));
+  TRY(cuda_ok(ctx, cudaEventRecord(ctx->gev[1], ctx->gstream), "graph: order"));
+  return cuda_ok(ctx, cudaStreamWaitEvent(user, ctx->gev[1], 0), "graph: order");
 }
 
 int cg_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul, void *x,
@@ -873,8 +880,8 @@ int cg_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
   CGState h{};
   int st = HMC_OK;
   if (whole) {
-    Tally t;
-    st = capture_solve(s, &t);
+    LoopTally t;
+    st = capture_loop(ctx, solve_parts(s), &t, &s.whole);
     if (!st) st = run_solve(s, t, &h);
   } else {
     // batches of loop bodies sized from the observed convergence rate to end

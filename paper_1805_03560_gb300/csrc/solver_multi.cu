@@ -9,7 +9,10 @@
 // converged is frozen (alpha_r = 0, p_r no longer updated) while the others
 // continue.  Mixed precision: reliable updates are done for all right-hand
 // sides together (one multi-RHS FP64 operator application) whenever one of
-// them needs one, at batch boundaries; each restarts from its true residual.
+// them needs one; each restarts from its true residual.  As in the
+// single-system solver, the decisions are taken on the device after every
+// pair of iterations (k_mdecide, k_mru_end), and the solve runs as one CUDA
+// graph (capture_loop) or as the same kernels launched directly in batches.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -35,6 +38,12 @@ struct MState {
   // counters each; adv: arrivals of the state-advancing xpay
   unsigned int cnt[2][1 + RED_MAX_GROUPS];
   unsigned int adv;
+  int iter_cap;  // the xpay clears `active` once iter reaches it
+  // iteration control on the device (k_mcontrol_init, k_mdecide, k_mru_end)
+  double maxr2[NR_MAX];  // largest |r_q|^2 since the last reliable update
+  double delta2;
+  int n, mixed, max_iter, ru, stop;  // stop: 0 running, 1 converged, 2 NaN/Inf, 3 limit
+  int reliable, restarts, bodies, max_bodies;
 };
 
 // alpha_q = rr_q / pap_q for live q (0 for frozen);  x += alpha p;  r -= alpha Ap
@@ -130,8 +139,8 @@ __global__ void __launch_bounds__(BL_NT) k_mcg_xpay(void *p, const void *r, int 
     }
     any |= st->live[q];
   }
-  st->active = any;
   st->iter += 1;
+  st->active = any && st->iter < st->iter_cap;
   st->adv = 0u;
 }
 
@@ -196,6 +205,7 @@ __global__ void __launch_bounds__(FIN_NT) k_mstate(MState *st, const double *par
         st->live[q] = st->done[q] == 0;
       } else if (st->done[q] != 2) {
         st->rr[par][q] = s;
+        st->rr[par ^ 1][q] = s;
         const bool conv = s <= tol2 * st->b2[q];
         st->done[q] = conv ? 1 : (isfinite(s) ? 0 : 2);
         st->live[q] = st->done[q] == 0;
@@ -210,10 +220,95 @@ __global__ void __launch_bounds__(FIN_NT) k_mstate(MState *st, const double *par
     if (mode == 0) {
       st->tol2 = tol2;
       st->iter = 0;
+      st->iter_cap = 0x7fffffff;
       st->adv = 0u;
     }
   }
 }
+
+// ---- iteration control on the device ------------------------------------------------
+__global__ void k_mcontrol_init(MState *st, int n, double delta2, int max_iter, int mixed,
+                                int max_bodies) {
+  int nan = 0;
+  for (int q = 0; q < n; ++q) {
+    st->maxr2[q] = st->b2[q];
+    nan |= st->done[q] == 2;
+  }
+  st->n = n;
+  st->delta2 = delta2;
+  st->mixed = mixed;
+  st->max_iter = max_iter;
+  st->iter_cap = max_iter;
+  st->ru = 0;
+  st->reliable = st->restarts = st->bodies = 0;
+  st->max_bodies = max_bodies;
+  st->stop = nan ? 2 : (!st->active ? 1 : (max_iter > 0 ? 0 : 3));
+  if (st->stop) st->active = 0;
+}
+
+// after each pair of iterations: NaN, a reliable update (mixed: some live
+// |r_q|^2 below its tolerance or delta^2 times its largest value since the
+// last update; plain: every live system converged on its recursive residual),
+// or the iteration limit; in a graph `upd` receives whether the update runs
+// and `loop` whether the loop goes on (as in k_cg_decide)
+__global__ void k_mdecide(MState *st, cudaGraphConditionalHandle upd,
+                          cudaGraphConditionalHandle loop, int in_graph) {
+  int ru = 0;
+  if (st->stop == 0) {
+    int nan = 0;
+    for (int q = 0; q < st->n; ++q) nan |= st->done[q] == 2;
+    if (nan) {
+      st->stop = 2;
+      st->active = 0;
+    } else if (!st->mixed) {
+      ru = !st->active && st->iter < st->max_iter;
+    } else {
+      for (int q = 0; q < st->n; ++q) {
+        if (!st->live[q]) continue;
+        const double rr = st->rr[st->iter & 1][q];
+        if (rr > st->maxr2[q]) st->maxr2[q] = rr;
+        if (rr <= st->tol2 * st->b2[q] || rr < st->delta2 * st->maxr2[q]) ru = 1;
+      }
+    }
+    if (!ru && st->stop == 0 && st->iter >= st->max_iter) {
+      st->stop = 3;
+      st->active = 0;
+    }
+  }
+  if (ru) st->active = 0;
+  st->ru = ru;
+  st->bodies += 1;
+  if (in_graph) {
+    cudaGraphSetConditional(upd, ru ? 1u : 0u);
+    cudaGraphSetConditional(loop, st->stop == 0 && st->bodies < st->max_bodies ? 1u : 0u);
+  }
+}
+
+// end of a reliable update (k_mstate mode 1 has restarted every system from
+// its true residual): count it, stop when every system has converged
+__global__ void k_mru_end(MState *st) {
+  int nan = 0;
+  for (int q = 0; q < st->n; ++q) {
+    st->maxr2[q] = st->aux[q];
+    nan |= st->done[q] == 2;
+  }
+  if (st->mixed)
+    st->reliable += 1;
+  else
+    st->restarts += 1;
+  st->ru = 0;
+  if (nan) {
+    st->stop = 2;
+    st->active = 0;
+  } else if (!st->active) {
+    st->stop = 1;
+  } else if ((!st->mixed && st->restarts > 5) || st->iter >= st->max_iter) {
+    st->stop = 3;
+    st->active = 0;
+  }
+}
+
+
 
 __global__ void __launch_bounds__(BL_NT) k_mfold(void *x, void *y, int S) {
   int i = blockIdx.x * BL_NT + threadIdx.x;
@@ -252,6 +347,11 @@ struct MSolve {
   const void *b;
   int nb_ds, nb_bl;
   HiOps hi;  // the FP64-accurate A x of the true residuals
+  double tol2;
+  cudaGraphExec_t whole = nullptr;  // the whole solve (capture_loop)
+  ~MSolve() {
+    if (whole) cudaGraphExecDestroy(whole);
+  }
 };
 
 int m_apply_A64(MSolve &s, const void *in, void *out) {
@@ -362,6 +462,36 @@ int m_true_residual(MSolve &s, int par, double tol2) {
   return launched(s.ctx, "cg_multi_restart");
 }
 
+// the reliable update of every system (plain CG: the true-residual check)
+int m_body_update(MSolve &s) {
+  if (s.plo != HMC_F64) {
+    k_mfold<<<s.nb_bl, BL_NT, 0, s.ctx->stream>>>(s.x, s.xlo, s.S);
+    TRY(launched(s.ctx, "fold_multi"));
+  }
+  TRY(m_true_residual(s, 0, s.tol2));
+  k_mru_end<<<1, 1, 0, s.ctx->stream>>>(s.st);
+  return launched(s.ctx, "cg_multi_ru_end");
+}
+
+int m_body_pair(MSolve &s) {
+  TRY(m_iteration(s, 0));
+  TRY(m_iteration(s, 1));
+  k_mdecide<<<1, 1, 0, s.ctx->stream>>>(s.st, 0, 0, 0);
+  return launched(s.ctx, "cg_multi_decide");
+}
+
+LoopParts m_parts(MSolve &s) {
+  LoopParts L;
+  L.iter = [&s]() { return m_iteration(s, 0); };
+  L.rest = [&s](cudaGraphConditionalHandle upd, cudaGraphConditionalHandle loop) {
+    TRY(m_iteration(s, 1));
+    k_mdecide<<<1, 1, 0, s.ctx->stream>>>(s.st, upd, loop, 1);
+    return launched(s.ctx, "cg_multi_decide");
+  };
+  L.update = [&s]() { return m_body_update(s); };
+  return L;
+}
+
 }  // namespace
 
 int cg_solve_multi(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul, void *x,
@@ -447,67 +577,78 @@ int cg_solve_multi(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_ga
     TRY(dslash_tune(ctx, g, s.Ul, s.plo, n_rhs, s.tlo, s.p));
     s.mr = dslash_mr_nr(ctx, g, s.plo, s.Ul.fmt, n_rhs);
   }
+  s.tol2 = tol * tol;
+  // the FP64-accurate operator's scratch (and tuned classes) for the capture
+  TRY(hi_prepare(s.hi, n_rhs));
+  const int cap = max_iter > 0 ? max_iter : 0;
+  const long long bodies = 2LL * cap + 16;
+  k_mcontrol_init<<<1, 1, 0, ctx->stream>>>(s.st, n_rhs, delta * delta, cap, mixed ? 1 : 0,
+                                            bodies < 0x7fffffff ? (int)bodies : 0x7fffffff);
+  TRY(launched(ctx, "cg_multi_control"));
+  bool sampled = false;
+  if (ctx->timing == 3) sampled = (ctx->solve_seq++ % kTimingSample) == 0;
+  const bool whole = ctx->cg_graph && (ctx->timing == 0 || (ctx->timing == 3 && !sampled));
+  const int sample_prev = ctx->sample_on;
+  if (ctx->timing == 3) ctx->sample_on = sampled ? 1 : 0;
   MState h{};
-  TRY(m_read(s, &h));
-  std::vector<double> maxr2(n_rhs), rr(n_rhs);
-  std::vector<int> reliable(n_rhs, 0);
-  for (int q = 0; q < n_rhs; ++q) maxr2[q] = rr[q] = h.b2[q];
-  int k = 0, restarts = 0;
-  bool nan = false;
-  double rate = 0.0;  // slowest observed log-decrease per iteration
-  while (h.active && k < max_iter) {
-    int todo = check;
-    if (rate < 0.0) {
-      double left = 0.0;
-      for (int q = 0; q < n_rhs; ++q) {
-        if (!h.live[q]) continue;
-        const double target =
-            mixed ? fmax(tol * tol * h.b2[q], delta * delta * maxr2[q]) : tol * tol * h.b2[q];
-        left = fmax(left, log(target / rr[q]) / rate);
+  int st = HMC_OK;
+  if (whole) {
+    LoopTally t;
+    st = capture_loop(ctx, m_parts(s), &t, &s.whole);
+    if (!st) st = run_loop(ctx, s.whole);
+    if (!st) st = m_read(s, &h);
+    if (!st) {
+      const long long nu = h.reliable + h.restarts;
+      ctx->launches += t.body * h.bodies + t.update * nu;
+      tally_add(ctx, t.t_iter, h.iter);
+      tally_add(ctx, t.t_update, nu);
+    }
+  } else {
+    // batches of loop bodies ending before the earliest predicted decision,
+    // the state read after each
+    st = m_read(s, &h);
+    std::vector<double> rr(n_rhs);
+    for (int q = 0; q < n_rhs; ++q) rr[q] = h.b2[q];
+    double rate = 0.0;  // slowest observed log-decrease per iteration
+    while (!st && h.stop == 0) {
+      if (h.ru) {
+        st = m_body_update(s);
+        if (!st) st = m_read(s, &h);
+        for (int q = 0; q < n_rhs; ++q) rr[q] = h.aux[q];
+        continue;
       }
-      if (left < todo) todo = left < 1.0 ? 1 : (int)ceil(left);
-    }
-    if (k + todo > max_iter) todo = max_iter - k;
-    for (int j = 0; j < todo; ++j) TRY(m_iteration(s, k + j));
-    std::vector<double> before(rr);
-    TRY(m_read(s, &h));
-    const int did = h.iter - k;
-    k = h.iter;
-    double worst = 0.0;
-    bool update = false;
-    for (int q = 0; q < n_rhs; ++q) {
-      if (h.done[q] == 2) nan = true;
-      const double now = h.rr[k & 1][q];
-      if (h.live[q] && did > 0 && now > 0.0 && now < before[q])
-        worst = worst == 0.0 ? log(now / before[q]) / did : fmax(worst, log(now / before[q]) / did);
-      rr[q] = now;
-      if (now > maxr2[q]) maxr2[q] = now;
-      if (mixed && h.live[q] &&
-          (now <= tol * tol * h.b2[q] || now < delta * delta * maxr2[q]))
-        update = true;
-    }
-    if (nan) break;
-    if (worst < 0.0) rate = worst;
-    if (mixed && update) {
-      // reliable update of every right-hand side at once
-      k_mfold<<<s.nb_bl, BL_NT, 0, ctx->stream>>>(s.x, s.xlo, s.S);
-      TRY(launched(ctx, "fold_multi"));
-      TRY(m_true_residual(s, k & 1, tol * tol));
-      TRY(m_read(s, &h));
-      for (int q = 0; q < n_rhs; ++q) {
-        ++reliable[q];
-        rr[q] = maxr2[q] = h.aux[q];
+      int pairs = check > 1 ? check / 2 : 1;
+      if (rate < 0.0) {
+        double left = 1e30;
+        for (int q = 0; q < n_rhs; ++q) {
+          if (!h.live[q]) continue;
+          const double target = mixed ? fmax(h.tol2 * h.b2[q], h.delta2 * h.maxr2[q])
+                                       : h.tol2 * h.b2[q];
+          left = fmin(left, log(target / rr[q]) / rate);
+        }
+        const int whole_pairs = left < 2.0 * pairs ? (int)floor(0.5 * left) : pairs;
+        pairs = whole_pairs < 1 ? 1 : whole_pairs;
       }
-      continue;
-    }
-    if (!mixed && !h.active) {
-      // every RHS converged on its recursive residual: confirm on the true one
-      TRY(m_true_residual(s, k & 1, tol * tol));
-      TRY(m_read(s, &h));
-      if (!h.active || ++restarts > 5) break;
-      for (int q = 0; q < n_rhs; ++q) rr[q] = h.aux[q];
+      const int k0 = h.iter;
+      for (int j = 0; !st && j < pairs; ++j) st = m_body_pair(s);
+      if (!st) st = m_read(s, &h);
+      if (st) break;
+      const int did = h.iter - k0;
+      double worst = 0.0;
+      for (int q = 0; q < n_rhs; ++q) {
+        const double now = h.rr[h.iter & 1][q];
+        if (h.live[q] && did > 0 && now > 0.0 && now < rr[q])
+          worst = worst == 0.0 ? log(now / rr[q]) / did : fmax(worst, log(now / rr[q]) / did);
+        rr[q] = now;
+      }
+      if (worst < 0.0) rate = worst;
     }
   }
+  ctx->sample_on = sample_prev;
+  TRY(st);
+  const int k = h.iter;
+  const bool nan = h.stop == 2;
+  std::vector<int> reliable(n_rhs, h.reliable);
   if (mixed) {
     k_mfold<<<s.nb_bl, BL_NT, 0, ctx->stream>>>(s.x, s.xlo, s.S);
     TRY(launched(ctx, "fold_multi"));

@@ -256,3 +256,55 @@ def test_sampled_timing_counts_graph_launches(ctx, H):
     assert timed3 >= 4 * it3[0] and n3 - timed3 == 4 * (it3[1] + it3[2])
     assert b3 / n3 == b1 / n1
     assert ms3 > 0.0 and ms3 / timed3 == pytest.approx(ms1 / timed1, rel=0.5)
+
+
+@pytest.mark.parametrize("inner", [0, 1])
+@pytest.mark.parametrize("n_rhs", [3, 4])
+def test_cg_multi_graph_bits_and_syncs(ctx, H, inner, n_rhs):
+    """The batched solve as one CUDA graph (decisions on the device, all
+    systems' reliable updates together) gives the same bits and statistics
+    as its kernels launched directly in batches, with at most four host
+    waits per solve (the state at the end and the final residuals')."""
+    L = (16, 8, 8, 8)
+    kappas = [0.150, 0.154, 0.1575, 0.156][:n_rhs]
+    U = I.gauge_links(L, 0.3, 1)
+    phi = I.gaussian_half(L, 2, n_rhs=n_rhs)
+    Uh = ctx.pack_gauge(L, U, 0, 18)
+    Ul = ctx.pack_gauge(L, U, inner, 12) if inner else None
+    b = ctx.pack_spinor(L, phi, 0)
+    got = {}
+    for graph in (1, 0):
+        ctx.set_cg_graph(graph)
+        x = ctx.new_spinor(L, 0, n_rhs)
+        ctx.cg_solve_multi(L, Uh, x, b, kappas, 1e-11, U_lo=Ul, inner_prec=inner)
+        y0 = ctx.host_syncs()
+        r = ctx.cg_solve_multi(L, Uh, x, b, kappas, 1e-11, U_lo=Ul, inner_prec=inner)
+        got[graph] = (_np(ctx.unpack_spinor(L, x)), r, ctx.host_syncs() - y0)
+    ctx.set_cg_graph(1)
+    (xg, rg, yg), (xd, rd, yd) = got[1], got[0]
+    assert rg["status"] == 0 and max(rg["true_rel_res"]) <= 1e-11
+    assert np.array_equal(xg, xd)
+    assert rg["iterations"] == rd["iterations"] and rg["reliable_updates"] == rd["reliable_updates"]
+    assert yg <= 4 and yd > yg, (yg, yd)
+
+
+def test_cg_multi_iteration_limit_on_device(ctx, H):
+    """max_iter ends the batched loop at exactly max_iter iterations with
+    ENOCONV, with and without the graph, identically."""
+    L = (4, 6, 6, 10)
+    U = I.gauge_links(L, 0.3, 1)
+    phi = I.gaussian_half(L, 2, n_rhs=3)
+    Uh = ctx.pack_gauge(L, U, 0, 18)
+    Ul = ctx.pack_gauge(L, U, H.F32, 12)
+    b = ctx.pack_spinor(L, phi, 0)
+    out = []
+    for graph in (1, 0):
+        ctx.set_cg_graph(graph)
+        x = ctx.new_spinor(L, 0, 3)
+        r = ctx.cg_solve_multi(L, Uh, x, b, [0.150, 0.154, 0.1575], 1e-14, max_iter=9, U_lo=Ul,
+                               inner_prec=H.F32)
+        out.append((_np(ctx.unpack_spinor(L, x)), r))
+    ctx.set_cg_graph(1)
+    for x, r in out:
+        assert r["status"] == H.ENOCONV and r["iterations"] == [9, 9, 9], r
+    assert np.array_equal(out[0][0], out[1][0])
