@@ -237,7 +237,7 @@ def run_kernel(args):
     for i in range(args.launches):
         ctx.dslash(LAT, U, out, srcs[i % 2], i % 2)
     torch.cuda.synchronize()
-    n, ms, byt, _ = next(iter(ctx.timing().values()))
+    n, ms, byt, _, _ = next(iter(ctx.timing().values()))
     Vh = int(np.prod(LAT)) // 2
     pk = peaks()
     gbs = byt / (ms * 1e-3) / 1e9
@@ -520,9 +520,9 @@ def run_hmc(args):
     # dominant Dslash class by time (average over its timed launches x launches)
     dom = max((k for k in kst if k.startswith("dslash") and kst[k][3]),
               key=lambda k: kst[k][1] / kst[k][3] * kst[k][0])
-    n_all, ms_t, b_all, t_dom = kst[dom]
-    # per timed launch: the average duration, the algorithmic bytes per launch
-    n_dom, ms_dom, b_dom = t_dom, ms_t, b_all / n_all * t_dom
+    n_all, ms_t, b_all, t_dom, tb_dom = kst[dom]
+    # the timed launches: their count, summed duration and algorithmic bytes
+    n_dom, ms_dom, b_dom = t_dom, ms_t, tb_dom
     pk = peaks()
     if dom.startswith("dslash_f64_"):
         # native FP64: bound by the FP64 units (measured FMA rate)
@@ -547,7 +547,7 @@ def run_hmc(args):
                 "peak_source": "measured" if pk else "fallback"}
     kernels = {k: {"launches_per_step": v[0] // args.steps, "timed_launches": v[3],
                    "us": round(v[1] / v[3] * 1e3, 2) if v[3] else None,
-                   "GBs": round(v[2] / v[0] / (v[1] / v[3] * 1e-3) / 1e9, 1) if v[3] else None}
+                   "GBs": round(v[4] / (v[1] * 1e-3) / 1e9, 1) if v[3] else None}
                for k, v in sorted(kst.items())}
     dHs = [r["dH"] for r in results]
     if args.c5:

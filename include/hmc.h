@@ -138,8 +138,8 @@ long long hmc_host_sync_count(hmc_ctx *ctx);
  * solve in eight (the first of every eight since timing was enabled, run with
  * direct launches) and the hemi-Dslash launches outside CG solves are
  * bracketed by events; the other solves run as in mode 0.  The average
- * duration of a class is its summed time over its event-timed launches
- * (hmc_timing_get_timed).  Modes 1 and 2 launch every kernel directly.
+ * duration of a class is its summed time over its event-timed launches, its
+ * throughput their bytes over that time (hmc_timing_get_timed).  Modes 1 and 2 launch every kernel directly.
  * Mode 0 switches timing off.  Any call clears the statistics. */
 int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
 /* Tuning options.  HMC_OPT_DSLASH_VARIANT selects the hemi-Dslash kernel
@@ -204,9 +204,11 @@ int hmc_workspace_check(hmc_ctx *ctx, int *n_bad);
 int hmc_timing_get(hmc_ctx *ctx, int index, char *name, int name_len,
                    long long *launches, double *total_ms, double *bytes);
 /* Number of the index-th class's launches that were bracketed by events
- * (equal to its launches except in timing mode 3).  Synchronises the stream.
- * HMC_EINVAL past the last class or for a NULL timed. */
-int hmc_timing_get_timed(hmc_ctx *ctx, int index, long long *timed);
+ * (equal to its launches except in timing mode 3) and, when timed_bytes is
+ * not NULL, their summed algorithmic bytes (a class can mix launch sizes,
+ * e.g. batched solves of different right-hand-side counts).  Synchronises
+ * the stream.  HMC_EINVAL past the last class or for a NULL timed. */
+int hmc_timing_get_timed(hmc_ctx *ctx, int index, long long *timed, double *timed_bytes);
 
 /* hmc_measure_fma_peak: measured CUDA-core multiply-add throughput of the
  * context's device in TFLOP/s (2 flops per FMA, 4 per paired FMA), for the

@@ -149,6 +149,7 @@ int timing_resolve(hmc_ctx *ctx) {
       hmc_ctx::KStat &k = ctx->kstats[p.cls];
       k.n += 1;
       k.timed += 1;
+      k.timed_bytes += p.bytes;
       k.ms += ms;
       k.bytes += p.bytes;
     }
@@ -376,11 +377,12 @@ int hmc_timing_get(hmc_ctx *ctx, int index, char *name, int name_len, long long 
   return HMC_OK;
 }
 
-int hmc_timing_get_timed(hmc_ctx *ctx, int index, long long *timed) {
+int hmc_timing_get_timed(hmc_ctx *ctx, int index, long long *timed, double *timed_bytes) {
   CTX_CHECK(ctx);
   TRY(timing_resolve(ctx));
   if (index < 0 || index >= (int)ctx->kstats.size() || !timed) return HMC_EINVAL;
   *timed = ctx->kstats[index].timed;
+  if (timed_bytes) *timed_bytes = ctx->kstats[index].timed_bytes;
   return HMC_OK;
 }
 

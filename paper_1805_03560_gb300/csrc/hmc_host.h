@@ -61,7 +61,7 @@ struct hmc_ctx {
   struct KStat {
     std::string name;
     long long n = 0, timed = 0;  // launches, event-timed launches
-    double ms = 0.0, bytes = 0.0;
+    double ms = 0.0, bytes = 0.0, timed_bytes = 0.0;  // time and bytes of the timed ones
   };
   std::vector<cudaEvent_t> ev_free;
   std::vector<Pending> pending;

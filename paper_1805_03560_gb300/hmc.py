@@ -92,7 +92,7 @@ _SIGS = {
     "hmc_ctx_set_stream": (_I, [_P, _P]),
     "hmc_last_error": (ctypes.c_char_p, [_P]),
     "hmc_launch_count": (ctypes.c_longlong, [_P]),
-    "hmc_timing_get_timed": (_I, [_P, _I, _P]),
+    "hmc_timing_get_timed": (_I, [_P, _I, _P, _P]),
     "hmc_host_sync_count": (ctypes.c_longlong, [_P]),
     "hmc_ctx_set_timing": (_I, [_P, _I]),
     "hmc_ctx_set_option": (_I, [_P, _I, _I]),
@@ -300,8 +300,9 @@ class Context:
         self._check(lib().hmc_ctx_set_timing(self.h, int(enable)), "hmc_ctx_set_timing")
 
     def timing(self):
-        """{class: (launches, total_ms, algorithmic_bytes, timed_launches)} since
-        timing was enabled (total_ms is summed over the timed launches)."""
+        """{class: (launches, total_ms, algorithmic_bytes, timed_launches,
+        timed_bytes)} since timing was enabled (total_ms and timed_bytes are
+        summed over the timed launches)."""
         out = {}
         i = 0
         while True:
@@ -312,9 +313,10 @@ class Context:
             if st:
                 break
             t = ctypes.c_longlong(0)
-            self._check(lib().hmc_timing_get_timed(self.h, i, ctypes.byref(t)),
+            tb = ctypes.c_double(0)
+            self._check(lib().hmc_timing_get_timed(self.h, i, ctypes.byref(t), ctypes.byref(tb)),
                         "hmc_timing_get_timed")
-            out[name.value.decode()] = (n.value, ms.value, b.value, t.value)
+            out[name.value.decode()] = (n.value, ms.value, b.value, t.value, tb.value)
             i += 1
         return out
 

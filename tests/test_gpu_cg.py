@@ -248,13 +248,14 @@ def test_sampled_timing_counts_graph_launches(ctx, H):
     (it1, t1), (it3, t3) = stats[1], stats[3]
     assert it1 == it3
     cls = "dslash_f32_12/cg"
-    n1, ms1, b1, timed1 = t1[cls]
-    n3, ms3, b3, timed3 = t3[cls]
+    n1, ms1, b1, timed1, tb1 = t1[cls]
+    n3, ms3, b3, timed3, tb3 = t3[cls]
     # direct launches are counted as issued: a body gated off by a pending
     # update (rare: batches end before the predicted decision) counts too
     assert timed1 == n1 and n1 >= 4 * sum(it1)
     assert timed3 >= 4 * it3[0] and n3 - timed3 == 4 * (it3[1] + it3[2])
-    assert b3 / n3 == b1 / n1
+    assert b3 / n3 == b1 / n1 and tb1 == b1
+    assert tb3 == pytest.approx(b3 / n3 * timed3, rel=1e-3)
     assert ms3 > 0.0 and ms3 / timed3 == pytest.approx(ms1 / timed1, rel=0.5)
 
 
