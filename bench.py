@@ -134,6 +134,9 @@ def parse():
     ap.add_argument("--variant", type=int, default=None,
                     help="hemi-Dslash kernel variant 0..3, -1 built-in default, -2 autotuned "
                          "(the trajectory benchmark autotunes by default)")
+    ap.add_argument("--no-pdl", action="store_true",
+                    help="launch the hemi-Dslash and CG-update kernels without programmatic "
+                         "dependent launch")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the CG kernels directly (no CUDA graphs), e.g. for an ncu "
                          "launch list")
@@ -154,6 +157,8 @@ def run_kernel(args):
         ctx.set_dslash_variant(args.variant)
     if args.no_graph:
         ctx.set_cg_graph(0)
+    if args.no_pdl:
+        ctx.set_pdl(0)
     if pname == "cgm":
         # batched solve of n systems (kappas of mass-preconditioned
         # pseudo-fermions) on the benchmark lattice, links shared per launch
@@ -388,6 +393,8 @@ def run_hmc(args):
     ctx = hmc.Context(local)
     if args.no_graph:
         ctx.set_cg_graph(0)  # every kernel a direct launch (e.g. for an ncu launch list)
+    if args.no_pdl:
+        ctx.set_pdl(0)
     # measured CUDA-core FMA ceilings (the arithmetic rooflines)
     fma = {k: round(ctx.fma_peak(i), 2) for i, k in enumerate(("fp64", "fp32", "fp32x2"))}
     # autotuned hemi-Dslash variants (tuned during the warm-up steps)
@@ -578,6 +585,7 @@ def run_hmc(args):
                    "force_prec": args.force_prec, "f64_emul": args.f64_emul,
                    "solver": args.solver,
                    "dslash_variant": "autotuned" if args.variant is None else args.variant,
+                   "pdl": not args.no_pdl,
                    "cg_graph": "direct launches" if args.no_graph else
                    "one CUDA graph per solve (one solve in eight direct and event-timed)",
                    "links": "12-real (inner), 18-real FP64",

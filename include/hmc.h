@@ -182,6 +182,13 @@ int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
  * state read after each (the same kernels on the same data: results are
  * bit-identical).  Graphs are not used in timing modes 1 and 2. */
 #define HMC_OPT_CG_GRAPH 2
+/* HMC_OPT_PDL: 1 (default) launches the hemi-Dslash kernels and the CG's
+ * xpay as programmatic dependent launches: each may be scheduled while the
+ * kernel before it on the stream finishes its last blocks, and waits for that
+ * kernel's completion (griddepcontrol.wait) before touching its data, so the
+ * gap between dependent launches closes; results are bit-identical.  0
+ * launches them normally. */
+#define HMC_OPT_PDL 4
 /* HMC_OPT_WORKSPACE_GUARD: 1 frees the context's workspace and gives every
  * buffer allocated afterwards a 4 KiB guard region of the byte 0xA5 after its
  * end; hmc_workspace_check then reports any buffer whose guard was written (a
@@ -189,7 +196,7 @@ int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
  * is not used).  0 (default): no guards. */
 #define HMC_OPT_WORKSPACE_GUARD 3
 /* Sets option (HMC_OPT_DSLASH_VARIANT: -2..8, HMC_OPT_CG_GRAPH: 0 or 1,
- * HMC_OPT_WORKSPACE_GUARD: 0 or 1) for
+ * HMC_OPT_WORKSPACE_GUARD: 0 or 1, HMC_OPT_PDL: 0 or 1) for
  * every later call on ctx.  HMC_EINVAL for an unknown option or value. */
 int hmc_ctx_set_option(hmc_ctx *ctx, int option, int value);
 /* hmc_workspace_check: synchronises the context's streams and checks the

@@ -479,6 +479,10 @@ __global__ void __launch_bounds__(DS_NT, ds_min_blocks(SP)) k_dslash(const Dslas
   using SIO = SpinorIO<SP>;
   using R = typename SIO::R;
   constexpr int SF = DAG ? -1 : 1;  // forwards: 1 - gamma (1 + gamma for the adjoint)
+  griddep_launch_dependents();
+  if constexpr ((SP == HMC_F32 || SP == HMC_F16 || SP == HMC_BF16) && FMT == 12)
+    if (a.prefetch) prefetch_block_links<SP, FMT>(a);  // links: not written by the kernel before
+  griddep_wait();
   if (a.gate && *a.gate == 0) return;
   if (a.red_src && blockIdx.x == 0) {
     const double t = block_sum_partials<DS_NT>(a.red_src, a.red_n);
@@ -491,8 +495,6 @@ __global__ void __launch_bounds__(DS_NT, ds_min_blocks(SP)) k_dslash(const Dslas
       }
     }
   }
-  if constexpr ((SP == HMC_F32 || SP == HMC_F16 || SP == HMC_BF16) && FMT == 12)
-    if (a.prefetch) prefetch_block_links<SP, FMT>(a);
   const int S_ = a.g.Vh * a.n_rhs;
   const int i = dslash_site(a);
   double nrm = 0.0;
@@ -601,16 +603,17 @@ __global__ void __launch_bounds__(DS_NT, ds_min_blocks(SP)) k_dslash(const Dslas
 
 template <int SP, int FMT>
 static void launch_sf(const DslashArgs &a, int dagger, bool pair, int nb, cudaStream_t st) {
+  const bool pdl = a.pdl != 0;
   if (pair) {
     if (dagger)
-      k_dslash<SP, FMT, true, true><<<nb, DS_NT, 0, st>>>(a);
+      launch_pdl(k_dslash<SP, FMT, true, true>, nb, DS_NT, st, pdl, a);
     else
-      k_dslash<SP, FMT, false, true><<<nb, DS_NT, 0, st>>>(a);
+      launch_pdl(k_dslash<SP, FMT, false, true>, nb, DS_NT, st, pdl, a);
   } else {
     if (dagger)
-      k_dslash<SP, FMT, true, false><<<nb, DS_NT, 0, st>>>(a);
+      launch_pdl(k_dslash<SP, FMT, true, false>, nb, DS_NT, st, pdl, a);
     else
-      k_dslash<SP, FMT, false, false><<<nb, DS_NT, 0, st>>>(a);
+      launch_pdl(k_dslash<SP, FMT, false, false>, nb, DS_NT, st, pdl, a);
   }
 }
 
@@ -810,8 +813,10 @@ int dslash(hmc_ctx *ctx, const DslashArgs &a, const hmc_gauge &U, int sprec, int
     return fail(ctx, HMC_EINVAL, "dslash: the fused batched update needs the multi-rhs kernel");
   if (var >= 4 && var < 7 && nblocks)
     *nblocks = blocks_for((long long)a.g.Vh * (a.n_rhs / (var - 2)), DS_NT);
+  DslashArgs la = a;
+  la.pdl = ctx->pdl;
   TimedLaunch timer(ctx, cls, bytes);
-  if (!launch_any(a, sprec, U.fmt, dagger, var, nb, st))
+  if (!launch_any(la, sprec, U.fmt, dagger, var, nb, st))
     return fail(ctx, HMC_EINVAL, "dslash: unsupported precision %d / link format %d", sprec,
                 U.fmt);
   return launched(ctx, cls);

@@ -248,6 +248,8 @@ constexpr int mr_min_blocks(int nr) {
 template <int SP, int FMT, bool DAG, int NR>
 __global__ void __launch_bounds__(DS_NT, mr_min_blocks(NR)) k_dslash_mr(const DslashArgs a) {
   constexpr int SF = DAG ? -1 : 1;
+  griddep_launch_dependents();
+  griddep_wait();
   if (a.gate && *a.gate == 0) return;
   const int n = a.n_rhs, NG = n / NR, St = a.g.Vh * n;
   const int i = blockIdx.x * DS_NT + threadIdx.x;
@@ -341,9 +343,9 @@ template <int SP, int FMT, int NR>
 void launch_nr(const DslashArgs &a, int dagger, cudaStream_t st) {
   const int nb = blocks_for((long long)a.g.Vh * (a.n_rhs / NR), DS_NT);
   if (dagger)
-    k_dslash_mr<SP, FMT, true, NR><<<nb, DS_NT, 0, st>>>(a);
+    launch_pdl(k_dslash_mr<SP, FMT, true, NR>, nb, DS_NT, st, a.pdl != 0, a);
   else
-    k_dslash_mr<SP, FMT, false, NR><<<nb, DS_NT, 0, st>>>(a);
+    launch_pdl(k_dslash_mr<SP, FMT, false, NR>, nb, DS_NT, st, a.pdl != 0, a);
 }
 
 template <int SP, int FMT>

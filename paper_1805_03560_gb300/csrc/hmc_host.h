@@ -39,6 +39,9 @@ struct hmc_ctx {
   // library's own non-blocking stream for capture and replay, ordered after
   // and before the caller's stream by gev
   int cg_graph = 1;
+  // hemi-Dslash and CG-update kernels as programmatic dependent launches
+  // (HMC_OPT_PDL)
+  int pdl = 1;
   // autotuned hemi-Dslash variant per launch class (ds_variant == -2);
   // tune_frozen: use tuned classes, never tune (untuned: built-in default)
   std::map<std::string, int> ds_tuned;
@@ -136,6 +139,7 @@ struct DslashArgs {
   const char *tag;  // timing class suffix (nullable)
   int tile_nseg;    // set by the launcher: 32-site segments per (x, t) plane, 0 = linear
   int prefetch;     // set by the launcher: bulk L2 prefetch of the block's links (variants 7, 8)
+  int pdl;          // set by dslash(): programmatic dependent launch (launch_pdl)
   // with partials: the last block also sums them into *total (counter: a
   // zeroed device int, returned to zero)
   double *total;
@@ -224,6 +228,29 @@ int cg_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
 
 // BiCGstab on Mhat (dagger 0) or Mhat^dag, and (Mhat^dag Mhat)^{-1} as two
 // such solves (bicgstab.cu)
+// kernel<<<nb, nt, 0, st>>>(args...), as a programmatic dependent launch
+// (cudaLaunchAttributeProgrammaticStreamSerialization) when pdl: the kernel
+// must then call griddep_wait() before touching the previous kernel's data
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), int nb, int nt, cudaStream_t st, bool pdl,
+                       Args... args) {
+  if (!pdl) {
+    kernel<<<nb, nt, 0, st>>>(args...);
+    return;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(nb);
+  cfg.blockDim = dim3(nt);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // the context's graph-replay stream, its two ordering events and the two
 // streams on which conditional bodies are captured, created on first use
 int graph_stream(hmc_ctx *ctx);

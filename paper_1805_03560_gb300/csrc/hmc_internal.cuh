@@ -622,6 +622,19 @@ __device__ __forceinline__ const void *link_base(const void *gauge, int Vh, int 
   return (const char *)gauge + (size_t)(p * 4 + mu) * IO::NC * n * IO::chunk;
 }
 
+// ---- programmatic dependent launch ------------------------------------------------
+// A kernel launched with programmatic stream serialization (launch_pdl) may
+// start while the kernel before it on the stream is still running: its
+// blocks call griddep_launch_dependents() first (the kernel after it may then
+// be scheduled once every block of this one has started) and griddep_wait()
+// before reading or writing anything the previous kernel writes or reads
+// (the wait returns when that kernel has completed and its memory is
+// visible).  Both are no-ops in a kernel launched normally.
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---- block reductions -----------------------------------------------------------
 
 // Sum of v over the block; the result is valid in thread 0.  Fixed order, so

@@ -160,6 +160,8 @@ template <int PL>
 __global__ void __launch_bounds__(BL_NT) k_cg_xpay(void *p, const void *r, int S, CGState *st,
                                                    int par, int plain, const double *rr_part,
                                                    int n_part) {
+  griddep_launch_dependents();
+  griddep_wait();
   if (!st->active) return;
   using R = RT<PL>;
   // the first grid-stride element's r and p are loaded before the sum of the
@@ -500,9 +502,8 @@ int apply_A64(Solve &s, const void *in, void *out) {
 template <int PL>
 void launch_xpay(Solve &s, int par, int n_part) {
   const int nb = s.nb_bl < 2 * s.ctx->sm_count ? s.nb_bl : 2 * s.ctx->sm_count;
-  k_cg_xpay<PL><<<nb, BL_NT, 0, s.ctx->stream>>>(s.p, s.rlo, s.S, s.st, par,
-                                                      s.plo == HMC_F64 ? 1 : 0, s.rr_part,
-                                                      n_part);
+  launch_pdl(k_cg_xpay<PL>, nb, BL_NT, s.ctx->stream, s.ctx->pdl != 0, s.p, (const void *)s.rlo,
+             s.S, s.st, par, s.plo == HMC_F64 ? 1 : 0, (const double *)s.rr_part, n_part);
 }
 
 // One iteration, five launches: y = Mhat p (the second hemi-Dslash leaves

@@ -290,8 +290,13 @@ class Context:
         return msg.split(": ", 1)[-1].split(", ")
 
     def set_cg_graph(self, on):
-        """Replay CG iterations from a captured CUDA graph (default on)."""
+        """Run each CG solve as one captured CUDA graph (default on)."""
         self._check(lib().hmc_ctx_set_option(self.h, 2, int(bool(on))), "hmc_ctx_set_option")
+
+    def set_pdl(self, on):
+        """Programmatic dependent launch of the hemi-Dslash and CG-update
+        kernels (default on)."""
+        self._check(lib().hmc_ctx_set_option(self.h, 4, int(bool(on))), "hmc_ctx_set_option")
 
     def set_timing(self, enable):
         """Per-launch timing: 0 off, 1 event-timed Dslash classes, 2 timeline of
