@@ -170,27 +170,37 @@ def run_kernel(args):
         Ul = ctx.pack_gauge(LAT, Ulat, inner, hmc.LINK12) if inner != hmc.F64 else None
         b = ctx.pack_spinor(LAT, I.gaussian_half(LAT, 2, n_rhs=n), hmc.F64)
         x = ctx.new_spinor(LAT, hmc.F64, n)
-        ctx.cg_solve_multi(LAT, Uh, x, b, ks, 1e-10, U_lo=Ul, inner_prec=inner,
-                           reliable_delta=args.delta)
+        kw = dict(U_lo=Ul, inner_prec=inner, reliable_delta=args.delta, f64_emul=args.f64_emul)
+        ctx.cg_solve_multi(LAT, Uh, x, b, ks, 1e-10, **kw)
         torch.cuda.synchronize()
+        # solve time as run in production (graph, timing off), then per-class
+        # kernel times (timing on, direct launches)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        ctx.cg_solve_multi(LAT, Uh, x, b, ks, 1e-10, **kw)
+        t1.record()
+        torch.cuda.synchronize()
+        untimed = round(t0.elapsed_time(t1), 3)
         ctx.set_timing(True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        r = ctx.cg_solve_multi(LAT, Uh, x, b, ks, 1e-10, U_lo=Ul, inner_prec=inner,
-                               reliable_delta=args.delta)
+        r = ctx.cg_solve_multi(LAT, Uh, x, b, ks, 1e-10, **kw)
         e1.record()
         torch.cuda.synchronize()
         st = ctx.timing()
         ms = e0.elapsed_time(e1)
         print(json.dumps({"kernel": args.kernel, "solve_ms": round(ms, 3),
-                          "ms_per_rhs": round(ms / n, 3), **r,
+                          "ms_per_rhs": round(ms / n, 3), "solve_ms_untimed": untimed,
+                          "ms_per_rhs_untimed": round(untimed / n, 3),
+                          "f64_emul": args.f64_emul, **r,
                           "classes": {k: {"launches": v[0], "us": round(v[1] / v[0] * 1e3, 2),
                                           "GBs": round(v[2] / (v[1] * 1e-3) / 1e9, 1)}
                                       for k, v in st.items()}}), flush=True)
         return
     if pname == "cg":
         # one CG solve of Mhat^dag Mhat on the benchmark lattice to 1e-10 with the
-        # given inner precision (FP64 reliable updates), all Dslash classes timed
+        # given inner precision (reliable updates in emulated or native FP64,
+        # --f64-emul), all Dslash classes timed
         inner = {"f64": hmc.F64, "f32": hmc.F32, "f16": hmc.F16, "bf16": hmc.BF16}[fmt]
         Ulat = I.gauge_links(LAT, EPS_LINKS, 1)
         Uh = ctx.pack_gauge(LAT, Ulat, hmc.F64, hmc.LINK18)
@@ -198,7 +208,7 @@ def run_kernel(args):
         b = ctx.pack_spinor(LAT, I.gaussian_half(LAT, 2), hmc.F64)
         x = ctx.new_spinor(LAT, hmc.F64)
         ctx.cg_solve(LAT, Uh, x, b, WORK["kappa"], 1e-10, U_lo=Ul, inner_prec=inner,
-                     reliable_delta=args.delta)
+                     reliable_delta=args.delta, f64_emul=args.f64_emul)
         torch.cuda.synchronize()
         # solve time with and without the CUDA-graph replay of the iterations
         # (kernel timing off), then per-class kernel times (timing on)
@@ -208,7 +218,7 @@ def run_kernel(args):
             t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             t0.record()
             ctx.cg_solve(LAT, Uh, x, b, WORK["kappa"], 1e-10, U_lo=Ul, inner_prec=inner,
-                         reliable_delta=args.delta)
+                         reliable_delta=args.delta, f64_emul=args.f64_emul)
             t1.record()
             torch.cuda.synchronize()
             graph_ms["graph" if graph else "direct"] = round(t0.elapsed_time(t1), 3)
@@ -217,12 +227,12 @@ def run_kernel(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         r = ctx.cg_solve(LAT, Uh, x, b, WORK["kappa"], 1e-10, U_lo=Ul, inner_prec=inner,
-                         reliable_delta=args.delta)
+                         reliable_delta=args.delta, f64_emul=args.f64_emul)
         e1.record()
         torch.cuda.synchronize()
         st = ctx.timing()
         print(json.dumps({"kernel": args.kernel, "solve_ms": round(e0.elapsed_time(e1), 3),
-                          "solve_ms_untimed": graph_ms, **r,
+                          "solve_ms_untimed": graph_ms, "f64_emul": args.f64_emul, **r,
                           "classes": {k: {"launches": v[0], "us": round(v[1] / v[0] * 1e3, 2),
                                           "GBs": round(v[2] / (v[1] * 1e-3) / 1e9, 1)}
                                       for k, v in st.items()}}), flush=True)
