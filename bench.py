@@ -134,6 +134,9 @@ def parse():
     ap.add_argument("--variant", type=int, default=None,
                     help="hemi-Dslash kernel variant 0..3, -1 built-in default, -2 autotuned "
                          "(the trajectory benchmark autotunes by default)")
+    ap.add_argument("--batch", type=int, default=2, choices=[0, 1, 2],
+                    help="batched solves: 0 one solve per system, 1 lock step, 2 lock step "
+                         "only for equal kappas (library default)")
     ap.add_argument("--no-pdl", action="store_true",
                     help="launch the hemi-Dslash and CG-update kernels without programmatic "
                          "dependent launch")
@@ -159,6 +162,7 @@ def run_kernel(args):
         ctx.set_cg_graph(0)
     if args.no_pdl:
         ctx.set_pdl(0)
+    ctx.set_batch(args.batch)
     if pname == "cgm":
         # batched solve of n systems (kappas of mass-preconditioned
         # pseudo-fermions) on the benchmark lattice, links shared per launch
@@ -192,7 +196,7 @@ def run_kernel(args):
         print(json.dumps({"kernel": args.kernel, "solve_ms": round(ms, 3),
                           "ms_per_rhs": round(ms / n, 3), "solve_ms_untimed": untimed,
                           "ms_per_rhs_untimed": round(untimed / n, 3),
-                          "f64_emul": args.f64_emul, **r,
+                          "f64_emul": args.f64_emul, "batch": args.batch, **r,
                           "classes": {k: {"launches": v[0], "us": round(v[1] / v[0] * 1e3, 2),
                                           "GBs": round(v[2] / (v[1] * 1e-3) / 1e9, 1)}
                                       for k, v in st.items()}}), flush=True)
@@ -405,6 +409,7 @@ def run_hmc(args):
         ctx.set_cg_graph(0)  # every kernel a direct launch (e.g. for an ncu launch list)
     if args.no_pdl:
         ctx.set_pdl(0)
+    ctx.set_batch(args.batch)
     # measured CUDA-core FMA ceilings (the arithmetic rooflines)
     fma = {k: round(ctx.fma_peak(i), 2) for i, k in enumerate(("fp64", "fp32", "fp32x2"))}
     # autotuned hemi-Dslash variants (tuned during the warm-up steps)
@@ -574,7 +579,9 @@ def run_hmc(args):
               ",".join(str(m) for m in C5_LEVEL_STEPS) + f",{work['n_md']}")
     elif args.mp:
         wl = (f"hmc-trajectory {lat_name()} kappa={work['kappa']} beta=5.6 "
-              "mass-preconditioned kappa'=0.150,0.154 (batched solves)")
+              "mass-preconditioned kappa'=0.150,0.154 (" +
+              {0: "one solve per term", 1: "solves of the terms in lock step",
+               2: "one solve per term: kappas differ"}[args.batch] + ")")
     elif args.rooted:
         wl = (f"hmc-trajectory {lat_name()} kappa={work['kappa']} beta=5.6 kappa^4 "
               f"rooted polynomials N={args.rooted} (degrees 16, 42)")
@@ -596,6 +603,8 @@ def run_hmc(args):
                    "solver": args.solver,
                    "dslash_variant": "autotuned" if args.variant is None else args.variant,
                    "pdl": not args.no_pdl,
+                   "batch": {0: "one solve per system", 1: "lock step",
+                             2: "lock step for equal kappas only"}[args.batch],
                    "cg_graph": "direct launches" if args.no_graph else
                    "one CUDA graph per solve (one solve in eight direct and event-timed)",
                    "links": "12-real (inner), 18-real FP64",

@@ -189,6 +189,16 @@ int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
  * gap between dependent launches closes; results are bit-identical.  0
  * launches them normally. */
 #define HMC_OPT_PDL 4
+/* HMC_OPT_BATCH: how hmc_cg_solve_multi (and the batched solves of the
+ * mass-preconditioned terms) run n_rhs > 1 systems: 1 in lock step (each
+ * hemi-Dslash launch for all right-hand sides, links loaded once), 0 one
+ * after another with the single-system solver, 2 (default) in lock step
+ * when all kappas are equal and one after another otherwise.  Measured on
+ * 24^3 x 48 with the kappas of a mass-preconditioning chain (0.150, 0.154,
+ * 0.1575): the lock-step solve runs to the slowest system's convergence and
+ * restarts every system at each reliable update one of them needs, which
+ * costs more than the shared link loads save. */
+#define HMC_OPT_BATCH 5
 /* HMC_OPT_WORKSPACE_GUARD: 1 frees the context's workspace and gives every
  * buffer allocated afterwards a 4 KiB guard region of the byte 0xA5 after its
  * end; hmc_workspace_check then reports any buffer whose guard was written (a
@@ -196,7 +206,8 @@ int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
  * is not used).  0 (default): no guards. */
 #define HMC_OPT_WORKSPACE_GUARD 3
 /* Sets option (HMC_OPT_DSLASH_VARIANT: -2..8, HMC_OPT_CG_GRAPH: 0 or 1,
- * HMC_OPT_WORKSPACE_GUARD: 0 or 1, HMC_OPT_PDL: 0 or 1) for
+ * HMC_OPT_WORKSPACE_GUARD: 0 or 1, HMC_OPT_PDL: 0 or 1, HMC_OPT_BATCH:
+ * 0..2) for
  * every later call on ctx.  HMC_EINVAL for an unknown option or value. */
 int hmc_ctx_set_option(hmc_ctx *ctx, int option, int value);
 /* hmc_workspace_check: synchronises the context's streams and checks the
@@ -373,15 +384,17 @@ int hmc_cg_solve(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
                  hmc_solve_stats *stats);
 
 /* hmc_cg_solve_multi: n_rhs (1..16) systems Mhat_r^dag Mhat_r x_r = phi_r
- * with per-system kappas[r] (host array), solved together: every hemi-Dslash
- * launch serves all right-hand sides and loads each link once (the
+ * with per-system kappas[r] (host array).  In lock step (HMC_OPT_BATCH 1, or
+ * 2 with equal kappas) they are solved together: every hemi-Dslash launch
+ * serves all right-hand sides and loads each link once (the
  * mass-preconditioned pseudo-fermions the paper motivates in Sec. I share the
- * links but not kappa).  x and phi are F64 even fields with n_rhs right-hand
- * sides (layout above); U_hi/U_lo and opts as for hmc_cg_solve.  Each system
- * stops on its own FP64 true residual; converged systems are frozen while the
- * others iterate, and in mixed precision a reliable update is applied to all
- * systems when any of them needs one.  stats (nullable) is an array of n_rhs
- * entries.  Blocks. */
+ * links but not kappa); each system stops on its own FP64 true residual,
+ * converged systems are frozen while the others iterate, and in mixed
+ * precision a reliable update is applied to all systems when any of them
+ * needs one.  Otherwise the systems are solved one after another by the
+ * single-system solver.  x and phi are F64 even fields with n_rhs right-hand
+ * sides (layout above); U_hi/U_lo and opts as for hmc_cg_solve.  stats
+ * (nullable) is an array of n_rhs entries.  Blocks. */
 int hmc_cg_solve_multi(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
                        const hmc_gauge *U_lo, void *x, const void *phi,
                        const double *kappas, int n_rhs, double tol, int max_iter,

@@ -350,6 +350,10 @@ int hmc_ctx_set_option(hmc_ctx *ctx, int option, int value) {
       if (value != 0 && value != 1) return fail(ctx, HMC_EINVAL, "cg graph option must be 0 or 1");
       ctx->cg_graph = value;
       return HMC_OK;
+    case HMC_OPT_BATCH:
+      if (value < 0 || value > 2) return fail(ctx, HMC_EINVAL, "batch option must be 0, 1 or 2");
+      ctx->batch = value;
+      return HMC_OK;
     case HMC_OPT_PDL:
       if (value != 0 && value != 1) return fail(ctx, HMC_EINVAL, "pdl option must be 0 or 1");
       ctx->pdl = value;

@@ -42,6 +42,10 @@ struct hmc_ctx {
   // hemi-Dslash and CG-update kernels as programmatic dependent launches
   // (HMC_OPT_PDL)
   int pdl = 1;
+  // systems of a batched solve (hmc_cg_solve_multi and the mass-preconditioned
+  // terms): 0 one solve per system, 1 in lock step, 2 (default) in lock step
+  // when all kappas are equal, else one solve per system (HMC_OPT_BATCH)
+  int batch = 2;
   // autotuned hemi-Dslash variant per launch class (ds_variant == -2);
   // tune_frozen: use tuned classes, never tune (untuned: built-in default)
   std::map<std::string, int> ds_tuned;
@@ -318,6 +322,8 @@ int hi_poly_K(const HiOps &h, void *out, const void *in, const double *c, int n,
 
 // batched CG of n_rhs systems with per-system kappas (host array); stats:
 // array of n_rhs (nullable)
+// F64 field <-> right-hand side r of an n-RHS F64 field (to_multi: into it)
+int rhs_copy(hmc_ctx *ctx, const Geo &g, const void *src, void *dst, int n, int r, bool to_multi);
 int cg_solve_multi(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul, void *x,
                    const void *b, const double *kappas, int n_rhs, double tol, int max_iter,
                    const hmc_solver_opts *opts, hmc_solve_stats *stats);

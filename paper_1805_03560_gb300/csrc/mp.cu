@@ -22,8 +22,6 @@
 
 namespace hmc {
 
-namespace {
-
 #define TRY(e)         \
   do {                 \
     int _s = (e);      \
@@ -49,6 +47,8 @@ int rhs_copy(hmc_ctx *ctx, const Geo &g, const void *src, void *dst, int n, int 
       (const double2 *)src, (double2 *)dst, g.Vh, n, r, to_multi ? 1 : 0);
   return launched(ctx, to_multi ? "rhs_gather" : "rhs_scatter");
 }
+
+namespace {
 
 void *ws_j(hmc_ctx *ctx, const char *base, int j, size_t bytes) {
   char name[64];

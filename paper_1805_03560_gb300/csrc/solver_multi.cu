@@ -492,6 +492,30 @@ LoopParts m_parts(MSolve &s) {
   return L;
 }
 
+// the systems one after another with the single-system solver, gathered
+// from and scattered into the n-RHS layout
+int solve_separately(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
+                     void *x, const void *b, const double *kappas, int n, double tol,
+                     int max_iter, const hmc_solver_opts *opts, hmc_solve_stats *stats) {
+  const size_t f1 = spinor_bytes(g, HMC_F64, 1);
+  void *bq = workspace(ctx, "cgs_b", f1), *xq = workspace(ctx, "cgs_x", f1);
+  if (!bq || !xq) return HMC_ENOMEM;
+  int worst = 0;
+  for (int q = 0; q < n; ++q) {
+    TRY(rhs_copy(ctx, g, b, bq, n, q, false));
+    hmc_solve_stats st{};
+    const int r = cg_solve(ctx, g, Uh, Ul, xq, bq, kappas[q], tol, max_iter, opts, &st);
+    if (r && r != HMC_ENOCONV) return r;
+    if (r) worst = q + 1;
+    if (stats) stats[q] = st;
+    TRY(rhs_copy(ctx, g, xq, x, n, q, true));
+  }
+  if (worst)
+    return fail(ctx, HMC_ENOCONV, "cg_multi: system %d (one solve per system) not converged",
+                worst - 1);
+  return HMC_OK;
+}
+
 }  // namespace
 
 int cg_solve_multi(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul, void *x,
@@ -499,6 +523,10 @@ int cg_solve_multi(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_ga
                    const hmc_solver_opts *opts, hmc_solve_stats *stats) {
   if (n_rhs < 1 || n_rhs > NR_MAX)
     return fail(ctx, HMC_EINVAL, "cg_multi: n_rhs must be 1..%d", NR_MAX);
+  bool equal = true;
+  for (int q = 1; q < n_rhs; ++q) equal = equal && kappas[q] == kappas[0];
+  if (n_rhs > 1 && (ctx->batch == 0 || (ctx->batch == 2 && !equal)))
+    return solve_separately(ctx, g, Uh, Ul, x, b, kappas, n_rhs, tol, max_iter, opts, stats);
   MSolve s{};
   s.ctx = ctx;
   s.g = g;

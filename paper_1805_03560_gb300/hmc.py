@@ -293,6 +293,11 @@ class Context:
         """Run each CG solve as one captured CUDA graph (default on)."""
         self._check(lib().hmc_ctx_set_option(self.h, 2, int(bool(on))), "hmc_ctx_set_option")
 
+    def set_batch(self, mode):
+        """Batched solves (hmc_cg_solve_multi, mass-preconditioned terms): 0 one
+        solve per system, 1 lock step, 2 lock step only for equal kappas (default)."""
+        self._check(lib().hmc_ctx_set_option(self.h, 5, int(mode)), "hmc_ctx_set_option")
+
     def set_pdl(self, on):
         """Programmatic dependent launch of the hemi-Dslash and CG-update
         kernels (default on)."""

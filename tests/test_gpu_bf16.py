@@ -54,9 +54,11 @@ def test_cg_multi_bf16_inner(orc, ctx, H):
     phi = I.gaussian_half(L, 9, n_rhs=4)
     tol = 1e-10
     x = ctx.new_spinor(L, 0, 4)
+    ctx.set_batch(1)  # the lock-step solver in BF16 storage
     r = ctx.cg_solve_multi(L, ctx.pack_gauge(L, U, 0, 18), x, ctx.pack_spinor(L, phi, 0), kappas,
                            tol, U_lo=ctx.pack_gauge(L, U, BF16, 12), inner_prec=BF16,
                            reliable_delta=1e-2)
+    ctx.set_batch(2)
     assert r["status"] == 0, r
     xs = _np(ctx.unpack_spinor(L, x))
     for q, k in enumerate(kappas):

@@ -160,8 +160,10 @@ def test_random_fields_link_update_trajectory(ctx, H, L):
     assert cU.intact() and cUe.intact() and cPe.intact()
 
 
+@pytest.mark.parametrize("batch", [1, 0])
 @pytest.mark.parametrize("L", LATTICES)
-def test_batched_cg_and_ratio_terms(ctx, H, L):
+def test_batched_cg_and_ratio_terms(ctx, H, L, batch):
+    ctx.set_batch(batch)
     U = I.gauge_links(L, 0.3, 1)
     Uh = ctx.pack_gauge(L, U, H.F64, 18)
     Ul = ctx.pack_gauge(L, U, H.F32, 12)
@@ -173,5 +175,6 @@ def test_batched_cg_and_ratio_terms(ctx, H, L):
     cF, F = _algebra(ctx, H, L)
     ctx.force_mp(L, Uh, phis, [0.0, 0.12, 0.13], [0.12, 0.13, 0.14], F, tol=1e-10, U_lo=Ul,
                  inner_prec=H.F32, reliable_delta=1e-3)
+    ctx.set_batch(2)
     ctx.torch.cuda.synchronize()
     assert cx.intact() and cF.intact()

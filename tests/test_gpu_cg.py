@@ -112,11 +112,14 @@ def test_cg_throughput_lattice(orc, ctx, H, inner):
     assert np.linalg.norm(r) / np.linalg.norm(phi) <= 1.01e-10
 
 
+@pytest.mark.parametrize("batch", [1, 0])
 @pytest.mark.parametrize("inner", [0, 1, 2])
-def test_cg_multi_rhs_per_kappa(orc, ctx, H, inner):
+def test_cg_multi_rhs_per_kappa(orc, ctx, H, inner, batch):
     """Three systems with the kappas of the mass-preconditioned pseudo-fermions
-    solved together: each matches the oracle's solve with its own kappa and
-    meets the tolerance on its FP64 true residual."""
+    solved together (in lock step, and one after another): each matches the
+    oracle's solve with its own kappa and meets the tolerance on its FP64
+    true residual."""
+    ctx.set_batch(batch)
     L = (4, 6, 6, 10)
     kappas = [0.150, 0.154, 0.1575]
     U = I.gauge_links(L, 0.3, 1)
@@ -127,7 +130,10 @@ def test_cg_multi_rhs_per_kappa(orc, ctx, H, inner):
     b = ctx.pack_spinor(L, phi, 0)
     x = ctx.new_spinor(L, 0, 3)
     res = ctx.cg_solve_multi(L, Uh, x, b, kappas, tol, U_lo=Ul, inner_prec=inner)
+    ctx.set_batch(2)
     assert res["status"] == 0, res
+    if batch == 1:
+        assert len(set(res["iterations"])) == 1  # lock step: one count for all
     xs = _np(ctx.unpack_spinor(L, x))
     for r, k in enumerate(kappas):
         assert res["true_rel_res"][r] <= tol
@@ -273,6 +279,7 @@ def test_cg_multi_graph_bits_and_syncs(ctx, H, inner, n_rhs):
     Uh = ctx.pack_gauge(L, U, 0, 18)
     Ul = ctx.pack_gauge(L, U, inner, 12) if inner else None
     b = ctx.pack_spinor(L, phi, 0)
+    ctx.set_batch(1)
     got = {}
     for graph in (1, 0):
         ctx.set_cg_graph(graph)
@@ -282,6 +289,7 @@ def test_cg_multi_graph_bits_and_syncs(ctx, H, inner, n_rhs):
         r = ctx.cg_solve_multi(L, Uh, x, b, kappas, 1e-11, U_lo=Ul, inner_prec=inner)
         got[graph] = (_np(ctx.unpack_spinor(L, x)), r, ctx.host_syncs() - y0)
     ctx.set_cg_graph(1)
+    ctx.set_batch(2)
     (xg, rg, yg), (xd, rd, yd) = got[1], got[0]
     assert rg["status"] == 0 and max(rg["true_rel_res"]) <= 1e-11
     assert np.array_equal(xg, xd)
@@ -298,6 +306,7 @@ def test_cg_multi_iteration_limit_on_device(ctx, H):
     Uh = ctx.pack_gauge(L, U, 0, 18)
     Ul = ctx.pack_gauge(L, U, H.F32, 12)
     b = ctx.pack_spinor(L, phi, 0)
+    ctx.set_batch(1)
     out = []
     for graph in (1, 0):
         ctx.set_cg_graph(graph)
@@ -306,6 +315,7 @@ def test_cg_multi_iteration_limit_on_device(ctx, H):
                                inner_prec=H.F32)
         out.append((_np(ctx.unpack_spinor(L, x)), r))
     ctx.set_cg_graph(1)
+    ctx.set_batch(2)
     for x, r in out:
         assert r["status"] == H.ENOCONV and r["iterations"] == [9, 9, 9], r
     assert np.array_equal(out[0][0], out[1][0])
@@ -324,6 +334,7 @@ def test_programmatic_dependent_launch_bit_identical(ctx, H, graph):
     Uh = ctx.pack_gauge(L, U, 0, 18)
     Ul = ctx.pack_gauge(L, U, H.F32, 12)
     ctx.set_cg_graph(graph)
+    ctx.set_batch(1)
     out = []
     for pdl in (1, 0):
         ctx.set_pdl(pdl)
@@ -337,6 +348,7 @@ def test_programmatic_dependent_launch_bit_identical(ctx, H, graph):
                     r3["iterations"]))
     ctx.set_pdl(1)
     ctx.set_cg_graph(1)
+    ctx.set_batch(2)
     (a, ia, b, ib), (c, ic, d, idd) = out
     assert np.array_equal(a, c) and ia == ic
     assert np.array_equal(b, d) and ib == idd

@@ -37,7 +37,9 @@ def H():
 
 @pytest.fixture(scope="module")
 def ctx(H):
-    return H.Context(0)
+    c = H.Context(0)
+    c.set_batch(1)  # the lock-step solver: its multi-RHS kernels are what this module tests
+    return c
 
 
 @pytest.fixture(scope="module")

@@ -60,13 +60,18 @@ def test_cg_nan_source(ctx, H, U, inner):
     _usable(ctx, H, U)
 
 
-def test_cg_multi_nan_source(ctx, H, U):
+@pytest.mark.parametrize("batch", [1, 0])
+def test_cg_multi_nan_source(ctx, H, U, batch):
     Uh = ctx.pack_gauge(L, U, 0, 18)
     Ul = ctx.pack_gauge(L, U, 1, 12)
     x = ctx.new_spinor(L, 0, 3)
-    with pytest.raises(H.HmcError) as e:
-        ctx.cg_solve_multi(L, Uh, x, ctx.pack_spinor(L, _nan_source(3), 0), [0.15, 0.154, 0.156],
-                           1e-10, U_lo=Ul, inner_prec=1)
+    ctx.set_batch(batch)
+    try:
+        with pytest.raises(H.HmcError) as e:
+            ctx.cg_solve_multi(L, Uh, x, ctx.pack_spinor(L, _nan_source(3), 0),
+                               [0.15, 0.154, 0.156], 1e-10, U_lo=Ul, inner_prec=1)
+    finally:
+        ctx.set_batch(2)
     assert e.value.status == H.ENAN
     _usable(ctx, H, U)
 
