@@ -134,9 +134,9 @@ def parse():
     ap.add_argument("--variant", type=int, default=None,
                     help="hemi-Dslash kernel variant 0..3, -1 built-in default, -2 autotuned "
                          "(the trajectory benchmark autotunes by default)")
-    ap.add_argument("--batch", type=int, default=2, choices=[0, 1, 2],
-                    help="batched solves: 0 one solve per system, 1 lock step, 2 lock step "
-                         "only for equal kappas (library default)")
+    ap.add_argument("--batch", type=int, default=0, choices=[0, 1, 2],
+                    help="batched solves: 0 one solve per system (library default), 1 lock "
+                         "step, 2 lock step only for equal kappas")
     ap.add_argument("--no-pdl", action="store_true",
                     help="launch the hemi-Dslash and CG-update kernels without programmatic "
                          "dependent launch")
@@ -168,7 +168,8 @@ def run_kernel(args):
         # pseudo-fermions) on the benchmark lattice, links shared per launch
         inner = {"f64": hmc.F64, "f32": hmc.F32, "f16": hmc.F16, "bf16": hmc.BF16}[fmt]
         n = int(parts[2])
-        ks = ([0.150, 0.154, 0.1575] * 6)[:n]
+        # the kappas of a mass-preconditioning chain, or all equal to --kappa
+        ks = [args.kappa] * n if args.kappa else ([0.150, 0.154, 0.1575] * 6)[:n]
         Ulat = I.gauge_links(LAT, EPS_LINKS, 1)
         Uh = ctx.pack_gauge(LAT, Ulat, hmc.F64, hmc.LINK18)
         Ul = ctx.pack_gauge(LAT, Ulat, inner, hmc.LINK12) if inner != hmc.F64 else None

@@ -191,13 +191,16 @@ int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
 #define HMC_OPT_PDL 4
 /* HMC_OPT_BATCH: how hmc_cg_solve_multi (and the batched solves of the
  * mass-preconditioned terms) run n_rhs > 1 systems: 1 in lock step (each
- * hemi-Dslash launch for all right-hand sides, links loaded once), 0 one
- * after another with the single-system solver, 2 (default) in lock step
+ * hemi-Dslash launch for all right-hand sides, links loaded once), 0
+ * (default) one after another with the single-system solver, 2 in lock step
  * when all kappas are equal and one after another otherwise.  Measured on
- * 24^3 x 48 with the kappas of a mass-preconditioning chain (0.150, 0.154,
- * 0.1575): the lock-step solve runs to the slowest system's convergence and
- * restarts every system at each reliable update one of them needs, which
- * costs more than the shared link loads save. */
+ * 24^3 x 48 (three-system solve 34.9 ms one after another against 45.6 ms in
+ * lock step with the kappas 0.150, 0.154, 0.1575 of a mass-preconditioning
+ * chain; 31.0 against 31.3 ms for three and 126 against 135 ms for twelve
+ * systems at one kappa): the lock-step solve runs to the slowest system's
+ * convergence and restarts every system at each reliable update one of them
+ * needs, and its multi-right-hand-side kernel is instruction-bound, so the
+ * shared link loads do not pay. */
 #define HMC_OPT_BATCH 5
 /* HMC_OPT_WORKSPACE_GUARD: 1 frees the context's workspace and gives every
  * buffer allocated afterwards a 4 KiB guard region of the byte 0xA5 after its
@@ -391,8 +394,8 @@ int hmc_cg_solve(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
  * links but not kappa); each system stops on its own FP64 true residual,
  * converged systems are frozen while the others iterate, and in mixed
  * precision a reliable update is applied to all systems when any of them
- * needs one.  Otherwise the systems are solved one after another by the
- * single-system solver.  x and phi are F64 even fields with n_rhs right-hand
+ * needs one.  Otherwise (the default) the systems are solved one after
+ * another by the single-system solver.  x and phi are F64 even fields with n_rhs right-hand
  * sides (layout above); U_hi/U_lo and opts as for hmc_cg_solve.  stats
  * (nullable) is an array of n_rhs entries.  Blocks. */
 int hmc_cg_solve_multi(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,

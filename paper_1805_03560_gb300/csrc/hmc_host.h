@@ -43,9 +43,9 @@ struct hmc_ctx {
   // (HMC_OPT_PDL)
   int pdl = 1;
   // systems of a batched solve (hmc_cg_solve_multi and the mass-preconditioned
-  // terms): 0 one solve per system, 1 in lock step, 2 (default) in lock step
+  // terms): 0 (default) one solve per system, 1 in lock step, 2 in lock step
   // when all kappas are equal, else one solve per system (HMC_OPT_BATCH)
-  int batch = 2;
+  int batch = 0;
   // autotuned hemi-Dslash variant per launch class (ds_variant == -2);
   // tune_frozen: use tuned classes, never tune (untuned: built-in default)
   std::map<std::string, int> ds_tuned;

@@ -295,7 +295,7 @@ class Context:
 
     def set_batch(self, mode):
         """Batched solves (hmc_cg_solve_multi, mass-preconditioned terms): 0 one
-        solve per system, 1 lock step, 2 lock step only for equal kappas (default)."""
+        solve per system (default), 1 lock step, 2 lock step only for equal kappas."""
         self._check(lib().hmc_ctx_set_option(self.h, 5, int(mode)), "hmc_ctx_set_option")
 
     def set_pdl(self, on):

@@ -58,7 +58,7 @@ def test_cg_multi_bf16_inner(orc, ctx, H):
     r = ctx.cg_solve_multi(L, ctx.pack_gauge(L, U, 0, 18), x, ctx.pack_spinor(L, phi, 0), kappas,
                            tol, U_lo=ctx.pack_gauge(L, U, BF16, 12), inner_prec=BF16,
                            reliable_delta=1e-2)
-    ctx.set_batch(2)
+    ctx.set_batch(0)
     assert r["status"] == 0, r
     xs = _np(ctx.unpack_spinor(L, x))
     for q, k in enumerate(kappas):

@@ -175,6 +175,6 @@ def test_batched_cg_and_ratio_terms(ctx, H, L, batch):
     cF, F = _algebra(ctx, H, L)
     ctx.force_mp(L, Uh, phis, [0.0, 0.12, 0.13], [0.12, 0.13, 0.14], F, tol=1e-10, U_lo=Ul,
                  inner_prec=H.F32, reliable_delta=1e-3)
-    ctx.set_batch(2)
+    ctx.set_batch(0)
     ctx.torch.cuda.synchronize()
     assert cx.intact() and cF.intact()

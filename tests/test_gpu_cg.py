@@ -130,7 +130,7 @@ def test_cg_multi_rhs_per_kappa(orc, ctx, H, inner, batch):
     b = ctx.pack_spinor(L, phi, 0)
     x = ctx.new_spinor(L, 0, 3)
     res = ctx.cg_solve_multi(L, Uh, x, b, kappas, tol, U_lo=Ul, inner_prec=inner)
-    ctx.set_batch(2)
+    ctx.set_batch(0)
     assert res["status"] == 0, res
     if batch == 1:
         assert len(set(res["iterations"])) == 1  # lock step: one count for all
@@ -289,7 +289,7 @@ def test_cg_multi_graph_bits_and_syncs(ctx, H, inner, n_rhs):
         r = ctx.cg_solve_multi(L, Uh, x, b, kappas, 1e-11, U_lo=Ul, inner_prec=inner)
         got[graph] = (_np(ctx.unpack_spinor(L, x)), r, ctx.host_syncs() - y0)
     ctx.set_cg_graph(1)
-    ctx.set_batch(2)
+    ctx.set_batch(0)
     (xg, rg, yg), (xd, rd, yd) = got[1], got[0]
     assert rg["status"] == 0 and max(rg["true_rel_res"]) <= 1e-11
     assert np.array_equal(xg, xd)
@@ -315,7 +315,7 @@ def test_cg_multi_iteration_limit_on_device(ctx, H):
                                inner_prec=H.F32)
         out.append((_np(ctx.unpack_spinor(L, x)), r))
     ctx.set_cg_graph(1)
-    ctx.set_batch(2)
+    ctx.set_batch(0)
     for x, r in out:
         assert r["status"] == H.ENOCONV and r["iterations"] == [9, 9, 9], r
     assert np.array_equal(out[0][0], out[1][0])
@@ -348,7 +348,7 @@ def test_programmatic_dependent_launch_bit_identical(ctx, H, graph):
                     r3["iterations"]))
     ctx.set_pdl(1)
     ctx.set_cg_graph(1)
-    ctx.set_batch(2)
+    ctx.set_batch(0)
     (a, ia, b, ib), (c, ic, d, idd) = out
     assert np.array_equal(a, c) and ia == ic
     assert np.array_equal(b, d) and ib == idd

@@ -71,7 +71,7 @@ def test_cg_multi_nan_source(ctx, H, U, batch):
             ctx.cg_solve_multi(L, Uh, x, ctx.pack_spinor(L, _nan_source(3), 0),
                                [0.15, 0.154, 0.156], 1e-10, U_lo=Ul, inner_prec=1)
     finally:
-        ctx.set_batch(2)
+        ctx.set_batch(0)
     assert e.value.status == H.ENAN
     _usable(ctx, H, U)
 
