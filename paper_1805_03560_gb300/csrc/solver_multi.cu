@@ -13,6 +13,10 @@
 // single-system solver, the decisions are taken on the device after every
 // pair of iterations (k_mdecide, k_mru_end), and the solve runs as one CUDA
 // graph (capture_loop) or as the same kernels launched directly in batches.
+// By default (HMC_OPT_BATCH 0) cg_solve_multi instead solves the systems one
+// after another with the single-system solver (solve_separately), which
+// measured faster; the lock-step solver runs with HMC_OPT_BATCH 1 (or 2 and
+// equal kappas).
 #include <cmath>
 #include <cstring>
 #include <vector>
