@@ -47,9 +47,11 @@
  *   algebra double [2][4][8][Vh]: ((p*4 + mu)*8 + a)*Vh + h.
  *
  * Memory and streams.  Every field pointer is a caller-owned DEVICE pointer,
- * 256-byte aligned, of the size the *_bytes helpers return (for spinors of
- * every precision: S rounded up to a multiple of 32 elements, then to 256
- * bytes).  The library
+ * 256-byte aligned (cudaMalloc's alignment; the kernels' 16-byte vector
+ * accesses need at least 16, and a pointer off a 16-byte boundary returns
+ * HMC_EINVAL without a launch), of the size the *_bytes helpers return (for
+ * spinors of every precision: S rounded up to a multiple of 32 elements, then
+ * to 256 bytes).  The library
  * never frees or reallocates caller memory; it owns only workspace inside the
  * context, released by hmc_ctx_destroy.  Calls are asynchronous on the
  * context's stream (hmc_ctx_set_stream) unless stated otherwise; calls that
@@ -58,8 +60,8 @@
  *
  * Errors.  Every call returns an hmc_status.  On failure nothing is thrown
  * across the ABI; hmc_last_error(ctx) returns a message.  HMC_EINVAL: bad
- * argument (null pointer, odd or too small extent, unsupported precision or
- * format); HMC_ENOMEM: workspace allocation failed; HMC_ENOCONV: a solver hit
+ * argument (null or misaligned pointer, odd or too small extent, unsupported
+ * precision or format); HMC_ENOMEM: workspace allocation failed; HMC_ENOCONV: a solver hit
  * max_iter (its output holds the last iterate); HMC_ENAN: a reduction saw a
  * NaN or Inf; HMC_ECUDA: a CUDA error (message has the CUDA error string).
  */
@@ -337,8 +339,13 @@ typedef struct {
                             precision with FP64 reliable updates */
   double reliable_delta; /* reliable update when |r| drops below delta times
                             its maximum since the last update (0: 0.1) */
-  int check_every;       /* iterations between host convergence checks
-                            (0: 16); does not change the result */
+  int check_every;       /* direct launches only (HMC_OPT_CG_GRAPH off, or
+                            timing modes 1 and 2): at most this many
+                            iterations between host reads of the solver
+                            state (0: 16).  The convergence and update
+                            decisions are taken on the device either way,
+                            so it does not change the result; a solve run
+                            as one graph reads the state once. */
   int force_prec;        /* forces only: precision of the Dslash
                             applications, filter polynomials and outer
                             products outside the solves (the solves always

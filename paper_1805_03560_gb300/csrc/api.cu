@@ -194,6 +194,19 @@ int check_gauge(hmc_ctx *ctx, const hmc_gauge *U) {
   if (check_prec(ctx, U->prec)) return HMC_EINVAL;
   if (U->fmt != HMC_LINK18 && U->fmt != HMC_LINK12)
     return fail(ctx, HMC_EINVAL, "unsupported link format %d", U->fmt);
+  if ((uintptr_t)U->data & 15)
+    return fail(ctx, HMC_EINVAL, "gauge field %p is not 16-byte aligned", U->data);
+  return HMC_OK;
+}
+
+int check_aligned(hmc_ctx *ctx, const char *fn, std::initializer_list<const void *> ptrs) {
+  int i = 0;
+  for (const void *q : ptrs) {
+    if (q && ((uintptr_t)q & 15))
+      return fail(ctx, HMC_EINVAL, "%s: device pointer argument %d (%p) is not 16-byte aligned",
+                  fn, i, q);
+    ++i;
+  }
   return HMC_OK;
 }
 
@@ -414,6 +427,7 @@ int hmc_pack_gauge(hmc_ctx *ctx, const hmc_lattice *lat, const double *U_canon, 
   CTX_CHECK(ctx);
   TRY(check_lattice(ctx, lat));
   if (!U_canon || !U_dev) return fail(ctx, HMC_EINVAL, "pack_gauge: NULL pointer");
+  TRY(check_aligned(ctx, "pack_gauge", {U_canon, U_dev}));
   return pack_gauge(ctx, make_geo(*lat), U_canon, U_dev, prec, fmt, true);
 }
 
@@ -422,6 +436,7 @@ int hmc_unpack_gauge(hmc_ctx *ctx, const hmc_lattice *lat, const void *U_dev, in
   CTX_CHECK(ctx);
   TRY(check_lattice(ctx, lat));
   if (!U_canon || !U_dev) return fail(ctx, HMC_EINVAL, "unpack_gauge: NULL pointer");
+  TRY(check_aligned(ctx, "unpack_gauge", {U_dev, U_canon}));
   return pack_gauge(ctx, make_geo(*lat), U_canon, (void *)U_dev, prec, fmt, false);
 }
 
@@ -430,6 +445,7 @@ int hmc_pack_spinor(hmc_ctx *ctx, const hmc_lattice *lat, const double *psi_cano
   CTX_CHECK(ctx);
   TRY(check_lattice(ctx, lat));
   if (!psi_canon || !psi_dev || n_rhs < 1) return fail(ctx, HMC_EINVAL, "pack_spinor: bad args");
+  TRY(check_aligned(ctx, "pack_spinor", {psi_canon, psi_dev}));
   return pack_spinor(ctx, make_geo(*lat), psi_canon, psi_dev, prec, n_rhs, true);
 }
 
@@ -439,6 +455,7 @@ int hmc_unpack_spinor(hmc_ctx *ctx, const hmc_lattice *lat, const void *psi_dev,
   TRY(check_lattice(ctx, lat));
   if (!psi_canon || !psi_dev || n_rhs < 1)
     return fail(ctx, HMC_EINVAL, "unpack_spinor: bad args");
+  TRY(check_aligned(ctx, "unpack_spinor", {psi_dev, psi_canon}));
   return pack_spinor(ctx, make_geo(*lat), psi_canon, (void *)psi_dev, prec, n_rhs, false);
 }
 
@@ -446,6 +463,7 @@ int hmc_pack_algebra(hmc_ctx *ctx, const hmc_lattice *lat, const double *A_canon
   CTX_CHECK(ctx);
   TRY(check_lattice(ctx, lat));
   if (!A_canon || !A_dev) return fail(ctx, HMC_EINVAL, "pack_algebra: NULL pointer");
+  TRY(check_aligned(ctx, "pack_algebra", {A_canon, A_dev}));
   return pack_algebra(ctx, make_geo(*lat), A_canon, A_dev, true);
 }
 
@@ -454,6 +472,7 @@ int hmc_unpack_algebra(hmc_ctx *ctx, const hmc_lattice *lat, const double *A_dev
   CTX_CHECK(ctx);
   TRY(check_lattice(ctx, lat));
   if (!A_canon || !A_dev) return fail(ctx, HMC_EINVAL, "unpack_algebra: NULL pointer");
+  TRY(check_aligned(ctx, "unpack_algebra", {A_dev, A_canon}));
   return pack_algebra(ctx, make_geo(*lat), A_canon, (double *)A_dev, false);
 }
 
@@ -466,6 +485,7 @@ int hmc_dslash(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U, void *o
   if (!out || !in || n_rhs < 1 || (out_parity != 0 && out_parity != 1))
     return fail(ctx, HMC_EINVAL, "dslash: bad arguments");
   if (out == in) return fail(ctx, HMC_EINVAL, "dslash: out must not alias in");
+  TRY(check_aligned(ctx, "dslash", {out, in}));
   DslashArgs a{};
   a.g = make_geo(*lat);
   a.p = out_parity;
@@ -485,6 +505,7 @@ int hmc_mhat(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U, void *out
   TRY(check_prec(ctx, prec));
   if (!out || !in || n_rhs < 1) return fail(ctx, HMC_EINVAL, "mhat: bad arguments");
   if (out == in) return fail(ctx, HMC_EINVAL, "mhat: out must not alias in");
+  TRY(check_aligned(ctx, "mhat", {out, in}));
   Geo g = make_geo(*lat);
   void *tmp = workspace(ctx, "mhat_tmp", spinor_bytes(g, prec, n_rhs));
   if (!tmp) return HMC_ENOMEM;
@@ -511,6 +532,7 @@ int hmc_cg_solve(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
   TRY(check_gauge(ctx, U_hi));
   if (!x || !phi || max_iter < 1) return fail(ctx, HMC_EINVAL, "cg: bad arguments");
   if (x == phi) return fail(ctx, HMC_EINVAL, "cg: x must not alias phi");
+  TRY(check_aligned(ctx, "cg", {x, phi}));
   if (opts && opts->inner_prec != HMC_F64) TRY(check_gauge(ctx, U_lo));
   return cg_solve(ctx, make_geo(*lat), *U_hi, U_lo, x, phi, kappa, tol, max_iter, opts, stats);
 }

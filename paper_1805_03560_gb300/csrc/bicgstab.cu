@@ -677,6 +677,7 @@ extern "C" int hmc_bicgstab_solve(hmc_ctx *ctx, const hmc_lattice *lat, const hm
     if (U_lo->prec != HMC_F32) return fail(ctx, HMC_EINVAL, "bicgstab: U_lo must be F32");
   }
   if (!x || !b || x == b || !(tol > 0.0)) return fail(ctx, HMC_EINVAL, "bicgstab: bad arguments");
+  TRY(check_aligned(ctx, "bicgstab", {x, b}));
   hmc_solver_opts o{};
   if (opts) o = *opts;
   const int st = bicgstab_solve(ctx, make_geo(*lat), *U_hi, U_lo, x, b, kappa, dagger ? 1 : 0, tol,

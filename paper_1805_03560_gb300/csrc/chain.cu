@@ -65,6 +65,7 @@ int hmc_chain(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj_para
   TRY(check_lattice(ctx, lat));
   if (!U || !prm || !cp || !results || cp->n_traj < 0)
     return fail(ctx, HMC_EINVAL, "chain: bad arguments");
+  TRY(check_aligned(ctx, "chain", {U}));
   const Geo g = make_geo(*lat);
   const int nf = traj_eta_fields(prm);
   const size_t ab = (size_t)g.Vh * 2 * 4 * 8 * sizeof(double);

@@ -75,6 +75,7 @@ extern "C" int hmc_link_gradient(hmc_ctx *ctx, const hmc_lattice *lat, const dou
   if (s) return s;
   if (!U_canon || !F || !G_canon) return fail(ctx, HMC_EINVAL, "link_gradient: NULL pointer");
   if (G_canon == U_canon) return fail(ctx, HMC_EINVAL, "link_gradient: G aliases U");
+  if ((s = check_aligned(ctx, "link_gradient", {U_canon, F, G_canon}))) return s;
   const Geo g = make_geo(*lat);
   k_link_gradient<<<blocks_for(8LL * g.Vh, 128), 128, 0, ctx->stream>>>(g, U_canon, F, scale,
                                                                         G_canon);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <functional>
+#include <initializer_list>
 #include <map>
 #include <string>
 #include <vector>
@@ -118,6 +119,11 @@ void *workspace(hmc_ctx *ctx, const char *name, size_t bytes);
 int check_lattice(hmc_ctx *ctx, const hmc_lattice *lat);
 int check_prec(hmc_ctx *ctx, int prec);
 int check_gauge(hmc_ctx *ctx, const hmc_gauge *U);
+// Device pointer arguments: the kernels access fields with 16-byte vector
+// loads and stores, so a pointer off that boundary would fault the GPU; it
+// is rejected with HMC_EINVAL instead.  NULL entries are skipped (callers
+// check the mandatory ones).
+int check_aligned(hmc_ctx *ctx, const char *fn, std::initializer_list<const void *> ptrs);
 
 inline int blocks_for(long long n, int nt) { return (int)((n + nt - 1) / nt); }
 

@@ -2,6 +2,8 @@
 // intermediate (H_oe in) in context workspace, which it cudaMallocs on first
 // use.  This entry point keeps that intermediate in one file-scope device
 // array instead, so a call never allocates or frees device memory.
+#include <atomic>
+
 #include "hmc_host.h"
 
 // The scratch of every call on every device: the odd intermediate field.
@@ -11,8 +13,10 @@ static __device__ __align__(256) unsigned char g_mhat_scratch[HMC_MHAT_NOALLOC_M
 namespace {
 constexpr int kMaxDevices = 128;
 // Device address of g_mhat_scratch per device (the name itself is only a
-// host-side stand-in for the symbol, not a device pointer).
-void *g_scratch_addr[kMaxDevices] = {};
+// host-side stand-in for the symbol, not a device pointer).  Atomic: host
+// threads with contexts on one device may make their first call together
+// (both look up the same address).
+std::atomic<void *> g_scratch_addr[kMaxDevices] = {};
 }  // namespace
 
 using namespace hmc;
@@ -27,6 +31,7 @@ extern "C" int hmc_mhat_noalloc(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_
   if ((st = check_prec(ctx, prec))) return st;
   if (!out || !in || n_rhs < 1) return fail(ctx, HMC_EINVAL, "mhat_noalloc: bad arguments");
   if (out == in) return fail(ctx, HMC_EINVAL, "mhat_noalloc: out must not alias in");
+  if ((st = check_aligned(ctx, "mhat_noalloc", {out, in}))) return st;
   const Geo g = make_geo(*lat);
   const size_t need = spinor_bytes(g, prec, n_rhs);
   if (need > HMC_MHAT_NOALLOC_MAX_BYTES)
@@ -37,7 +42,7 @@ extern "C" int hmc_mhat_noalloc(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_
   const int dev = ctx->device;
   if (dev < 0 || dev >= kMaxDevices)
     return fail(ctx, HMC_EINVAL, "mhat_noalloc: device index %d out of range", dev);
-  void *tmp = g_scratch_addr[dev];
+  void *tmp = g_scratch_addr[dev].load(std::memory_order_acquire);
   if (!tmp) {
     // one-time set-up on this device: the symbol's device address, looked up
     // with that device current
@@ -49,7 +54,7 @@ extern "C" int hmc_mhat_noalloc(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_
     if (e != cudaSuccess || !tmp)
       return fail(ctx, HMC_ECUDA, "mhat_noalloc: cudaGetSymbolAddress failed: %s",
                   cudaGetErrorString(e));
-    g_scratch_addr[dev] = tmp;
+    g_scratch_addr[dev].store(tmp, std::memory_order_release);
   }
   // the optional per-launch event timing and the autotuner create CUDA
   // events (and the autotuner synchronises the stream and relaunches), so

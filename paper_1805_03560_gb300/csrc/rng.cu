@@ -152,6 +152,7 @@ int hmc_random_momenta(hmc_ctx *ctx, const hmc_lattice *lat, double *P, uint64_t
   int st = check_lattice(ctx, lat);
   if (st) return st;
   if (!P) return fail(ctx, HMC_EINVAL, "random_momenta: NULL field");
+  if ((st = check_aligned(ctx, "random_momenta", {P}))) return st;
   return random_momenta(ctx, make_geo(*lat), P, seed, counter);
 }
 
@@ -161,6 +162,7 @@ int hmc_random_sources(hmc_ctx *ctx, const hmc_lattice *lat, void *eta, int n_fi
   int st = check_lattice(ctx, lat);
   if (st) return st;
   if (!eta || n_fields < 1) return fail(ctx, HMC_EINVAL, "random_sources: bad arguments");
+  if ((st = check_aligned(ctx, "random_sources", {eta}))) return st;
   return random_sources(ctx, make_geo(*lat), eta, n_fields, seed, counter);
 }
 
@@ -168,6 +170,7 @@ int hmc_random_uniforms(hmc_ctx *ctx, double *u, int n, uint64_t seed, uint64_t 
                         uint64_t counter) {
   if (!ctx) return HMC_EINVAL;
   if (!u || n < 1) return fail(ctx, HMC_EINVAL, "random_uniforms: bad arguments");
+  if (int st = check_aligned(ctx, "random_uniforms", {u})) return st;
   return random_uniforms(ctx, u, n, seed, stream, counter);
 }
 

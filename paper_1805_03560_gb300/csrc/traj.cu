@@ -830,6 +830,7 @@ int hmc_force_pf(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
   TRY(check_lattice(ctx, lat));
   TRY(check_solver_args(ctx, U_hi, U_lo, opts));
   if (!phi || !F) return fail(ctx, HMC_EINVAL, "force_pf: NULL field");
+  TRY(check_aligned(ctx, "force_pf", {phi, F}));
   if (stats) memset(stats, 0, sizeof(*stats));
   return force_pf(ctx, make_geo(*lat), *U_hi, U_lo, phi, kappa, filt, coeff, F, tol, opts, stats);
 }
@@ -842,6 +843,7 @@ int hmc_action_pf(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
   TRY(check_lattice(ctx, lat));
   TRY(check_solver_args(ctx, U_hi, U_lo, opts));
   if (!phi || !action) return fail(ctx, HMC_EINVAL, "action_pf: NULL argument");
+  TRY(check_aligned(ctx, "action_pf", {phi}));
   if (stats) memset(stats, 0, sizeof(*stats));
   return action_pf(ctx, make_geo(*lat), *U_hi, U_lo, phi, kappa, filt, tol, opts, action, stats);
 }
@@ -855,6 +857,7 @@ int hmc_force_fratio(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi
   TRY(check_solver_args(ctx, U_hi, U_lo, opts));
   if (!phi || !F || !filt || !filt->b || filt->n < 0)
     return fail(ctx, HMC_EINVAL, "force_fratio: NULL field or bad filter");
+  TRY(check_aligned(ctx, "force_fratio", {phi, F}));
   if (!(kappa_a >= 0.0)) return fail(ctx, HMC_EINVAL, "force_fratio: kappa_a must be >= 0");
   if (stats) memset(stats, 0, sizeof(*stats));
   return force_fratio(ctx, make_geo(*lat), *U_hi, U_lo, phi, kappa, *filt, kappa_a, coeff, F, tol,
@@ -870,6 +873,7 @@ int hmc_action_fratio(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_h
   TRY(check_solver_args(ctx, U_hi, U_lo, opts));
   if (!phi || !action || !filt || !filt->b || filt->n < 0)
     return fail(ctx, HMC_EINVAL, "action_fratio: NULL argument or bad filter");
+  TRY(check_aligned(ctx, "action_fratio", {phi}));
   if (!(kappa_a >= 0.0)) return fail(ctx, HMC_EINVAL, "action_fratio: kappa_a must be >= 0");
   if (stats) memset(stats, 0, sizeof(*stats));
   return action_fratio(ctx, make_geo(*lat), *U_hi, U_lo, phi, kappa, *filt, kappa_a, tol, opts,
@@ -884,6 +888,7 @@ int hmc_force_hopexp(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U, d
   if (U->prec == HMC_F16) return fail(ctx, HMC_EINVAL, "force_hopexp: U must be F64 or F32");
   if (action && U->prec != HMC_F64)
     return fail(ctx, HMC_EINVAL, "force_hopexp: the action needs F64 links");
+  TRY(check_aligned(ctx, "force_hopexp", {F}));
   Geo g = make_geo(*lat);
   if (F) TRY(gauge_force(ctx, g, *U, beta, kappa, k, coeff, F));
   if (action) TRY(gauge_action(ctx, g, *U, beta, kappa, k, action, nullptr));
@@ -911,6 +916,7 @@ int hmc_poly_apply(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U, voi
   TRY(check_prec(ctx, prec));
   if (!out || !in || !coeffs || degree < 0) return fail(ctx, HMC_EINVAL, "poly_apply: bad args");
   if (out == in) return fail(ctx, HMC_EINVAL, "poly_apply: out must not alias in");
+  TRY(check_aligned(ctx, "poly_apply", {out, in, horner_store}));
   Geo g = make_geo(*lat);
   size_t fb = spinor_bytes(g, prec, 1);
   void *tmp = workspace(ctx, "poly_tmp", fb);
@@ -939,6 +945,7 @@ int hmc_poly_solve(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
   }
   if (!x || !b || !coeffs || degree < 0 || x == b || !(tol > 0.0))
     return fail(ctx, HMC_EINVAL, "poly_solve: bad arguments");
+  TRY(check_aligned(ctx, "poly_solve", {x, b}));
   int it = 0;
   double rel = 0.0;
   const int st = poly_solve(ctx, make_geo(*lat), *U_hi, U_lo, x, b, coeffs, degree, kappa, tol,
@@ -955,6 +962,7 @@ int hmc_update_links(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const double
   CTX_CHECK(ctx);
   TRY(check_lattice(ctx, lat));
   if (!U || !P) return fail(ctx, HMC_EINVAL, "update_links: NULL");
+  TRY(check_aligned(ctx, "update_links", {U, P}));
   return update_links(ctx, make_geo(*lat), U, P, eps);
 }
 
@@ -963,6 +971,7 @@ int hmc_update_momenta(hmc_ctx *ctx, const hmc_lattice *lat, double *P, const do
   CTX_CHECK(ctx);
   TRY(check_lattice(ctx, lat));
   if (!P || !F) return fail(ctx, HMC_EINVAL, "update_momenta: NULL");
+  TRY(check_aligned(ctx, "update_momenta", {P, F}));
   return update_momenta(ctx, make_geo(*lat), P, F, eps);
 }
 
@@ -970,6 +979,7 @@ int hmc_kinetic(hmc_ctx *ctx, const hmc_lattice *lat, const double *P, double *o
   CTX_CHECK(ctx);
   TRY(check_lattice(ctx, lat));
   if (!P || !out) return fail(ctx, HMC_EINVAL, "kinetic: NULL");
+  TRY(check_aligned(ctx, "kinetic", {P}));
   Geo g = make_geo(*lat);
   double *part = partials_buf(ctx, g), *dst = scalars(ctx);
   if (!part || !dst) return HMC_ENOMEM;
@@ -988,6 +998,7 @@ int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj
   CTX_CHECK(ctx);
   TRY(check_lattice(ctx, lat));
   if (!U || !prm || !P0 || !eta || !res) return fail(ctx, HMC_EINVAL, "trajectory: NULL argument");
+  TRY(check_aligned(ctx, "trajectory", {U, P0, eta, U_end, P_end}));
   TRY(check_traj_params(ctx, prm));
   memset(res, 0, sizeof(*res));
   Geo g = make_geo(*lat);
@@ -1112,6 +1123,7 @@ extern "C" int hmc_md_evolve(hmc_ctx *ctx, const hmc_lattice *lat, void *U, doub
   CTX_CHECK(ctx);
   TRY(check_lattice(ctx, lat));
   if (!U || !P || !phi || !prm) return fail(ctx, HMC_EINVAL, "md_evolve: NULL argument");
+  TRY(check_aligned(ctx, "md_evolve", {U, P, phi}));
   TRY(check_traj_params(ctx, prm));
   Geo g = make_geo(*lat);
   const int plo = prm->solver.inner_prec;

@@ -12,14 +12,22 @@ Run file (every key optional except lattice, beta, kappa):
   lattice      [T, X, Y, Z] (even extents)
   beta, kappa
   action       {"filter_k": 0|1|2, "n_t": 9, "n_max": 29}            (Sec. II)
-               or {"mass_preconditioning": [0.150, 0.154]}           (ratio terms)
                or {"rooted": {"N": 2, "degrees": [16, 42], "n_b": 29,
                               "n_t": 15, "filter_k": 2}}              (Sec. II.A)
+               either with {"mass_preconditioning": [0.150, 0.154]}  (heavier
+               kappas of the mass-preconditioned terms, Sec. I), or that alone
   integrator   {"type": "leapfrog"|"omelyan", "lambda": 1/6, "tau": 1.0,
                 "n_md": 10, "n_gauge": 4}                             (Sec. I)
+               with "level_steps": [m_0, ..., m_{J-2}] for J time scales
+               (steps of level i per step of level i+1; n_md on the
+               coarsest) and "term_level": the level of each pseudo-fermion
+               term in the order of its fields
   solver       {"type": "cg"|"bicgstab", "inner": "f32"|"f16"|"f64",
                 "reliable_delta": 1e-5, "tol_md": 1e-10, "tol_action": 1e-12,
-                "f64_emul": 1, "force_prec": "f32"|"f64"}
+                "f64_emul": 1, "force_prec": "f64e"|"f64"|"f32"}
+               (force_prec: precision of the force's operator applications,
+               emulated FP64 by default, the one that meets a force error
+               of 1e-8 relative)
   start        {"checkpoint": path} or {"eps": 0.3, "seed": 1,
                 "relax": {"beta": 5.85, "trajectories": 40, "steps": 20}}
   chain        {"seed": 1, "n_traj": 10, "block": 10, "spike_threshold": 5.0,
@@ -56,18 +64,28 @@ def load_config(cfg):
     act = dict(cfg.get("action", {}))
     if set(act) - ACTION_KEYS:
         raise ValueError(f"unknown action keys {sorted(set(act) - ACTION_KEYS)}")
-    if "mass_preconditioning" in act and ("rooted" in act or act.get("filter_k", 0)):
-        raise ValueError("mass preconditioning is not combined with filtering or roots")
+    if "rooted" in act and act.get("filter_k", 0):
+        raise ValueError("give the filter of a rooted action inside its \"rooted\" entry")
+    if "mass_preconditioning" in act:
+        kmp = [float(v) for v in act["mass_preconditioning"]]
+        if not kmp or any(not (0.0 < a < b) for a, b in zip(kmp, kmp[1:] + [out["kappa"]])):
+            raise ValueError(f"mass_preconditioning {kmp}: need 0 < kappa_1 < ... < kappa")
     out["action"] = act
     integ = {"type": "leapfrog", "lambda": 1.0 / 6.0, "tau": 1.0, "n_md": 10, "n_gauge": 4}
     integ.update(cfg.get("integrator", {}))
     if integ["type"] not in ("leapfrog", "omelyan"):
         raise ValueError(f"integrator {integ['type']}")
+    if "level_steps" in integ and (not 1 <= len(integ["level_steps"]) <= 7
+                                   or any(int(m) < 1 for m in integ["level_steps"])):
+        raise ValueError(f"level_steps {integ['level_steps']}: 1 to 7 entries >= 1")
+    if "term_level" in integ and "level_steps" not in integ:
+        raise ValueError("term_level needs level_steps")
     out["integrator"] = integ
     solver = {"type": "cg", "inner": "f32", "reliable_delta": 1e-5, "tol_md": 1e-10,
-              "tol_action": 1e-12, "f64_emul": 1, "force_prec": "f32"}
+              "tol_action": 1e-12, "f64_emul": 1, "force_prec": "f64e"}
     solver.update(cfg.get("solver", {}))
-    if solver["type"] not in ("cg", "bicgstab") or solver["inner"] not in ("f64", "f32", "f16"):
+    if (solver["type"] not in ("cg", "bicgstab") or solver["inner"] not in ("f64", "f32", "f16")
+            or solver["force_prec"] not in ("f64e", "f64", "f32")):
         raise ValueError(f"solver {solver}")
     out["solver"] = solver
     start = {"eps": 0.3, "seed": 1}
@@ -92,7 +110,7 @@ def traj_kwargs(cfg, hmc):
               n_gauge=integ["n_gauge"], tol_md=sol["tol_md"], tol_action=sol["tol_action"],
               inner_prec=prec[sol["inner"]], link_fmt_lo=hmc.LINK12,
               reliable_delta=sol["reliable_delta"],
-              force_prec=hmc.F32 if sol["force_prec"] == "f32" else hmc.F64,
+              force_prec={"f32": hmc.F32, "f64": hmc.F64, "f64e": hmc.F64E}[sol["force_prec"]],
               f64_emul=int(sol["f64_emul"]),
               integrator=hmc.OMELYAN if integ["type"] == "omelyan" else hmc.LEAPFROG,
               lam=integ["lambda"],
@@ -105,8 +123,6 @@ def traj_kwargs(cfg, hmc):
         _, _, c = hmc.filter_coeffs(k, n_b)
         kw.update(filter_k=k, n_t=int(r.get("n_t", n_b)), n_max=n_b, b=b, c=c, alpha=alpha,
                   root_polys=polys, root_N=int(r["N"]))
-    elif "mass_preconditioning" in act:
-        kw.update(kappa_mp=[float(v) for v in act["mass_preconditioning"]])
     else:
         k = int(act.get("filter_k", 0))
         kw.update(filter_k=k)
@@ -115,6 +131,12 @@ def traj_kwargs(cfg, hmc):
             b, alpha, _ = hmc.filter_coeffs(k, n_max, with_c=False)
             _, _, c = hmc.filter_coeffs(k, n_max)
             kw.update(n_t=int(act.get("n_t", 9)), n_max=n_max, b=b, c=c, alpha=alpha)
+    if "mass_preconditioning" in act:
+        kw.update(kappa_mp=[float(v) for v in act["mass_preconditioning"]])
+    if "level_steps" in integ:
+        kw.update(level_steps=[int(m) for m in integ["level_steps"]])
+        if "term_level" in integ:
+            kw.update(term_level=[int(v) for v in integ["term_level"]])
     return kw
 
 

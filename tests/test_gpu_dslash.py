@@ -195,6 +195,37 @@ def test_bad_arguments_are_rejected(ctx, H):
         ctx.dslash(L, U, ctx.new_spinor(L, 1), ctx.new_spinor(L, 1), 0)  # precision mismatch
 
 
+def test_misaligned_pointers_are_rejected(ctx, H):
+    """The kernels move fields with 16-byte vector accesses; a device pointer
+    off that boundary is rejected on the host with HMC_EINVAL before anything
+    is launched (it would otherwise fault the GPU)."""
+    import ctypes
+    lib = H.lib()
+    L = (4, 4, 4, 4)
+    lat = H.lattice(L)
+    U = ctx.pack_gauge(L, I.unit_links(L), 0, 18)
+    g = U.gauge()
+    a, b = ctx.new_spinor(L, 0), ctx.new_spinor(L, 0)
+    off = ctypes.c_void_p(b.data.data_ptr() + 8)
+    g_off = H.Gauge(U.data.data_ptr() + 8, 0, 18)
+    opts = H.SolverOpts(0, 0.1, 16, 0, 0)
+    ctx._stream()
+    n0 = ctx.launches()
+    calls = [
+        lib.hmc_dslash(ctx.h, ctypes.byref(lat), ctypes.byref(g), a.ptr(), off, 0, 0, 0, 1),
+        lib.hmc_dslash(ctx.h, ctypes.byref(lat), ctypes.byref(g_off), a.ptr(), b.ptr(), 0, 0, 0,
+                       1),
+        lib.hmc_mhat(ctx.h, ctypes.byref(lat), ctypes.byref(g), off, a.ptr(), 0.1, 0, 0, 1, None),
+        lib.hmc_mhat_noalloc(ctx.h, ctypes.byref(lat), ctypes.byref(g), a.ptr(), off, 0.1, 0, 0,
+                             1),
+        lib.hmc_cg_solve(ctx.h, ctypes.byref(lat), ctypes.byref(g), None, off, a.ptr(), 0.1,
+                         1e-8, 10, ctypes.byref(opts), None),
+    ]
+    assert calls == [H.EINVAL] * len(calls)
+    assert b"not 16-byte aligned" in lib.hmc_last_error(ctx.h)
+    assert ctx.launches() == n0
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_dslash_variants_bit_identical(orc, ctx, H, prec):
     """The kernel variants (tiled site mapping, paired loads, and 7, 8: the

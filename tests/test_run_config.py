@@ -32,7 +32,11 @@ def test_defaults_and_round_trip(tmp_path):
 @pytest.mark.parametrize("bad", [
     {"lattice": [8, 4, 4, 3]}, {"lattice": [8, 4, 4]}, {"extra": 1},
     {"integrator": {"type": "rk4"}}, {"solver": {"type": "gmres"}}, {"solver": {"inner": "bf16"}},
-    {"action": {"mass_preconditioning": [0.15], "filter_k": 2}}, {"action": {"roots": 2}},
+    {"solver": {"force_prec": "f16"}},
+    {"action": {"mass_preconditioning": [0.157]}},
+    {"action": {"mass_preconditioning": [0.154, 0.150]}},
+    {"action": {"rooted": {"N": 2, "degrees": [6, 12]}, "filter_k": 2}}, {"action": {"roots": 2}},
+    {"integrator": {"level_steps": [3, 0]}}, {"integrator": {"term_level": [1]}},
     {"chain": {"block": 0}}])
 def test_rejected(bad):
     with pytest.raises(ValueError):
@@ -67,6 +71,25 @@ def test_rooted_and_mp_kwargs(H):
     cfg = run.load_config({**BASE, "action": {"mass_preconditioning": [0.150, 0.154]}})
     kw = run.traj_kwargs(cfg, H)
     assert kw["kappa_mp"] == [0.150, 0.154] and "b" not in kw
+
+
+def test_combined_action_and_levels_kwargs(H):
+    """Mass preconditioning with the kappa^4 filter (and with roots) on a
+    J-level scheme: the paper's Sec. IV.B layout of four time scales."""
+    cfg = run.load_config({**BASE, "action": {"filter_k": 2, "n_t": 15, "n_max": 29,
+                                              "mass_preconditioning": [0.150]},
+                           "integrator": {"type": "omelyan", "n_md": 4,
+                                          "level_steps": [40, 3, 2], "term_level": [2, 3]}})
+    kw = run.traj_kwargs(cfg, H)
+    assert kw["kappa_mp"] == [0.150] and kw["filter_k"] == 2 and kw["n_t"] == 15
+    assert kw["force_prec"] == H.F64E  # the default
+    assert kw["level_steps"] == [40, 3, 2] and kw["term_level"] == [2, 3]
+    b, alpha, _ = C.filter_coeffs(2, 29)
+    assert np.allclose(kw["b"], b, rtol=1e-14, atol=1e-300)
+    cfg = run.load_config({**BASE, "action": {"rooted": {"N": 2, "degrees": [6, 12], "n_b": 20},
+                                              "mass_preconditioning": [0.145, 0.150]}})
+    kw = run.traj_kwargs(cfg, H)
+    assert kw["kappa_mp"] == [0.145, 0.150] and kw["root_N"] == 2 and "level_steps" not in kw
 
 
 class _FakeCtx:
