@@ -306,17 +306,19 @@ int hmc_workspace_check(hmc_ctx *ctx, int *n_bad) {
 
 int hmc_ctx_destroy(hmc_ctx *ctx) {
   CTX_CHECK(ctx);
+  // the graph streams' work reads the workspace: wait for every stream of
+  // the context before anything is freed
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->gstream) cudaStreamSynchronize(ctx->gstream);
+  for (cudaStream_t b : ctx->bstream)
+    if (b) cudaStreamSynchronize(b);
   timing_resolve(ctx);
   if (ctx->trace_prev) cudaEventDestroy(ctx->trace_prev);
   for (cudaEvent_t e : ctx->ev_free) cudaEventDestroy(e);
   for (auto &kv : ctx->ws)
     if (kv.second.p) cudaFree(kv.second.p);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
-  if (ctx->gstream) {
-    cudaStreamSynchronize(ctx->gstream);
-    cudaStreamDestroy(ctx->gstream);
-  }
+  if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
   for (cudaStream_t b : ctx->bstream)
     if (b) cudaStreamDestroy(b);
   for (cudaEvent_t e : ctx->gev)

@@ -10,7 +10,10 @@ statistics over the per-trajectory results of Context.chain / trajectory.
   gauge forces over all molecular-dynamics evaluations (with measure_forces),
   the quantities whose variances set Var(dH) at order dtau^4 for the
   second-order Omelyan scheme with lambda = 1/6;
-* the average plaquette of the chain's fields.
+* the average plaquette of the chain's fields, with its error from the
+  means of consecutive bins of trajectories (which carries the chain's
+  autocorrelations once the bins are longer than the autocorrelation time),
+  after an optional thermalisation cut.
 """
 import json
 import math
@@ -25,10 +28,28 @@ def _mean_err(x):
     return float(x.mean()), float(x.std(ddof=1) / math.sqrt(x.size))
 
 
-def summarize(results):
-    """Chain statistics from a list of result dicts (hmc_traj_result fields)."""
+def binned_mean_err(x, bin_size):
+    """Mean of x and its standard error from the means of consecutive bins of
+    bin_size entries (a trailing partial bin is dropped); with bin_size 1 the
+    naive error.  (nan, nan) without two full bins."""
+    x = np.asarray(x, dtype=np.float64)
+    b = max(int(bin_size), 1)
+    nb = x.size // b
+    if nb < 2:
+        return float("nan"), float("nan")
+    m = x[:nb * b].reshape(nb, b).mean(axis=1)
+    return float(m.mean()), float(m.std(ddof=1) / math.sqrt(nb))
+
+
+def summarize(results, skip=0, bin_size=1):
+    """Chain statistics from a list of result dicts (hmc_traj_result fields),
+    over the trajectories after the first skip (thermalisation); the
+    plaquette's error from bins of bin_size trajectories."""
+    results = list(results)[max(int(skip), 0):]
     dH = np.array([r["dH"] for r in results], dtype=np.float64)
     out = {"n": int(dH.size)}
+    if skip:
+        out["skipped"] = int(skip)
     if dH.size == 0:
         return out
     acc, acc_err = _mean_err(np.minimum(1.0, np.exp(-dH)))
@@ -46,6 +67,9 @@ def summarize(results):
     # plaquette of the field each trajectory leaves behind
     plaq = [r["plaq1"] if r["accepted"] else r["plaq0"] for r in results]
     out["plaquette"], out["plaquette_err"] = _mean_err(plaq)
+    if bin_size > 1:
+        out["plaquette_bin"] = int(bin_size)
+        out["plaquette_err_binned"] = binned_mean_err(plaq, bin_size)[1]
     for tag in ("pf", "g"):
         n = sum(int(r.get(f"n_f_{tag}", 0)) for r in results)
         if n:

@@ -31,7 +31,9 @@ Run file (every key optional except lattice, beta, kappa):
   start        {"checkpoint": path} or {"eps": 0.3, "seed": 1,
                 "relax": {"beta": 5.85, "trajectories": 40, "steps": 20}}
   chain        {"seed": 1, "n_traj": 10, "block": 10, "spike_threshold": 5.0,
-                "measure_forces": true}
+                "measure_forces": true, "thermalization": 0, "bin": 1}
+               (the summary skips the first "thermalization" trajectories of
+               this run and bins the plaquette in runs of "bin")
   output       {"checkpoint": path, "jsonl": path}
 """
 import json
@@ -92,9 +94,9 @@ def load_config(cfg):
     start.update(cfg.get("start", {}))
     out["start"] = start
     chain = {"seed": 1, "n_traj": 10, "block": 10, "spike_threshold": 5.0,
-             "measure_forces": True}
+             "measure_forces": True, "thermalization": 0, "bin": 1}
     chain.update(cfg.get("chain", {}))
-    if chain["n_traj"] < 0 or chain["block"] < 1:
+    if chain["n_traj"] < 0 or chain["block"] < 1 or chain["thermalization"] < 0 or chain["bin"] < 1:
         raise ValueError(f"chain {chain}")
     out["chain"] = chain
     out["output"] = dict(cfg.get("output", {}))
@@ -226,7 +228,8 @@ def run(cfg, device=0, log=print):
                                 int(chain["seed"]), counter, counter)
         log(json.dumps({"block_end": counter, "accepted": sum(r["accepted"] for r in res),
                         "dH": [round(r["dH"], 6) for r in res]}))
-    summary = metrics.summarize(results)
+    summary = metrics.summarize(results, skip=int(chain["thermalization"]),
+                                bin_size=int(chain["bin"]))
     log(json.dumps({"summary": summary}))
     return results, summary
 

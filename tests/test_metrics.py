@@ -78,3 +78,39 @@ def test_summarize_edge_cases():
     assert s["n"] == 1 and s["var_dH"] == 0.0 and s["acceptance_erfc"] == 1.0
     assert abs(s["acceptance"] - math.exp(-0.3)) < 1e-15 and s["plaquette"] == 0.6
     assert math.isnan(s["acceptance_err"]) and "force_pf2_mean" not in s
+
+
+def test_binned_error_carries_autocorrelation():
+    """On an AR(1) series x_t = rho x_{t-1} + e_t the variance of the mean of N
+    entries is, for N far above the autocorrelation time, sigma^2 (1 + rho) /
+    ((1 - rho) N), with sigma^2 = var(e) / (1 - rho^2): bins much longer than
+    the autocorrelation time recover it, single entries underestimate it by
+    the factor (1 + rho) / (1 - rho)."""
+    rng = np.random.default_rng(3)
+    rho, n = 0.8, 400000
+    e = rng.normal(0.0, 1.0, n)
+    x = np.empty(n)
+    x[0] = e[0] / math.sqrt(1 - rho * rho)
+    for t in range(1, n):
+        x[t] = rho * x[t - 1] + e[t]
+    sigma2 = 1.0 / (1 - rho * rho)
+    want = math.sqrt(sigma2 * (1 + rho) / ((1 - rho) * n))
+    m, err = metrics.binned_mean_err(x, 2000)  # 200 bins: the estimate to ~5 %
+    assert 0.8 < err / want < 1.25
+    assert abs(m) < 5 * want
+    _, naive = metrics.binned_mean_err(x, 1)
+    assert 0.8 < naive / math.sqrt(sigma2 / n) < 1.25
+
+
+def test_binned_error_exact_and_thermalisation_cut():
+    # bins of 4 equal entries alternating 0 and 1: bin means 0, 1, 0, 1
+    x = np.repeat([0.0, 1.0, 0.0, 1.0], 4)
+    m, err = metrics.binned_mean_err(np.append(x, [9.0, 9.0]), 4)  # partial bin dropped
+    assert m == 0.5 and abs(err - math.sqrt(1.0 / 3.0) / 2.0) < 1e-15
+    assert all(math.isnan(v) for v in metrics.binned_mean_err(x, 16))
+    rs = [dict(dH=0.0, accepted=1, plaq0=0.0, plaq1=float(p), cg_iterations=1)
+          for p in [5.0] * 10 + list(x)]
+    s = metrics.summarize(rs, skip=10, bin_size=4)
+    assert s["n"] == 16 and s["skipped"] == 10 and s["plaquette"] == 0.5
+    assert s["plaquette_bin"] == 4
+    assert abs(s["plaquette_err_binned"] - math.sqrt(1.0 / 3.0) / 2.0) < 1e-15
