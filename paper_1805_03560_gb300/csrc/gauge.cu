@@ -233,7 +233,7 @@ static int hopexp_coeffs(hmc_ctx *ctx, const Geo &g, double beta, double kappa, 
 
 int gauge_force(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U, double beta, double kappa, int k,
                 double coeff, double *F) {
-  double beff, cl[4];
+  double beff = beta, cl[4] = {0.0, 0.0, 0.0, 0.0};
   bool lines;
   int st = hopexp_coeffs(ctx, g, beta, kappa, k, &beff, cl, &lines);
   if (st) return st;

@@ -811,7 +811,6 @@ int cg_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
   s.nb_ds = blocks_for(g.Vh, DS_NT);
   s.nb_bl = blocks_for(g.Vh, BL_NT);
   const size_t f64 = spinor_bytes(g, HMC_F64, 1);
-  const size_t flo = spinor_bytes(g, s.plo, 1);
   const size_t f32 = spinor_bytes(g, HMC_F32, 1);
   char *stbuf = (char *)workspace(ctx, "cg_state", sizeof(CGState));
   // end-of-kernel reductions need red_part_len entries (partials + group sums)
@@ -842,7 +841,6 @@ int cg_solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
     s.p = workspace(ctx, "cg_plo", f64);
     s.y = workspace(ctx, "cg_ylo", f64);
     s.tlo = workspace(ctx, "cg_tlo", f64);
-    (void)flo;
     if (!s.xlo || !s.rlo || !s.p || !s.y || !s.tlo) return HMC_ENOMEM;
   }
   // x = 0, r = b, p = r, |b|^2

@@ -440,7 +440,6 @@ int m_read(MSolve &s, MState *h) {
 // r = b - A x for every RHS, restart the recursion from it (p = r_lo = r)
 int m_true_residual(MSolve &s, int par, double tol2) {
   TRY(m_apply_A64(s, s.x, s.q));
-  const bool mixed = s.plo != HMC_F64;
   cudaStream_t st = s.ctx->stream;
   switch (s.plo) {
     case HMC_F64:
@@ -460,7 +459,6 @@ int m_true_residual(MSolve &s, int par, double tol2) {
                                                        s.tmp_part);
       break;
   }
-  (void)mixed;
   TRY(launched(s.ctx, "residual_multi"));
   k_mstate<<<1, FIN_NT, 0, st>>>(s.st, s.tmp_part, s.nb_bl, s.n, par, tol2, 1);
   return launched(s.ctx, "cg_multi_restart");

@@ -114,18 +114,17 @@ static int solve(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gaug
 }
 
 // F += coeff * d/dU 2 Re[A^dag dK B] = coeff kappa^2 (W^dag dH V + h.c.),
-// W = (A, H_eo^dag A), V = (B, H_oe B).  A, B are fields of precision fp, Uf
-// the gauge field of that precision (for the two hemi-Dslashes) and U64 the
-// FP64 links (for the outer products).
-static int pair_force(hmc_ctx *ctx, const Geo &g, const hmc_gauge &U64, const hmc_gauge &Uf,
-                      int fp, double kappa, const void *A, const void *B, double coeff, double *F) {
+// W = (A, H_eo^dag A), V = (B, H_oe B).  A, B are fields of precision fp and
+// Uf the gauge field of that precision, for the two hemi-Dslashes and the
+// outer products alike.
+static int pair_force(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uf, int fp, double kappa,
+                      const void *A, const void *B, double coeff, double *F) {
   // scratch is always requested at its FP64 size so it is never reallocated
   size_t f64 = spinor_bytes(g, HMC_F64, 1);
   void *Wo = workspace(ctx, "pf_wo", f64), *Vo = workspace(ctx, "pf_vo", f64);
   if (!Wo || !Vo) return HMC_ENOMEM;
   TRY(hop(ctx, g, Uf, fp, 1, 1, Wo, A, nullptr, 0.0, 1.0));  // H_eo^dag A
   TRY(hop(ctx, g, Uf, fp, 1, 0, Vo, B, nullptr, 0.0, 1.0));  // H_oe B
-  (void)U64;
   return hop_force(ctx, g, Uf, A, Wo, B, Vo, F, coeff * kappa * kappa, fp);
 }
 
@@ -213,7 +212,7 @@ static int force_filt(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc
       Xp = Xf;
     }
     TRY(mhat(ctx, g, Uf, fp, 0, 1, Y, Xp, tmp, kappa, nullptr, nullptr, nullptr));
-    return pair_force(ctx, g, Uh, Uf, fp, kappa, Y, Xp, coeff, F);
+    return pair_force(ctx, g, Uf, fp, kappa, Y, Xp, coeff, F);
   }
   const int n = filt->n;
   if (n < 0 || !filt->b) return fail(ctx, HMC_EINVAL, "force_pf: bad filter");
@@ -311,7 +310,7 @@ static int force_filt(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc
     TRY(to_fp(phf, phi_a));
     pa = phf;
   }
-  return pair_force(ctx, g, Uh, Uf, fp, kappa_a, w, pa, -coeff, F);
+  return pair_force(ctx, g, Uf, fp, kappa_a, w, pa, -coeff, F);
 }
 
 int action_pf(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul,
