@@ -61,9 +61,10 @@
  * Errors.  Every call returns an hmc_status.  On failure nothing is thrown
  * across the ABI; hmc_last_error(ctx) returns a message.  HMC_EINVAL: bad
  * argument (null or misaligned pointer, odd or too small extent, unsupported
- * precision or format); HMC_ENOMEM: workspace allocation failed; HMC_ENOCONV: a solver hit
- * max_iter (its output holds the last iterate); HMC_ENAN: a reduction saw a
- * NaN or Inf; HMC_ECUDA: a CUDA error (message has the CUDA error string).
+ * precision or format); HMC_ENOMEM: workspace allocation failed;
+ * HMC_ENOCONV: a solver hit max_iter (its output holds the last iterate);
+ * HMC_ENAN: a reduction saw a NaN or Inf; HMC_ECUDA: a CUDA error (message
+ * has the CUDA error string).
  */
 #ifndef HMC_H
 #define HMC_H
@@ -116,7 +117,8 @@ typedef struct {
 /* Create a context on CUDA device `device` (made current for the call).
  * *out receives the handle.  The default stream is the legacy stream 0. */
 int hmc_ctx_create(int device, hmc_ctx **out);
-/* Free the context and its workspace.  Synchronises its stream. */
+/* Free the context and its workspace.  Synchronises its stream and the
+ * streams of its CUDA graphs first. */
 int hmc_ctx_destroy(hmc_ctx *ctx);
 /* Make every later call run on `stream` (a cudaStream_t, may be NULL). */
 int hmc_ctx_set_stream(hmc_ctx *ctx, void *stream);
@@ -135,54 +137,52 @@ long long hmc_host_sync_count(hmc_ctx *ctx);
  * input, output and epilogue spinors, each once) are counted.  Mode 2 (launch
  * timeline): one event after every kernel launch; the time since the previous
  * event (kernel time plus any idle gap before it) is charged to the launch.
- * Mode 3 (sampled): every hemi-Dslash launch is counted with its bytes,
- * those replayed from the CUDA graph of a CG solve included, but only one CG
- * solve in eight (the first of every eight since timing was enabled, run with
- * direct launches) and the hemi-Dslash launches outside CG solves are
- * bracketed by events; the other solves run as in mode 0.  The average
- * duration of a class is its summed time over its event-timed launches, its
- * throughput their bytes over that time (hmc_timing_get_timed).  Modes 1 and 2 launch every kernel directly.
- * Mode 0 switches timing off.  Any call clears the statistics. */
+ * Mode 3 (sampled): every hemi-Dslash launch is counted with its bytes, those
+ * replayed from the CUDA graph of a CG solve included, but only one CG solve in
+ * eight (the first of every eight since timing was enabled, run with direct
+ * launches) and the hemi-Dslash launches outside CG solves are bracketed by
+ * events; the other solves run as in mode 0.  The average duration of a class
+ * is its summed time over its event-timed launches, its throughput their bytes
+ * over that time (hmc_timing_get_timed).  Modes 1 and 2 launch every kernel
+ * directly.  Mode 0 switches timing off.  Any call clears the statistics. */
 int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
 /* Tuning options.  HMC_OPT_DSLASH_VARIANT selects the hemi-Dslash kernel
- * variant: bit 0 maps each block of 128 threads onto four 32-site segments
- * at the offsets {0, +x, +t, +x+t} (when Ly*Lz/2 is a multiple of 32 and
- * n_rhs == 1; otherwise consecutive sites), bit 1 issues the loads of both
- * hops of a direction before their arithmetic (for F16/BF16 storage with
- * 12-real links: of the four hops of two directions).  Variants 0..3 compute the
- * same result bit for bit.  Values 4, 5, 6 select, for n_rhs > 1 and FP32 or
- * FP16 storage, the multi-right-hand-side kernel with 2, 3 or 4 right-hand
- * sides per thread (each link loaded, rebuilt and indexed once for them,
- * packed paired-FP32 arithmetic; exact on exactly representable inputs,
- * otherwise within FP32 rounding of the other variants); where the count
- * does not divide n_rhs the built-in default is used.  Values 7 and 8 are
- * variants 0 and 2 (linear site mapping) whose blocks first ask for a bulk
- * L2 prefetch of the links they will read (12-real FP32, F16 and BF16
- * links, one right-hand side; bit-identical results; elsewhere variant 0 or
- * 2 runs).  Default -1: for
- * n_rhs > 1 in FP32/FP16 the multi-right-hand-side kernel with 2 (else 3)
- * per thread where that divides n_rhs, otherwise paired loads for LINK18
- * only (the fastest choice measured on 24^3 x 48).  -2: autotune: the first
- * launch of
- * each class (precision, link format, dagger, n_rhs, lattice) that can be
- * repeated without changing its result times every applicable variant (one
- * warm-up and three timed launches each, synchronising the stream) and the
- * class keeps the fastest; the solvers tune their classes on scratch fields
- * before iterating.  Launches during stream capture are never tuned. */
+ * variant: bit 0 maps each block of 128 threads onto four 32-site segments at
+ * the offsets {0, +x, +t, +x+t} (when Ly*Lz/2 is a multiple of 32 and n_rhs ==
+ * 1; otherwise consecutive sites), bit 1 issues the loads of both hops of a
+ * direction before their arithmetic (for F16/BF16 storage with 12-real links:
+ * of the four hops of two directions).  Variants 0..3 compute the same result
+ * bit for bit.  Values 4, 5, 6 select, for n_rhs > 1 and FP32 or FP16 storage,
+ * the multi-right-hand-side kernel with 2, 3 or 4 right-hand sides per thread
+ * (each link loaded, rebuilt and indexed once for them, packed paired-FP32
+ * arithmetic; exact on exactly representable inputs, otherwise within FP32
+ * rounding of the other variants); where the count does not divide n_rhs the
+ * built-in default is used.  Values 7 and 8 are variants 0 and 2 (linear site
+ * mapping) whose blocks first ask for a bulk L2 prefetch of the links they will
+ * read (12-real FP32, F16 and BF16 links, one right-hand side; bit-identical
+ * results; elsewhere variant 0 or 2 runs).  Default -1: for n_rhs > 1 in
+ * FP32/FP16 the multi-right-hand-side kernel with 2 (else 3) per thread where
+ * that divides n_rhs, otherwise paired loads for LINK18 only (the fastest
+ * choice measured on 24^3 x 48).  -2: autotune: the first launch of each class
+ * (precision, link format, dagger, n_rhs, lattice) that can be repeated without
+ * changing its result times every applicable variant (one warm-up and three
+ * timed launches each, synchronising the stream) and the class keeps the
+ * fastest; the solvers tune their classes on scratch fields before iterating.
+ * Launches during stream capture are never tuned. */
 #define HMC_OPT_DSLASH_VARIANT 1
 /* HMC_OPT_CG_GRAPH: 1 (default) runs every CG solve of hmc_cg_solve and
- * hmc_cg_solve_multi (and every solve inside the force, action and
- * trajectory calls) as one CUDA graph captured per solve: a while node over the loop body (two
- * iterations and a decision kernel), the reliable update in an if node, the
- * convergence, reliable-update and iteration-limit decisions taken on the
- * device (for a batched solve: for all systems together), the host reading
- * the solver state once at the end.  The graph runs
- * on a stream of the library's own that is ordered after the caller's stream
- * and before its next work.  BiCGstab passes replay one captured iteration
- * in batches of 16, reading the state after each batch.  0 launches every
- * kernel on the caller's stream, the CG in batches of loop bodies with the
- * state read after each (the same kernels on the same data: results are
- * bit-identical).  Graphs are not used in timing modes 1 and 2. */
+ * hmc_cg_solve_multi (and every solve inside the force, action and trajectory
+ * calls) as one CUDA graph captured per solve: a while node over the loop body
+ * (two iterations and a decision kernel), the reliable update in an if node,
+ * the convergence, reliable-update and iteration-limit decisions taken on the
+ * device (for a batched solve: for all systems together), the host reading the
+ * solver state once at the end.  The graph runs on a stream of the library's
+ * own that is ordered after the caller's stream and before its next work.
+ * BiCGstab passes replay one captured iteration in batches of 16, reading the
+ * state after each batch.  0 launches every kernel on the caller's stream, the
+ * CG in batches of loop bodies with the state read after each (the same kernels
+ * on the same data: results are bit-identical).  Graphs are not used in timing
+ * modes 1 and 2. */
 #define HMC_OPT_CG_GRAPH 2
 /* HMC_OPT_PDL: 1 (default) launches the hemi-Dslash kernels and the CG's
  * xpay as programmatic dependent launches: each may be scheduled while the
@@ -211,9 +211,8 @@ int hmc_ctx_set_timing(hmc_ctx *ctx, int enable);
  * is not used).  0 (default): no guards. */
 #define HMC_OPT_WORKSPACE_GUARD 3
 /* Sets option (HMC_OPT_DSLASH_VARIANT: -2..8, HMC_OPT_CG_GRAPH: 0 or 1,
- * HMC_OPT_WORKSPACE_GUARD: 0 or 1, HMC_OPT_PDL: 0 or 1, HMC_OPT_BATCH:
- * 0..2) for
- * every later call on ctx.  HMC_EINVAL for an unknown option or value. */
+ * HMC_OPT_WORKSPACE_GUARD: 0 or 1, HMC_OPT_PDL: 0 or 1, HMC_OPT_BATCH: 0..2)
+ * for every later call on ctx.  HMC_EINVAL for an unknown option or value. */
 int hmc_ctx_set_option(hmc_ctx *ctx, int option, int value);
 /* hmc_workspace_check: synchronises the context's streams and checks the
  * guard regions of its workspace buffers (HMC_OPT_WORKSPACE_GUARD); *n_bad
@@ -288,9 +287,12 @@ int hmc_unpack_algebra(hmc_ctx *ctx, const hmc_lattice *lat, const double *A_dev
  * hmc_dslash: hemi-Dslash (Sec. I, definition of H_xy; Sec. II.B for the
  * even/odd blocks).  out (parity p) = H_{p,1-p} in (parity 1-p); with
  * dagger != 0, out = gamma_5 H_{p,1-p} gamma_5 in = (H_{1-p,p})^dag in.
- * `prec` is the storage precision of in and out (F64 computes in double,
- * F32/F16 in float); U may have any precision and format.  n_rhs fields are
- * processed in one launch, sharing every link load.  out must not alias in. */
+ * `prec` is the storage precision of in and out (F64 computes in double, F64E
+ * in double-float, F32/F16/BF16 in float); U must have the same precision, in
+ * either link format (HMC_EINVAL otherwise).  n_rhs fields are processed in
+ * one launch (for FP32/FP16 storage by default several right-hand sides per
+ * thread, each link loaded once for them; HMC_OPT_DSLASH_VARIANT).  out must
+ * not alias in. */
 int hmc_dslash(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U,
                void *out, const void *in, int out_parity, int dagger, int prec,
                int n_rhs);
@@ -299,8 +301,8 @@ int hmc_dslash(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U,
  * of Sec. I): out = Mhat in, Mhat = 1 - kappa^2 H_eo H_oe, or
  * Mhat^dag = gamma_5 Mhat gamma_5 when dagger != 0.  in/out are even fields.
  * kappas (nullable, host array of n_rhs) gives each right-hand side its own
- * kappa (mass preconditioning); otherwise every RHS uses `kappa`.  Two
- * launches; out must not alias in. */
+ * kappa (mass preconditioning); otherwise every RHS uses `kappa`.  prec and
+ * U as for hmc_dslash.  Two launches; out must not alias in. */
 int hmc_mhat(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U,
              void *out, const void *in, double kappa, int dagger, int prec,
              int n_rhs, const double *kappas);
@@ -402,9 +404,9 @@ int hmc_cg_solve(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
  * converged systems are frozen while the others iterate, and in mixed
  * precision a reliable update is applied to all systems when any of them
  * needs one.  Otherwise (the default) the systems are solved one after
- * another by the single-system solver.  x and phi are F64 even fields with n_rhs right-hand
- * sides (layout above); U_hi/U_lo and opts as for hmc_cg_solve.  stats
- * (nullable) is an array of n_rhs entries.  Blocks. */
+ * another by the single-system solver.  x and phi are F64 even fields with
+ * n_rhs right-hand sides (layout above); U_hi/U_lo and opts as for
+ * hmc_cg_solve.  stats (nullable) is an array of n_rhs entries.  Blocks. */
 int hmc_cg_solve_multi(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
                        const hmc_gauge *U_lo, void *x, const void *phi,
                        const double *kappas, int n_rhs, double tol, int max_iter,
@@ -516,11 +518,13 @@ int hmc_poly_apply(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U,
  * kappa_b).  The calls below take n_terms (1..16) terms at once: phi / eta
  * are n_terms consecutive F64 even fields (n_rhs = 1 layout, field j at byte
  * offset j * hmc_spinor_bytes(lat, HMC_F64, 1)), kappa_a / kappa_b host
- * arrays with 0 <= kappa_a[j] < kappa_b[j] (else HMC_EINVAL).  The terms
- * share the links, so their solves run as multi-right-hand-side CGs (one per
- * solve stage), every hemi-Dslash launch serving all terms.  U_hi, U_lo and
- * opts as for hmc_cg_solve; stats (nullable) sums the stages (per stage the
- * largest count over the batched systems).  Blocking. */
+ * arrays with 0 <= kappa_a[j] < kappa_b[j] (else HMC_EINVAL).  Each solve
+ * stage is one batched solve of the terms (hmc_cg_solve_multi's solver,
+ * HMC_OPT_BATCH: by default one system after another; in lock step every
+ * hemi-Dslash launch serves all terms, which share the links).  U_hi, U_lo
+ * and opts as for hmc_cg_solve; stats (nullable) sums the stages (per stage
+ * the iterations of all systems solved one after another, or in lock step
+ * the largest count over the systems).  Blocking. */
 
 /* F += coeff * sum_j force of S_R(phi_j): with chi = Mhat_b^{-dag} phi,
  * psi = Mhat_a^dag chi, xi = Mhat_b^{-1} Mhat_a psi,

@@ -326,10 +326,13 @@ int hi_mdagm(const HiOps &h, void *out, const void *in, double kappa, int n_rhs,
 int hi_poly_K(const HiOps &h, void *out, const void *in, const double *c, int n, double kappa,
               int dagger = 0);
 
-// batched CG of n_rhs systems with per-system kappas (host array); stats:
-// array of n_rhs (nullable)
 // F64 field <-> right-hand side r of an n-RHS F64 field (to_multi: into it)
 int rhs_copy(hmc_ctx *ctx, const Geo &g, const void *src, void *dst, int n, int r, bool to_multi);
+// whether cg_solve_multi solves these n_rhs systems in lock step (else one
+// after another), from HMC_OPT_BATCH and the kappas; true for one system
+bool multi_lockstep(const hmc_ctx *ctx, const double *kappas, int n_rhs);
+// batched CG of n_rhs systems with per-system kappas (host array); stats:
+// array of n_rhs (nullable)
 int cg_solve_multi(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul, void *x,
                    const void *b, const double *kappas, int n_rhs, double tol, int max_iter,
                    const hmc_solver_opts *opts, hmc_solve_stats *stats);

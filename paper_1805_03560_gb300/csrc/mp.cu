@@ -62,13 +62,21 @@ int mhat64(const HiOps &h, int dagger, void *out, const void *in, double kappa) 
   return hi_mhat(h, dagger, out, in, kappa, 1, nullptr);
 }
 
-void add_stats(hmc_solve_stats *acc, const hmc_solve_stats *s, int n) {
+// statistics of one batched solve stage: in lock step the systems share
+// their iterations (the largest count is the stage's), solved one after
+// another their counts add up
+void add_stats(hmc_solve_stats *acc, const hmc_solve_stats *s, int n, bool lockstep) {
   if (!acc) return;
   int it = 0, ru = 0;
   double rr = 0.0;
   for (int q = 0; q < n; ++q) {
-    it = s[q].iterations > it ? s[q].iterations : it;
-    ru = s[q].reliable_updates > ru ? s[q].reliable_updates : ru;
+    if (lockstep) {
+      it = s[q].iterations > it ? s[q].iterations : it;
+      ru = s[q].reliable_updates > ru ? s[q].reliable_updates : ru;
+    } else {
+      it += s[q].iterations;
+      ru += s[q].reliable_updates;
+    }
     rr = fmax(rr, s[q].true_rel_res);
   }
   acc->iterations += it;
@@ -90,7 +98,7 @@ int first_solves(const HiOps &hi, const hmc_gauge *Ul, const void *phi, int n, c
     TRY(rhs_copy(ctx, g, (const char *)phi + f64 * j, Phi, n, j, true));
   hmc_solve_stats s[16] = {};
   TRY(cg_solve_multi(ctx, g, Uh, Ul, X, Phi, kb, n, tol, 100000, opts, s));
-  add_stats(acc, s, n);
+  add_stats(acc, s, n, multi_lockstep(ctx, kb, n));
   for (int j = 0; j < n; ++j) {
     void *xj = ws_j(ctx, "mp_x", j, f64), *cj = ws_j(ctx, "mp_chi", j, f64);
     if (!xj || !cj) return HMC_ENOMEM;
@@ -146,7 +154,7 @@ int force_mp(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *U
   if (m) {
     hmc_solve_stats st[16] = {};
     TRY(cg_solve_multi(ctx, g, Uh, Ul, Xi, Sm, kbr, m, tol, 100000, opts, st));
-    add_stats(acc, st, m);
+    add_stats(acc, st, m, multi_lockstep(ctx, kbr, m));
   }
   // outer products: v = kappa_b^2 xi - kappa_a^2 psi, all terms in one pass
   const void *Wp[16][2], *Vp[16][2];
@@ -245,7 +253,7 @@ int heatbath_mp(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge
   if (m) {
     hmc_solve_stats st[16] = {};
     TRY(cg_solve_multi(ctx, g, Uh, Ul, X, E, kar, m, tol, 100000, opts, st));
-    add_stats(acc, st, m);
+    add_stats(acc, st, m, multi_lockstep(ctx, kar, m));
   }
   for (int j = 0; j < n; ++j) {
     const void *zj = (const char *)eta + f64 * j;

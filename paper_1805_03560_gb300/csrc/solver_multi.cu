@@ -520,14 +520,19 @@ int solve_separately(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_
 
 }  // namespace
 
+bool multi_lockstep(const hmc_ctx *ctx, const double *kappas, int n_rhs) {
+  if (n_rhs < 2 || ctx->batch == 0) return n_rhs < 2;
+  bool equal = true;
+  for (int q = 1; q < n_rhs; ++q) equal = equal && kappas[q] == kappas[0];
+  return ctx->batch == 1 || equal;
+}
+
 int cg_solve_multi(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_gauge *Ul, void *x,
                    const void *b, const double *kappas, int n_rhs, double tol, int max_iter,
                    const hmc_solver_opts *opts, hmc_solve_stats *stats) {
   if (n_rhs < 1 || n_rhs > NR_MAX)
     return fail(ctx, HMC_EINVAL, "cg_multi: n_rhs must be 1..%d", NR_MAX);
-  bool equal = true;
-  for (int q = 1; q < n_rhs; ++q) equal = equal && kappas[q] == kappas[0];
-  if (n_rhs > 1 && (ctx->batch == 0 || (ctx->batch == 2 && !equal)))
+  if (!multi_lockstep(ctx, kappas, n_rhs))
     return solve_separately(ctx, g, Uh, Ul, x, b, kappas, n_rhs, tol, max_iter, opts, stats);
   MSolve s{};
   s.ctx = ctx;
