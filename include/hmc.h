@@ -609,8 +609,8 @@ int hmc_kinetic(hmc_ctx *ctx, const hmc_lattice *lat, const double *P,
 
 typedef struct {
   double beta, kappa, tau;
-  int n_md;      /* coarse (pseudo-fermion) leapfrog steps per trajectory */
-  int n_gauge;   /* fine gauge steps per coarse step */
+  int n_md;      /* steps of the coarse (outermost) level per trajectory */
+  int n_gauge;   /* fine gauge steps per coarse step (two levels) */
   int filter_k;  /* 0: plain S_PF; 1, 2: kappa^2 / kappa^4 filtering */
   int n_t, n_max;
   const double *b; /* host, b_0 .. b_{n_max} (filter_k > 0) */
@@ -707,10 +707,12 @@ typedef struct {
 } hmc_traj_result;
 
 /* hmc_trajectory: one HMC trajectory (Sec. I): heatbath phi = Mhat^dag eta
- * (plain) or phi = Mhat sum_n c_n K^n eta (filtered); H0; leapfrog on two
- * time scales, T_L = P(dt/2) T(dt) P(dt/2), pseudo-fermion force on the coarse
- * scale and gauge (+ hopping-expansion) force on the fine scale (Sec. I,
- * Sec. IV); H1 with the action solves at tol_action; Metropolis
+ * (plain) or phi = Mhat sum_n c_n K^n eta (filtered); H0; the molecular
+ * dynamics with the integrator of params (leapfrog or Omelyan; two time
+ * scales, the pseudo-fermion forces on the coarse one and the gauge
+ * (+ hopping-expansion) force on the fine one as in Sec. IV, or J levels with
+ * a level per pseudo-fermion term); H1 with the action solves at tol_action;
+ * Metropolis
  * min(1, exp(-dH)) against u.  The random inputs are the caller's: P (algebra
  * field, device, N(0,1) components), eta (F64 even spinor, device, density
  * ~ exp(-|eta|^2)) and u (uniform in [0,1)).  U (F64/LINK18, device) is
@@ -724,8 +726,9 @@ typedef struct {
  * FP64 (double-float on the FP32 units, on an F64E copy of the links); the
  * heatbath, the actions of H0 and H1 and the link updates stay FP64-accurate
  * (native, or emulated with solver.f64_emul).  With
- * params->n_mp > 0, eta holds n_mp + 1 consecutive F64 even fields and the
- * heatbath is phi_j = Mhat_b^dag Mhat_a^{-dag} eta_j (hmc_heatbath_mp).
+ * params->n_mp > 0 or root_levels > 0, eta holds one F64 even field per
+ * pseudo-fermion in the order given at hmc_traj_params (the heavy ratio terms'
+ * heatbath phi_j = Mhat_b^dag Mhat_a^{-dag} eta_j as in hmc_heatbath_mp).
  * Blocks; *res is filled on the host. */
 int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U,
                    const hmc_traj_params *params, const double *P,
@@ -733,12 +736,12 @@ int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U,
                    void *U_end, double *P_end);
 
 /* hmc_md_evolve: the molecular-dynamics part of hmc_trajectory alone: evolve
- * (U, P) in place for tau with the same two-scale leapfrog, the
- * pseudo-fermion field phi held fixed (the phi-algorithm, Sec. I).  With the
+ * (U, P) in place for tau with the integrator of params, the pseudo-fermion
+ * fields phi held fixed (the phi-algorithm, Sec. I).  With the
  * momenta flipped at the end this runs the trajectory backwards, which is the
  * reversibility test of Sec. IV.  U: F64/LINK18; P: algebra field; phi: F64
- * even field (the heatbath output; n_mp + 1 consecutive fields with mass
- * preconditioning); res (nullable) receives cg_iterations and solves.
+ * even fields (the heatbath output, one per pseudo-fermion as eta of
+ * hmc_trajectory); res (nullable) receives cg_iterations and solves.
  * Blocks. */
 int hmc_md_evolve(hmc_ctx *ctx, const hmc_lattice *lat, void *U, double *P,
                   const void *phi, const hmc_traj_params *params,
