@@ -7,7 +7,7 @@
  * Conventions shared by every call
  * --------------------------------
  * Lattice.  hmc_lattice.L = {Lt, Lx, Ly, Lz}; every extent even and >= 2,
- *   Lz >= 2; the volume V = Lt Lx Ly Lz < 2^31.  Site (t, x, y, z) has the
+ *   Lz >= 2; the volume V = Lt Lx Ly Lz < 2^29.  Site (t, x, y, z) has the
  *   lexicographic index ((t*Lx + x)*Ly + y)*Lz + z; direction mu = 0 is time.
  *   Parity (t+x+y+z) mod 2, even = 0; the h-th site of a parity is the site of
  *   that parity with lex >> 1 == h (Vh = V/2 sites per parity).  Fermions are
@@ -251,7 +251,9 @@ int hmc_measure_fma_peak(hmc_ctx *ctx, int kind, double *tflops);
  * unsupported precision / format. */
 size_t hmc_gauge_bytes(const hmc_lattice *lat, int prec, int fmt);
 /* Bytes of a half-lattice (one parity) spinor field of precision prec with
- * n_rhs right-hand sides; 0 as above. */
+ * n_rhs right-hand sides; 0 as above, and 0 when Vh * n_rhs exceeds
+ * 2^31 - 64 elements (the kernels index elements in 32 bits; the calls that
+ * take n_rhs, n_fields or n_terms return HMC_EINVAL there). */
 size_t hmc_spinor_bytes(const hmc_lattice *lat, int prec, int n_rhs);
 /* Bytes of an algebra field (momenta or forces: 8 doubles per link). */
 size_t hmc_algebra_bytes(const hmc_lattice *lat);

@@ -178,7 +178,8 @@ int check_lattice(hmc_ctx *ctx, const hmc_lattice *lat) {
       return fail(ctx, HMC_EINVAL, "lattice extent L[%d] = %d must be even and >= 2", i, l);
     V *= l;
   }
-  if (V >= (1LL << 31)) return fail(ctx, HMC_EINVAL, "lattice volume %lld too large", V);
+  // link-indexed kernels count the 8 Vh = 4 V links of a field in 32 bits
+  if (V >= (1LL << 29)) return fail(ctx, HMC_EINVAL, "lattice volume %lld >= 2^29", V);
   return HMC_OK;
 }
 
@@ -196,6 +197,13 @@ int check_gauge(hmc_ctx *ctx, const hmc_gauge *U) {
     return fail(ctx, HMC_EINVAL, "unsupported link format %d", U->fmt);
   if ((uintptr_t)U->data & 15)
     return fail(ctx, HMC_EINVAL, "gauge field %p is not 16-byte aligned", U->data);
+  return HMC_OK;
+}
+
+int check_elements(hmc_ctx *ctx, const Geo &g, long long n, const char *fn) {
+  if ((long long)g.Vh * n > kMaxElements)
+    return fail(ctx, HMC_EINVAL, "%s: %lld sites x %lld fields exceed 2^31 - 64 elements", fn,
+                (long long)g.Vh, n);
   return HMC_OK;
 }
 
@@ -416,7 +424,9 @@ size_t hmc_gauge_bytes(const hmc_lattice *lat, int prec, int fmt) {
 
 size_t hmc_spinor_bytes(const hmc_lattice *lat, int prec, int n_rhs) {
   if (check_lattice(nullptr, lat) || n_rhs < 1) return 0;
-  return spinor_bytes(make_geo(*lat), prec, n_rhs);
+  const Geo g = make_geo(*lat);
+  if (check_elements(nullptr, g, n_rhs, "spinor_bytes")) return 0;
+  return spinor_bytes(g, prec, n_rhs);
 }
 
 size_t hmc_algebra_bytes(const hmc_lattice *lat) {
@@ -448,6 +458,7 @@ int hmc_pack_spinor(hmc_ctx *ctx, const hmc_lattice *lat, const double *psi_cano
   TRY(check_lattice(ctx, lat));
   if (!psi_canon || !psi_dev || n_rhs < 1) return fail(ctx, HMC_EINVAL, "pack_spinor: bad args");
   TRY(check_aligned(ctx, "pack_spinor", {psi_canon, psi_dev}));
+  TRY(check_elements(ctx, make_geo(*lat), n_rhs, "pack_spinor"));
   return pack_spinor(ctx, make_geo(*lat), psi_canon, psi_dev, prec, n_rhs, true);
 }
 
@@ -458,6 +469,7 @@ int hmc_unpack_spinor(hmc_ctx *ctx, const hmc_lattice *lat, const void *psi_dev,
   if (!psi_canon || !psi_dev || n_rhs < 1)
     return fail(ctx, HMC_EINVAL, "unpack_spinor: bad args");
   TRY(check_aligned(ctx, "unpack_spinor", {psi_dev, psi_canon}));
+  TRY(check_elements(ctx, make_geo(*lat), n_rhs, "unpack_spinor"));
   return pack_spinor(ctx, make_geo(*lat), psi_canon, (void *)psi_dev, prec, n_rhs, false);
 }
 
@@ -488,6 +500,7 @@ int hmc_dslash(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U, void *o
     return fail(ctx, HMC_EINVAL, "dslash: bad arguments");
   if (out == in) return fail(ctx, HMC_EINVAL, "dslash: out must not alias in");
   TRY(check_aligned(ctx, "dslash", {out, in}));
+  TRY(check_elements(ctx, make_geo(*lat), n_rhs, "dslash"));
   DslashArgs a{};
   a.g = make_geo(*lat);
   a.p = out_parity;
@@ -508,6 +521,7 @@ int hmc_mhat(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U, void *out
   if (!out || !in || n_rhs < 1) return fail(ctx, HMC_EINVAL, "mhat: bad arguments");
   if (out == in) return fail(ctx, HMC_EINVAL, "mhat: out must not alias in");
   TRY(check_aligned(ctx, "mhat", {out, in}));
+  TRY(check_elements(ctx, make_geo(*lat), n_rhs, "mhat"));
   Geo g = make_geo(*lat);
   void *tmp = workspace(ctx, "mhat_tmp", spinor_bytes(g, prec, n_rhs));
   if (!tmp) return HMC_ENOMEM;

@@ -67,6 +67,7 @@ int hmc_chain(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj_para
     return fail(ctx, HMC_EINVAL, "chain: bad arguments");
   TRY(check_aligned(ctx, "chain", {U}));
   const Geo g = make_geo(*lat);
+  TRY(traj_check(ctx, g, prm));
   const int nf = traj_eta_fields(prm);
   const size_t ab = (size_t)g.Vh * 2 * 4 * 8 * sizeof(double);
   double *P = (double *)workspace(ctx, "ch_p", ab);

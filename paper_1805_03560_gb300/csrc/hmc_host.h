@@ -124,6 +124,11 @@ int check_gauge(hmc_ctx *ctx, const hmc_gauge *U);
 // is rejected with HMC_EINVAL instead.  NULL entries are skipped (callers
 // check the mandatory ones).
 int check_aligned(hmc_ctx *ctx, const char *fn, std::initializer_list<const void *> ptrs);
+// Fields of n right-hand sides (or n consecutive fields handled in one
+// launch): the kernels index their Vh * n elements in 32 bits, so larger
+// counts are rejected with HMC_EINVAL.
+constexpr long long kMaxElements = (1LL << 31) - 64;
+int check_elements(hmc_ctx *ctx, const Geo &g, long long n, const char *fn);
 
 inline int blocks_for(long long n, int nt) { return (int)((n + nt - 1) / nt); }
 
@@ -373,6 +378,8 @@ struct ForceStats {
 };
 // number of F64 even fields of hmc_trajectory's eta for these parameters
 int traj_eta_fields(const hmc_traj_params *prm);
+// the checks of hmc_trajectory's parameters and of their field count
+int traj_check(hmc_ctx *ctx, const Geo &g, const hmc_traj_params *prm);
 
 // counter-based random numbers (rng.cu)
 int random_momenta(hmc_ctx *ctx, const Geo &g, double *P, uint64_t seed, uint64_t counter);

@@ -15,13 +15,15 @@ namespace hmc {
 
 using C = Cx<double>;
 
-__global__ void k_update_momenta(double *P, const double *F, double eps, int n) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+// algebra fields hold 64 Vh doubles, beyond 32-bit indices on large lattices
+__global__ void k_update_momenta(double *P, const double *F, double eps, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) P[i] = fma(-eps, F[i], P[i]);
 }
 
-__global__ void __launch_bounds__(BL_NT) k_kinetic(const double *P, int n, double *partials) {
-  int i = blockIdx.x * BL_NT + threadIdx.x;
+__global__ void __launch_bounds__(BL_NT) k_kinetic(const double *P, long long n,
+                                                   double *partials) {
+  const long long i = (long long)blockIdx.x * BL_NT + threadIdx.x;
   double s = 0.0;
   if (i < n) s = P[i] * P[i];
   s = block_sum<BL_NT>(s);
@@ -327,13 +329,13 @@ __global__ void k_convert_gauge(Geo g, const void *src, void *dst) {
 }
 
 int update_momenta(hmc_ctx *ctx, const Geo &g, double *P, const double *F, double eps) {
-  int n = 2 * 4 * 8 * g.Vh;
+  const long long n = 64LL * g.Vh;
   k_update_momenta<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(P, F, eps, n);
   return launched(ctx, "update_momenta");
 }
 
 int kinetic_partials(hmc_ctx *ctx, const Geo &g, const double *P, double *partials, int *nb) {
-  int n = 2 * 4 * 8 * g.Vh;
+  const long long n = 64LL * g.Vh;
   *nb = blocks_for(n, BL_NT);
   k_kinetic<<<*nb, BL_NT, 0, ctx->stream>>>(P, n, partials);
   return launched(ctx, "kinetic");

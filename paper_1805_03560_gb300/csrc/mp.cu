@@ -292,6 +292,7 @@ int hmc_force_mp(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
   TRY(mp_args(ctx, lat, U_hi, U_lo, opts));
   if (!phi || !F) return fail(ctx, HMC_EINVAL, "force_mp: NULL field");
   TRY(check_aligned(ctx, "force_mp", {phi, F}));
+  TRY(check_elements(ctx, make_geo(*lat), n_terms, "force_mp"));
   if (stats) *stats = hmc_solve_stats{};
   return force_mp(ctx, make_geo(*lat), *U_hi, U_lo, phi, n_terms, kappa_a, kappa_b, coeff, F, tol,
                   opts, stats);
@@ -304,6 +305,7 @@ int hmc_action_mp(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
   TRY(mp_args(ctx, lat, U_hi, U_lo, opts));
   if (!phi || !action) return fail(ctx, HMC_EINVAL, "action_mp: NULL argument");
   TRY(check_aligned(ctx, "action_mp", {phi}));
+  TRY(check_elements(ctx, make_geo(*lat), n_terms, "action_mp"));
   if (stats) *stats = hmc_solve_stats{};
   return action_mp(ctx, make_geo(*lat), *U_hi, U_lo, phi, n_terms, kappa_a, kappa_b, tol, opts,
                    action, stats);
@@ -317,6 +319,7 @@ int hmc_heatbath_mp(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_gauge *U_hi,
   if (!eta || !phi) return fail(ctx, HMC_EINVAL, "heatbath_mp: NULL field");
   if (eta == phi) return fail(ctx, HMC_EINVAL, "heatbath_mp: phi must not alias eta");
   TRY(check_aligned(ctx, "heatbath_mp", {eta, phi}));
+  TRY(check_elements(ctx, make_geo(*lat), n_terms, "heatbath_mp"));
   if (stats) *stats = hmc_solve_stats{};
   return heatbath_mp(ctx, make_geo(*lat), *U_hi, U_lo, eta, n_terms, kappa_a, kappa_b, tol, opts,
                      phi, stats);

@@ -33,6 +33,7 @@ extern "C" int hmc_mhat_noalloc(hmc_ctx *ctx, const hmc_lattice *lat, const hmc_
   if (out == in) return fail(ctx, HMC_EINVAL, "mhat_noalloc: out must not alias in");
   if ((st = check_aligned(ctx, "mhat_noalloc", {out, in}))) return st;
   const Geo g = make_geo(*lat);
+  if ((st = check_elements(ctx, g, n_rhs, "mhat_noalloc"))) return st;
   const size_t need = spinor_bytes(g, prec, n_rhs);
   if (need > HMC_MHAT_NOALLOC_MAX_BYTES)
     return fail(ctx, HMC_EINVAL,

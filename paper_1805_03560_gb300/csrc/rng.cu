@@ -163,6 +163,7 @@ int hmc_random_sources(hmc_ctx *ctx, const hmc_lattice *lat, void *eta, int n_fi
   if (st) return st;
   if (!eta || n_fields < 1) return fail(ctx, HMC_EINVAL, "random_sources: bad arguments");
   if ((st = check_aligned(ctx, "random_sources", {eta}))) return st;
+  if ((st = check_elements(ctx, make_geo(*lat), n_fields, "random_sources"))) return st;
   return random_sources(ctx, make_geo(*lat), eta, n_fields, seed, counter);
 }
 

@@ -731,6 +731,7 @@ extern "C" int hmc_cg_solve_multi(hmc_ctx *ctx, const hmc_lattice *lat, const hm
   if (!x || !phi || !kappas || max_iter < 1) return fail(ctx, HMC_EINVAL, "cg_multi: bad arguments");
   if (x == phi) return fail(ctx, HMC_EINVAL, "cg_multi: x must not alias phi");
   if ((st = check_aligned(ctx, "cg_multi", {x, phi}))) return st;
+  if ((st = check_elements(ctx, make_geo(*lat), n_rhs, "cg_multi"))) return st;
   if (opts && opts->inner_prec != HMC_F64 && (st = check_gauge(ctx, U_lo))) return st;
   return cg_solve_multi(ctx, make_geo(*lat), *U_hi, U_lo, x, phi, kappas, n_rhs, tol, max_iter,
                         opts, stats);

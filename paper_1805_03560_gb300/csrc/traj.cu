@@ -804,6 +804,12 @@ static int check_traj_params(hmc_ctx *ctx, const hmc_traj_params *prm) {
   return check_prec(ctx, prm->solver.inner_prec);
 }
 
+int traj_check(hmc_ctx *ctx, const Geo &g, const hmc_traj_params *prm) {
+  TRY(check_traj_params(ctx, prm));
+  // the pseudo-fermion fields are drawn, and batched, as one multi-field set
+  return check_elements(ctx, g, n_terms(prm), "trajectory");
+}
+
 }  // namespace hmc
 
 using namespace hmc;
@@ -998,9 +1004,9 @@ int hmc_trajectory(hmc_ctx *ctx, const hmc_lattice *lat, void *U, const hmc_traj
   TRY(check_lattice(ctx, lat));
   if (!U || !prm || !P0 || !eta || !res) return fail(ctx, HMC_EINVAL, "trajectory: NULL argument");
   TRY(check_aligned(ctx, "trajectory", {U, P0, eta, U_end, P_end}));
-  TRY(check_traj_params(ctx, prm));
-  memset(res, 0, sizeof(*res));
   Geo g = make_geo(*lat);
+  TRY(traj_check(ctx, g, prm));
+  memset(res, 0, sizeof(*res));
   const int plo = prm->solver.inner_prec;
   const int fmt_lo = prm->link_fmt_lo ? prm->link_fmt_lo : HMC_LINK12;
   TRY(check_prec(ctx, plo));
@@ -1123,8 +1129,8 @@ extern "C" int hmc_md_evolve(hmc_ctx *ctx, const hmc_lattice *lat, void *U, doub
   TRY(check_lattice(ctx, lat));
   if (!U || !P || !phi || !prm) return fail(ctx, HMC_EINVAL, "md_evolve: NULL argument");
   TRY(check_aligned(ctx, "md_evolve", {U, P, phi}));
-  TRY(check_traj_params(ctx, prm));
   Geo g = make_geo(*lat);
+  TRY(traj_check(ctx, g, prm));
   const int plo = prm->solver.inner_prec;
   const int fmt_lo = prm->link_fmt_lo ? prm->link_fmt_lo : HMC_LINK12;
   const size_t ab = (size_t)g.Vh * 2 * 4 * 8 * sizeof(double);

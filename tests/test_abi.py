@@ -54,6 +54,17 @@ def test_sizes(H):
     assert lib.hmc_gauge_bytes(ctypes.byref(T), H.F32, 12) == 2 * 4 * 32 * 48
     bad = H.lattice((4, 4, 4, 3))
     assert lib.hmc_spinor_bytes(ctypes.byref(bad), H.F64, 1) == 0
+    # the kernels index sites x right-hand sides in 32 bits: 64^3 x 128 has
+    # Vh = 2^24, so 127 right-hand sides fit below 2^31 - 64 and 128 do not
+    big = H.lattice((128, 64, 64, 64))
+    assert lib.hmc_spinor_bytes(ctypes.byref(big), H.F16, 127) == (127 << 24) * 52
+    assert lib.hmc_spinor_bytes(ctypes.byref(big), H.F16, 128) == 0
+    # volumes from 2^29 sites on are rejected (links counted in 32 bits)
+    edge = H.lattice((256, 128, 64, 128))  # V = 2^28
+    assert lib.hmc_algebra_bytes(ctypes.byref(edge)) == (1 << 28) * 4 * 8 * 8
+    over = H.lattice((512, 128, 64, 128))  # V = 2^29
+    assert lib.hmc_algebra_bytes(ctypes.byref(over)) == 0
+    assert lib.hmc_gauge_bytes(ctypes.byref(over), H.F32, 12) == 0
     assert lib.hmc_gauge_bytes(ctypes.byref(L), 7, 18) == 0
 
 
