@@ -258,14 +258,6 @@ int pack_algebra(hmc_ctx *ctx, const Geo &g, const double *c, double *d, bool pa
 
 using namespace hmc;
 
-#define CTX_CHECK(ctx) \
-  if (!(ctx)) return HMC_EINVAL
-#define TRY(e)         \
-  do {                 \
-    int _s = (e);      \
-    if (_s) return _s; \
-  } while (0)
-
 extern "C" {
 
 int hmc_ctx_create(int device, hmc_ctx **out) {

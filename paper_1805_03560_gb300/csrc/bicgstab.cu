@@ -21,12 +21,6 @@
 namespace hmc {
 namespace {
 
-#define TRY(e)         \
-  do {                 \
-    int _s = (e);      \
-    if (_s) return _s; \
-  } while (0)
-
 // <a, b> of one site (re, im) in the arithmetic precision R: per-site sums
 // of the FP32 solver stay on the FP32 units (the FP64 units are a small
 // fraction of them on this GPU); cross-site sums are double

@@ -11,12 +11,6 @@
 
 using namespace hmc;
 
-#define TRY(e)         \
-  do {                 \
-    int _s = (e);      \
-    if (_s) return _s; \
-  } while (0)
-
 namespace {
 
 constexpr size_t kHeaderBytes = 80;

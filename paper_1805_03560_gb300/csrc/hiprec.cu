@@ -11,12 +11,6 @@
 
 namespace hmc {
 
-#define TRY(e)         \
-  do {                 \
-    int _s = (e);      \
-    if (_s) return _s; \
-  } while (0)
-
 int hi_begin(hmc_ctx *ctx, const Geo &g, const hmc_gauge &Uh, const hmc_solver_opts *opts,
              HiOps *h, const char *tag) {
   h->ctx = ctx;

@@ -11,6 +11,16 @@
 
 #include "hmc_internal.cuh"
 
+// Every library function returns an hmc_status: TRY returns a failing one to
+// the caller; CTX_CHECK rejects a NULL context.
+#define TRY(e)         \
+  do {                 \
+    int _s = (e);      \
+    if (_s) return _s; \
+  } while (0)
+#define CTX_CHECK(ctx) \
+  if (!(ctx)) return HMC_EINVAL
+
 struct hmc_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;

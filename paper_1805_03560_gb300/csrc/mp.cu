@@ -22,12 +22,6 @@
 
 namespace hmc {
 
-#define TRY(e)         \
-  do {                 \
-    int _s = (e);      \
-    if (_s) return _s; \
-  } while (0)
-
 // F64 field <-> right-hand side r of an n-RHS F64 field (layout s = h n + r)
 __global__ void k_rhs_copy(const double2 *src, double2 *dst, int Vh, int n, int r, int to_multi) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;

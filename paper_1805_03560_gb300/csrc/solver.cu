@@ -468,12 +468,6 @@ int dot_partials(hmc_ctx *ctx, const void *x, const void *y, int S, double *part
 
 namespace {
 
-#define TRY(e)          \
-  do {                  \
-    int _s = (e);       \
-    if (_s) return _s;  \
-  } while (0)
-
 struct Solve {
   hmc_ctx *ctx;
   Geo g;

@@ -331,12 +331,6 @@ __global__ void __launch_bounds__(BL_NT) k_mfold(void *x, void *y, int S) {
 
 namespace {
 
-#define TRY(e)         \
-  do {                 \
-    int _s = (e);      \
-    if (_s) return _s; \
-  } while (0)
-
 struct MSolve {
   hmc_ctx *ctx;
   Geo g;

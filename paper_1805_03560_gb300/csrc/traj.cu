@@ -9,12 +9,6 @@
 
 namespace hmc {
 
-#define TRY(e)         \
-  do {                 \
-    int _s = (e);      \
-    if (_s) return _s; \
-  } while (0)
-
 static int read_dev(hmc_ctx *ctx, const double *dev, int n, double *host) {
   cudaError_t e =
       cudaMemcpyAsync(ctx->h_pinned, dev, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream);
@@ -813,9 +807,6 @@ int traj_check(hmc_ctx *ctx, const Geo &g, const hmc_traj_params *prm) {
 }  // namespace hmc
 
 using namespace hmc;
-
-#define CTX_CHECK(ctx) \
-  if (!(ctx)) return HMC_EINVAL
 
 static int check_solver_args(hmc_ctx *ctx, const hmc_gauge *U_hi, const hmc_gauge *U_lo,
                              const hmc_solver_opts *opts) {
