@@ -288,13 +288,17 @@ def dslash_source_hash():
 
 def ncu_traffic(kclass):
     """DRAM bytes per launch from the committed ncu summary of this kernel, or
-    None when absent or taken on a different kernel source."""
+    None when absent, taken on a different kernel source or on another lattice
+    (a smaller field stays in L2, so its traffic does not scale with sites)."""
     path = os.path.join(ROOT, "profiles", "dslash_traffic.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
     if not m or m.group(1) != dslash_source_hash():
+        return None
+    m = re.search(r"^lattice:\s*(\S+)", txt, re.M)
+    if not m or m.group(1) != lat_name():
         return None
     for name in (kclass, kclass.split("/")[0]):
         m = re.search(r"^" + re.escape(name) + r"\s+traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt,

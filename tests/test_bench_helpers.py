@@ -1,7 +1,7 @@
 """Host helpers of bench.py that feed the JSON line: the clock sampler's
 parsing of nvidia-smi rows (median SM clock, throttle reasons) and the DRAM
-traffic read from the committed ncu summary (only for the kernel source the
-summary was taken on)."""
+traffic read from the committed ncu summary (only for the kernel source and
+the lattice the summary was taken on)."""
 import os
 import sys
 
@@ -54,5 +54,10 @@ def test_traffic_only_for_the_profiled_source(monkeypatch):
         assert t is None
     monkeypatch.setattr(bench, "dslash_source_hash", lambda: profiled)
     assert bench.ncu_traffic("dslash_f32_12/cg") == pytest.approx(value)
+    # taken on 24^3 x 48 only: another lattice gets no traffic figure
+    assert re.search(r"^lattice:\s*24\^3x48$", txt, re.M)
+    monkeypatch.setattr(bench, "LAT", bench.LATTICES["16x32"])
+    assert bench.ncu_traffic("dslash_f32_12/cg") is None
+    monkeypatch.setattr(bench, "LAT", bench.LATTICES["24x48"])
     monkeypatch.setattr(bench, "dslash_source_hash", lambda: "0000000000000000")
     assert bench.ncu_traffic("dslash_f32_12/cg") is None
