@@ -114,8 +114,11 @@ typedef struct {
 
 /* ---- context --------------------------------------------------------------- */
 
-/* Create a context on CUDA device `device` (made current for the call).
- * *out receives the handle.  The default stream is the legacy stream 0. */
+/* Create a context on CUDA device `device`, which the call makes the current
+ * device of the calling thread and leaves current: every later call on the
+ * context must be made with that device current (its workspace is allocated
+ * on the current device and its kernels run on the context's stream).  *out
+ * receives the handle.  The default stream is the legacy stream 0. */
 int hmc_ctx_create(int device, hmc_ctx **out);
 /* Free the context and its workspace.  Synchronises its stream and the
  * streams of its CUDA graphs first. */

@@ -244,6 +244,10 @@ class Context:
 
     # ---- plumbing -----------------------------------------------------------
     def _stream(self):
+        cur = self.torch.cuda.current_device()
+        if cur != self.device:
+            # the library allocates on, and launches for, the current device
+            raise HmcError(EINVAL, f"context of cuda:{self.device} used with cuda:{cur} current")
         s = self.torch.cuda.current_stream(self.device).cuda_stream
         lib().hmc_ctx_set_stream(self.h, ctypes.c_void_p(s))
 
