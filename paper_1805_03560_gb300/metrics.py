@@ -12,8 +12,9 @@ statistics over the per-trajectory results of Context.chain / trajectory.
   second-order Omelyan scheme with lambda = 1/6;
 * the average plaquette of the chain's fields, with its error from the
   means of consecutive bins of trajectories (which carries the chain's
-  autocorrelations once the bins are longer than the autocorrelation time),
-  after an optional thermalisation cut.
+  autocorrelations once the bins are longer than the autocorrelation time)
+  and from its integrated autocorrelation time, after an optional
+  thermalisation cut.
 """
 import json
 import math
@@ -39,6 +40,29 @@ def binned_mean_err(x, bin_size):
         return float("nan"), float("nan")
     m = x[:nb * b].reshape(nb, b).mean(axis=1)
     return float(m.mean()), float(m.std(ddof=1) / math.sqrt(nb))
+
+
+def integrated_autocorr(x, c=5.0):
+    """Integrated autocorrelation time tau_int = 1/2 + sum_{t=1}^{W} rho(t) of
+    a series (the variance of its mean is 2 tau_int var / N), with the window
+    W chosen automatically as the smallest W >= c tau_int(W) (Madras and
+    Sokal, J. Stat. Phys. 50 (1988) 109).  Returns (tau_int, its error
+    tau_int sqrt((4 W + 2) / N), W); (nan, nan, 0) below 10 entries or for a
+    constant series."""
+    x = np.asarray(x, dtype=np.float64)
+    n = x.size
+    if n < 10:
+        return float("nan"), float("nan"), 0
+    d = x - x.mean()
+    var = float(d @ d) / n
+    if var == 0.0:
+        return float("nan"), float("nan"), 0
+    tau = 0.5
+    for w in range(1, n // 2):
+        tau += float(d[:-w] @ d[w:]) / ((n - w) * var)
+        if w >= c * tau:
+            return tau, tau * math.sqrt((4 * w + 2) / n), w
+    return tau, tau * math.sqrt((4 * (n // 2) + 2) / n), n // 2 - 1
 
 
 def summarize(results, skip=0, bin_size=1):
@@ -70,6 +94,10 @@ def summarize(results, skip=0, bin_size=1):
     if bin_size > 1:
         out["plaquette_bin"] = int(bin_size)
         out["plaquette_err_binned"] = binned_mean_err(plaq, bin_size)[1]
+    tau, tau_err, _ = integrated_autocorr(plaq)
+    if tau > 0.0:  # nan for short or constant series
+        out["plaquette_tau_int"], out["plaquette_tau_int_err"] = tau, tau_err
+        out["plaquette_err_tau"] = math.sqrt(2.0 * tau * float(np.var(plaq)) / len(plaq))
     for tag in ("pf", "g"):
         n = sum(int(r.get(f"n_f_{tag}", 0)) for r in results)
         if n:

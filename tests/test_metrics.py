@@ -114,3 +114,36 @@ def test_binned_error_exact_and_thermalisation_cut():
     assert s["n"] == 16 and s["skipped"] == 10 and s["plaquette"] == 0.5
     assert s["plaquette_bin"] == 4
     assert abs(s["plaquette_err_binned"] - math.sqrt(1.0 / 3.0) / 2.0) < 1e-15
+
+
+def _ar1(rho, n, seed):
+    rng = np.random.default_rng(seed)
+    e = rng.normal(0.0, 1.0, n)
+    x = np.empty(n)
+    x[0] = e[0] / math.sqrt(1 - rho * rho)
+    for t in range(1, n):
+        x[t] = rho * x[t - 1] + e[t]
+    return x
+
+
+@pytest.mark.parametrize("rho", [0.0, 0.5, 0.8])
+def test_integrated_autocorrelation_of_ar1(rho):
+    """AR(1) has rho(t) = rho^t, so tau_int = 1/2 + sum_t rho^t =
+    (1 + rho) / (2 (1 - rho)): 0.5, 1.5 and 4.5 here."""
+    x = _ar1(rho, 200000, 11)
+    tau, err, w = metrics.integrated_autocorr(x)
+    want = (1 + rho) / (2 * (1 - rho))
+    assert abs(tau - want) < 0.05 * want + 3 * err
+    assert w >= 1 and err > 0
+    assert all(math.isnan(v) for v in metrics.integrated_autocorr(np.ones(50))[:2])
+    assert math.isnan(metrics.integrated_autocorr(x[:5])[0])
+
+
+def test_summary_reports_the_plaquette_autocorrelation():
+    x = 0.57 + 1e-3 * _ar1(0.8, 20000, 2)
+    rs = [dict(dH=0.0, accepted=1, plaq0=0.0, plaq1=float(p), cg_iterations=1) for p in x]
+    s = metrics.summarize(rs, bin_size=500)
+    assert abs(s["plaquette_tau_int"] - 4.5) < 1.0
+    # the autocorrelated error and the binned one agree, both well above the naive error
+    assert 0.7 < s["plaquette_err_tau"] / s["plaquette_err_binned"] < 1.4
+    assert s["plaquette_err_tau"] > 2.5 * s["plaquette_err"]
